@@ -1,0 +1,357 @@
+"""Benchmark: W1 solves/s at 512x512 on the GB300 (one JSON line on stdout).
+
+Workload (512x512 image-shaped pairs, 6-level cascade 16->512, both norms):
+one step = a fresh density pair (already resident in HBM) solved with the L1
+and the L2 ground norm, i.e. two full Algorithm-3 solves, each ending with the
+read-back of its W1 value.  The L2 cache is flushed (a 256 MiB write) before
+every step, inside the timed region.
+
+Also measured in the same run:
+  e2e      : the same solves through w1_solve_host (host densities, H2D copies
+             and the D2H result inside the timed region);
+  roofline : the streaming step kernel on an 8192x8192 grid (1.9 GB of state,
+             far above L2), 28 algorithmic bytes per node and step, timed with
+             CUDA events on the stream it is launched on;
+  cpu_baseline: the FP64 oracle on this host's cores, per-level step cost
+             measured on a bounded sample and scaled by the oracle's own
+             per-level iteration counts for the same pairs (oracle/iter_table.json).
+
+--impl reference runs that oracle arm alone (CPU only).
+Multi-GPU (torchrun): every rank solves its own pairs (independent replicas).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 512
+LEVELS = 6
+NORMS = (1, 2)
+WORKLOAD = 2  # synth recipe: ellipses + smoothed noise texture
+METRIC = "W1 solves/s at 512^2 (rel 1e-4); PDHG HBM GB/s vs peak; p50/p99 latency"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_cost(norm_list, pairs, budget_s=12.0):
+    """Seconds per oracle solve for each norm, from per-level step costs
+    measured here (bounded sample) and the oracle's iteration counts."""
+    import oracle
+    import synth
+
+    with open(os.path.join(ROOT, "oracle", "iter_table.json")) as f:
+        table = json.load(f)
+    r0, r1 = synth.pair(WORKLOAD, pairs[0])
+    _, _, d0, d1 = synth.to_f32_pair(r0, r1)
+    rho = d0 - d1
+    rho -= rho.mean()
+    pyr = [rho]
+    for _ in range(LEVELS - 1):
+        pyr.append(oracle.restrict(pyr[-1]))
+    pyr = pyr[::-1]
+    per_norm = {}
+    sample = []
+    per_level_budget = budget_s / (len(norm_list) * LEVELS)
+    for norm in norm_list:
+        counts = np.mean([table[f"{norm}"][str(k)] for k in pairs if str(k) in table[f"{norm}"]], axis=0)
+        total = 0.0
+        for lvl, rl in enumerate(pyr):
+            n = rl.shape[0]
+            h = 1.0 / n
+            z = np.zeros_like(rl)
+            # calibrate the number of steps that fit the budget
+            steps, dt = 8, 0.0
+            while True:
+                t0 = time.perf_counter()
+                oracle.cp_iterate(rl, z, z, z, h, norm, steps)
+                dt = time.perf_counter() - t0
+                if dt > per_level_budget / 4 or steps >= counts[lvl]:
+                    break
+                steps *= 2
+            per_step = dt / steps
+            total += per_step * counts[lvl]
+            sample.append(f"p{norm} {n}^2: {steps} steps")
+        per_norm[norm] = total
+    return per_norm, "; ".join(sample)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    pairs = list(range(4))
+    per_solve, sample = None, None
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        per_norm, sample = oracle_cost(NORMS, pairs, budget_s=args.ref_budget)
+        el = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(sum(per_norm.values()))
+        per_solve = per_norm
+    t_step = float(np.mean(times))
+    value = len(NORMS) / t_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "ellipse_texture_512x512_pair_6_levels_both_norms", "grid": [N, N],
+                   "levels": LEVELS, "norms": ["L1", "L2"], "stop": "FPR, eq. stop_tol"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "per-level step cost timed on a bounded sample (" + sample +
+                                   "), scaled by the oracle's own per-level iteration counts"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "per_solve_s": {f"L{k}": v for k, v in per_solve.items()},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    import synth
+    from paper_1810_00118_gb300 import w1
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    stream = torch.cuda.current_stream()
+    plans = {norm: w1.Plan(N, N, levels=LEVELS, norm=norm) for norm in NORMS}
+    total_steps = args.warmup + args.steps
+    # distinct pairs per step and rank, resident in HBM before timing
+    host_pairs, dev_pairs = [], []
+    for s in range(total_steps):
+        k = rank * 1000 + s
+        r0, r1 = synth.pair(WORKLOAD, k)
+        a0, a1 = (np.ascontiguousarray(x, dtype=np.float32) for x in (r0, r1))
+        host_pairs.append((a0, a1))
+        dev_pairs.append((torch.from_numpy(a0).cuda(), torch.from_numpy(a1).cuda()))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def do_step(s, host=False):
+        flush.fill_(float(s))
+        out = []
+        for norm in NORMS:
+            if host:
+                a0, a1 = host_pairs[s]
+                v, st, _ = plans[norm].solve_host(a0, a1, stream=stream, allow=(w1.OK, w1.ERR_NOT_CONVERGED))
+            else:
+                t0, t1 = dev_pairs[s]
+                v, st, _ = plans[norm].solve(t0, t1, stream=stream, allow=(w1.OK, w1.ERR_NOT_CONVERGED))
+            out.append((v, st))
+        return out
+
+    def launches(st):
+        n = 2 + (st.levels - 1) + st.levels + (st.levels - 1) + 2
+        for p, it in zip(st.path, st.iters):
+            n += 1 if p == 1 else it
+        return n
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for s in range(args.warmup):
+        do_step(s)
+    barrier()
+    results = []
+    step_ms = []
+    with ClockSampler(local) as clk:
+        barrier()
+        t0 = time.perf_counter()
+        for s in range(args.warmup, total_steps):
+            ts = time.perf_counter()
+            results.append(do_step(s))
+            step_ms.append((time.perf_counter() - ts) * 1e3)
+        barrier()
+        elapsed = time.perf_counter() - t0
+    elapsed = max_over_ranks(elapsed)
+    solves = args.steps * len(NORMS) * world
+    value = solves / elapsed
+    n_launch = sum(launches(st) for step in results for _, st in step)
+
+    # end to end through the host entry point
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(args.warmup, total_steps):
+        do_step(s, host=True)
+    barrier()
+    e2e_el = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": solves / e2e_el, "unit": "solves/s",
+           "h2d_bytes_per_step": 2 * N * N * 4 * len(NORMS), "d2h_bytes_per_step": 552 * len(NORMS)}
+
+    # roofline of the streaming step kernel (8192^2, T = 1)
+    roof = None
+    if not args.no_roofline:
+        roof = roofline_stream(w1, torch, stream, args)
+
+    line = None
+    if rank == 0:
+        lat = np.array(step_ms) / len(NORMS)
+        iters = {f"L{n}": results[-1][i][1].iters for i, n in enumerate(NORMS)}
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 iterates, f64 reductions", "data": "synthetic",
+            "config": {"workload": "ellipse_texture_512x512_pair_6_levels_both_norms", "grid": [N, N],
+                       "levels": LEVELS, "norms": ["L1", "L2"], "stop": "FPR, eq. stop_tol",
+                       "l2": "flushed before every step (256 MiB write, inside the timed region)",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "iters": iters,
+            "w1": [[v for v, _ in step] for step in results[:2]],
+            "gpu_launches": n_launch,
+            "e2e": e2e,
+            "roofline": roof,
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline:
+            per_norm, sample = oracle_cost(NORMS, list(range(4)), budget_s=args.ref_budget)
+            cpu_v = len(NORMS) / sum(per_norm.values())
+            line["cpu_baseline"] = {"value": cpu_v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": "per-level step cost timed on a bounded sample (" + sample +
+                                              "), scaled by the oracle's own per-level iteration counts"}
+        print(json.dumps(line), flush=True)
+    for p in plans.values():
+        p.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline_stream(w1, torch, stream, args):
+    n = args.roof_n
+    h = 1.0 / n
+    rng = np.random.default_rng(7)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
+    rho = torch.randn((n, n), device="cuda") * 0.1
+    rho -= rho.mean()
+    m1 = torch.zeros((n, n), device="cuda")
+    m2 = torch.zeros((n, n), device="cuda")
+    phi = torch.zeros((n, n), device="cuda")
+    del rng, dev
+    mu = float(np.float32(0.5 * h / (2 * np.sqrt(2.0))))
+    w1.cp_steps(rho, m1, m2, phi, h, 1, mu, mu, 4, path=2, stream=stream)
+    iters = args.roof_iters
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    w1.cp_steps(rho, m1, m2, phi, h, 1, mu, mu, iters, path=2, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    peak, kind = peaks()
+    achieved = 28.0 * n * n / (ms * 1e-3) / 1e9
+    return {"kernel": "k_step (streaming, T=1)", "grid": [n, n], "bound": "hbm", "achieved": achieved,
+            "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "ms_per_launch": ms, "algorithmic_bytes_per_launch": 28 * n * n}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-roofline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--roof-n", type=int, default=8192)
+    ap.add_argument("--roof-iters", type=int, default=100)
+    ap.add_argument("--ref-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * w1.h -- C ABI of the GB300 multilevel primal-dual Wasserstein-1 solver.
+ *
+ * Method: Liu, Yin, Li, Chow, "Multilevel Optimal Transport: a Fast
+ * Approximation of Wasserstein-1 distances" (arXiv 1810.00118).
+ *   - The problem is the discrete Beckmann (minimal flux) form of W1,
+ *       min_m  sum_x ||m(x)||_p h^2   s.t.  div^h m = rho0 - rho1,
+ *     zero-flux boundary, on a uniform 2-D grid (Sec. 2.2, eq. opt_flux_dis).
+ *   - Each level runs Algorithm 1, the primal-dual iteration of eq. primaldual:
+ *       m   <- prox_{mu||.||_p}(m + mu grad phi)      (shrink toward m + mu grad phi)
+ *       phi <- phi + tau (div(2 m_new - m_old) - rho) (dual ascent, extrapolated residual)
+ *   - Algorithm 3 solves coarse to fine: densities are restricted by 2x2 block
+ *     means, and (m, phi) of level l-1 are interpolated (Sec. 3.3) to start level l.
+ *
+ * Grid and layout (all entry points):
+ *   - nx * ny nodes at pixel centres, spacing h; node (i, j), i along x.
+ *   - Every plane is float32, dense, row-major [ny][nx] (index j*nx + i).
+ *   - A flux is two planes, m1 (x-edges (i,j)->(i+1,j)) then m2 (y-edges
+ *     (i,j)->(i,j+1)); m1[j][nx-1] and m2[ny-1][i] are always 0.
+ *   - Level l of L has (nx, ny) / 2^(L-l) nodes and spacing h * 2^(L-l);
+ *     nx and ny must be divisible by 2^(L-1).
+ *
+ * Stopping rule (Algorithm 1 with eq. pd_stop): after every K-th step the
+ * fixed-point residual R^k of that step is formed on the device (FP64 sums);
+ * level l stops when R^k < eps_l, eps_l = tol * (h_l / h)^alpha
+ * (eq. tol_formula_propose; alpha = -1 and tol from eq. stop_tol are the
+ * paper's choices).  Iteration counts are therefore multiples of K.
+ *
+ * Errors: no entry point aborts; every one returns a w1_status.  The text of
+ * the last error of the calling thread is available from w1_last_error().
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Work is enqueued on it in order; calls that return host values
+ * synchronise with it before returning.
+ */
+#ifndef W1_H_
+#define W1_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define W1_MAX_LEVELS 16
+
+typedef enum {
+    W1_NORM_L1 = 1, /* p = 1, anisotropic: ||m(x)|| = |m1| + |m2|, componentwise shrink */
+    W1_NORM_L2 = 2  /* p = 2, isotropic:  ||m(x)|| = sqrt(m1^2 + m2^2), vector shrink  */
+} w1_norm;
+
+typedef enum {
+    W1_OK = 0,
+    W1_ERR_INVALID_ARG = 1,   /* a NULL pointer, a non-positive size, an unknown norm  */
+    W1_ERR_SHAPE = 2,         /* nx or ny not divisible by 2^(levels-1), or too many levels */
+    W1_ERR_MASS = 3,          /* |M0 - M1| > 1e-6 max(|M0|,|M1|) or a non-finite input   */
+    W1_ERR_NOMEM = 4,         /* device or pinned host allocation failed                 */
+    W1_ERR_CUDA = 5,          /* a CUDA call failed (message in w1_last_error)           */
+    W1_ERR_NOT_CONVERGED = 6, /* a level hit max_iters; dist and stats are still written */
+    W1_ERR_TIMEOUT = 7,       /* a level hit the device wall-clock guard; ditto          */
+    W1_PENDING = 8,           /* w1_poll: the request has not finished                   */
+    W1_ERR_BUDGET = 9,        /* w1_submit: request larger than the server's HBM budget  */
+    W1_ERR_UNSUPPORTED = 10   /* a feature this build or device does not provide         */
+} w1_status;
+
+/* Plan options; w1_default_options() fills the defaults given here. */
+typedef struct {
+    int check_every;       /* K >= 2, even: steps between stop tests (default 32)             */
+    long long max_iters;   /* cap on steps per level (default 1000000)                        */
+    double theta;          /* mu = tau = theta / ||A_h||, ||A_h|| <= 2 sqrt(2) / h (Sec. 4);
+                              0.5 is the paper's choice (default), 1.0 its footnote's         */
+    double alpha;          /* eps_l = tol * (h_l / h)^alpha (default -1)                      */
+    double time_budget_s;  /* device wall-clock guard per level (default 60 s)               */
+    int path;              /* 0 automatic; 1 shared-memory resident; 2 streaming (global)     */
+    int rows_per_thread;   /* streaming kernel: rows marched per thread (0 = automatic)       */
+} w1_options;
+
+/* What a solve reports.  Values are FP64 sums of the FP32 state. */
+typedef struct {
+    int levels;
+    int nx[W1_MAX_LEVELS];          /* level sizes, coarsest first */
+    int ny[W1_MAX_LEVELS];
+    long long iters[W1_MAX_LEVELS]; /* steps taken on each level */
+    double fpr[W1_MAX_LEVELS];      /* R^k at the last stop test of each level */
+    double tol[W1_MAX_LEVELS];      /* eps_l of each level */
+    int path[W1_MAX_LEVELS];        /* 1 resident (cluster size in cluster[]), 2 streaming */
+    int cluster[W1_MAX_LEVELS];
+    double w1;       /* f(m) of the returned finest flux: the W1 estimate (Sec. 5 reports f(m^K)) */
+    double dual;     /* -<phi, rho>_h of the returned potential */
+    double lb;       /* certified lower bound on the discrete W1: dual / max(1, gmax) */
+    double ub;       /* certified upper bound: w1 + route */
+    double route;    /* cost of an explicit flux carrying the residual rho - div m */
+    double res_l1;   /* sum |rho - div m| h^2 */
+    double rho_l1;   /* sum |rho| h^2 */
+    double gmax;     /* max over nodes of ||grad phi(x)||_q (q dual to p) */
+    double mass0;    /* sum rho0 h^2 */
+    double mass1;    /* sum rho1 h^2 */
+    double mass_shift; /* mean of rho0 - rho1 removed so that the constraint is solvable */
+    int converged;   /* 1 when every level met its tolerance */
+} w1_stats;
+
+typedef struct w1_plan w1_plan;
+
+/* Fills *opt with the defaults documented in w1_options. */
+void w1_default_options(w1_options* opt);
+
+/*
+ * Creates a plan for nx x ny grids (Algorithm 3 input, Sec. 3.2).
+ *   h      : finest spacing; <= 0 means 1 / max(nx, ny).
+ *   levels : L; <= 0 means the paper's L = log2(1/h) - 3 (Sec. 5.3), reduced
+ *            until nx and ny are divisible by 2^(L-1) and the coarsest side >= 2.
+ *   norm   : W1_NORM_L1 or W1_NORM_L2.
+ *   tol    : eps_L of the finest level; <= 0 means eq. stop_tol for Alg. 3,
+ *            eps_L = 1e-6/128 * (512 h)^2.
+ * The plan owns its device workspace (allocated on the current device) unless
+ * w1_plan_set_workspace() hands it one.  Returns W1_ERR_SHAPE on bad sizes.
+ */
+w1_status w1_plan_create(int nx, int ny, double h, int levels, int norm, double tol, w1_plan** out);
+w1_status w1_plan_create_ex(int nx, int ny, double h, int levels, int norm, double tol, const w1_options* opt,
+                            w1_plan** out);
+w1_status w1_plan_destroy(w1_plan* plan);
+
+/* Bytes of device workspace the plan needs (levels' state, reductions). */
+size_t w1_plan_workspace_bytes(const w1_plan* plan);
+/* Use caller-owned device memory (>= w1_plan_workspace_bytes, 256-byte aligned)
+ * instead of the plan's own; the caller keeps it alive until the plan dies. */
+w1_status w1_plan_set_workspace(w1_plan* plan, void* device_ptr, size_t bytes);
+
+/*
+ * One W1 solve (Algorithm 3), enqueued on `stream`.
+ *   rho0, rho1 : device, [ny][nx] float32 densities, caller-owned, read only.
+ *   dist       : host; receives the W1 estimate f(m) (blocks until the stream
+ *                reaches the end of the solve).
+ *   flux       : device [2][ny][nx] float32 (m1 then m2) or NULL.
+ *   stats      : host or NULL.
+ * Returns W1_OK, W1_ERR_MASS (nothing solved), W1_ERR_NOT_CONVERGED or
+ * W1_ERR_TIMEOUT (dist and stats still written), or an error.
+ */
+w1_status w1_solve(w1_plan* plan, const float* rho0, const float* rho1, void* stream, double* dist, float* flux,
+                   w1_stats* stats);
+
+/* Same as w1_solve, for densities and flux in (pageable or pinned) host
+ * memory: the copies to and from the device are part of the call. */
+w1_status w1_solve_host(w1_plan* plan, const float* rho0, const float* rho1, void* stream, double* dist,
+                        float* flux, w1_stats* stats);
+
+/* Final potential phi of the last solve, device [ny][nx] float32 (the
+ * Kantorovich potential of Algorithm 1, Appendix B); enqueued on stream. */
+w1_status w1_plan_potential(w1_plan* plan, float* phi, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Building blocks (device pointers, float32 planes [ny][nx]); used by the   */
+/* parity tests and by callers that drive the levels themselves.             */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * `iters` steps of eq. primaldual in place on (m1, m2, phi) with density rho,
+ * step sizes mu, tau, spacing h.  path: 1 shared-memory resident (grids up to
+ * 16 * 4096 nodes), 2 streaming.  If fpr_last is not NULL it receives R^k of
+ * the last step (FP64 sums).  The boundary flux entries must be 0 on entry.
+ */
+w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, float tau, const float* rho, float* m1,
+                      float* m2, float* phi, long long iters, int path, void* stream, double* fpr_last);
+
+/* coarse[ny/2][nx/2] = mean of each 2x2 block of fine[ny][nx] (density restriction). */
+w1_status w1_restrict(int nx, int ny, const float* fine, float* coarse, void* stream);
+
+/* Interpolate (Sec. 3.3, pixel-grid restatement) from a coarse ncx x ncy state
+ * to the fine 2ncx x 2ncy state; see the oracle for the rules. */
+w1_status w1_prolong(int ncx, int ncy, const float* m1c, const float* m2c, const float* phic, float* m1f,
+                     float* m2f, float* phif, void* stream);
+
+/* Statistics of a state (fields w1, dual, lb, ub, route, res_l1, rho_l1, gmax
+ * of *out), rho already balanced; blocks until done. */
+w1_status w1_state_stats(int nx, int ny, double h, int norm, const float* rho, const float* m1, const float* m2,
+                         const float* phi, void* stream, w1_stats* out);
+
+/* Text for a status, and the last error message of the calling thread. */
+const char* w1_status_string(w1_status s);
+const char* w1_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* W1_H_ */

@@ -423,15 +423,16 @@ static int converged(int stop_mode, const w1o_stats_t* st, double tol)
 }
 
 /* Algorithm 1 on one level, started from (m1, m2, phi), in place.
- * Every `check_every` steps (and before the first) the state z^k = (m^k, phi^k)
- * is tested:
- *   gap mode : (UB - min(LB, f)) <= tol * UB, i.e. f(m^k) is within a relative
- *              tol of the exact discrete W1_h (certified);
- *   fpr mode : R^k < tol with R^k of the step z^k -> z^{k+1} (eq. pd_stop).
- * In gap mode the level returns z^k; in fpr mode it returns z^{k+1} (the
- * paper's loop stops after the step whose residual is small).
- * If replay >= 0 the test is skipped and exactly `replay` steps are taken.
- * Returns W1O_OK or W1O_NOT_CONVERGED (max_iters steps without passing). */
+ * The stop test runs after every `check_every`-th step (k = K, 2K, ...), on the
+ * step just taken (z^{k-1} -> z^k):
+ *   fpr mode : R of eq. pd_stop for that step is below tol (the paper's rule;
+ *              testing every K-th step instead of every step only delays the
+ *              stop by less than K steps, since R^k is non-increasing);
+ *   gap mode : (UB - min(LB, f)) <= tol * UB for z^k, i.e. f(m^k) is within a
+ *              relative tol of the exact discrete W1_h (certified).
+ * The level returns z^k.  If replay >= 0 the test is skipped and exactly
+ * `replay` steps are taken.  Returns W1O_OK, or W1O_NOT_CONVERGED when
+ * max_iters steps passed without the test passing. */
 int w1o_solve_level(int nx, int ny, double h, int norm, double theta, const double* rho, double* m1, double* m2,
                     double* phi, double tol, int stop_mode, int check_every, long max_iters, long replay,
                     long* iters_out, w1o_stats_t* stats_out)
@@ -445,39 +446,39 @@ int w1o_solve_level(int nx, int ny, double h, int norm, double theta, const doub
     }
     int status = W1O_NOT_CONVERGED;
     long k = 0;
-    w1o_stats_t st;
-    memset(&st, 0, sizeof(st));
+    double last_fpr = 0.0;
     if (replay >= 0) {
         for (k = 0; k < replay; ++k) cp_step(&s, h, norm, mu, tau, rho, m1, m2, phi, NULL);
         status = W1O_OK;
     } else {
         for (;;) {
-            if (k % check_every == 0) {
-                w1o_stats(nx, ny, h, norm, rho, m1, m2, phi, &st);
-                if (stop_mode == W1O_STOP_FPR) {
-                    double fpr = 0.0;
-                    cp_step(&s, h, norm, mu, tau, rho, m1, m2, phi, &fpr);
-                    ++k;
-                    st.fpr = fpr;
-                    if (converged(stop_mode, &st, tol)) {
-                        status = W1O_OK;
-                        break;
-                    }
-                    if (k >= max_iters) break;
-                    continue;
-                }
-                if (converged(stop_mode, &st, tol)) {
-                    status = W1O_OK;
-                    break;
-                }
-                if (k >= max_iters) break;
-            }
-            cp_step(&s, h, norm, mu, tau, rho, m1, m2, phi, NULL);
+            const int check = ((k + 1) % check_every == 0);
+            double fpr = 0.0;
+            cp_step(&s, h, norm, mu, tau, rho, m1, m2, phi, check ? &fpr : NULL);
             ++k;
+            if (!check) continue;
+            last_fpr = fpr;
+            int ok;
+            if (stop_mode == W1O_STOP_FPR) {
+                ok = fpr < tol;
+            } else {
+                w1o_stats_t st;
+                w1o_stats(nx, ny, h, norm, rho, m1, m2, phi, &st);
+                st.fpr = fpr;
+                ok = converged(stop_mode, &st, tol);
+            }
+            if (ok) {
+                status = W1O_OK;
+                break;
+            }
+            if (k >= max_iters) break;
         }
     }
     if (iters_out) *iters_out = k;
-    if (stats_out) w1o_stats(nx, ny, h, norm, rho, m1, m2, phi, stats_out);
+    if (stats_out) {
+        w1o_stats(nx, ny, h, norm, rho, m1, m2, phi, stats_out);
+        stats_out->fpr = last_fpr;
+    }
     scratch_free(&s);
     return status;
 }

@@ -1,0 +1,95 @@
+// w1_internal.h -- declarations shared by the kernels and the host driver of the
+// GB300 W1 library (not part of the public ABI; include/w1.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/w1.h"
+
+namespace w1 {
+
+// Device-resident control block of one plan: reduction counter, error flags,
+// per-level iteration counts and residuals, and the final statistics.
+struct Ctl {
+    unsigned int counter;  // last-block counter of the grid reductions (reset by the last block)
+    int error;             // 1: rejected input (mass imbalance or non-finite value)
+    int timeout;           // 1: a level hit the wall-clock guard
+    int pad0;
+    double mass0, mass1, mean;
+    long long iters[W1_MAX_LEVELS];
+    double fpr[W1_MAX_LEVELS];
+    int conv[W1_MAX_LEVELS];
+    unsigned long long t_start[W1_MAX_LEVELS];
+    // final statistics of the returned finest state
+    double f, dual, res_l1, rho_l1, gmax, route, lb, ub;
+};
+
+// Iteration arguments shared by both level paths.
+struct IterArgs {
+    int nx, ny;
+    float mu, tau, ih;  // step sizes and 1/h, as the FP32 iteration uses them
+    double h;           // spacing for the FP64 residual sums
+    double tol;         // eps_l
+    long long cap;      // max steps (or the exact step count when fixed)
+    int K;              // steps between stop tests
+    int fixed;          // 1: take exactly `cap` steps, form R^k of the last one
+    int level;
+    unsigned long long budget_ns;
+    Ctl* ctl;
+    double* fpr_out;       // optional (device): R^k of the last tested step
+    long long* iters_out;  // optional (device)
+};
+
+// Streaming (global memory) one-step kernel arguments.
+struct StepArgs {
+    const float* m1;
+    const float* m2;
+    const float* phi;
+    const float* rho;
+    float* m1o;
+    float* m2o;
+    float* phio;
+    int rows;  // rows marched per thread
+    IterArgs it;
+    double* part;  // per-block partials (check step)
+    cudaGraphConditionalHandle cond;
+    int use_cond;
+};
+
+// Shared-memory resident level solver arguments (state in place).
+struct ResArgs {
+    float* m1;
+    float* m2;
+    float* phi;
+    const float* rho;
+    IterArgs it;
+};
+
+// Kernel launchers (w1_kernels.cu).  All enqueue on `s` and return the launch status.
+cudaError_t launch_prep(const float* r0, const float* r1, long long n, double h, Ctl* ctl, double* part,
+                        float* rho, cudaStream_t s);
+cudaError_t launch_restrict(const float* fine, int nx, int ny, float* coarse, cudaStream_t s);
+cudaError_t launch_prolong(int ncx, int ncy, const float* m1c, const float* m2c, const float* phic, float* m1f,
+                           float* m2f, float* phif, cudaStream_t s);
+cudaError_t launch_level_begin(Ctl* ctl, int level, cudaStream_t s);
+// Streaming step; check selects the variant that forms R^k and tests it.
+cudaError_t launch_step(int norm, bool check, const StepArgs& a, cudaStream_t s);
+int stream_rows_auto(int nx, int ny);
+dim3 stream_grid(int nx, int ny, int rows);
+// Resident level solve with a cluster of `cluster` CTAs.
+cudaError_t launch_resident(int norm, int cluster, const ResArgs& a, cudaStream_t s);
+// Largest band (nodes per CTA) the resident kernel takes, and the cluster size
+// it would use for a level (0 when the level does not fit).
+int resident_max_nodes();
+int resident_cluster_for(int nx, int ny);
+cudaError_t resident_prepare(int device);
+// Active clusters the device can hold for this configuration (0: cannot launch).
+int resident_cluster_ok(int norm, int cluster, int nx, int ny);
+// Final statistics of a state into ctl (q: FP64 scratch of 2 * nx * ny).
+cudaError_t launch_final(int norm, const float* m1, const float* m2, const float* phi, const float* rho, int nx,
+                         int ny, double h, double* q, double* part, Ctl* ctl, cudaStream_t s);
+size_t final_part_doubles();
+size_t step_part_doubles(int nx, int ny, int rows);
+
+}  // namespace w1

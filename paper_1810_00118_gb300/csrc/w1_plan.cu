@@ -1,0 +1,693 @@
+// w1_plan.cu -- host driver and C ABI of the GB300 multilevel W1 solver.
+//
+// A plan fixes the grid, the level hierarchy of Algorithm 3 (h_l = 2^{L-l} h,
+// Sec. 3.2), the norm and the tolerances, and owns one device arena:
+//   control block | partial sums | FP64 scratch for the final certificate |
+//   per level: rho_l, state A (m1, m2, phi), state B (streaming levels only).
+// The level sequence (restriction, level starts, level solves) is captured once
+// into a CUDA graph.  Resident levels are single cluster launches that run to
+// their stop test on the device; streaming levels are conditional WHILE nodes
+// whose body is K steps, the last of which forms R^k and sets the condition.
+// A solve is: prep (rho = rho0 - rho1, mass check) -> graph -> final
+// statistics -> one device-to-host copy of the control block.  No host
+// synchronisation happens between the first and the last of these.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "w1_internal.h"
+
+using namespace w1;
+
+namespace {
+
+thread_local std::string g_err;
+
+w1_status fail(w1_status s, const std::string& msg)
+{
+    g_err = msg;
+    return s;
+}
+
+#define W1_CK(call)                                                                                \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            cudaGetLastError();                                                                    \
+            return fail(e_ == cudaErrorMemoryAllocation ? W1_ERR_NOMEM : W1_ERR_CUDA,              \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+        }                                                                                          \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+std::mutex g_prep_mu;
+bool g_prepared[64] = {};
+
+w1_status prepare_device(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_prep_mu);
+    if (dev >= 0 && dev < 64 && g_prepared[dev]) return W1_OK;
+    W1_CK(resident_prepare(dev));
+    if (dev >= 0 && dev < 64) g_prepared[dev] = true;
+    return W1_OK;
+}
+
+}  // namespace
+
+struct LevelPlan {
+    int nx, ny;
+    double h;
+    float mu, tau;
+    double tol;
+    int path;     // 1 resident, 2 streaming
+    int cluster;  // resident cluster size
+    int rows;     // streaming march length
+    float* rho;
+    float* m1[2];
+    float* m2[2];
+    float* phi[2];
+};
+
+struct w1_plan {
+    int device;
+    int nx, ny, L, norm;
+    double h, tol;
+    w1_options opt;
+    LevelPlan lv[W1_MAX_LEVELS];
+    size_t ws_bytes;
+    char* ws;
+    bool own_ws;
+    Ctl* ctl;
+    double* part;
+    size_t part_doubles;
+    double* q;
+    Ctl* host_ctl;
+    cudaStream_t cap_stream;
+    cudaStream_t body_stream;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    bool graph_ok;
+    float* in0;
+    float* in1;
+    float* flux_d;
+};
+
+extern "C" void w1_default_options(w1_options* o)
+{
+    if (!o) return;
+    o->check_every = 32;
+    o->max_iters = 1000000;
+    o->theta = 0.5;
+    o->alpha = -1.0;
+    o->time_budget_s = 60.0;
+    o->path = 0;
+    o->rows_per_thread = 0;
+}
+
+extern "C" const char* w1_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* w1_status_string(w1_status s)
+{
+    switch (s) {
+    case W1_OK: return "ok";
+    case W1_ERR_INVALID_ARG: return "invalid argument";
+    case W1_ERR_SHAPE: return "grid not divisible by 2^(levels-1)";
+    case W1_ERR_MASS: return "mass imbalance or non-finite density";
+    case W1_ERR_NOMEM: return "out of memory";
+    case W1_ERR_CUDA: return "CUDA error";
+    case W1_ERR_NOT_CONVERGED: return "iteration cap reached";
+    case W1_ERR_TIMEOUT: return "device time budget reached";
+    case W1_PENDING: return "pending";
+    case W1_ERR_BUDGET: return "over the memory budget";
+    case W1_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+// Carves the arena: control block, partials, FP64 certificate scratch, levels.
+static size_t layout(w1_plan* p, char* base)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        off = align_up(off, 256);
+        char* r = base ? base + off : nullptr;
+        off += bytes;
+        return r;
+    };
+    p->ctl = reinterpret_cast<Ctl*>(take(sizeof(Ctl)));
+    size_t pd = final_part_doubles();
+    if (pd < 304 * 4) pd = 304 * 4;
+    for (int l = 0; l < p->L; ++l)
+        if (p->lv[l].path == 2) {
+            size_t s = step_part_doubles(p->lv[l].nx, p->lv[l].ny, p->lv[l].rows);
+            if (s > pd) pd = s;
+        }
+    p->part_doubles = pd;
+    p->part = reinterpret_cast<double*>(take(pd * sizeof(double)));
+    const size_t n = (size_t)p->nx * p->ny;
+    p->q = reinterpret_cast<double*>(take(2 * n * sizeof(double)));
+    for (int l = 0; l < p->L; ++l) {
+        LevelPlan& v = p->lv[l];
+        const size_t b = (size_t)v.nx * v.ny * sizeof(float);
+        v.rho = reinterpret_cast<float*>(take(b));
+        const int nb = v.path == 2 ? 2 : 1;
+        for (int s = 0; s < 2; ++s) {
+            v.m1[s] = s < nb ? reinterpret_cast<float*>(take(b)) : nullptr;
+            v.m2[s] = s < nb ? reinterpret_cast<float*>(take(b)) : nullptr;
+            v.phi[s] = s < nb ? reinterpret_cast<float*>(take(b)) : nullptr;
+        }
+    }
+    return align_up(off, 256);
+}
+
+static w1_status bind_arena(w1_plan* p, char* base, size_t bytes)
+{
+    if (bytes < p->ws_bytes) return fail(W1_ERR_INVALID_ARG, "workspace smaller than w1_plan_workspace_bytes");
+    if (reinterpret_cast<uintptr_t>(base) % 256 != 0) return fail(W1_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+    layout(p, base);
+    p->ws = base;
+    W1_CK(cudaMemset(p->ctl, 0, sizeof(Ctl)));
+    return W1_OK;
+}
+
+extern "C" w1_status w1_plan_create_ex(int nx, int ny, double h, int levels, int norm, double tol,
+                                       const w1_options* opt, w1_plan** out)
+{
+    if (!out) return fail(W1_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1) return fail(W1_ERR_INVALID_ARG, "nx and ny must be >= 1");
+    if (norm != W1_NORM_L1 && norm != W1_NORM_L2) return fail(W1_ERR_INVALID_ARG, "norm must be 1 or 2");
+    w1_options o;
+    w1_default_options(&o);
+    if (opt) o = *opt;
+    if (o.check_every < 2 || (o.check_every & 1)) return fail(W1_ERR_INVALID_ARG, "check_every must be even and >= 2");
+    if (!(o.theta > 0.0) || o.theta > 1.0) return fail(W1_ERR_INVALID_ARG, "theta must lie in (0, 1]");
+    if (o.max_iters < 1) return fail(W1_ERR_INVALID_ARG, "max_iters must be >= 1");
+    if (o.path < 0 || o.path > 2) return fail(W1_ERR_INVALID_ARG, "path must be 0, 1 or 2");
+    if (!(h > 0.0)) h = 1.0 / (double)(nx > ny ? nx : ny);
+    if (levels <= 0) {
+        // the paper's L = log2(1/h) - 3 (Sec. 5.3), kept divisible
+        int L = (int)std::lround(std::log2(1.0 / h)) - 3;
+        if (L < 1) L = 1;
+        while (L > 1 && ((nx % (1 << (L - 1))) || (ny % (1 << (L - 1))) || (nx >> (L - 1)) < 2 ||
+                         (ny >> (L - 1)) < 2))
+            --L;
+        levels = L;
+    }
+    if (levels > W1_MAX_LEVELS) return fail(W1_ERR_SHAPE, "at most 16 levels");
+    const int div = 1 << (levels - 1);
+    if (nx % div || ny % div) return fail(W1_ERR_SHAPE, "nx and ny must be divisible by 2^(levels-1)");
+    if (!(tol > 0.0)) tol = 1e-6 / 128.0 * (512.0 * h) * (512.0 * h);  // eq. stop_tol, Alg. 3
+
+    int dev = 0;
+    W1_CK(cudaGetDevice(&dev));
+    w1_status st = prepare_device(dev);
+    if (st != W1_OK) return st;
+
+    w1_plan* p = new (std::nothrow) w1_plan();
+    if (!p) return fail(W1_ERR_NOMEM, "host allocation failed");
+    p->device = dev;
+    p->nx = nx;
+    p->ny = ny;
+    p->L = levels;
+    p->norm = norm;
+    p->h = h;
+    p->tol = tol;
+    p->opt = o;
+    for (int l = 0; l < levels; ++l) {
+        LevelPlan& v = p->lv[l];
+        const int sh = levels - 1 - l;
+        v.nx = nx >> sh;
+        v.ny = ny >> sh;
+        v.h = h * (double)(1 << sh);
+        const double mu = o.theta * v.h / (2.0 * std::sqrt(2.0));  // theta / ||A_h||, ||A_h|| <= 2 sqrt(2) / h
+        v.mu = (float)mu;
+        v.tau = (float)mu;
+        v.tol = tol * std::pow(v.h / h, o.alpha);  // eq. tol_formula_propose
+        int c = resident_cluster_for(v.nx, v.ny);
+        if (c > 0 && resident_cluster_ok(norm, c, v.nx, v.ny) <= 0) c = 0;
+        if (o.path == 1 && c == 0) {
+            delete p;
+            return fail(W1_ERR_UNSUPPORTED, "level too large for the resident path");
+        }
+        v.path = (o.path == 2 || c == 0) ? 2 : 1;
+        v.cluster = v.path == 1 ? c : 0;
+        v.rows = o.rows_per_thread > 0 ? o.rows_per_thread : stream_rows_auto(v.nx, v.ny);
+    }
+    p->ws_bytes = layout(p, nullptr);
+    p->own_ws = false;
+    p->ws = nullptr;
+    char* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, p->ws_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return fail(W1_ERR_NOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+    }
+    st = bind_arena(p, base, p->ws_bytes);
+    if (st != W1_OK) {
+        cudaFree(base);
+        delete p;
+        return st;
+    }
+    p->own_ws = true;
+    e = cudaMallocHost(&p->host_ctl, sizeof(Ctl));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->body_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        w1_plan_destroy(p);
+        return fail(W1_ERR_CUDA, std::string("plan streams: ") + cudaGetErrorString(e));
+    }
+    *out = p;
+    return W1_OK;
+}
+
+extern "C" w1_status w1_plan_create(int nx, int ny, double h, int levels, int norm, double tol, w1_plan** out)
+{
+    return w1_plan_create_ex(nx, ny, h, levels, norm, tol, nullptr, out);
+}
+
+extern "C" w1_status w1_plan_destroy(w1_plan* p)
+{
+    if (!p) return W1_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->body_stream) cudaStreamDestroy(p->body_stream);
+    if (p->host_ctl) cudaFreeHost(p->host_ctl);
+    if (p->own_ws && p->ws) cudaFree(p->ws);
+    if (p->in0) cudaFree(p->in0);
+    if (p->in1) cudaFree(p->in1);
+    if (p->flux_d) cudaFree(p->flux_d);
+    cudaGetLastError();
+    cudaSetDevice(cur);
+    delete p;
+    return W1_OK;
+}
+
+extern "C" size_t w1_plan_workspace_bytes(const w1_plan* p) { return p ? p->ws_bytes : 0; }
+
+extern "C" w1_status w1_plan_set_workspace(w1_plan* p, void* dev, size_t bytes)
+{
+    if (!p || !dev) return fail(W1_ERR_INVALID_ARG, "NULL plan or workspace");
+    char* old = p->ws;
+    const bool old_own = p->own_ws;
+    w1_status st = bind_arena(p, static_cast<char*>(dev), bytes);
+    if (st != W1_OK) {
+        layout(p, old);
+        p->ws = old;
+        return st;
+    }
+    if (old_own && old) cudaFree(old);
+    p->own_ws = false;
+    // the graph holds the old addresses
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->exec = nullptr;
+    p->graph = nullptr;
+    p->graph_ok = false;
+    return W1_OK;
+}
+
+static IterArgs iter_args(const w1_plan* p, int l)
+{
+    const LevelPlan& v = p->lv[l];
+    IterArgs it{};
+    it.nx = v.nx;
+    it.ny = v.ny;
+    it.mu = v.mu;
+    it.tau = v.tau;
+    it.ih = (float)(1.0 / v.h);
+    it.h = v.h;
+    it.tol = v.tol;
+    it.cap = p->opt.max_iters;
+    it.K = p->opt.check_every;
+    it.fixed = 0;
+    it.level = l;
+    it.budget_ns = (unsigned long long)(p->opt.time_budget_s * 1e9);
+    it.ctl = p->ctl;
+    it.fpr_out = nullptr;
+    it.iters_out = nullptr;
+    return it;
+}
+
+// Captures restriction and the level loop of Algorithm 3 into p->graph.
+static w1_status build_graph(w1_plan* p)
+{
+    cudaStream_t s = p->cap_stream;
+    W1_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    auto abort_capture = [&](w1_status st) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st;
+    };
+#define CAP_CK(call)                                                                               \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return abort_capture(fail(W1_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
+    } while (0)
+    for (int l = p->L - 1; l > 0; --l) CAP_CK(launch_restrict(p->lv[l].rho, p->lv[l].nx, p->lv[l].ny, p->lv[l - 1].rho, s));
+    for (int l = 0; l < p->L; ++l) {
+        LevelPlan& v = p->lv[l];
+        const size_t b = (size_t)v.nx * v.ny * sizeof(float);
+        CAP_CK(launch_level_begin(p->ctl, l, s));
+        if (l == 0) {
+            CAP_CK(cudaMemsetAsync(v.m1[0], 0, b, s));
+            CAP_CK(cudaMemsetAsync(v.m2[0], 0, b, s));
+            CAP_CK(cudaMemsetAsync(v.phi[0], 0, b, s));
+        } else {
+            const LevelPlan& c = p->lv[l - 1];
+            CAP_CK(launch_prolong(c.nx, c.ny, c.m1[0], c.m2[0], c.phi[0], v.m1[0], v.m2[0], v.phi[0], s));
+        }
+        if (v.path == 1) {
+            ResArgs a{};
+            a.m1 = v.m1[0];
+            a.m2 = v.m2[0];
+            a.phi = v.phi[0];
+            a.rho = v.rho;
+            a.it = iter_args(p, l);
+            CAP_CK(launch_resident(p->norm, v.cluster, a, s));
+        } else {
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t g = nullptr;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t ndeps = 0;
+            CAP_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+            cudaGraphConditionalHandle h;
+            CAP_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+            alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+            std::memset(npbuf, 0, sizeof(npbuf));
+            cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(npbuf);
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            CAP_CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np));
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            CAP_CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+            CAP_CK(cudaStreamBeginCaptureToGraph(p->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+            const int K = p->opt.check_every;
+            for (int k = 0; k < K; ++k) {
+                StepArgs a{};
+                const int src = k & 1, dst = src ^ 1;
+                a.m1 = v.m1[src];
+                a.m2 = v.m2[src];
+                a.phi = v.phi[src];
+                a.rho = v.rho;
+                a.m1o = v.m1[dst];
+                a.m2o = v.m2[dst];
+                a.phio = v.phi[dst];
+                a.rows = v.rows;
+                a.it = iter_args(p, l);
+                a.part = p->part;
+                a.cond = h;
+                a.use_cond = 1;
+                cudaError_t e = launch_step(p->norm, k == K - 1, a, p->body_stream);
+                if (e != cudaSuccess) {
+                    cudaGraph_t bg;
+                    cudaStreamEndCapture(p->body_stream, &bg);
+                    return abort_capture(fail(W1_ERR_CUDA, std::string("capture step: ") + cudaGetErrorString(e)));
+                }
+            }
+            cudaGraph_t bg = nullptr;
+            CAP_CK(cudaStreamEndCapture(p->body_stream, &bg));
+        }
+    }
+#undef CAP_CK
+    cudaGraph_t g = nullptr;
+    W1_CK(cudaStreamEndCapture(s, &g));
+    p->graph = g;
+    W1_CK(cudaGraphInstantiate(&p->exec, g, 0));
+    p->graph_ok = true;
+    return W1_OK;
+}
+
+static void fill_stats(const w1_plan* p, const Ctl* c, w1_stats* st)
+{
+    std::memset(st, 0, sizeof(*st));
+    st->levels = p->L;
+    int conv = 1;
+    for (int l = 0; l < p->L; ++l) {
+        st->nx[l] = p->lv[l].nx;
+        st->ny[l] = p->lv[l].ny;
+        st->iters[l] = c->iters[l];
+        st->fpr[l] = c->fpr[l];
+        st->tol[l] = p->lv[l].tol;
+        st->path[l] = p->lv[l].path;
+        st->cluster[l] = p->lv[l].cluster;
+        conv &= c->conv[l] ? 1 : 0;
+    }
+    st->w1 = c->f;
+    st->dual = c->dual;
+    st->lb = c->lb;
+    st->ub = c->ub;
+    st->route = c->route;
+    st->res_l1 = c->res_l1;
+    st->rho_l1 = c->rho_l1;
+    st->gmax = c->gmax;
+    st->mass0 = c->mass0;
+    st->mass1 = c->mass1;
+    st->mass_shift = c->mean;
+    st->converged = conv && !c->error && !c->timeout;
+}
+
+static w1_status solve_device(w1_plan* p, const float* rho0, const float* rho1, cudaStream_t s, double* dist,
+                              float* flux, w1_stats* stats)
+{
+    if (!p->graph_ok) {
+        w1_status st = build_graph(p);
+        if (st != W1_OK) return st;
+    }
+    const long long n = (long long)p->nx * p->ny;
+    const LevelPlan& f = p->lv[p->L - 1];
+    W1_CK(launch_prep(rho0, rho1, n, p->h, p->ctl, p->part, f.rho, s));
+    W1_CK(cudaGraphLaunch(p->exec, s));
+    W1_CK(launch_final(p->norm, f.m1[0], f.m2[0], f.phi[0], f.rho, f.nx, f.ny, f.h, p->q, p->part, p->ctl, s));
+    if (flux) {
+        W1_CK(cudaMemcpyAsync(flux, f.m1[0], n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        W1_CK(cudaMemcpyAsync(flux + n, f.m2[0], n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    }
+    W1_CK(cudaMemcpyAsync(p->host_ctl, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    W1_CK(cudaStreamSynchronize(s));
+    const Ctl* c = p->host_ctl;
+    w1_stats tmp;
+    fill_stats(p, c, &tmp);
+    if (stats) *stats = tmp;
+    if (c->error) {
+        *dist = NAN;
+        return fail(W1_ERR_MASS, "densities have different mass or a non-finite value");
+    }
+    *dist = c->f;
+    if (c->timeout) return fail(W1_ERR_TIMEOUT, "a level hit the device time budget");
+    if (!tmp.converged) return fail(W1_ERR_NOT_CONVERGED, "a level hit max_iters");
+    return W1_OK;
+}
+
+extern "C" w1_status w1_solve(w1_plan* p, const float* rho0, const float* rho1, void* stream, double* dist,
+                              float* flux, w1_stats* stats)
+{
+    if (!p || !rho0 || !rho1 || !dist) return fail(W1_ERR_INVALID_ARG, "NULL plan, density or dist");
+    W1_CK(cudaSetDevice(p->device));
+    return solve_device(p, rho0, rho1, static_cast<cudaStream_t>(stream), dist, flux, stats);
+}
+
+extern "C" w1_status w1_solve_host(w1_plan* p, const float* rho0, const float* rho1, void* stream, double* dist,
+                                   float* flux, w1_stats* stats)
+{
+    if (!p || !rho0 || !rho1 || !dist) return fail(W1_ERR_INVALID_ARG, "NULL plan, density or dist");
+    W1_CK(cudaSetDevice(p->device));
+    const size_t n = (size_t)p->nx * p->ny;
+    if (!p->in0) W1_CK(cudaMalloc(&p->in0, n * sizeof(float)));
+    if (!p->in1) W1_CK(cudaMalloc(&p->in1, n * sizeof(float)));
+    if (flux && !p->flux_d) W1_CK(cudaMalloc(&p->flux_d, 2 * n * sizeof(float)));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    W1_CK(cudaMemcpyAsync(p->in0, rho0, n * sizeof(float), cudaMemcpyHostToDevice, s));
+    W1_CK(cudaMemcpyAsync(p->in1, rho1, n * sizeof(float), cudaMemcpyHostToDevice, s));
+    w1_status st = solve_device(p, p->in0, p->in1, s, dist, flux ? p->flux_d : nullptr, stats);
+    if (flux && (st == W1_OK || st == W1_ERR_NOT_CONVERGED || st == W1_ERR_TIMEOUT)) {
+        W1_CK(cudaMemcpyAsync(flux, p->flux_d, 2 * n * sizeof(float), cudaMemcpyDeviceToHost, s));
+        W1_CK(cudaStreamSynchronize(s));
+    }
+    return st;
+}
+
+extern "C" w1_status w1_plan_potential(w1_plan* p, float* phi, void* stream)
+{
+    if (!p || !phi) return fail(W1_ERR_INVALID_ARG, "NULL plan or phi");
+    W1_CK(cudaSetDevice(p->device));
+    const LevelPlan& f = p->lv[p->L - 1];
+    W1_CK(cudaMemcpyAsync(phi, f.phi[0], (size_t)f.nx * f.ny * sizeof(float), cudaMemcpyDeviceToDevice,
+                          static_cast<cudaStream_t>(stream)));
+    return W1_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Building blocks
+// ---------------------------------------------------------------------------
+
+extern "C" w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, float tau, const float* rho,
+                                 float* m1, float* m2, float* phi, long long iters, int path, void* stream,
+                                 double* fpr_last)
+{
+    if (nx < 1 || ny < 1 || !(h > 0.0) || !rho || !m1 || !m2 || !phi || iters < 0)
+        return fail(W1_ERR_INVALID_ARG, "bad arguments to w1_cp_steps");
+    if (norm != W1_NORM_L1 && norm != W1_NORM_L2) return fail(W1_ERR_INVALID_ARG, "norm must be 1 or 2");
+    int dev = 0;
+    W1_CK(cudaGetDevice(&dev));
+    w1_status st = prepare_device(dev);
+    if (st != W1_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (iters == 0) {
+        if (fpr_last) *fpr_last = 0.0;
+        return W1_OK;
+    }
+    double* dfpr = nullptr;
+    W1_CK(cudaMalloc(&dfpr, sizeof(double)));
+    IterArgs it{};
+    it.nx = nx;
+    it.ny = ny;
+    it.mu = mu;
+    it.tau = tau;
+    it.ih = (float)(1.0 / h);
+    it.h = h;
+    it.tol = 0.0;
+    it.cap = iters;
+    it.K = 2;
+    it.fixed = 1;
+    it.level = 0;
+    it.budget_ns = 600ull * 1000000000ull;
+    it.ctl = nullptr;
+    it.fpr_out = dfpr;
+    w1_status ret = W1_OK;
+    if (path == 1) {
+        const int c = resident_cluster_for(nx, ny);
+        if (c == 0 || resident_cluster_ok(norm, c, nx, ny) <= 0) {
+            cudaFree(dfpr);
+            return fail(W1_ERR_UNSUPPORTED, "grid too large for the resident path");
+        }
+        ResArgs a{};
+        a.m1 = m1;
+        a.m2 = m2;
+        a.phi = phi;
+        a.rho = rho;
+        a.it = it;
+        cudaError_t e = launch_resident(norm, c, a, s);
+        if (e != cudaSuccess) ret = fail(W1_ERR_CUDA, std::string("resident launch: ") + cudaGetErrorString(e));
+    } else {
+        const size_t n = (size_t)nx * ny;
+        const int rows = stream_rows_auto(nx, ny);
+        float* buf = nullptr;
+        double* part = nullptr;
+        Ctl* ctl = nullptr;
+        cudaError_t e = cudaMalloc(&buf, 3 * n * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&part, step_part_doubles(nx, ny, rows) * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&ctl, sizeof(Ctl));
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
+        float* A[3] = {m1, m2, phi};
+        float* B[3] = {buf, buf + n, buf + 2 * n};
+        for (long long k = 0; k < iters && e == cudaSuccess; ++k) {
+            float** src = (k & 1) ? B : A;
+            float** dst = (k & 1) ? A : B;
+            StepArgs a{};
+            a.m1 = src[0];
+            a.m2 = src[1];
+            a.phi = src[2];
+            a.rho = rho;
+            a.m1o = dst[0];
+            a.m2o = dst[1];
+            a.phio = dst[2];
+            a.rows = rows;
+            a.it = it;
+            a.it.ctl = ctl;
+            a.part = part;
+            a.use_cond = 0;
+            e = launch_step(norm, k == iters - 1, a, s);
+        }
+        if (e == cudaSuccess && (iters & 1)) {
+            for (int c = 0; c < 3 && e == cudaSuccess; ++c)
+                e = cudaMemcpyAsync(A[c], B[c], n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) ret = fail(W1_ERR_CUDA, std::string("streaming steps: ") + cudaGetErrorString(e));
+        cudaFree(buf);
+        cudaFree(part);
+        cudaFree(ctl);
+    }
+    if (ret == W1_OK) {
+        double v = 0.0;
+        cudaError_t e = cudaMemcpyAsync(&v, dfpr, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) ret = fail(W1_ERR_CUDA, std::string("fpr readback: ") + cudaGetErrorString(e));
+        if (fpr_last) *fpr_last = v;
+    }
+    cudaFree(dfpr);
+    cudaGetLastError();
+    return ret;
+}
+
+extern "C" w1_status w1_restrict(int nx, int ny, const float* fine, float* coarse, void* stream)
+{
+    if (nx < 2 || ny < 2 || (nx & 1) || (ny & 1) || !fine || !coarse)
+        return fail(W1_ERR_INVALID_ARG, "w1_restrict needs even nx, ny >= 2");
+    W1_CK(launch_restrict(fine, nx, ny, coarse, static_cast<cudaStream_t>(stream)));
+    return W1_OK;
+}
+
+extern "C" w1_status w1_prolong(int ncx, int ncy, const float* m1c, const float* m2c, const float* phic, float* m1f,
+                                float* m2f, float* phif, void* stream)
+{
+    if (ncx < 1 || ncy < 1 || !m1c || !m2c || !phic || !m1f || !m2f || !phif)
+        return fail(W1_ERR_INVALID_ARG, "bad arguments to w1_prolong");
+    W1_CK(launch_prolong(ncx, ncy, m1c, m2c, phic, m1f, m2f, phif, static_cast<cudaStream_t>(stream)));
+    return W1_OK;
+}
+
+extern "C" w1_status w1_state_stats(int nx, int ny, double h, int norm, const float* rho, const float* m1,
+                                    const float* m2, const float* phi, void* stream, w1_stats* out)
+{
+    if (nx < 1 || ny < 1 || !(h > 0.0) || !rho || !m1 || !m2 || !phi || !out)
+        return fail(W1_ERR_INVALID_ARG, "bad arguments to w1_state_stats");
+    if (norm != W1_NORM_L1 && norm != W1_NORM_L2) return fail(W1_ERR_INVALID_ARG, "norm must be 1 or 2");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)nx * ny;
+    double *q = nullptr, *part = nullptr;
+    Ctl* ctl = nullptr;
+    cudaError_t e = cudaMalloc(&q, 2 * n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&part, final_part_doubles() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&ctl, sizeof(Ctl));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
+    if (e == cudaSuccess) e = launch_final(norm, m1, m2, phi, rho, nx, ny, h, q, part, ctl, s);
+    Ctl c{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&c, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(q);
+    cudaFree(part);
+    cudaFree(ctl);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(W1_ERR_CUDA, std::string("w1_state_stats: ") + cudaGetErrorString(e));
+    }
+    std::memset(out, 0, sizeof(*out));
+    out->w1 = c.f;
+    out->dual = c.dual;
+    out->lb = c.lb;
+    out->ub = c.ub;
+    out->route = c.route;
+    out->res_l1 = c.res_l1;
+    out->rho_l1 = c.rho_l1;
+    out->gmax = c.gmax;
+    return W1_OK;
+}

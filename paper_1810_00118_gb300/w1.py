@@ -1,0 +1,264 @@
+"""Thin ctypes binding of libw1.so (include/w1.h): argument marshalling only.
+
+Every step of the solver runs in the library's sm_103a kernels.  Tensors are
+torch CUDA float32, C-contiguous, shaped [ny, nx] (a flux is [2, ny, nx]);
+streams are torch.cuda streams (default: the current stream).  There is no CPU
+fallback: if the library cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+from . import _build
+
+NORM_L1 = 1
+NORM_L2 = 2
+MAX_LEVELS = 16
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_SHAPE = 2
+ERR_MASS = 3
+ERR_NOMEM = 4
+ERR_CUDA = 5
+ERR_NOT_CONVERGED = 6
+ERR_TIMEOUT = 7
+PENDING = 8
+ERR_BUDGET = 9
+ERR_UNSUPPORTED = 10
+
+_STATUS_NAMES = {
+    OK: "OK", ERR_INVALID_ARG: "ERR_INVALID_ARG", ERR_SHAPE: "ERR_SHAPE", ERR_MASS: "ERR_MASS",
+    ERR_NOMEM: "ERR_NOMEM", ERR_CUDA: "ERR_CUDA", ERR_NOT_CONVERGED: "ERR_NOT_CONVERGED",
+    ERR_TIMEOUT: "ERR_TIMEOUT", PENDING: "PENDING", ERR_BUDGET: "ERR_BUDGET", ERR_UNSUPPORTED: "ERR_UNSUPPORTED",
+}
+
+
+class W1Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("check_every", ctypes.c_int), ("max_iters", ctypes.c_longlong), ("theta", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("time_budget_s", ctypes.c_double), ("path", ctypes.c_int),
+                ("rows_per_thread", ctypes.c_int)]
+
+
+class _Stats(ctypes.Structure):
+    L = MAX_LEVELS
+    _fields_ = [("levels", ctypes.c_int), ("nx", ctypes.c_int * L), ("ny", ctypes.c_int * L),
+                ("iters", ctypes.c_longlong * L), ("fpr", ctypes.c_double * L), ("tol", ctypes.c_double * L),
+                ("path", ctypes.c_int * L), ("cluster", ctypes.c_int * L),
+                ("w1", ctypes.c_double), ("dual", ctypes.c_double), ("lb", ctypes.c_double),
+                ("ub", ctypes.c_double), ("route", ctypes.c_double), ("res_l1", ctypes.c_double),
+                ("rho_l1", ctypes.c_double), ("gmax", ctypes.c_double), ("mass0", ctypes.c_double),
+                ("mass1", ctypes.c_double), ("mass_shift", ctypes.c_double), ("converged", ctypes.c_int)]
+
+
+@dataclass
+class Stats:
+    levels: int = 0
+    sizes: list = field(default_factory=list)
+    iters: list = field(default_factory=list)
+    fpr: list = field(default_factory=list)
+    tol: list = field(default_factory=list)
+    path: list = field(default_factory=list)
+    cluster: list = field(default_factory=list)
+    w1: float = 0.0
+    dual: float = 0.0
+    lb: float = 0.0
+    ub: float = 0.0
+    route: float = 0.0
+    res_l1: float = 0.0
+    rho_l1: float = 0.0
+    gmax: float = 0.0
+    mass0: float = 0.0
+    mass1: float = 0.0
+    mass_shift: float = 0.0
+    converged: bool = False
+
+    @staticmethod
+    def _from(s: _Stats) -> "Stats":
+        L = s.levels
+        return Stats(L, [(s.nx[k], s.ny[k]) for k in range(L)], [s.iters[k] for k in range(L)],
+                     [s.fpr[k] for k in range(L)], [s.tol[k] for k in range(L)], [s.path[k] for k in range(L)],
+                     [s.cluster[k] for k in range(L)], s.w1, s.dual, s.lb, s.ub, s.route, s.res_l1, s.rho_l1,
+                     s.gmax, s.mass0, s.mass1, s.mass_shift, bool(s.converged))
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path) or _build._stale():
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, I, D, LL, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_float
+    st = ctypes.c_int
+    sig = {
+        "w1_default_options": (None, [ctypes.POINTER(Options)]),
+        "w1_plan_create": (st, [I, I, D, I, I, D, ctypes.POINTER(P)]),
+        "w1_plan_create_ex": (st, [I, I, D, I, I, D, ctypes.POINTER(Options), ctypes.POINTER(P)]),
+        "w1_plan_destroy": (st, [P]),
+        "w1_plan_workspace_bytes": (ctypes.c_size_t, [P]),
+        "w1_plan_set_workspace": (st, [P, P, ctypes.c_size_t]),
+        "w1_solve": (st, [P, P, P, P, ctypes.POINTER(D), P, ctypes.POINTER(_Stats)]),
+        "w1_solve_host": (st, [P, P, P, P, ctypes.POINTER(D), P, ctypes.POINTER(_Stats)]),
+        "w1_plan_potential": (st, [P, P, P]),
+        "w1_cp_steps": (st, [I, I, D, I, F, F, P, P, P, P, LL, I, P, ctypes.POINTER(D)]),
+        "w1_restrict": (st, [I, I, P, P, P]),
+        "w1_prolong": (st, [I, I, P, P, P, P, P, P, P]),
+        "w1_state_stats": (st, [I, I, D, I, P, P, P, P, P, ctypes.POINTER(_Stats)]),
+        "w1_status_string": (ctypes.c_char_p, [st]),
+        "w1_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _check(status: int, ok=(OK,)):
+    if status not in ok:
+        raise W1Error(status, _lib.w1_last_error().decode())
+    return status
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    _lib.w1_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _dev_ptr(t, shape=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A solver plan for nx x ny grids (w1_plan_create_ex)."""
+
+    def __init__(self, nx, ny, h=0.0, levels=0, norm=NORM_L1, tol=0.0, **options):
+        self._p = ctypes.c_void_p()
+        self.nx, self.ny = nx, ny
+        opt = default_options(**options)
+        _check(_lib.w1_plan_create_ex(nx, ny, h, levels, norm, tol, ctypes.byref(opt), ctypes.byref(self._p)))
+
+    def close(self):
+        if self._p:
+            _lib.w1_plan_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def workspace_bytes(self) -> int:
+        return _lib.w1_plan_workspace_bytes(self._p)
+
+    def set_workspace(self, tensor):
+        _check(_lib.w1_plan_set_workspace(self._p, ctypes.c_void_p(tensor.data_ptr()),
+                                          tensor.numel() * tensor.element_size()))
+
+    def solve(self, rho0, rho1, flux=None, stream=None, allow=(OK,)):
+        """Returns (W1 estimate, Stats, status).  Raises on statuses not in `allow`."""
+        shape = (self.ny, self.nx)
+        d = ctypes.c_double(0.0)
+        s = _Stats()
+        fp = _dev_ptr(flux, (2,) + shape) if flux is not None else None
+        status = _lib.w1_solve(self._p, _dev_ptr(rho0, shape), _dev_ptr(rho1, shape), _stream_ptr(stream),
+                               ctypes.byref(d), fp, ctypes.byref(s))
+        _check(status, allow)
+        return d.value, Stats._from(s), status
+
+    def solve_host(self, rho0, rho1, flux=None, stream=None, allow=(OK,)):
+        """Densities and flux as C-contiguous float32 numpy arrays (host memory)."""
+        import numpy as np
+        shape = (self.ny, self.nx)
+        for a in (rho0, rho1):
+            if a.dtype != np.float32 or a.shape != shape or not a.flags.c_contiguous:
+                raise TypeError("expected C-contiguous float32 arrays of shape (ny, nx)")
+        d = ctypes.c_double(0.0)
+        s = _Stats()
+        fp = None
+        if flux is not None:
+            if flux.dtype != np.float32 or flux.shape != (2,) + shape or not flux.flags.c_contiguous:
+                raise TypeError("flux must be a C-contiguous float32 array of shape (2, ny, nx)")
+            fp = ctypes.c_void_p(flux.ctypes.data)
+        status = _lib.w1_solve_host(self._p, ctypes.c_void_p(rho0.ctypes.data), ctypes.c_void_p(rho1.ctypes.data),
+                                    _stream_ptr(stream), ctypes.byref(d), fp, ctypes.byref(s))
+        _check(status, allow)
+        return d.value, Stats._from(s), status
+
+    def potential(self, out, stream=None):
+        _check(_lib.w1_plan_potential(self._p, _dev_ptr(out, (self.ny, self.nx)), _stream_ptr(stream)))
+        return out
+
+
+def cp_steps(rho, m1, m2, phi, h, norm, mu, tau, iters, path=2, stream=None) -> float:
+    """`iters` steps of eq. primaldual in place on device state; returns R^k of the last step."""
+    ny, nx = rho.shape
+    f = ctypes.c_double(0.0)
+    _check(_lib.w1_cp_steps(nx, ny, h, norm, mu, tau, _dev_ptr(rho), _dev_ptr(m1, rho.shape),
+                            _dev_ptr(m2, rho.shape), _dev_ptr(phi, rho.shape), int(iters), path,
+                            _stream_ptr(stream), ctypes.byref(f)))
+    return f.value
+
+
+def restrict(fine, out, stream=None):
+    ny, nx = fine.shape
+    _check(_lib.w1_restrict(nx, ny, _dev_ptr(fine), _dev_ptr(out, (ny // 2, nx // 2)), _stream_ptr(stream)))
+    return out
+
+
+def prolong(m1c, m2c, phic, m1f, m2f, phif, stream=None):
+    ncy, ncx = phic.shape
+    fs = (2 * ncy, 2 * ncx)
+    _check(_lib.w1_prolong(ncx, ncy, _dev_ptr(m1c, phic.shape), _dev_ptr(m2c, phic.shape), _dev_ptr(phic),
+                           _dev_ptr(m1f, fs), _dev_ptr(m2f, fs), _dev_ptr(phif, fs), _stream_ptr(stream)))
+
+
+def state_stats(rho, m1, m2, phi, h, norm, stream=None) -> Stats:
+    ny, nx = rho.shape
+    s = _Stats()
+    _check(_lib.w1_state_stats(nx, ny, h, norm, _dev_ptr(rho), _dev_ptr(m1, rho.shape), _dev_ptr(m2, rho.shape),
+                               _dev_ptr(phi, rho.shape), _stream_ptr(stream), ctypes.byref(s)))
+    return Stats._from(s)
+
+
+def status_string(status: int) -> str:
+    return _lib.w1_status_string(status).decode()

@@ -1,0 +1,62 @@
+"""The C ABI library builds for sm_103a, loads without a GPU and exports every
+entry point declared in include/w1.h (no compute calls here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(w1_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    from paper_1810_00118_gb300 import _build
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    names = declared_symbols()
+    assert len(names) >= 15
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (w1_\w+)", out))
+    assert names <= exported
+
+
+def test_host_only_entry_points_work_without_gpu():
+    from paper_1810_00118_gb300 import w1
+    o = w1.default_options()
+    assert o.check_every == 32 and o.theta == 0.5 and o.alpha == -1.0
+    assert w1.status_string(w1.ERR_MASS).startswith("mass")
+    assert w1.status_string(99) == "unknown status"
+
+
+def test_binding_struct_layout_matches_header():
+    """ctypes mirrors of w1_options / w1_stats have the C sizes."""
+    from paper_1810_00118_gb300 import w1
+    # w1_options: int, long long, 3 doubles, 2 ints -> 4 (+4 pad) + 8 + 24 + 8 = 48
+    assert ctypes.sizeof(w1.Options) == 48
+    # w1_stats: int + 2*16 ints (132, pad to 136) + 16 ll + 2*16 doubles + 2*16 ints + 11 doubles + int (+pad)
+    assert ctypes.sizeof(w1._Stats) == 136 + 128 + 256 + 128 + 88 + 8
+
+
+def test_oracle_is_not_imported_by_the_product():
+    """The product package never loads the oracle (the oracle is test-only)."""
+    pkg = os.path.join(ROOT, "paper_1810_00118_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".h", ".cuh")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text and "w1_oracle" not in text, f

@@ -1,0 +1,282 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Floating-point tolerances (FP32 iterates against FP64):
+  - a few steps of eq. primaldual from the same state: max |diff| <= 2e-5 of the
+    state's scale (rounding of order 1e-7 per step, non-expansive iteration);
+  - full solves, oracle replaying the GPU's per-level iteration counts:
+    W1 relative 1e-4, flux relative L1 1e-3 (the accuracy targets of the build);
+  - FP64 statistics of the same FP32 state: relative 1e-9.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+L1, L2 = 1, 2
+
+
+@pytest.fixture(scope="module")
+def w1():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1810_00118_gb300 import w1 as mod
+    return mod
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def rand_state(rng, ny, nx, scale=0.5):
+    m1, m2, phi = rng.normal(scale=scale, size=(3, ny, nx)).astype(np.float32)
+    m1[:, -1] = 0
+    m2[-1, :] = 0
+    rho = rng.normal(size=(ny, nx))
+    rho = (rho - rho.mean()).astype(np.float32)
+    return rho, m1, m2, phi
+
+
+def mu_of(h, theta=0.5):
+    return float(np.float32(theta * h / (2 * np.sqrt(2.0))))
+
+
+def flux_rel_l1(f, m1, m2):
+    return (np.abs(f[0] - m1).sum() + np.abs(f[1] - m2).sum()) / (np.abs(m1).sum() + np.abs(m2).sum())
+
+
+# --------------------------------------------------------------------------------------
+# Building blocks
+# --------------------------------------------------------------------------------------
+
+SHAPES = [(1, 37), (37, 1), (3, 5), (17, 33), (40, 33), (64, 64), (128, 96), (200, 300)]
+
+
+@pytest.mark.parametrize("norm", [L1, L2])
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("path", [1, 2])
+def test_cp_steps_match_oracle(w1, norm, shape, path):
+    ny, nx = shape
+    if path == 1 and ny * nx > 16 * 4096:
+        pytest.skip("larger than the resident path")
+    rng = np.random.default_rng(ny * 1000 + nx + norm)
+    rho, m1, m2, phi = rand_state(rng, ny, nx)
+    h = 1.0 / max(nx, ny)
+    mu = mu_of(h)
+    for iters in (1, 7, 64):
+        g = [dev(a) for a in (rho, m1, m2, phi)]
+        fpr = w1.cp_steps(g[0], g[1], g[2], g[3], h, norm, mu, mu, iters, path=path)
+        o1, o2, op, ofpr = oracle.cp_iterate(rho, m1, m2, phi, h, norm, iters, mu=mu, tau=mu)
+        scale = max(np.abs(o1).max(), np.abs(o2).max(), np.abs(op).max(), 1.0)
+        for got, want in ((g[1], o1), (g[2], o2), (g[3], op)):
+            err = np.abs(host(got) - want).max()
+            assert err <= 2e-5 * scale, (iters, err, scale)
+        assert fpr == pytest.approx(ofpr, rel=2e-3, abs=1e-12 * scale)
+
+
+@pytest.mark.parametrize("norm", [L1, L2])
+def test_resident_and_streaming_paths_agree(w1, norm):
+    rng = np.random.default_rng(77)
+    rho, m1, m2, phi = rand_state(rng, 96, 128)
+    h = 1 / 128
+    out = []
+    for path in (1, 2):
+        g = [dev(a) for a in (rho, m1, m2, phi)]
+        w1.cp_steps(*g, h, norm, mu_of(h), mu_of(h), 200, path=path)
+        out.append([host(t) for t in g[1:]])
+    for a, b in zip(*out):
+        assert np.abs(a - b).max() <= 2e-5 * max(np.abs(b).max(), 1.0)
+
+
+@pytest.mark.parametrize("shape", [(2, 2), (6, 10), (64, 64), (256, 130), (512, 512)])
+def test_restrict_matches_oracle(w1, shape):
+    rng = np.random.default_rng(3)
+    f = rng.normal(size=shape).astype(np.float32)
+    out = torch.empty((shape[0] // 2, shape[1] // 2), device="cuda")
+    w1.restrict(dev(f), out)
+    np.testing.assert_allclose(host(out), oracle.restrict(f.astype(np.float64)), rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 5), (3, 4), (32, 32), (64, 17)])
+def test_prolong_matches_oracle(w1, shape):
+    rng = np.random.default_rng(4)
+    m1c, m2c, phic = rng.normal(size=(3,) + shape).astype(np.float32)
+    m1c[:, -1] = 0
+    m2c[-1, :] = 0
+    fs = (2 * shape[0], 2 * shape[1])
+    f = [torch.empty(fs, device="cuda") for _ in range(3)]
+    w1.prolong(dev(m1c), dev(m2c), dev(phic), *f)
+    want = oracle.prolong(m1c, m2c, phic)
+    for got, ref in zip(f, want):
+        np.testing.assert_allclose(host(got), ref, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("norm", [L1, L2])
+@pytest.mark.parametrize("shape", [(1, 16), (5, 7), (64, 64), (96, 80), (512, 512)])
+def test_state_stats_match_oracle(w1, norm, shape):
+    rng = np.random.default_rng(5)
+    rho, m1, m2, phi = rand_state(rng, *shape, scale=0.2)
+    h = 1.0 / max(shape)
+    g = w1.state_stats(dev(rho), dev(m1), dev(m2), dev(phi), h, norm)
+    o = oracle.stats(rho, m1, m2, phi, h, norm)
+    for name in ("f", "dual", "res_l1", "rho_l1", "gmax", "route", "lb", "ub"):
+        got = getattr(g, "w1" if name == "f" else name)
+        assert got == pytest.approx(getattr(o, name), rel=1e-9, abs=1e-13), name
+
+
+# --------------------------------------------------------------------------------------
+# Full solves (Algorithm 3) against the oracle replaying the GPU's iteration counts
+# --------------------------------------------------------------------------------------
+
+def solve_and_replay(w1, r0, r1, norm, levels, tol=0.0, **opt):
+    a0, a1, d0, d1 = synth.to_f32_pair(r0, r1)
+    ny, nx = a0.shape
+    flux = torch.empty((2, ny, nx), device="cuda")
+    phi = torch.empty((ny, nx), device="cuda")
+    with w1.Plan(nx, ny, levels=levels, norm=norm, tol=tol, **opt) as plan:
+        val, st, _ = plan.solve(dev(a0), dev(a1), flux=flux)
+        plan.potential(phi)
+    theta = opt.get("theta", 0.5)
+    ref = oracle.multilevel(d0, d1, levels=levels, norm=norm, theta=theta, replay=st.iters)
+    return val, st, host(flux), host(phi), ref
+
+
+def assert_parity(val, st, flux, ref):
+    assert st.converged
+    assert val == st.w1
+    assert abs(val - ref.w1) <= 1e-4 * abs(ref.w1), (val, ref.w1)
+    assert flux_rel_l1(flux, ref.m1, ref.m2) <= 1e-3
+    # the GPU's certificate brackets its own value consistently with the oracle's
+    assert st.lb <= st.ub
+    assert st.ub == pytest.approx(ref.stats.ub, rel=1e-3)
+
+
+def test_solve_64_l1_three_levels(w1):
+    """64x64, L1, 3-level cascade 16->32->64, FPR threshold 1e-6 on the finest level."""
+    r0, r1 = synth.pair(0, 0)
+    val, st, flux, phi, ref = solve_and_replay(w1, r0, r1, L1, 3, tol=1e-6)
+    assert [s for s in st.sizes] == [(16, 16), (32, 32), (64, 64)]
+    assert all(k % 32 == 0 and k > 0 for k in st.iters)
+    assert_parity(val, st, flux, ref)
+    # the potential is the oracle's (up to FP32 rounding)
+    assert np.abs(phi - ref.phi).max() <= 1e-3 * max(np.abs(ref.phi).max(), 1.0)
+    # free-running oracle (its own stop decisions) agrees as well
+    a0, a1, d0, d1 = synth.to_f32_pair(r0, r1)
+    free = oracle.multilevel(d0, d1, levels=3, norm=L1, tol=1e-6, stop=oracle.STOP_FPR)
+    assert abs(val - free.w1) <= 1e-3 * free.w1
+    for a, b in zip(st.iters, free.iters):
+        assert abs(a - b) <= max(0.1 * b, 64)
+
+
+def test_solve_256_l2_five_levels(w1):
+    r0, r1 = synth.pair(1, 0)
+    val, st, flux, _, ref = solve_and_replay(w1, r0, r1, L2, 5)
+    assert st.sizes[0] == (16, 16) and st.sizes[-1] == (256, 256)
+    assert_parity(val, st, flux, ref)
+
+
+@pytest.mark.parametrize("norm", [L2, L1])
+def test_solve_512_six_levels(w1, norm):
+    """The 512x512 image-shaped workload, 6 levels 16->512, the bench configuration."""
+    r0, r1 = synth.pair(2, 0)
+    val, st, flux, _, ref = solve_and_replay(w1, r0, r1, norm, 6)
+    assert st.sizes[-1] == (512, 512)
+    assert_parity(val, st, flux, ref)
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_forced_paths_give_the_same_solution(w1, path):
+    r0, r1 = synth.pair(0, 1)
+    val, st, flux, _, ref = solve_and_replay(w1, r0, r1, L1, 3, tol=1e-6, path=path)
+    assert all(p == path for p in st.path)
+    assert_parity(val, st, flux, ref)
+
+
+@pytest.mark.parametrize("nx,ny,levels", [(128, 64, 3), (80, 48, 2), (33, 17, 1), (64, 1, 1), (1, 40, 1)])
+def test_ragged_and_nonsquare(w1, nx, ny, levels):
+    rng = np.random.default_rng(nx * ny)
+    r0 = rng.uniform(0.1, 1.0, (ny, nx))
+    r1 = rng.uniform(0.1, 1.0, (ny, nx))
+    h = 1.0 / max(nx, ny)
+    r0 /= r0.sum() * h * h
+    r1 /= r1.sum() * h * h
+    val, st, flux, _, ref = solve_and_replay(w1, r0, r1, L2 if nx % 2 else L1, levels, tol=1e-5)
+    assert_parity(val, st, flux, ref)
+
+
+def test_equal_densities_give_zero(w1):
+    r0, _ = synth.pair(0, 2)
+    a0 = dev(r0)
+    with w1.Plan(64, 64, levels=3, norm=L1) as plan:
+        val, st, _ = plan.solve(a0, a0)
+    assert val == 0.0 and st.iters == [32, 32, 32]
+
+
+def test_mass_imbalance_and_nonfinite_are_rejected(w1):
+    r0, r1 = synth.pair(0, 3)
+    with w1.Plan(64, 64, levels=3, norm=L1) as plan:
+        val, st, status = plan.solve(dev(r0), dev(1.01 * r1), allow=(w1.ERR_MASS,))
+        assert status == w1.ERR_MASS and np.isnan(val)
+        bad = r1.copy()
+        bad[5, 5] = np.inf
+        _, _, status = plan.solve(dev(r0), dev(bad), allow=(w1.ERR_MASS,))
+        assert status == w1.ERR_MASS
+        # the plan is still usable afterwards
+        val, st, status = plan.solve(dev(r0), dev(r1))
+        assert status == w1.OK and val > 0
+
+
+def test_shape_errors(w1):
+    with pytest.raises(w1.W1Error, match="ERR_SHAPE"):
+        w1.Plan(60, 64, levels=4)
+    with pytest.raises(w1.W1Error, match="ERR_INVALID_ARG"):
+        w1.Plan(64, 64, levels=3, norm=3)
+    with pytest.raises(w1.W1Error, match="ERR_INVALID_ARG"):
+        w1.Plan(64, 64, levels=3, check_every=7)
+
+
+def test_iteration_cap_and_time_budget_end_a_level(w1):
+    """The device loops are bounded: an iteration cap and a wall-clock budget end
+    a level with a status instead of running on."""
+    r0, r1 = synth.pair(0, 4)
+    for path in (1, 2):
+        with w1.Plan(64, 64, levels=3, norm=L1, tol=1e-12, max_iters=64, path=path) as plan:
+            val, st, status = plan.solve(dev(r0), dev(r1), allow=(w1.ERR_NOT_CONVERGED,))
+            assert status == w1.ERR_NOT_CONVERGED and val > 0 and not st.converged
+            assert st.iters == [64, 64, 64]
+        with w1.Plan(64, 64, levels=3, norm=L1, tol=1e-12, time_budget_s=1e-6, path=path) as plan:
+            val, st, status = plan.solve(dev(r0), dev(r1), allow=(w1.ERR_TIMEOUT,))
+            assert status == w1.ERR_TIMEOUT and val > 0
+            assert all(0 < k <= 64 for k in st.iters)
+
+
+def test_deterministic_and_host_entry_point(w1):
+    r0, r1 = synth.pair(2, 1, n=256)
+    a0, a1 = (np.ascontiguousarray(x, dtype=np.float32) for x in (r0, r1))
+    with w1.Plan(256, 256, norm=L1) as plan:
+        f1 = torch.empty((2, 256, 256), device="cuda")
+        f2 = torch.empty_like(f1)
+        v1, s1, _ = plan.solve(dev(a0), dev(a1), flux=f1)
+        v2, s2, _ = plan.solve(dev(a0), dev(a1), flux=f2)
+        fh = np.empty((2, 256, 256), dtype=np.float32)
+        v3, s3, _ = plan.solve_host(a0, a1, flux=fh)
+    assert v1 == v2 == v3 and s1.iters == s2.iters == s3.iters
+    assert torch.equal(f1, f2)
+    np.testing.assert_array_equal(fh, f1.cpu().numpy())
+
+
+def test_caller_workspace(w1):
+    r0, r1 = synth.pair(0, 5)
+    with w1.Plan(64, 64, levels=3, norm=L2) as plan:
+        v_own, _, _ = plan.solve(dev(r0), dev(r1))
+        ws = torch.empty(plan.workspace_bytes // 4 + 64, dtype=torch.float32, device="cuda")
+        plan.set_workspace(ws)
+        v_ws, _, _ = plan.solve(dev(r0), dev(r1))
+    assert v_own == v_ws
