@@ -259,14 +259,16 @@ def run_gpu(args):
     n_launch = sum(launches(st) for step in results for _, st in step)
 
     # end to end through the host entry point
-    barrier()
-    t0 = time.perf_counter()
-    for s in range(args.warmup, total_steps):
-        do_step(s, host=True)
-    barrier()
-    e2e_el = max_over_ranks(time.perf_counter() - t0)
-    e2e = {"value": solves / e2e_el, "unit": "solves/s",
-           "h2d_bytes_per_step": 2 * N * N * 4 * len(NORMS), "d2h_bytes_per_step": 552 * len(NORMS)}
+    e2e = None
+    if not args.no_e2e:
+        barrier()
+        t0 = time.perf_counter()
+        for s in range(args.warmup, total_steps):
+            do_step(s, host=True)
+        barrier()
+        e2e_el = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": solves / e2e_el, "unit": "solves/s",
+               "h2d_bytes_per_step": 2 * N * N * 4 * len(NORMS), "d2h_bytes_per_step": 552 * len(NORMS)}
 
     # roofline of the streaming step kernel (8192^2, T = 1)
     roof = None
@@ -347,10 +349,48 @@ def main():
     ap.add_argument("--roof-n", type=int, default=8192)
     ap.add_argument("--roof-iters", type=int, default=100)
     ap.add_argument("--ref-budget", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", default="solve", choices=["solve", "stream-kernel", "resident-kernel"],
+                    help="kernel-only runs for profiling: one level's steps through w1_cp_steps")
+    ap.add_argument("--kn", type=int, default=256, help="grid side for --only *-kernel")
+    ap.add_argument("--kiters", type=int, default=1000, help="steps for --only *-kernel")
+    ap.add_argument("--knorm", type=int, default=1)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only != "solve":
+        return run_kernel_only(args)
     return run_gpu(args)
+
+
+def run_kernel_only(args):
+    """One level's steps on an ellipse-texture density, timed with CUDA events."""
+    import torch
+
+    import synth
+    from paper_1810_00118_gb300 import w1
+
+    n = args.kn
+    r0, r1 = synth.pair(WORKLOAD, 0, n=n)
+    rho = torch.from_numpy(np.ascontiguousarray(r0 - r1 - (r0 - r1).mean(), dtype=np.float32)).cuda()
+    m1, m2, phi = (torch.zeros((n, n), device="cuda") for _ in range(3))
+    h = 1.0 / n
+    mu = float(np.float32(0.5 * h / (2 * np.sqrt(2.0))))
+    path = 1 if args.only == "resident-kernel" else 2
+    stream = torch.cuda.current_stream()
+    w1.cp_steps(rho, m1, m2, phi, h, args.knorm, mu, mu, 2, path=path, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fpr = w1.cp_steps(rho, m1, m2, phi, h, args.knorm, mu, mu, args.kiters, path=path, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    us_step = ms * 1e3 / args.kiters
+    print(json.dumps({"only": args.only, "n": n, "norm": args.knorm, "steps": args.kiters, "ms": ms,
+                      "us_per_step": us_step, "node_steps_per_s": n * n / (us_step * 1e-6),
+                      "alg_GBps": 28.0 * n * n / (us_step * 1e-6) / 1e9, "fpr_last": fpr}))
+    return 0
 
 
 if __name__ == "__main__":

@@ -44,6 +44,11 @@ def rand_state(rng, ny, nx, scale=0.5):
     return rho, m1, m2, phi
 
 
+def resident_fits(nx, ny):
+    """A cluster of 1..16 CTAs, each holding whole rows, at most 4096 nodes per CTA."""
+    return any(ny % c == 0 and (ny // c) * nx <= 4096 for c in (1, 2, 4, 8, 16))
+
+
 def mu_of(h, theta=0.5):
     return float(np.float32(theta * h / (2 * np.sqrt(2.0))))
 
@@ -63,8 +68,10 @@ SHAPES = [(1, 37), (37, 1), (3, 5), (17, 33), (40, 33), (64, 64), (128, 96), (20
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("path", [1, 2])
 def test_cp_steps_match_oracle(w1, norm, shape, path):
+    """Steps of eq. primaldual from the same random state on odd shapes: 1xN and
+    Nx1 strips, ragged widths, several warps and several cluster bands."""
     ny, nx = shape
-    if path == 1 and ny * nx > 16 * 4096:
+    if path == 1 and not resident_fits(nx, ny):
         pytest.skip("larger than the resident path")
     rng = np.random.default_rng(ny * 1000 + nx + norm)
     rho, m1, m2, phi = rand_state(rng, ny, nx)
@@ -280,3 +287,9 @@ def test_caller_workspace(w1):
         plan.set_workspace(ws)
         v_ws, _, _ = plan.solve(dev(r0), dev(r1))
     assert v_own == v_ws
+
+
+def test_resident_path_rejects_grids_it_cannot_hold(w1):
+    g = [torch.zeros((200, 300), device="cuda") for _ in range(4)]
+    with pytest.raises(w1.W1Error, match="ERR_UNSUPPORTED"):
+        w1.cp_steps(*g, 1 / 300, 1, 1e-3, 1e-3, 2, path=1)
