@@ -175,6 +175,31 @@ w1_status w1_prolong(int ncx, int ncy, const float* m1c, const float* m2c, const
 w1_status w1_state_stats(int nx, int ny, double h, int norm, const float* rho, const float* m1, const float* m2,
                          const float* phi, void* stream, w1_stats* out);
 
+/*
+ * w1_state_stats without allocating device memory.  The paper has no
+ * counterpart; this exists for callers that cannot call cudaMalloc: code that
+ * runs while a stream is captured into a CUDA graph (allocation is not allowed
+ * there), loops that must not pay cudaMalloc/cudaFree's implicit device
+ * synchronisation, and frameworks that own all device memory through their
+ * own pools.  Same arguments, results and numbers as w1_state_stats.
+ *   - Scratch lives in one file-scope static device array of about 4.2 MB
+ *     (control block, partial sums, 2 * W1_NOALLOC_MAX_NODES FP64 masses) that
+ *     every GPU loading the library holds until the process exits.
+ *   - Grids with more than W1_NOALLOC_MAX_NODES nodes are rejected with
+ *     W1_ERR_INVALID_ARG (message in w1_noalloc_last_error()).
+ *   - The first call on a device looks up the array's device address with that
+ *     device current; make that first call before any stream capture.
+ *   - Every call on a device shares the one array, which keeps the last call's
+ *     contents (the call clears what must start at zero).  Calls whose work
+ *     overlaps on the GPU (other streams, other host threads) race on it:
+ *     serialise them.
+ *   - The call copies the result to the host and synchronises the stream.
+ */
+#define W1_NOALLOC_MAX_NODES 262144
+w1_status w1_state_stats_noalloc(int nx, int ny, double h, int norm, const float* rho, const float* m1,
+                                 const float* m2, const float* phi, void* stream, w1_stats* out);
+const char* w1_noalloc_last_error(void);
+
 /* Text for a status, and the last error message of the calling thread. */
 const char* w1_status_string(w1_status s);
 const char* w1_last_error(void);

@@ -111,6 +111,8 @@ def _load() -> ctypes.CDLL:
         "w1_restrict": (st, [I, I, P, P, P]),
         "w1_prolong": (st, [I, I, P, P, P, P, P, P, P]),
         "w1_state_stats": (st, [I, I, D, I, P, P, P, P, P, ctypes.POINTER(_Stats)]),
+        "w1_state_stats_noalloc": (st, [I, I, D, I, P, P, P, P, P, ctypes.POINTER(_Stats)]),
+        "w1_noalloc_last_error": (ctypes.c_char_p, []),
         "w1_status_string": (ctypes.c_char_p, [st]),
         "w1_last_error": (ctypes.c_char_p, []),
     }
