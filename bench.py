@@ -1,10 +1,11 @@
 """Benchmark: W1 solves/s at 512x512 on the GB300 (one JSON line on stdout).
 
 Workload (512x512 image-shaped pairs, 6-level cascade 16->512, both norms):
-one step = a fresh density pair (already resident in HBM) solved with the L1
-and the L2 ground norm, i.e. two full Algorithm-3 solves, each ending with the
-read-back of its W1 value.  The L2 cache is flushed (a 256 MiB write) before
-every step, inside the timed region.
+one step = a batch of B fresh density pairs (already resident in HBM) solved
+with the L1 and with the L2 ground norm through w1_solve_batch, i.e. 2B full
+Algorithm-3 solves, each batch ending with the read-back of its W1 values.
+The L2 cache is flushed (a 256 MiB write) before every step, inside the timed
+region.
 
 Also measured in the same run:
   e2e      : the same solves through w1_solve_host (host densities, H2D copies
@@ -170,8 +171,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "ellipse_texture_512x512_pair_6_levels_both_norms", "grid": [N, N],
-                   "levels": LEVELS, "norms": ["L1", "L2"], "stop": "FPR, eq. stop_tol"},
+        "config": {"workload": "ellipse_texture_512x512_pairs_6_levels_both_norms", "grid": [N, N],
+                   "levels": LEVELS, "norms": ["L1", "L2"], "stop": "FPR, eq. stop_tol",
+                   "batch_per_norm": args.batch},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
                          "sample": "per-level step cost timed on a bounded sample (" + sample +
                                    "), scaled by the oracle's own per-level iteration counts"},
@@ -196,35 +198,81 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
     stream = torch.cuda.current_stream()
-    plans = {norm: w1.Plan(N, N, levels=LEVELS, norm=norm) for norm in NORMS}
+    B = args.batch
     total_steps = args.warmup + args.steps
     # distinct pairs per step and rank, resident in HBM before timing
     host_pairs, dev_pairs = [], []
     for s in range(total_steps):
-        k = rank * 1000 + s
-        r0, r1 = synth.pair(WORKLOAD, k)
-        a0, a1 = (np.ascontiguousarray(x, dtype=np.float32) for x in (r0, r1))
-        host_pairs.append((a0, a1))
+        r = [synth.pair(WORKLOAD, rank * 100000 + s * B + k) for k in range(B)]
+        a0 = np.ascontiguousarray(np.stack([x[0] for x in r]), dtype=np.float32)
+        a1 = np.ascontiguousarray(np.stack([x[1] for x in r]), dtype=np.float32)
+        host_pairs.append((torch.from_numpy(a0).pin_memory(), torch.from_numpy(a1).pin_memory()))
         dev_pairs.append((torch.from_numpy(a0).cuda(), torch.from_numpy(a1).cuda()))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ok = (w1.OK, w1.ERR_NOT_CONVERGED)
+    if args.mode == "lockstep":
+        # one batched plan per norm: every launch advances all B pairs together
+        plans = {norm: w1.Plan(N, N, levels=LEVELS, norm=norm, batch=B) for norm in NORMS}
+    else:
+        # lanes: one plan and one stream per pair, all enqueued asynchronously, so
+        # every pair moves through its levels at its own pace and the kernels of
+        # different pairs overlap on the device
+        plans = {norm: [w1.Plan(N, N, levels=LEVELS, norm=norm) for _ in range(B)] for norm in NORMS}
+        lanes = {norm: [torch.cuda.Stream() for _ in range(B)] for norm in NORMS}
+        done_ev = {norm: [torch.cuda.Event(enable_timing=True) for _ in range(B)] for norm in NORMS}
+    pair_ms = []
+    in_dev = [torch.empty((B, N, N), device="cuda") for _ in range(2)]
 
     def do_step(s, host=False):
         flush.fill_(float(s))
         out = []
+        if host:
+            # end to end: copy this step's inputs from pinned host memory first
+            in_dev[0].copy_(host_pairs[s][0], non_blocking=True)
+            in_dev[1].copy_(host_pairs[s][1], non_blocking=True)
+            t0, t1 = in_dev
+        else:
+            t0, t1 = dev_pairs[s]
+        if args.mode == "lockstep":
+            for norm in NORMS:
+                v, st, _, _ = plans[norm].solve_batch(t0, t1, stream=stream, allow=ok)
+                out.append((v, st))
+            return out
+        ready = torch.cuda.Event(enable_timing=True)
+        ready.record(stream)
         for norm in NORMS:
-            if host:
-                a0, a1 = host_pairs[s]
-                v, st, _ = plans[norm].solve_host(a0, a1, stream=stream, allow=(w1.OK, w1.ERR_NOT_CONVERGED))
-            else:
-                t0, t1 = dev_pairs[s]
-                v, st, _ = plans[norm].solve(t0, t1, stream=stream, allow=(w1.OK, w1.ERR_NOT_CONVERGED))
-            out.append((v, st))
+            for b in range(B):
+                lanes[norm][b].wait_event(ready)
+                plans[norm][b].solve_async(t0[b], t1[b], stream=lanes[norm][b])
+                done_ev[norm][b].record(lanes[norm][b])
+        for norm in NORMS:
+            vals, sts = [], []
+            for b in range(B):
+                lanes[norm][b].synchronize()
+                v, st, _, _ = plans[norm][b].results(allow=ok)
+                vals.append(v[0])
+                sts.append(st[0])
+                pair_ms.append(ready.elapsed_time(done_ev[norm][b]))
+            out.append((vals, sts))
         return out
 
-    def launches(st):
-        n = 2 + (st.levels - 1) + st.levels + (st.levels - 1) + 2
-        for p, it in zip(st.path, st.iters):
-            n += 1 if p == 1 else it
+    def launches(sts):
+        # prep 2, restrictions, level starts, prolongations, final 2; one launch per
+        # resident level; per streaming level the steps plus one decide kernel per
+        # K steps (for a batched plan: those of the slowest pair)
+        st = sts[0]
+        per = 2 + (st.levels - 1) + st.levels + (st.levels - 1) + 2
+        if args.mode == "lockstep":
+            n = per
+            for lvl, p in enumerate(st.path):
+                k = max(x.iters[lvl] for x in sts)
+                n += 1 if p == 1 else k + k // 32
+            return n
+        n = 0
+        for x in sts:
+            n += per
+            for lvl, p in enumerate(x.path):
+                n += 1 if p == 1 else x.iters[lvl] + x.iters[lvl] // 32
         return n
 
     def barrier():
@@ -242,6 +290,7 @@ def run_gpu(args):
     for s in range(args.warmup):
         do_step(s)
     barrier()
+    pair_ms.clear()
     results = []
     step_ms = []
     with ClockSampler(local) as clk:
@@ -254,9 +303,10 @@ def run_gpu(args):
         barrier()
         elapsed = time.perf_counter() - t0
     elapsed = max_over_ranks(elapsed)
-    solves = args.steps * len(NORMS) * world
+    solves = args.steps * len(NORMS) * B * world
     value = solves / elapsed
-    n_launch = sum(launches(st) for step in results for _, st in step)
+    n_launch = sum(launches(sts) for step in results for _, sts in step)
+    pair_lat = list(pair_ms)
 
     # end to end through the host entry point
     e2e = None
@@ -268,7 +318,7 @@ def run_gpu(args):
         barrier()
         e2e_el = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": solves / e2e_el, "unit": "solves/s",
-               "h2d_bytes_per_step": 2 * N * N * 4 * len(NORMS), "d2h_bytes_per_step": 552 * len(NORMS)}
+               "h2d_bytes_per_step": 2 * N * N * 4 * B, "d2h_bytes_per_step": 552 * B * len(NORMS)}
 
     # roofline of the streaming step kernel (8192^2, T = 1)
     roof = None
@@ -278,18 +328,23 @@ def run_gpu(args):
     line = None
     if rank == 0:
         lat = np.array(step_ms) / len(NORMS)
-        iters = {f"L{n}": results[-1][i][1].iters for i, n in enumerate(NORMS)}
+        iters = {f"L{n}": results[-1][i][1][0].iters for i, n in enumerate(NORMS)}
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 iterates, f64 reductions", "data": "synthetic",
-            "config": {"workload": "ellipse_texture_512x512_pair_6_levels_both_norms", "grid": [N, N],
+            "config": {"workload": "ellipse_texture_512x512_pairs_6_levels_both_norms", "grid": [N, N],
                        "levels": LEVELS, "norms": ["L1", "L2"], "stop": "FPR, eq. stop_tol",
+                       "batch_per_norm": B, "mode": args.mode,
                        "l2": "flushed before every step (256 MiB write, inside the timed region)",
                        "parallelism": f"replicas x{world}"},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-            "iters": iters,
-            "w1": [[v for v, _ in step] for step in results[:2]],
+            "batch_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                 "what": "one step (B pairs, both norms) / 2, submit to W1 values on the host"},
+            "pair_latency_ms": ({"p50": float(np.percentile(pair_lat, 50)), "p99": float(np.percentile(pair_lat, 99)),
+                                 "what": "per pair: step start to the end of its solve on its stream (CUDA events)"}
+                                if pair_lat else None),
+            "iters_first_pair": iters,
+            "w1_first_step": [[float(x) for x in v] for v, _ in results[0]],
             "gpu_launches": n_launch,
             "e2e": e2e,
             "roofline": roof,
@@ -303,7 +358,8 @@ def run_gpu(args):
                                               "), scaled by the oracle's own per-level iteration counts"}
         print(json.dumps(line), flush=True)
     for p in plans.values():
-        p.close()
+        for q in (p if isinstance(p, list) else [p]):
+            q.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
@@ -341,6 +397,9 @@ def roofline_stream(w1, torch, stream, args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--batch", type=int, default=32, help="pairs per norm per step")
+    ap.add_argument("--mode", default="lanes", choices=["lanes", "lockstep"],
+                    help="lanes: one async plan+stream per pair; lockstep: one batched plan per norm")
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
@@ -350,7 +409,11 @@ def main():
     ap.add_argument("--roof-iters", type=int, default=100)
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--only", default="solve", choices=["solve", "stream-kernel", "resident-kernel"],
+    ap.add_argument("--rates", default="10,30,100,300,1000,2000", help="serving: arrival rates (req/s)")
+    ap.add_argument("--requests", type=int, default=400, help="serving: requests per rate (at least)")
+    ap.add_argument("--min-seconds", type=float, default=0.0, help="serving: at least rate*this requests")
+    ap.add_argument("--slots", type=int, default=48, help="serving: solves in flight")
+    ap.add_argument("--only", default="solve", choices=["solve", "stream-kernel", "resident-kernel", "serve"],
                     help="kernel-only runs for profiling: one level's steps through w1_cp_steps")
     ap.add_argument("--kn", type=int, default=256, help="grid side for --only *-kernel")
     ap.add_argument("--kiters", type=int, default=1000, help="steps for --only *-kernel")
@@ -358,9 +421,87 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only == "serve":
+        return run_serve(args)
     if args.only != "solve":
         return run_kernel_only(args)
     return run_gpu(args)
+
+
+SERVE_SIZES = (128, 256, 512, 1024)
+SERVE_PROBS = (0.4, 0.3, 0.2, 0.1)
+
+
+def serve_pool(torch, rank=0, per_size=(24, 16, 8, 4)):
+    """Device-resident ellipse-texture pairs for each serving size."""
+    import synth
+    pool = {}
+    for size, cnt in zip(SERVE_SIZES, per_size):
+        pool[size] = []
+        for k in range(cnt):
+            r0, r1 = synth.pair(4, rank * 100000 + size * 100 + k, n=size)
+            pool[size].append(tuple(torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+                                    for x in (r0, r1)))
+    return pool
+
+
+def serve_run(w1, srv, pool, rate, n_req, seed):
+    """Poisson arrivals at `rate` req/s of mixed sizes and norms; returns
+    (p50 ms, p99 ms, completed/s, statuses)."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, n_req)
+    sizes = rng.choice(SERVE_SIZES, size=n_req, p=SERVE_PROBS)
+    norms = rng.integers(1, 3, n_req)
+    picks = rng.integers(0, 1 << 30, n_req)
+    tickets = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for k in range(n_req):
+        t_next += gaps[k]
+        while True:
+            d = t_next - time.perf_counter()
+            if d <= 0:
+                break
+            time.sleep(min(d, 0.002))
+        lst = pool[int(sizes[k])]
+        a, b = lst[picks[k] % len(lst)]
+        tickets.append(srv.submit(a, b, norm=int(norms[k])))
+    lat, statuses = [], []
+    for t in tickets:
+        while True:
+            st, v, stats, l = srv.poll(t)
+            if st != w1.PENDING:
+                break
+            time.sleep(0.0005)
+        statuses.append(st)
+        lat.append(l)
+    t_end = time.perf_counter()
+    lat = np.array(lat) * 1e3
+    return float(np.percentile(lat, 50)), float(np.percentile(lat, 99)), n_req / (t_end - t0), statuses
+
+
+def run_serve(args):
+    import torch
+
+    from paper_1810_00118_gb300 import w1
+
+    pool = serve_pool(torch)
+    rates = [float(x) for x in args.rates.split(",")]
+    out = []
+    with w1.Server(hbm_budget_bytes=40 << 30, max_slots=args.slots) as srv:
+        # warm-up: one request of every class builds its slot
+        serve_run(w1, srv, pool, 1000.0, 16, seed=1)
+        for r in rates:
+            n = max(args.requests, int(r * args.min_seconds))
+            p50, p99, thr, sts = serve_run(w1, srv, pool, r, n, seed=int(r))
+            bad = sum(1 for x in sts if x not in (w1.OK, w1.ERR_NOT_CONVERGED))
+            out.append({"rate_req_s": r, "requests": n, "p50_ms": p50, "p99_ms": p99, "solves_per_s": thr,
+                        "failed": bad})
+            print(json.dumps(out[-1]), flush=True)
+        info = srv.info()
+    print(json.dumps({"serving": out, "server": info, "sizes": SERVE_SIZES, "probs": SERVE_PROBS,
+                      "budget_GiB": 40, "slots": args.slots}))
+    return 0
 
 
 def run_kernel_only(args):

@@ -120,6 +120,15 @@ w1_status w1_plan_create_ex(int nx, int ny, double h, int levels, int norm, doub
                             w1_plan** out);
 w1_status w1_plan_destroy(w1_plan* plan);
 
+/*
+ * A plan for batches of up to max_batch pairs of the same grid (north-star
+ * batching; every kernel launch advances all pairs of the batch).  Arguments
+ * as w1_plan_create_ex.  Device memory grows linearly with max_batch.
+ */
+w1_status w1_plan_create_batch(int nx, int ny, double h, int levels, int norm, double tol, int max_batch,
+                               const w1_options* opt, w1_plan** out);
+int w1_plan_max_batch(const w1_plan* plan);
+
 /* Bytes of device workspace the plan needs (levels' state, reductions). */
 size_t w1_plan_workspace_bytes(const w1_plan* plan);
 /* Use caller-owned device memory (>= w1_plan_workspace_bytes, 256-byte aligned)
@@ -139,14 +148,100 @@ w1_status w1_plan_set_workspace(w1_plan* plan, void* device_ptr, size_t bytes);
 w1_status w1_solve(w1_plan* plan, const float* rho0, const float* rho1, void* stream, double* dist, float* flux,
                    w1_stats* stats);
 
+/*
+ * Solves `batch` pairs (1 <= batch <= max_batch) in one pass of Algorithm 3.
+ *   rho0, rho1 : device, [batch][ny][nx] float32.
+ *   dist       : host [batch].  flux: device [batch][2][ny][nx] or NULL.
+ *   stats      : host [batch] or NULL.  status: host [batch] or NULL, each
+ *                pair's own status (W1_OK, W1_ERR_MASS, W1_ERR_NOT_CONVERGED,
+ *                W1_ERR_TIMEOUT).
+ * Pairs are independent: each stops on its own test, and a rejected pair does
+ * not affect the others.  Returns W1_OK when every pair is W1_OK, else the
+ * first pair's non-OK status (dist of a rejected pair is NaN).
+ */
+w1_status w1_solve_batch(w1_plan* plan, int batch, const float* rho0, const float* rho1, void* stream, double* dist,
+                         float* flux, w1_stats* stats, int* status);
+/*
+ * Asynchronous solve: enqueues everything w1_solve_batch does on `stream` and
+ * returns without waiting.  Once the stream has passed the enqueued work
+ * (cudaStreamSynchronize, an event, a host callback), w1_plan_results() gives
+ * dist, stats and per-pair status exactly as w1_solve_batch would.  A plan
+ * holds the results of its last enqueued solve only, and must not have two
+ * solves in flight at once (use one plan per stream for concurrent solves;
+ * their work overlaps on the device).  rho0/rho1/flux must stay valid until
+ * the stream has passed the solve.
+ */
+w1_status w1_solve_async(w1_plan* plan, int batch, const float* rho0, const float* rho1, void* stream, float* flux);
+w1_status w1_plan_results(w1_plan* plan, double* dist, w1_stats* stats, int* status);
+
+/* w1_solve_batch for host (pageable or pinned) densities and flux; the copies
+ * to and from the device are part of the call. */
+w1_status w1_solve_batch_host(w1_plan* plan, int batch, const float* rho0, const float* rho1, void* stream,
+                              double* dist, float* flux, w1_stats* stats, int* status);
+
 /* Same as w1_solve, for densities and flux in (pageable or pinned) host
  * memory: the copies to and from the device are part of the call. */
 w1_status w1_solve_host(w1_plan* plan, const float* rho0, const float* rho1, void* stream, double* dist,
                         float* flux, w1_stats* stats);
 
-/* Final potential phi of the last solve, device [ny][nx] float32 (the
+/* Final potential phi of the last solve, device [batch][ny][nx] float32 (the
  * Kantorovich potential of Algorithm 1, Appendix B); enqueued on stream. */
 w1_status w1_plan_potential(w1_plan* plan, float* phi, void* stream);
+
+/* Device bytes a plan with these arguments would allocate (0 on invalid
+ * arguments); lets a caller admit work against a memory budget. */
+size_t w1_plan_bytes(int nx, int ny, double h, int levels, int norm, double tol, int max_batch,
+                     const w1_options* opt);
+
+/* ------------------------------------------------------------------------- */
+/* Serving: continuous batching of W1 requests of mixed sizes                */
+/* ------------------------------------------------------------------------- */
+/*
+ * A server owns a worker thread and device-resident plans ("slots") for the
+ * size classes it has seen (grid, h, levels, norm, tol).  Requests are queued
+ * by w1_submit and started as soon as a slot of their class is free or can be
+ * created within the HBM budget (idle slots of other classes are evicted,
+ * least recently used first); up to max_slots solves run at once on their own
+ * streams, so their work overlaps on the device.  A request's result does not
+ * depend on what else is in flight.  All calls are thread-safe.
+ */
+typedef struct w1_server w1_server;
+
+typedef struct {
+    size_t hbm_budget_bytes; /* device memory for slots (plans + input staging); default 40 GiB */
+    int max_slots;           /* solves in flight at once; default 32 */
+    int max_batch;           /* requests of one class solved together in a slot; default 1 */
+    w1_options opt;          /* plan options of every slot */
+} w1_server_config;
+
+typedef struct {
+    long long submitted, completed, rejected, queued, in_flight, slots, evictions;
+    size_t bytes_in_use;
+} w1_server_info;
+
+void w1_server_default_config(w1_server_config* cfg);
+/* hbm_budget_bytes = 0 and max_slots <= 0 take the defaults. Uses the current device. */
+w1_status w1_server_create(size_t hbm_budget_bytes, int max_slots, w1_server** out);
+w1_status w1_server_create_ex(const w1_server_config* cfg, w1_server** out);
+/*
+ * Queues one request (arguments as w1_plan_create + w1_solve).  rho0, rho1 are
+ * device [ny][nx] float32 and must stay valid until the request is finished.
+ * Returns W1_ERR_BUDGET if one slot of this class alone exceeds the budget,
+ * W1_ERR_SHAPE / W1_ERR_INVALID_ARG for bad arguments.
+ */
+w1_status w1_submit(w1_server* srv, int nx, int ny, double h, int levels, int norm, double tol, const float* rho0,
+                    const float* rho1, uint64_t* ticket);
+/* W1_PENDING while queued or running; then the request's own status (as
+ * w1_solve) with dist and stats written, and the ticket is released. */
+w1_status w1_poll(w1_server* srv, uint64_t ticket, double* dist, w1_stats* stats);
+/* w1_poll that also returns the submit-to-finish time measured by the server. */
+w1_status w1_poll_latency(w1_server* srv, uint64_t ticket, double* dist, w1_stats* stats, double* latency_s);
+/* Blocks until the request finishes or timeout_s passes (<= 0: no limit). */
+w1_status w1_wait(w1_server* srv, uint64_t ticket, double timeout_s, double* dist, w1_stats* stats);
+w1_status w1_server_query(w1_server* srv, w1_server_info* info);
+/* Finishes the solves in flight, fails queued requests, frees every slot. */
+w1_status w1_server_destroy(w1_server* srv);
+const char* w1_server_last_error(void);
 
 /* ------------------------------------------------------------------------- */
 /* Building blocks (device pointers, float32 planes [ny][nx]); used by the   */

@@ -1,5 +1,10 @@
 // w1_internal.h -- declarations shared by the kernels and the host driver of the
 // GB300 W1 library (not part of the public ABI; include/w1.h is).
+//
+// Batching: a plan holds `B` pairs of the same grid.  Every plane of level l is
+// stored as B consecutive [ny_l][nx_l] planes (pair stride n_l = nx_l * ny_l),
+// and every kernel takes the pair from its grid (blockIdx.z, blockIdx.y, or the
+// cluster index), so one launch advances all pairs.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -9,13 +14,13 @@
 
 namespace w1 {
 
-// Device-resident control block of one plan: reduction counter, error flags,
-// per-level iteration counts and residuals, and the final statistics.
+// Per-pair device control block: reduction counter, flags, per-level iteration
+// counts and residuals, and the final statistics.
 struct Ctl {
-    unsigned int counter;  // last-block counter of the grid reductions (reset by the last block)
-    int error;             // 1: rejected input (mass imbalance or non-finite value)
+    unsigned int counter;  // last-block counter of this pair's grid reductions (reset by the last block)
+    int error;             // 0 ok, 1 rejected input (mass or non-finite), 2 unused batch slot
     int timeout;           // 1: a level hit the wall-clock guard
-    int pad0;
+    int active;            // streaming level: 1 while this pair still iterates
     double mass0, mass1, mean;
     long long iters[W1_MAX_LEVELS];
     double fpr[W1_MAX_LEVELS];
@@ -36,12 +41,13 @@ struct IterArgs {
     int fixed;          // 1: take exactly `cap` steps, form R^k of the last one
     int level;
     unsigned long long budget_ns;
-    Ctl* ctl;
-    double* fpr_out;       // optional (device): R^k of the last tested step
-    long long* iters_out;  // optional (device)
+    long long stride;      // elements between consecutive pairs' planes
+    Ctl* ctl;              // per-pair control blocks (may be null for building blocks)
+    double* fpr_out;       // optional (device, per pair): R^k of the last tested step
+    long long* iters_out;  // optional (device, per pair)
 };
 
-// Streaming (global memory) one-step kernel arguments.
+// Streaming (global memory) one-step kernel arguments; pointers are pair 0's planes.
 struct StepArgs {
     const float* m1;
     const float* m2;
@@ -51,10 +57,10 @@ struct StepArgs {
     float* m2o;
     float* phio;
     int rows;  // rows marched per thread
+    int pairs;
     IterArgs it;
-    double* part;  // per-block partials (check step)
-    cudaGraphConditionalHandle cond;
-    int use_cond;
+    double* part;  // per-pair, per-block partials (check step)
+    int use_cond;  // graph mode: keep per-pair active flags and counts
 };
 
 // Shared-memory resident level solver arguments (state in place).
@@ -63,33 +69,38 @@ struct ResArgs {
     float* m2;
     float* phi;
     const float* rho;
+    int pairs;
     IterArgs it;
 };
 
 // Kernel launchers (w1_kernels.cu).  All enqueue on `s` and return the launch status.
-cudaError_t launch_prep(const float* r0, const float* r1, long long n, double h, Ctl* ctl, double* part,
-                        float* rho, cudaStream_t s);
-cudaError_t launch_restrict(const float* fine, int nx, int ny, float* coarse, cudaStream_t s);
+// prep: rho = rho0 - rho1 per pair, mass check, exact zero mean; pairs >= nbatch are
+// marked unused.  r0, r1 and rho have pair stride n.
+cudaError_t launch_prep(const float* r0, const float* r1, long long n, int nbatch, int pairs, double h, Ctl* ctl,
+                        double* part, float* rho, cudaStream_t s);
+size_t prep_part_doubles(int pairs);
+cudaError_t launch_restrict(const float* fine, int nx, int ny, float* coarse, int pairs, const Ctl* ctl,
+                            cudaStream_t s);
 cudaError_t launch_prolong(int ncx, int ncy, const float* m1c, const float* m2c, const float* phic, float* m1f,
-                           float* m2f, float* phif, cudaStream_t s);
-cudaError_t launch_level_begin(Ctl* ctl, int level, cudaStream_t s);
+                           float* m2f, float* phif, int pairs, const Ctl* ctl, cudaStream_t s);
+cudaError_t launch_level_begin(Ctl* ctl, int level, int pairs, cudaStream_t s);
 // Streaming step; check selects the variant that forms R^k and tests it.
 cudaError_t launch_step(int norm, bool check, const StepArgs& a, cudaStream_t s);
-int stream_rows_auto(int nx, int ny);
-dim3 stream_grid(int nx, int ny, int rows);
-// Resident level solve with a cluster of `cluster` CTAs.
+// After a check step in graph mode: continue the WHILE node while any pair is active.
+cudaError_t launch_decide(const Ctl* ctl, int pairs, cudaGraphConditionalHandle cond, cudaStream_t s);
+int stream_rows_auto(int nx, int ny, int pairs);
+dim3 stream_grid(int nx, int ny, int rows, int pairs);
+size_t step_part_doubles(int nx, int ny, int rows, int pairs);
+// Resident level solve with a cluster of `cluster` CTAs per pair.
 cudaError_t launch_resident(int norm, int cluster, const ResArgs& a, cudaStream_t s);
-// Largest band (nodes per CTA) the resident kernel takes, and the cluster size
-// it would use for a level (0 when the level does not fit).
 int resident_max_nodes();
 int resident_cluster_for(int nx, int ny);
 cudaError_t resident_prepare(int device);
 // Active clusters the device can hold for this configuration (0: cannot launch).
 int resident_cluster_ok(int norm, int cluster, int nx, int ny);
-// Final statistics of a state into ctl (q: FP64 scratch of 2 * nx * ny).
+// Final statistics of a state into ctl (q: FP64 scratch of 2 * nx * ny per pair).
 cudaError_t launch_final(int norm, const float* m1, const float* m2, const float* phi, const float* rho, int nx,
-                         int ny, double h, double* q, double* part, Ctl* ctl, cudaStream_t s);
-size_t final_part_doubles();
-size_t step_part_doubles(int nx, int ny, int rows);
+                         int ny, double h, double* q, double* part, Ctl* ctl, int pairs, cudaStream_t s);
+size_t final_part_doubles(int pairs);
 
 }  // namespace w1

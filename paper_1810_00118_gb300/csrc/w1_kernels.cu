@@ -12,14 +12,15 @@
 //
 // The step is a memory-bound 5-point stencil (about 30 flops per 28 bytes), so
 // no tensor cores are involved.  Two level paths:
-//   * resident: a whole level lives in shared memory and registers of one CTA
-//     or of a thread-block cluster (bands of rows, halo rows read through
-//     distributed shared memory); all iterations and stop tests of the level run
-//     inside one launch, two cluster barriers per step.
+//   * resident: a whole level lives on chip in one CTA or one thread-block
+//     cluster (bands of rows; halo rows read through distributed shared
+//     memory); all steps and stop tests of the level run inside one launch.
 //   * streaming: one launch per step over global memory (ping-pong buffers);
 //     each warp covers 32 columns and marches up a strip of rows, carrying the
-//     row below in registers and exchanging the left/right neighbours by warp
-//     shuffles, so every value is read once per step (28 B/node/step).
+//     row below in registers, prefetching the row above, and exchanging the
+//     left/right neighbours by warp shuffles, so every value is read once per
+//     step (28 B/node/step).
+// Every kernel is batched over the pairs of a plan (same grid for all pairs).
 // Reductions are FP64 with a fixed summation order (deterministic).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -65,6 +66,36 @@ __device__ __forceinline__ unsigned long long globaltimer()
     return t;
 }
 
+// Distributed shared memory through 32-bit shared::cluster addresses (cheaper
+// in registers than generic 64-bit pointers).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t dsmem_map(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float dsmem_ld(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void dsmem_st_f64(uint32_t addr, double v)
+{
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ double dsmem_ld_f64(uint32_t addr)
+{
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+// Split cluster barrier (release on arrive, acquire on wait).
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
 // Warp / block reductions in a fixed order.
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -105,14 +136,34 @@ __device__ void block_sum(double (&v)[N], double* sh)
 // Prep: rho = rho0 - rho1 (Sec. 2.2), mass check, exact zero mean
 // ---------------------------------------------------------------------------
 
-static constexpr int PREP_BLOCKS = 304, PREP_THREADS = 256;
+static constexpr int PREP_THREADS = 256;
+
+// A fixed number of blocks per pair, whatever the batch size, so that every
+// pair's sums run in the same order alone and inside a batch (bitwise equal results).
+static constexpr int PREP_BLOCKS_PER_PAIR = 64;
+static int prep_blocks_per_pair(int) { return PREP_BLOCKS_PER_PAIR; }
+
+size_t prep_part_doubles(int pairs) { return (size_t)prep_blocks_per_pair(pairs) * pairs * 4; }
 
 __global__ void __launch_bounds__(PREP_THREADS) k_prep_reduce(const float* __restrict__ r0,
-                                                              const float* __restrict__ r1, long long n, double h,
-                                                              Ctl* ctl, double* part)
+                                                              const float* __restrict__ r1, long long n, int nbatch,
+                                                              double h, Ctl* ctls, double* part)
 {
     __shared__ double sh[32 * 4];
     __shared__ bool last;
+    const int pair = blockIdx.y;
+    Ctl* ctl = ctls + pair;
+    if (pair >= nbatch) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctl->error = 2;
+            ctl->timeout = 0;
+            ctl->counter = 0;
+        }
+        return;
+    }
+    r0 += (size_t)pair * n;
+    r1 += (size_t)pair * n;
+    double* pp = part + (size_t)pair * gridDim.x * 4;
     double v[4] = {0.0, 0.0, 0.0, 0.0};  // sum r0, sum r1, sum (r0 - r1), non-finite count
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         float a = r0[k], b = r1[k];
@@ -123,7 +174,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep_reduce(const float* __res
     }
     block_sum<4>(v, sh);
     if (threadIdx.x == 0) {
-        for (int c = 0; c < 4; ++c) part[blockIdx.x * 4 + c] = v[c];
+        for (int c = 0; c < 4; ++c) pp[blockIdx.x * 4 + c] = v[c];
         __threadfence();
         last = (atomicAdd(&ctl->counter, 1u) == gridDim.x - 1);
     }
@@ -132,7 +183,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep_reduce(const float* __res
     __threadfence();
     double t[4] = {0.0, 0.0, 0.0, 0.0};
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-        for (int c = 0; c < 4; ++c) t[c] += ((volatile double*)part)[b * 4 + c];
+        for (int c = 0; c < 4; ++c) t[c] += ((volatile double*)pp)[b * 4 + c];
     block_sum<4>(t, sh);
     if (threadIdx.x == 0) {
         double M0 = t[0] * h * h, M1 = t[1] * h * h;
@@ -146,19 +197,23 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep_reduce(const float* __res
     }
 }
 
-__global__ void k_prep_apply(const float* __restrict__ r0, const float* __restrict__ r1, long long n,
-                             const Ctl* __restrict__ ctl, float* __restrict__ rho)
+__global__ void k_prep_apply(const float* __restrict__ r0, const float* __restrict__ r1, long long n, int nbatch,
+                             const Ctl* __restrict__ ctls, float* __restrict__ rho)
 {
-    const double mean = ctl->mean;
+    const int pair = blockIdx.y;
+    if (pair >= nbatch) return;
+    const double mean = ctls[pair].mean;
+    const size_t off = (size_t)pair * n;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
-        rho[k] = (float)(((double)r0[k] - (double)r1[k]) - mean);
+        rho[off + k] = (float)(((double)r0[off + k] - (double)r1[off + k]) - mean);
 }
 
-cudaError_t launch_prep(const float* r0, const float* r1, long long n, double h, Ctl* ctl, double* part,
-                        float* rho, cudaStream_t s)
+cudaError_t launch_prep(const float* r0, const float* r1, long long n, int nbatch, int pairs, double h, Ctl* ctl,
+                        double* part, float* rho, cudaStream_t s)
 {
-    k_prep_reduce<<<PREP_BLOCKS, PREP_THREADS, 0, s>>>(r0, r1, n, h, ctl, part);
-    k_prep_apply<<<PREP_BLOCKS * 2, 256, 0, s>>>(r0, r1, n, ctl, rho);
+    const int bpp = prep_blocks_per_pair(pairs);
+    k_prep_reduce<<<dim3(bpp, pairs), PREP_THREADS, 0, s>>>(r0, r1, n, nbatch, h, ctl, part);
+    k_prep_apply<<<dim3(2 * bpp, pairs), 256, 0, s>>>(r0, r1, n, nbatch, ctl, rho);
     return cudaGetLastError();
 }
 
@@ -166,20 +221,25 @@ cudaError_t launch_prep(const float* r0, const float* r1, long long n, double h,
 // Restriction (2x2 block mean) and Interpolate (Sec. 3.3, pixel-grid reading)
 // ---------------------------------------------------------------------------
 
-__global__ void k_restrict(const float* __restrict__ f, int nx, int ny, float* __restrict__ c)
+__global__ void k_restrict(const float* __restrict__ f, int nx, int ny, float* __restrict__ c, const Ctl* ctls)
 {
     const int ncx = nx / 2, ncy = ny / 2;
+    const int pair = blockIdx.z;
+    if (ctls && ctls[pair].error) return;
     const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
     if (I >= ncx || J >= ncy) return;
+    f += (size_t)pair * nx * ny;
+    c += (size_t)pair * ncx * ncy;
     const float* r0 = f + (size_t)(2 * J) * nx + 2 * I;
     const float* r1 = r0 + nx;
     c[(size_t)J * ncx + I] = 0.25f * ((r0[0] + r0[1]) + (r1[0] + r1[1]));
 }
 
-cudaError_t launch_restrict(const float* fine, int nx, int ny, float* coarse, cudaStream_t s)
+cudaError_t launch_restrict(const float* fine, int nx, int ny, float* coarse, int pairs, const Ctl* ctl,
+                            cudaStream_t s)
 {
-    dim3 b(32, 8), g((nx / 2 + 31) / 32, (ny / 2 + 7) / 8);
-    k_restrict<<<g, b, 0, s>>>(fine, nx, ny, coarse);
+    dim3 b(32, 8), g((nx / 2 + 31) / 32, (ny / 2 + 7) / 8, pairs);
+    k_restrict<<<g, b, 0, s>>>(fine, nx, ny, coarse, ctl);
     return cudaGetLastError();
 }
 
@@ -189,11 +249,17 @@ cudaError_t launch_restrict(const float* fine, int nx, int ny, float* coarse, cu
 // copy; m2 likewise with the axes exchanged.
 __global__ void k_prolong(int ncx, int ncy, const float* __restrict__ m1c, const float* __restrict__ m2c,
                           const float* __restrict__ phic, float* __restrict__ m1f, float* __restrict__ m2f,
-                          float* __restrict__ phif)
+                          float* __restrict__ phif, const Ctl* ctls)
 {
     const int nx = 2 * ncx, ny = 2 * ncy;
+    const int pair = blockIdx.z;
+    if (ctls && ctls[pair].error) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= nx || j >= ny) return;
+    const size_t co = (size_t)pair * ncx * ncy, fo = (size_t)pair * nx * ny;
+    m1c += co;
+    m2c += co;
+    phic += co;
     const int I = i >> 1, J = j >> 1;
     const int In = min(max((i & 1) ? I + 1 : I - 1, 0), ncx - 1);
     const int Jn = min(max((j & 1) ? J + 1 : J - 1, 0), ncy - 1);
@@ -215,31 +281,35 @@ __global__ void k_prolong(int ncx, int ncy, const float* __restrict__ m1c, const
         v2 = 0.5f * (below + m2c[(size_t)J * ncx + I]);
     }
     if (j == ny - 1) v2 = 0.f;
-    const size_t k = (size_t)j * nx + i;
+    const size_t k = fo + (size_t)j * nx + i;
     phif[k] = p;
     m1f[k] = v1;
     m2f[k] = v2;
 }
 
 cudaError_t launch_prolong(int ncx, int ncy, const float* m1c, const float* m2c, const float* phic, float* m1f,
-                           float* m2f, float* phif, cudaStream_t s)
+                           float* m2f, float* phif, int pairs, const Ctl* ctl, cudaStream_t s)
 {
-    dim3 b(32, 8), g((2 * ncx + 31) / 32, (2 * ncy + 7) / 8);
-    k_prolong<<<g, b, 0, s>>>(ncx, ncy, m1c, m2c, phic, m1f, m2f, phif);
+    dim3 b(32, 8), g((2 * ncx + 31) / 32, (2 * ncy + 7) / 8, pairs);
+    k_prolong<<<g, b, 0, s>>>(ncx, ncy, m1c, m2c, phic, m1f, m2f, phif, ctl);
     return cudaGetLastError();
 }
 
-__global__ void k_level_begin(Ctl* ctl, int level)
+__global__ void k_level_begin(Ctl* ctls, int level, int pairs)
 {
-    ctl->iters[level] = 0;
-    ctl->fpr[level] = 0.0;
-    ctl->conv[level] = 0;
-    ctl->t_start[level] = globaltimer();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= pairs) return;
+    Ctl* c = ctls + p;
+    c->iters[level] = 0;
+    c->fpr[level] = 0.0;
+    c->conv[level] = 0;
+    c->t_start[level] = globaltimer();
+    c->active = c->error ? 0 : 1;
 }
 
-cudaError_t launch_level_begin(Ctl* ctl, int level, cudaStream_t s)
+cudaError_t launch_level_begin(Ctl* ctl, int level, int pairs, cudaStream_t s)
 {
-    k_level_begin<<<1, 1, 0, s>>>(ctl, level);
+    k_level_begin<<<(pairs + 127) / 128, 128, 0, s>>>(ctl, level, pairs);
     return cudaGetLastError();
 }
 
@@ -249,9 +319,11 @@ cudaError_t launch_level_begin(Ctl* ctl, int level, cudaStream_t s)
 
 static constexpr int STEP_THREADS = 256;  // 8 warps stacked in y
 
-int stream_rows_auto(int nx, int ny)
+int stream_rows_auto(int nx, int ny, int)
 {
-    // enough blocks for ~4 waves of 152 SMs, marching at most 16 rows per thread
+    // enough blocks for ~4 waves of 152 SMs for one pair, marching at most 16
+    // rows per thread; independent of the batch size so that each pair's R^k is
+    // summed in the same order alone and inside a batch
     long long colblocks = (nx + 31) / 32;
     long long r = (long long)ny * colblocks / (8LL * 152 * 4);
     if (r < 2) r = 2;
@@ -259,45 +331,52 @@ int stream_rows_auto(int nx, int ny)
     return (int)r;
 }
 
-dim3 stream_grid(int nx, int ny, int rows)
+dim3 stream_grid(int nx, int ny, int rows, int pairs)
 {
-    return dim3((nx + 31) / 32, (ny + 8 * rows - 1) / (8 * rows), 1);
+    return dim3((nx + 31) / 32, (ny + 8 * rows - 1) / (8 * rows), pairs);
 }
 
-size_t step_part_doubles(int nx, int ny, int rows)
+size_t step_part_doubles(int nx, int ny, int rows, int pairs)
 {
-    dim3 g = stream_grid(nx, ny, rows);
-    return (size_t)g.x * g.y * 3;
+    dim3 g = stream_grid(nx, ny, rows, pairs);
+    return (size_t)g.x * g.y * g.z * 3;
 }
 
 template <int NORM, bool CHECK>
 __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
 {
     const IterArgs& P = a.it;
+    const int pair = blockIdx.z;
+    Ctl* pc = P.ctl ? P.ctl + pair : nullptr;
+    // a pair that was rejected, is an unused slot, or has converged does no work
+    if (pc && (pc->error || (a.use_cond && !pc->active))) return;  // uniform over the pair's blocks
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nx = P.nx, ny = P.ny;
     const int i = blockIdx.x * 32 + lane;
     const int j0 = (blockIdx.y * (STEP_THREADS / 32) + warp) * a.rows;
     const bool act = i < nx;
     const float mu = P.mu, tau = P.tau, ih = P.ih;
+    const size_t off = (size_t)pair * P.stride;
     double sa = 0.0, sb = 0.0, sc = 0.0;
-    const bool err = P.ctl != nullptr && P.ctl->error != 0;
-    if (!err && j0 < ny) {
+    if (j0 < ny) {
         const int j1 = min(j0 + a.rows, ny);
-        const float* __restrict__ phi = a.phi;
-        const float* __restrict__ m1 = a.m1;
-        const float* __restrict__ m2 = a.m2;
-        const float* __restrict__ rho = a.rho;
+        const float* __restrict__ phi = a.phi + off;
+        const float* __restrict__ m1 = a.m1 + off;
+        const float* __restrict__ m2 = a.m2 + off;
+        const float* __restrict__ rho = a.rho + off;
+        float* __restrict__ m1o = a.m1o + off;
+        float* __restrict__ m2o = a.m2o + off;
+        float* __restrict__ phio = a.phio + off;
         auto at = [nx](int j, int ii) { return (size_t)j * nx + ii; };
-        float pc = act ? __ldg(phi + at(j0, i)) : 0.f;
+        float pc_ = act ? __ldg(phi + at(j0, i)) : 0.f;
         // mbar2 and dm2 of the node below the strip (row j0 - 1)
         float b2b = 0.f;
         double d2b = 0.0;
         if (j0 > 0) {
             float pb = act ? __ldg(phi + at(j0 - 1, i)) : 0.f;
             float c2 = act ? __ldg(m2 + at(j0 - 1, i)) : 0.f;
-            float g2 = (pc - pb) * ih;
-            float o1, o2;
+            float g2 = (pc_ - pb) * ih;
+            float o1 = 0.f, o2;
             if (NORM == W1_NORM_L1) {
                 o2 = soft(c2 + mu * g2, mu);
             } else {
@@ -307,18 +386,27 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
                 float c1 = act ? __ldg(m1 + at(j0 - 1, i)) : 0.f;
                 prox<NORM>(c1 + mu * g1, c2 + mu * g2, mu, o1, o2);
             }
+            (void)o1;
             b2b = 2.f * o2 - c2;
             d2b = (double)o2 - (double)c2;
         }
+        // row j's values are loaded one row ahead (software pipelining)
+        float nu = (act && j0 + 1 < ny) ? __ldg(phi + at(j0 + 1, i)) : 0.f;
+        float na1 = act ? __ldg(m1 + at(j0, i)) : 0.f;
+        float na2 = act ? __ldg(m2 + at(j0, i)) : 0.f;
+        float nr = act ? __ldg(rho + at(j0, i)) : 0.f;
         for (int j = j0; j < j1; ++j) {
-            const float pu = (act && j + 1 < ny) ? __ldg(phi + at(j + 1, i)) : 0.f;
-            float pr = __shfl_down_sync(FULL, pc, 1);
+            const float pu = nu, a1 = na1, a2 = na2, r = nr;
+            if (j + 1 < j1) {
+                nu = (act && j + 2 < ny) ? __ldg(phi + at(j + 2, i)) : 0.f;
+                na1 = act ? __ldg(m1 + at(j + 1, i)) : 0.f;
+                na2 = act ? __ldg(m2 + at(j + 1, i)) : 0.f;
+                nr = act ? __ldg(rho + at(j + 1, i)) : 0.f;
+            }
+            float pr = __shfl_down_sync(FULL, pc_, 1);
             if (lane == 31 && i + 1 < nx) pr = __ldg(phi + at(j, i + 1));
-            const float a1 = act ? __ldg(m1 + at(j, i)) : 0.f;
-            const float a2 = act ? __ldg(m2 + at(j, i)) : 0.f;
-            const float r = act ? __ldg(rho + at(j, i)) : 0.f;
-            const float g1 = (i < nx - 1) ? (pr - pc) * ih : 0.f;
-            const float g2 = (j < ny - 1) ? (pu - pc) * ih : 0.f;
+            const float g1 = (i < nx - 1) ? (pr - pc_) * ih : 0.f;
+            const float g2 = (j < ny - 1) ? (pu - pc_) * ih : 0.f;
             float n1, n2;
             prox<NORM>(a1 + mu * g1, a2 + mu * g2, mu, n1, n2);
             if (i >= nx - 1) n1 = 0.f;
@@ -332,7 +420,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
                     // the left neighbour belongs to the previous warp: recompute its m1'
                     const float ql = __ldg(phi + at(j, i - 1));
                     const float c1 = __ldg(m1 + at(j, i - 1));
-                    const float gl1 = (pc - ql) * ih;
+                    const float gl1 = (pc_ - ql) * ih;
                     float o1, o2;
                     if (NORM == W1_NORM_L1) {
                         o1 = soft(c1 + mu * gl1, mu);
@@ -350,15 +438,15 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
                 }
             }
             const float dv = ((b1 - b1l) + (b2 - b2b)) * ih;
-            const float pn = pc + tau * (dv - r);
+            const float pn = pc_ + tau * (dv - r);
             if (act) {
-                a.m1o[at(j, i)] = n1;
-                a.m2o[at(j, i)] = n2;
-                a.phio[at(j, i)] = pn;
+                m1o[at(j, i)] = n1;
+                m2o[at(j, i)] = n2;
+                phio[at(j, i)] = pn;
             }
             if (CHECK && act) {
                 const double e1 = (double)n1 - (double)a1, e2 = (double)n2 - (double)a2;
-                const double ep = (double)pn - (double)pc;
+                const double ep = (double)pn - (double)pc_;
                 const double dd = ((e1 - d1l) + (e2 - d2b)) / P.h;
                 sa += e1 * e1 + e2 * e2;
                 sb += ep * ep;
@@ -366,7 +454,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
                 d2b = e2;
             }
             b2b = b2;
-            pc = pu;
+            pc_ = pu;
         }
     }
     if (!CHECK) return;
@@ -378,43 +466,42 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
     block_sum<3>(v, sh);
     const int nblk = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    double* pp = a.part + (size_t)pair * nblk * 3;
     if (threadIdx.x == 0) {
-        a.part[bid * 3 + 0] = v[0];
-        a.part[bid * 3 + 1] = v[1];
-        a.part[bid * 3 + 2] = v[2];
+        pp[bid * 3 + 0] = v[0];
+        pp[bid * 3 + 1] = v[1];
+        pp[bid * 3 + 2] = v[2];
         __threadfence();
-        last = (atomicAdd(&P.ctl->counter, 1u) == (unsigned)nblk - 1);
+        last = (atomicAdd(&pc->counter, 1u) == (unsigned)nblk - 1);
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
     double t[3] = {0.0, 0.0, 0.0};
     for (int b = threadIdx.x; b < nblk; b += blockDim.x)
-        for (int c = 0; c < 3; ++c) t[c] += ((volatile double*)a.part)[b * 3 + c];
+        for (int c = 0; c < 3; ++c) t[c] += ((volatile double*)pp)[b * 3 + c];
     block_sum<3>(t, sh);
     if (threadIdx.x == 0) {
-        Ctl* ctl = P.ctl;
         const double h2 = P.h * P.h;
         const double R = (t[0] / (double)P.mu + t[1] / (double)P.tau - 2.0 * t[2]) * h2;
-        ctl->counter = 0;
-        if (P.fpr_out) *P.fpr_out = R;
+        pc->counter = 0;
+        if (P.fpr_out) P.fpr_out[pair] = R;
         if (a.use_cond) {
-            const long long it = ctl->iters[P.level] + P.K;
-            ctl->iters[P.level] = it;
-            ctl->fpr[P.level] = R;
+            const long long it = pc->iters[P.level] + P.K;
+            pc->iters[P.level] = it;
+            pc->fpr[P.level] = R;
             const int conv = R < P.tol;
-            ctl->conv[P.level] = conv;
-            const bool late = (globaltimer() - ctl->t_start[P.level]) > P.budget_ns;
-            if (late && !conv) ctl->timeout = 1;
-            const bool go = !conv && it < P.cap && !late && ctl->error == 0;
-            cudaGraphSetConditional(a.cond, go ? 1u : 0u);
+            pc->conv[P.level] = conv;
+            const bool late = (globaltimer() - pc->t_start[P.level]) > P.budget_ns;
+            if (late && !conv) pc->timeout = 1;
+            if (conv || it >= P.cap || late) pc->active = 0;
         }
     }
 }
 
 cudaError_t launch_step(int norm, bool check, const StepArgs& a, cudaStream_t s)
 {
-    dim3 g = stream_grid(a.it.nx, a.it.ny, a.rows);
+    dim3 g = stream_grid(a.it.nx, a.it.ny, a.rows, a.pairs);
     if (norm == W1_NORM_L1) {
         if (check) k_step<W1_NORM_L1, true><<<g, STEP_THREADS, 0, s>>>(a);
         else k_step<W1_NORM_L1, false><<<g, STEP_THREADS, 0, s>>>(a);
@@ -425,24 +512,41 @@ cudaError_t launch_step(int norm, bool check, const StepArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+__global__ void k_decide(const Ctl* __restrict__ ctls, int pairs, cudaGraphConditionalHandle cond)
+{
+    int any = 0;
+    for (int p = threadIdx.x; p < pairs; p += blockDim.x) any |= ctls[p].active;
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
+}
+
+cudaError_t launch_decide(const Ctl* ctl, int pairs, cudaGraphConditionalHandle cond, cudaStream_t s)
+{
+    k_decide<<<1, 256, 0, s>>>(ctl, pairs, cond);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Resident level solver: Algorithm 1 to its stop test inside one launch
 // ---------------------------------------------------------------------------
 //
-// A cluster of C CTAs holds one level; CTA r owns rows [r*ny/C, (r+1)*ny/C).
-// The band lives in shared memory: rho, phi, m (m1, m2), D = div m^k and, on
-// test steps, dm = m' - m.  One step:
+// A cluster of C CTAs holds one pair's level; CTA r owns rows
+// [r*ny/C, (r+1)*ny/C).  Shared memory holds the band: phi and m (what
+// neighbours read), rho, D = div m^k and, on test steps, dm = m' - m.  A
+// single CTA also keeps its own nodes' m and phi (and, with at most two nodes
+// per thread, rho and D) in registers; in a cluster the addressing of the
+// remote rows leaves no room for that without spills.  One step:
 //   phase A: m' from m and phi (own, right, up; the row above the band is read
-//            from the next CTA's shared memory), m <- m' in place;  cluster barrier
+//            from the next CTA's shared memory), publish m'
 //   phase B: Dn = div m' (left, below; the row below the band from the previous
 //            CTA), div mbar = 2 Dn - D, phi' = phi + tau (div mbar - rho),
-//            D <- Dn, phi <- phi' in place;                       cluster barrier
-// Phase A only reads other nodes' phi and phase B only other nodes' m, so the
-// in-place updates are safe between the barriers.
+//            D <- Dn, publish phi'
+// With C > 1 the phases are separated by cluster barriers (release/acquire),
+// which also order the distributed-shared-memory reads of the halo rows.
 // Stop tests: each CTA's FP64 partials go to CTA 0, which decides; every CTA
 // reads the decision, so all leave the loop after the same step.
 
-static constexpr int RES_MAX_NODES = 4096;  // nodes per CTA
+static constexpr int RES_MAX_NODES = 4096;  // nodes per CTA (512 threads x 8)
 static constexpr int RES_THREADS = 1024;
 static constexpr int RES_RED_BYTES = 1024;  // 32 warps x 3 doubles
 static constexpr int RES_SLOT_BYTES = 512;  // 16 CTAs x 3 doubles + decision
@@ -466,12 +570,19 @@ static size_t resident_smem(int band)
     return RES_RED_BYTES + RES_SLOT_BYTES + (size_t)band * 7 * sizeof(float);
 }
 
-template <int NORM>
-__global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
+template <int NORM, int NPT, bool CL>
+__global__ void __launch_bounds__(NPT >= 8 ? RES_THREADS / 2 : RES_THREADS, 1) k_resident(ResArgs a)
 {
-    cg::cluster_group cl = cg::this_cluster();
     const IterArgs& P = a.it;
-    const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    int C = 1, rank = 0;
+    if (CL) {
+        cg::cluster_group cl = cg::this_cluster();
+        C = (int)cl.num_blocks();
+        rank = (int)cl.block_rank();
+    }
+    const int pair = blockIdx.x / C;
+    Ctl* pc = P.ctl ? P.ctl + pair : nullptr;
+    if (pc && pc->error) return;  // uniform over the cluster (one pair)
     const int nx = P.nx, ny = P.ny;
     const int rows = ny / C, jb = rank * rows, nb = rows * nx;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -484,32 +595,61 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
     float* e2s = e1s + nb;
     float* rs = e2s + nb;
     float* Ds = rs + nb;
-    if (P.ctl != nullptr && P.ctl->error != 0) return;  // uniform over the cluster
+    const size_t off = (size_t)pair * P.stride + (size_t)jb * nx;
+    constexpr bool SREG = !CL;                // m and phi of own nodes in registers (single CTA)
+    constexpr bool REG = SREG && NPT <= 2;    // rho and D in registers too
 
     const float mu = P.mu, tau = P.tau, ih = P.ih;
     const int T = blockDim.x;
-    for (int idx = threadIdx.x; idx < nb; idx += T) {
-        const size_t g = (size_t)jb * nx + idx;
-        s1[idx] = a.m1[g];
-        s2[idx] = a.m2[g];
-        ph[idx] = a.phi[g];
-        rs[idx] = a.rho[g];
+    float m1r[NPT], m2r[NPT], pr[NPT], rr[REG ? NPT : 1], Dr[REG ? NPT : 1];
+    int ij[NPT];  // i | (local row << 16), -1: no node
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = threadIdx.x + k * T;
+        ij[k] = -1;
+        m1r[k] = m2r[k] = pr[k] = 0.f;
+        if (REG) rr[REG ? k : 0] = Dr[REG ? k : 0] = 0.f;
+        if (idx < nb) {
+            const int jl = idx / nx, i = idx - jl * nx;
+            ij[k] = i | (jl << 16);
+            m1r[k] = a.m1[off + idx];
+            m2r[k] = a.m2[off + idx];
+            pr[k] = a.phi[off + idx];
+            if (REG) rr[REG ? k : 0] = a.rho[off + idx];
+            else rs[idx] = a.rho[off + idx];
+            ph[idx] = pr[k];
+            s1[idx] = m1r[k];
+            s2[idx] = m2r[k];
+        }
     }
-    cl.sync();
-    const float* ph_up = (rank + 1 < C) ? cl.map_shared_rank(ph, rank + 1) : nullptr;
-    const float* s2_dn = (rank > 0) ? cl.map_shared_rank(s2, rank - 1) : nullptr;
-    const float* e2_dn = (rank > 0) ? cl.map_shared_rank(e2s, rank - 1) : nullptr;
-    double* slots0 = cl.map_shared_rank(slots, 0);
+    if (CL) cg::this_cluster().sync();
+    else __syncthreads();
+    // remote rows: the first row of the next CTA's phi, the last row of the
+    // previous CTA's m2' (and dm2); CTA 0's decision slots
     const int last_row = (rows - 1) * nx;
+    uint32_t ph_up = 0, s2_dn = 0, e2_dn = 0, slots0 = smem_u32(slots);
+    if (CL) {
+        if (rank + 1 < C) ph_up = dsmem_map(smem_u32(ph), rank + 1);
+        if (rank > 0) {
+            s2_dn = dsmem_map(smem_u32(s2 + last_row), rank - 1);
+            e2_dn = dsmem_map(smem_u32(e2s + last_row), rank - 1);
+        }
+        slots0 = dsmem_map(smem_u32(slots), 0);
+    }
 
     // D^0 = div m^0
-    for (int idx = threadIdx.x; idx < nb; idx += T) {
-        const int jl = idx / nx, i = idx - jl * nx;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        if (ij[k] < 0) continue;
+        const int idx = threadIdx.x + k * T, i = ij[k] & 0xffff, jl = ij[k] >> 16;
         const float l1 = i > 0 ? s1[idx - 1] : 0.f;
-        const float d2 = jl > 0 ? s2[idx - nx] : (rank > 0 ? s2_dn[last_row + i] : 0.f);
-        Ds[idx] = ((s1[idx] - l1) + (s2[idx] - d2)) * ih;
+        const float d2 = jl > 0 ? s2[idx - nx] : ((CL && rank > 0) ? dsmem_ld(s2_dn + 4u * i) : 0.f);
+        const float D0 = ((s1[idx] - l1) + (s2[idx] - d2)) * ih;
+        if (REG) Dr[REG ? k : 0] = D0;
+        else Ds[idx] = D0;
     }
-    cl.sync();
+    if (CL) cg::this_cluster().sync();
+    else __syncthreads();
 
     unsigned long long t0 = 0;
     if (rank == 0 && threadIdx.x == 0) t0 = globaltimer();
@@ -520,14 +660,15 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
     while (it < cap) {
         const bool check = P.fixed ? (it + 1 == cap) : ((it + 1) % P.K == 0);
         double sa = 0.0, sb = 0.0, sc = 0.0;
-        // phase A: m' = prox(m + mu grad phi)
-        for (int idx = threadIdx.x; idx < nb; idx += T) {
-            const int jl = idx / nx, i = idx - jl * nx, j = jb + jl;
-            const float pc = ph[idx];
+        // ---- phase A: m' = prox(m + mu grad phi)
+        auto phaseA = [&](int k) {
+            const int idx = threadIdx.x + k * T, i = ij[k] & 0xffff, jl = ij[k] >> 16, j = jb + jl;
+            const float pc_ = SREG ? pr[k] : ph[idx];
+            const float a1 = SREG ? m1r[k] : s1[idx];
+            const float a2 = SREG ? m2r[k] : s2[idx];
             float g1 = 0.f, g2 = 0.f;
-            if (i < nx - 1) g1 = (ph[idx + 1] - pc) * ih;
-            if (j < ny - 1) g2 = ((jl < rows - 1 ? ph[idx + nx] : ph_up[i]) - pc) * ih;
-            const float a1 = s1[idx], a2 = s2[idx];
+            if (i < nx - 1) g1 = (ph[idx + 1] - pc_) * ih;
+            if (j < ny - 1) g2 = ((jl < rows - 1 ? ph[idx + nx] : dsmem_ld(ph_up + 4u * i)) - pc_) * ih;
             float n1, n2;
             prox<NORM>(a1 + mu * g1, a2 + mu * g2, mu, n1, n2);
             if (i == nx - 1) n1 = 0.f;
@@ -538,40 +679,68 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
                 e2s[idx] = d2;
                 sa += (double)d1 * d1 + (double)d2 * d2;
             }
+            if (SREG) {
+                m1r[k] = n1;
+                m2r[k] = n2;
+            }
             s1[idx] = n1;
             s2[idx] = n2;
-        }
-        cl.sync();
-        // phase B: phi' = phi + tau (div(2m' - m) - rho)
-        for (int idx = threadIdx.x; idx < nb; idx += T) {
-            const int jl = idx / nx, i = idx - jl * nx;
+        };
+        // ---- phase B: phi' = phi + tau (div(2m' - m) - rho)
+        auto phaseB = [&](int k) {
+            const int idx = threadIdx.x + k * T, i = ij[k] & 0xffff, jl = ij[k] >> 16;
             const float l1 = i > 0 ? s1[idx - 1] : 0.f;
-            const float d2 = jl > 0 ? s2[idx - nx] : (rank > 0 ? s2_dn[last_row + i] : 0.f);
-            const float Dn = ((s1[idx] - l1) + (s2[idx] - d2)) * ih;
-            const float pc = ph[idx];
-            const float pn = pc + tau * ((2.f * Dn - Ds[idx]) - rs[idx]);
+            const float d2 = jl > 0 ? s2[idx - nx] : ((CL && rank > 0) ? dsmem_ld(s2_dn + 4u * i) : 0.f);
+            const float o1 = SREG ? m1r[k] : s1[idx];
+            const float o2 = SREG ? m2r[k] : s2[idx];
+            const float pc_ = SREG ? pr[k] : ph[idx];
+            const float Dn = ((o1 - l1) + (o2 - d2)) * ih;
+            const float Dk = REG ? Dr[REG ? k : 0] : Ds[idx];
+            const float rk = REG ? rr[REG ? k : 0] : rs[idx];
+            const float pn = pc_ + tau * ((2.f * Dn - Dk) - rk);
             if (check) {
                 const double el = i > 0 ? (double)e1s[idx - 1] : 0.0;
-                const double eb = jl > 0 ? (double)e2s[idx - nx] : (rank > 0 ? (double)e2_dn[last_row + i] : 0.0);
+                const double eb = jl > 0 ? (double)e2s[idx - nx]
+                                         : ((CL && rank > 0) ? (double)dsmem_ld(e2_dn + 4u * i) : 0.0);
                 const double dd = (((double)e1s[idx] - el) + ((double)e2s[idx] - eb)) / P.h;
-                const double ep = (double)pn - (double)pc;
+                const double ep = (double)pn - (double)pc_;
                 sb += ep * ep;
                 sc += ep * dd;
             }
-            Ds[idx] = Dn;
+            if (REG) Dr[REG ? k : 0] = Dn;
+            else Ds[idx] = Dn;
+            if (SREG) pr[k] = pn;
             ph[idx] = pn;
+        };
+#pragma unroll
+        for (int k = 0; k < NPT; ++k)
+            if (ij[k] >= 0) phaseA(k);
+        if (CL) {
+            cluster_arrive();
+            cluster_wait();
+        } else {
+            __syncthreads();
         }
-        cl.sync();
+#pragma unroll
+        for (int k = 0; k < NPT; ++k)
+            if (ij[k] >= 0) phaseB(k);
+        if (CL) {
+            cluster_arrive();
+            cluster_wait();
+        } else {
+            __syncthreads();
+        }
         ++it;
         if (check) {
             double v[3] = {sa, sb, sc};
             block_sum<3>(v, red);
             if (threadIdx.x == 0) {
-                slots0[rank * 3 + 0] = v[0];
-                slots0[rank * 3 + 1] = v[1];
-                slots0[rank * 3 + 2] = v[2];
+                dsmem_st_f64(slots0 + 8u * (rank * 3 + 0), v[0]);
+                dsmem_st_f64(slots0 + 8u * (rank * 3 + 1), v[1]);
+                dsmem_st_f64(slots0 + 8u * (rank * 3 + 2), v[2]);
             }
-            cl.sync();
+            if (CL) cg::this_cluster().sync();
+            else __syncthreads();
             if (rank == 0 && threadIdx.x == 0) {
                 double t[3] = {0.0, 0.0, 0.0};
                 for (int r = 0; r < C; ++r)
@@ -583,75 +752,124 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
                 slots[48] = Rk;
                 slots[49] = (double)(cv | (lt << 1) | (stop << 2));
             }
-            cl.sync();
-            R = slots0[48];
-            const int d = (int)slots0[49];
+            if (CL) cg::this_cluster().sync();
+            else __syncthreads();
+            R = dsmem_ld_f64(slots0 + 8u * 48);
+            const int d = (int)dsmem_ld_f64(slots0 + 8u * 49);
             conv = d & 1;
             late = (d >> 1) & 1;
             if (d & 4) break;
         }
     }
     // write the level state back
-    for (int idx = threadIdx.x; idx < nb; idx += T) {
-        const size_t g = (size_t)jb * nx + idx;
-        a.m1[g] = s1[idx];
-        a.m2[g] = s2[idx];
-        a.phi[g] = ph[idx];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        if (ij[k] < 0) continue;
+        const int idx = threadIdx.x + k * T;
+        a.m1[off + idx] = SREG ? m1r[k] : s1[idx];
+        a.m2[off + idx] = SREG ? m2r[k] : s2[idx];
+        a.phi[off + idx] = SREG ? pr[k] : ph[idx];
     }
     if (rank == 0 && threadIdx.x == 0) {
-        if (P.ctl) {
-            P.ctl->iters[P.level] = it;
-            P.ctl->fpr[P.level] = R;
-            P.ctl->conv[P.level] = conv;
-            if (late && !conv) P.ctl->timeout = 1;
+        if (pc) {
+            pc->iters[P.level] = it;
+            pc->fpr[P.level] = R;
+            pc->conv[P.level] = conv;
+            if (late && !conv) pc->timeout = 1;
         }
-        if (P.fpr_out) *P.fpr_out = R;
-        if (P.iters_out) *P.iters_out = it;
+        if (P.fpr_out) P.fpr_out[pair] = R;
+        if (P.iters_out) P.iters_out[pair] = it;
     }
     // keep every CTA's shared memory alive until the remote reads are done
-    cl.sync();
+    if (CL) cg::this_cluster().sync();
+}
+
+template <int NORM, int NPT, bool CL>
+static cudaError_t res_attr()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_resident<NORM, NPT, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)resident_smem(RES_MAX_NODES));
+    if (e != cudaSuccess) return e;
+    if (CL) return cudaFuncSetAttribute(k_resident<NORM, NPT, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return cudaSuccess;
 }
 
 template <int NORM>
-static cudaError_t res_attr()
+static cudaError_t res_attr_norm()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_resident<NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)resident_smem(RES_MAX_NODES));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_resident<NORM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e;
+    if ((e = res_attr<NORM, 1, false>()) != cudaSuccess) return e;
+    if ((e = res_attr<NORM, 2, false>()) != cudaSuccess) return e;
+    if ((e = res_attr<NORM, 8, false>()) != cudaSuccess) return e;
+    if ((e = res_attr<NORM, 1, true>()) != cudaSuccess) return e;
+    if ((e = res_attr<NORM, 2, true>()) != cudaSuccess) return e;
+    return res_attr<NORM, 4, true>();
 }
 
 cudaError_t resident_prepare(int)
 {
-    cudaError_t e;
-    if ((e = res_attr<W1_NORM_L1>()) != cudaSuccess) return e;
-    return res_attr<W1_NORM_L2>();
+    cudaError_t e = res_attr_norm<W1_NORM_L1>();
+    if (e != cudaSuccess) return e;
+    return res_attr_norm<W1_NORM_L2>();
 }
 
-static void resident_config(int norm, int cluster, int nx, int ny, cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr,
-                            const void** fn)
+template <int NORM>
+static const void* res_fn(int npt, bool cl)
+{
+    if (cl) {
+        if (npt <= 1) return (const void*)k_resident<NORM, 1, true>;
+        if (npt <= 2) return (const void*)k_resident<NORM, 2, true>;
+        return (const void*)k_resident<NORM, 4, true>;
+    }
+    if (npt <= 1) return (const void*)k_resident<NORM, 1, false>;
+    if (npt <= 2) return (const void*)k_resident<NORM, 2, false>;
+    return (const void*)k_resident<NORM, 8, false>;
+}
+
+static void resident_config(int norm, int cluster, int nx, int ny, int pairs, cudaLaunchConfig_t& cfg,
+                            cudaLaunchAttribute* attr, const void** fn)
 {
     const int band = (ny / cluster) * nx;
-    const int threads = band < RES_THREADS ? ((band + 31) / 32) * 32 : RES_THREADS;
+    // up to 1024 nodes: one per thread; up to 2048: two per thread; beyond:
+    // 512 threads x 8 for a single CTA, 1024 x 4 in a cluster (fewer registers
+    // next to the distributed-shared-memory addressing)
+    int threads, npt;
+    if (band <= RES_THREADS) {
+        threads = ((band + 31) / 32) * 32;
+        npt = 1;
+    } else if (band <= 2 * RES_THREADS) {
+        threads = RES_THREADS;
+        npt = 2;
+    } else if (cluster > 1) {
+        threads = RES_THREADS;
+        npt = 4;
+    } else {
+        threads = RES_THREADS / 2;
+        npt = 8;
+    }
     cfg = cudaLaunchConfig_t{};
-    cfg.gridDim = dim3(cluster, 1, 1);
+    cfg.gridDim = dim3(cluster * pairs, 1, 1);
     cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = resident_smem(band);
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    *fn = norm == W1_NORM_L1 ? (const void*)k_resident<W1_NORM_L1> : (const void*)k_resident<W1_NORM_L2>;
+    cfg.numAttrs = 0;
+    if (cluster > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    *fn = norm == W1_NORM_L1 ? res_fn<W1_NORM_L1>(npt, cluster > 1) : res_fn<W1_NORM_L2>(npt, cluster > 1);
 }
 
 int resident_cluster_ok(int norm, int cluster, int nx, int ny)
 {
+    if (cluster == 1) return 1;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
     const void* fn = nullptr;
-    resident_config(norm, cluster, nx, ny, cfg, attr, &fn);
+    resident_config(norm, cluster, nx, ny, 1, cfg, attr, &fn);
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
         cudaGetLastError();
@@ -665,7 +883,7 @@ cudaError_t launch_resident(int norm, int cluster, const ResArgs& a, cudaStream_
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
     const void* fn = nullptr;
-    resident_config(norm, cluster, a.it.nx, a.it.ny, cfg, attr, &fn);
+    resident_config(norm, cluster, a.it.nx, a.it.ny, a.pairs, cfg, attr, &fn);
     cfg.stream = s;
     void* args[1] = {(void*)&a};
     return cudaLaunchKernelExC(&cfg, fn, args);
@@ -675,20 +893,32 @@ cudaError_t launch_resident(int norm, int cluster, const ResArgs& a, cudaStream_
 // Final statistics: W1 = f(m), dual bound, residual, certified bracket
 // ---------------------------------------------------------------------------
 
-static constexpr int FIN_BLOCKS = 304, FIN_THREADS = 256;
+static constexpr int FIN_THREADS = 256;
 
-size_t final_part_doubles() { return (size_t)FIN_BLOCKS * 5; }
+// Fixed per pair for the same reason as the prep blocks.
+static constexpr int FIN_BLOCKS_PER_PAIR = 64;
+static int final_blocks_per_pair(int) { return FIN_BLOCKS_PER_PAIR; }
+
+size_t final_part_doubles(int pairs) { return (size_t)final_blocks_per_pair(pairs) * pairs * 5; }
 
 template <int NORM>
 __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict__ m1, const float* __restrict__ m2,
                                                          const float* __restrict__ phi, const float* __restrict__ rho,
                                                          int nx, int ny, double h, double* __restrict__ q,
-                                                         double* part)
+                                                         double* part, const Ctl* ctls)
 {
     __shared__ double sh[32 * 4];
+    const int pair = blockIdx.y;
+    if (ctls && ctls[pair].error == 2) return;
+    const long long n = (long long)nx * ny;
+    const size_t off = (size_t)pair * n;
+    m1 += off;
+    m2 += off;
+    phi += off;
+    rho += off;
+    q += 2 * off;
     double v[4] = {0.0, 0.0, 0.0, 0.0};  // f, dual, res_l1, rho_l1
     double gm = 0.0;
-    const long long n = (long long)nx * ny;
     const double h2 = h * h;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(k / nx), i = (int)(k - (long long)j * nx);
@@ -710,26 +940,33 @@ __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict
         gm = fmax(gm, gq);
     }
     block_sum<4>(v, sh);
-    // max over the block
     gm = warp_max(gm);
     __shared__ double shm[32];
     if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = gm;
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) gm = fmax(gm, shm[w]);
-        for (int c = 0; c < 4; ++c) part[blockIdx.x * 5 + c] = v[c];
-        part[blockIdx.x * 5 + 4] = gm;
+        double* pp = part + ((size_t)pair * gridDim.x + blockIdx.x) * 5;
+        for (int c = 0; c < 4; ++c) pp[c] = v[c];
+        pp[4] = gm;
     }
 }
 
-// One block: sums the partials, then routes the residual masses q along the
-// dyadic tree (each 2x2 block sends its masses to its first node; offsets
-// (1,0), (0,1) cost one edge of the current spacing, (1,1) two), finishing
-// with a diameter bound on the last grid.  This is an explicit flux carrying
-// rho - div m, hence f + route >= W1 of the discrete problem.
-__global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, double* q, double* q2,
-                                                  const double* part, int nparts, Ctl* ctl)
+// One block per pair: sums the partials, then routes the residual masses q
+// along the dyadic tree (each 2x2 block sends its masses to its first node;
+// offsets (1,0), (0,1) cost one edge of the current spacing, (1,1) two),
+// finishing with a diameter bound on the last grid.  This is an explicit flux
+// carrying rho - div m, hence f + route >= W1 of the discrete problem.
+__global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, double* q, const double* part,
+                                                  int nparts, Ctl* ctls)
 {
+    const int pair = blockIdx.x;
+    Ctl* ctl = ctls + pair;
+    if (ctl->error == 2) return;
+    const size_t n = (size_t)nx * ny;
+    double* src = q + 2 * n * pair;
+    double* dst = src + n;
+    part += (size_t)pair * nparts * 5;
     __shared__ double sh[32 * 4];
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     double gm = 0.0;
@@ -750,8 +987,6 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
 
     int cx = nx, cy = ny;
     double hx = h, hy = h, cost = 0.0;
-    double* src = q;
-    double* dst = q2;
     for (;;) {
         const int px = (cx > 1 && (cx & 1) == 0), py = (cy > 1 && (cy & 1) == 0);
         const int stopx = (cx > 1 && (cx & 1)), stopy = (cy > 1 && (cy & 1));
@@ -802,14 +1037,15 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
 }
 
 cudaError_t launch_final(int norm, const float* m1, const float* m2, const float* phi, const float* rho, int nx,
-                         int ny, double h, double* q, double* part, Ctl* ctl, cudaStream_t s)
+                         int ny, double h, double* q, double* part, Ctl* ctl, int pairs, cudaStream_t s)
 {
-    double* q2 = q + (size_t)nx * ny;
+    const int bpp = final_blocks_per_pair(pairs);
+    dim3 g(bpp, pairs);
     if (norm == W1_NORM_L1)
-        k_final_a<W1_NORM_L1><<<FIN_BLOCKS, FIN_THREADS, 0, s>>>(m1, m2, phi, rho, nx, ny, h, q, part);
+        k_final_a<W1_NORM_L1><<<g, FIN_THREADS, 0, s>>>(m1, m2, phi, rho, nx, ny, h, q, part, ctl);
     else
-        k_final_a<W1_NORM_L2><<<FIN_BLOCKS, FIN_THREADS, 0, s>>>(m1, m2, phi, rho, nx, ny, h, q, part);
-    k_final_b<<<1, 1024, 0, s>>>(nx, ny, h, q, q2, part, FIN_BLOCKS, ctl);
+        k_final_a<W1_NORM_L2><<<g, FIN_THREADS, 0, s>>>(m1, m2, phi, rho, nx, ny, h, q, part, ctl);
+    k_final_b<<<pairs, 1024, 0, s>>>(nx, ny, h, q, part, bpp, ctl);
     return cudaGetLastError();
 }
 

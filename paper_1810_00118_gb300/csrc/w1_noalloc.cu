@@ -26,7 +26,7 @@ constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign;
 
 // Layout of the static scratch: control block | partial sums | 2 * n FP64 masses.
 constexpr size_t kCtlBytes = align_up(sizeof(Ctl));
-constexpr size_t kPartBytes = align_up(304 * 5 * sizeof(double));
+constexpr size_t kPartBytes = align_up(304 * 5 * sizeof(double));  // >= final_part_doubles(1)
 constexpr size_t kQBytes = 2 * (size_t)W1_NOALLOC_MAX_NODES * sizeof(double);
 constexpr size_t kScratchBytes = kCtlBytes + kPartBytes + kQBytes;
 
@@ -87,7 +87,7 @@ extern "C" w1_status w1_state_stats_noalloc(int nx, int ny, double h, int norm, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // The array keeps the previous call's contents: the control block must start at zero.
     e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
-    if (e == cudaSuccess) e = launch_final(norm, m1, m2, phi, rho, nx, ny, h, q, part, ctl, s);
+    if (e == cudaSuccess) e = launch_final(norm, m1, m2, phi, rho, nx, ny, h, q, part, ctl, 1, s);
     Ctl c;
     std::memset(&c, 0, sizeof(c));
     if (e == cudaSuccess) e = cudaMemcpyAsync(&c, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);

@@ -1,23 +1,28 @@
 // w1_plan.cu -- host driver and C ABI of the GB300 multilevel W1 solver.
 //
 // A plan fixes the grid, the level hierarchy of Algorithm 3 (h_l = 2^{L-l} h,
-// Sec. 3.2), the norm and the tolerances, and owns one device arena:
-//   control block | partial sums | FP64 scratch for the final certificate |
-//   per level: rho_l, state A (m1, m2, phi), state B (streaming levels only).
-// The level sequence (restriction, level starts, level solves) is captured once
-// into a CUDA graph.  Resident levels are single cluster launches that run to
-// their stop test on the device; streaming levels are conditional WHILE nodes
-// whose body is K steps, the last of which forms R^k and sets the condition.
-// A solve is: prep (rho = rho0 - rho1, mass check) -> graph -> final
-// statistics -> one device-to-host copy of the control block.  No host
-// synchronisation happens between the first and the last of these.
+// Sec. 3.2), the norm, the tolerances and the batch size B, and owns one device
+// arena:
+//   per-pair control blocks | partial sums | FP64 scratch for the certificate |
+//   per level: rho_l, state A (m1, m2, phi), state B (streaming levels only),
+// each plane holding B pairs back to back.  The level sequence (restriction,
+// level starts, level solves) is captured once into a CUDA graph.  Resident
+// levels are single launches (one CTA or cluster per pair) that run every pair
+// to its stop test on the device; streaming levels are conditional WHILE nodes
+// whose body is K batched steps, the last of which forms each pair's R^k,
+// retires converged pairs, and lets a one-block kernel set the condition while
+// any pair is still active.  A solve is: prep (rho = rho0 - rho1, mass check)
+// -> graph -> final statistics -> one device-to-host copy of the control
+// blocks.  No host synchronisation happens between the first and the last.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <string>
+#include <vector>
 
 #include "w1_internal.h"
 
@@ -75,7 +80,7 @@ struct LevelPlan {
 
 struct w1_plan {
     int device;
-    int nx, ny, L, norm;
+    int nx, ny, L, norm, batch;
     double h, tol;
     w1_options opt;
     LevelPlan lv[W1_MAX_LEVELS];
@@ -95,6 +100,7 @@ struct w1_plan {
     float* in0;
     float* in1;
     float* flux_d;
+    int last_batch;
 };
 
 extern "C" void w1_default_options(w1_options* o)
@@ -129,7 +135,7 @@ extern "C" const char* w1_status_string(w1_status s)
     return "unknown status";
 }
 
-// Carves the arena: control block, partials, FP64 certificate scratch, levels.
+// Carves the arena: control blocks, partials, FP64 certificate scratch, levels.
 static size_t layout(w1_plan* p, char* base)
 {
     size_t off = 0;
@@ -139,21 +145,22 @@ static size_t layout(w1_plan* p, char* base)
         off += bytes;
         return r;
     };
-    p->ctl = reinterpret_cast<Ctl*>(take(sizeof(Ctl)));
-    size_t pd = final_part_doubles();
-    if (pd < 304 * 4) pd = 304 * 4;
+    const int B = p->batch;
+    p->ctl = reinterpret_cast<Ctl*>(take(sizeof(Ctl) * B));
+    size_t pd = final_part_doubles(B);
+    if (prep_part_doubles(B) > pd) pd = prep_part_doubles(B);
     for (int l = 0; l < p->L; ++l)
         if (p->lv[l].path == 2) {
-            size_t s = step_part_doubles(p->lv[l].nx, p->lv[l].ny, p->lv[l].rows);
+            size_t s = step_part_doubles(p->lv[l].nx, p->lv[l].ny, p->lv[l].rows, B);
             if (s > pd) pd = s;
         }
     p->part_doubles = pd;
     p->part = reinterpret_cast<double*>(take(pd * sizeof(double)));
     const size_t n = (size_t)p->nx * p->ny;
-    p->q = reinterpret_cast<double*>(take(2 * n * sizeof(double)));
+    p->q = reinterpret_cast<double*>(take(2 * n * B * sizeof(double)));
     for (int l = 0; l < p->L; ++l) {
         LevelPlan& v = p->lv[l];
-        const size_t b = (size_t)v.nx * v.ny * sizeof(float);
+        const size_t b = (size_t)v.nx * v.ny * sizeof(float) * B;
         v.rho = reinterpret_cast<float*>(take(b));
         const int nb = v.path == 2 ? 2 : 1;
         for (int s = 0; s < 2; ++s) {
@@ -171,16 +178,17 @@ static w1_status bind_arena(w1_plan* p, char* base, size_t bytes)
     if (reinterpret_cast<uintptr_t>(base) % 256 != 0) return fail(W1_ERR_INVALID_ARG, "workspace not 256-byte aligned");
     layout(p, base);
     p->ws = base;
-    W1_CK(cudaMemset(p->ctl, 0, sizeof(Ctl)));
+    W1_CK(cudaMemset(p->ctl, 0, sizeof(Ctl) * p->batch));
     return W1_OK;
 }
 
-extern "C" w1_status w1_plan_create_ex(int nx, int ny, double h, int levels, int norm, double tol,
-                                       const w1_options* opt, w1_plan** out)
+// Fills every field of p that does not need device memory (levels, paths,
+// tolerances, arena size).  Shared by plan creation and w1_plan_bytes.
+static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int norm, double tol, int max_batch,
+                           const w1_options* opt)
 {
-    if (!out) return fail(W1_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
     if (nx < 1 || ny < 1) return fail(W1_ERR_INVALID_ARG, "nx and ny must be >= 1");
+    if (max_batch < 1 || max_batch > 65535) return fail(W1_ERR_INVALID_ARG, "max_batch must lie in [1, 65535]");
     if (norm != W1_NORM_L1 && norm != W1_NORM_L2) return fail(W1_ERR_INVALID_ARG, "norm must be 1 or 2");
     w1_options o;
     w1_default_options(&o);
@@ -189,6 +197,8 @@ extern "C" w1_status w1_plan_create_ex(int nx, int ny, double h, int levels, int
     if (!(o.theta > 0.0) || o.theta > 1.0) return fail(W1_ERR_INVALID_ARG, "theta must lie in (0, 1]");
     if (o.max_iters < 1) return fail(W1_ERR_INVALID_ARG, "max_iters must be >= 1");
     if (o.path < 0 || o.path > 2) return fail(W1_ERR_INVALID_ARG, "path must be 0, 1 or 2");
+    // stop tests happen every K steps, so the cap is a multiple of K
+    o.max_iters = (o.max_iters + o.check_every - 1) / o.check_every * o.check_every;
     if (!(h > 0.0)) h = 1.0 / (double)(nx > ny ? nx : ny);
     if (levels <= 0) {
         // the paper's L = log2(1/h) - 3 (Sec. 5.3), kept divisible
@@ -203,19 +213,16 @@ extern "C" w1_status w1_plan_create_ex(int nx, int ny, double h, int levels, int
     const int div = 1 << (levels - 1);
     if (nx % div || ny % div) return fail(W1_ERR_SHAPE, "nx and ny must be divisible by 2^(levels-1)");
     if (!(tol > 0.0)) tol = 1e-6 / 128.0 * (512.0 * h) * (512.0 * h);  // eq. stop_tol, Alg. 3
-
     int dev = 0;
     W1_CK(cudaGetDevice(&dev));
     w1_status st = prepare_device(dev);
     if (st != W1_OK) return st;
-
-    w1_plan* p = new (std::nothrow) w1_plan();
-    if (!p) return fail(W1_ERR_NOMEM, "host allocation failed");
     p->device = dev;
     p->nx = nx;
     p->ny = ny;
     p->L = levels;
     p->norm = norm;
+    p->batch = max_batch;
     p->h = h;
     p->tol = tol;
     p->opt = o;
@@ -231,17 +238,35 @@ extern "C" w1_status w1_plan_create_ex(int nx, int ny, double h, int levels, int
         v.tol = tol * std::pow(v.h / h, o.alpha);  // eq. tol_formula_propose
         int c = resident_cluster_for(v.nx, v.ny);
         if (c > 0 && resident_cluster_ok(norm, c, v.nx, v.ny) <= 0) c = 0;
-        if (o.path == 1 && c == 0) {
-            delete p;
-            return fail(W1_ERR_UNSUPPORTED, "level too large for the resident path");
-        }
+        if (o.path == 1 && c == 0) return fail(W1_ERR_UNSUPPORTED, "level too large for the resident path");
         v.path = (o.path == 2 || c == 0) ? 2 : 1;
         v.cluster = v.path == 1 ? c : 0;
-        v.rows = o.rows_per_thread > 0 ? o.rows_per_thread : stream_rows_auto(v.nx, v.ny);
+        v.rows = o.rows_per_thread > 0 ? o.rows_per_thread : stream_rows_auto(v.nx, v.ny, max_batch);
     }
     p->ws_bytes = layout(p, nullptr);
-    p->own_ws = false;
-    p->ws = nullptr;
+    return W1_OK;
+}
+
+extern "C" size_t w1_plan_bytes(int nx, int ny, double h, int levels, int norm, double tol, int max_batch,
+                                const w1_options* opt)
+{
+    w1_plan tmp{};
+    if (configure(&tmp, nx, ny, h, levels, norm, tol, max_batch, opt) != W1_OK) return 0;
+    return tmp.ws_bytes;
+}
+
+extern "C" w1_status w1_plan_create_batch(int nx, int ny, double h, int levels, int norm, double tol, int max_batch,
+                                          const w1_options* opt, w1_plan** out)
+{
+    if (!out) return fail(W1_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    w1_plan* p = new (std::nothrow) w1_plan();
+    if (!p) return fail(W1_ERR_NOMEM, "host allocation failed");
+    w1_status st = configure(p, nx, ny, h, levels, norm, tol, max_batch, opt);
+    if (st != W1_OK) {
+        delete p;
+        return st;
+    }
     char* base = nullptr;
     cudaError_t e = cudaMalloc(&base, p->ws_bytes);
     if (e != cudaSuccess) {
@@ -256,7 +281,7 @@ extern "C" w1_status w1_plan_create_ex(int nx, int ny, double h, int levels, int
         return st;
     }
     p->own_ws = true;
-    e = cudaMallocHost(&p->host_ctl, sizeof(Ctl));
+    e = cudaMallocHost(&p->host_ctl, sizeof(Ctl) * max_batch);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->body_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -268,9 +293,15 @@ extern "C" w1_status w1_plan_create_ex(int nx, int ny, double h, int levels, int
     return W1_OK;
 }
 
+extern "C" w1_status w1_plan_create_ex(int nx, int ny, double h, int levels, int norm, double tol,
+                                       const w1_options* opt, w1_plan** out)
+{
+    return w1_plan_create_batch(nx, ny, h, levels, norm, tol, 1, opt, out);
+}
+
 extern "C" w1_status w1_plan_create(int nx, int ny, double h, int levels, int norm, double tol, w1_plan** out)
 {
-    return w1_plan_create_ex(nx, ny, h, levels, norm, tol, nullptr, out);
+    return w1_plan_create_batch(nx, ny, h, levels, norm, tol, 1, nullptr, out);
 }
 
 extern "C" w1_status w1_plan_destroy(w1_plan* p)
@@ -295,6 +326,8 @@ extern "C" w1_status w1_plan_destroy(w1_plan* p)
 }
 
 extern "C" size_t w1_plan_workspace_bytes(const w1_plan* p) { return p ? p->ws_bytes : 0; }
+
+extern "C" int w1_plan_max_batch(const w1_plan* p) { return p ? p->batch : 0; }
 
 extern "C" w1_status w1_plan_set_workspace(w1_plan* p, void* dev, size_t bytes)
 {
@@ -334,6 +367,7 @@ static IterArgs iter_args(const w1_plan* p, int l)
     it.fixed = 0;
     it.level = l;
     it.budget_ns = (unsigned long long)(p->opt.time_budget_s * 1e9);
+    it.stride = (long long)v.nx * v.ny;
     it.ctl = p->ctl;
     it.fpr_out = nullptr;
     it.iters_out = nullptr;
@@ -344,6 +378,7 @@ static IterArgs iter_args(const w1_plan* p, int l)
 static w1_status build_graph(w1_plan* p)
 {
     cudaStream_t s = p->cap_stream;
+    const int B = p->batch;
     W1_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
     auto abort_capture = [&](w1_status st) {
         cudaGraph_t g = nullptr;
@@ -358,18 +393,19 @@ static w1_status build_graph(w1_plan* p)
         if (e_ != cudaSuccess)                                                                     \
             return abort_capture(fail(W1_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
     } while (0)
-    for (int l = p->L - 1; l > 0; --l) CAP_CK(launch_restrict(p->lv[l].rho, p->lv[l].nx, p->lv[l].ny, p->lv[l - 1].rho, s));
+    for (int l = p->L - 1; l > 0; --l)
+        CAP_CK(launch_restrict(p->lv[l].rho, p->lv[l].nx, p->lv[l].ny, p->lv[l - 1].rho, B, p->ctl, s));
     for (int l = 0; l < p->L; ++l) {
         LevelPlan& v = p->lv[l];
-        const size_t b = (size_t)v.nx * v.ny * sizeof(float);
-        CAP_CK(launch_level_begin(p->ctl, l, s));
+        const size_t b = (size_t)v.nx * v.ny * sizeof(float) * B;
+        CAP_CK(launch_level_begin(p->ctl, l, B, s));
         if (l == 0) {
             CAP_CK(cudaMemsetAsync(v.m1[0], 0, b, s));
             CAP_CK(cudaMemsetAsync(v.m2[0], 0, b, s));
             CAP_CK(cudaMemsetAsync(v.phi[0], 0, b, s));
         } else {
             const LevelPlan& c = p->lv[l - 1];
-            CAP_CK(launch_prolong(c.nx, c.ny, c.m1[0], c.m2[0], c.phi[0], v.m1[0], v.m2[0], v.phi[0], s));
+            CAP_CK(launch_prolong(c.nx, c.ny, c.m1[0], c.m2[0], c.phi[0], v.m1[0], v.m2[0], v.phi[0], B, p->ctl, s));
         }
         if (v.path == 1) {
             ResArgs a{};
@@ -377,6 +413,7 @@ static w1_status build_graph(w1_plan* p)
             a.m2 = v.m2[0];
             a.phi = v.phi[0];
             a.rho = v.rho;
+            a.pairs = B;
             a.it = iter_args(p, l);
             CAP_CK(launch_resident(p->norm, v.cluster, a, s));
         } else {
@@ -400,7 +437,8 @@ static w1_status build_graph(w1_plan* p)
             CAP_CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
             CAP_CK(cudaStreamBeginCaptureToGraph(p->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
             const int K = p->opt.check_every;
-            for (int k = 0; k < K; ++k) {
+            cudaError_t e = cudaSuccess;
+            for (int k = 0; k < K && e == cudaSuccess; ++k) {
                 StepArgs a{};
                 const int src = k & 1, dst = src ^ 1;
                 a.m1 = v.m1[src];
@@ -411,16 +449,17 @@ static w1_status build_graph(w1_plan* p)
                 a.m2o = v.m2[dst];
                 a.phio = v.phi[dst];
                 a.rows = v.rows;
+                a.pairs = B;
                 a.it = iter_args(p, l);
                 a.part = p->part;
-                a.cond = h;
                 a.use_cond = 1;
-                cudaError_t e = launch_step(p->norm, k == K - 1, a, p->body_stream);
-                if (e != cudaSuccess) {
-                    cudaGraph_t bg;
-                    cudaStreamEndCapture(p->body_stream, &bg);
-                    return abort_capture(fail(W1_ERR_CUDA, std::string("capture step: ") + cudaGetErrorString(e)));
-                }
+                e = launch_step(p->norm, k == K - 1, a, p->body_stream);
+            }
+            if (e == cudaSuccess) e = launch_decide(p->ctl, B, h, p->body_stream);
+            if (e != cudaSuccess) {
+                cudaGraph_t bg;
+                cudaStreamEndCapture(p->body_stream, &bg);
+                return abort_capture(fail(W1_ERR_CUDA, std::string("capture step: ") + cudaGetErrorString(e)));
             }
             cudaGraph_t bg = nullptr;
             CAP_CK(cudaStreamEndCapture(p->body_stream, &bg));
@@ -432,6 +471,15 @@ static w1_status build_graph(w1_plan* p)
     p->graph = g;
     W1_CK(cudaGraphInstantiate(&p->exec, g, 0));
     p->graph_ok = true;
+    return W1_OK;
+}
+
+static w1_status pair_status(const w1_plan* p, const Ctl* c)
+{
+    if (c->error == 1) return W1_ERR_MASS;
+    if (c->timeout) return W1_ERR_TIMEOUT;
+    for (int l = 0; l < p->L; ++l)
+        if (!c->conv[l]) return W1_ERR_NOT_CONVERGED;
     return W1_OK;
 }
 
@@ -464,64 +512,119 @@ static void fill_stats(const w1_plan* p, const Ctl* c, w1_stats* st)
     st->converged = conv && !c->error && !c->timeout;
 }
 
-static w1_status solve_device(w1_plan* p, const float* rho0, const float* rho1, cudaStream_t s, double* dist,
-                              float* flux, w1_stats* stats)
+// Enqueues one batched solve on s: prep -> graph -> final statistics -> flux
+// copy -> device-to-host copy of the control blocks into the plan's pinned
+// result block.  Nothing waits.
+static w1_status enqueue(w1_plan* p, int nbatch, const float* rho0, const float* rho1, cudaStream_t s, float* flux)
 {
     if (!p->graph_ok) {
         w1_status st = build_graph(p);
         if (st != W1_OK) return st;
     }
     const long long n = (long long)p->nx * p->ny;
+    const int B = p->batch;
     const LevelPlan& f = p->lv[p->L - 1];
-    W1_CK(launch_prep(rho0, rho1, n, p->h, p->ctl, p->part, f.rho, s));
+    W1_CK(launch_prep(rho0, rho1, n, nbatch, B, p->h, p->ctl, p->part, f.rho, s));
     W1_CK(cudaGraphLaunch(p->exec, s));
-    W1_CK(launch_final(p->norm, f.m1[0], f.m2[0], f.phi[0], f.rho, f.nx, f.ny, f.h, p->q, p->part, p->ctl, s));
+    W1_CK(launch_final(p->norm, f.m1[0], f.m2[0], f.phi[0], f.rho, f.nx, f.ny, f.h, p->q, p->part, p->ctl, B, s));
     if (flux) {
-        W1_CK(cudaMemcpyAsync(flux, f.m1[0], n * sizeof(float), cudaMemcpyDeviceToDevice, s));
-        W1_CK(cudaMemcpyAsync(flux + n, f.m2[0], n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        // flux[b] = (m1 of pair b, m2 of pair b)
+        W1_CK(cudaMemcpy2DAsync(flux, 2 * n * sizeof(float), f.m1[0], n * sizeof(float), n * sizeof(float), nbatch,
+                                cudaMemcpyDeviceToDevice, s));
+        W1_CK(cudaMemcpy2DAsync(flux + n, 2 * n * sizeof(float), f.m2[0], n * sizeof(float), n * sizeof(float),
+                                nbatch, cudaMemcpyDeviceToDevice, s));
     }
-    W1_CK(cudaMemcpyAsync(p->host_ctl, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-    W1_CK(cudaStreamSynchronize(s));
-    const Ctl* c = p->host_ctl;
-    w1_stats tmp;
-    fill_stats(p, c, &tmp);
-    if (stats) *stats = tmp;
-    if (c->error) {
-        *dist = NAN;
-        return fail(W1_ERR_MASS, "densities have different mass or a non-finite value");
-    }
-    *dist = c->f;
-    if (c->timeout) return fail(W1_ERR_TIMEOUT, "a level hit the device time budget");
-    if (!tmp.converged) return fail(W1_ERR_NOT_CONVERGED, "a level hit max_iters");
+    W1_CK(cudaMemcpyAsync(p->host_ctl, p->ctl, sizeof(Ctl) * nbatch, cudaMemcpyDeviceToHost, s));
+    p->last_batch = nbatch;
     return W1_OK;
+}
+
+// Reads the pinned result block of the last enqueued solve (the stream must
+// have passed its end).
+static w1_status results(w1_plan* p, double* dist, w1_stats* stats, int* status)
+{
+    const int nbatch = p->last_batch;
+    w1_status worst = W1_OK;
+    for (int b = 0; b < nbatch; ++b) {
+        const Ctl* c = p->host_ctl + b;
+        if (stats) fill_stats(p, c, &stats[b]);
+        const w1_status sb = pair_status(p, c);
+        if (dist) dist[b] = sb == W1_ERR_MASS ? NAN : c->f;
+        if (status) status[b] = sb;
+        if (worst == W1_OK && sb != W1_OK) worst = sb;
+    }
+    if (worst == W1_ERR_MASS) return fail(worst, "densities have different mass or a non-finite value");
+    if (worst == W1_ERR_TIMEOUT) return fail(worst, "a level hit the device time budget");
+    if (worst == W1_ERR_NOT_CONVERGED) return fail(worst, "a level hit max_iters");
+    return W1_OK;
+}
+
+static w1_status solve_device(w1_plan* p, int nbatch, const float* rho0, const float* rho1, cudaStream_t s,
+                              double* dist, float* flux, w1_stats* stats, int* status)
+{
+    w1_status st = enqueue(p, nbatch, rho0, rho1, s, flux);
+    if (st != W1_OK) return st;
+    W1_CK(cudaStreamSynchronize(s));
+    return results(p, dist, stats, status);
+}
+
+extern "C" w1_status w1_solve_async(w1_plan* p, int nbatch, const float* rho0, const float* rho1, void* stream,
+                                    float* flux)
+{
+    if (!p || !rho0 || !rho1) return fail(W1_ERR_INVALID_ARG, "NULL plan or density");
+    if (nbatch < 1 || nbatch > p->batch) return fail(W1_ERR_INVALID_ARG, "batch must lie in [1, max_batch]");
+    W1_CK(cudaSetDevice(p->device));
+    return enqueue(p, nbatch, rho0, rho1, static_cast<cudaStream_t>(stream), flux);
+}
+
+extern "C" w1_status w1_plan_results(w1_plan* p, double* dist, w1_stats* stats, int* status)
+{
+    if (!p) return fail(W1_ERR_INVALID_ARG, "NULL plan");
+    if (p->last_batch < 1) return fail(W1_ERR_INVALID_ARG, "no solve was enqueued on this plan");
+    return results(p, dist, stats, status);
+}
+
+extern "C" w1_status w1_solve_batch(w1_plan* p, int nbatch, const float* rho0, const float* rho1, void* stream,
+                                    double* dist, float* flux, w1_stats* stats, int* status)
+{
+    if (!p || !rho0 || !rho1 || !dist) return fail(W1_ERR_INVALID_ARG, "NULL plan, density or dist");
+    if (nbatch < 1 || nbatch > p->batch) return fail(W1_ERR_INVALID_ARG, "batch must lie in [1, max_batch]");
+    W1_CK(cudaSetDevice(p->device));
+    return solve_device(p, nbatch, rho0, rho1, static_cast<cudaStream_t>(stream), dist, flux, stats, status);
 }
 
 extern "C" w1_status w1_solve(w1_plan* p, const float* rho0, const float* rho1, void* stream, double* dist,
                               float* flux, w1_stats* stats)
 {
+    return w1_solve_batch(p, 1, rho0, rho1, stream, dist, flux, stats, nullptr);
+}
+
+extern "C" w1_status w1_solve_batch_host(w1_plan* p, int nbatch, const float* rho0, const float* rho1, void* stream,
+                                         double* dist, float* flux, w1_stats* stats, int* status)
+{
     if (!p || !rho0 || !rho1 || !dist) return fail(W1_ERR_INVALID_ARG, "NULL plan, density or dist");
+    if (nbatch < 1 || nbatch > p->batch) return fail(W1_ERR_INVALID_ARG, "batch must lie in [1, max_batch]");
     W1_CK(cudaSetDevice(p->device));
-    return solve_device(p, rho0, rho1, static_cast<cudaStream_t>(stream), dist, flux, stats);
+    const size_t n = (size_t)p->nx * p->ny;
+    const size_t bytes = n * sizeof(float) * p->batch;
+    if (!p->in0) W1_CK(cudaMalloc(&p->in0, bytes));
+    if (!p->in1) W1_CK(cudaMalloc(&p->in1, bytes));
+    if (flux && !p->flux_d) W1_CK(cudaMalloc(&p->flux_d, 2 * bytes));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    W1_CK(cudaMemcpyAsync(p->in0, rho0, n * sizeof(float) * nbatch, cudaMemcpyHostToDevice, s));
+    W1_CK(cudaMemcpyAsync(p->in1, rho1, n * sizeof(float) * nbatch, cudaMemcpyHostToDevice, s));
+    w1_status st = solve_device(p, nbatch, p->in0, p->in1, s, dist, flux ? p->flux_d : nullptr, stats, status);
+    if (flux && st != W1_ERR_CUDA && st != W1_ERR_NOMEM && st != W1_ERR_INVALID_ARG) {
+        W1_CK(cudaMemcpyAsync(flux, p->flux_d, 2 * n * sizeof(float) * nbatch, cudaMemcpyDeviceToHost, s));
+        W1_CK(cudaStreamSynchronize(s));
+    }
+    return st;
 }
 
 extern "C" w1_status w1_solve_host(w1_plan* p, const float* rho0, const float* rho1, void* stream, double* dist,
                                    float* flux, w1_stats* stats)
 {
-    if (!p || !rho0 || !rho1 || !dist) return fail(W1_ERR_INVALID_ARG, "NULL plan, density or dist");
-    W1_CK(cudaSetDevice(p->device));
-    const size_t n = (size_t)p->nx * p->ny;
-    if (!p->in0) W1_CK(cudaMalloc(&p->in0, n * sizeof(float)));
-    if (!p->in1) W1_CK(cudaMalloc(&p->in1, n * sizeof(float)));
-    if (flux && !p->flux_d) W1_CK(cudaMalloc(&p->flux_d, 2 * n * sizeof(float)));
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    W1_CK(cudaMemcpyAsync(p->in0, rho0, n * sizeof(float), cudaMemcpyHostToDevice, s));
-    W1_CK(cudaMemcpyAsync(p->in1, rho1, n * sizeof(float), cudaMemcpyHostToDevice, s));
-    w1_status st = solve_device(p, p->in0, p->in1, s, dist, flux ? p->flux_d : nullptr, stats);
-    if (flux && (st == W1_OK || st == W1_ERR_NOT_CONVERGED || st == W1_ERR_TIMEOUT)) {
-        W1_CK(cudaMemcpyAsync(flux, p->flux_d, 2 * n * sizeof(float), cudaMemcpyDeviceToHost, s));
-        W1_CK(cudaStreamSynchronize(s));
-    }
-    return st;
+    return w1_solve_batch_host(p, 1, rho0, rho1, stream, dist, flux, stats, nullptr);
 }
 
 extern "C" w1_status w1_plan_potential(w1_plan* p, float* phi, void* stream)
@@ -529,7 +632,8 @@ extern "C" w1_status w1_plan_potential(w1_plan* p, float* phi, void* stream)
     if (!p || !phi) return fail(W1_ERR_INVALID_ARG, "NULL plan or phi");
     W1_CK(cudaSetDevice(p->device));
     const LevelPlan& f = p->lv[p->L - 1];
-    W1_CK(cudaMemcpyAsync(phi, f.phi[0], (size_t)f.nx * f.ny * sizeof(float), cudaMemcpyDeviceToDevice,
+    const int nb = p->last_batch > 0 ? p->last_batch : 1;
+    W1_CK(cudaMemcpyAsync(phi, f.phi[0], (size_t)f.nx * f.ny * sizeof(float) * nb, cudaMemcpyDeviceToDevice,
                           static_cast<cudaStream_t>(stream)));
     return W1_OK;
 }
@@ -569,6 +673,7 @@ extern "C" w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, f
     it.fixed = 1;
     it.level = 0;
     it.budget_ns = 600ull * 1000000000ull;
+    it.stride = (long long)nx * ny;
     it.ctl = nullptr;
     it.fpr_out = dfpr;
     w1_status ret = W1_OK;
@@ -583,17 +688,18 @@ extern "C" w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, f
         a.m2 = m2;
         a.phi = phi;
         a.rho = rho;
+        a.pairs = 1;
         a.it = it;
         cudaError_t e = launch_resident(norm, c, a, s);
         if (e != cudaSuccess) ret = fail(W1_ERR_CUDA, std::string("resident launch: ") + cudaGetErrorString(e));
     } else {
         const size_t n = (size_t)nx * ny;
-        const int rows = stream_rows_auto(nx, ny);
+        const int rows = stream_rows_auto(nx, ny, 1);
         float* buf = nullptr;
         double* part = nullptr;
         Ctl* ctl = nullptr;
         cudaError_t e = cudaMalloc(&buf, 3 * n * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc(&part, step_part_doubles(nx, ny, rows) * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&part, step_part_doubles(nx, ny, rows, 1) * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&ctl, sizeof(Ctl));
         if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
         float* A[3] = {m1, m2, phi};
@@ -610,6 +716,7 @@ extern "C" w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, f
             a.m2o = dst[1];
             a.phio = dst[2];
             a.rows = rows;
+            a.pairs = 1;
             a.it = it;
             a.it.ctl = ctl;
             a.part = part;
@@ -642,7 +749,7 @@ extern "C" w1_status w1_restrict(int nx, int ny, const float* fine, float* coars
 {
     if (nx < 2 || ny < 2 || (nx & 1) || (ny & 1) || !fine || !coarse)
         return fail(W1_ERR_INVALID_ARG, "w1_restrict needs even nx, ny >= 2");
-    W1_CK(launch_restrict(fine, nx, ny, coarse, static_cast<cudaStream_t>(stream)));
+    W1_CK(launch_restrict(fine, nx, ny, coarse, 1, nullptr, static_cast<cudaStream_t>(stream)));
     return W1_OK;
 }
 
@@ -651,7 +758,7 @@ extern "C" w1_status w1_prolong(int ncx, int ncy, const float* m1c, const float*
 {
     if (ncx < 1 || ncy < 1 || !m1c || !m2c || !phic || !m1f || !m2f || !phif)
         return fail(W1_ERR_INVALID_ARG, "bad arguments to w1_prolong");
-    W1_CK(launch_prolong(ncx, ncy, m1c, m2c, phic, m1f, m2f, phif, static_cast<cudaStream_t>(stream)));
+    W1_CK(launch_prolong(ncx, ncy, m1c, m2c, phic, m1f, m2f, phif, 1, nullptr, static_cast<cudaStream_t>(stream)));
     return W1_OK;
 }
 
@@ -666,10 +773,10 @@ extern "C" w1_status w1_state_stats(int nx, int ny, double h, int norm, const fl
     double *q = nullptr, *part = nullptr;
     Ctl* ctl = nullptr;
     cudaError_t e = cudaMalloc(&q, 2 * n * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&part, final_part_doubles() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&part, final_part_doubles(1) * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&ctl, sizeof(Ctl));
     if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
-    if (e == cudaSuccess) e = launch_final(norm, m1, m2, phi, rho, nx, ny, h, q, part, ctl, s);
+    if (e == cudaSuccess) e = launch_final(norm, m1, m2, phi, rho, nx, ny, h, q, part, ctl, 1, s);
     Ctl c{};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&c, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -48,6 +48,16 @@ class Options(ctypes.Structure):
                 ("rows_per_thread", ctypes.c_int)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("opt", Options)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_longlong) for n in ("submitted", "completed", "rejected", "queued", "in_flight",
+                                                  "slots", "evictions")] + [("bytes_in_use", ctypes.c_size_t)]
+
+
 class _Stats(ctypes.Structure):
     L = MAX_LEVELS
     _fields_ = [("levels", ctypes.c_int), ("nx", ctypes.c_int * L), ("ny", ctypes.c_int * L),
@@ -101,6 +111,12 @@ def _load() -> ctypes.CDLL:
         "w1_default_options": (None, [ctypes.POINTER(Options)]),
         "w1_plan_create": (st, [I, I, D, I, I, D, ctypes.POINTER(P)]),
         "w1_plan_create_ex": (st, [I, I, D, I, I, D, ctypes.POINTER(Options), ctypes.POINTER(P)]),
+        "w1_plan_create_batch": (st, [I, I, D, I, I, D, I, ctypes.POINTER(Options), ctypes.POINTER(P)]),
+        "w1_plan_max_batch": (I, [P]),
+        "w1_solve_batch": (st, [P, I, P, P, P, P, P, P, P]),
+        "w1_solve_batch_host": (st, [P, I, P, P, P, P, P, P, P]),
+        "w1_solve_async": (st, [P, I, P, P, P, P]),
+        "w1_plan_results": (st, [P, P, P, P]),
         "w1_plan_destroy": (st, [P]),
         "w1_plan_workspace_bytes": (ctypes.c_size_t, [P]),
         "w1_plan_set_workspace": (st, [P, P, ctypes.c_size_t]),
@@ -113,6 +129,17 @@ def _load() -> ctypes.CDLL:
         "w1_state_stats": (st, [I, I, D, I, P, P, P, P, P, ctypes.POINTER(_Stats)]),
         "w1_state_stats_noalloc": (st, [I, I, D, I, P, P, P, P, P, ctypes.POINTER(_Stats)]),
         "w1_noalloc_last_error": (ctypes.c_char_p, []),
+        "w1_plan_bytes": (ctypes.c_size_t, [I, I, D, I, I, D, I, ctypes.POINTER(Options)]),
+        "w1_server_default_config": (None, [ctypes.POINTER(ServerConfig)]),
+        "w1_server_create_ex": (st, [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]),
+        "w1_server_create": (st, [ctypes.c_size_t, I, ctypes.POINTER(P)]),
+        "w1_submit": (st, [P, I, I, D, I, I, D, P, P, ctypes.POINTER(ctypes.c_uint64)]),
+        "w1_poll": (st, [P, ctypes.c_uint64, ctypes.POINTER(D), ctypes.POINTER(_Stats)]),
+        "w1_poll_latency": (st, [P, ctypes.c_uint64, ctypes.POINTER(D), ctypes.POINTER(_Stats), ctypes.POINTER(D)]),
+        "w1_wait": (st, [P, ctypes.c_uint64, D, ctypes.POINTER(D), ctypes.POINTER(_Stats)]),
+        "w1_server_query": (st, [P, ctypes.POINTER(ServerInfo)]),
+        "w1_server_destroy": (st, [P]),
+        "w1_server_last_error": (ctypes.c_char_p, []),
         "w1_status_string": (ctypes.c_char_p, [st]),
         "w1_last_error": (ctypes.c_char_p, []),
     }
@@ -163,13 +190,14 @@ def _stream_ptr(stream):
 
 
 class Plan:
-    """A solver plan for nx x ny grids (w1_plan_create_ex)."""
+    """A solver plan for batches of up to `batch` nx x ny pairs (w1_plan_create_batch)."""
 
-    def __init__(self, nx, ny, h=0.0, levels=0, norm=NORM_L1, tol=0.0, **options):
+    def __init__(self, nx, ny, h=0.0, levels=0, norm=NORM_L1, tol=0.0, batch=1, **options):
         self._p = ctypes.c_void_p()
-        self.nx, self.ny = nx, ny
+        self.nx, self.ny, self.batch = nx, ny, batch
         opt = default_options(**options)
-        _check(_lib.w1_plan_create_ex(nx, ny, h, levels, norm, tol, ctypes.byref(opt), ctypes.byref(self._p)))
+        _check(_lib.w1_plan_create_batch(nx, ny, h, levels, norm, tol, batch, ctypes.byref(opt),
+                                         ctypes.byref(self._p)))
 
     def close(self):
         if self._p:
@@ -226,8 +254,67 @@ class Plan:
         _check(status, allow)
         return d.value, Stats._from(s), status
 
+    def solve_batch(self, rho0, rho1, flux=None, stream=None, allow=(OK,)):
+        """rho0, rho1: [b, ny, nx] device tensors (b <= batch).  Returns
+        (list of W1, list of Stats, list of per-pair statuses, status)."""
+        b = rho0.shape[0]
+        shape = (b, self.ny, self.nx)
+        d = (ctypes.c_double * b)()
+        s = (_Stats * b)()
+        ps = (ctypes.c_int * b)()
+        fp = _dev_ptr(flux, (b, 2, self.ny, self.nx)) if flux is not None else None
+        status = _lib.w1_solve_batch(self._p, b, _dev_ptr(rho0, shape), _dev_ptr(rho1, shape), _stream_ptr(stream),
+                                     ctypes.cast(d, ctypes.c_void_p), fp, ctypes.cast(s, ctypes.c_void_p),
+                                     ctypes.cast(ps, ctypes.c_void_p))
+        _check(status, allow)
+        return list(d), [Stats._from(x) for x in s], list(ps), status
+
+    def solve_batch_host(self, rho0, rho1, flux=None, stream=None, allow=(OK,)):
+        """Host float32 arrays [b, ny, nx] (and flux [b, 2, ny, nx])."""
+        import numpy as np
+        b = rho0.shape[0]
+        for a in (rho0, rho1):
+            if a.dtype != np.float32 or a.shape != (b, self.ny, self.nx) or not a.flags.c_contiguous:
+                raise TypeError("expected C-contiguous float32 arrays of shape (b, ny, nx)")
+        d = (ctypes.c_double * b)()
+        s = (_Stats * b)()
+        ps = (ctypes.c_int * b)()
+        fp = None
+        if flux is not None:
+            if flux.dtype != np.float32 or flux.shape != (b, 2, self.ny, self.nx) or not flux.flags.c_contiguous:
+                raise TypeError("flux must be a C-contiguous float32 array of shape (b, 2, ny, nx)")
+            fp = ctypes.c_void_p(flux.ctypes.data)
+        status = _lib.w1_solve_batch_host(self._p, b, ctypes.c_void_p(rho0.ctypes.data),
+                                          ctypes.c_void_p(rho1.ctypes.data), _stream_ptr(stream),
+                                          ctypes.cast(d, ctypes.c_void_p), fp, ctypes.cast(s, ctypes.c_void_p),
+                                          ctypes.cast(ps, ctypes.c_void_p))
+        _check(status, allow)
+        return list(d), [Stats._from(x) for x in s], list(ps), status
+
+    def solve_async(self, rho0, rho1, flux=None, stream=None):
+        """Enqueue a solve of rho0, rho1 ([ny, nx] or [b, ny, nx] device tensors)
+        on `stream` without waiting; read it with results() once the stream is done."""
+        b = 1 if rho0.dim() == 2 else rho0.shape[0]
+        shape = tuple(rho0.shape)
+        fshape = (2, self.ny, self.nx) if rho0.dim() == 2 else (b, 2, self.ny, self.nx)
+        fp = _dev_ptr(flux, fshape) if flux is not None else None
+        _check(_lib.w1_solve_async(self._p, b, _dev_ptr(rho0, shape), _dev_ptr(rho1, shape), _stream_ptr(stream), fp))
+        self._pending = b
+
+    def results(self, allow=(OK, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_MASS)):
+        """(list of W1, list of Stats, list of statuses, status) of the last solve_async."""
+        b = getattr(self, "_pending", 1)
+        d = (ctypes.c_double * b)()
+        s = (_Stats * b)()
+        ps = (ctypes.c_int * b)()
+        status = _lib.w1_plan_results(self._p, ctypes.cast(d, ctypes.c_void_p), ctypes.cast(s, ctypes.c_void_p),
+                                      ctypes.cast(ps, ctypes.c_void_p))
+        _check(status, allow)
+        return list(d), [Stats._from(x) for x in s], list(ps), status
+
     def potential(self, out, stream=None):
-        _check(_lib.w1_plan_potential(self._p, _dev_ptr(out, (self.ny, self.nx)), _stream_ptr(stream)))
+        shape = (self.ny, self.nx) if out.dim() == 2 else (out.shape[0], self.ny, self.nx)
+        _check(_lib.w1_plan_potential(self._p, _dev_ptr(out, shape), _stream_ptr(stream)))
         return out
 
 
@@ -264,3 +351,72 @@ def state_stats(rho, m1, m2, phi, h, norm, stream=None) -> Stats:
 
 def status_string(status: int) -> str:
     return _lib.w1_status_string(status).decode()
+
+
+def plan_bytes(nx, ny, h=0.0, levels=0, norm=NORM_L1, tol=0.0, batch=1, **options) -> int:
+    opt = default_options(**options)
+    return _lib.w1_plan_bytes(nx, ny, h, levels, norm, tol, batch, ctypes.byref(opt))
+
+
+class Server:
+    """Continuous-batching request loop (w1_server_create_ex)."""
+
+    def __init__(self, hbm_budget_bytes=40 << 30, max_slots=32, max_batch=1, **options):
+        cfg = ServerConfig()
+        _lib.w1_server_default_config(ctypes.byref(cfg))
+        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        cfg.max_slots = max_slots
+        cfg.max_batch = max_batch
+        for k, v in options.items():
+            setattr(cfg.opt, k, v)
+        self._s = ctypes.c_void_p()
+        st = _lib.w1_server_create_ex(ctypes.byref(cfg), ctypes.byref(self._s))
+        if st != OK:
+            raise W1Error(st, _lib.w1_server_last_error().decode())
+
+    def submit(self, rho0, rho1, norm=NORM_L1, levels=0, tol=0.0, h=0.0) -> int:
+        """Queue one pair ([ny, nx] device tensors, kept alive by the caller until done)."""
+        ny, nx = rho0.shape
+        t = ctypes.c_uint64(0)
+        st = _lib.w1_submit(self._s, nx, ny, h, levels, norm, tol, _dev_ptr(rho0), _dev_ptr(rho1, (ny, nx)),
+                            ctypes.byref(t))
+        if st != OK:
+            raise W1Error(st, _lib.w1_server_last_error().decode())
+        return t.value
+
+    def poll(self, ticket):
+        """(status, W1, Stats, server latency in s); status PENDING while not finished."""
+        d, lat = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        s = _Stats()
+        st = _lib.w1_poll_latency(self._s, ticket, ctypes.byref(d), ctypes.byref(s), ctypes.byref(lat))
+        if st == PENDING:
+            return st, None, None, None
+        return st, d.value, Stats._from(s), lat.value
+
+    def wait(self, ticket, timeout_s=0.0):
+        d = ctypes.c_double(0.0)
+        s = _Stats()
+        st = _lib.w1_wait(self._s, ticket, timeout_s, ctypes.byref(d), ctypes.byref(s))
+        return st, d.value, Stats._from(s)
+
+    def info(self) -> dict:
+        i = ServerInfo()
+        _lib.w1_server_query(self._s, ctypes.byref(i))
+        return {n: getattr(i, n) for n, _ in ServerInfo._fields_}
+
+    def close(self):
+        if self._s:
+            _lib.w1_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

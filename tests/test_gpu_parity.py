@@ -293,3 +293,62 @@ def test_resident_path_rejects_grids_it_cannot_hold(w1):
     g = [torch.zeros((200, 300), device="cuda") for _ in range(4)]
     with pytest.raises(w1.W1Error, match="ERR_UNSUPPORTED"):
         w1.cp_steps(*g, 1 / 300, 1, 1e-3, 1e-3, 2, path=1)
+
+
+# --------------------------------------------------------------------------------------
+# Batched solves
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("norm,n,levels", [(L1, 64, 3), (L2, 128, 4), (L1, 512, 6)])
+def test_batch_results_equal_single_solves(w1, norm, n, levels):
+    """A pair gives bitwise the same W1, flux and iteration counts alone and
+    inside a batch (fixed per-pair reduction order)."""
+    B = 3
+    pairs = [synth.pair(2 if n == 512 else 0, 10 + k, n=n) for k in range(B)]
+    a0 = np.stack([p[0] for p in pairs]).astype(np.float32)
+    a1 = np.stack([p[1] for p in pairs]).astype(np.float32)
+    fb = torch.empty((B, 2, n, n), device="cuda")
+    with w1.Plan(n, n, levels=levels, norm=norm, batch=4) as plan:
+        vals, stats, statuses, _ = plan.solve_batch(dev(a0), dev(a1), flux=fb)
+    assert statuses == [w1.OK] * B
+    with w1.Plan(n, n, levels=levels, norm=norm) as single:
+        for k in range(B):
+            f1 = torch.empty((2, n, n), device="cuda")
+            v, st, _ = single.solve(dev(a0[k]), dev(a1[k]), flux=f1)
+            assert v == vals[k] and st.iters == stats[k].iters
+            assert torch.equal(f1, fb[k])
+
+
+def test_batch_isolates_a_rejected_pair(w1):
+    r = [synth.pair(0, 20 + k) for k in range(3)]
+    a0 = np.stack([x[0] for x in r]).astype(np.float32)
+    a1 = np.stack([x[1] for x in r]).astype(np.float32)
+    a1[1] *= 1.01  # pair 1 loses mass balance
+    with w1.Plan(64, 64, levels=3, norm=L1, batch=3) as plan:
+        vals, stats, statuses, status = plan.solve_batch(dev(a0), dev(a1), allow=(w1.ERR_MASS,))
+        assert status == w1.ERR_MASS and statuses == [w1.OK, w1.ERR_MASS, w1.OK]
+        assert np.isnan(vals[1]) and vals[0] > 0 and vals[2] > 0
+        with w1.Plan(64, 64, levels=3, norm=L1) as single:
+            v0, _, _ = single.solve(dev(a0[0]), dev(a1[0]))
+            v2, _, _ = single.solve(dev(a0[2]), dev(a1[2]))
+        assert vals[0] == v0 and vals[2] == v2
+        # a partial batch (fewer pairs than the plan holds) and the host entry point
+        fh = np.empty((2, 2, 64, 64), dtype=np.float32)
+        hv, _, hs, _ = plan.solve_batch_host(np.ascontiguousarray(a0[[0, 2]]), np.ascontiguousarray(a1[[0, 2]]),
+                                             flux=fh)
+        assert hv == [v0, v2] and hs == [w1.OK, w1.OK]
+
+
+def test_batch_oracle_parity_512(w1):
+    """Every pair of a 512x512 batch against the oracle replaying its counts (p = 2)."""
+    B = 2
+    pairs = [synth.pair(2, 30 + k) for k in range(B)]
+    a0 = np.stack([p[0] for p in pairs]).astype(np.float32)
+    a1 = np.stack([p[1] for p in pairs]).astype(np.float32)
+    fb = torch.empty((B, 2, 512, 512), device="cuda")
+    with w1.Plan(512, 512, levels=6, norm=L2, batch=B) as plan:
+        vals, stats, _, _ = plan.solve_batch(dev(a0), dev(a1), flux=fb)
+    for k in range(B):
+        ref = oracle.multilevel(a0[k].astype(np.float64), a1[k].astype(np.float64), levels=6, norm=L2,
+                                replay=stats[k].iters)
+        assert_parity(vals[k], stats[k], host(fb[k]), ref)
