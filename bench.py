@@ -34,6 +34,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# Many concurrent solves use many streams; give the context 32 hardware work
+# queues instead of the default 8 (must be set before CUDA initialises).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 N = 512
 LEVELS = 6

@@ -65,13 +65,16 @@ typedef enum {
 
 /* Plan options; w1_default_options() fills the defaults given here. */
 typedef struct {
-    int check_every;       /* K >= 2, even: steps between stop tests (default 32)             */
+    int check_every;       /* K: steps between stop tests, a multiple of 8 (default 32)       */
     long long max_iters;   /* cap on steps per level (default 1000000)                        */
     double theta;          /* mu = tau = theta / ||A_h||, ||A_h|| <= 2 sqrt(2) / h (Sec. 4);
                               0.5 is the paper's choice (default), 1.0 its footnote's         */
     double alpha;          /* eps_l = tol * (h_l / h)^alpha (default -1)                      */
     double time_budget_s;  /* device wall-clock guard per level (default 60 s)               */
-    int path;              /* 0 automatic; 1 shared-memory resident; 2 streaming (global)     */
+    int path;              /* 0 automatic; 1 shared-memory resident; 2 streaming, one step per
+                              launch; 3 streaming with temporal blocking (4 steps per launch,
+                              needs nx % 4 == 0); automatic = 1 where a level fits on chip,
+                              else 3 where possible, else 2                                 */
     int rows_per_thread;   /* streaming kernel: rows marched per thread (0 = automatic)       */
 } w1_options;
 
@@ -83,7 +86,7 @@ typedef struct {
     long long iters[W1_MAX_LEVELS]; /* steps taken on each level */
     double fpr[W1_MAX_LEVELS];      /* R^k at the last stop test of each level */
     double tol[W1_MAX_LEVELS];      /* eps_l of each level */
-    int path[W1_MAX_LEVELS];        /* 1 resident (cluster size in cluster[]), 2 streaming */
+    int path[W1_MAX_LEVELS];        /* 1 resident (cluster size in cluster[]), 2 streaming, 3 blocked */
     int cluster[W1_MAX_LEVELS];
     double w1;       /* f(m) of the returned finest flux: the W1 estimate (Sec. 5 reports f(m^K)) */
     double dual;     /* -<phi, rho>_h of the returned potential */
@@ -203,7 +206,10 @@ size_t w1_plan_bytes(int nx, int ny, double h, int levels, int norm, double tol,
  * created within the HBM budget (idle slots of other classes are evicted,
  * least recently used first); up to max_slots solves run at once on their own
  * streams, so their work overlaps on the device.  A request's result does not
- * depend on what else is in flight.  All calls are thread-safe.
+ * depend on what else is in flight.  All calls are thread-safe.  Streams share
+ * the context's hardware work queues (8 unless CUDA_DEVICE_MAX_CONNECTIONS is
+ * set, up to 32, before CUDA initialises); with more slots than queues, long
+ * level solves on one queue delay the launches of the streams that share it.
  */
 typedef struct w1_server w1_server;
 
@@ -251,7 +257,8 @@ const char* w1_server_last_error(void);
 /*
  * `iters` steps of eq. primaldual in place on (m1, m2, phi) with density rho,
  * step sizes mu, tau, spacing h.  path: 1 shared-memory resident (grids up to
- * 16 * 4096 nodes), 2 streaming.  If fpr_last is not NULL it receives R^k of
+ * 16 * 4096 nodes), 2 streaming, 3 temporally blocked streaming (nx and iters
+ * multiples of 4).  If fpr_last is not NULL it receives R^k of
  * the last step (FP64 sums).  The boundary flux entries must be 0 on entry.
  */
 w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, float tau, const float* rho, float* m1,

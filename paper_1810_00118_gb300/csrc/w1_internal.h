@@ -86,6 +86,12 @@ cudaError_t launch_prolong(int ncx, int ncy, const float* m1c, const float* m2c,
 cudaError_t launch_level_begin(Ctl* ctl, int level, int pairs, cudaStream_t s);
 // Streaming step; check selects the variant that forms R^k and tests it.
 cudaError_t launch_step(int norm, bool check, const StepArgs& a, cudaStream_t s);
+// Temporally blocked streaming steps: tblock_depth() steps per launch (the
+// last one forms R^k when check is set); same arguments as launch_step.
+cudaError_t launch_tblock(int norm, bool check, const StepArgs& a, cudaStream_t s);
+int tblock_depth();
+dim3 tblock_grid(int nx, int ny, int pairs);
+size_t tblock_part_doubles(int nx, int ny, int pairs);
 // After a check step in graph mode: continue the WHILE node while any pair is active.
 cudaError_t launch_decide(const Ctl* ctl, int pairs, cudaGraphConditionalHandle cond, cudaStream_t s);
 int stream_rows_auto(int nx, int ny, int pairs);

@@ -512,6 +512,247 @@ cudaError_t launch_step(int norm, bool check, const StepArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Temporally blocked streaming step: TB steps per launch
+// ---------------------------------------------------------------------------
+//
+// Each CTA loads a tile of (TBX + 2 TB) x (TBY + 2 TB) nodes (its TBX x TBY
+// interior plus a halo of TB on every side) into shared memory, runs TB steps
+// of eq. primaldual there with four consecutive nodes of a row per thread, and
+// writes the interior back.  A wrong value at the tile's edge moves inwards by
+// at most one node per step, so after TB steps the interior is exact.  Nodes
+// outside the grid are loaded as zeros and never influence a node of the grid
+// (the zero-flux boundary conditions test global indices).  On a test launch
+// the last step forms the interior nodes' share of R^k, summed per pair as in
+// k_step.  Global traffic per step: (16 B x tile/interior + 12 B) / TB per node.
+
+static constexpr int TBX = 64, TBY = 32, TB = 4;
+static constexpr int TLW = TBX + 2 * TB, TLH = TBY + 2 * TB, TLN = TLW * TLH;  // 72 x 40 = 2880
+static constexpr int TB_THREADS = ((TLN / 4 + 31) / 32) * 32;                // 736
+
+dim3 tblock_grid(int nx, int ny, int pairs) { return dim3((nx + TBX - 1) / TBX, (ny + TBY - 1) / TBY, pairs); }
+size_t tblock_part_doubles(int nx, int ny, int pairs)
+{
+    dim3 g = tblock_grid(nx, ny, pairs);
+    return (size_t)g.x * g.y * g.z * 3;
+}
+int tblock_depth() { return TB; }
+
+template <int NORM, bool CHECK>
+__global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
+{
+    const IterArgs& P = a.it;
+    const int pair = blockIdx.z;
+    Ctl* pc = P.ctl ? P.ctl + pair : nullptr;
+    if (pc && (pc->error || (a.use_cond && !pc->active))) return;  // uniform over the pair's blocks
+    const int nx = P.nx, ny = P.ny;
+    const int X0 = blockIdx.x * TBX - TB, Y0 = blockIdx.y * TBY - TB;  // tile origin (may be negative)
+    extern __shared__ __align__(16) unsigned char tb_smem[];
+    float* ph = reinterpret_cast<float*>(tb_smem);
+    float* s1 = ph + TLN;
+    float* s2 = s1 + TLN;
+    float* e1s = s2 + TLN;  // test launches only
+    float* e2s = e1s + TLN;
+    const size_t off = (size_t)pair * P.stride;
+    const float mu = P.mu, tau = P.tau, ih = P.ih;
+    const int t = threadIdx.x;
+    const bool own = t < TLN / 4;
+    const int W = TLW / 4;
+    const int jl = own ? t / W : 0;
+    const int il = own ? 4 * (t - jl * W) : 0;
+    const int idx = jl * TLW + il;
+    const int gj = Y0 + jl, gi0 = X0 + il;
+    const bool row_in = gj >= 0 && gj < ny;
+    float m1[4], m2[4], pv[4], rv[4], Dv[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int gi = gi0 + c;
+        const bool in = own && row_in && gi >= 0 && gi < nx;
+        const size_t g = off + (size_t)(in ? gj : 0) * nx + (in ? gi : 0);
+        m1[c] = in ? __ldg(a.m1 + g) : 0.f;
+        m2[c] = in ? __ldg(a.m2 + g) : 0.f;
+        pv[c] = in ? __ldg(a.phi + g) : 0.f;
+        rv[c] = in ? __ldg(a.rho + g) : 0.f;
+    }
+    if (own) {
+        *reinterpret_cast<float4*>(ph + idx) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+        *reinterpret_cast<float4*>(s1 + idx) = make_float4(m1[0], m1[1], m1[2], m1[3]);
+        *reinterpret_cast<float4*>(s2 + idx) = make_float4(m2[0], m2[1], m2[2], m2[3]);
+    }
+    __syncthreads();
+    if (own) {  // D^0 = div m^0 (wrong on the tile's first column and row, as it should be)
+        const float l = il > 0 ? s1[idx - 1] : 0.f;
+        const float4 b = jl > 0 ? *reinterpret_cast<const float4*>(s2 + idx - TLW) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int gi = gi0 + c;
+            const float left = c ? m1[c - 1] : l;
+            Dv[c] = (((gi < nx - 1 ? m1[c] : 0.f) - (gi > 0 ? left : 0.f)) + ((gj < ny - 1 ? m2[c] : 0.f) - (gj > 0 ? bb[c] : 0.f))) * ih;
+        }
+    }
+    __syncthreads();
+    double sa = 0.0, sb = 0.0, sc = 0.0;
+    const bool interior_row = jl >= TB && jl < TB + TBY && row_in;
+#pragma unroll 1
+    for (int step = 0; step < TB; ++step) {
+        const bool last = CHECK && step == TB - 1;
+        if (own) {
+            float up[4] = {0.f, 0.f, 0.f, 0.f};
+            if (jl < TLH - 1) {
+                const float4 u = *reinterpret_cast<const float4*>(ph + idx + TLW);
+                up[0] = u.x; up[1] = u.y; up[2] = u.z; up[3] = u.w;
+            }
+            const float right = il + 4 < TLW ? ph[idx + 4] : 0.f;
+            float n1[4], n2[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int gi = gi0 + c;
+                const float pr_ = c < 3 ? pv[c + 1] : right;
+                const float g1 = gi < nx - 1 ? (pr_ - pv[c]) * ih : 0.f;
+                const float g2 = gj < ny - 1 ? (up[c] - pv[c]) * ih : 0.f;
+                prox<NORM>(m1[c] + mu * g1, m2[c] + mu * g2, mu, n1[c], n2[c]);
+                if (gi >= nx - 1) n1[c] = 0.f;
+                if (gj >= ny - 1) n2[c] = 0.f;
+            }
+            if (last) {
+                float d1[4], d2[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    d1[c] = n1[c] - m1[c];
+                    d2[c] = n2[c] - m2[c];
+                    const int ci = il + c;
+                    if (interior_row && ci >= TB && ci < TB + TBX && gi0 + c < nx)
+                        sa += (double)d1[c] * d1[c] + (double)d2[c] * d2[c];
+                }
+                *reinterpret_cast<float4*>(e1s + idx) = make_float4(d1[0], d1[1], d1[2], d1[3]);
+                *reinterpret_cast<float4*>(e2s + idx) = make_float4(d2[0], d2[1], d2[2], d2[3]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                m1[c] = n1[c];
+                m2[c] = n2[c];
+            }
+            *reinterpret_cast<float4*>(s1 + idx) = make_float4(n1[0], n1[1], n1[2], n1[3]);
+            *reinterpret_cast<float4*>(s2 + idx) = make_float4(n2[0], n2[1], n2[2], n2[3]);
+        }
+        __syncthreads();
+        if (own) {
+            const float l = il > 0 ? s1[idx - 1] : 0.f;
+            const float4 b = jl > 0 ? *reinterpret_cast<const float4*>(s2 + idx - TLW) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float bb[4] = {b.x, b.y, b.z, b.w};
+            float pn[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int gi = gi0 + c;
+                const float left = c ? m1[c - 1] : l;
+                const float Dn = ((m1[c] - (gi > 0 ? left : 0.f)) + (m2[c] - (gj > 0 ? bb[c] : 0.f))) * ih;
+                pn[c] = pv[c] + tau * ((2.f * Dn - Dv[c]) - rv[c]);
+                Dv[c] = Dn;
+            }
+            if (last) {
+                const float4 e1 = *reinterpret_cast<const float4*>(e1s + idx);
+                const float4 e2 = *reinterpret_cast<const float4*>(e2s + idx);
+                const float el = il > 0 ? e1s[idx - 1] : 0.f;
+                const float4 eb = jl > 0 ? *reinterpret_cast<const float4*>(e2s + idx - TLW) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float a1[4] = {e1.x, e1.y, e1.z, e1.w}, a2[4] = {e2.x, e2.y, e2.z, e2.w};
+                const float bl[4] = {eb.x, eb.y, eb.z, eb.w};
+                const double ihd = 1.0 / P.h;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int ci = il + c, gi = gi0 + c;
+                    if (!(interior_row && ci >= TB && ci < TB + TBX && gi < nx)) continue;
+                    const double left = c ? (double)a1[c - 1] : (gi > 0 ? (double)el : 0.0);
+                    const double below = gj > 0 ? (double)bl[c] : 0.0;
+                    const double dd = (((double)a1[c] - left) + ((double)a2[c] - below)) * ihd;
+                    const double ep = (double)pn[c] - (double)pv[c];
+                    sb += ep * ep;
+                    sc += ep * dd;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) pv[c] = pn[c];
+            *reinterpret_cast<float4*>(ph + idx) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+        }
+        __syncthreads();
+    }
+    // write the interior
+    if (own && interior_row) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int ci = il + c, gi = gi0 + c;
+            if (ci < TB || ci >= TB + TBX || gi >= nx) continue;
+            const size_t g = off + (size_t)gj * nx + gi;
+            a.m1o[g] = m1[c];
+            a.m2o[g] = m2[c];
+            a.phio[g] = pv[c];
+        }
+    }
+    if (!CHECK) return;
+    __shared__ double sh[32 * 3];
+    __shared__ bool lastblk;
+    double v[3] = {sa, sb, sc};
+    block_sum<3>(v, sh);
+    const int nblk = gridDim.x * gridDim.y;
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    double* pp = a.part + (size_t)pair * nblk * 3;
+    if (t == 0) {
+        pp[bid * 3 + 0] = v[0];
+        pp[bid * 3 + 1] = v[1];
+        pp[bid * 3 + 2] = v[2];
+        __threadfence();
+        lastblk = (atomicAdd(&pc->counter, 1u) == (unsigned)nblk - 1);
+    }
+    __syncthreads();
+    if (!lastblk) return;
+    __threadfence();
+    double tt[3] = {0.0, 0.0, 0.0};
+    for (int b = t; b < nblk; b += blockDim.x)
+        for (int c = 0; c < 3; ++c) tt[c] += ((volatile double*)pp)[b * 3 + c];
+    block_sum<3>(tt, sh);
+    if (t == 0) {
+        const double h2 = P.h * P.h;
+        const double R = (tt[0] / (double)P.mu + tt[1] / (double)P.tau - 2.0 * tt[2]) * h2;
+        pc->counter = 0;
+        if (P.fpr_out) P.fpr_out[pair] = R;
+        if (a.use_cond) {
+            const long long it = pc->iters[P.level] + P.K;
+            pc->iters[P.level] = it;
+            pc->fpr[P.level] = R;
+            const int conv = R < P.tol;
+            pc->conv[P.level] = conv;
+            const bool late = (globaltimer() - pc->t_start[P.level]) > P.budget_ns;
+            if (late && !conv) pc->timeout = 1;
+            if (conv || it >= P.cap || late) pc->active = 0;
+        }
+    }
+}
+
+static constexpr size_t TB_SMEM_PLAIN = 3 * TLN * sizeof(float), TB_SMEM_CHECK = 5 * TLN * sizeof(float);
+
+cudaError_t tblock_prepare()
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_tblock<W1_NORM_L1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)TB_SMEM_CHECK)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_tblock<W1_NORM_L2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TB_SMEM_CHECK);
+}
+
+cudaError_t launch_tblock(int norm, bool check, const StepArgs& a, cudaStream_t s)
+{
+    dim3 g = tblock_grid(a.it.nx, a.it.ny, a.pairs);
+    if (norm == W1_NORM_L1) {
+        if (check) k_tblock<W1_NORM_L1, true><<<g, TB_THREADS, TB_SMEM_CHECK, s>>>(a);
+        else k_tblock<W1_NORM_L1, false><<<g, TB_THREADS, TB_SMEM_PLAIN, s>>>(a);
+    } else {
+        if (check) k_tblock<W1_NORM_L2, true><<<g, TB_THREADS, TB_SMEM_CHECK, s>>>(a);
+        else k_tblock<W1_NORM_L2, false><<<g, TB_THREADS, TB_SMEM_PLAIN, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 __global__ void k_decide(const Ctl* __restrict__ ctls, int pairs, cudaGraphConditionalHandle cond)
 {
     int any = 0;
@@ -784,6 +1025,239 @@ __global__ void __launch_bounds__(NPT >= 8 ? RES_THREADS / 2 : RES_THREADS, 1) k
     if (CL) cg::this_cluster().sync();
 }
 
+// Vectorised variant for rows whose width is a multiple of 4: a thread owns
+// four consecutive nodes of one row and keeps their m1, m2, phi, rho and
+// D = div m^k in registers.  Shared memory holds the band's phi, m1', m2' (and
+// dm on test steps) so that neighbours can read them: the row above and the
+// row below as one 16-byte access, the left/right neighbour of the run as one
+// scalar access.  Same arithmetic and stop test as k_resident.
+__device__ __forceinline__ float4 dsmem_ld4(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+template <int NORM, bool CL>
+__global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
+{
+    const IterArgs& P = a.it;
+    int C = 1, rank = 0;
+    if (CL) {
+        cg::cluster_group cl = cg::this_cluster();
+        C = (int)cl.num_blocks();
+        rank = (int)cl.block_rank();
+    }
+    const int pair = blockIdx.x / C;
+    Ctl* pc = P.ctl ? P.ctl + pair : nullptr;
+    if (pc && pc->error) return;  // uniform over the cluster (one pair)
+    const int nx = P.nx, ny = P.ny;
+    const int rows = ny / C, jb = rank * rows, nb = rows * nx;
+    const int W = nx >> 2;  // threads per row
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* red = reinterpret_cast<double*>(smraw);
+    double* slots = reinterpret_cast<double*>(smraw + RES_RED_BYTES);
+    float* ph = reinterpret_cast<float*>(smraw + RES_RED_BYTES + RES_SLOT_BYTES);
+    float* s1 = ph + nb;
+    float* s2 = s1 + nb;
+    float* e1s = s2 + nb;
+    float* e2s = e1s + nb;
+    const size_t off = (size_t)pair * P.stride + (size_t)jb * nx;
+    const float mu = P.mu, tau = P.tau, ih = P.ih;
+
+    const int t = threadIdx.x;
+    const bool own = t < rows * W;
+    const int jl = own ? t / W : 0;
+    const int i0 = own ? 4 * (t - jl * W) : 0;
+    const int idx = jl * nx + i0;
+    const int j = jb + jl;
+    float m1[4] = {0.f, 0.f, 0.f, 0.f}, m2[4] = {0.f, 0.f, 0.f, 0.f}, pv[4] = {0.f, 0.f, 0.f, 0.f};
+    float rv[4] = {0.f, 0.f, 0.f, 0.f}, Dv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (own) {
+        const float4 x1 = *reinterpret_cast<const float4*>(a.m1 + off + idx);
+        const float4 x2 = *reinterpret_cast<const float4*>(a.m2 + off + idx);
+        const float4 xp = *reinterpret_cast<const float4*>(a.phi + off + idx);
+        const float4 xr = *reinterpret_cast<const float4*>(a.rho + off + idx);
+        m1[0] = x1.x; m1[1] = x1.y; m1[2] = x1.z; m1[3] = x1.w;
+        m2[0] = x2.x; m2[1] = x2.y; m2[2] = x2.z; m2[3] = x2.w;
+        pv[0] = xp.x; pv[1] = xp.y; pv[2] = xp.z; pv[3] = xp.w;
+        rv[0] = xr.x; rv[1] = xr.y; rv[2] = xr.z; rv[3] = xr.w;
+        *reinterpret_cast<float4*>(ph + idx) = xp;
+        *reinterpret_cast<float4*>(s1 + idx) = x1;
+        *reinterpret_cast<float4*>(s2 + idx) = x2;
+    }
+    if (CL) cg::this_cluster().sync();
+    else __syncthreads();
+    const int last_row = (rows - 1) * nx;
+    uint32_t ph_up = 0, s2_dn = 0, e2_dn = 0, slots0 = smem_u32(slots);
+    if (CL) {
+        if (rank + 1 < C) ph_up = dsmem_map(smem_u32(ph + i0), rank + 1);
+        if (rank > 0) {
+            s2_dn = dsmem_map(smem_u32(s2 + last_row + i0), rank - 1);
+            e2_dn = dsmem_map(smem_u32(e2s + last_row + i0), rank - 1);
+        }
+        slots0 = dsmem_map(smem_u32(slots), 0);
+    }
+    // m2 of the row below the run (zero flux below the grid)
+    auto below4 = [&](const float* arr, uint32_t remote) -> float4 {
+        if (jl > 0) return *reinterpret_cast<const float4*>(arr + idx - nx);
+        if (CL && rank > 0) return dsmem_ld4(remote);
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    if (own) {  // D^0 = div m^0
+        const float l = i0 > 0 ? s1[idx - 1] : 0.f;
+        const float4 b = below4(s2, s2_dn);
+        const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Dv[c] = ((m1[c] - (c ? m1[c - 1] : l)) + (m2[c] - bb[c])) * ih;
+    }
+    if (CL) cg::this_cluster().sync();
+    else __syncthreads();
+
+    unsigned long long t0 = 0;
+    if (rank == 0 && t == 0) t0 = globaltimer();
+    long long it = 0;
+    double R = 0.0;
+    int conv = 0, late = 0;
+    const long long cap = P.cap;
+    const bool last_col = own && (i0 + 4 == nx);
+    while (it < cap) {
+        const bool check = P.fixed ? (it + 1 == cap) : ((it + 1) % P.K == 0);
+        double sa = 0.0, sb = 0.0, sc = 0.0;
+        // ---- phase A: m' = prox(m + mu grad phi)
+        if (own) {
+            float up[4] = {0.f, 0.f, 0.f, 0.f};
+            if (j < ny - 1) {
+                const float4 u = (jl < rows - 1) ? *reinterpret_cast<const float4*>(ph + idx + nx) : dsmem_ld4(ph_up);
+                up[0] = u.x; up[1] = u.y; up[2] = u.z; up[3] = u.w;
+            }
+            const float right = last_col ? 0.f : ph[idx + 4];
+            float n1[4], n2[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float pr_ = c < 3 ? pv[c + 1] : right;
+                const float g1 = (c == 3 && last_col) ? 0.f : (pr_ - pv[c]) * ih;
+                const float g2 = (j < ny - 1) ? (up[c] - pv[c]) * ih : 0.f;
+                prox<NORM>(m1[c] + mu * g1, m2[c] + mu * g2, mu, n1[c], n2[c]);
+                if (c == 3 && last_col) n1[c] = 0.f;
+                if (j == ny - 1) n2[c] = 0.f;
+            }
+            if (check) {
+                float d1[4], d2[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    d1[c] = n1[c] - m1[c];
+                    d2[c] = n2[c] - m2[c];
+                    sa += (double)d1[c] * d1[c] + (double)d2[c] * d2[c];
+                }
+                *reinterpret_cast<float4*>(e1s + idx) = make_float4(d1[0], d1[1], d1[2], d1[3]);
+                *reinterpret_cast<float4*>(e2s + idx) = make_float4(d2[0], d2[1], d2[2], d2[3]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                m1[c] = n1[c];
+                m2[c] = n2[c];
+            }
+            *reinterpret_cast<float4*>(s1 + idx) = make_float4(n1[0], n1[1], n1[2], n1[3]);
+            *reinterpret_cast<float4*>(s2 + idx) = make_float4(n2[0], n2[1], n2[2], n2[3]);
+        }
+        if (CL) {
+            cluster_arrive();
+            cluster_wait();
+        } else {
+            __syncthreads();
+        }
+        // ---- phase B: phi' = phi + tau (div(2m' - m) - rho)
+        if (own) {
+            const float l = i0 > 0 ? s1[idx - 1] : 0.f;
+            const float4 b = below4(s2, s2_dn);
+            const float bb[4] = {b.x, b.y, b.z, b.w};
+            float pn[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float Dn = ((m1[c] - (c ? m1[c - 1] : l)) + (m2[c] - bb[c])) * ih;
+                pn[c] = pv[c] + tau * ((2.f * Dn - Dv[c]) - rv[c]);
+                Dv[c] = Dn;
+            }
+            if (check) {
+                const float4 e1 = *reinterpret_cast<const float4*>(e1s + idx);
+                const float4 e2 = *reinterpret_cast<const float4*>(e2s + idx);
+                const float el = i0 > 0 ? e1s[idx - 1] : 0.f;
+                const float4 eb = below4(e2s, e2_dn);
+                const float a1[4] = {e1.x, e1.y, e1.z, e1.w}, a2[4] = {e2.x, e2.y, e2.z, e2.w};
+                const float bl[4] = {eb.x, eb.y, eb.z, eb.w};
+                const double ihd = 1.0 / P.h;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const double left = c ? (double)a1[c - 1] : (double)el;
+                    const double dd = (((double)a1[c] - left) + ((double)a2[c] - (double)bl[c])) * ihd;
+                    const double ep = (double)pn[c] - (double)pv[c];
+                    sb += ep * ep;
+                    sc += ep * dd;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) pv[c] = pn[c];
+            *reinterpret_cast<float4*>(ph + idx) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+        }
+        if (CL) {
+            cluster_arrive();
+            cluster_wait();
+        } else {
+            __syncthreads();
+        }
+        ++it;
+        if (check) {
+            double v[3] = {sa, sb, sc};
+            block_sum<3>(v, red);
+            if (t == 0) {
+                dsmem_st_f64(slots0 + 8u * (rank * 3 + 0), v[0]);
+                dsmem_st_f64(slots0 + 8u * (rank * 3 + 1), v[1]);
+                dsmem_st_f64(slots0 + 8u * (rank * 3 + 2), v[2]);
+            }
+            if (CL) cg::this_cluster().sync();
+            else __syncthreads();
+            if (rank == 0 && t == 0) {
+                double tt[3] = {0.0, 0.0, 0.0};
+                for (int r = 0; r < C; ++r)
+                    for (int c = 0; c < 3; ++c) tt[c] += slots[r * 3 + c];
+                const double Rk = (tt[0] / (double)mu + tt[1] / (double)tau - 2.0 * tt[2]) * P.h * P.h;
+                const int cv = Rk < P.tol;
+                const int lt = (globaltimer() - t0) > P.budget_ns;
+                const int stop = P.fixed || cv || lt || it >= cap;
+                slots[48] = Rk;
+                slots[49] = (double)(cv | (lt << 1) | (stop << 2));
+            }
+            if (CL) cg::this_cluster().sync();
+            else __syncthreads();
+            R = dsmem_ld_f64(slots0 + 8u * 48);
+            const int d = (int)dsmem_ld_f64(slots0 + 8u * 49);
+            conv = d & 1;
+            late = (d >> 1) & 1;
+            if (d & 4) break;
+        }
+    }
+    if (own) {
+        *reinterpret_cast<float4*>(a.m1 + off + idx) = make_float4(m1[0], m1[1], m1[2], m1[3]);
+        *reinterpret_cast<float4*>(a.m2 + off + idx) = make_float4(m2[0], m2[1], m2[2], m2[3]);
+        *reinterpret_cast<float4*>(a.phi + off + idx) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+    }
+    if (rank == 0 && t == 0) {
+        if (pc) {
+            pc->iters[P.level] = it;
+            pc->fpr[P.level] = R;
+            pc->conv[P.level] = conv;
+            if (late && !conv) pc->timeout = 1;
+        }
+        if (P.fpr_out) P.fpr_out[pair] = R;
+        if (P.iters_out) P.iters_out[pair] = it;
+    }
+    if (CL) cg::this_cluster().sync();
+}
+
 template <int NORM, int NPT, bool CL>
 static cudaError_t res_attr()
 {
@@ -806,11 +1280,27 @@ static cudaError_t res_attr_norm()
     return res_attr<NORM, 4, true>();
 }
 
+template <int NORM, bool CL>
+static cudaError_t res4_attr()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_resident4<NORM, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)resident_smem(RES_MAX_NODES));
+    if (e != cudaSuccess) return e;
+    if (CL) return cudaFuncSetAttribute(k_resident4<NORM, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return cudaSuccess;
+}
+
 cudaError_t resident_prepare(int)
 {
-    cudaError_t e = res_attr_norm<W1_NORM_L1>();
+    cudaError_t e = tblock_prepare();
     if (e != cudaSuccess) return e;
-    return res_attr_norm<W1_NORM_L2>();
+    e = res_attr_norm<W1_NORM_L1>();
+    if (e != cudaSuccess) return e;
+    if ((e = res_attr_norm<W1_NORM_L2>()) != cudaSuccess) return e;
+    if ((e = res4_attr<W1_NORM_L1, false>()) != cudaSuccess) return e;
+    if ((e = res4_attr<W1_NORM_L1, true>()) != cudaSuccess) return e;
+    if ((e = res4_attr<W1_NORM_L2, false>()) != cudaSuccess) return e;
+    return res4_attr<W1_NORM_L2, true>();
 }
 
 template <int NORM>
@@ -830,6 +1320,28 @@ static void resident_config(int norm, int cluster, int nx, int ny, int pairs, cu
                             cudaLaunchAttribute* attr, const void** fn)
 {
     const int band = (ny / cluster) * nx;
+    if (nx % 4 == 0 && band / 4 <= RES_THREADS) {
+        // four consecutive nodes of a row per thread
+        const int threads = ((band / 4 + 31) / 32) * 32;
+        cfg = cudaLaunchConfig_t{};
+        cfg.gridDim = dim3(cluster * pairs, 1, 1);
+        cfg.blockDim = dim3(threads, 1, 1);
+        cfg.dynamicSmemBytes = resident_smem(band);
+        cfg.numAttrs = 0;
+        if (cluster > 1) {
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = cluster;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+        }
+        if (norm == W1_NORM_L1)
+            *fn = cluster > 1 ? (const void*)k_resident4<W1_NORM_L1, true> : (const void*)k_resident4<W1_NORM_L1, false>;
+        else
+            *fn = cluster > 1 ? (const void*)k_resident4<W1_NORM_L2, true> : (const void*)k_resident4<W1_NORM_L2, false>;
+        return;
+    }
     // up to 1024 nodes: one per thread; up to 2048: two per thread; beyond:
     // 512 threads x 8 for a single CTA, 1024 x 4 in a cluster (fewer registers
     // next to the distributed-shared-memory addressing)

@@ -153,6 +153,9 @@ static size_t layout(w1_plan* p, char* base)
         if (p->lv[l].path == 2) {
             size_t s = step_part_doubles(p->lv[l].nx, p->lv[l].ny, p->lv[l].rows, B);
             if (s > pd) pd = s;
+        } else if (p->lv[l].path == 3) {
+            size_t s = tblock_part_doubles(p->lv[l].nx, p->lv[l].ny, B);
+            if (s > pd) pd = s;
         }
     p->part_doubles = pd;
     p->part = reinterpret_cast<double*>(take(pd * sizeof(double)));
@@ -162,7 +165,7 @@ static size_t layout(w1_plan* p, char* base)
         LevelPlan& v = p->lv[l];
         const size_t b = (size_t)v.nx * v.ny * sizeof(float) * B;
         v.rho = reinterpret_cast<float*>(take(b));
-        const int nb = v.path == 2 ? 2 : 1;
+        const int nb = v.path == 1 ? 1 : 2;
         for (int s = 0; s < 2; ++s) {
             v.m1[s] = s < nb ? reinterpret_cast<float*>(take(b)) : nullptr;
             v.m2[s] = s < nb ? reinterpret_cast<float*>(take(b)) : nullptr;
@@ -196,7 +199,9 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
     if (o.check_every < 2 || (o.check_every & 1)) return fail(W1_ERR_INVALID_ARG, "check_every must be even and >= 2");
     if (!(o.theta > 0.0) || o.theta > 1.0) return fail(W1_ERR_INVALID_ARG, "theta must lie in (0, 1]");
     if (o.max_iters < 1) return fail(W1_ERR_INVALID_ARG, "max_iters must be >= 1");
-    if (o.path < 0 || o.path > 2) return fail(W1_ERR_INVALID_ARG, "path must be 0, 1 or 2");
+    if (o.path < 0 || o.path > 3) return fail(W1_ERR_INVALID_ARG, "path must be 0, 1, 2 or 3");
+    if (o.check_every % (2 * tblock_depth()) != 0)
+        return fail(W1_ERR_INVALID_ARG, "check_every must be a multiple of twice the temporal block depth (8)");
     // stop tests happen every K steps, so the cap is a multiple of K
     o.max_iters = (o.max_iters + o.check_every - 1) / o.check_every * o.check_every;
     if (!(h > 0.0)) h = 1.0 / (double)(nx > ny ? nx : ny);
@@ -239,7 +244,13 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
         int c = resident_cluster_for(v.nx, v.ny);
         if (c > 0 && resident_cluster_ok(norm, c, v.nx, v.ny) <= 0) c = 0;
         if (o.path == 1 && c == 0) return fail(W1_ERR_UNSUPPORTED, "level too large for the resident path");
-        v.path = (o.path == 2 || c == 0) ? 2 : 1;
+        if (o.path == 3 && v.nx % 4 != 0) return fail(W1_ERR_UNSUPPORTED, "temporal blocking needs nx % 4 == 0");
+        if (o.path == 1 || (o.path == 0 && c > 0))
+            v.path = 1;
+        else if (o.path == 3 || (o.path == 0 && v.nx % 4 == 0))
+            v.path = 3;  // temporally blocked streaming
+        else
+            v.path = 2;  // one step per launch
         v.cluster = v.path == 1 ? c : 0;
         v.rows = o.rows_per_thread > 0 ? o.rows_per_thread : stream_rows_auto(v.nx, v.ny, max_batch);
     }
@@ -437,8 +448,10 @@ static w1_status build_graph(w1_plan* p)
             CAP_CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
             CAP_CK(cudaStreamBeginCaptureToGraph(p->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
             const int K = p->opt.check_every;
+            const int per = v.path == 3 ? tblock_depth() : 1;  // steps per launch
+            const int nl = K / per;                             // launches per body (even: K and per are)
             cudaError_t e = cudaSuccess;
-            for (int k = 0; k < K && e == cudaSuccess; ++k) {
+            for (int k = 0; k < nl && e == cudaSuccess; ++k) {
                 StepArgs a{};
                 const int src = k & 1, dst = src ^ 1;
                 a.m1 = v.m1[src];
@@ -453,7 +466,8 @@ static w1_status build_graph(w1_plan* p)
                 a.it = iter_args(p, l);
                 a.part = p->part;
                 a.use_cond = 1;
-                e = launch_step(p->norm, k == K - 1, a, p->body_stream);
+                e = v.path == 3 ? launch_tblock(p->norm, k == nl - 1, a, p->body_stream)
+                                : launch_step(p->norm, k == nl - 1, a, p->body_stream);
             }
             if (e == cudaSuccess) e = launch_decide(p->ctl, B, h, p->body_stream);
             if (e != cudaSuccess) {
@@ -693,18 +707,25 @@ extern "C" w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, f
         cudaError_t e = launch_resident(norm, c, a, s);
         if (e != cudaSuccess) ret = fail(W1_ERR_CUDA, std::string("resident launch: ") + cudaGetErrorString(e));
     } else {
+        if (path == 3 && (nx % 4 != 0 || iters % tblock_depth() != 0)) {
+            cudaFree(dfpr);
+            return fail(W1_ERR_UNSUPPORTED, "temporal blocking needs nx % 4 == 0 and iters % 4 == 0");
+        }
         const size_t n = (size_t)nx * ny;
         const int rows = stream_rows_auto(nx, ny, 1);
+        const long long launches = path == 3 ? iters / tblock_depth() : iters;
+        size_t pd = step_part_doubles(nx, ny, rows, 1);
+        if (tblock_part_doubles(nx, ny, 1) > pd) pd = tblock_part_doubles(nx, ny, 1);
         float* buf = nullptr;
         double* part = nullptr;
         Ctl* ctl = nullptr;
         cudaError_t e = cudaMalloc(&buf, 3 * n * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc(&part, step_part_doubles(nx, ny, rows, 1) * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&part, pd * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&ctl, sizeof(Ctl));
         if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
         float* A[3] = {m1, m2, phi};
         float* B[3] = {buf, buf + n, buf + 2 * n};
-        for (long long k = 0; k < iters && e == cudaSuccess; ++k) {
+        for (long long k = 0; k < launches && e == cudaSuccess; ++k) {
             float** src = (k & 1) ? B : A;
             float** dst = (k & 1) ? A : B;
             StepArgs a{};
@@ -721,9 +742,9 @@ extern "C" w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, f
             a.it.ctl = ctl;
             a.part = part;
             a.use_cond = 0;
-            e = launch_step(norm, k == iters - 1, a, s);
+            e = path == 3 ? launch_tblock(norm, k == launches - 1, a, s) : launch_step(norm, k == launches - 1, a, s);
         }
-        if (e == cudaSuccess && (iters & 1)) {
+        if (e == cudaSuccess && (launches & 1)) {
             for (int c = 0; c < 3 && e == cudaSuccess; ++c)
                 e = cudaMemcpyAsync(A[c], B[c], n * sizeof(float), cudaMemcpyDeviceToDevice, s);
         }

@@ -64,20 +64,26 @@ def flux_rel_l1(f, m1, m2):
 SHAPES = [(1, 37), (37, 1), (3, 5), (17, 33), (40, 33), (64, 64), (128, 96), (200, 300)]
 
 
+SHAPES4 = [(1, 64), (3, 8), (40, 36), (64, 64), (96, 128), (200, 300), (130, 72)]
+
+
 @pytest.mark.parametrize("norm", [L1, L2])
-@pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("shape", SHAPES + SHAPES4)
+@pytest.mark.parametrize("path", [1, 2, 3])
 def test_cp_steps_match_oracle(w1, norm, shape, path):
     """Steps of eq. primaldual from the same random state on odd shapes: 1xN and
-    Nx1 strips, ragged widths, several warps and several cluster bands."""
+    Nx1 strips, ragged widths, several warps and several cluster bands, tiles
+    with ragged edges (path 3: 4 steps per launch)."""
     ny, nx = shape
     if path == 1 and not resident_fits(nx, ny):
         pytest.skip("larger than the resident path")
+    if path == 3 and nx % 4:
+        pytest.skip("temporal blocking needs nx % 4 == 0")
     rng = np.random.default_rng(ny * 1000 + nx + norm)
     rho, m1, m2, phi = rand_state(rng, ny, nx)
     h = 1.0 / max(nx, ny)
     mu = mu_of(h)
-    for iters in (1, 7, 64):
+    for iters in ((4, 8, 64) if path == 3 else (1, 7, 64)):
         g = [dev(a) for a in (rho, m1, m2, phi)]
         fpr = w1.cp_steps(g[0], g[1], g[2], g[3], h, norm, mu, mu, iters, path=path)
         o1, o2, op, ofpr = oracle.cp_iterate(rho, m1, m2, phi, h, norm, iters, mu=mu, tau=mu)
@@ -94,12 +100,13 @@ def test_resident_and_streaming_paths_agree(w1, norm):
     rho, m1, m2, phi = rand_state(rng, 96, 128)
     h = 1 / 128
     out = []
-    for path in (1, 2):
+    for path in (1, 2, 3):
         g = [dev(a) for a in (rho, m1, m2, phi)]
         w1.cp_steps(*g, h, norm, mu_of(h), mu_of(h), 200, path=path)
         out.append([host(t) for t in g[1:]])
-    for a, b in zip(*out):
-        assert np.abs(a - b).max() <= 2e-5 * max(np.abs(b).max(), 1.0)
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert np.abs(a - b).max() <= 2e-5 * max(np.abs(b).max(), 1.0)
 
 
 @pytest.mark.parametrize("shape", [(2, 2), (6, 10), (64, 64), (256, 130), (512, 512)])
@@ -198,7 +205,7 @@ def test_solve_512_six_levels(w1, norm):
     assert_parity(val, st, flux, ref)
 
 
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("path", [1, 2, 3])
 def test_forced_paths_give_the_same_solution(w1, path):
     r0, r1 = synth.pair(0, 1)
     val, st, flux, _, ref = solve_and_replay(w1, r0, r1, L1, 3, tol=1e-6, path=path)
@@ -247,13 +254,17 @@ def test_shape_errors(w1):
         w1.Plan(64, 64, levels=3, norm=3)
     with pytest.raises(w1.W1Error, match="ERR_INVALID_ARG"):
         w1.Plan(64, 64, levels=3, check_every=7)
+    with pytest.raises(w1.W1Error, match="ERR_INVALID_ARG"):
+        w1.Plan(64, 64, levels=3, check_every=12)
+    with pytest.raises(w1.W1Error, match="ERR_UNSUPPORTED"):
+        w1.Plan(66, 64, levels=1, path=3)
 
 
 def test_iteration_cap_and_time_budget_end_a_level(w1):
     """The device loops are bounded: an iteration cap and a wall-clock budget end
     a level with a status instead of running on."""
     r0, r1 = synth.pair(0, 4)
-    for path in (1, 2):
+    for path in (1, 2, 3):
         with w1.Plan(64, 64, levels=3, norm=L1, tol=1e-12, max_iters=64, path=path) as plan:
             val, st, status = plan.solve(dev(r0), dev(r1), allow=(w1.ERR_NOT_CONVERGED,))
             assert status == w1.ERR_NOT_CONVERGED and val > 0 and not st.converged
