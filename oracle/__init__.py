@@ -27,6 +27,7 @@ _lib = None
 
 NORM_L1 = 1
 NORM_L2 = 2
+NORM_LINF = 3
 STOP_GAP = 0
 STOP_FPR = 1
 

@@ -31,6 +31,7 @@
 
 #define W1O_NORM_L1 1
 #define W1O_NORM_L2 2
+#define W1O_NORM_LINF 3
 
 #define W1O_STOP_GAP 0
 #define W1O_STOP_FPR 1
@@ -95,15 +96,42 @@ void w1o_grad(int nx, int ny, double h, const double* phi, double* g1, double* g
     }
 }
 
+/* Euclidean projection of (u1, u2) onto the unit l1 ball {|a| + |b| <= 1}:
+ * soft thresholding by the lambda >= 0 that makes the l1 norm exactly 1. */
+static void proj_l1_ball(double u1, double u2, double* p1, double* p2)
+{
+    double a = fabs(u1), b = fabs(u2);
+    if (a + b <= 1.0) {
+        *p1 = u1;
+        *p2 = u2;
+        return;
+    }
+    /* sum_i max(|u_i| - lambda, 0) = 1 */
+    double lambda;
+    if (a - b >= 1.0) lambda = a - 1.0;
+    else if (b - a >= 1.0) lambda = b - 1.0;
+    else lambda = 0.5 * (a + b - 1.0);
+    double r1 = a - lambda, r2 = b - lambda;
+    *p1 = r1 > 0.0 ? copysign(r1, u1) : 0.0;
+    *p2 = r2 > 0.0 ? copysign(r2, u2) : 0.0;
+}
+
 /* Proximal map of mu*||.||_p at one node, the closed form of the argmin in the
  * first line of eq. primaldual (p = 1: componentwise soft threshold; p = 2:
- * shrink the vector's length by mu). */
+ * shrink the vector's length by mu; p = infinity: by the Moreau decomposition
+ * named in Sec. 4, v - mu * Proj_{l1 ball}(v / mu), the l1 ball being the unit
+ * ball of the dual norm). */
 static void prox_node(int norm, double mu, double v1, double v2, double* o1, double* o2)
 {
     if (norm == W1O_NORM_L1) {
         double a1 = fabs(v1) - mu, a2 = fabs(v2) - mu;
         *o1 = a1 > 0.0 ? copysign(a1, v1) : 0.0;
         *o2 = a2 > 0.0 ? copysign(a2, v2) : 0.0;
+    } else if (norm == W1O_NORM_LINF) {
+        double p1, p2;
+        proj_l1_ball(v1 / mu, v2 / mu, &p1, &p2);
+        *o1 = v1 - mu * p1;
+        *o2 = v2 - mu * p2;
     } else {
         double len = sqrt(v1 * v1 + v2 * v2);
         double s = (len > mu) ? 1.0 - mu / len : 0.0;
@@ -120,13 +148,17 @@ void w1o_prox(int norm, double mu, int n, const double* v1, const double* v2, do
 /* ||m(x)||_p at one node */
 static double node_norm(int norm, double a, double b)
 {
-    return norm == W1O_NORM_L1 ? fabs(a) + fabs(b) : sqrt(a * a + b * b);
+    if (norm == W1O_NORM_L1) return fabs(a) + fabs(b);
+    if (norm == W1O_NORM_LINF) return fmax(fabs(a), fabs(b));
+    return sqrt(a * a + b * b);
 }
 
-/* ||g||_q at one node, q = infinity for p = 1 and q = 2 for p = 2 */
+/* ||g||_q at one node, 1/p + 1/q = 1: q = infinity for p = 1, 2 for 2, 1 for infinity */
 static double node_dual_norm(int norm, double a, double b)
 {
-    return norm == W1O_NORM_L1 ? fmax(fabs(a), fabs(b)) : sqrt(a * a + b * b);
+    if (norm == W1O_NORM_L1) return fmax(fabs(a), fabs(b));
+    if (norm == W1O_NORM_LINF) return fabs(a) + fabs(b);
+    return sqrt(a * a + b * b);
 }
 
 /* ------------------------------------------------------------------------- */

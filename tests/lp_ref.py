@@ -118,3 +118,37 @@ def w1_p2_bruteforce(rho: np.ndarray, h: float) -> float:
                             options={"xatol": 1e-12, "maxiter": 2000})
         return float(r.fun)
     raise ValueError("grid too large for the brute-force p=2 solver")
+
+
+def w1_lp_linf(rho: np.ndarray, h: float) -> float:
+    """Exact discrete p = infinity W1: min sum_x t_x h^2 with |m1(x)| <= t_x,
+    |m2(x)| <= t_x and div m = rho (boundary flux components absent), an LP."""
+    import scipy.sparse as sp
+    from scipy.optimize import linprog
+
+    ny, nx = rho.shape
+    edges = _edges(nx, ny)
+    E, N = len(edges), nx * ny
+    # variables: flux per edge (free), t per node (>= 0)
+    rows, cols, vals = [], [], []
+    for k, (a, b) in enumerate(edges):
+        rows += [a, b]
+        cols += [k, k]
+        vals += [1.0 / h, -1.0 / h]
+    Aeq = sp.csr_matrix((vals, (rows, cols)), shape=(N, E + N))
+    # |m_e| <= t_{tail node of e}: the edge (i,j)->(i+1,j) is m1 at (i,j), (i,j)->(i,j+1) is m2 at (i,j)
+    ur, uc, uv = [], [], []
+    r = 0
+    for k, (a, b) in enumerate(edges):
+        for sgn in (1.0, -1.0):
+            ur += [r, r]
+            uc += [k, E + a]
+            uv += [sgn, -1.0]
+            r += 1
+    Aub = sp.csr_matrix((uv, (ur, uc)), shape=(r, E + N))
+    cost = np.concatenate([np.zeros(E), np.full(N, h * h)])
+    bounds = [(None, None)] * E + [(0, None)] * N
+    res = linprog(cost, A_ub=Aub, b_ub=np.zeros(r), A_eq=Aeq, b_eq=rho.ravel(), bounds=bounds, method="highs",
+                  options={"primal_feasibility_tolerance": 1e-10, "dual_feasibility_tolerance": 1e-10})
+    assert res.status == 0, res.message
+    return float(res.fun)

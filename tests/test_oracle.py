@@ -11,7 +11,7 @@ import oracle
 import synth
 from tests import lp_ref
 
-L1, L2 = oracle.NORM_L1, oracle.NORM_L2
+L1, L2, LINF = oracle.NORM_L1, oracle.NORM_L2, oracle.NORM_LINF
 
 
 def rand_zero_mass(rng, ny, nx, h):
@@ -75,7 +75,7 @@ def test_div_of_constant_flux_is_boundary_only():
     assert np.all(d[:, 0] == 2.0 / h) and np.all(d[:, -1] == -2.0 / h)
 
 
-@pytest.mark.parametrize("norm", [L1, L2])
+@pytest.mark.parametrize("norm", [L1, L2, LINF])
 def test_prox_is_the_argmin(norm):
     """prox_{mu||.||_p}(v) minimises mu||m||_p + ||m - v||^2/2: no point of a
     fine grid around it does better, and the optimality conditions hold."""
@@ -87,7 +87,8 @@ def test_prox_is_the_argmin(norm):
         v = rng.normal(scale=0.6, size=2)
         o1, o2 = oracle.prox(norm, mu, v[:1], v[1:])
         o = np.array([o1[0], o2[0]])
-        nrm = (lambda m: np.abs(m).sum()) if norm == L1 else (lambda m: np.sqrt((m * m).sum()))
+        nrm = {L1: lambda m: np.abs(m).sum(), L2: lambda m: np.sqrt((m * m).sum()),
+               LINF: lambda m: np.abs(m).max()}[norm]
         obj = lambda m: mu * nrm(m) + 0.5 * ((m - v) ** 2).sum()  # noqa: E731
         best = minimize(obj, v, method="Nelder-Mead", options={"xatol": 1e-12, "fatol": 1e-15, "maxiter": 4000})
         assert obj(o) <= best.fun + 1e-12
@@ -136,6 +137,24 @@ def test_p1_matches_network_simplex_16x16():
     assert abs(res.w1 - exact) <= 1e-6 * exact
 
 
+@pytest.mark.parametrize("shape", [(2, 2), (3, 4), (8, 8), (10, 12)])
+def test_pinf_matches_exact_lp(shape):
+    """p = infinity: the discrete problem is an LP (max of the two components
+    bounded by a per-node variable); the oracle reaches it to relative 1e-6."""
+    ny, nx = shape
+    rng = np.random.default_rng(nx * 31 + ny)
+    h = 1.0 / max(nx, ny)
+    rho = rand_zero_mass(rng, ny, nx, h)
+    exact = lp_ref.w1_lp_linf(rho, h)
+    res = tight(rho, h, LINF, tol=1e-8)
+    assert abs(res.stats.f - exact) <= 1e-6 * exact
+    assert res.stats.lb <= exact * (1 + 1e-12) and res.stats.ub >= exact * (1 - 1e-12)
+    # the three norms order the distances: W1_inf <= W1_2 <= W1_1
+    w2 = tight(rho, h, L2, tol=1e-8).stats.f
+    w1 = lp_ref.w1_lp(rho, h)
+    assert exact <= w2 * (1 + 1e-6) and w2 <= w1 * (1 + 1e-6)
+
+
 @pytest.mark.parametrize("shape", [(2, 2), (2, 3), (3, 2)])
 def test_p2_matches_bruteforce(shape):
     ny, nx = shape
@@ -148,7 +167,7 @@ def test_p2_matches_bruteforce(shape):
         assert abs(res.stats.f - exact) <= 1e-6 * exact
 
 
-@pytest.mark.parametrize("norm", [L1, L2])
+@pytest.mark.parametrize("norm", [L1, L2, LINF])
 def test_certificates_bracket_exact_for_any_state(norm):
     """LB <= W1_h <= UB holds for every (m, phi), converged or not: pins the
     dual objective, its sign, the dual norm and the residual-routing flux."""
@@ -157,7 +176,10 @@ def test_certificates_bracket_exact_for_any_state(norm):
         ny, nx = shape
         h = 1.0 / max(nx, ny)
         rho = rand_zero_mass(rng, ny, nx, h)
-        exact = lp_ref.w1_lp(rho, h) if norm == L1 or shape[0] * shape[1] > 6 else lp_ref.w1_p2_bruteforce(rho, h)
+        if norm == LINF:
+            exact = lp_ref.w1_lp_linf(rho, h)
+        else:
+            exact = lp_ref.w1_lp(rho, h) if norm == L1 or shape[0] * shape[1] > 6 else lp_ref.w1_p2_bruteforce(rho, h)
         if norm == L2 and shape[0] * shape[1] > 6:
             # p = 2 W1 lies between (1/sqrt 2) * (p = 1 W1) and the p = 1 W1
             lo_ex, hi_ex = exact / np.sqrt(2.0), exact
@@ -189,7 +211,7 @@ def test_route_bound_exact_cases():
 # Closed forms
 # --------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("norm", [L1, L2])
+@pytest.mark.parametrize("norm", [L1, L2, LINF])
 @pytest.mark.parametrize("n,horizontal", [(16, True), (32, False)])
 def test_strip_closed_form(norm, n, horizontal):
     """1 x N strip: the 1-D W1 is sum |C_i| h with C_i the cumulative mass
@@ -237,7 +259,7 @@ def test_translated_bump(norm, shift):
 # Invariants of Algorithm 1
 # --------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("norm", [L1, L2])
+@pytest.mark.parametrize("norm", [L1, L2, LINF])
 def test_fpr_nonnegative_and_nonincreasing(norm):
     """R^k of eq. pd_stop is ||z^{k+1} - z^k||^2 in the metric M_h (Sec. 4), so
     it is >= 0 and, for mu tau ||A||^2 < 1, non-increasing in k."""
