@@ -52,6 +52,22 @@ def dist_env():
     return rank, world, local
 
 
+def pair_ids(rank: int, step: int, batch: int):
+    """Seeds of the pairs a rank solves in a step: disjoint across ranks and
+    steps (replicas: each GPU works on its own pairs, nothing is exchanged)."""
+    return [rank * 100000 + step * batch + k for k in range(batch)]
+
+
+def reduce_max(dist, x: float, device) -> float:
+    """Max of a per-rank scalar over all ranks (the job's wall time)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -206,7 +222,7 @@ def run_gpu(args):
     # distinct pairs per step and rank, resident in HBM before timing
     host_pairs, dev_pairs = [], []
     for s in range(total_steps):
-        r = [synth.pair(WORKLOAD, rank * 100000 + s * B + k) for k in range(B)]
+        r = [synth.pair(WORKLOAD, k) for k in pair_ids(rank, s, B)]
         a0 = np.ascontiguousarray(np.stack([x[0] for x in r]), dtype=np.float32)
         a1 = np.ascontiguousarray(np.stack([x[1] for x in r]), dtype=np.float32)
         host_pairs.append((torch.from_numpy(a0).pin_memory(), torch.from_numpy(a1).pin_memory()))
@@ -215,12 +231,13 @@ def run_gpu(args):
     ok = (w1.OK, w1.ERR_NOT_CONVERGED)
     if args.mode == "lockstep":
         # one batched plan per norm: every launch advances all B pairs together
-        plans = {norm: w1.Plan(N, N, levels=LEVELS, norm=norm, batch=B) for norm in NORMS}
+        plans = {norm: w1.Plan(N, N, levels=LEVELS, norm=norm, batch=B, eager=int(args.eager)) for norm in NORMS}
     else:
         # lanes: one plan and one stream per pair, all enqueued asynchronously, so
         # every pair moves through its levels at its own pace and the kernels of
         # different pairs overlap on the device
-        plans = {norm: [w1.Plan(N, N, levels=LEVELS, norm=norm) for _ in range(B)] for norm in NORMS}
+        plans = {norm: [w1.Plan(N, N, levels=LEVELS, norm=norm, eager=int(args.eager)) for _ in range(B)]
+                 for norm in NORMS}
         lanes = {norm: [torch.cuda.Stream() for _ in range(B)] for norm in NORMS}
         done_ev = {norm: [torch.cuda.Event(enable_timing=True) for _ in range(B)] for norm in NORMS}
     pair_ms = []
@@ -259,24 +276,21 @@ def run_gpu(args):
             out.append((vals, sts))
         return out
 
+    def level_launches(p, k):
+        # resident: one launch; streaming: one per step (path 2) or per 4 steps
+        # (path 3, temporal blocking), plus one decide kernel per 32 steps
+        if p == 1:
+            return 1
+        return (k if p == 2 else k // 4) + k // 32
+
     def launches(sts):
-        # prep 2, restrictions, level starts, prolongations, final 2; one launch per
-        # resident level; per streaming level the steps plus one decide kernel per
-        # K steps (for a batched plan: those of the slowest pair)
+        # prep 2, restrictions, level starts, prolongations, final 2, and the levels
+        # (for a batched plan: those of the slowest pair)
         st = sts[0]
         per = 2 + (st.levels - 1) + st.levels + (st.levels - 1) + 2
         if args.mode == "lockstep":
-            n = per
-            for lvl, p in enumerate(st.path):
-                k = max(x.iters[lvl] for x in sts)
-                n += 1 if p == 1 else k + k // 32
-            return n
-        n = 0
-        for x in sts:
-            n += per
-            for lvl, p in enumerate(x.path):
-                n += 1 if p == 1 else x.iters[lvl] + x.iters[lvl] // 32
-        return n
+            return per + sum(level_launches(p, max(x.iters[lvl] for x in sts)) for lvl, p in enumerate(st.path))
+        return sum(per + sum(level_launches(p, x.iters[lvl]) for lvl, p in enumerate(x.path)) for x in sts)
 
     def barrier():
         if dist is not None:
@@ -284,11 +298,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(dist, x, "cuda")
 
     for s in range(args.warmup):
         do_step(s)
@@ -369,32 +379,41 @@ def run_gpu(args):
 
 
 def roofline_stream(w1, torch, stream, args):
+    """HBM roofline of the streaming level kernels on an n x n grid far above L2:
+    algorithmic bytes = 28 B per node and step (read m1, m2, phi, rho; write
+    m1, m2, phi), timed with CUDA events on the launching stream.  Path 3 (the
+    default for streaming levels) moves fewer DRAM bytes than that (4 steps per
+    launch on chip); its figure is effective bandwidth, labelled as such."""
     n = args.roof_n
     h = 1.0 / n
-    rng = np.random.default_rng(7)
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
     rho = torch.randn((n, n), device="cuda") * 0.1
     rho -= rho.mean()
-    m1 = torch.zeros((n, n), device="cuda")
-    m2 = torch.zeros((n, n), device="cuda")
-    phi = torch.zeros((n, n), device="cuda")
-    del rng, dev
-    mu = float(np.float32(0.5 * h / (2 * np.sqrt(2.0))))
-    w1.cp_steps(rho, m1, m2, phi, h, 1, mu, mu, 4, path=2, stream=stream)
-    iters = args.roof_iters
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    w1.cp_steps(rho, m1, m2, phi, h, 1, mu, mu, iters, path=2, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / iters
     peak, kind = peaks()
-    achieved = 28.0 * n * n / (ms * 1e-3) / 1e9
-    return {"kernel": "k_step (streaming, T=1)", "grid": [n, n], "bound": "hbm", "achieved": achieved,
-            "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "ms_per_launch": ms, "algorithmic_bytes_per_launch": 28 * n * n}
+    mu = float(np.float32(0.5 * h / (2 * np.sqrt(2.0))))
+    out = {}
+    for path, name in ((3, "k_tblock (temporal blocking, 4 steps per launch)"), (2, "k_step (one step per launch)")):
+        m1, m2, phi = (torch.zeros((n, n), device="cuda") for _ in range(3))
+        w1.cp_steps(rho, m1, m2, phi, h, 1, mu, mu, 8, path=path, stream=stream)
+        iters = args.roof_iters
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        w1.cp_steps(rho, m1, m2, phi, h, 1, mu, mu, iters, path=path, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_step = e0.elapsed_time(e1) / iters
+        per_launch = 4 if path == 3 else 1
+        achieved = 28.0 * n * n / (ms_step * 1e-3) / 1e9
+        out[path] = {"kernel": name, "grid": [n, n], "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "ms_per_launch": ms_step * per_launch, "steps_per_launch": per_launch,
+                     "algorithmic_bytes_per_launch": 28 * n * n * per_launch}
+        del m1, m2, phi
+    out[3]["note"] = "effective bandwidth: 28 B per node-step; DRAM moves about (16 x 1.41 + 12) / 4 B"
+    r = dict(out[3])
+    r["one_step_per_launch"] = out[2]
+    return r
 
 
 def main():
@@ -409,14 +428,17 @@ def main():
     ap.add_argument("--no-roofline", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--roof-n", type=int, default=8192)
-    ap.add_argument("--roof-iters", type=int, default=100)
+    ap.add_argument("--roof-iters", type=int, default=96)
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch level kernels directly (no CUDA graph) so profilers see every kernel")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000", help="serving: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=400, help="serving: requests per rate (at least)")
     ap.add_argument("--min-seconds", type=float, default=0.0, help="serving: at least rate*this requests")
     ap.add_argument("--slots", type=int, default=48, help="serving: solves in flight")
-    ap.add_argument("--only", default="solve", choices=["solve", "stream-kernel", "resident-kernel", "serve"],
+    ap.add_argument("--only", default="solve",
+                    choices=["solve", "stream-kernel", "tblock-kernel", "resident-kernel", "serve"],
                     help="kernel-only runs for profiling: one level's steps through w1_cp_steps")
     ap.add_argument("--kn", type=int, default=256, help="grid side for --only *-kernel")
     ap.add_argument("--kiters", type=int, default=1000, help="steps for --only *-kernel")
@@ -520,9 +542,9 @@ def run_kernel_only(args):
     m1, m2, phi = (torch.zeros((n, n), device="cuda") for _ in range(3))
     h = 1.0 / n
     mu = float(np.float32(0.5 * h / (2 * np.sqrt(2.0))))
-    path = 1 if args.only == "resident-kernel" else 2
+    path = {"resident-kernel": 1, "stream-kernel": 2, "tblock-kernel": 3}[args.only]
     stream = torch.cuda.current_stream()
-    w1.cp_steps(rho, m1, m2, phi, h, args.knorm, mu, mu, 2, path=path, stream=stream)
+    w1.cp_steps(rho, m1, m2, phi, h, args.knorm, mu, mu, 4, path=path, stream=stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)

@@ -45,8 +45,10 @@ extern "C" {
 #define W1_MAX_LEVELS 16
 
 typedef enum {
-    W1_NORM_L1 = 1, /* p = 1, anisotropic: ||m(x)|| = |m1| + |m2|, componentwise shrink */
-    W1_NORM_L2 = 2  /* p = 2, isotropic:  ||m(x)|| = sqrt(m1^2 + m2^2), vector shrink  */
+    W1_NORM_L1 = 1,  /* p = 1, anisotropic: ||m(x)|| = |m1| + |m2|, componentwise shrink */
+    W1_NORM_L2 = 2,  /* p = 2, isotropic:  ||m(x)|| = sqrt(m1^2 + m2^2), vector shrink  */
+    W1_NORM_LINF = 3 /* p = infinity: ||m(x)|| = max(|m1|, |m2|); shrink by the Moreau
+                        decomposition v - mu Proj_{l1 ball}(v / mu) (Sec. 4)          */
 } w1_norm;
 
 typedef enum {
@@ -76,6 +78,10 @@ typedef struct {
                               needs nx % 4 == 0); automatic = 1 where a level fits on chip,
                               else 3 where possible, else 2                                 */
     int rows_per_thread;   /* streaming kernel: rows marched per thread (0 = automatic)       */
+    int eager;             /* 1: launch the level kernels directly and test convergence of
+                              streaming levels on the host (for profilers that do not follow
+                              conditional graph nodes); 0: one CUDA graph (default)           */
+    int reserved;          /* must be 0 */
 } w1_options;
 
 /* What a solve reports.  Values are FP64 sums of the FP32 state. */
@@ -95,7 +101,7 @@ typedef struct {
     double route;    /* cost of an explicit flux carrying the residual rho - div m */
     double res_l1;   /* sum |rho - div m| h^2 */
     double rho_l1;   /* sum |rho| h^2 */
-    double gmax;     /* max over nodes of ||grad phi(x)||_q (q dual to p) */
+    double gmax;     /* max over nodes of ||grad phi(x)||_q (q dual to p: inf, 2, 1) */
     double mass0;    /* sum rho0 h^2 */
     double mass1;    /* sum rho1 h^2 */
     double mass_shift; /* mean of rho0 - rho1 removed so that the constraint is solvable */
@@ -112,7 +118,7 @@ void w1_default_options(w1_options* opt);
  *   h      : finest spacing; <= 0 means 1 / max(nx, ny).
  *   levels : L; <= 0 means the paper's L = log2(1/h) - 3 (Sec. 5.3), reduced
  *            until nx and ny are divisible by 2^(L-1) and the coarsest side >= 2.
- *   norm   : W1_NORM_L1 or W1_NORM_L2.
+ *   norm   : W1_NORM_L1, W1_NORM_L2 or W1_NORM_LINF.
  *   tol    : eps_L of the finest level; <= 0 means eq. stop_tol for Alg. 3,
  *            eps_L = 1e-6/128 * (512 h)^2.
  * The plan owns its device workspace (allocated on the current device) unless

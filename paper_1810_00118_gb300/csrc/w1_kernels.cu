@@ -51,6 +51,24 @@ __device__ __forceinline__ void prox(float v1, float v2, float mu, float& o1, fl
     if (NORM == W1_NORM_L1) {
         o1 = soft(v1, mu);
         o2 = soft(v2, mu);
+    } else if (NORM == W1_NORM_LINF) {
+        // v - mu * Proj_{l1 ball}(v / mu) (Moreau): zero inside the ball; else the
+        // larger component loses mu, or both magnitudes meet at (|v1| + |v2| - mu) / 2
+        const float a = fabsf(v1), b = fabsf(v2);
+        if (a + b <= mu) {
+            o1 = 0.f;
+            o2 = 0.f;
+        } else if (a - b >= mu) {
+            o1 = copysignf(a - mu, v1);
+            o2 = v2;
+        } else if (b - a >= mu) {
+            o1 = v1;
+            o2 = copysignf(b - mu, v2);
+        } else {
+            const float c = 0.5f * (a + b - mu);
+            o1 = copysignf(c, v1);
+            o2 = copysignf(c, v2);
+        }
     } else {
         float len = sqrtf(v1 * v1 + v2 * v2);
         float s = (len > mu) ? 1.f - mu / len : 0.f;
@@ -505,9 +523,12 @@ cudaError_t launch_step(int norm, bool check, const StepArgs& a, cudaStream_t s)
     if (norm == W1_NORM_L1) {
         if (check) k_step<W1_NORM_L1, true><<<g, STEP_THREADS, 0, s>>>(a);
         else k_step<W1_NORM_L1, false><<<g, STEP_THREADS, 0, s>>>(a);
-    } else {
+    } else if (norm == W1_NORM_L2) {
         if (check) k_step<W1_NORM_L2, true><<<g, STEP_THREADS, 0, s>>>(a);
         else k_step<W1_NORM_L2, false><<<g, STEP_THREADS, 0, s>>>(a);
+    } else {
+        if (check) k_step<W1_NORM_LINF, true><<<g, STEP_THREADS, 0, s>>>(a);
+        else k_step<W1_NORM_LINF, false><<<g, STEP_THREADS, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
@@ -736,7 +757,10 @@ cudaError_t tblock_prepare()
     if ((e = cudaFuncSetAttribute(k_tblock<W1_NORM_L1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)TB_SMEM_CHECK)) != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(k_tblock<W1_NORM_L2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(k_tblock<W1_NORM_L2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)TB_SMEM_CHECK)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_tblock<W1_NORM_LINF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)TB_SMEM_CHECK);
 }
 
@@ -746,9 +770,12 @@ cudaError_t launch_tblock(int norm, bool check, const StepArgs& a, cudaStream_t 
     if (norm == W1_NORM_L1) {
         if (check) k_tblock<W1_NORM_L1, true><<<g, TB_THREADS, TB_SMEM_CHECK, s>>>(a);
         else k_tblock<W1_NORM_L1, false><<<g, TB_THREADS, TB_SMEM_PLAIN, s>>>(a);
-    } else {
+    } else if (norm == W1_NORM_L2) {
         if (check) k_tblock<W1_NORM_L2, true><<<g, TB_THREADS, TB_SMEM_CHECK, s>>>(a);
         else k_tblock<W1_NORM_L2, false><<<g, TB_THREADS, TB_SMEM_PLAIN, s>>>(a);
+    } else {
+        if (check) k_tblock<W1_NORM_LINF, true><<<g, TB_THREADS, TB_SMEM_CHECK, s>>>(a);
+        else k_tblock<W1_NORM_LINF, false><<<g, TB_THREADS, TB_SMEM_PLAIN, s>>>(a);
     }
     return cudaGetLastError();
 }
@@ -791,6 +818,8 @@ static constexpr int RES_MAX_NODES = 4096;  // nodes per CTA (512 threads x 8)
 static constexpr int RES_THREADS = 1024;
 static constexpr int RES_RED_BYTES = 1024;  // 32 warps x 3 doubles
 static constexpr int RES_SLOT_BYTES = 512;  // 16 CTAs x 3 doubles + decision
+static constexpr int RESW_RUNS = 4;         // wide bands: runs of four nodes per thread
+static constexpr int RESW_MAX_NODES = RES_THREADS * 4 * RESW_RUNS;  // 16384
 
 int resident_max_nodes() { return RES_MAX_NODES; }
 
@@ -803,6 +832,8 @@ int resident_cluster_for(int nx, int ny)
         long long band = (long long)(ny / c) * nx;
         if (band <= RES_MAX_NODES) return c;
     }
+    // wide bands (four runs of four nodes per thread) need 16 CTAs and nx % 4 == 0
+    if (nx % 4 == 0 && ny % 16 == 0 && (long long)(ny / 16) * nx <= RESW_MAX_NODES) return 16;
     return 0;
 }
 
@@ -1258,6 +1289,194 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
     if (CL) cg::this_cluster().sync();
 }
 
+// Wide-band variant for levels of up to 16 x 16384 nodes (512 x 512 in one
+// 16-CTA cluster): a thread owns four runs of four nodes.  Shared memory holds
+// only phi, m1 and m2 of the band (12 B per node, 192 KB at 16384 nodes), own
+// values are re-read from it, and rho and D = div m^k stay in registers.  The
+// test step's cross term <dphi, div dm> uses div dm = div m' - div m^k, both
+// already formed in FP32 (no shared-memory copy of dm is needed).
+
+static size_t resident_wide_smem(int band)
+{
+    return RES_RED_BYTES + RES_SLOT_BYTES + (size_t)band * 3 * sizeof(float);
+}
+
+template <int NORM>
+__global__ void __launch_bounds__(RES_THREADS, 1) k_resident_wide(ResArgs a)
+{
+    const IterArgs& P = a.it;
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int pair = blockIdx.x / C;
+    Ctl* pc = P.ctl ? P.ctl + pair : nullptr;
+    if (pc && pc->error) return;  // uniform over the cluster (one pair)
+    const int nx = P.nx, ny = P.ny;
+    const int rows = ny / C, jb = rank * rows, nb = rows * nx;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* red = reinterpret_cast<double*>(smraw);
+    double* slots = reinterpret_cast<double*>(smraw + RES_RED_BYTES);
+    float* ph = reinterpret_cast<float*>(smraw + RES_RED_BYTES + RES_SLOT_BYTES);
+    float* s1 = ph + nb;
+    float* s2 = s1 + nb;
+    const size_t off = (size_t)pair * P.stride + (size_t)jb * nx;
+    const float mu = P.mu, tau = P.tau, ih = P.ih;
+    const int t = threadIdx.x, T = blockDim.x;
+    int idx[RESW_RUNS];
+    float rv[RESW_RUNS][4], Dv[RESW_RUNS][4];
+#pragma unroll
+    for (int r = 0; r < RESW_RUNS; ++r) {
+        const int q = t + r * T;  // run index
+        idx[r] = q * 4 < nb ? q * 4 : -1;
+        if (idx[r] >= 0) {
+            const float4 x1 = *reinterpret_cast<const float4*>(a.m1 + off + idx[r]);
+            const float4 x2 = *reinterpret_cast<const float4*>(a.m2 + off + idx[r]);
+            const float4 xp = *reinterpret_cast<const float4*>(a.phi + off + idx[r]);
+            const float4 xr = *reinterpret_cast<const float4*>(a.rho + off + idx[r]);
+            *reinterpret_cast<float4*>(ph + idx[r]) = xp;
+            *reinterpret_cast<float4*>(s1 + idx[r]) = x1;
+            *reinterpret_cast<float4*>(s2 + idx[r]) = x2;
+            rv[r][0] = xr.x; rv[r][1] = xr.y; rv[r][2] = xr.z; rv[r][3] = xr.w;
+        }
+    }
+    cl.sync();
+    const int last_row = (rows - 1) * nx;
+    const uint32_t ph_up = (rank + 1 < C) ? dsmem_map(smem_u32(ph), rank + 1) : 0u;
+    const uint32_t s2_dn = (rank > 0) ? dsmem_map(smem_u32(s2 + last_row), rank - 1) : 0u;
+    const uint32_t slots0 = dsmem_map(smem_u32(slots), 0);
+    // div of the m currently in s1, s2 at run r
+    auto divergence = [&](int r, float out[4]) {
+        const int id = idx[r], jl = id / nx, i0 = id - jl * nx;
+        const float4 m1 = *reinterpret_cast<const float4*>(s1 + id);
+        const float4 m2 = *reinterpret_cast<const float4*>(s2 + id);
+        const float l = i0 > 0 ? s1[id - 1] : 0.f;
+        float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (jl > 0) b = *reinterpret_cast<const float4*>(s2 + id - nx);
+        else if (rank > 0) b = dsmem_ld4(s2_dn + 4u * i0);
+        out[0] = ((m1.x - l) + (m2.x - b.x)) * ih;
+        out[1] = ((m1.y - m1.x) + (m2.y - b.y)) * ih;
+        out[2] = ((m1.z - m1.y) + (m2.z - b.z)) * ih;
+        out[3] = ((m1.w - m1.z) + (m2.w - b.w)) * ih;
+    };
+#pragma unroll
+    for (int r = 0; r < RESW_RUNS; ++r)
+        if (idx[r] >= 0) divergence(r, Dv[r]);
+    cl.sync();
+
+    unsigned long long t0 = 0;
+    if (rank == 0 && t == 0) t0 = globaltimer();
+    long long it = 0;
+    double R = 0.0;
+    int conv = 0, late = 0;
+    const long long cap = P.cap;
+    while (it < cap) {
+        const bool check = P.fixed ? (it + 1 == cap) : ((it + 1) % P.K == 0);
+        double sa = 0.0, sb = 0.0, sc = 0.0;
+        // ---- phase A: m' = prox(m + mu grad phi)
+#pragma unroll
+        for (int r = 0; r < RESW_RUNS; ++r) {
+            if (idx[r] < 0) continue;
+            const int id = idx[r], jl = id / nx, i0 = id - jl * nx, j = jb + jl;
+            const bool last_col = i0 + 4 == nx;
+            const float4 p4 = *reinterpret_cast<const float4*>(ph + id);
+            const float4 a1 = *reinterpret_cast<const float4*>(s1 + id);
+            const float4 a2 = *reinterpret_cast<const float4*>(s2 + id);
+            float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j < ny - 1) u = (jl < rows - 1) ? *reinterpret_cast<const float4*>(ph + id + nx) : dsmem_ld4(ph_up + 4u * i0);
+            const float right = last_col ? 0.f : ph[id + 4];
+            const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, up[4] = {u.x, u.y, u.z, u.w};
+            const float m1[4] = {a1.x, a1.y, a1.z, a1.w}, m2[4] = {a2.x, a2.y, a2.z, a2.w};
+            float n1[4], n2[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float pr_ = c < 3 ? pv[c + 1] : right;
+                const float g1 = (c == 3 && last_col) ? 0.f : (pr_ - pv[c]) * ih;
+                const float g2 = (j < ny - 1) ? (up[c] - pv[c]) * ih : 0.f;
+                prox<NORM>(m1[c] + mu * g1, m2[c] + mu * g2, mu, n1[c], n2[c]);
+                if (c == 3 && last_col) n1[c] = 0.f;
+                if (j == ny - 1) n2[c] = 0.f;
+                if (check) {
+                    const double d1 = (double)n1[c] - m1[c], d2 = (double)n2[c] - m2[c];
+                    sa += d1 * d1 + d2 * d2;
+                }
+            }
+            *reinterpret_cast<float4*>(s1 + id) = make_float4(n1[0], n1[1], n1[2], n1[3]);
+            *reinterpret_cast<float4*>(s2 + id) = make_float4(n2[0], n2[1], n2[2], n2[3]);
+        }
+        cluster_arrive();
+        cluster_wait();
+        // ---- phase B: phi' = phi + tau (div(2m' - m) - rho)
+#pragma unroll
+        for (int r = 0; r < RESW_RUNS; ++r) {
+            if (idx[r] < 0) continue;
+            const int id = idx[r];
+            float Dn[4];
+            divergence(r, Dn);
+            const float4 p4 = *reinterpret_cast<const float4*>(ph + id);
+            const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+            float pn[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                pn[c] = pv[c] + tau * ((2.f * Dn[c] - Dv[r][c]) - rv[r][c]);
+                if (check) {
+                    const double ep = (double)pn[c] - (double)pv[c];
+                    sb += ep * ep;
+                    sc += ep * ((double)Dn[c] - (double)Dv[r][c]);
+                }
+                Dv[r][c] = Dn[c];
+            }
+            *reinterpret_cast<float4*>(ph + id) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+        }
+        cluster_arrive();
+        cluster_wait();
+        ++it;
+        if (check) {
+            double v[3] = {sa, sb, sc};
+            block_sum<3>(v, red);
+            if (t == 0) {
+                dsmem_st_f64(slots0 + 8u * (rank * 3 + 0), v[0]);
+                dsmem_st_f64(slots0 + 8u * (rank * 3 + 1), v[1]);
+                dsmem_st_f64(slots0 + 8u * (rank * 3 + 2), v[2]);
+            }
+            cl.sync();
+            if (rank == 0 && t == 0) {
+                double tt[3] = {0.0, 0.0, 0.0};
+                for (int q = 0; q < C; ++q)
+                    for (int c = 0; c < 3; ++c) tt[c] += slots[q * 3 + c];
+                const double Rk = (tt[0] / (double)mu + tt[1] / (double)tau - 2.0 * tt[2]) * P.h * P.h;
+                const int cv = Rk < P.tol;
+                const int lt = (globaltimer() - t0) > P.budget_ns;
+                const int stop = P.fixed || cv || lt || it >= cap;
+                slots[48] = Rk;
+                slots[49] = (double)(cv | (lt << 1) | (stop << 2));
+            }
+            cl.sync();
+            R = dsmem_ld_f64(slots0 + 8u * 48);
+            const int d = (int)dsmem_ld_f64(slots0 + 8u * 49);
+            conv = d & 1;
+            late = (d >> 1) & 1;
+            if (d & 4) break;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RESW_RUNS; ++r) {
+        if (idx[r] < 0) continue;
+        *reinterpret_cast<float4*>(a.m1 + off + idx[r]) = *reinterpret_cast<const float4*>(s1 + idx[r]);
+        *reinterpret_cast<float4*>(a.m2 + off + idx[r]) = *reinterpret_cast<const float4*>(s2 + idx[r]);
+        *reinterpret_cast<float4*>(a.phi + off + idx[r]) = *reinterpret_cast<const float4*>(ph + idx[r]);
+    }
+    if (rank == 0 && t == 0) {
+        if (pc) {
+            pc->iters[P.level] = it;
+            pc->fpr[P.level] = R;
+            pc->conv[P.level] = conv;
+            if (late && !conv) pc->timeout = 1;
+        }
+        if (P.fpr_out) P.fpr_out[pair] = R;
+        if (P.iters_out) P.iters_out[pair] = it;
+    }
+    cl.sync();
+}
+
 template <int NORM, int NPT, bool CL>
 static cudaError_t res_attr()
 {
@@ -1290,6 +1509,15 @@ static cudaError_t res4_attr()
     return cudaSuccess;
 }
 
+template <int NORM>
+static cudaError_t resw_attr()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_resident_wide<NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)resident_wide_smem(RESW_MAX_NODES));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_resident_wide<NORM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
 cudaError_t resident_prepare(int)
 {
     cudaError_t e = tblock_prepare();
@@ -1297,10 +1525,16 @@ cudaError_t resident_prepare(int)
     e = res_attr_norm<W1_NORM_L1>();
     if (e != cudaSuccess) return e;
     if ((e = res_attr_norm<W1_NORM_L2>()) != cudaSuccess) return e;
+    if ((e = res_attr_norm<W1_NORM_LINF>()) != cudaSuccess) return e;
     if ((e = res4_attr<W1_NORM_L1, false>()) != cudaSuccess) return e;
     if ((e = res4_attr<W1_NORM_L1, true>()) != cudaSuccess) return e;
     if ((e = res4_attr<W1_NORM_L2, false>()) != cudaSuccess) return e;
-    return res4_attr<W1_NORM_L2, true>();
+    if ((e = res4_attr<W1_NORM_L2, true>()) != cudaSuccess) return e;
+    if ((e = res4_attr<W1_NORM_LINF, false>()) != cudaSuccess) return e;
+    if ((e = res4_attr<W1_NORM_LINF, true>()) != cudaSuccess) return e;
+    if ((e = resw_attr<W1_NORM_L1>()) != cudaSuccess) return e;
+    if ((e = resw_attr<W1_NORM_L2>()) != cudaSuccess) return e;
+    return resw_attr<W1_NORM_LINF>();
 }
 
 template <int NORM>
@@ -1320,6 +1554,23 @@ static void resident_config(int norm, int cluster, int nx, int ny, int pairs, cu
                             cudaLaunchAttribute* attr, const void** fn)
 {
     const int band = (ny / cluster) * nx;
+    if (band > RES_MAX_NODES) {
+        // wide band: one 16-CTA cluster, four runs of four nodes per thread
+        cfg = cudaLaunchConfig_t{};
+        cfg.gridDim = dim3(cluster * pairs, 1, 1);
+        cfg.blockDim = dim3(RES_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = resident_wide_smem(band);
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        *fn = norm == W1_NORM_L1   ? (const void*)k_resident_wide<W1_NORM_L1>
+              : norm == W1_NORM_L2 ? (const void*)k_resident_wide<W1_NORM_L2>
+                                   : (const void*)k_resident_wide<W1_NORM_LINF>;
+        return;
+    }
     if (nx % 4 == 0 && band / 4 <= RES_THREADS) {
         // four consecutive nodes of a row per thread
         const int threads = ((band / 4 + 31) / 32) * 32;
@@ -1338,8 +1589,11 @@ static void resident_config(int norm, int cluster, int nx, int ny, int pairs, cu
         }
         if (norm == W1_NORM_L1)
             *fn = cluster > 1 ? (const void*)k_resident4<W1_NORM_L1, true> : (const void*)k_resident4<W1_NORM_L1, false>;
-        else
+        else if (norm == W1_NORM_L2)
             *fn = cluster > 1 ? (const void*)k_resident4<W1_NORM_L2, true> : (const void*)k_resident4<W1_NORM_L2, false>;
+        else
+            *fn = cluster > 1 ? (const void*)k_resident4<W1_NORM_LINF, true>
+                              : (const void*)k_resident4<W1_NORM_LINF, false>;
         return;
     }
     // up to 1024 nodes: one per thread; up to 2048: two per thread; beyond:
@@ -1372,7 +1626,9 @@ static void resident_config(int norm, int cluster, int nx, int ny, int pairs, cu
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    *fn = norm == W1_NORM_L1 ? res_fn<W1_NORM_L1>(npt, cluster > 1) : res_fn<W1_NORM_L2>(npt, cluster > 1);
+    *fn = norm == W1_NORM_L1   ? res_fn<W1_NORM_L1>(npt, cluster > 1)
+          : norm == W1_NORM_L2 ? res_fn<W1_NORM_L2>(npt, cluster > 1)
+                               : res_fn<W1_NORM_LINF>(npt, cluster > 1);
 }
 
 int resident_cluster_ok(int norm, int cluster, int nx, int ny)
@@ -1436,7 +1692,8 @@ __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict
         const int j = (int)(k / nx), i = (int)(k - (long long)j * nx);
         const double a1 = (i < nx - 1) ? (double)m1[k] : 0.0;
         const double a2 = (j < ny - 1) ? (double)m2[k] : 0.0;
-        v[0] += (NORM == W1_NORM_L1 ? fabs(a1) + fabs(a2) : sqrt(a1 * a1 + a2 * a2)) * h2;
+        v[0] += (NORM == W1_NORM_L1 ? fabs(a1) + fabs(a2)
+                                    : (NORM == W1_NORM_LINF ? fmax(fabs(a1), fabs(a2)) : sqrt(a1 * a1 + a2 * a2))) * h2;
         const double p = phi[k], r = rho[k];
         v[1] -= p * r * h2;
         double d = a1 + a2;
@@ -1448,7 +1705,8 @@ __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict
         v[3] += fabs(r) * h2;
         const double g1 = (i < nx - 1) ? ((double)phi[k + 1] - p) / h : 0.0;
         const double g2 = (j < ny - 1) ? ((double)phi[k + nx] - p) / h : 0.0;
-        const double gq = (NORM == W1_NORM_L1) ? fmax(fabs(g1), fabs(g2)) : sqrt(g1 * g1 + g2 * g2);
+        const double gq = (NORM == W1_NORM_L1) ? fmax(fabs(g1), fabs(g2))
+                          : (NORM == W1_NORM_LINF ? fabs(g1) + fabs(g2) : sqrt(g1 * g1 + g2 * g2));
         gm = fmax(gm, gq);
     }
     block_sum<4>(v, sh);
@@ -1555,8 +1813,10 @@ cudaError_t launch_final(int norm, const float* m1, const float* m2, const float
     dim3 g(bpp, pairs);
     if (norm == W1_NORM_L1)
         k_final_a<W1_NORM_L1><<<g, FIN_THREADS, 0, s>>>(m1, m2, phi, rho, nx, ny, h, q, part, ctl);
-    else
+    else if (norm == W1_NORM_L2)
         k_final_a<W1_NORM_L2><<<g, FIN_THREADS, 0, s>>>(m1, m2, phi, rho, nx, ny, h, q, part, ctl);
+    else
+        k_final_a<W1_NORM_LINF><<<g, FIN_THREADS, 0, s>>>(m1, m2, phi, rho, nx, ny, h, q, part, ctl);
     k_final_b<<<pairs, 1024, 0, s>>>(nx, ny, h, q, part, bpp, ctl);
     return cudaGetLastError();
 }

@@ -57,7 +57,7 @@ extern "C" w1_status w1_state_stats_noalloc(int nx, int ny, double h, int norm, 
 {
     if (nx < 1 || ny < 1 || !(h > 0.0) || !rho || !m1 || !m2 || !phi || !out)
         return na_fail(W1_ERR_INVALID_ARG, "bad arguments to w1_state_stats_noalloc");
-    if (norm != W1_NORM_L1 && norm != W1_NORM_L2) return na_fail(W1_ERR_INVALID_ARG, "norm must be 1 or 2");
+    if (norm != W1_NORM_L1 && norm != W1_NORM_L2 && norm != W1_NORM_LINF) return na_fail(W1_ERR_INVALID_ARG, "norm must be 1, 2 or 3");
     if ((long long)nx * (long long)ny > (long long)W1_NOALLOC_MAX_NODES)
         return na_fail(W1_ERR_INVALID_ARG, "grid has more than W1_NOALLOC_MAX_NODES (262144) nodes");
     int dev = 0;

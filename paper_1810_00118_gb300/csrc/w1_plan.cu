@@ -113,6 +113,8 @@ extern "C" void w1_default_options(w1_options* o)
     o->time_budget_s = 60.0;
     o->path = 0;
     o->rows_per_thread = 0;
+    o->eager = 0;
+    o->reserved = 0;
 }
 
 extern "C" const char* w1_last_error(void) { return g_err.c_str(); }
@@ -192,7 +194,7 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
 {
     if (nx < 1 || ny < 1) return fail(W1_ERR_INVALID_ARG, "nx and ny must be >= 1");
     if (max_batch < 1 || max_batch > 65535) return fail(W1_ERR_INVALID_ARG, "max_batch must lie in [1, 65535]");
-    if (norm != W1_NORM_L1 && norm != W1_NORM_L2) return fail(W1_ERR_INVALID_ARG, "norm must be 1 or 2");
+    if (norm != W1_NORM_L1 && norm != W1_NORM_L2 && norm != W1_NORM_LINF) return fail(W1_ERR_INVALID_ARG, "norm must be 1, 2 or 3");
     w1_options o;
     w1_default_options(&o);
     if (opt) o = *opt;
@@ -526,12 +528,75 @@ static void fill_stats(const w1_plan* p, const Ctl* c, w1_stats* st)
     st->converged = conv && !c->error && !c->timeout;
 }
 
+// The level sequence of build_graph, launched directly on s.  Streaming levels
+// test convergence on the host after every K steps (one small copy and a
+// stream synchronisation per test), so this mode is for profiling only.
+static w1_status run_eager(w1_plan* p, cudaStream_t s)
+{
+    const int B = p->batch;
+    for (int l = p->L - 1; l > 0; --l)
+        W1_CK(launch_restrict(p->lv[l].rho, p->lv[l].nx, p->lv[l].ny, p->lv[l - 1].rho, B, p->ctl, s));
+    std::vector<Ctl> host(B);
+    for (int l = 0; l < p->L; ++l) {
+        LevelPlan& v = p->lv[l];
+        const size_t b = (size_t)v.nx * v.ny * sizeof(float) * B;
+        W1_CK(launch_level_begin(p->ctl, l, B, s));
+        if (l == 0) {
+            W1_CK(cudaMemsetAsync(v.m1[0], 0, b, s));
+            W1_CK(cudaMemsetAsync(v.m2[0], 0, b, s));
+            W1_CK(cudaMemsetAsync(v.phi[0], 0, b, s));
+        } else {
+            const LevelPlan& c = p->lv[l - 1];
+            W1_CK(launch_prolong(c.nx, c.ny, c.m1[0], c.m2[0], c.phi[0], v.m1[0], v.m2[0], v.phi[0], B, p->ctl, s));
+        }
+        if (v.path == 1) {
+            ResArgs a{};
+            a.m1 = v.m1[0];
+            a.m2 = v.m2[0];
+            a.phi = v.phi[0];
+            a.rho = v.rho;
+            a.pairs = B;
+            a.it = iter_args(p, l);
+            W1_CK(launch_resident(p->norm, v.cluster, a, s));
+            continue;
+        }
+        const int K = p->opt.check_every;
+        const int per = v.path == 3 ? tblock_depth() : 1;
+        const int nl = K / per;
+        for (;;) {
+            for (int k = 0; k < nl; ++k) {
+                StepArgs a{};
+                const int src = k & 1, dst = src ^ 1;
+                a.m1 = v.m1[src];
+                a.m2 = v.m2[src];
+                a.phi = v.phi[src];
+                a.rho = v.rho;
+                a.m1o = v.m1[dst];
+                a.m2o = v.m2[dst];
+                a.phio = v.phi[dst];
+                a.rows = v.rows;
+                a.pairs = B;
+                a.it = iter_args(p, l);
+                a.part = p->part;
+                a.use_cond = 1;
+                W1_CK(v.path == 3 ? launch_tblock(p->norm, k == nl - 1, a, s) : launch_step(p->norm, k == nl - 1, a, s));
+            }
+            W1_CK(cudaMemcpyAsync(host.data(), p->ctl, sizeof(Ctl) * B, cudaMemcpyDeviceToHost, s));
+            W1_CK(cudaStreamSynchronize(s));
+            bool any = false;
+            for (int q = 0; q < B; ++q) any |= host[q].active != 0;
+            if (!any) break;
+        }
+    }
+    return W1_OK;
+}
+
 // Enqueues one batched solve on s: prep -> graph -> final statistics -> flux
 // copy -> device-to-host copy of the control blocks into the plan's pinned
 // result block.  Nothing waits.
 static w1_status enqueue(w1_plan* p, int nbatch, const float* rho0, const float* rho1, cudaStream_t s, float* flux)
 {
-    if (!p->graph_ok) {
+    if (!p->opt.eager && !p->graph_ok) {
         w1_status st = build_graph(p);
         if (st != W1_OK) return st;
     }
@@ -539,7 +604,12 @@ static w1_status enqueue(w1_plan* p, int nbatch, const float* rho0, const float*
     const int B = p->batch;
     const LevelPlan& f = p->lv[p->L - 1];
     W1_CK(launch_prep(rho0, rho1, n, nbatch, B, p->h, p->ctl, p->part, f.rho, s));
-    W1_CK(cudaGraphLaunch(p->exec, s));
+    if (p->opt.eager) {
+        w1_status st = run_eager(p, s);
+        if (st != W1_OK) return st;
+    } else {
+        W1_CK(cudaGraphLaunch(p->exec, s));
+    }
     W1_CK(launch_final(p->norm, f.m1[0], f.m2[0], f.phi[0], f.rho, f.nx, f.ny, f.h, p->q, p->part, p->ctl, B, s));
     if (flux) {
         // flux[b] = (m1 of pair b, m2 of pair b)
@@ -662,7 +732,7 @@ extern "C" w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, f
 {
     if (nx < 1 || ny < 1 || !(h > 0.0) || !rho || !m1 || !m2 || !phi || iters < 0)
         return fail(W1_ERR_INVALID_ARG, "bad arguments to w1_cp_steps");
-    if (norm != W1_NORM_L1 && norm != W1_NORM_L2) return fail(W1_ERR_INVALID_ARG, "norm must be 1 or 2");
+    if (norm != W1_NORM_L1 && norm != W1_NORM_L2 && norm != W1_NORM_LINF) return fail(W1_ERR_INVALID_ARG, "norm must be 1, 2 or 3");
     int dev = 0;
     W1_CK(cudaGetDevice(&dev));
     w1_status st = prepare_device(dev);
@@ -788,7 +858,7 @@ extern "C" w1_status w1_state_stats(int nx, int ny, double h, int norm, const fl
 {
     if (nx < 1 || ny < 1 || !(h > 0.0) || !rho || !m1 || !m2 || !phi || !out)
         return fail(W1_ERR_INVALID_ARG, "bad arguments to w1_state_stats");
-    if (norm != W1_NORM_L1 && norm != W1_NORM_L2) return fail(W1_ERR_INVALID_ARG, "norm must be 1 or 2");
+    if (norm != W1_NORM_L1 && norm != W1_NORM_L2 && norm != W1_NORM_LINF) return fail(W1_ERR_INVALID_ARG, "norm must be 1, 2 or 3");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t n = (size_t)nx * ny;
     double *q = nullptr, *part = nullptr;

@@ -377,7 +377,7 @@ extern "C" w1_status w1_submit(w1_server* srv, int nx, int ny, double h, int lev
 {
     if (!srv || !rho0 || !rho1 || !ticket) return srv_fail(W1_ERR_INVALID_ARG, "NULL server, density or ticket");
     if (nx < 1 || ny < 1) return srv_fail(W1_ERR_INVALID_ARG, "nx and ny must be >= 1");
-    if (norm != W1_NORM_L1 && norm != W1_NORM_L2) return srv_fail(W1_ERR_INVALID_ARG, "norm must be 1 or 2");
+    if (norm != W1_NORM_L1 && norm != W1_NORM_L2 && norm != W1_NORM_LINF) return srv_fail(W1_ERR_INVALID_ARG, "norm must be 1, 2 or 3");
     if (!(h > 0.0)) h = 1.0 / (double)(nx > ny ? nx : ny);
     Key k{nx, ny, levels, norm, h, tol};
     const size_t need = slot_bytes(srv, k);

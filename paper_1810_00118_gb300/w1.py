@@ -15,6 +15,7 @@ from . import _build
 
 NORM_L1 = 1
 NORM_L2 = 2
+NORM_LINF = 3
 MAX_LEVELS = 16
 
 OK = 0
@@ -45,7 +46,7 @@ class W1Error(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("check_every", ctypes.c_int), ("max_iters", ctypes.c_longlong), ("theta", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("time_budget_s", ctypes.c_double), ("path", ctypes.c_int),
-                ("rows_per_thread", ctypes.c_int)]
+                ("rows_per_thread", ctypes.c_int), ("eager", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 import oracle  # noqa: E402
 import synth  # noqa: E402
 
-L1, L2 = 1, 2
+L1, L2, LINF = 1, 2, 3
 
 
 @pytest.fixture(scope="module")
@@ -45,8 +45,10 @@ def rand_state(rng, ny, nx, scale=0.5):
 
 
 def resident_fits(nx, ny):
-    """A cluster of 1..16 CTAs, each holding whole rows, at most 4096 nodes per CTA."""
-    return any(ny % c == 0 and (ny // c) * nx <= 4096 for c in (1, 2, 4, 8, 16))
+    """A cluster of 1..16 CTAs, each holding whole rows, at most 4096 nodes per
+    CTA (16384 in 16 CTAs when nx is a multiple of 4)."""
+    return any(ny % c == 0 and (ny // c) * nx <= 4096 for c in (1, 2, 4, 8, 16)) or \
+        (nx % 4 == 0 and ny % 16 == 0 and (ny // 16) * nx <= 16384)
 
 
 def mu_of(h, theta=0.5):
@@ -64,10 +66,10 @@ def flux_rel_l1(f, m1, m2):
 SHAPES = [(1, 37), (37, 1), (3, 5), (17, 33), (40, 33), (64, 64), (128, 96), (200, 300)]
 
 
-SHAPES4 = [(1, 64), (3, 8), (40, 36), (64, 64), (96, 128), (200, 300), (130, 72)]
+SHAPES4 = [(1, 64), (3, 8), (40, 36), (64, 64), (96, 128), (200, 300), (130, 72), (512, 512), (256, 1024)]
 
 
-@pytest.mark.parametrize("norm", [L1, L2])
+@pytest.mark.parametrize("norm", [L1, L2, LINF])
 @pytest.mark.parametrize("shape", SHAPES + SHAPES4)
 @pytest.mark.parametrize("path", [1, 2, 3])
 def test_cp_steps_match_oracle(w1, norm, shape, path):
@@ -94,7 +96,7 @@ def test_cp_steps_match_oracle(w1, norm, shape, path):
         assert fpr == pytest.approx(ofpr, rel=2e-3, abs=1e-12 * scale)
 
 
-@pytest.mark.parametrize("norm", [L1, L2])
+@pytest.mark.parametrize("norm", [L1, L2, LINF])
 def test_resident_and_streaming_paths_agree(w1, norm):
     rng = np.random.default_rng(77)
     rho, m1, m2, phi = rand_state(rng, 96, 128)
@@ -132,7 +134,7 @@ def test_prolong_matches_oracle(w1, shape):
         np.testing.assert_allclose(host(got), ref, rtol=1e-6, atol=1e-6)
 
 
-@pytest.mark.parametrize("norm", [L1, L2])
+@pytest.mark.parametrize("norm", [L1, L2, LINF])
 @pytest.mark.parametrize("shape", [(1, 16), (5, 7), (64, 64), (96, 80), (512, 512)])
 def test_state_stats_match_oracle(w1, norm, shape):
     rng = np.random.default_rng(5)
@@ -189,6 +191,12 @@ def test_solve_64_l1_three_levels(w1):
         assert abs(a - b) <= max(0.1 * b, 64)
 
 
+def test_solve_64_linf_three_levels(w1):
+    r0, r1 = synth.pair(0, 6)
+    val, st, flux, _, ref = solve_and_replay(w1, r0, r1, LINF, 3, tol=1e-6)
+    assert_parity(val, st, flux, ref)
+
+
 def test_solve_256_l2_five_levels(w1):
     r0, r1 = synth.pair(1, 0)
     val, st, flux, _, ref = solve_and_replay(w1, r0, r1, L2, 5)
@@ -196,7 +204,7 @@ def test_solve_256_l2_five_levels(w1):
     assert_parity(val, st, flux, ref)
 
 
-@pytest.mark.parametrize("norm", [L2, L1])
+@pytest.mark.parametrize("norm", [L2, L1, LINF])
 def test_solve_512_six_levels(w1, norm):
     """The 512x512 image-shaped workload, 6 levels 16->512, the bench configuration."""
     r0, r1 = synth.pair(2, 0)
@@ -251,7 +259,7 @@ def test_shape_errors(w1):
     with pytest.raises(w1.W1Error, match="ERR_SHAPE"):
         w1.Plan(60, 64, levels=4)
     with pytest.raises(w1.W1Error, match="ERR_INVALID_ARG"):
-        w1.Plan(64, 64, levels=3, norm=3)
+        w1.Plan(64, 64, levels=3, norm=4)
     with pytest.raises(w1.W1Error, match="ERR_INVALID_ARG"):
         w1.Plan(64, 64, levels=3, check_every=7)
     with pytest.raises(w1.W1Error, match="ERR_INVALID_ARG"):
@@ -363,3 +371,19 @@ def test_batch_oracle_parity_512(w1):
         ref = oracle.multilevel(a0[k].astype(np.float64), a1[k].astype(np.float64), levels=6, norm=L2,
                                 replay=stats[k].iters)
         assert_parity(vals[k], stats[k], host(fb[k]), ref)
+
+
+@pytest.mark.parametrize("norm", [L1, L2])
+def test_eager_mode_equals_graph_mode(w1, norm):
+    """Launching the level kernels directly (profiling mode) runs the same
+    kernels in the same order as the CUDA graph: bitwise equal results."""
+    r0, r1 = synth.pair(2, 40, n=256)
+    a0, a1 = dev(r0), dev(r1)
+    out = []
+    for eager in (0, 1):
+        f = torch.empty((2, 256, 256), device="cuda")
+        with w1.Plan(256, 256, norm=norm, eager=eager) as plan:
+            v, st, _ = plan.solve(a0, a1, flux=f)
+        out.append((v, st.iters, f))
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
+    assert torch.equal(out[0][2], out[1][2])
