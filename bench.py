@@ -265,6 +265,7 @@ def run_gpu(args):
                 lanes[norm][b].wait_event(ready)
                 plans[norm][b].solve_async(t0[b], t1[b], stream=lanes[norm][b])
                 done_ev[norm][b].record(lanes[norm][b])
+                stream.wait_event(done_ev[norm][b])  # the launching stream joins every lane
         for norm in NORMS:
             vals, sts = [], []
             for b in range(B):
@@ -306,16 +307,21 @@ def run_gpu(args):
     pair_ms.clear()
     results = []
     step_ms = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         barrier()
         t0 = time.perf_counter()
+        ev0.record(stream)
         for s in range(args.warmup, total_steps):
             ts = time.perf_counter()
             results.append(do_step(s))
             step_ms.append((time.perf_counter() - ts) * 1e3)
+        ev1.record(stream)
         barrier()
-        elapsed = time.perf_counter() - t0
-    elapsed = max_over_ranks(elapsed)
+        wall = time.perf_counter() - t0
+    # device time on the launching stream (every lane joins it), max over ranks
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+    wall = max_over_ranks(wall)
     solves = args.steps * len(NORMS) * B * world
     value = solves / elapsed
     n_launch = sum(launches(sts) for step in results for _, sts in step)
@@ -325,11 +331,12 @@ def run_gpu(args):
     e2e = None
     if not args.no_e2e:
         barrier()
-        t0 = time.perf_counter()
+        ev0.record(stream)
         for s in range(args.warmup, total_steps):
             do_step(s, host=True)
+        ev1.record(stream)
         barrier()
-        e2e_el = max_over_ranks(time.perf_counter() - t0)
+        e2e_el = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
         e2e = {"value": solves / e2e_el, "unit": "solves/s",
                "h2d_bytes_per_step": 2 * N * N * 4 * B, "d2h_bytes_per_step": 552 * B * len(NORMS)}
 
@@ -351,6 +358,7 @@ def run_gpu(args):
                        "batch_per_norm": B, "mode": args.mode,
                        "l2": "flushed before every step (256 MiB write, inside the timed region)",
                        "parallelism": f"replicas x{world}"},
+            "timer": {"kind": "CUDA events on the launching stream, every lane joined to it", "wall_s": wall},
             "batch_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                  "what": "one step (B pairs, both norms) / 2, submit to W1 values on the host"},
             "pair_latency_ms": ({"p50": float(np.percentile(pair_lat, 50)), "p99": float(np.percentile(pair_lat, 99)),
@@ -438,19 +446,184 @@ def main():
     ap.add_argument("--min-seconds", type=float, default=0.0, help="serving: at least rate*this requests")
     ap.add_argument("--slots", type=int, default=48, help="serving: solves in flight")
     ap.add_argument("--only", default="solve",
-                    choices=["solve", "stream-kernel", "tblock-kernel", "resident-kernel", "serve"],
+                    choices=["solve", "stream-kernel", "tblock-kernel", "resident-kernel", "serve", "mixed",
+                             "tol-sweep"],
                     help="kernel-only runs for profiling: one level's steps through w1_cp_steps")
     ap.add_argument("--kn", type=int, default=256, help="grid side for --only *-kernel")
     ap.add_argument("--kiters", type=int, default=1000, help="steps for --only *-kernel")
     ap.add_argument("--knorm", type=int, default=1)
+    ap.add_argument("--kcluster", type=int, default=0, help="--only resident-kernel: CTAs per level (0: auto)")
+    ap.add_argument("--mixed-norm", type=int, default=2, help="mixed-size batch: ground norm")
+    ap.add_argument("--mixed-modes", default="loop,lanes,lockstep,lockstep-tuned")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.only == "serve":
         return run_serve(args)
+    if args.only == "mixed":
+        return run_mixed(args)
+    if args.only == "tol-sweep":
+        return run_tol_sweep(args)
     if args.only != "solve":
         return run_kernel_only(args)
     return run_gpu(args)
+
+
+# Mixed-size batch: (grid side, pairs, levels 16 -> side), Gaussian-mixture densities
+MIXED = ((64, 128, 3), (128, 96, 4), (256, 32, 5))
+
+
+def run_mixed(args):
+    """256 pairs of three grid sizes solved per step, in several ways: a loop of
+    single solves (one at a time), lanes (one async single-pair plan and stream
+    per pair), lockstep (one batched plan per size, the three on their own
+    streams), and lockstep with per-level kernels chosen by the autotuner
+    (throughput objective).  Times with CUDA events on the launching stream."""
+    import torch
+
+    import synth
+    from paper_1810_00118_gb300 import w1
+
+    torch.cuda.set_device(0)
+    norm = args.mixed_norm
+    stream = torch.cuda.current_stream()
+    passes = args.warmup + args.steps
+    data = []  # per pass: per class (t0, t1) [B, n, n]
+    for s in range(passes):
+        per = []
+        for ci, (n, B, _) in enumerate(MIXED):
+            r = [synth.pair(3, 100000 * s + 1000 * ci + k, n=n) for k in range(B)]
+            a0 = np.ascontiguousarray(np.stack([x[0] for x in r]), dtype=np.float32)
+            a1 = np.ascontiguousarray(np.stack([x[1] for x in r]), dtype=np.float32)
+            per.append((torch.from_numpy(a0).cuda(), torch.from_numpy(a1).cuda()))
+        data.append(per)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ok = (w1.OK, w1.ERR_NOT_CONVERGED)
+    total = sum(B for _, B, _ in MIXED)
+    modes = [m for m in args.mixed_modes.split(",") if m]
+    out = {}
+    w1_ref = None
+    for mode in modes:
+        if mode == "loop":
+            plans = [w1.Plan(n, n, levels=L, norm=norm) for n, _, L in MIXED]
+        elif mode == "lanes":
+            plans = [[w1.Plan(n, n, levels=L, norm=norm) for _ in range(B)] for n, B, L in MIXED]
+            lanes = [[torch.cuda.Stream() for _ in range(B)] for _, B, _ in MIXED]
+        else:
+            tune = 2 if mode == "lockstep-tuned" else 0
+            plans = [w1.Plan(n, n, levels=L, norm=norm, batch=B, tune=tune) for n, B, L in MIXED]
+            lanes = [torch.cuda.Stream() for _ in MIXED]
+
+        def one_pass(s):
+            flush.fill_(float(s))
+            vals = []
+            if mode == "loop":
+                for ci, (n, B, _) in enumerate(MIXED):
+                    t0, t1 = data[s][ci]
+                    for b in range(B):
+                        v, _, _ = plans[ci].solve(t0[b], t1[b], stream=stream, allow=ok)
+                        vals.append(v)
+                return vals
+            ready = torch.cuda.Event()
+            ready.record(stream)
+            for ci, (n, B, _) in enumerate(MIXED):
+                t0, t1 = data[s][ci]
+                if mode == "lanes":
+                    for b in range(B):
+                        lanes[ci][b].wait_event(ready)
+                        plans[ci][b].solve_async(t0[b], t1[b], stream=lanes[ci][b])
+                else:
+                    lanes[ci].wait_event(ready)
+                    plans[ci].solve_async(t0, t1, stream=lanes[ci])
+            for ci, (n, B, _) in enumerate(MIXED):
+                if mode == "lanes":
+                    for b in range(B):
+                        stream.wait_stream(lanes[ci][b])
+                        lanes[ci][b].synchronize()
+                        vals.append(plans[ci][b].results(allow=ok)[0][0])
+                else:
+                    stream.wait_stream(lanes[ci])
+                    lanes[ci].synchronize()
+                    vals.extend(plans[ci].results(allow=ok)[0])
+            return vals
+
+        for s in range(args.warmup):
+            one_pass(s)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        vals = [one_pass(s) for s in range(args.warmup, passes)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        flat = np.array([v for p in vals for v in p])
+        if w1_ref is None:
+            w1_ref = flat
+        out[mode] = {"solves_per_s": args.steps * total / (ms / 1e3), "ms_per_pass": ms / args.steps,
+                     "max_rel_diff_vs_first_mode": float(np.max(np.abs(flat - w1_ref) / np.abs(w1_ref)))}
+        del plans
+        torch.cuda.synchronize()
+    print(json.dumps({"only": "mixed", "workload": "gauss8 mixed: 128 x 64^2 (3 levels), 96 x 128^2 (4), "
+                      "32 x 256^2 (5)", "norm": norm, "pairs_per_pass": total, "passes": args.steps,
+                      "l2": "flushed before every pass", "modes": out}), flush=True)
+    return 0
+
+
+def run_tol_sweep(args):
+    """Tolerance schedule study (eq. tol_formula_propose): per level tolerance
+    eps_l = eps_L (h_l / h)^alpha for several alpha, and the number of levels,
+    on the 512^2 workload; W1 error against a reference solve with the finest
+    tolerance divided by 100, and time per solve (lanes, CUDA events)."""
+    import torch
+
+    import synth
+    from paper_1810_00118_gb300 import w1
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    B = args.batch
+    pairs = [synth.pair(WORKLOAD, 700 + k) for k in range(B)]
+    t0 = torch.from_numpy(np.ascontiguousarray(np.stack([p[0] for p in pairs]), dtype=np.float32)).cuda()
+    t1 = torch.from_numpy(np.ascontiguousarray(np.stack([p[1] for p in pairs]), dtype=np.float32)).cuda()
+    eps = 1e-6 / 128 * (512 / N) ** 2  # eq. stop_tol at h = 1/512
+    ok = (w1.OK, w1.ERR_NOT_CONVERGED)
+    lanes = [torch.cuda.Stream() for _ in range(B)]
+
+    def solve_all(norm, levels, alpha, tol):
+        plans = [w1.Plan(N, N, levels=levels, norm=norm, tol=tol, alpha=alpha) for _ in range(B)]
+        ready = torch.cuda.Event()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ready.record(stream)
+        for b in range(B):
+            lanes[b].wait_event(ready)
+            plans[b].solve_async(t0[b], t1[b], stream=lanes[b])
+            stream.wait_stream(lanes[b])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        vals, iters = [], []
+        for p in plans:
+            v, st, _, _ = p.results(allow=ok)
+            vals.append(v[0])
+            iters.append(st[0].iters)
+            p.close()
+        return np.array(vals), e0.elapsed_time(e1), iters
+
+    out = []
+    for norm in NORMS:
+        ref, _, _ = solve_all(norm, LEVELS, -1.0, eps / 100)
+        for levels in (LEVELS - 1, LEVELS, LEVELS + 1):
+            for alpha in (-2.0, -1.0, 0.0, 1.0):
+                vals, ms, iters = solve_all(norm, levels, alpha, eps)
+                err = np.abs(vals - ref) / np.abs(ref)
+                out.append({"norm": norm, "levels": levels, "alpha": alpha, "ms_per_batch": ms,
+                            "solves_per_s": B / (ms / 1e3), "max_rel_err": float(err.max()),
+                            "mean_rel_err": float(err.mean()), "iters_pair0": iters[0]})
+                print(json.dumps(out[-1]), flush=True)
+    print(json.dumps({"only": "tol-sweep", "grid": N, "pairs": B, "eps_L": eps,
+                      "reference": "same pairs, alpha -1, default levels, eps_L / 100", "rows": out}))
+    return 0
 
 
 SERVE_SIZES = (128, 256, 512, 1024)
@@ -544,16 +717,18 @@ def run_kernel_only(args):
     mu = float(np.float32(0.5 * h / (2 * np.sqrt(2.0))))
     path = {"resident-kernel": 1, "stream-kernel": 2, "tblock-kernel": 3}[args.only]
     stream = torch.cuda.current_stream()
-    w1.cp_steps(rho, m1, m2, phi, h, args.knorm, mu, mu, 4, path=path, stream=stream)
+    kw = {"cluster": args.kcluster} if path == 1 else {}
+    w1.cp_steps(rho, m1, m2, phi, h, args.knorm, mu, mu, 4, path=path, stream=stream, **kw)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    fpr = w1.cp_steps(rho, m1, m2, phi, h, args.knorm, mu, mu, args.kiters, path=path, stream=stream)
+    fpr = w1.cp_steps(rho, m1, m2, phi, h, args.knorm, mu, mu, args.kiters, path=path, stream=stream, **kw)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     us_step = ms * 1e3 / args.kiters
-    print(json.dumps({"only": args.only, "n": n, "norm": args.knorm, "steps": args.kiters, "ms": ms,
+    print(json.dumps({"only": args.only, "n": n, "norm": args.knorm, "cluster": args.kcluster, "steps": args.kiters,
+                      "ms": ms,
                       "us_per_step": us_step, "node_steps_per_s": n * n / (us_step * 1e-6),
                       "alg_GBps": 28.0 * n * n / (us_step * 1e-6) / 1e9, "fpr_last": fpr}))
     return 0

@@ -81,7 +81,9 @@ typedef struct {
     int eager;             /* 1: launch the level kernels directly and test convergence of
                               streaming levels on the host (for profilers that do not follow
                               conditional graph nodes); 0: one CUDA graph (default)           */
-    int reserved;          /* must be 0 */
+    int tune;              /* 0: fixed rules pick each level's kernel; 1: the autotuner picks
+                              the fastest for one pair (latency); 2: the fastest for the
+                              plan's batch advancing together (throughput)                  */
 } w1_options;
 
 /* What a solve reports.  Values are FP64 sums of the FP32 state. */
@@ -197,6 +199,31 @@ w1_status w1_solve_host(w1_plan* plan, const float* rho0, const float* rho1, voi
  * Kantorovich potential of Algorithm 1, Appendix B); enqueued on stream. */
 w1_status w1_plan_potential(w1_plan* plan, float* phi, void* stream);
 
+/* One way to run a level, as measured by the autotuner. */
+typedef struct {
+    int path;           /* 1 on chip, 2 streaming, 3 streaming with temporal blocking */
+    int cluster;        /* CTAs per pair for path 1 */
+    int batch;          /* pairs advancing together when it was timed */
+    double us_per_step; /* measured time of one step of the whole batch */
+} w1_level_choice;
+
+/*
+ * Times every configuration that can run an nx x ny level (`steps` steps each,
+ * synthetic density, CUDA events) and returns the fastest in `best`.
+ * objective 1: one pair alone (latency); objective 2: `batch` pairs advancing
+ * together as in a batched plan (throughput: a configuration with fewer CTAs
+ * per pair can finish a large batch sooner).  `all` (room for 8) receives every
+ * measured candidate when not NULL, n_all their number.  Results are cached
+ * per device, grid, norm and batch for the process, and in the file named by
+ * the environment variable W1_AUTOTUNE_CACHE when it is set.  The choice is
+ * the kernel and its cluster size; the tiles of the streaming kernels are
+ * fixed at compile time (64 x 32 nodes, 4 steps per launch for path 3).
+ * Allocates up to 2 GiB of scratch while it runs.
+ */
+w1_status w1_autotune_level(int nx, int ny, int norm, int batch, int objective, int steps, w1_level_choice* best,
+                            w1_level_choice* all, int* n_all);
+const char* w1_autotune_last_error(void);
+
 /* Device bytes a plan with these arguments would allocate (0 on invalid
  * arguments); lets a caller admit work against a memory budget. */
 size_t w1_plan_bytes(int nx, int ny, double h, int levels, int norm, double tol, int max_batch,
@@ -262,13 +289,24 @@ const char* w1_server_last_error(void);
 
 /*
  * `iters` steps of eq. primaldual in place on (m1, m2, phi) with density rho,
- * step sizes mu, tau, spacing h.  path: 1 shared-memory resident (grids up to
- * 16 * 4096 nodes), 2 streaming, 3 temporally blocked streaming (nx and iters
- * multiples of 4).  If fpr_last is not NULL it receives R^k of
- * the last step (FP64 sums).  The boundary flux entries must be 0 on entry.
+ * step sizes mu, tau, spacing h.  path: 1 shared-memory resident (bands of
+ * whole rows in a cluster of up to 16 CTAs: at most 4096 nodes per CTA, or
+ * 16384 when nx % 4 == 0 and the band is a multiple of 128 nodes; else
+ * W1_ERR_UNSUPPORTED), 2 streaming, 3 temporally blocked streaming
+ * (nx and iters multiples of 4).  The four planes must be 16-byte aligned
+ * (W1_ERR_INVALID_ARG otherwise).  If fpr_last is not NULL it receives R^k of
+ * the last step (FP64 sums).  The boundary flux entries m1[.][nx-1] and
+ * m2[ny-1][.] are zero by definition (zero flux); values stored there are
+ * ignored and come back as 0.
  */
 w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, float tau, const float* rho, float* m1,
                       float* m2, float* phi, long long iters, int path, void* stream, double* fpr_last);
+/* w1_cp_steps with the cluster size of the resident path chosen by the caller
+ * (cluster = 1, 2, 4, 8 or 16 CTAs; 0 picks it as w1_cp_steps does; ignored by
+ * paths 2 and 3).  W1_ERR_UNSUPPORTED if the level does not fit that cluster. */
+w1_status w1_cp_steps_ex(int nx, int ny, double h, int norm, float mu, float tau, const float* rho, float* m1,
+                         float* m2, float* phi, long long iters, int path, int cluster, void* stream,
+                         double* fpr_last);
 
 /* coarse[ny/2][nx/2] = mean of each 2x2 block of fine[ny][nx] (density restriction). */
 w1_status w1_restrict(int nx, int ny, const float* fine, float* coarse, void* stream);

@@ -100,6 +100,9 @@ size_t step_part_doubles(int nx, int ny, int rows, int pairs);
 // Resident level solve with a cluster of `cluster` CTAs per pair.
 cudaError_t launch_resident(int norm, int cluster, const ResArgs& a, cudaStream_t s);
 int resident_max_nodes();
+// Whether a level of nx x ny fits on chip in a cluster of `cluster` CTAs (bands of
+// whole rows: at most 4096 nodes per CTA, or 16384 with 16 CTAs and nx % 4 == 0).
+bool resident_fits(int nx, int ny, int cluster);
 int resident_cluster_for(int nx, int ny);
 cudaError_t resident_prepare(int device);
 // Active clusters the device can hold for this configuration (0: cannot launch).

@@ -41,8 +41,8 @@ static constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ float soft(float v, float mu)
 {
-    float a = fabsf(v) - mu;
-    return a > 0.f ? copysignf(a, v) : 0.f;
+    // sign(v) max(|v| - mu, 0), written as v minus its clamp to [-mu, mu]
+    return v - fminf(fmaxf(v, -mu), mu);
 }
 
 template <int NORM>
@@ -70,8 +70,8 @@ __device__ __forceinline__ void prox(float v1, float v2, float mu, float& o1, fl
             o2 = copysignf(c, v2);
         }
     } else {
-        float len = sqrtf(v1 * v1 + v2 * v2);
-        float s = (len > mu) ? 1.f - mu / len : 0.f;
+        // v max(0, 1 - mu / |v|); rsqrt(0) = inf gives 0
+        const float s = fmaxf(1.f - mu * rsqrtf(fmaf(v1, v1, v2 * v2)), 0.f);
         o1 = v1 * s;
         o2 = v2 * s;
     }
@@ -373,7 +373,8 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
     const int i = blockIdx.x * 32 + lane;
     const int j0 = (blockIdx.y * (STEP_THREADS / 32) + warp) * a.rows;
     const bool act = i < nx;
-    const float mu = P.mu, tau = P.tau, ih = P.ih;
+    const float mu = P.mu, tau = P.tau;
+    const float cm = P.mu * P.ih, ct = P.tau * P.ih;  // mu / h, tau / h
     const size_t off = (size_t)pair * P.stride;
     double sa = 0.0, sb = 0.0, sc = 0.0;
     if (j0 < ny) {
@@ -393,16 +394,16 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
         if (j0 > 0) {
             float pb = act ? __ldg(phi + at(j0 - 1, i)) : 0.f;
             float c2 = act ? __ldg(m2 + at(j0 - 1, i)) : 0.f;
-            float g2 = (pc_ - pb) * ih;
+            const float v2 = fmaf(cm, pc_ - pb, c2);
             float o1 = 0.f, o2;
             if (NORM == W1_NORM_L1) {
-                o2 = soft(c2 + mu * g2, mu);
+                o2 = soft(v2, mu);
             } else {
                 float pbr = __shfl_down_sync(FULL, pb, 1);
                 if (lane == 31 && i + 1 < nx) pbr = __ldg(phi + at(j0 - 1, i + 1));
-                float g1 = (i < nx - 1) ? (pbr - pb) * ih : 0.f;
-                float c1 = act ? __ldg(m1 + at(j0 - 1, i)) : 0.f;
-                prox<NORM>(c1 + mu * g1, c2 + mu * g2, mu, o1, o2);
+                const float c1 = act ? __ldg(m1 + at(j0 - 1, i)) : 0.f;
+                const float v1 = (i < nx - 1) ? fmaf(cm, pbr - pb, c1) : 0.f;
+                prox<NORM>(v1, v2, mu, o1, o2);
             }
             (void)o1;
             b2b = 2.f * o2 - c2;
@@ -423,10 +424,11 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
             }
             float pr = __shfl_down_sync(FULL, pc_, 1);
             if (lane == 31 && i + 1 < nx) pr = __ldg(phi + at(j, i + 1));
-            const float g1 = (i < nx - 1) ? (pr - pc_) * ih : 0.f;
-            const float g2 = (j < ny - 1) ? (pu - pc_) * ih : 0.f;
+            // pinned entries (last column, top row) enter as zero and stay zero
+            const float v1 = (i < nx - 1) ? fmaf(cm, pr - pc_, a1) : 0.f;
+            const float v2 = (j < ny - 1) ? fmaf(cm, pu - pc_, a2) : 0.f;
             float n1, n2;
-            prox<NORM>(a1 + mu * g1, a2 + mu * g2, mu, n1, n2);
+            prox<NORM>(v1, v2, mu, n1, n2);
             if (i >= nx - 1) n1 = 0.f;
             if (j == ny - 1) n2 = 0.f;
             const float b1 = 2.f * n1 - a1, b2 = 2.f * n2 - a2;
@@ -438,15 +440,15 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
                     // the left neighbour belongs to the previous warp: recompute its m1'
                     const float ql = __ldg(phi + at(j, i - 1));
                     const float c1 = __ldg(m1 + at(j, i - 1));
-                    const float gl1 = (pc_ - ql) * ih;
+                    const float vl1 = fmaf(cm, pc_ - ql, c1);
                     float o1, o2;
                     if (NORM == W1_NORM_L1) {
-                        o1 = soft(c1 + mu * gl1, mu);
+                        o1 = soft(vl1, mu);
                     } else {
                         const float qlu = (j + 1 < ny) ? __ldg(phi + at(j + 1, i - 1)) : 0.f;
                         const float c2 = __ldg(m2 + at(j, i - 1));
-                        const float gl2 = (j < ny - 1) ? (qlu - ql) * ih : 0.f;
-                        prox<NORM>(c1 + mu * gl1, c2 + mu * gl2, mu, o1, o2);
+                        const float vl2 = (j < ny - 1) ? fmaf(cm, qlu - ql, c2) : 0.f;
+                        prox<NORM>(vl1, vl2, mu, o1, o2);
                     }
                     b1l = 2.f * o1 - c1;
                     d1l = (double)o1 - (double)c1;
@@ -455,8 +457,8 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
                     d1l = 0.0;
                 }
             }
-            const float dv = ((b1 - b1l) + (b2 - b2b)) * ih;
-            const float pn = pc_ + tau * (dv - r);
+            const float dv = (b1 - b1l) + (b2 - b2b);  // h div mbar
+            const float pn = fmaf(ct, dv, fmaf(-tau, r, pc_));
             if (act) {
                 m1o[at(j, i)] = n1;
                 m2o[at(j, i)] = n2;
@@ -548,6 +550,7 @@ cudaError_t launch_step(int norm, bool check, const StepArgs& a, cudaStream_t s)
 // k_step.  Global traffic per step: (16 B x tile/interior + 12 B) / TB per node.
 
 static constexpr int TBX = 64, TBY = 32, TB = 4;
+static_assert(TB % 4 == 0 && TBX % 4 == 0, "runs of four nodes must not straddle the tile's interior edge");
 static constexpr int TLW = TBX + 2 * TB, TLH = TBY + 2 * TB, TLN = TLW * TLH;  // 72 x 40 = 2880
 static constexpr int TB_THREADS = ((TLN / 4 + 31) / 32) * 32;                // 736
 
@@ -575,7 +578,8 @@ __global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
     float* e1s = s2 + TLN;  // test launches only
     float* e2s = e1s + TLN;
     const size_t off = (size_t)pair * P.stride;
-    const float mu = P.mu, tau = P.tau, ih = P.ih;
+    const float mu = P.mu, tau = P.tau;
+    const float cm = P.mu * P.ih, ct = P.tau * P.ih;  // mu / h, tau / h
     const int t = threadIdx.x;
     const bool own = t < TLN / 4;
     const int W = TLW / 4;
@@ -584,16 +588,22 @@ __global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
     const int idx = jl * TLW + il;
     const int gj = Y0 + jl, gi0 = X0 + il;
     const bool row_in = gj >= 0 && gj < ny;
+    // nx % 4 == 0 and gi0 % 4 == 0: a run of four lies wholly inside or outside the grid
+    const bool run_in = own && row_in && gi0 >= 0 && gi0 < nx;
     float m1[4], m2[4], pv[4], rv[4], Dv[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int gi = gi0 + c;
-        const bool in = own && row_in && gi >= 0 && gi < nx;
-        const size_t g = off + (size_t)(in ? gj : 0) * nx + (in ? gi : 0);
-        m1[c] = in ? __ldg(a.m1 + g) : 0.f;
-        m2[c] = in ? __ldg(a.m2 + g) : 0.f;
-        pv[c] = in ? __ldg(a.phi + g) : 0.f;
-        rv[c] = in ? __ldg(a.rho + g) : 0.f;
+    {
+        float4 x1 = make_float4(0.f, 0.f, 0.f, 0.f), x2 = x1, xp = x1, xr = x1;
+        if (run_in) {
+            const size_t g = off + (size_t)gj * nx + gi0;
+            x1 = __ldg(reinterpret_cast<const float4*>(a.m1 + g));
+            x2 = __ldg(reinterpret_cast<const float4*>(a.m2 + g));
+            xp = __ldg(reinterpret_cast<const float4*>(a.phi + g));
+            xr = __ldg(reinterpret_cast<const float4*>(a.rho + g));
+        }
+        m1[0] = x1.x; m1[1] = x1.y; m1[2] = x1.z; m1[3] = x1.w;
+        m2[0] = x2.x; m2[1] = x2.y; m2[2] = x2.z; m2[3] = x2.w;
+        pv[0] = xp.x; pv[1] = xp.y; pv[2] = xp.z; pv[3] = xp.w;
+        rv[0] = xr.x; rv[1] = xr.y; rv[2] = xr.z; rv[3] = xr.w;
     }
     if (own) {
         *reinterpret_cast<float4*>(ph + idx) = make_float4(pv[0], pv[1], pv[2], pv[3]);
@@ -601,7 +611,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
         *reinterpret_cast<float4*>(s2 + idx) = make_float4(m2[0], m2[1], m2[2], m2[3]);
     }
     __syncthreads();
-    if (own) {  // D^0 = div m^0 (wrong on the tile's first column and row, as it should be)
+    if (own) {  // D^0 = h div m^0 (wrong on the tile's first column and row, as it should be)
         const float l = il > 0 ? s1[idx - 1] : 0.f;
         const float4 b = jl > 0 ? *reinterpret_cast<const float4*>(s2 + idx - TLW) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float bb[4] = {b.x, b.y, b.z, b.w};
@@ -609,7 +619,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
         for (int c = 0; c < 4; ++c) {
             const int gi = gi0 + c;
             const float left = c ? m1[c - 1] : l;
-            Dv[c] = (((gi < nx - 1 ? m1[c] : 0.f) - (gi > 0 ? left : 0.f)) + ((gj < ny - 1 ? m2[c] : 0.f) - (gj > 0 ? bb[c] : 0.f))) * ih;
+            Dv[c] = ((gi < nx - 1 ? m1[c] : 0.f) - (gi > 0 ? left : 0.f)) + ((gj < ny - 1 ? m2[c] : 0.f) - (gj > 0 ? bb[c] : 0.f));
         }
     }
     __syncthreads();
@@ -628,13 +638,12 @@ __global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
             float n1[4], n2[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
+                // pinned entries (last column, top row) and nodes past them: v = 0 gives m' = 0
                 const int gi = gi0 + c;
                 const float pr_ = c < 3 ? pv[c + 1] : right;
-                const float g1 = gi < nx - 1 ? (pr_ - pv[c]) * ih : 0.f;
-                const float g2 = gj < ny - 1 ? (up[c] - pv[c]) * ih : 0.f;
-                prox<NORM>(m1[c] + mu * g1, m2[c] + mu * g2, mu, n1[c], n2[c]);
-                if (gi >= nx - 1) n1[c] = 0.f;
-                if (gj >= ny - 1) n2[c] = 0.f;
+                const float v1 = gi < nx - 1 ? fmaf(cm, pr_ - pv[c], m1[c]) : 0.f;
+                const float v2 = gj < ny - 1 ? fmaf(cm, up[c] - pv[c], m2[c]) : 0.f;
+                prox<NORM>(v1, v2, mu, n1[c], n2[c]);
             }
             if (last) {
                 float d1[4], d2[4];
@@ -667,8 +676,8 @@ __global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
             for (int c = 0; c < 4; ++c) {
                 const int gi = gi0 + c;
                 const float left = c ? m1[c - 1] : l;
-                const float Dn = ((m1[c] - (gi > 0 ? left : 0.f)) + (m2[c] - (gj > 0 ? bb[c] : 0.f))) * ih;
-                pn[c] = pv[c] + tau * ((2.f * Dn - Dv[c]) - rv[c]);
+                const float Dn = (m1[c] - (gi > 0 ? left : 0.f)) + (m2[c] - (gj > 0 ? bb[c] : 0.f));
+                pn[c] = fmaf(ct, fmaf(2.f, Dn, -Dv[c]), fmaf(-tau, rv[c], pv[c]));
                 Dv[c] = Dn;
             }
             if (last) {
@@ -697,17 +706,12 @@ __global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
         }
         __syncthreads();
     }
-    // write the interior
-    if (own && interior_row) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int ci = il + c, gi = gi0 + c;
-            if (ci < TB || ci >= TB + TBX || gi >= nx) continue;
-            const size_t g = off + (size_t)gj * nx + gi;
-            a.m1o[g] = m1[c];
-            a.m2o[g] = m2[c];
-            a.phio[g] = pv[c];
-        }
+    // write the interior (TB % 4 == 0: a run is wholly interior or wholly halo)
+    if (run_in && interior_row && il >= TB && il < TB + TBX) {
+        const size_t g = off + (size_t)gj * nx + gi0;
+        *reinterpret_cast<float4*>(a.m1o + g) = make_float4(m1[0], m1[1], m1[2], m1[3]);
+        *reinterpret_cast<float4*>(a.m2o + g) = make_float4(m2[0], m2[1], m2[2], m2[3]);
+        *reinterpret_cast<float4*>(a.phio + g) = make_float4(pv[0], pv[1], pv[2], pv[3]);
     }
     if (!CHECK) return;
     __shared__ double sh[32 * 3];
@@ -823,17 +827,26 @@ static constexpr int RESW_MAX_NODES = RES_THREADS * 4 * RESW_RUNS;  // 16384
 
 int resident_max_nodes() { return RES_MAX_NODES; }
 
+bool resident_fits(int nx, int ny, int cluster)
+{
+    if (nx < 1 || ny < 1 || nx > 65535 || cluster < 1 || cluster > 16 || ny % cluster != 0) return false;
+    if (cluster & (cluster - 1)) return false;
+    const long long band = (long long)(ny / cluster) * nx;
+    if (band <= RES_MAX_NODES) return true;
+    // wide bands (four runs of four nodes per thread) need nx % 4 == 0 and a
+    // multiple of 128 nodes (so that a warp's runs are all present or all absent)
+    return nx % 4 == 0 && band <= RESW_MAX_NODES && band % 128 == 0;
+}
+
 int resident_cluster_for(int nx, int ny)
 {
+    // the fewest CTAs that hold at most 4096 nodes each; else the most CTAs
+    // (the fastest step) with wide bands of up to 16384 nodes
     const int cs[5] = {1, 2, 4, 8, 16};
-    if (nx > 65535) return 0;
-    for (int c : cs) {
-        if (ny % c != 0) continue;
-        long long band = (long long)(ny / c) * nx;
-        if (band <= RES_MAX_NODES) return c;
-    }
-    // wide bands (four runs of four nodes per thread) need 16 CTAs and nx % 4 == 0
-    if (nx % 4 == 0 && ny % 16 == 0 && (long long)(ny / 16) * nx <= RESW_MAX_NODES) return 16;
+    for (int c : cs)
+        if (resident_fits(nx, ny, c) && (long long)(ny / c) * nx <= RES_MAX_NODES) return c;
+    for (int k = 4; k >= 0; --k)
+        if (resident_fits(nx, ny, cs[k])) return cs[k];
     return 0;
 }
 
@@ -1097,21 +1110,28 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
     float* e1s = s2 + nb;
     float* e2s = e1s + nb;
     const size_t off = (size_t)pair * P.stride + (size_t)jb * nx;
-    const float mu = P.mu, tau = P.tau, ih = P.ih;
+    const float mu = P.mu, tau = P.tau;
+    const float cm = P.mu * P.ih, ct = P.tau * P.ih;  // mu / h, tau / h
 
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31;
     const bool own = t < rows * W;
     const int jl = own ? t / W : 0;
     const int i0 = own ? 4 * (t - jl * W) : 0;
-    const int idx = jl * nx + i0;
+    const int idx = jl * nx + i0;  // = 4 t: consecutive threads own consecutive runs
     const int j = jb + jl;
+    const bool last_col = own && (i0 + 4 == nx);
+    const bool top = j == ny - 1;
+    // own nodes: m, phi, rho and D = h div m^k, all in registers
     float m1[4] = {0.f, 0.f, 0.f, 0.f}, m2[4] = {0.f, 0.f, 0.f, 0.f}, pv[4] = {0.f, 0.f, 0.f, 0.f};
     float rv[4] = {0.f, 0.f, 0.f, 0.f}, Dv[4] = {0.f, 0.f, 0.f, 0.f};
     if (own) {
-        const float4 x1 = *reinterpret_cast<const float4*>(a.m1 + off + idx);
-        const float4 x2 = *reinterpret_cast<const float4*>(a.m2 + off + idx);
+        float4 x1 = *reinterpret_cast<const float4*>(a.m1 + off + idx);
+        float4 x2 = *reinterpret_cast<const float4*>(a.m2 + off + idx);
         const float4 xp = *reinterpret_cast<const float4*>(a.phi + off + idx);
         const float4 xr = *reinterpret_cast<const float4*>(a.rho + off + idx);
+        // the pinned entries (zero flux through the right and top boundaries) are zero
+        if (last_col) x1.w = 0.f;
+        if (top) x2 = make_float4(0.f, 0.f, 0.f, 0.f);
         m1[0] = x1.x; m1[1] = x1.y; m1[2] = x1.z; m1[3] = x1.w;
         m2[0] = x2.x; m2[1] = x2.y; m2[2] = x2.z; m2[3] = x2.w;
         pv[0] = xp.x; pv[1] = xp.y; pv[2] = xp.z; pv[3] = xp.w;
@@ -1138,43 +1158,54 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
         if (CL && rank > 0) return dsmem_ld4(remote);
         return make_float4(0.f, 0.f, 0.f, 0.f);
     };
-    if (own) {  // D^0 = div m^0
-        const float l = i0 > 0 ? s1[idx - 1] : 0.f;
-        const float4 b = below4(s2, s2_dn);
-        const float bb[4] = {b.x, b.y, b.z, b.w};
+    // m1 of the node left of the run: the previous lane's last node, or shared
+    // memory for lane 0 (every lane takes part in the shuffle)
+    auto left_of = [&](float prev_lane, const float* arr) -> float {
+        if (i0 == 0) return 0.f;
+        return lane == 0 ? arr[idx - 1] : prev_lane;
+    };
+    {  // D^0 = h div m^0
+        const float ln = __shfl_up_sync(FULL, m1[3], 1);
+        if (own) {
+            const float l = left_of(ln, s1);
+            const float4 b = below4(s2, s2_dn);
+            const float bb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) Dv[c] = ((m1[c] - (c ? m1[c - 1] : l)) + (m2[c] - bb[c])) * ih;
+            for (int c = 0; c < 4; ++c) Dv[c] = (m1[c] - (c ? m1[c - 1] : l)) + (m2[c] - bb[c]);
+        }
     }
     if (CL) cg::this_cluster().sync();
     else __syncthreads();
 
-    unsigned long long t0 = 0;
-    if (rank == 0 && t == 0) t0 = globaltimer();
-    long long it = 0;
-    double R = 0.0;
-    int conv = 0, late = 0;
-    const long long cap = P.cap;
-    const bool last_col = own && (i0 + 4 == nx);
+    // the start time, R^k and the decision live in CTA 0's slots (registers are scarce)
+    if (rank == 0 && t == 0) {
+        reinterpret_cast<unsigned long long*>(slots)[50] = globaltimer();
+        slots[48] = 0.0;
+        slots[49] = 0.0;
+    }
+    if (CL) cg::this_cluster().sync();
+    else __syncthreads();
+    int it = 0;
+    const int cap = (int)min(P.cap, (long long)INT_MAX);
+    int next = P.fixed ? cap : P.K;  // step after which the next test runs
     while (it < cap) {
-        const bool check = P.fixed ? (it + 1 == cap) : ((it + 1) % P.K == 0);
+        const bool check = it + 1 == next;
         double sa = 0.0, sb = 0.0, sc = 0.0;
-        // ---- phase A: m' = prox(m + mu grad phi)
+        // ---- phase A: m' = prox(m + mu grad phi); on the last column and the top
+        // row the gradient component is zero and so is m, hence m' too
+        const float rn = __shfl_down_sync(FULL, pv[0], 1);
         if (own) {
-            float up[4] = {0.f, 0.f, 0.f, 0.f};
-            if (j < ny - 1) {
+            float up[4] = {pv[0], pv[1], pv[2], pv[3]};
+            if (!top) {
                 const float4 u = (jl < rows - 1) ? *reinterpret_cast<const float4*>(ph + idx + nx) : dsmem_ld4(ph_up);
                 up[0] = u.x; up[1] = u.y; up[2] = u.z; up[3] = u.w;
             }
-            const float right = last_col ? 0.f : ph[idx + 4];
+            const float right = last_col ? pv[3] : (lane == 31 ? ph[idx + 4] : rn);
             float n1[4], n2[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float pr_ = c < 3 ? pv[c + 1] : right;
-                const float g1 = (c == 3 && last_col) ? 0.f : (pr_ - pv[c]) * ih;
-                const float g2 = (j < ny - 1) ? (up[c] - pv[c]) * ih : 0.f;
-                prox<NORM>(m1[c] + mu * g1, m2[c] + mu * g2, mu, n1[c], n2[c]);
-                if (c == 3 && last_col) n1[c] = 0.f;
-                if (j == ny - 1) n2[c] = 0.f;
+                prox<NORM>(fmaf(cm, pr_ - pv[c], m1[c]), fmaf(cm, up[c] - pv[c], m2[c]), mu, n1[c], n2[c]);
             }
             if (check) {
                 float d1[4], d2[4];
@@ -1202,15 +1233,16 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
             __syncthreads();
         }
         // ---- phase B: phi' = phi + tau (div(2m' - m) - rho)
+        const float ln = __shfl_up_sync(FULL, m1[3], 1);
         if (own) {
-            const float l = i0 > 0 ? s1[idx - 1] : 0.f;
+            const float l = left_of(ln, s1);
             const float4 b = below4(s2, s2_dn);
             const float bb[4] = {b.x, b.y, b.z, b.w};
             float pn[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const float Dn = ((m1[c] - (c ? m1[c - 1] : l)) + (m2[c] - bb[c])) * ih;
-                pn[c] = pv[c] + tau * ((2.f * Dn - Dv[c]) - rv[c]);
+                const float Dn = (m1[c] - (c ? m1[c - 1] : l)) + (m2[c] - bb[c]);
+                pn[c] = fmaf(ct, fmaf(2.f, Dn, -Dv[c]), fmaf(-tau, rv[c], pv[c]));
                 Dv[c] = Dn;
             }
             if (check) {
@@ -1242,6 +1274,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
         }
         ++it;
         if (check) {
+            next += P.K;
             double v[3] = {sa, sb, sc};
             block_sum<3>(v, red);
             if (t == 0) {
@@ -1257,18 +1290,14 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
                     for (int c = 0; c < 3; ++c) tt[c] += slots[r * 3 + c];
                 const double Rk = (tt[0] / (double)mu + tt[1] / (double)tau - 2.0 * tt[2]) * P.h * P.h;
                 const int cv = Rk < P.tol;
-                const int lt = (globaltimer() - t0) > P.budget_ns;
+                const int lt = (globaltimer() - reinterpret_cast<const unsigned long long*>(slots)[50]) > P.budget_ns;
                 const int stop = P.fixed || cv || lt || it >= cap;
                 slots[48] = Rk;
                 slots[49] = (double)(cv | (lt << 1) | (stop << 2));
             }
             if (CL) cg::this_cluster().sync();
             else __syncthreads();
-            R = dsmem_ld_f64(slots0 + 8u * 48);
-            const int d = (int)dsmem_ld_f64(slots0 + 8u * 49);
-            conv = d & 1;
-            late = (d >> 1) & 1;
-            if (d & 4) break;
+            if ((int)dsmem_ld_f64(slots0 + 8u * 49) & 4) break;
         }
     }
     if (own) {
@@ -1277,6 +1306,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
         *reinterpret_cast<float4*>(a.phi + off + idx) = make_float4(pv[0], pv[1], pv[2], pv[3]);
     }
     if (rank == 0 && t == 0) {
+        const double R = slots[48];
+        const int d = (int)slots[49], conv = d & 1, late = (d >> 1) & 1;
         if (pc) {
             pc->iters[P.level] = it;
             pc->fpr[P.level] = R;
@@ -1301,12 +1332,20 @@ static size_t resident_wide_smem(int band)
     return RES_RED_BYTES + RES_SLOT_BYTES + (size_t)band * 3 * sizeof(float);
 }
 
-template <int NORM>
+template <int NORM, bool CL>
 __global__ void __launch_bounds__(RES_THREADS, 1) k_resident_wide(ResArgs a)
 {
     const IterArgs& P = a.it;
-    cg::cluster_group cl = cg::this_cluster();
-    const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    int C = 1, rank = 0;
+    if (CL) {
+        cg::cluster_group cl = cg::this_cluster();
+        C = (int)cl.num_blocks();
+        rank = (int)cl.block_rank();
+    }
+    auto group_sync = [&]() {
+        if (CL) cg::this_cluster().sync();
+        else __syncthreads();
+    };
     const int pair = blockIdx.x / C;
     Ctl* pc = P.ctl ? P.ctl + pair : nullptr;
     if (pc && pc->error) return;  // uniform over the cluster (one pair)
@@ -1319,81 +1358,99 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident_wide(ResArgs a)
     float* s1 = ph + nb;
     float* s2 = s1 + nb;
     const size_t off = (size_t)pair * P.stride + (size_t)jb * nx;
-    const float mu = P.mu, tau = P.tau, ih = P.ih;
-    const int t = threadIdx.x, T = blockDim.x;
-    int idx[RESW_RUNS];
-    float rv[RESW_RUNS][4], Dv[RESW_RUNS][4];
+    const float mu = P.mu, tau = P.tau;
+    const float cm = P.mu * P.ih, ct = P.tau * P.ih;  // mu / h, tau / h
+    const int t = threadIdx.x, T = blockDim.x, lane = t & 31;
+    // run r of this thread: nodes 4 q .. 4 q + 3 of the band, q = t + r T;
+    // pk = (row << 16) | column of its first node, or -1 past the band
+    int pk[RESW_RUNS];
+    float Dv[RESW_RUNS][4];  // h div m^k (rho is re-read from L1/L2 every step: registers are scarce)
+    const float* __restrict__ rho = a.rho + off;
 #pragma unroll
     for (int r = 0; r < RESW_RUNS; ++r) {
-        const int q = t + r * T;  // run index
-        idx[r] = q * 4 < nb ? q * 4 : -1;
-        if (idx[r] >= 0) {
-            const float4 x1 = *reinterpret_cast<const float4*>(a.m1 + off + idx[r]);
-            const float4 x2 = *reinterpret_cast<const float4*>(a.m2 + off + idx[r]);
-            const float4 xp = *reinterpret_cast<const float4*>(a.phi + off + idx[r]);
-            const float4 xr = *reinterpret_cast<const float4*>(a.rho + off + idx[r]);
-            *reinterpret_cast<float4*>(ph + idx[r]) = xp;
-            *reinterpret_cast<float4*>(s1 + idx[r]) = x1;
-            *reinterpret_cast<float4*>(s2 + idx[r]) = x2;
-            rv[r][0] = xr.x; rv[r][1] = xr.y; rv[r][2] = xr.z; rv[r][3] = xr.w;
+        const int id = 4 * (t + r * T);
+        pk[r] = -1;
+        if (id < nb) {
+            const int jl = id / nx, i0 = id - jl * nx;
+            pk[r] = (jl << 16) | i0;
+            float4 x1 = *reinterpret_cast<const float4*>(a.m1 + off + id);
+            float4 x2 = *reinterpret_cast<const float4*>(a.m2 + off + id);
+            const float4 xp = *reinterpret_cast<const float4*>(a.phi + off + id);
+            // the pinned entries (zero flux through the right and top boundaries) are zero
+            if (i0 + 4 == nx) x1.w = 0.f;
+            if (jb + jl == ny - 1) x2 = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4*>(ph + id) = xp;
+            *reinterpret_cast<float4*>(s1 + id) = x1;
+            *reinterpret_cast<float4*>(s2 + id) = x2;
         }
     }
-    cl.sync();
+    group_sync();
     const int last_row = (rows - 1) * nx;
-    const uint32_t ph_up = (rank + 1 < C) ? dsmem_map(smem_u32(ph), rank + 1) : 0u;
-    const uint32_t s2_dn = (rank > 0) ? dsmem_map(smem_u32(s2 + last_row), rank - 1) : 0u;
-    const uint32_t slots0 = dsmem_map(smem_u32(slots), 0);
-    // div of the m currently in s1, s2 at run r
+    uint32_t ph_up = 0u, s2_dn = 0u, slots0 = smem_u32(slots);
+    if (CL) {
+        if (rank + 1 < C) ph_up = dsmem_map(smem_u32(ph), rank + 1);
+        if (rank > 0) s2_dn = dsmem_map(smem_u32(s2 + last_row), rank - 1);
+        slots0 = dsmem_map(smem_u32(slots), 0);
+    }
+    // h div of the m currently in s1, s2 at run r (the left neighbour comes from the
+    // previous lane by a shuffle: a warp's runs are all present or all absent,
+    // since the band holds a multiple of 128 nodes)
     auto divergence = [&](int r, float out[4]) {
-        const int id = idx[r], jl = id / nx, i0 = id - jl * nx;
+        const int jl = pk[r] >> 16, i0 = pk[r] & 0xffff, id = jl * nx + i0;
         const float4 m1 = *reinterpret_cast<const float4*>(s1 + id);
+        const float ln = __shfl_up_sync(FULL, m1.w, 1);
         const float4 m2 = *reinterpret_cast<const float4*>(s2 + id);
-        const float l = i0 > 0 ? s1[id - 1] : 0.f;
+        const float l = i0 == 0 ? 0.f : (lane == 0 ? s1[id - 1] : ln);
         float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
         if (jl > 0) b = *reinterpret_cast<const float4*>(s2 + id - nx);
-        else if (rank > 0) b = dsmem_ld4(s2_dn + 4u * i0);
-        out[0] = ((m1.x - l) + (m2.x - b.x)) * ih;
-        out[1] = ((m1.y - m1.x) + (m2.y - b.y)) * ih;
-        out[2] = ((m1.z - m1.y) + (m2.z - b.z)) * ih;
-        out[3] = ((m1.w - m1.z) + (m2.w - b.w)) * ih;
+        else if (CL && rank > 0) b = dsmem_ld4(s2_dn + 4u * i0);
+        out[0] = (m1.x - l) + (m2.x - b.x);
+        out[1] = (m1.y - m1.x) + (m2.y - b.y);
+        out[2] = (m1.z - m1.y) + (m2.z - b.z);
+        out[3] = (m1.w - m1.z) + (m2.w - b.w);
     };
 #pragma unroll
     for (int r = 0; r < RESW_RUNS; ++r)
-        if (idx[r] >= 0) divergence(r, Dv[r]);
-    cl.sync();
+        if (pk[r] >= 0) divergence(r, Dv[r]);
+    group_sync();
 
-    unsigned long long t0 = 0;
-    if (rank == 0 && t == 0) t0 = globaltimer();
+    // the start time, R^k and the decision live in CTA 0's slots (registers are scarce)
+    if (rank == 0 && t == 0) {
+        reinterpret_cast<unsigned long long*>(slots)[50] = globaltimer();
+        slots[48] = 0.0;
+        slots[49] = 0.0;
+    }
+    group_sync();
+    // (a 32-bit step counter with a running "next test" step made this loop
+    // several times slower here, measured; the 64-bit modulo costs little per node)
     long long it = 0;
-    double R = 0.0;
-    int conv = 0, late = 0;
     const long long cap = P.cap;
     while (it < cap) {
         const bool check = P.fixed ? (it + 1 == cap) : ((it + 1) % P.K == 0);
         double sa = 0.0, sb = 0.0, sc = 0.0;
-        // ---- phase A: m' = prox(m + mu grad phi)
+        // ---- phase A: m' = prox(m + mu grad phi); on the last column and the top
+        // row the gradient component is zero and so is m, hence m' too
 #pragma unroll
         for (int r = 0; r < RESW_RUNS; ++r) {
-            if (idx[r] < 0) continue;
-            const int id = idx[r], jl = id / nx, i0 = id - jl * nx, j = jb + jl;
-            const bool last_col = i0 + 4 == nx;
+            if (pk[r] < 0) continue;
+            const int jl = pk[r] >> 16, i0 = pk[r] & 0xffff, id = jl * nx + i0;
             const float4 p4 = *reinterpret_cast<const float4*>(ph + id);
+            const float rn = __shfl_down_sync(FULL, p4.x, 1);
+            const int j = jb + jl;
+            const bool last_col = i0 + 4 == nx;
             const float4 a1 = *reinterpret_cast<const float4*>(s1 + id);
             const float4 a2 = *reinterpret_cast<const float4*>(s2 + id);
-            float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (j < ny - 1) u = (jl < rows - 1) ? *reinterpret_cast<const float4*>(ph + id + nx) : dsmem_ld4(ph_up + 4u * i0);
-            const float right = last_col ? 0.f : ph[id + 4];
+            float4 u = p4;
+            if (j < ny - 1)
+                u = (!CL || jl < rows - 1) ? *reinterpret_cast<const float4*>(ph + id + nx) : dsmem_ld4(ph_up + 4u * i0);
+            const float right = last_col ? p4.w : (lane == 31 ? ph[id + 4] : rn);
             const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, up[4] = {u.x, u.y, u.z, u.w};
             const float m1[4] = {a1.x, a1.y, a1.z, a1.w}, m2[4] = {a2.x, a2.y, a2.z, a2.w};
             float n1[4], n2[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float pr_ = c < 3 ? pv[c + 1] : right;
-                const float g1 = (c == 3 && last_col) ? 0.f : (pr_ - pv[c]) * ih;
-                const float g2 = (j < ny - 1) ? (up[c] - pv[c]) * ih : 0.f;
-                prox<NORM>(m1[c] + mu * g1, m2[c] + mu * g2, mu, n1[c], n2[c]);
-                if (c == 3 && last_col) n1[c] = 0.f;
-                if (j == ny - 1) n2[c] = 0.f;
+                prox<NORM>(fmaf(cm, pr_ - pv[c], m1[c]), fmaf(cm, up[c] - pv[c], m2[c]), mu, n1[c], n2[c]);
                 if (check) {
                     const double d1 = (double)n1[c] - m1[c], d2 = (double)n2[c] - m2[c];
                     sa += d1 * d1 + d2 * d2;
@@ -1402,69 +1459,77 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident_wide(ResArgs a)
             *reinterpret_cast<float4*>(s1 + id) = make_float4(n1[0], n1[1], n1[2], n1[3]);
             *reinterpret_cast<float4*>(s2 + id) = make_float4(n2[0], n2[1], n2[2], n2[3]);
         }
-        cluster_arrive();
-        cluster_wait();
+        if (CL) {
+            cluster_arrive();
+            cluster_wait();
+        } else {
+            __syncthreads();
+        }
         // ---- phase B: phi' = phi + tau (div(2m' - m) - rho)
 #pragma unroll
         for (int r = 0; r < RESW_RUNS; ++r) {
-            if (idx[r] < 0) continue;
-            const int id = idx[r];
+            if (pk[r] < 0) continue;
             float Dn[4];
             divergence(r, Dn);
+            const int id = (pk[r] >> 16) * nx + (pk[r] & 0xffff);
             const float4 p4 = *reinterpret_cast<const float4*>(ph + id);
-            const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+            const float4 r4 = __ldg(reinterpret_cast<const float4*>(rho + id));
+            const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, rv[4] = {r4.x, r4.y, r4.z, r4.w};
             float pn[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                pn[c] = pv[c] + tau * ((2.f * Dn[c] - Dv[r][c]) - rv[r][c]);
+                pn[c] = fmaf(ct, fmaf(2.f, Dn[c], -Dv[r][c]), fmaf(-tau, rv[c], pv[c]));
                 if (check) {
                     const double ep = (double)pn[c] - (double)pv[c];
                     sb += ep * ep;
-                    sc += ep * ((double)Dn[c] - (double)Dv[r][c]);
+                    sc += ep * ((double)Dn[c] - (double)Dv[r][c]);  // h <dphi, div dm>, scaled below
                 }
                 Dv[r][c] = Dn[c];
             }
             *reinterpret_cast<float4*>(ph + id) = make_float4(pn[0], pn[1], pn[2], pn[3]);
         }
-        cluster_arrive();
-        cluster_wait();
+        if (CL) {
+            cluster_arrive();
+            cluster_wait();
+        } else {
+            __syncthreads();
+        }
         ++it;
         if (check) {
-            double v[3] = {sa, sb, sc};
+            double v[3] = {sa, sb, sc / P.h};
             block_sum<3>(v, red);
             if (t == 0) {
                 dsmem_st_f64(slots0 + 8u * (rank * 3 + 0), v[0]);
                 dsmem_st_f64(slots0 + 8u * (rank * 3 + 1), v[1]);
                 dsmem_st_f64(slots0 + 8u * (rank * 3 + 2), v[2]);
             }
-            cl.sync();
+            group_sync();
             if (rank == 0 && t == 0) {
                 double tt[3] = {0.0, 0.0, 0.0};
                 for (int q = 0; q < C; ++q)
                     for (int c = 0; c < 3; ++c) tt[c] += slots[q * 3 + c];
                 const double Rk = (tt[0] / (double)mu + tt[1] / (double)tau - 2.0 * tt[2]) * P.h * P.h;
                 const int cv = Rk < P.tol;
-                const int lt = (globaltimer() - t0) > P.budget_ns;
+                const int lt = (globaltimer() - reinterpret_cast<const unsigned long long*>(slots)[50]) > P.budget_ns;
                 const int stop = P.fixed || cv || lt || it >= cap;
                 slots[48] = Rk;
                 slots[49] = (double)(cv | (lt << 1) | (stop << 2));
             }
-            cl.sync();
-            R = dsmem_ld_f64(slots0 + 8u * 48);
-            const int d = (int)dsmem_ld_f64(slots0 + 8u * 49);
-            conv = d & 1;
-            late = (d >> 1) & 1;
-            if (d & 4) break;
+            group_sync();
+            if ((int)dsmem_ld_f64(slots0 + 8u * 49) & 4) break;
         }
     }
 #pragma unroll
     for (int r = 0; r < RESW_RUNS; ++r) {
-        if (idx[r] < 0) continue;
-        *reinterpret_cast<float4*>(a.m1 + off + idx[r]) = *reinterpret_cast<const float4*>(s1 + idx[r]);
-        *reinterpret_cast<float4*>(a.m2 + off + idx[r]) = *reinterpret_cast<const float4*>(s2 + idx[r]);
-        *reinterpret_cast<float4*>(a.phi + off + idx[r]) = *reinterpret_cast<const float4*>(ph + idx[r]);
+        if (pk[r] < 0) continue;
+        const int id = (pk[r] >> 16) * nx + (pk[r] & 0xffff);
+        *reinterpret_cast<float4*>(a.m1 + off + id) = *reinterpret_cast<const float4*>(s1 + id);
+        *reinterpret_cast<float4*>(a.m2 + off + id) = *reinterpret_cast<const float4*>(s2 + id);
+        *reinterpret_cast<float4*>(a.phi + off + id) = *reinterpret_cast<const float4*>(ph + id);
     }
     if (rank == 0 && t == 0) {
+        const double R = slots[48];
+        const int d = (int)slots[49], conv = d & 1, late = (d >> 1) & 1;
         if (pc) {
             pc->iters[P.level] = it;
             pc->fpr[P.level] = R;
@@ -1474,7 +1539,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident_wide(ResArgs a)
         if (P.fpr_out) P.fpr_out[pair] = R;
         if (P.iters_out) P.iters_out[pair] = it;
     }
-    cl.sync();
+    if (CL) cg::this_cluster().sync();
 }
 
 template <int NORM, int NPT, bool CL>
@@ -1512,10 +1577,13 @@ static cudaError_t res4_attr()
 template <int NORM>
 static cudaError_t resw_attr()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_resident_wide<NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_resident_wide<NORM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)resident_wide_smem(RESW_MAX_NODES));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_resident_wide<NORM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(k_resident_wide<NORM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)resident_wide_smem(RESW_MAX_NODES));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_resident_wide<NORM, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
 cudaError_t resident_prepare(int)
@@ -1555,20 +1623,28 @@ static void resident_config(int norm, int cluster, int nx, int ny, int pairs, cu
 {
     const int band = (ny / cluster) * nx;
     if (band > RES_MAX_NODES) {
-        // wide band: one 16-CTA cluster, four runs of four nodes per thread
+        // wide band: four runs of four nodes per thread
         cfg = cudaLaunchConfig_t{};
         cfg.gridDim = dim3(cluster * pairs, 1, 1);
         cfg.blockDim = dim3(RES_THREADS, 1, 1);
         cfg.dynamicSmemBytes = resident_wide_smem(band);
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = cluster;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        *fn = norm == W1_NORM_L1   ? (const void*)k_resident_wide<W1_NORM_L1>
-              : norm == W1_NORM_L2 ? (const void*)k_resident_wide<W1_NORM_L2>
-                                   : (const void*)k_resident_wide<W1_NORM_LINF>;
+        cfg.numAttrs = 0;
+        const bool cl = cluster > 1;
+        if (cl) {
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = cluster;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+        }
+        if (norm == W1_NORM_L1)
+            *fn = cl ? (const void*)k_resident_wide<W1_NORM_L1, true> : (const void*)k_resident_wide<W1_NORM_L1, false>;
+        else if (norm == W1_NORM_L2)
+            *fn = cl ? (const void*)k_resident_wide<W1_NORM_L2, true> : (const void*)k_resident_wide<W1_NORM_L2, false>;
+        else
+            *fn = cl ? (const void*)k_resident_wide<W1_NORM_LINF, true>
+                     : (const void*)k_resident_wide<W1_NORM_LINF, false>;
         return;
     }
     if (nx % 4 == 0 && band / 4 <= RES_THREADS) {
@@ -1633,6 +1709,7 @@ static void resident_config(int norm, int cluster, int nx, int ny, int pairs, cu
 
 int resident_cluster_ok(int norm, int cluster, int nx, int ny)
 {
+    if (!resident_fits(nx, ny, cluster)) return 0;
     if (cluster == 1) return 1;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
@@ -1648,6 +1725,7 @@ int resident_cluster_ok(int norm, int cluster, int nx, int ny)
 
 cudaError_t launch_resident(int norm, int cluster, const ResArgs& a, cudaStream_t s)
 {
+    if (!resident_fits(a.it.nx, a.it.ny, cluster)) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
     const void* fn = nullptr;

@@ -114,7 +114,7 @@ extern "C" void w1_default_options(w1_options* o)
     o->path = 0;
     o->rows_per_thread = 0;
     o->eager = 0;
-    o->reserved = 0;
+    o->tune = 0;
 }
 
 extern "C" const char* w1_last_error(void) { return g_err.c_str(); }
@@ -151,14 +151,17 @@ static size_t layout(w1_plan* p, char* base)
     p->ctl = reinterpret_cast<Ctl*>(take(sizeof(Ctl) * B));
     size_t pd = final_part_doubles(B);
     if (prep_part_doubles(B) > pd) pd = prep_part_doubles(B);
-    for (int l = 0; l < p->L; ++l)
-        if (p->lv[l].path == 2) {
+    for (int l = 0; l < p->L; ++l) {
+        // with tuning a level may take either streaming kernel: room for both
+        if (p->lv[l].path == 2 || p->opt.tune) {
             size_t s = step_part_doubles(p->lv[l].nx, p->lv[l].ny, p->lv[l].rows, B);
             if (s > pd) pd = s;
-        } else if (p->lv[l].path == 3) {
+        }
+        if (p->lv[l].path == 3 || p->opt.tune) {
             size_t s = tblock_part_doubles(p->lv[l].nx, p->lv[l].ny, B);
             if (s > pd) pd = s;
         }
+    }
     p->part_doubles = pd;
     p->part = reinterpret_cast<double*>(take(pd * sizeof(double)));
     const size_t n = (size_t)p->nx * p->ny;
@@ -167,7 +170,7 @@ static size_t layout(w1_plan* p, char* base)
         LevelPlan& v = p->lv[l];
         const size_t b = (size_t)v.nx * v.ny * sizeof(float) * B;
         v.rho = reinterpret_cast<float*>(take(b));
-        const int nb = v.path == 1 ? 1 : 2;
+        const int nb = (v.path == 1 && !p->opt.tune) ? 1 : 2;
         for (int s = 0; s < 2; ++s) {
             v.m1[s] = s < nb ? reinterpret_cast<float*>(take(b)) : nullptr;
             v.m2[s] = s < nb ? reinterpret_cast<float*>(take(b)) : nullptr;
@@ -190,7 +193,7 @@ static w1_status bind_arena(w1_plan* p, char* base, size_t bytes)
 // Fills every field of p that does not need device memory (levels, paths,
 // tolerances, arena size).  Shared by plan creation and w1_plan_bytes.
 static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int norm, double tol, int max_batch,
-                           const w1_options* opt)
+                           const w1_options* opt, bool tune_now)
 {
     if (nx < 1 || ny < 1) return fail(W1_ERR_INVALID_ARG, "nx and ny must be >= 1");
     if (max_batch < 1 || max_batch > 65535) return fail(W1_ERR_INVALID_ARG, "max_batch must lie in [1, 65535]");
@@ -202,6 +205,7 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
     if (!(o.theta > 0.0) || o.theta > 1.0) return fail(W1_ERR_INVALID_ARG, "theta must lie in (0, 1]");
     if (o.max_iters < 1) return fail(W1_ERR_INVALID_ARG, "max_iters must be >= 1");
     if (o.path < 0 || o.path > 3) return fail(W1_ERR_INVALID_ARG, "path must be 0, 1, 2 or 3");
+    if (o.tune < 0 || o.tune > 2) return fail(W1_ERR_INVALID_ARG, "tune must be 0, 1 or 2");
     if (o.check_every % (2 * tblock_depth()) != 0)
         return fail(W1_ERR_INVALID_ARG, "check_every must be a multiple of twice the temporal block depth (8)");
     // stop tests happen every K steps, so the cap is a multiple of K
@@ -254,6 +258,13 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
         else
             v.path = 2;  // one step per launch
         v.cluster = v.path == 1 ? c : 0;
+        if (o.tune && o.path == 0 && tune_now) {
+            w1_level_choice ch;
+            if (w1_autotune_level(v.nx, v.ny, norm, max_batch, o.tune, 128, &ch, nullptr, nullptr) == W1_OK) {
+                v.path = ch.path;
+                v.cluster = ch.path == 1 ? ch.cluster : 0;
+            }
+        }
         v.rows = o.rows_per_thread > 0 ? o.rows_per_thread : stream_rows_auto(v.nx, v.ny, max_batch);
     }
     p->ws_bytes = layout(p, nullptr);
@@ -264,7 +275,7 @@ extern "C" size_t w1_plan_bytes(int nx, int ny, double h, int levels, int norm, 
                                 const w1_options* opt)
 {
     w1_plan tmp{};
-    if (configure(&tmp, nx, ny, h, levels, norm, tol, max_batch, opt) != W1_OK) return 0;
+    if (configure(&tmp, nx, ny, h, levels, norm, tol, max_batch, opt, false) != W1_OK) return 0;
     return tmp.ws_bytes;
 }
 
@@ -275,7 +286,7 @@ extern "C" w1_status w1_plan_create_batch(int nx, int ny, double h, int levels, 
     *out = nullptr;
     w1_plan* p = new (std::nothrow) w1_plan();
     if (!p) return fail(W1_ERR_NOMEM, "host allocation failed");
-    w1_status st = configure(p, nx, ny, h, levels, norm, tol, max_batch, opt);
+    w1_status st = configure(p, nx, ny, h, levels, norm, tol, max_batch, opt, true);
     if (st != W1_OK) {
         delete p;
         return st;
@@ -730,9 +741,19 @@ extern "C" w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, f
                                  float* m1, float* m2, float* phi, long long iters, int path, void* stream,
                                  double* fpr_last)
 {
+    return w1_cp_steps_ex(nx, ny, h, norm, mu, tau, rho, m1, m2, phi, iters, path, 0, stream, fpr_last);
+}
+
+extern "C" w1_status w1_cp_steps_ex(int nx, int ny, double h, int norm, float mu, float tau, const float* rho,
+                                    float* m1, float* m2, float* phi, long long iters, int path, int cluster,
+                                    void* stream, double* fpr_last)
+{
     if (nx < 1 || ny < 1 || !(h > 0.0) || !rho || !m1 || !m2 || !phi || iters < 0)
         return fail(W1_ERR_INVALID_ARG, "bad arguments to w1_cp_steps");
     if (norm != W1_NORM_L1 && norm != W1_NORM_L2 && norm != W1_NORM_LINF) return fail(W1_ERR_INVALID_ARG, "norm must be 1, 2 or 3");
+    if ((reinterpret_cast<uintptr_t>(rho) | reinterpret_cast<uintptr_t>(m1) | reinterpret_cast<uintptr_t>(m2) |
+         reinterpret_cast<uintptr_t>(phi)) % 16 != 0)
+        return fail(W1_ERR_INVALID_ARG, "planes must be 16-byte aligned");
     int dev = 0;
     W1_CK(cudaGetDevice(&dev));
     w1_status st = prepare_device(dev);
@@ -762,10 +783,10 @@ extern "C" w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, f
     it.fpr_out = dfpr;
     w1_status ret = W1_OK;
     if (path == 1) {
-        const int c = resident_cluster_for(nx, ny);
+        const int c = cluster > 0 ? cluster : resident_cluster_for(nx, ny);
         if (c == 0 || resident_cluster_ok(norm, c, nx, ny) <= 0) {
             cudaFree(dfpr);
-            return fail(W1_ERR_UNSUPPORTED, "grid too large for the resident path");
+            return fail(W1_ERR_UNSUPPORTED, "this grid does not fit the resident path with this cluster size");
         }
         ResArgs a{};
         a.m1 = m1;

@@ -46,7 +46,12 @@ class W1Error(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("check_every", ctypes.c_int), ("max_iters", ctypes.c_longlong), ("theta", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("time_budget_s", ctypes.c_double), ("path", ctypes.c_int),
-                ("rows_per_thread", ctypes.c_int), ("eager", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("rows_per_thread", ctypes.c_int), ("eager", ctypes.c_int), ("tune", ctypes.c_int)]
+
+
+class LevelChoice(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int), ("cluster", ctypes.c_int), ("batch", ctypes.c_int),
+                ("us_per_step", ctypes.c_double)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -125,12 +130,16 @@ def _load() -> ctypes.CDLL:
         "w1_solve_host": (st, [P, P, P, P, ctypes.POINTER(D), P, ctypes.POINTER(_Stats)]),
         "w1_plan_potential": (st, [P, P, P]),
         "w1_cp_steps": (st, [I, I, D, I, F, F, P, P, P, P, LL, I, P, ctypes.POINTER(D)]),
+        "w1_cp_steps_ex": (st, [I, I, D, I, F, F, P, P, P, P, LL, I, I, P, ctypes.POINTER(D)]),
         "w1_restrict": (st, [I, I, P, P, P]),
         "w1_prolong": (st, [I, I, P, P, P, P, P, P, P]),
         "w1_state_stats": (st, [I, I, D, I, P, P, P, P, P, ctypes.POINTER(_Stats)]),
         "w1_state_stats_noalloc": (st, [I, I, D, I, P, P, P, P, P, ctypes.POINTER(_Stats)]),
         "w1_noalloc_last_error": (ctypes.c_char_p, []),
         "w1_plan_bytes": (ctypes.c_size_t, [I, I, D, I, I, D, I, ctypes.POINTER(Options)]),
+        "w1_autotune_level": (st, [I, I, I, I, I, I, ctypes.POINTER(LevelChoice), ctypes.POINTER(LevelChoice),
+                                   ctypes.POINTER(I)]),
+        "w1_autotune_last_error": (ctypes.c_char_p, []),
         "w1_server_default_config": (None, [ctypes.POINTER(ServerConfig)]),
         "w1_server_create_ex": (st, [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]),
         "w1_server_create": (st, [ctypes.c_size_t, I, ctypes.POINTER(P)]),
@@ -319,13 +328,14 @@ class Plan:
         return out
 
 
-def cp_steps(rho, m1, m2, phi, h, norm, mu, tau, iters, path=2, stream=None) -> float:
-    """`iters` steps of eq. primaldual in place on device state; returns R^k of the last step."""
+def cp_steps(rho, m1, m2, phi, h, norm, mu, tau, iters, path=2, stream=None, cluster=0) -> float:
+    """`iters` steps of eq. primaldual in place on device state; returns R^k of the
+    last step.  cluster: CTAs of the resident path (0: the library's choice)."""
     ny, nx = rho.shape
     f = ctypes.c_double(0.0)
-    _check(_lib.w1_cp_steps(nx, ny, h, norm, mu, tau, _dev_ptr(rho), _dev_ptr(m1, rho.shape),
-                            _dev_ptr(m2, rho.shape), _dev_ptr(phi, rho.shape), int(iters), path,
-                            _stream_ptr(stream), ctypes.byref(f)))
+    _check(_lib.w1_cp_steps_ex(nx, ny, h, norm, mu, tau, _dev_ptr(rho), _dev_ptr(m1, rho.shape),
+                               _dev_ptr(m2, rho.shape), _dev_ptr(phi, rho.shape), int(iters), path, int(cluster),
+                               _stream_ptr(stream), ctypes.byref(f)))
     return f.value
 
 
@@ -421,3 +431,16 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def autotune_level(nx, ny, norm=NORM_L1, objective=2, steps=256, batch=1):
+    """(best, all candidates) as dicts: path, cluster, batch, us_per_step (one
+    step of the whole batch; objective 1 times one pair alone)."""
+    best = LevelChoice()
+    allc = (LevelChoice * 8)()
+    n = ctypes.c_int(0)
+    st = _lib.w1_autotune_level(nx, ny, norm, batch, objective, steps, ctypes.byref(best), allc, ctypes.byref(n))
+    if st != OK:
+        raise W1Error(st, _lib.w1_autotune_last_error().decode())
+    conv = lambda c: {f: getattr(c, f) for f, _ in LevelChoice._fields_}  # noqa: E731
+    return conv(best), [conv(allc[k]) for k in range(n.value)]

@@ -46,9 +46,11 @@ def rand_state(rng, ny, nx, scale=0.5):
 
 def resident_fits(nx, ny):
     """A cluster of 1..16 CTAs, each holding whole rows, at most 4096 nodes per
-    CTA (16384 in 16 CTAs when nx is a multiple of 4)."""
-    return any(ny % c == 0 and (ny // c) * nx <= 4096 for c in (1, 2, 4, 8, 16)) or \
-        (nx % 4 == 0 and ny % 16 == 0 and (ny // 16) * nx <= 16384)
+    CTA (16384 when nx is a multiple of 4 and the band a multiple of 128 nodes)."""
+    def fits(c):
+        band = (ny // c) * nx
+        return ny % c == 0 and (band <= 4096 or (nx % 4 == 0 and band <= 16384 and band % 128 == 0))
+    return any(fits(c) for c in (1, 2, 4, 8, 16))
 
 
 def mu_of(h, theta=0.5):
@@ -94,6 +96,35 @@ def test_cp_steps_match_oracle(w1, norm, shape, path):
             err = np.abs(host(got) - want).max()
             assert err <= 2e-5 * scale, (iters, err, scale)
         assert fpr == pytest.approx(ofpr, rel=2e-3, abs=1e-12 * scale)
+
+
+@pytest.mark.parametrize("norm", [L1, L2, LINF])
+@pytest.mark.parametrize("shape,cluster", [((64, 64), 1), ((64, 64), 16), ((128, 128), 1), ((128, 128), 2),
+                                           ((128, 128), 4), ((128, 128), 8), ((256, 256), 4), ((512, 512), 16),
+                                           ((96, 160), 1)])
+def test_resident_cluster_sizes_match_oracle(w1, norm, shape, cluster):
+    """Every on-chip layout: one CTA or a cluster, four nodes per thread (up to
+    4096 per CTA) or wide bands (up to 16384 per CTA, single CTA included)."""
+    ny, nx = shape
+    rng = np.random.default_rng(ny + nx + cluster + 10 * norm)
+    rho, m1, m2, phi = rand_state(rng, ny, nx)
+    h = 1.0 / max(nx, ny)
+    mu = mu_of(h)
+    g = [dev(a) for a in (rho, m1, m2, phi)]
+    fpr = w1.cp_steps(*g, h, norm, mu, mu, 64, path=1, cluster=cluster)
+    o1, o2, op, ofpr = oracle.cp_iterate(rho, m1, m2, phi, h, norm, 64, mu=mu, tau=mu)
+    scale = max(np.abs(o1).max(), np.abs(o2).max(), np.abs(op).max(), 1.0)
+    for got, want in ((g[1], o1), (g[2], o2), (g[3], op)):
+        assert np.abs(host(got) - want).max() <= 2e-5 * scale
+    assert fpr == pytest.approx(ofpr, rel=2e-3, abs=1e-12 * scale)
+
+
+def test_resident_cluster_that_does_not_fit_is_refused(w1):
+    g = [torch.zeros((256, 256), device="cuda") for _ in range(4)]
+    with pytest.raises(w1.W1Error):
+        w1.cp_steps(*g, 1 / 256, L1, 0.01, 0.01, 8, path=1, cluster=1)  # 65536 nodes in one CTA
+    with pytest.raises(w1.W1Error):
+        w1.cp_steps(*g, 1 / 256, L1, 0.01, 0.01, 8, path=1, cluster=3)
 
 
 @pytest.mark.parametrize("norm", [L1, L2, LINF])
