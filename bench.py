@@ -343,7 +343,7 @@ def run_gpu(args):
     # roofline of the streaming step kernel (8192^2, T = 1)
     roof = None
     if not args.no_roofline:
-        roof = roofline_stream(w1, torch, stream, args)
+        roof = roofline(w1, torch, stream, args)
 
     line = None
     if rank == 0:
@@ -386,42 +386,86 @@ def run_gpu(args):
     return 0
 
 
-def roofline_stream(w1, torch, stream, args):
-    """HBM roofline of the streaming level kernels on an n x n grid far above L2:
-    algorithmic bytes = 28 B per node and step (read m1, m2, phi, rho; write
-    m1, m2, phi), timed with CUDA events on the launching stream.  Path 3 (the
-    default for streaming levels) moves fewer DRAM bytes than that (4 steps per
-    launch on chip); its figure is effective bandwidth, labelled as such."""
+# ncu DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum), from
+# the captures summarised under profiles/; None where no capture of the current
+# kernel exists.  Streaming kernels: captured at 4096^2 and scaled by 4 to 8192^2
+# (their traffic grows with the number of nodes).
+TRAFFIC = {"k_step": None, "k_tblock": None, "k_resident4": None}
+
+FP32_LANES_PER_SM = 128  # FP32 units per SM; two flops per FMA
+SM_MAX_MHZ = 2070.0
+FLOPS_PER_NODE_STEP = {1: 25, 2: 30, 3: 30}  # eq. primaldual: gradient, shrink, extrapolation, divergence, dual step
+
+
+def _time_steps(w1, torch, stream, rho, h, norm, mu, path, a, b, cluster=0):
+    """Time per step from two runs of a and b steps (the difference removes the
+    fixed cost of a call: allocation and the load and store of the level)."""
+    n = rho.shape[0]
+    kw = {"cluster": cluster} if path == 1 else {}
+    ms = []
+    for k in (a, b):
+        m1, m2, phi = (torch.zeros((n, n), device="cuda") for _ in range(3))
+        w1.cp_steps(rho, m1, m2, phi, h, norm, mu, mu, 8 if path != 1 else 32, path=path, stream=stream, **kw)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        w1.cp_steps(rho, m1, m2, phi, h, norm, mu, mu, k, path=path, stream=stream, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        del m1, m2, phi
+    return (ms[1] - ms[0]) / (b - a)
+
+
+def roofline(w1, torch, stream, args):
+    """Rooflines, timed with CUDA events on the launching stream.
+
+    resident (the dominant kernel of a solve: the on-chip level solve, here a
+    256^2 level in a 16-CTA cluster, p = 1): arithmetic of eq. primaldual per
+    node and step against the FP32 rate of the SMs the launch occupies (its
+    limit in practice is instruction issue and the two cluster barriers per step).
+    streaming: one step per launch on an 8192^2 grid (1.9 GB, far above L2),
+    28 algorithmic bytes per node and step against the measured HBM copy rate.
+    temporal_blocking: 4 steps per launch on chip; its figure is effective
+    bandwidth (28 B per node-step), not DRAM traffic."""
+    peak, kind = peaks()
+    out = {}
     n = args.roof_n
     h = 1.0 / n
     rho = torch.randn((n, n), device="cuda") * 0.1
     rho -= rho.mean()
-    peak, kind = peaks()
     mu = float(np.float32(0.5 * h / (2 * np.sqrt(2.0))))
-    out = {}
-    for path, name in ((3, "k_tblock (temporal blocking, 4 steps per launch)"), (2, "k_step (one step per launch)")):
-        m1, m2, phi = (torch.zeros((n, n), device="cuda") for _ in range(3))
-        w1.cp_steps(rho, m1, m2, phi, h, 1, mu, mu, 8, path=path, stream=stream)
-        iters = args.roof_iters
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        w1.cp_steps(rho, m1, m2, phi, h, 1, mu, mu, iters, path=path, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_step = e0.elapsed_time(e1) / iters
+    for path, key, name in ((2, "k_step", "k_step (one step per launch)"),
+                            (3, "k_tblock", "k_tblock (temporal blocking, 4 steps per launch)")):
+        ms_step = _time_steps(w1, torch, stream, rho, h, 1, mu, path, 16, 16 + args.roof_iters)
         per_launch = 4 if path == 3 else 1
         achieved = 28.0 * n * n / (ms_step * 1e-3) / 1e9
-        out[path] = {"kernel": name, "grid": [n, n], "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "peak_kind": kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                     "ms_per_launch": ms_step * per_launch, "steps_per_launch": per_launch,
-                     "algorithmic_bytes_per_launch": 28 * n * n * per_launch}
-        del m1, m2, phi
-    out[3]["note"] = "effective bandwidth: 28 B per node-step; DRAM moves about (16 x 1.41 + 12) / 4 B"
-    r = dict(out[3])
-    r["one_step_per_launch"] = out[2]
-    return r
+        out[key] = {"kernel": name, "grid": [n, n], "bound": "hbm", "achieved": achieved, "peak": peak,
+                    "peak_kind": kind, "unit": "GB/s", "frac": achieved / peak, "traffic": TRAFFIC[key],
+                    "ms_per_launch": ms_step * per_launch, "steps_per_launch": per_launch,
+                    "algorithmic_bytes_per_launch": 28 * n * n * per_launch}
+    out["k_tblock"]["note"] = ("effective bandwidth, not DRAM traffic: 28 B per node-step; the tile and its "
+                               "halo are read once per 4 steps")
+    del rho
+    nr, kr = 256, 2000
+    hr = 1.0 / nr
+    rr = torch.randn((nr, nr), device="cuda") * 0.1
+    rr -= rr.mean()
+    mur = float(np.float32(0.5 * hr / (2 * np.sqrt(2.0))))
+    ms_step = _time_steps(w1, torch, stream, rr, hr, 1, mur, 1, 256, 256 + kr, cluster=16)
+    flops_step = FLOPS_PER_NODE_STEP[1] * nr * nr
+    fpeak = 16 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops_step / (ms_step * 1e-3) / 1e12
+    res = {"kernel": "k_resident4 (on-chip level solve, 256^2 level, cluster of 16 CTAs, p = 1)", "grid": [nr, nr],
+           "bound": "alu", "achieved": achieved, "peak": fpeak,
+           "peak_kind": "derived: 16 SMs x 128 FP32 lanes x 2 flops x 2070 MHz", "unit": "TFLOP/s",
+           "frac": achieved / fpeak, "traffic": TRAFFIC["k_resident4"], "us_per_step": ms_step * 1e3,
+           "steps_per_launch": kr, "flops_per_node_step": FLOPS_PER_NODE_STEP[1],
+           "note": "issue and barrier-latency bound: no HBM traffic per step; traffic is per launch of "
+                   f"{kr} steps (the level is loaded once)"}
+    res["streaming"] = out["k_step"]
+    res["temporal_blocking"] = out["k_tblock"]
+    return res
 
 
 def main():

@@ -376,7 +376,9 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
     const float mu = P.mu, tau = P.tau;
     const float cm = P.mu * P.ih, ct = P.tau * P.ih;  // mu / h, tau / h
     const size_t off = (size_t)pair * P.stride;
-    double sa = 0.0, sb = 0.0, sc = 0.0;
+    // test-step sums: FP32 terms and per-thread partials (a strip of rows), FP64
+    // across threads and blocks (FP64 is a small fraction of FP32 throughput here)
+    float sa = 0.f, sb = 0.f, sc = 0.f;
     if (j0 < ny) {
         const int j1 = min(j0 + a.rows, ny);
         const float* __restrict__ phi = a.phi + off;
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
         float pc_ = act ? __ldg(phi + at(j0, i)) : 0.f;
         // mbar2 and dm2 of the node below the strip (row j0 - 1)
         float b2b = 0.f;
-        double d2b = 0.0;
+        float d2b = 0.f;
         if (j0 > 0) {
             float pb = act ? __ldg(phi + at(j0 - 1, i)) : 0.f;
             float c2 = act ? __ldg(m2 + at(j0 - 1, i)) : 0.f;
@@ -407,7 +409,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
             }
             (void)o1;
             b2b = 2.f * o2 - c2;
-            d2b = (double)o2 - (double)c2;
+            d2b = o2 - c2;
         }
         // row j's values are loaded one row ahead (software pipelining)
         float nu = (act && j0 + 1 < ny) ? __ldg(phi + at(j0 + 1, i)) : 0.f;
@@ -433,8 +435,8 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
             if (j == ny - 1) n2 = 0.f;
             const float b1 = 2.f * n1 - a1, b2 = 2.f * n2 - a2;
             float b1l = __shfl_up_sync(FULL, b1, 1);
-            double d1l = 0.0;
-            if (CHECK) d1l = __shfl_up_sync(FULL, (double)n1 - (double)a1, 1);
+            float d1l = 0.f;
+            if (CHECK) d1l = __shfl_up_sync(FULL, n1 - a1, 1);
             if (lane == 0) {
                 if (i > 0) {
                     // the left neighbour belongs to the previous warp: recompute its m1'
@@ -451,10 +453,10 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
                         prox<NORM>(vl1, vl2, mu, o1, o2);
                     }
                     b1l = 2.f * o1 - c1;
-                    d1l = (double)o1 - (double)c1;
+                    d1l = o1 - c1;
                 } else {
                     b1l = 0.f;
-                    d1l = 0.0;
+                    d1l = 0.f;
                 }
             }
             const float dv = (b1 - b1l) + (b2 - b2b);  // h div mbar
@@ -465,12 +467,12 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
                 phio[at(j, i)] = pn;
             }
             if (CHECK && act) {
-                const double e1 = (double)n1 - (double)a1, e2 = (double)n2 - (double)a2;
-                const double ep = (double)pn - (double)pc_;
-                const double dd = ((e1 - d1l) + (e2 - d2b)) / P.h;
-                sa += e1 * e1 + e2 * e2;
-                sb += ep * ep;
-                sc += ep * dd;
+                const float e1 = n1 - a1, e2 = n2 - a2;
+                const float ep = pn - pc_;
+                const float dd = (e1 - d1l) + (e2 - d2b);  // h div dm
+                sa = fmaf(e1, e1, fmaf(e2, e2, sa));
+                sb = fmaf(ep, ep, sb);
+                sc = fmaf(ep, dd, sc);
                 d2b = e2;
             }
             b2b = b2;
@@ -482,7 +484,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
     // R^k = (|dm|^2 / mu + |dphi|^2 / tau - 2 <dphi, div dm>) h^2   (eq. pd_stop)
     __shared__ double sh[32 * 3];
     __shared__ bool last;
-    double v[3] = {sa, sb, sc};
+    double v[3] = {(double)sa, (double)sb, (double)sc / P.h};
     block_sum<3>(v, sh);
     const int nblk = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
@@ -623,7 +625,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
         }
     }
     __syncthreads();
-    double sa = 0.0, sb = 0.0, sc = 0.0;
+    float sa = 0.f, sb = 0.f, sc = 0.f;  // FP32 terms and per-thread partials, FP64 across threads
     const bool interior_row = jl >= TB && jl < TB + TBY && row_in;
 #pragma unroll 1
     for (int step = 0; step < TB; ++step) {
@@ -653,7 +655,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
                     d2[c] = n2[c] - m2[c];
                     const int ci = il + c;
                     if (interior_row && ci >= TB && ci < TB + TBX && gi0 + c < nx)
-                        sa += (double)d1[c] * d1[c] + (double)d2[c] * d2[c];
+                        sa = fmaf(d1[c], d1[c], fmaf(d2[c], d2[c], sa));
                 }
                 *reinterpret_cast<float4*>(e1s + idx) = make_float4(d1[0], d1[1], d1[2], d1[3]);
                 *reinterpret_cast<float4*>(e2s + idx) = make_float4(d2[0], d2[1], d2[2], d2[3]);
@@ -687,17 +689,16 @@ __global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
                 const float4 eb = jl > 0 ? *reinterpret_cast<const float4*>(e2s + idx - TLW) : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float a1[4] = {e1.x, e1.y, e1.z, e1.w}, a2[4] = {e2.x, e2.y, e2.z, e2.w};
                 const float bl[4] = {eb.x, eb.y, eb.z, eb.w};
-                const double ihd = 1.0 / P.h;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const int ci = il + c, gi = gi0 + c;
                     if (!(interior_row && ci >= TB && ci < TB + TBX && gi < nx)) continue;
-                    const double left = c ? (double)a1[c - 1] : (gi > 0 ? (double)el : 0.0);
-                    const double below = gj > 0 ? (double)bl[c] : 0.0;
-                    const double dd = (((double)a1[c] - left) + ((double)a2[c] - below)) * ihd;
-                    const double ep = (double)pn[c] - (double)pv[c];
-                    sb += ep * ep;
-                    sc += ep * dd;
+                    const float left = c ? a1[c - 1] : (gi > 0 ? el : 0.f);
+                    const float below = gj > 0 ? bl[c] : 0.f;
+                    const float dd = (a1[c] - left) + (a2[c] - below);  // h div dm
+                    const float ep = pn[c] - pv[c];
+                    sb = fmaf(ep, ep, sb);
+                    sc = fmaf(ep, dd, sc);
                 }
             }
 #pragma unroll
@@ -716,7 +717,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
     if (!CHECK) return;
     __shared__ double sh[32 * 3];
     __shared__ bool lastblk;
-    double v[3] = {sa, sb, sc};
+    double v[3] = {(double)sa, (double)sb, (double)sc / P.h};
     block_sum<3>(v, sh);
     const int nblk = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
@@ -944,7 +945,7 @@ __global__ void __launch_bounds__(NPT >= 8 ? RES_THREADS / 2 : RES_THREADS, 1) k
     const long long cap = P.cap;
     while (it < cap) {
         const bool check = P.fixed ? (it + 1 == cap) : ((it + 1) % P.K == 0);
-        double sa = 0.0, sb = 0.0, sc = 0.0;
+        float sa = 0.f, sb = 0.f, sc = 0.f;  // FP32 terms and per-thread partials, FP64 across threads
         // ---- phase A: m' = prox(m + mu grad phi)
         auto phaseA = [&](int k) {
             const int idx = threadIdx.x + k * T, i = ij[k] & 0xffff, jl = ij[k] >> 16, j = jb + jl;
@@ -962,7 +963,7 @@ __global__ void __launch_bounds__(NPT >= 8 ? RES_THREADS / 2 : RES_THREADS, 1) k
                 const float d1 = n1 - a1, d2 = n2 - a2;
                 e1s[idx] = d1;
                 e2s[idx] = d2;
-                sa += (double)d1 * d1 + (double)d2 * d2;
+                sa = fmaf(d1, d1, fmaf(d2, d2, sa));
             }
             if (SREG) {
                 m1r[k] = n1;
@@ -984,13 +985,12 @@ __global__ void __launch_bounds__(NPT >= 8 ? RES_THREADS / 2 : RES_THREADS, 1) k
             const float rk = REG ? rr[REG ? k : 0] : rs[idx];
             const float pn = pc_ + tau * ((2.f * Dn - Dk) - rk);
             if (check) {
-                const double el = i > 0 ? (double)e1s[idx - 1] : 0.0;
-                const double eb = jl > 0 ? (double)e2s[idx - nx]
-                                         : ((CL && rank > 0) ? (double)dsmem_ld(e2_dn + 4u * i) : 0.0);
-                const double dd = (((double)e1s[idx] - el) + ((double)e2s[idx] - eb)) / P.h;
-                const double ep = (double)pn - (double)pc_;
-                sb += ep * ep;
-                sc += ep * dd;
+                const float el = i > 0 ? e1s[idx - 1] : 0.f;
+                const float eb = jl > 0 ? e2s[idx - nx] : ((CL && rank > 0) ? dsmem_ld(e2_dn + 4u * i) : 0.f);
+                const float dd = (e1s[idx] - el) + (e2s[idx] - eb);  // h div dm
+                const float ep = pn - pc_;
+                sb = fmaf(ep, ep, sb);
+                sc = fmaf(ep, dd, sc);
             }
             if (REG) Dr[REG ? k : 0] = Dn;
             else Ds[idx] = Dn;
@@ -1017,7 +1017,7 @@ __global__ void __launch_bounds__(NPT >= 8 ? RES_THREADS / 2 : RES_THREADS, 1) k
         }
         ++it;
         if (check) {
-            double v[3] = {sa, sb, sc};
+            double v[3] = {(double)sa, (double)sb, (double)sc / P.h};
             block_sum<3>(v, red);
             if (threadIdx.x == 0) {
                 dsmem_st_f64(slots0 + 8u * (rank * 3 + 0), v[0]);
@@ -1190,7 +1190,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
     int next = P.fixed ? cap : P.K;  // step after which the next test runs
     while (it < cap) {
         const bool check = it + 1 == next;
-        double sa = 0.0, sb = 0.0, sc = 0.0;
+        float sa = 0.f, sb = 0.f, sc = 0.f;  // FP32 terms and per-thread partials, FP64 across threads
         // ---- phase A: m' = prox(m + mu grad phi); on the last column and the top
         // row the gradient component is zero and so is m, hence m' too
         const float rn = __shfl_down_sync(FULL, pv[0], 1);
@@ -1213,7 +1213,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
                 for (int c = 0; c < 4; ++c) {
                     d1[c] = n1[c] - m1[c];
                     d2[c] = n2[c] - m2[c];
-                    sa += (double)d1[c] * d1[c] + (double)d2[c] * d2[c];
+                    sa = fmaf(d1[c], d1[c], fmaf(d2[c], d2[c], sa));
                 }
                 *reinterpret_cast<float4*>(e1s + idx) = make_float4(d1[0], d1[1], d1[2], d1[3]);
                 *reinterpret_cast<float4*>(e2s + idx) = make_float4(d2[0], d2[1], d2[2], d2[3]);
@@ -1252,14 +1252,13 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
                 const float4 eb = below4(e2s, e2_dn);
                 const float a1[4] = {e1.x, e1.y, e1.z, e1.w}, a2[4] = {e2.x, e2.y, e2.z, e2.w};
                 const float bl[4] = {eb.x, eb.y, eb.z, eb.w};
-                const double ihd = 1.0 / P.h;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const double left = c ? (double)a1[c - 1] : (double)el;
-                    const double dd = (((double)a1[c] - left) + ((double)a2[c] - (double)bl[c])) * ihd;
-                    const double ep = (double)pn[c] - (double)pv[c];
-                    sb += ep * ep;
-                    sc += ep * dd;
+                    const float left = c ? a1[c - 1] : el;
+                    const float dd = (a1[c] - left) + (a2[c] - bl[c]);  // h div dm
+                    const float ep = pn[c] - pv[c];
+                    sb = fmaf(ep, ep, sb);
+                    sc = fmaf(ep, dd, sc);
                 }
             }
 #pragma unroll
@@ -1275,7 +1274,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
         ++it;
         if (check) {
             next += P.K;
-            double v[3] = {sa, sb, sc};
+            double v[3] = {(double)sa, (double)sb, (double)sc / P.h};
             block_sum<3>(v, red);
             if (t == 0) {
                 dsmem_st_f64(slots0 + 8u * (rank * 3 + 0), v[0]);
@@ -1427,7 +1426,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident_wide(ResArgs a)
     const long long cap = P.cap;
     while (it < cap) {
         const bool check = P.fixed ? (it + 1 == cap) : ((it + 1) % P.K == 0);
-        double sa = 0.0, sb = 0.0, sc = 0.0;
+        float sa = 0.f, sb = 0.f, sc = 0.f;  // FP32 terms and per-thread partials, FP64 across threads
         // ---- phase A: m' = prox(m + mu grad phi); on the last column and the top
         // row the gradient component is zero and so is m, hence m' too
 #pragma unroll
@@ -1452,8 +1451,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident_wide(ResArgs a)
                 const float pr_ = c < 3 ? pv[c + 1] : right;
                 prox<NORM>(fmaf(cm, pr_ - pv[c], m1[c]), fmaf(cm, up[c] - pv[c], m2[c]), mu, n1[c], n2[c]);
                 if (check) {
-                    const double d1 = (double)n1[c] - m1[c], d2 = (double)n2[c] - m2[c];
-                    sa += d1 * d1 + d2 * d2;
+                    const float d1 = n1[c] - m1[c], d2 = n2[c] - m2[c];
+                    sa = fmaf(d1, d1, fmaf(d2, d2, sa));
                 }
             }
             *reinterpret_cast<float4*>(s1 + id) = make_float4(n1[0], n1[1], n1[2], n1[3]);
@@ -1480,9 +1479,9 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident_wide(ResArgs a)
             for (int c = 0; c < 4; ++c) {
                 pn[c] = fmaf(ct, fmaf(2.f, Dn[c], -Dv[r][c]), fmaf(-tau, rv[c], pv[c]));
                 if (check) {
-                    const double ep = (double)pn[c] - (double)pv[c];
-                    sb += ep * ep;
-                    sc += ep * ((double)Dn[c] - (double)Dv[r][c]);  // h <dphi, div dm>, scaled below
+                    const float ep = pn[c] - pv[c];
+                    sb = fmaf(ep, ep, sb);
+                    sc = fmaf(ep, Dn[c] - Dv[r][c], sc);  // h <dphi, div dm>, scaled below
                 }
                 Dv[r][c] = Dn[c];
             }
@@ -1496,7 +1495,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident_wide(ResArgs a)
         }
         ++it;
         if (check) {
-            double v[3] = {sa, sb, sc / P.h};
+            double v[3] = {(double)sa, (double)sb, (double)sc / P.h};
             block_sum<3>(v, red);
             if (t == 0) {
                 dsmem_st_f64(slots0 + 8u * (rank * 3 + 0), v[0]);
