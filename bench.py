@@ -362,7 +362,25 @@ def run_gpu(args):
         e2e = {"value": solves / e2e_el, "unit": "solves/s",
                "h2d_bytes_per_step": 2 * N * N * 4 * B, "d2h_bytes_per_step": 552 * B * len(NORMS)}
 
-    # roofline of the streaming step kernel (8192^2, T = 1)
+    # latency of one solve with the GPU otherwise idle: one pair at a time through
+    # the blocking entry point, CUDA events around each solve
+    solo = {}
+    for norm in NORMS:
+        with w1.Plan(N, N, levels=LEVELS, norm=norm) as p1:
+            ts = []
+            for k in range(args.solo):
+                t0s, t1s = dev_pairs[k % total_steps][0][k % B], dev_pairs[k % total_steps][1][k % B]
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                p1.solve(t0s, t1s, stream=stream, allow=ok)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        solo[f"L{norm}"] = {"p50": float(np.percentile(ts, 50)), "p99": float(np.percentile(ts, 99)),
+                            "pairs": len(ts)}
+    solo["what"] = "one solve with the GPU otherwise idle (w1_solve, CUDA events)"
+
+    # rooflines (the dominant on-chip kernel; the streaming kernels at 8192^2)
     roof = None
     if not args.no_roofline:
         roof = roofline(w1, torch, stream, args)
@@ -383,6 +401,7 @@ def run_gpu(args):
             "timer": {"kind": "CUDA events on the launching stream, every lane joined to it", "wall_s": wall},
             "batch_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                  "what": "one step (B pairs, both norms) / 2, submit to W1 values on the host"},
+            "solo_latency_ms": solo,
             "pair_latency_ms": ({"p50": float(np.percentile(pair_lat, 50)), "p99": float(np.percentile(pair_lat, 99)),
                                  "what": "per pair: step start to the end of its solve on its stream (CUDA events)"}
                                 if pair_lat else None),
@@ -505,6 +524,7 @@ def main():
     ap.add_argument("--roof-iters", type=int, default=96)
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--solo", type=int, default=8, help="pairs solved one at a time for the latency figure")
     ap.add_argument("--eager", action="store_true",
                     help="launch level kernels directly (no CUDA graph) so profilers see every kernel")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000", help="serving: arrival rates (req/s)")
@@ -520,7 +540,7 @@ def main():
     ap.add_argument("--knorm", type=int, default=1)
     ap.add_argument("--kcluster", type=int, default=0, help="--only resident-kernel: CTAs per level (0: auto)")
     ap.add_argument("--mixed-norm", type=int, default=2, help="mixed-size batch: ground norm")
-    ap.add_argument("--mixed-modes", default="loop,lanes,lockstep,lockstep-tuned")
+    ap.add_argument("--mixed-modes", default="loop,lanes,lockstep,lockstep-tuned,persistent")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -575,6 +595,8 @@ def run_mixed(args):
         elif mode == "lanes":
             plans = [[w1.Plan(n, n, levels=L, norm=norm) for _ in range(B)] for n, B, L in MIXED]
             lanes = [[torch.cuda.Stream() for _ in range(B)] for _, B, _ in MIXED]
+        elif mode == "persistent":
+            plans = w1.Mixed([(n, n, B) for n, B, _ in MIXED], norm=norm)
         else:
             tune = 2 if mode == "lockstep-tuned" else 0
             plans = [w1.Plan(n, n, levels=L, norm=norm, batch=B, tune=tune) for n, B, L in MIXED]
@@ -589,6 +611,12 @@ def run_mixed(args):
                     for b in range(B):
                         v, _, _ = plans[ci].solve(t0[b], t1[b], stream=stream, allow=ok)
                         vals.append(v)
+                return vals
+            if mode == "persistent":
+                plans.solve_async([d[0] for d in data[s]], [d[1] for d in data[s]], stream=stream)
+                stream.synchronize()
+                for ci in range(len(MIXED)):
+                    vals.extend(plans.results(ci, allow=ok)[0])
                 return vals
             ready = torch.cuda.Event()
             ready.record(stream)
@@ -627,6 +655,9 @@ def run_mixed(args):
             w1_ref = flat
         out[mode] = {"solves_per_s": args.steps * total / (ms / 1e3), "ms_per_pass": ms / args.steps,
                      "max_rel_diff_vs_first_mode": float(np.max(np.abs(flat - w1_ref) / np.abs(w1_ref)))}
+        if mode == "persistent":
+            out[mode]["persistent_classes"] = [plans.persistent(c) for c in range(len(MIXED))]
+            plans.close()
         del plans
         torch.cuda.synchronize()
     print(json.dumps({"only": "mixed", "workload": "gauss8 mixed: 128 x 64^2 (3 levels), 96 x 128^2 (4), "

@@ -199,6 +199,38 @@ w1_status w1_solve_host(w1_plan* plan, const float* rho0, const float* rho1, voi
  * Kantorovich potential of Algorithm 1, Appendix B); enqueued on stream. */
 w1_status w1_plan_potential(w1_plan* plan, float* phi, void* stream);
 
+/* ------------------------------------------------------------------------- */
+/* Mixed-size batches                                                        */
+/* ------------------------------------------------------------------------- */
+
+typedef struct w1_mixed w1_mixed;
+
+/*
+ * A batch of pairs of several grid sizes, solved together (Algorithm 3 for
+ * every pair).  Class c has count[c] pairs of nx[c] x ny[c] (levels and h as
+ * w1_plan_create with levels = 0, h = 0).  Classes whose every level fits one
+ * CTA (nx % 4 == 0 at every level, at most 16384 nodes) run in ONE persistent
+ * launch: each CTA takes a pair, runs all of its levels (interpolation and the
+ * level solves) on chip, and takes the next pair, largest grids first.  Other
+ * classes run as batched plans on streams of their own, overlapping the
+ * persistent launch.  opt->path != 0 sends every class to the batched plans.
+ * The batch owns its device memory (one arena per class).
+ */
+w1_status w1_mixed_create(int n_classes, const int* nx, const int* ny, const int* count, int norm, double tol,
+                          const w1_options* opt, w1_mixed** out);
+w1_status w1_mixed_destroy(w1_mixed* batch);
+/* 1 if class cls runs in the persistent launch, 0 if as a batched plan, -1 on bad arguments. */
+int w1_mixed_persistent(const w1_mixed* batch, int cls);
+/*
+ * Enqueues a solve of every pair on `stream` and returns without waiting.
+ * rho0[c], rho1[c]: device [count[c]][ny[c]][nx[c]] float32 (host arrays of
+ * n_classes device pointers), caller-owned, valid until the stream has passed
+ * the solve.  Read the results with w1_mixed_results once the stream is done.
+ */
+w1_status w1_mixed_solve_async(w1_mixed* batch, const float* const* rho0, const float* const* rho1, void* stream);
+/* Results of class cls of the last solve: dist, stats, status as w1_solve_batch (each [count[cls]] or NULL). */
+w1_status w1_mixed_results(w1_mixed* batch, int cls, double* dist, w1_stats* stats, int* status);
+
 /* One way to run a level, as measured by the autotuner. */
 typedef struct {
     int path;           /* 1 on chip, 2 streaming, 3 streaming with temporal blocking */

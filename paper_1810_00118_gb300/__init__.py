@@ -3,5 +3,5 @@
 The computation lives in libw1.so (CUDA C++, C ABI in include/w1.h); this
 package is its thin Python binding.  See w1.Plan for the solve entry point.
 """
-from .w1 import (NORM_L1, NORM_L2, NORM_LINF, Options, Plan, Stats, W1Error, cp_steps, default_options, lib,  # noqa: F401
-                 prolong, restrict, state_stats, status_string)
+from .w1 import (NORM_L1, NORM_L2, NORM_LINF, Mixed, Options, Plan, Server, Stats, W1Error,  # noqa: F401
+                 autotune_level, cp_steps, default_options, lib, prolong, restrict, state_stats, status_string)

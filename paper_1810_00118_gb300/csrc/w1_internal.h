@@ -107,6 +107,40 @@ int resident_cluster_for(int nx, int ny);
 cudaError_t resident_prepare(int device);
 // Active clusters the device can hold for this configuration (0: cannot launch).
 int resident_cluster_ok(int norm, int cluster, int nx, int ny);
+// Mixed-size batches: one persistent launch runs the whole cascade of
+// Algorithm 3 (prolongation and every level's solve) for pairs of several grid
+// sizes, one CTA per pair; CTAs take pairs from a shared counter, largest grids
+// first.  Restriction, prep and the final statistics stay batched launches per
+// size class.
+struct CascadeLevel {
+    int nx, ny;
+    float mu, tau, ih;
+    double h, tol;
+    float* rho;  // pair 0's planes of this level; pair stride nx * ny
+    float* m1;
+    float* m2;
+    float* phi;
+};
+struct CascadeClass {
+    int levels, count;
+    Ctl* ctl;  // per-pair control blocks of the class
+    CascadeLevel lv[W1_MAX_LEVELS];
+};
+struct CascadeArgs {
+    const CascadeClass* cls;  // device array
+    int n_classes;
+    int total;            // pairs over all classes
+    unsigned int* next;   // work counter, zero before the launch
+    long long cap;        // per-level step cap
+    int K;                // steps between stop tests
+    unsigned long long budget_ns;
+};
+// Whether one CTA holds an nx x ny level (nx % 4 == 0; at most 4096 nodes, or
+// 16384 in multiples of 128).
+bool cascade_level_fits(int nx, int ny);
+// CTAs of the persistent launch (one per SM at the launch's shared memory).
+int cascade_ctas(int norm);
+cudaError_t launch_cascade(int norm, const CascadeArgs& a, int ctas, cudaStream_t s);
 // Final statistics of a state into ctl (q: FP64 scratch of 2 * nx * ny per pair).
 cudaError_t launch_final(int norm, const float* m1, const float* m2, const float* phi, const float* rho, int nx,
                          int ny, double h, double* q, double* part, Ctl* ctl, int pairs, cudaStream_t s);

@@ -239,6 +239,15 @@ cudaError_t launch_prep(const float* r0, const float* r1, long long n, int nbatc
 // Restriction (2x2 block mean) and Interpolate (Sec. 3.3, pixel-grid reading)
 // ---------------------------------------------------------------------------
 
+// coarse node (I, J) = mean of its 2x2 block of fine nodes (pointers at one pair's planes)
+__device__ __forceinline__ void restrict_node(const float* __restrict__ f, int nx, float* __restrict__ c, int ncx, int I,
+                                              int J)
+{
+    const float* r0 = f + (size_t)(2 * J) * nx + 2 * I;
+    const float* r1 = r0 + nx;
+    c[(size_t)J * ncx + I] = 0.25f * ((r0[0] + r0[1]) + (r1[0] + r1[1]));
+}
+
 __global__ void k_restrict(const float* __restrict__ f, int nx, int ny, float* __restrict__ c, const Ctl* ctls)
 {
     const int ncx = nx / 2, ncy = ny / 2;
@@ -246,11 +255,7 @@ __global__ void k_restrict(const float* __restrict__ f, int nx, int ny, float* _
     if (ctls && ctls[pair].error) return;
     const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
     if (I >= ncx || J >= ncy) return;
-    f += (size_t)pair * nx * ny;
-    c += (size_t)pair * ncx * ncy;
-    const float* r0 = f + (size_t)(2 * J) * nx + 2 * I;
-    const float* r1 = r0 + nx;
-    c[(size_t)J * ncx + I] = 0.25f * ((r0[0] + r0[1]) + (r1[0] + r1[1]));
+    restrict_node(f + (size_t)pair * nx * ny, nx, c + (size_t)pair * ncx * ncy, ncx, I, J);
 }
 
 cudaError_t launch_restrict(const float* fine, int nx, int ny, float* coarse, int pairs, const Ctl* ctl,
@@ -265,19 +270,13 @@ cudaError_t launch_restrict(const float* fine, int nx, int ny, float* coarse, in
 // fine node's side, clamped); m1: odd fine x-edges copy the coarse x-edge they
 // lie on, even ones average the coarse x-edges around their coarse cell, rows
 // copy; m2 likewise with the axes exchanged.
-__global__ void k_prolong(int ncx, int ncy, const float* __restrict__ m1c, const float* __restrict__ m2c,
-                          const float* __restrict__ phic, float* __restrict__ m1f, float* __restrict__ m2f,
-                          float* __restrict__ phif, const Ctl* ctls)
+// fine node (i, j) from the coarse state (pointers at one pair's planes)
+__device__ __forceinline__ void prolong_node(int ncx, int ncy, const float* __restrict__ m1c,
+                                             const float* __restrict__ m2c, const float* __restrict__ phic,
+                                             float* __restrict__ m1f, float* __restrict__ m2f,
+                                             float* __restrict__ phif, int i, int j)
 {
     const int nx = 2 * ncx, ny = 2 * ncy;
-    const int pair = blockIdx.z;
-    if (ctls && ctls[pair].error) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= nx || j >= ny) return;
-    const size_t co = (size_t)pair * ncx * ncy, fo = (size_t)pair * nx * ny;
-    m1c += co;
-    m2c += co;
-    phic += co;
     const int I = i >> 1, J = j >> 1;
     const int In = min(max((i & 1) ? I + 1 : I - 1, 0), ncx - 1);
     const int Jn = min(max((j & 1) ? J + 1 : J - 1, 0), ncy - 1);
@@ -299,10 +298,23 @@ __global__ void k_prolong(int ncx, int ncy, const float* __restrict__ m1c, const
         v2 = 0.5f * (below + m2c[(size_t)J * ncx + I]);
     }
     if (j == ny - 1) v2 = 0.f;
-    const size_t k = fo + (size_t)j * nx + i;
+    const size_t k = (size_t)j * nx + i;
     phif[k] = p;
     m1f[k] = v1;
     m2f[k] = v2;
+}
+
+__global__ void k_prolong(int ncx, int ncy, const float* __restrict__ m1c, const float* __restrict__ m2c,
+                          const float* __restrict__ phic, float* __restrict__ m1f, float* __restrict__ m2f,
+                          float* __restrict__ phif, const Ctl* ctls)
+{
+    const int nx = 2 * ncx, ny = 2 * ncy;
+    const int pair = blockIdx.z;
+    if (ctls && ctls[pair].error) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const size_t co = (size_t)pair * ncx * ncy, fo = (size_t)pair * nx * ny;
+    prolong_node(ncx, ncy, m1c + co, m2c + co, phic + co, m1f + fo, m2f + fo, phif + fo, i, j);
 }
 
 cudaError_t launch_prolong(int ncx, int ncy, const float* m1c, const float* m2c, const float* phic, float* m1f,
@@ -1085,23 +1097,17 @@ __device__ __forceinline__ float4 dsmem_ld4(uint32_t addr)
     return v;
 }
 
+// One level of one pair, on CTA `rank` of a group of C (a cluster when CL).
 template <int NORM, bool CL>
-__global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
+__device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, const int C, const int rank,
+                                           unsigned char* smraw)
 {
     const IterArgs& P = a.it;
-    int C = 1, rank = 0;
-    if (CL) {
-        cg::cluster_group cl = cg::this_cluster();
-        C = (int)cl.num_blocks();
-        rank = (int)cl.block_rank();
-    }
-    const int pair = blockIdx.x / C;
     Ctl* pc = P.ctl ? P.ctl + pair : nullptr;
     if (pc && pc->error) return;  // uniform over the cluster (one pair)
     const int nx = P.nx, ny = P.ny;
     const int rows = ny / C, jb = rank * rows, nb = rows * nx;
     const int W = nx >> 2;  // threads per row
-    extern __shared__ __align__(16) unsigned char smraw[];
     double* red = reinterpret_cast<double*>(smraw);
     double* slots = reinterpret_cast<double*>(smraw + RES_RED_BYTES);
     float* ph = reinterpret_cast<float*>(smraw + RES_RED_BYTES + RES_SLOT_BYTES);
@@ -1319,6 +1325,19 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
     if (CL) cg::this_cluster().sync();
 }
 
+template <int NORM, bool CL>
+__global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
+{
+    int C = 1, rank = 0;
+    if (CL) {
+        cg::cluster_group cl = cg::this_cluster();
+        C = (int)cl.num_blocks();
+        rank = (int)cl.block_rank();
+    }
+    extern __shared__ __align__(16) unsigned char smraw[];
+    res4_level<NORM, CL>(a, blockIdx.x / C, C, rank, smraw);
+}
+
 // Wide-band variant for levels of up to 16 x 16384 nodes (512 x 512 in one
 // 16-CTA cluster): a thread owns four runs of four nodes.  Shared memory holds
 // only phi, m1 and m2 of the band (12 B per node, 192 KB at 16384 nodes), own
@@ -1332,25 +1351,18 @@ static size_t resident_wide_smem(int band)
 }
 
 template <int NORM, bool CL>
-__global__ void __launch_bounds__(RES_THREADS, 1) k_resident_wide(ResArgs a)
+__device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, const int C, const int rank,
+                                           unsigned char* smraw)
 {
     const IterArgs& P = a.it;
-    int C = 1, rank = 0;
-    if (CL) {
-        cg::cluster_group cl = cg::this_cluster();
-        C = (int)cl.num_blocks();
-        rank = (int)cl.block_rank();
-    }
     auto group_sync = [&]() {
         if (CL) cg::this_cluster().sync();
         else __syncthreads();
     };
-    const int pair = blockIdx.x / C;
     Ctl* pc = P.ctl ? P.ctl + pair : nullptr;
     if (pc && pc->error) return;  // uniform over the cluster (one pair)
     const int nx = P.nx, ny = P.ny;
     const int rows = ny / C, jb = rank * rows, nb = rows * nx;
-    extern __shared__ __align__(16) unsigned char smraw[];
     double* red = reinterpret_cast<double*>(smraw);
     double* slots = reinterpret_cast<double*>(smraw + RES_RED_BYTES);
     float* ph = reinterpret_cast<float*>(smraw + RES_RED_BYTES + RES_SLOT_BYTES);
@@ -1541,6 +1553,168 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident_wide(ResArgs a)
     if (CL) cg::this_cluster().sync();
 }
 
+template <int NORM, bool CL>
+__global__ void __launch_bounds__(RES_THREADS, 1) k_resident_wide(ResArgs a)
+{
+    int C = 1, rank = 0;
+    if (CL) {
+        cg::cluster_group cl = cg::this_cluster();
+        C = (int)cl.num_blocks();
+        rank = (int)cl.block_rank();
+    }
+    extern __shared__ __align__(16) unsigned char smraw[];
+    wide_level<NORM, CL>(a, blockIdx.x / C, C, rank, smraw);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent cascade for mixed-size batches (one CTA per pair, every level)
+// ---------------------------------------------------------------------------
+
+bool cascade_level_fits(int nx, int ny)
+{
+    const long long n = (long long)nx * ny;
+    return nx >= 4 && ny >= 1 && nx % 4 == 0 && nx <= 65535 &&
+           (n <= RES_MAX_NODES || (n <= RESW_MAX_NODES && n % 128 == 0));
+}
+
+// The two level bodies as separate functions: inlined side by side into the
+// persistent loop they spill; apart, each keeps its own register allocation.
+template <int NORM>
+__device__ __noinline__ void cascade_level_small(const ResArgs& a, int pair, unsigned char* smraw)
+{
+    res4_level<NORM, false>(a, pair, 1, 0, smraw);
+}
+template <int NORM>
+__device__ __noinline__ void cascade_level_wide(const ResArgs& a, int pair, unsigned char* smraw)
+{
+    wide_level<NORM, false>(a, pair, 1, 0, smraw);
+}
+
+template <int NORM>
+__global__ void __launch_bounds__(RES_THREADS, 1) k_cascade(CascadeArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    // the pair and level being solved and the level's arguments live in shared
+    // memory and are re-read after every level solve: nothing but the solve's own
+    // state stays in registers across it (registers are scarce at 1024 threads)
+    __shared__ int s_c, s_b, s_l, s_go;
+    __shared__ ResArgs s_args;
+    volatile int* vc = &s_c;
+    volatile int* vb = &s_b;
+    volatile int* vl = &s_l;
+    volatile int* vgo = &s_go;
+    for (;;) {
+        __syncthreads();  // the previous pair is finished before the shared fields change
+        if (threadIdx.x == 0) {
+            const int w = (int)atomicAdd(a.next, 1u);
+            int c = 0, b = w;
+            while (c < a.n_classes - 1 && b >= a.cls[c].count) {
+                b -= a.cls[c].count;
+                ++c;
+            }
+            *vc = c;
+            *vb = b;
+            *vl = 0;
+            // 0: no work left; 1: solve; 2: skip (rejected input or unused slot)
+            *vgo = w >= a.total ? 0 : (a.cls[c].ctl[b].error ? 2 : 1);
+        }
+        __syncthreads();
+        const int go = *vgo;
+        if (go == 0) return;
+        if (go == 2) continue;
+        for (;;) {
+            const int l = *vl;
+            const CascadeClass* K = a.cls + *vc;
+            if (l >= K->levels) break;
+            const int b = *vb;
+            const CascadeLevel& v = K->lv[l];
+            const int n = v.nx * v.ny;
+            const size_t off = (size_t)b * n;
+            if (l == 0) {  // Algorithm 3 starts from m = 0, phi = 0 on the coarsest grid
+                for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                    v.m1[off + k] = 0.f;
+                    v.m2[off + k] = 0.f;
+                    v.phi[off + k] = 0.f;
+                }
+            } else {
+                const CascadeLevel& cv = K->lv[l - 1];
+                const size_t co = (size_t)b * cv.nx * cv.ny;
+                for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                    const int j = k / v.nx, i = k - j * v.nx;
+                    prolong_node(cv.nx, cv.ny, cv.m1 + co, cv.m2 + co, cv.phi + co, v.m1 + off, v.m2 + off,
+                                 v.phi + off, i, j);
+                }
+            }
+            if (threadIdx.x == 0) {
+                ResArgs& r = s_args;
+                r = ResArgs{};
+                r.m1 = v.m1;
+                r.m2 = v.m2;
+                r.phi = v.phi;
+                r.rho = v.rho;
+                r.pairs = 1;
+                IterArgs& it = r.it;
+                it.nx = v.nx;
+                it.ny = v.ny;
+                it.mu = v.mu;
+                it.tau = v.tau;
+                it.ih = v.ih;
+                it.h = v.h;
+                it.tol = v.tol;
+                it.cap = a.cap;
+                it.K = a.K;
+                it.fixed = 0;
+                it.level = l;
+                it.budget_ns = a.budget_ns;
+                it.stride = n;
+                it.ctl = K->ctl;
+            }
+            __syncthreads();  // the level's state is in global memory for the level solve to load
+            if (n <= RES_MAX_NODES) cascade_level_small<NORM>(s_args, b, smraw);
+            else cascade_level_wide<NORM>(s_args, b, smraw);
+            __syncthreads();  // the level's final state is stored before the next level reads it
+            if (threadIdx.x == 0) *vl = l + 1;
+            __syncthreads();
+        }
+    }
+}
+
+static size_t cascade_smem() { return resident_wide_smem(RESW_MAX_NODES); }
+
+template <int NORM>
+static cudaError_t cascade_attr()
+{
+    return cudaFuncSetAttribute(k_cascade<NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cascade_smem());
+}
+
+static const void* cascade_fn(int norm)
+{
+    return norm == W1_NORM_L1 ? (const void*)k_cascade<W1_NORM_L1>
+           : norm == W1_NORM_L2 ? (const void*)k_cascade<W1_NORM_L2>
+                                : (const void*)k_cascade<W1_NORM_LINF>;
+}
+
+int cascade_ctas(int norm)
+{
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, cascade_fn(norm), RES_THREADS, cascade_smem()) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms * per;
+}
+
+cudaError_t launch_cascade(int norm, const CascadeArgs& a, int ctas, cudaStream_t s)
+{
+    if (ctas < 1 || a.total < 1) return cudaErrorInvalidValue;
+    const int grid = ctas < a.total ? ctas : a.total;
+    if (norm == W1_NORM_L1) k_cascade<W1_NORM_L1><<<grid, RES_THREADS, cascade_smem(), s>>>(a);
+    else if (norm == W1_NORM_L2) k_cascade<W1_NORM_L2><<<grid, RES_THREADS, cascade_smem(), s>>>(a);
+    else k_cascade<W1_NORM_LINF><<<grid, RES_THREADS, cascade_smem(), s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int NORM, int NPT, bool CL>
 static cudaError_t res_attr()
 {
@@ -1601,7 +1775,10 @@ cudaError_t resident_prepare(int)
     if ((e = res4_attr<W1_NORM_LINF, true>()) != cudaSuccess) return e;
     if ((e = resw_attr<W1_NORM_L1>()) != cudaSuccess) return e;
     if ((e = resw_attr<W1_NORM_L2>()) != cudaSuccess) return e;
-    return resw_attr<W1_NORM_LINF>();
+    if ((e = resw_attr<W1_NORM_LINF>()) != cudaSuccess) return e;
+    if ((e = cascade_attr<W1_NORM_L1>()) != cudaSuccess) return e;
+    if ((e = cascade_attr<W1_NORM_L2>()) != cudaSuccess) return e;
+    return cascade_attr<W1_NORM_LINF>();
 }
 
 template <int NORM>

@@ -16,6 +16,7 @@
 // blocks.  No host synchronisation happens between the first and the last.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -731,6 +732,251 @@ extern "C" w1_status w1_plan_potential(w1_plan* p, float* phi, void* stream)
     W1_CK(cudaMemcpyAsync(phi, f.phi[0], (size_t)f.nx * f.ny * sizeof(float) * nb, cudaMemcpyDeviceToDevice,
                           static_cast<cudaStream_t>(stream)));
     return W1_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-size batches
+// ---------------------------------------------------------------------------
+//
+// One batched plan per size class holds that class's arena (levels, control
+// blocks, partials).  Classes whose every level fits one CTA run together in one
+// persistent launch (k_cascade: a CTA takes a pair, runs all its levels, takes
+// the next; pairs of the largest grids first); the other classes run their own
+// plan's graph on a stream of their own.  A solve is: record -> [other classes on
+// their streams] and [prep per class -> graph: restriction per class -> the
+// persistent launch -> final statistics and the read-back per class] -> join.
+
+struct w1_mixed {
+    int device, n, norm;
+    std::vector<w1_plan*> plans;
+    std::vector<int> count;
+    std::vector<int> persistent;   // 1: the class runs in the persistent launch
+    std::vector<int> order;        // persistent classes, largest grid first
+    CascadeClass* d_cls;
+    unsigned int* d_next;
+    int ctas, total;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t start;
+    cudaStream_t cap_stream;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    bool eager;
+};
+
+// restriction of every persistent class -> the persistent launch -> final
+// statistics and read-back of every persistent class, enqueued on s
+static w1_status mixed_sequence(w1_mixed* m, cudaStream_t s)
+{
+    if (m->total == 0) return W1_OK;
+    W1_CK(cudaMemsetAsync(m->d_next, 0, sizeof(unsigned int), s));
+    for (int c : m->order) {
+        w1_plan* p = m->plans[c];
+        for (int l = p->L - 1; l > 0; --l)
+            W1_CK(launch_restrict(p->lv[l].rho, p->lv[l].nx, p->lv[l].ny, p->lv[l - 1].rho, p->batch, p->ctl, s));
+    }
+    CascadeArgs a{};
+    a.cls = m->d_cls;
+    a.n_classes = (int)m->order.size();
+    a.total = m->total;
+    a.next = m->d_next;
+    const w1_options& o = m->plans[m->order[0]]->opt;
+    a.cap = o.max_iters;
+    a.K = o.check_every;
+    a.budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
+    W1_CK(launch_cascade(m->norm, a, m->ctas, s));
+    for (int c : m->order) {
+        w1_plan* p = m->plans[c];
+        const LevelPlan& f = p->lv[p->L - 1];
+        W1_CK(launch_final(p->norm, f.m1[0], f.m2[0], f.phi[0], f.rho, f.nx, f.ny, f.h, p->q, p->part, p->ctl,
+                           p->batch, s));
+        W1_CK(cudaMemcpyAsync(p->host_ctl, p->ctl, sizeof(Ctl) * p->batch, cudaMemcpyDeviceToHost, s));
+    }
+    return W1_OK;
+}
+
+extern "C" w1_status w1_mixed_destroy(w1_mixed* m)
+{
+    if (!m) return W1_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(m->device);
+    for (w1_plan* p : m->plans) w1_plan_destroy(p);
+    for (cudaStream_t s : m->streams)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : m->done)
+        if (e) cudaEventDestroy(e);
+    if (m->start) cudaEventDestroy(m->start);
+    if (m->exec) cudaGraphExecDestroy(m->exec);
+    if (m->graph) cudaGraphDestroy(m->graph);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    if (m->d_cls) cudaFree(m->d_cls);
+    if (m->d_next) cudaFree(m->d_next);
+    cudaGetLastError();
+    cudaSetDevice(cur);
+    delete m;
+    return W1_OK;
+}
+
+extern "C" w1_status w1_mixed_create(int n_classes, const int* nx, const int* ny, const int* count, int norm,
+                                     double tol, const w1_options* opt, w1_mixed** out)
+{
+    if (!out) return fail(W1_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_classes < 1 || n_classes > 64 || !nx || !ny || !count)
+        return fail(W1_ERR_INVALID_ARG, "need 1..64 size classes with nx, ny and count");
+    for (int c = 0; c < n_classes; ++c)
+        if (count[c] < 1) return fail(W1_ERR_INVALID_ARG, "every class needs at least one pair");
+    w1_mixed* m = new (std::nothrow) w1_mixed();
+    if (!m) return fail(W1_ERR_NOMEM, "host allocation failed");
+    m->n = n_classes;
+    m->norm = norm;
+    m->eager = opt && opt->eager;
+    cudaGetDevice(&m->device);
+    for (int c = 0; c < n_classes; ++c) {
+        w1_plan* p = nullptr;
+        w1_status st = w1_plan_create_batch(nx[c], ny[c], 0.0, 0, norm, tol, count[c], opt, &p);
+        if (st != W1_OK) {
+            const std::string msg = g_err;
+            w1_mixed_destroy(m);
+            return fail(st, "class " + std::to_string(c) + ": " + msg);
+        }
+        m->plans.push_back(p);
+        m->count.push_back(count[c]);
+        bool fits = !(opt && opt->path != 0);
+        for (int l = 0; l < p->L && fits; ++l) fits = cascade_level_fits(p->lv[l].nx, p->lv[l].ny);
+        m->persistent.push_back(fits ? 1 : 0);
+    }
+    // persistent classes, largest grid first
+    for (int c = 0; c < n_classes; ++c)
+        if (m->persistent[c]) m->order.push_back(c);
+    for (size_t a = 0; a < m->order.size(); ++a)
+        for (size_t b = a + 1; b < m->order.size(); ++b) {
+            const w1_plan* pa = m->plans[m->order[a]];
+            const w1_plan* pb = m->plans[m->order[b]];
+            if ((long long)pb->nx * pb->ny > (long long)pa->nx * pa->ny) std::swap(m->order[a], m->order[b]);
+        }
+    std::vector<CascadeClass> cls;
+    for (int c : m->order) {
+        const w1_plan* p = m->plans[c];
+        CascadeClass k{};
+        k.levels = p->L;
+        k.count = p->batch;
+        k.ctl = p->ctl;
+        for (int l = 0; l < p->L; ++l) {
+            const LevelPlan& v = p->lv[l];
+            CascadeLevel& d = k.lv[l];
+            d.nx = v.nx;
+            d.ny = v.ny;
+            d.mu = v.mu;
+            d.tau = v.tau;
+            d.ih = (float)(1.0 / v.h);
+            d.h = v.h;
+            d.tol = v.tol;
+            d.rho = v.rho;
+            d.m1 = v.m1[0];
+            d.m2 = v.m2[0];
+            d.phi = v.phi[0];
+        }
+        cls.push_back(k);
+        m->total += p->batch;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!cls.empty()) {
+        m->ctas = cascade_ctas(norm);
+        if (m->ctas < 1) {
+            w1_mixed_destroy(m);
+            return fail(W1_ERR_CUDA, "the persistent launch cannot be resident");
+        }
+        e = cudaMalloc(&m->d_cls, sizeof(CascadeClass) * cls.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(m->d_cls, cls.data(), sizeof(CascadeClass) * cls.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&m->d_next, sizeof(unsigned int));
+    }
+    m->streams.assign(n_classes, nullptr);
+    m->done.assign(n_classes, nullptr);
+    for (int c = 0; c < n_classes && e == cudaSuccess; ++c) {
+        if (m->persistent[c]) continue;
+        e = cudaStreamCreateWithFlags(&m->streams[c], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->done[c], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        w1_mixed_destroy(m);
+        return fail(W1_ERR_CUDA, std::string("mixed batch set-up: ") + cudaGetErrorString(e));
+    }
+    if (!cls.empty() && !m->eager) {
+        // the persistent part as one CUDA graph
+        W1_CK(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeRelaxed));
+        w1_status st = mixed_sequence(m, m->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(m->cap_stream, &g);
+        if (st != W1_OK || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            w1_mixed_destroy(m);
+            return st != W1_OK ? st : fail(W1_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+        }
+        m->graph = g;
+        e = cudaGraphInstantiate(&m->exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            w1_mixed_destroy(m);
+            return fail(W1_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+        }
+    }
+    *out = m;
+    return W1_OK;
+}
+
+extern "C" int w1_mixed_persistent(const w1_mixed* m, int cls)
+{
+    if (!m || cls < 0 || cls >= m->n) return -1;
+    return m->persistent[cls];
+}
+
+extern "C" w1_status w1_mixed_solve_async(w1_mixed* m, const float* const* rho0, const float* const* rho1,
+                                          void* stream)
+{
+    if (!m || !rho0 || !rho1) return fail(W1_ERR_INVALID_ARG, "NULL batch or densities");
+    for (int c = 0; c < m->n; ++c)
+        if (!rho0[c] || !rho1[c]) return fail(W1_ERR_INVALID_ARG, "NULL density of class " + std::to_string(c));
+    W1_CK(cudaSetDevice(m->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    W1_CK(cudaEventRecord(m->start, s));
+    for (int c = 0; c < m->n; ++c) {
+        if (m->persistent[c]) continue;
+        W1_CK(cudaStreamWaitEvent(m->streams[c], m->start, 0));
+        w1_status st = enqueue(m->plans[c], m->count[c], rho0[c], rho1[c], m->streams[c], nullptr);
+        if (st != W1_OK) return st;
+        W1_CK(cudaEventRecord(m->done[c], m->streams[c]));
+    }
+    for (int c : m->order) {
+        w1_plan* p = m->plans[c];
+        W1_CK(launch_prep(rho0[c], rho1[c], (long long)p->nx * p->ny, p->batch, p->batch, p->h, p->ctl, p->part,
+                          p->lv[p->L - 1].rho, s));
+        p->last_batch = p->batch;
+    }
+    if (!m->order.empty()) {
+        if (m->eager) {
+            w1_status st = mixed_sequence(m, s);
+            if (st != W1_OK) return st;
+        } else {
+            W1_CK(cudaGraphLaunch(m->exec, s));
+        }
+    }
+    for (int c = 0; c < m->n; ++c)
+        if (!m->persistent[c]) W1_CK(cudaStreamWaitEvent(s, m->done[c], 0));
+    return W1_OK;
+}
+
+extern "C" w1_status w1_mixed_results(w1_mixed* m, int cls, double* dist, w1_stats* stats, int* status)
+{
+    if (!m || cls < 0 || cls >= m->n) return fail(W1_ERR_INVALID_ARG, "NULL batch or class out of range");
+    if (m->plans[cls]->last_batch < 1) return fail(W1_ERR_INVALID_ARG, "no solve was enqueued on this batch");
+    return results(m->plans[cls], dist, stats, status);
 }
 
 // ---------------------------------------------------------------------------

@@ -131,6 +131,11 @@ def _load() -> ctypes.CDLL:
         "w1_plan_potential": (st, [P, P, P]),
         "w1_cp_steps": (st, [I, I, D, I, F, F, P, P, P, P, LL, I, P, ctypes.POINTER(D)]),
         "w1_cp_steps_ex": (st, [I, I, D, I, F, F, P, P, P, P, LL, I, I, P, ctypes.POINTER(D)]),
+        "w1_mixed_create": (st, [I, P, P, P, I, D, ctypes.POINTER(Options), ctypes.POINTER(P)]),
+        "w1_mixed_destroy": (st, [P]),
+        "w1_mixed_persistent": (I, [P, I]),
+        "w1_mixed_solve_async": (st, [P, P, P, P]),
+        "w1_mixed_results": (st, [P, I, P, P, P]),
         "w1_restrict": (st, [I, I, P, P, P]),
         "w1_prolong": (st, [I, I, P, P, P, P, P, P, P]),
         "w1_state_stats": (st, [I, I, D, I, P, P, P, P, P, ctypes.POINTER(_Stats)]),
@@ -326,6 +331,66 @@ class Plan:
         shape = (self.ny, self.nx) if out.dim() == 2 else (out.shape[0], self.ny, self.nx)
         _check(_lib.w1_plan_potential(self._p, _dev_ptr(out, shape), _stream_ptr(stream)))
         return out
+
+
+class Mixed:
+    """A batch of pairs of several grid sizes (w1_mixed_*).  classes: list of
+    (nx, ny, count).  Classes whose levels fit one CTA run in one persistent
+    launch; the others as batched plans overlapping it."""
+
+    def __init__(self, classes, norm=NORM_L1, tol=0.0, **options):
+        self.classes = [tuple(int(v) for v in c) for c in classes]
+        n = len(self.classes)
+        arr = lambda k: (ctypes.c_int * n)(*[c[k] for c in self.classes])  # noqa: E731
+        self._nx, self._ny, self._cnt = arr(0), arr(1), arr(2)
+        opt = default_options(**options)
+        p = ctypes.c_void_p()
+        _check(_lib.w1_mixed_create(n, ctypes.cast(self._nx, ctypes.c_void_p), ctypes.cast(self._ny, ctypes.c_void_p),
+                                    ctypes.cast(self._cnt, ctypes.c_void_p), norm, tol, ctypes.byref(opt),
+                                    ctypes.byref(p)))
+        self._p = p
+
+    def persistent(self, cls) -> bool:
+        return _lib.w1_mixed_persistent(self._p, cls) == 1
+
+    def solve_async(self, rho0, rho1, stream=None):
+        """rho0, rho1: lists (one per class) of device tensors [count, ny, nx]."""
+        n = len(self.classes)
+        if len(rho0) != n or len(rho1) != n:
+            raise ValueError(f"expected {n} tensors per density")
+        p0 = (ctypes.c_void_p * n)(*[_dev_ptr(t, (c[2], c[1], c[0])).value for t, c in zip(rho0, self.classes)])
+        p1 = (ctypes.c_void_p * n)(*[_dev_ptr(t, (c[2], c[1], c[0])).value for t, c in zip(rho1, self.classes)])
+        self._keep = (rho0, rho1)
+        _check(_lib.w1_mixed_solve_async(self._p, ctypes.cast(p0, ctypes.c_void_p), ctypes.cast(p1, ctypes.c_void_p),
+                                         _stream_ptr(stream)))
+
+    def results(self, cls, allow=(OK, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_MASS)):
+        """(list of W1, list of Stats, list of statuses, status) of class cls."""
+        b = self.classes[cls][2]
+        d = (ctypes.c_double * b)()
+        s = (_Stats * b)()
+        ps = (ctypes.c_int * b)()
+        status = _lib.w1_mixed_results(self._p, cls, ctypes.cast(d, ctypes.c_void_p), ctypes.cast(s, ctypes.c_void_p),
+                                       ctypes.cast(ps, ctypes.c_void_p))
+        _check(status, allow)
+        return list(d), [Stats._from(x) for x in s], list(ps), status
+
+    def close(self):
+        if getattr(self, "_p", None):
+            _lib.w1_mixed_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def cp_steps(rho, m1, m2, phi, h, norm, mu, tau, iters, path=2, stream=None, cluster=0) -> float:
