@@ -541,6 +541,7 @@ def main():
     ap.add_argument("--kcluster", type=int, default=0, help="--only resident-kernel: CTAs per level (0: auto)")
     ap.add_argument("--mixed-norm", type=int, default=2, help="mixed-size batch: ground norm")
     ap.add_argument("--mixed-modes", default="loop,lanes,lockstep,lockstep-tuned,persistent")
+    ap.add_argument("--mixed-spec", default="", help="mixed-size batch override, e.g. 64:128,128:96")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -574,6 +575,11 @@ def run_mixed(args):
     norm = args.mixed_norm
     stream = torch.cuda.current_stream()
     passes = args.warmup + args.steps
+    global MIXED
+    if args.mixed_spec:
+        # side:pairs,side:pairs,... (levels down to 16^2)
+        MIXED = tuple((int(a), int(b), int(np.log2(int(a) // 16)) + 1)
+                      for a, b in (x.split(":") for x in args.mixed_spec.split(",")))
     data = []  # per pass: per class (t0, t1) [B, n, n]
     for s in range(passes):
         per = []
@@ -660,8 +666,8 @@ def run_mixed(args):
             plans.close()
         del plans
         torch.cuda.synchronize()
-    print(json.dumps({"only": "mixed", "workload": "gauss8 mixed: 128 x 64^2 (3 levels), 96 x 128^2 (4), "
-                      "32 x 256^2 (5)", "norm": norm, "pairs_per_pass": total, "passes": args.steps,
+    print(json.dumps({"only": "mixed",
+                      "workload": "gauss8 mixed: " + ", ".join(f"{B} x {n}^2 ({L} levels)" for n, B, L in MIXED), "norm": norm, "pairs_per_pass": total, "passes": args.steps,
                       "l2": "flushed before every pass", "modes": out}), flush=True)
     return 0
 

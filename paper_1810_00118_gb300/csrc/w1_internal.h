@@ -135,12 +135,14 @@ struct CascadeArgs {
     int K;                // steps between stop tests
     unsigned long long budget_ns;
 };
-// Whether one CTA holds an nx x ny level (nx % 4 == 0; at most 4096 nodes, or
-// 16384 in multiples of 128).
-bool cascade_level_fits(int nx, int ny);
-// CTAs of the persistent launch (one per SM at the launch's shared memory).
-int cascade_ctas(int norm);
-cudaError_t launch_cascade(int norm, const CascadeArgs& a, int ctas, cudaStream_t s);
+// Which single-CTA layouts hold an nx x ny level (nx % 4 == 0): bit 0 four
+// nodes per thread (at most 4096 nodes), bit 1 wide (at most 16384 nodes, a
+// multiple of 128).  A persistent launch with wide = false runs only levels of
+// the first kind; with wide = true, larger levels on the wide layout.
+int cascade_level_fits(int nx, int ny);
+// CTAs of the persistent launch that fit the device at once.
+int cascade_ctas(int norm, bool wide);
+cudaError_t launch_cascade(int norm, bool wide, const CascadeArgs& a, int ctas, cudaStream_t s);
 // Final statistics of a state into ctl (q: FP64 scratch of 2 * nx * ny per pair).
 cudaError_t launch_final(int norm, const float* m1, const float* m2, const float* phi, const float* rho, int nx,
                          int ny, double h, double* q, double* part, Ctl* ctl, int pairs, cudaStream_t s);

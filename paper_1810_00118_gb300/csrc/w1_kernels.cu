@@ -1570,15 +1570,18 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident_wide(ResArgs a)
 // Persistent cascade for mixed-size batches (one CTA per pair, every level)
 // ---------------------------------------------------------------------------
 
-bool cascade_level_fits(int nx, int ny)
+int cascade_level_fits(int nx, int ny)
 {
     const long long n = (long long)nx * ny;
-    return nx >= 4 && ny >= 1 && nx % 4 == 0 && nx <= 65535 &&
-           (n <= RES_MAX_NODES || (n <= RESW_MAX_NODES && n % 128 == 0));
+    if (nx < 4 || ny < 1 || nx % 4 != 0 || nx > 65535) return 0;
+    return (n <= RES_MAX_NODES ? 1 : 0) | ((n <= RESW_MAX_NODES && n % 128 == 0) ? 2 : 0);
 }
 
-// The two level bodies as separate functions: inlined side by side into the
-// persistent loop they spill; apart, each keeps its own register allocation.
+// WIDE = false: every level on the four-nodes-per-thread layout (at most 4096
+// nodes), its body inlined.  WIDE = true: levels of up to 4096 nodes on that
+// layout, larger ones on the wide layout (at most 16384 nodes, a multiple of
+// 128); the two bodies are separate functions here, since inlined side by side
+// they spill (measured: the split is faster than the wide layout for every level).
 template <int NORM>
 __device__ __noinline__ void cascade_level_small(const ResArgs& a, int pair, unsigned char* smraw)
 {
@@ -1590,7 +1593,7 @@ __device__ __noinline__ void cascade_level_wide(const ResArgs& a, int pair, unsi
     wide_level<NORM, false>(a, pair, 1, 0, smraw);
 }
 
-template <int NORM>
+template <int NORM, bool WIDE>
 __global__ void __launch_bounds__(RES_THREADS, 1) k_cascade(CascadeArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1670,7 +1673,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cascade(CascadeArgs a)
                 it.ctl = K->ctl;
             }
             __syncthreads();  // the level's state is in global memory for the level solve to load
-            if (n <= RES_MAX_NODES) cascade_level_small<NORM>(s_args, b, smraw);
+            if (!WIDE) res4_level<NORM, false>(s_args, b, 1, 0, smraw);
+            else if (n <= RES_MAX_NODES) cascade_level_small<NORM>(s_args, b, smraw);
             else cascade_level_wide<NORM>(s_args, b, smraw);
             __syncthreads();  // the level's final state is stored before the next level reads it
             if (threadIdx.x == 0) *vl = l + 1;
@@ -1679,40 +1683,47 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cascade(CascadeArgs a)
     }
 }
 
-static size_t cascade_smem() { return resident_wide_smem(RESW_MAX_NODES); }
+static size_t cascade_smem(bool wide) { return wide ? resident_wide_smem(RESW_MAX_NODES) : resident_smem(RES_MAX_NODES); }
 
 template <int NORM>
 static cudaError_t cascade_attr()
 {
-    return cudaFuncSetAttribute(k_cascade<NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cascade_smem());
+    cudaError_t e = cudaFuncSetAttribute(k_cascade<NORM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cascade_smem(false));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_cascade<NORM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)cascade_smem(true));
 }
 
-static const void* cascade_fn(int norm)
+static const void* cascade_fn(int norm, bool wide)
 {
-    return norm == W1_NORM_L1 ? (const void*)k_cascade<W1_NORM_L1>
-           : norm == W1_NORM_L2 ? (const void*)k_cascade<W1_NORM_L2>
-                                : (const void*)k_cascade<W1_NORM_LINF>;
+    if (wide)
+        return norm == W1_NORM_L1 ? (const void*)k_cascade<W1_NORM_L1, true>
+               : norm == W1_NORM_L2 ? (const void*)k_cascade<W1_NORM_L2, true>
+                                    : (const void*)k_cascade<W1_NORM_LINF, true>;
+    return norm == W1_NORM_L1 ? (const void*)k_cascade<W1_NORM_L1, false>
+           : norm == W1_NORM_L2 ? (const void*)k_cascade<W1_NORM_L2, false>
+                                : (const void*)k_cascade<W1_NORM_LINF, false>;
 }
 
-int cascade_ctas(int norm)
+int cascade_ctas(int norm, bool wide)
 {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, cascade_fn(norm), RES_THREADS, cascade_smem()) != cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, cascade_fn(norm, wide), RES_THREADS, cascade_smem(wide)) !=
+            cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return sms * per;
 }
 
-cudaError_t launch_cascade(int norm, const CascadeArgs& a, int ctas, cudaStream_t s)
+cudaError_t launch_cascade(int norm, bool wide, const CascadeArgs& a, int ctas, cudaStream_t s)
 {
     if (ctas < 1 || a.total < 1) return cudaErrorInvalidValue;
     const int grid = ctas < a.total ? ctas : a.total;
-    if (norm == W1_NORM_L1) k_cascade<W1_NORM_L1><<<grid, RES_THREADS, cascade_smem(), s>>>(a);
-    else if (norm == W1_NORM_L2) k_cascade<W1_NORM_L2><<<grid, RES_THREADS, cascade_smem(), s>>>(a);
-    else k_cascade<W1_NORM_LINF><<<grid, RES_THREADS, cascade_smem(), s>>>(a);
-    return cudaGetLastError();
+    void* args[1] = {(void*)&a};
+    return cudaLaunchKernel(cascade_fn(norm, wide), dim3(grid), dim3(RES_THREADS), args, cascade_smem(wide), s);
 }
 
 template <int NORM, int NPT, bool CL>

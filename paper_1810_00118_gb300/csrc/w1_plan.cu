@@ -755,6 +755,7 @@ struct w1_mixed {
     CascadeClass* d_cls;
     unsigned int* d_next;
     int ctas, total;
+    bool wide;                     // the persistent launch's level layout
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> done;
     cudaEvent_t start;
@@ -784,7 +785,7 @@ static w1_status mixed_sequence(w1_mixed* m, cudaStream_t s)
     a.cap = o.max_iters;
     a.K = o.check_every;
     a.budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
-    W1_CK(launch_cascade(m->norm, a, m->ctas, s));
+    W1_CK(launch_cascade(m->norm, m->wide, a, m->ctas, s));
     for (int c : m->order) {
         w1_plan* p = m->plans[c];
         const LevelPlan& f = p->lv[p->L - 1];
@@ -843,9 +844,20 @@ extern "C" w1_status w1_mixed_create(int n_classes, const int* nx, const int* ny
         }
         m->plans.push_back(p);
         m->count.push_back(count[c]);
-        bool fits = !(opt && opt->path != 0);
-        for (int l = 0; l < p->L && fits; ++l) fits = cascade_level_fits(p->lv[l].nx, p->lv[l].ny);
-        m->persistent.push_back(fits ? 1 : 0);
+        // 1: every level fits the four-nodes-per-thread layout; 2: some level needs
+        // the wide one; 0: some level fits neither (or a path is forced)
+        int kind = (opt && opt->path != 0) ? 0 : 1;
+        for (int l = 0; l < p->L && kind; ++l) {
+            const int f = cascade_level_fits(p->lv[l].nx, p->lv[l].ny);
+            if (f == 0) kind = 0;
+            else if (!(f & 1)) kind = 2;
+        }
+        m->persistent.push_back(kind);
+    }
+    m->wide = false;
+    for (int c = 0; c < n_classes; ++c) {
+        if (m->persistent[c] == 2) m->wide = true;
+        m->persistent[c] = m->persistent[c] ? 1 : 0;
     }
     // persistent classes, largest grid first
     for (int c = 0; c < n_classes; ++c)
@@ -883,7 +895,7 @@ extern "C" w1_status w1_mixed_create(int n_classes, const int* nx, const int* ny
     }
     cudaError_t e = cudaSuccess;
     if (!cls.empty()) {
-        m->ctas = cascade_ctas(norm);
+        m->ctas = cascade_ctas(norm, m->wide);
         if (m->ctas < 1) {
             w1_mixed_destroy(m);
             return fail(W1_ERR_CUDA, "the persistent launch cannot be resident");
