@@ -170,6 +170,27 @@ def oracle_cost(norm_list, pairs, budget_s=12.0):
     return per_norm, "; ".join(sample)
 
 
+def oracle_cost_pdhg(norm_list, budget_s=12.0):
+    """Seconds per FP64 oracle solve with Algorithm 4 for each norm: whole
+    solves of the bench's first pair, repeated while the budget lasts."""
+    import synth
+    from oracle import pdhg
+
+    r0, r1 = synth.pair(WORKLOAD, 0)
+    _, _, d0, d1 = synth.to_f32_pair(r0, r1)
+    per_norm, sample = {}, []
+    for norm in norm_list:
+        t0, k = time.perf_counter(), 0
+        while True:
+            pdhg.multilevel(d0, d1, levels=LEVELS, norm=norm)
+            k += 1
+            if time.perf_counter() - t0 > budget_s / (2 * len(norm_list)):
+                break
+        per_norm[norm] = (time.perf_counter() - t0) / k
+        sample.append(f"p{norm}: {k} whole solves of pair 0")
+    return per_norm, "; ".join(sample)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -253,12 +274,14 @@ def run_gpu(args):
     ok = (w1.OK, w1.ERR_NOT_CONVERGED)
     if args.mode == "lockstep":
         # one batched plan per norm: every launch advances all B pairs together
-        plans = {norm: w1.Plan(N, N, levels=LEVELS, norm=norm, batch=B, eager=int(args.eager)) for norm in NORMS}
+        plans = {norm: w1.Plan(N, N, levels=LEVELS, norm=norm, batch=B, eager=int(args.eager), algorithm=args.algorithm)
+                 for norm in NORMS}
     else:
         # lanes: one plan and one stream per pair, all enqueued asynchronously, so
         # every pair moves through its levels at its own pace and the kernels of
         # different pairs overlap on the device
-        plans = {norm: [w1.Plan(N, N, levels=LEVELS, norm=norm, eager=int(args.eager)) for _ in range(B)]
+        plans = {norm: [w1.Plan(N, N, levels=LEVELS, norm=norm, eager=int(args.eager), algorithm=args.algorithm)
+                        for _ in range(B)]
                  for norm in NORMS}
         lanes = {norm: [torch.cuda.Stream() for _ in range(B)] for norm in NORMS}
         done_ev = {norm: [torch.cuda.Event(enable_timing=True) for _ in range(B)] for norm in NORMS}
@@ -366,7 +389,7 @@ def run_gpu(args):
     # the blocking entry point, CUDA events around each solve
     solo = {}
     for norm in NORMS:
-        with w1.Plan(N, N, levels=LEVELS, norm=norm) as p1:
+        with w1.Plan(N, N, levels=LEVELS, norm=norm, algorithm=args.algorithm) as p1:
             ts = []
             for k in range(args.solo):
                 t0s, t1s = dev_pairs[k % total_steps][0][k % B], dev_pairs[k % total_steps][1][k % B]
@@ -394,7 +417,10 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 iterates, f64 reductions", "data": "synthetic",
             "config": {"workload": "ellipse_texture_512x512_pairs_6_levels_both_norms", "grid": [N, N],
-                       "levels": LEVELS, "norms": ["L1", "L2"], "stop": "FPR, eq. stop_tol",
+                       "levels": LEVELS, "norms": ["L1", "L2"],
+                       "algorithm": {3: "Algorithm 3 (multilevel Chambolle-Pock)",
+                                     4: "Algorithm 4 (multilevel prox-PDHG)"}[args.algorithm],
+                       "stop": "eq. stop_tol for the algorithm",
                        "batch_per_norm": B, "mode": args.mode,
                        "l2": "flushed before every step (256 MiB write, inside the timed region)",
                        "parallelism": f"replicas x{world}"},
@@ -412,7 +438,11 @@ def run_gpu(args):
             "roofline": roof,
             "clocks": clk.summary(),
         }
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and args.algorithm == 4:
+            per_norm, sample = oracle_cost_pdhg(NORMS, budget_s=args.ref_budget)
+            line["cpu_baseline"] = {"value": len(NORMS) / sum(per_norm.values()), "unit": "solves/s", "cores": 1,
+                                    "kind": "oracle", "sample": "FP64 prox-PDHG oracle (numpy, one thread): " + sample}
+        elif not args.no_cpu_baseline:
             per_norm, sample = oracle_cost(NORMS, list(range(4)), budget_s=args.ref_budget)
             cpu_v = len(NORMS) / sum(per_norm.values())
             line["cpu_baseline"] = {"value": cpu_v, "unit": "solves/s", "cores": 1, "kind": "oracle",
@@ -525,6 +555,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--solo", type=int, default=8, help="pairs solved one at a time for the latency figure")
+    ap.add_argument("--algorithm", type=int, default=3, choices=[3, 4],
+                    help="3: multilevel Chambolle-Pock (the headline); 4: multilevel prox-PDHG")
     ap.add_argument("--eager", action="store_true",
                     help="launch level kernels directly (no CUDA graph) so profilers see every kernel")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000", help="serving: arrival rates (req/s)")
