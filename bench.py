@@ -274,13 +274,15 @@ def run_gpu(args):
     ok = (w1.OK, w1.ERR_NOT_CONVERGED)
     if args.mode == "lockstep":
         # one batched plan per norm: every launch advances all B pairs together
-        plans = {norm: w1.Plan(N, N, levels=LEVELS, norm=norm, batch=B, eager=int(args.eager), algorithm=args.algorithm)
+        plans = {norm: w1.Plan(N, N, levels=LEVELS, norm=norm, batch=B, eager=int(args.eager), algorithm=args.algorithm,
+                               check_every=args.check_every)
                  for norm in NORMS}
     else:
         # lanes: one plan and one stream per pair, all enqueued asynchronously, so
         # every pair moves through its levels at its own pace and the kernels of
         # different pairs overlap on the device
-        plans = {norm: [w1.Plan(N, N, levels=LEVELS, norm=norm, eager=int(args.eager), algorithm=args.algorithm)
+        plans = {norm: [w1.Plan(N, N, levels=LEVELS, norm=norm, eager=int(args.eager), algorithm=args.algorithm,
+                                check_every=args.check_every)
                         for _ in range(B)]
                  for norm in NORMS}
         lanes = {norm: [torch.cuda.Stream() for _ in range(B)] for norm in NORMS}
@@ -389,7 +391,7 @@ def run_gpu(args):
     # the blocking entry point, CUDA events around each solve
     solo = {}
     for norm in NORMS:
-        with w1.Plan(N, N, levels=LEVELS, norm=norm, algorithm=args.algorithm) as p1:
+        with w1.Plan(N, N, levels=LEVELS, norm=norm, algorithm=args.algorithm, check_every=args.check_every) as p1:
             ts = []
             for k in range(args.solo):
                 t0s, t1s = dev_pairs[k % total_steps][0][k % B], dev_pairs[k % total_steps][1][k % B]
@@ -555,6 +557,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--solo", type=int, default=8, help="pairs solved one at a time for the latency figure")
+    ap.add_argument("--check-every", type=int, default=0,
+                    help="steps between stop tests (multiple of 8; 0: 32 for Algorithm 3, 8 for Algorithm 4)")
     ap.add_argument("--algorithm", type=int, default=3, choices=[3, 4],
                     help="3: multilevel Chambolle-Pock (the headline); 4: multilevel prox-PDHG")
     ap.add_argument("--eager", action="store_true",

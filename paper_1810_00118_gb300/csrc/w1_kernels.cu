@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "w1_device.cuh"
 #include "w1_internal.h"
@@ -1078,9 +1079,10 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
     int it = 0;
     const int cap = (int)min(P.cap, (long long)INT_MAX);
     int next = P.fixed ? cap : P.K;  // step after which the next test runs
-    while (it < cap) {
-        const bool check = it + 1 == next;
-        float sa = 0.f, sb = 0.f, sc = 0.f;  // FP32 terms and per-thread partials, FP64 across threads
+    float sa = 0.f, sb = 0.f, sc = 0.f;  // FP32 terms and per-thread partials, FP64 across threads
+    // one step; the test-step work is compiled only into the step that tests
+    auto one_step = [&](auto test) {
+        constexpr bool check = decltype(test)::value;
         // ---- phase A: m' = prox(m + mu grad phi); on the last column and the top
         // row the gradient component is zero and so is m, hence m' too
         const float rn = __shfl_down_sync(FULL, pv[0], 1);
@@ -1097,7 +1099,7 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
                 const float pr_ = c < 3 ? pv[c + 1] : right;
                 prox<NORM>(fmaf(cm, pr_ - pv[c], m1[c]), fmaf(cm, up[c] - pv[c], m2[c]), mu, n1[c], n2[c]);
             }
-            if (check) {
+            if constexpr (check) {
                 float d1[4], d2[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
@@ -1135,7 +1137,7 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
                 pn[c] = fmaf(ct, fmaf(2.f, Dn, -Dv[c]), fmaf(-tau, rv[c], pv[c]));
                 Dv[c] = Dn;
             }
-            if (check) {
+            if constexpr (check) {
                 const float4 e1 = *reinterpret_cast<const float4*>(e1s + idx);
                 const float4 e2 = *reinterpret_cast<const float4*>(e2s + idx);
                 const float el = i0 > 0 ? e1s[idx - 1] : 0.f;
@@ -1161,8 +1163,17 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
         } else {
             __syncthreads();
         }
+    };
+    while (it < cap) {
+        // plain steps up to the one that tests
+        const int plain = (next - 1 < cap ? next - 1 : cap) - it;
+        for (int r = 0; r < plain; ++r) one_step(std::false_type{});
+        it += plain;
+        if (it >= cap) break;
+        sa = sb = sc = 0.f;
+        one_step(std::true_type{});
         ++it;
-        if (check) {
+        {
             next += P.K;
             double v[3] = {(double)sa, (double)sb, (double)sc / P.h};
             block_sum<3>(v, red);

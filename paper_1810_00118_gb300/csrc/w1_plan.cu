@@ -138,7 +138,7 @@ struct w1_plan {
 extern "C" void w1_default_options(w1_options* o)
 {
     if (!o) return;
-    o->check_every = 32;
+    o->check_every = 0;
     o->max_iters = 1000000;
     o->theta = 0.5;
     o->alpha = -1.0;
@@ -248,6 +248,8 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
     w1_options o;
     w1_default_options(&o);
     if (opt) o = *opt;
+    // K = 0: 32 steps between tests for Algorithm 3, 8 for Algorithm 4 (few steps per level)
+    if (o.check_every == 0) o.check_every = o.algorithm == 4 ? 8 : 32;
     if (o.check_every < 2 || (o.check_every & 1)) return fail(W1_ERR_INVALID_ARG, "check_every must be even and >= 2");
     if (!(o.theta > 0.0) || o.theta > 1.0) return fail(W1_ERR_INVALID_ARG, "theta must lie in (0, 1]");
     if (o.max_iters < 1) return fail(W1_ERR_INVALID_ARG, "max_iters must be >= 1");

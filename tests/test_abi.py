@@ -38,7 +38,7 @@ def test_library_builds_and_exports_every_declared_symbol():
 def test_host_only_entry_points_work_without_gpu():
     from paper_1810_00118_gb300 import w1
     o = w1.default_options()
-    assert o.check_every == 32 and o.theta == 0.5 and o.alpha == -1.0
+    assert o.check_every == 0 and o.theta == 0.5 and o.alpha == -1.0 and o.algorithm == 3
     assert w1.status_string(w1.ERR_MASS).startswith("mass")
     assert w1.status_string(99) == "unknown status"
 
