@@ -390,7 +390,7 @@ def run_gpu(args):
     # latency of one solve with the GPU otherwise idle: one pair at a time through
     # the blocking entry point, CUDA events around each solve
     solo = {}
-    for norm in NORMS:
+    for norm in (NORMS if args.solo > 0 else ()):
         with w1.Plan(N, N, levels=LEVELS, norm=norm, algorithm=args.algorithm, check_every=args.check_every) as p1:
             ts = []
             for k in range(args.solo):
@@ -463,7 +463,7 @@ def run_gpu(args):
 # the captures summarised under profiles/; None where no capture of the current
 # kernel exists.  Streaming kernels: captured at 4096^2 and scaled by 4 to 8192^2
 # (their traffic grows with the number of nodes).
-TRAFFIC = {"k_step": 4 * 444.46e6, "k_tblock": 4 * 432.7e6, "k_resident4": 1.0926e6}
+TRAFFIC = {"k_step": 4 * 444.46e6, "k_tblock": 4 * 432.7e6, "k_resident4": 1.0816e6}
 
 FP32_LANES_PER_SM = 128  # FP32 units per SM; two flops per FMA
 SM_MAX_MHZ = 2070.0
@@ -567,9 +567,10 @@ def main():
     ap.add_argument("--requests", type=int, default=400, help="serving: requests per rate (at least)")
     ap.add_argument("--min-seconds", type=float, default=0.0, help="serving: at least rate*this requests")
     ap.add_argument("--slots", type=int, default=48, help="serving: solves in flight")
+    ap.add_argument("--serve-batch", type=int, default=1, help="serving: pairs a slot solves together")
     ap.add_argument("--only", default="solve",
-                    choices=["solve", "stream-kernel", "tblock-kernel", "resident-kernel", "serve", "mixed",
-                             "tol-sweep"],
+                    choices=["solve", "stream-kernel", "tblock-kernel", "resident-kernel", "pdhg-kernel", "serve",
+                             "mixed", "tol-sweep"],
                     help="kernel-only runs for profiling: one level's steps through w1_cp_steps")
     ap.add_argument("--kn", type=int, default=256, help="grid side for --only *-kernel")
     ap.add_argument("--kiters", type=int, default=1000, help="steps for --only *-kernel")
@@ -825,7 +826,7 @@ def run_serve(args):
     pool = serve_pool(torch)
     rates = [float(x) for x in args.rates.split(",")]
     out = []
-    with w1.Server(hbm_budget_bytes=40 << 30, max_slots=args.slots) as srv:
+    with w1.Server(hbm_budget_bytes=40 << 30, max_slots=args.slots, max_batch=args.serve_batch) as srv:
         # warm-up: one request of every class builds its slot
         serve_run(w1, srv, pool, 1000.0, 16, seed=1)
         for r in rates:
@@ -837,7 +838,7 @@ def run_serve(args):
             print(json.dumps(out[-1]), flush=True)
         info = srv.info()
     print(json.dumps({"serving": out, "server": info, "sizes": SERVE_SIZES, "probs": SERVE_PROBS,
-                      "budget_GiB": 40, "slots": args.slots}))
+                      "budget_GiB": 40, "slots": args.slots, "max_batch": args.serve_batch}))
     return 0
 
 
@@ -854,8 +855,22 @@ def run_kernel_only(args):
     m1, m2, phi = (torch.zeros((n, n), device="cuda") for _ in range(3))
     h = 1.0 / n
     mu = float(np.float32(0.5 * h / (2 * np.sqrt(2.0))))
-    path = {"resident-kernel": 1, "stream-kernel": 2, "tblock-kernel": 3}[args.only]
     stream = torch.cuda.current_stream()
+    if args.only == "pdhg-kernel":
+        # steps of eq. pdhg (Poisson solve by DCT) from zero on one level
+        st = [torch.zeros((n, n), device="cuda") for _ in range(6)]
+        w1.pdhg_steps(rho, *st, h, args.knorm, 4, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        G = w1.pdhg_steps(rho, *st, h, args.knorm, args.kiters, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        print(json.dumps({"only": args.only, "n": n, "norm": args.knorm, "steps": args.kiters, "ms": ms,
+                          "us_per_step": ms * 1e3 / args.kiters, "G_last": G}))
+        return 0
+    path = {"resident-kernel": 1, "stream-kernel": 2, "tblock-kernel": 3}[args.only]
     kw = {"cluster": args.kcluster} if path == 1 else {}
     w1.cp_steps(rho, m1, m2, phi, h, args.knorm, mu, mu, 4, path=path, stream=stream, **kw)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
