@@ -281,12 +281,17 @@ def run_gpu(args):
         # lanes: one plan and one stream per pair, all enqueued asynchronously, so
         # every pair moves through its levels at its own pace and the kernels of
         # different pairs overlap on the device
+        # (--lane-batch g > 1: each lane is a batched plan of g pairs)
+        G = args.lane_batch
+        if G < 1 or B % G:
+            raise SystemExit("--lane-batch must divide --batch")
+        nlane = B // G
         plans = {norm: [w1.Plan(N, N, levels=LEVELS, norm=norm, eager=int(args.eager), algorithm=args.algorithm,
-                                check_every=args.check_every)
-                        for _ in range(B)]
+                                check_every=args.check_every, tune=args.tune, batch=G)
+                        for _ in range(nlane)]
                  for norm in NORMS}
-        lanes = {norm: [torch.cuda.Stream() for _ in range(B)] for norm in NORMS}
-        done_ev = {norm: [torch.cuda.Event(enable_timing=True) for _ in range(B)] for norm in NORMS}
+        lanes = {norm: [torch.cuda.Stream() for _ in range(nlane)] for norm in NORMS}
+        done_ev = {norm: [torch.cuda.Event(enable_timing=True) for _ in range(nlane)] for norm in NORMS}
     pair_ms = []
     in_dev = [torch.empty((B, N, N), device="cuda") for _ in range(2)]
 
@@ -308,19 +313,22 @@ def run_gpu(args):
         ready = torch.cuda.Event(enable_timing=True)
         ready.record(stream)
         for norm in NORMS:
-            for b in range(B):
+            for b in range(nlane):
                 lanes[norm][b].wait_event(ready)
-                plans[norm][b].solve_async(t0[b], t1[b], stream=lanes[norm][b])
+                if G == 1:
+                    plans[norm][b].solve_async(t0[b], t1[b], stream=lanes[norm][b])
+                else:
+                    plans[norm][b].solve_async(t0[b * G:(b + 1) * G], t1[b * G:(b + 1) * G], stream=lanes[norm][b])
                 done_ev[norm][b].record(lanes[norm][b])
                 stream.wait_event(done_ev[norm][b])  # the launching stream joins every lane
         for norm in NORMS:
             vals, sts = [], []
-            for b in range(B):
+            for b in range(nlane):
                 lanes[norm][b].synchronize()
                 v, st, _, _ = plans[norm][b].results(allow=ok)
-                vals.append(v[0])
-                sts.append(st[0])
-                pair_ms.append(ready.elapsed_time(done_ev[norm][b]))
+                vals.extend(v)
+                sts.extend(st)
+                pair_ms.extend([ready.elapsed_time(done_ev[norm][b])] * G)
             out.append((vals, sts))
         return out
 
@@ -336,9 +344,12 @@ def run_gpu(args):
         # (for a batched plan: those of the slowest pair)
         st = sts[0]
         per = 2 + (st.levels - 1) + st.levels + (st.levels - 1) + 2
+        def group(g):
+            return per + sum(level_launches(p, max(x.iters[lvl] for x in g)) for lvl, p in enumerate(st.path))
         if args.mode == "lockstep":
-            return per + sum(level_launches(p, max(x.iters[lvl] for x in sts)) for lvl, p in enumerate(st.path))
-        return sum(per + sum(level_launches(p, x.iters[lvl]) for lvl, p in enumerate(x.path)) for x in sts)
+            return group(sts)
+        G = args.lane_batch
+        return sum(group(sts[k:k + G]) for k in range(0, len(sts), G))
 
     def barrier():
         if dist is not None:
@@ -424,6 +435,7 @@ def run_gpu(args):
                                      4: "Algorithm 4 (multilevel prox-PDHG)"}[args.algorithm],
                        "stop": "eq. stop_tol for the algorithm",
                        "batch_per_norm": B, "mode": args.mode,
+                       "pairs_per_lane": args.lane_batch if args.mode == "lanes" else B,
                        "l2": "flushed before every step (256 MiB write, inside the timed region)",
                        "parallelism": f"replicas x{world}"},
             "timer": {"kind": "CUDA events on the launching stream, every lane joined to it", "wall_s": wall},
@@ -545,6 +557,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--batch", type=int, default=128, help="pairs per norm per step")
+    ap.add_argument("--lane-batch", type=int, default=1, help="lanes: pairs per lane (a batched plan per lane)")
     ap.add_argument("--mode", default="lanes", choices=["lanes", "lockstep"],
                     help="lanes: one async plan+stream per pair; lockstep: one batched plan per norm")
     ap.add_argument("--steps", type=int, default=5)
@@ -557,6 +570,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--solo", type=int, default=8, help="pairs solved one at a time for the latency figure")
+    ap.add_argument("--tune", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="lanes: per-level kernel choice (0 fixed rules, 1 latency, 3 SM-time; see w1_options.tune)")
     ap.add_argument("--check-every", type=int, default=0,
                     help="steps between stop tests (multiple of 8; 0: 32 for Algorithm 3, 8 for Algorithm 4)")
     ap.add_argument("--algorithm", type=int, default=3, choices=[3, 4],

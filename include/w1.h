@@ -84,7 +84,8 @@ typedef struct {
                               conditional graph nodes); 0: one CUDA graph (default)           */
     int tune;              /* 0: fixed rules pick each level's kernel; 1: the autotuner picks
                               the fastest for one pair (latency); 2: the fastest for the
-                              plan's batch advancing together (throughput)                  */
+                              plan's batch advancing together (throughput); 3: the least
+                              SM-time per step (many independent solves sharing the GPU) */
     int algorithm;         /* 3 (default, 0 too): Algorithm 3, Chambolle-Pock on every level
                               (eq. primaldual, stop R^k < eps_l); 4: Algorithm 4, prox-PDHG
                               (eq. pdhg: projection onto div m = rho by a DCT Poisson solve,
@@ -244,14 +245,18 @@ typedef struct {
     int cluster;        /* CTAs per pair for path 1 */
     int batch;          /* pairs advancing together when it was timed */
     double us_per_step; /* measured time of one step of the whole batch */
+    int concurrent;     /* path 1: pairs whose level fits on the GPU at once (CTAs or clusters
+                           resident together); streaming: 1 (a launch spans the GPU) */
 } w1_level_choice;
 
 /*
  * Times every configuration that can run an nx x ny level (`steps` steps each,
- * synthetic density, CUDA events) and returns the fastest in `best`.
- * objective 1: one pair alone (latency); objective 2: `batch` pairs advancing
- * together as in a batched plan (throughput: a configuration with fewer CTAs
- * per pair can finish a large batch sooner).  `all` (room for 8) receives every
+ * synthetic density, CUDA events) and returns the best in `best`.
+ * objective 1: fastest for one pair alone (latency); objective 2: fastest for
+ * `batch` pairs advancing together as in a batched plan (throughput: a
+ * configuration with fewer CTAs per pair can finish a large batch sooner);
+ * objective 3: least SM-time per step of one pair (time x SMs it holds: for many
+ * independent solves sharing the GPU, as with one plan per stream).  `all` (room for 8) receives every
  * measured candidate when not NULL, n_all their number.  Results are cached
  * per device, grid, norm and batch for the process, and in the file named by
  * the environment variable W1_AUTOTUNE_CACHE when it is set.  The choice is

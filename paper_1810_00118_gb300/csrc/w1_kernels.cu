@@ -1792,12 +1792,23 @@ static void resident_config(int norm, int cluster, int nx, int ny, int pairs, cu
 int resident_cluster_ok(int norm, int cluster, int nx, int ny)
 {
     if (!resident_fits(nx, ny, cluster)) return 0;
-    if (cluster == 1) return 1;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
     const void* fn = nullptr;
     resident_config(norm, cluster, nx, ny, 1, cfg, attr, &fn);
     int n = 0;
+    if (cluster == 1) {
+        // single CTAs: resident blocks per SM times SMs
+        int dev = 0, sms = 0, per = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, (int)(cfg.blockDim.x), cfg.dynamicSmemBytes) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return sms * per;
+    }
     if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;

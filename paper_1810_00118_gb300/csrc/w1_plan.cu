@@ -254,7 +254,7 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
     if (!(o.theta > 0.0) || o.theta > 1.0) return fail(W1_ERR_INVALID_ARG, "theta must lie in (0, 1]");
     if (o.max_iters < 1) return fail(W1_ERR_INVALID_ARG, "max_iters must be >= 1");
     if (o.path < 0 || o.path > 3) return fail(W1_ERR_INVALID_ARG, "path must be 0, 1, 2 or 3");
-    if (o.tune < 0 || o.tune > 2) return fail(W1_ERR_INVALID_ARG, "tune must be 0, 1 or 2");
+    if (o.tune < 0 || o.tune > 3) return fail(W1_ERR_INVALID_ARG, "tune must be 0, 1, 2 or 3");
     if (o.check_every % (2 * tblock_depth()) != 0)
         return fail(W1_ERR_INVALID_ARG, "check_every must be a multiple of twice the temporal block depth (8)");
     // stop tests happen every K steps, so the cap is a multiple of K

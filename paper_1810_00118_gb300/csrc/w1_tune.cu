@@ -56,8 +56,8 @@ void load_cache_file()
     if (!f) return;
     TuneKey k;
     w1_level_choice c;
-    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %lf", &k.dev, &k.nx, &k.ny, &k.norm, &k.batch, &c.path,
-                       &c.cluster, &c.batch, &c.us_per_step) == 9)
+    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %lf %d", &k.dev, &k.nx, &k.ny, &k.norm, &k.batch, &c.path,
+                       &c.cluster, &c.batch, &c.us_per_step, &c.concurrent) == 10)
         g_tune_cache[k] = c;
     std::fclose(f);
 }
@@ -68,8 +68,8 @@ void append_cache_file(const TuneKey& k, const w1_level_choice& c)
     if (!p) return;
     FILE* f = std::fopen(p, "a");
     if (!f) return;
-    std::fprintf(f, "%d %d %d %d %d %d %d %d %.6f\n", k.dev, k.nx, k.ny, k.norm, k.batch, c.path, c.cluster,
-                 c.batch, c.us_per_step);
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %.6f %d\n", k.dev, k.nx, k.ny, k.norm, k.batch, c.path, c.cluster,
+                 c.batch, c.us_per_step, c.concurrent);
     std::fclose(f);
 }
 
@@ -155,7 +155,7 @@ double time_candidate(int norm, int path, int cluster, int nx, int ny, int pairs
 extern "C" w1_status w1_autotune_level(int nx, int ny, int norm, int batch, int objective, int steps,
                                        w1_level_choice* best, w1_level_choice* all, int* n_all)
 {
-    if (nx < 1 || ny < 1 || batch < 1 || !best || (objective != 1 && objective != 2)) {
+    if (nx < 1 || ny < 1 || batch < 1 || !best || objective < 1 || objective > 3) {
         g_tune_err = "bad arguments to w1_autotune_level";
         return W1_ERR_INVALID_ARG;
     }
@@ -165,14 +165,14 @@ extern "C" w1_status w1_autotune_level(int nx, int ny, int norm, int batch, int 
     }
     if (steps < 32) steps = 32;
     steps = (steps + 31) / 32 * 32;
-    const int B = objective == 1 ? 1 : batch;
+    const int B = objective == 2 ? batch : 1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         g_tune_err = "cudaGetDevice failed";
         return W1_ERR_CUDA;
     }
-    const TuneKey key{dev, nx, ny, norm, B};
+    const TuneKey key{dev, nx, ny, norm, objective == 3 ? -1 : B};  // -1: the SM-time objective
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         load_cache_file();
@@ -198,9 +198,9 @@ extern "C" w1_status w1_autotune_level(int nx, int ny, int norm, int batch, int 
     const int cs[5] = {1, 2, 4, 8, 16};
     for (int c : cs)
         if (resident_fits(nx, ny, c) && resident_cluster_ok(norm, c, nx, ny) > 0)
-            cands.push_back(w1_level_choice{1, c, B, 0.0});
-    cands.push_back(w1_level_choice{2, 0, B, 0.0});
-    if (nx % 4 == 0) cands.push_back(w1_level_choice{3, 0, B, 0.0});
+            cands.push_back(w1_level_choice{1, c, B, 0.0, resident_cluster_ok(norm, c, nx, ny)});
+    cands.push_back(w1_level_choice{2, 0, B, 0.0, 1});
+    if (nx % 4 == 0) cands.push_back(w1_level_choice{3, 0, B, 0.0, 1});
 
     float* buf = nullptr;
     double* part = nullptr;
@@ -225,18 +225,23 @@ extern "C" w1_status w1_autotune_level(int nx, int ny, int norm, int batch, int 
     }
     w1_status ret = W1_OK;
     int n_ok = 0;
-    w1_level_choice pick{0, 0, B, 0.0};
+    w1_level_choice pick{0, 0, B, 0.0, 0};
     double best_cost = 1e300;
     if (e != cudaSuccess) {
         g_tune_err = std::string("autotune allocation: ") + cudaGetErrorString(e);
         ret = W1_ERR_CUDA;
     } else {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
         for (auto& c : cands) {
             const double us = time_candidate(norm, c.path, c.cluster, nx, ny, P, steps, buf, part, ctl, s);
             if (us <= 0.0) continue;
             c.us_per_step = us * (double)B / (double)P;
-            if (c.us_per_step < best_cost) {
-                best_cost = c.us_per_step;
+            // objective 3: SM-time of a step (on-chip levels hold one CTA per SM; a
+            // streaming launch spreads over the whole GPU)
+            const double cost = objective == 3 ? c.us_per_step * (c.path == 1 ? c.cluster : sms) : c.us_per_step;
+            if (cost < best_cost) {
+                best_cost = cost;
                 pick = c;
             }
             if (all && n_ok < 8) all[n_ok] = c;

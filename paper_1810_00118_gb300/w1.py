@@ -52,7 +52,7 @@ class Options(ctypes.Structure):
 
 class LevelChoice(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("cluster", ctypes.c_int), ("batch", ctypes.c_int),
-                ("us_per_step", ctypes.c_double)]
+                ("us_per_step", ctypes.c_double), ("concurrent", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):

@@ -20,28 +20,33 @@ def w1():
 
 
 @pytest.mark.parametrize("n", [32, 128, 512])
-@pytest.mark.parametrize("objective,batch", [(1, 1), (2, 1), (2, 48)])
+@pytest.mark.parametrize("objective,batch", [(1, 1), (2, 1), (2, 48), (3, 1)])
 def test_autotune_picks_the_fastest_candidate(w1, n, objective, batch):
     best, cands = w1.autotune_level(n, n, 1, objective, steps=64, batch=batch)
     assert len(cands) >= 3
     paths = {c["path"] for c in cands}
     assert {2, 3} <= paths  # both streaming kernels are always candidates here
     assert 1 in paths  # and every grid here fits on chip
-    assert best["us_per_step"] == min(c["us_per_step"] for c in cands)
+    if objective == 3:  # least SM-time: time x CTAs on chip, time x all SMs when streaming
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        cost = lambda c: c["us_per_step"] * (c["cluster"] if c["path"] == 1 else sms)  # noqa: E731
+        assert cost(best) == min(cost(c) for c in cands)
+    else:
+        assert best["us_per_step"] == min(c["us_per_step"] for c in cands)
     assert all(c["us_per_step"] > 0 for c in cands)
-    assert all(c["batch"] == (1 if objective == 1 else batch) for c in cands)
+    assert all(c["batch"] == (batch if objective == 2 else 1) for c in cands)
 
 
 def test_autotune_rejects_bad_arguments(w1):
     with pytest.raises(w1.W1Error):
         w1.autotune_level(64, 64, 4)
     with pytest.raises(w1.W1Error):
-        w1.autotune_level(64, 64, 1, objective=3)
+        w1.autotune_level(64, 64, 1, objective=4)
     with pytest.raises(w1.W1Error):
         w1.autotune_level(64, 64, 1, batch=0)
 
 
-@pytest.mark.parametrize("tune,batch", [(1, 1), (2, 1), (2, 3)])
+@pytest.mark.parametrize("tune,batch", [(1, 1), (2, 1), (2, 3), (3, 1)])
 def test_tuned_plan_solves_like_the_oracle(w1, tune, batch):
     pairs = [synth.pair(2, 50 + k, n=256) for k in range(batch)]
     a0 = np.ascontiguousarray(np.stack([p[0] for p in pairs]), dtype=np.float32)
