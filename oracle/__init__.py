@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "w1_oracle.c")
+_SRC3 = os.path.join(_HERE, "w1_oracle3.c")
 _LIB = os.path.join(_HERE, "libw1_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -72,9 +73,10 @@ class Stats:
 def build(force: bool = False) -> str:
     """Compile w1_oracle.c into libw1_oracle.so next to it (gcc, -O2, no -march)."""
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        stale = not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f) for f in (_SRC, _SRC3))
+        if force or stale:
             tmp = _LIB + f".tmp{os.getpid()}"
-            subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
+            subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, _SRC3, "-lm"],
                            check=True)
             os.replace(tmp, _LIB)
     return _LIB
