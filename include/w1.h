@@ -404,6 +404,60 @@ w1_status w1_state_stats_noalloc(int nx, int ny, double h, int norm, const float
                                  const float* m2, const float* phi, void* stream, w1_stats* out);
 const char* w1_noalloc_last_error(void);
 
+/* ---------------------------------------------------------------------------
+ * Three-dimensional grids.  The discretisation of Sec. 2-3 and Algorithm 3
+ * with d = 3: voxel-centre grid nx x ny x nz with spacing h, device arrays
+ * [nz][ny][nx] FP32 (x fastest), flux components m1, m2, m3 along x, y, z
+ * (the last x-, y-, z-face of the grid carries zero flux), sums weighted by
+ * h^3, backward-difference divergence and forward-difference gradient,
+ * ||A_h|| <= 2 sqrt(3) / h so mu = tau = theta h / (2 sqrt 3).  Each step of
+ * eq. primaldual is two launches (m' with the mbar extrapolation, then phi');
+ * the host reads R^k of eq. pd_stop after every K-th step.  Every pointer is a
+ * device pointer owned by the caller (16-byte alignment not required); the
+ * calls allocate their own scratch and synchronise the stream before they
+ * return.  Errors: W1_ERR_INVALID_ARG (NULL pointer, bad size, unknown norm,
+ * bad options), W1_ERR_SHAPE (sizes not divisible by 2^(levels-1)), W1_ERR_MASS,
+ * W1_ERR_NOMEM, W1_ERR_CUDA; message in w1_3d_last_error().
+ * ------------------------------------------------------------------------- */
+
+/* Algorithm 3 on a 3-D grid.  rho0, rho1: n = nx ny nz densities.  h <= 0 gives
+ * 1 / max(nx, ny, nz); levels <= 0 gives Sec. 5's L = log2(1/h) - 3 (at least 1,
+ * lowered until every side divides by 2^(L-1) and the coarsest side is >= 2);
+ * tol <= 0 gives eq. stop_tol's formula 1e-6/128 (512 h)^2 (the paper states it
+ * for 2-D grids; taken unchanged for 3-D); options as for the 2-D solver
+ * (check_every 0 = 32; path, tune, eager and algorithm do not apply: every level
+ * runs the two-launch step and the host tests R^k).  Writes *dist = f(m) of the
+ * finest flux; flux (3n floats: m1, m2, m3 planes) and potential (n floats), when
+ * not NULL, receive the finest state; stats: per-level iterations, R^k and eps_l
+ * (nx[], ny[] hold the level sizes; the level's nz is nz >> (levels-1-l)),
+ * f, the dual value, the certified bracket [lb, ub] with the octree route bound,
+ * the masses (sums weighted by h^3).  Returns W1_OK, W1_ERR_NOT_CONVERGED or
+ * W1_ERR_TIMEOUT (dist and stats still written), or an error. */
+w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, int norm, double tol,
+                     const w1_options* opt, const float* rho0, const float* rho1, void* stream,
+                     double* dist, float* flux, float* potential, w1_stats* stats);
+
+/* `iters` steps of eq. primaldual on one 3-D level, in place on m1, m2, m3, phi
+ * (zero-mean rho); mu, tau as given.  *fpr_last (may be NULL) = R^k of the last
+ * step (0 when iters == 0). */
+w1_status w1_cp_steps3d(int nx, int ny, int nz, double h, int norm, float mu, float tau, const float* rho,
+                        float* m1, float* m2, float* m3, float* phi, long long iters, void* stream,
+                        double* fpr_last);
+
+/* Restriction of Algorithm 3 in 3-D: coarse node = mean of its 2x2x2 block;
+ * fine is nx x ny x nz (all even), coarse (nx/2)(ny/2)(nz/2).  Asynchronous. */
+w1_status w1_restrict3d(int nx, int ny, int nz, const float* fine, float* coarse, void* stream);
+
+/* Interpolate of Sec. 3.3 in 3-D (coarse ncx x ncy x ncz to fine 2ncx x 2ncy x
+ * 2ncz): phi trilinear on voxel centres (3/4 own cell, 1/4 the neighbour on the
+ * fine voxel's side per axis, clamped at the walls); each flux component copies
+ * the coarse face on odd fine faces along its axis, averages the two coarse
+ * faces of the cell on even ones, copies across the other axes; zero on the
+ * last face.  Asynchronous. */
+w1_status w1_prolong3d(int ncx, int ncy, int ncz, const float* m1c, const float* m2c, const float* m3c,
+                       const float* phic, float* m1f, float* m2f, float* m3f, float* phif, void* stream);
+const char* w1_3d_last_error(void);
+
 /* Text for a status, and the last error message of the calling thread. */
 const char* w1_status_string(w1_status s);
 const char* w1_last_error(void);

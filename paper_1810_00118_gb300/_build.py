@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libw1.so")
-SOURCES = ["w1_kernels.cu", "w1_pdhg.cu", "w1_plan.cu", "w1_server.cu", "w1_tune.cu", "w1_noalloc.cu"]
+SOURCES = ["w1_kernels.cu", "w1_pdhg.cu", "w1_plan.cu", "w1_server.cu", "w1_tune.cu", "w1_noalloc.cu", "w1_3d.cu"]
 HEADERS = [os.path.join(CSRC, "w1_internal.h"), os.path.join(CSRC, "w1_device.cuh"), os.path.join(ROOT, "include", "w1.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -1,0 +1,644 @@
+// w1_3d.cu -- Algorithm 3 on three-dimensional grids (the paper's analysis is
+// for general d; this is d = 3).
+//
+// Voxel-centre grid nx x ny x nz, arrays [nz][ny][nx] (x fastest), flux
+// components m1, m2, m3 along x, y, z with zero flux through the boundary,
+// inner products weighted by h^3.  One step of eq. primaldual is two launches:
+//   k3_mprime  m' = prox_{mu||.||_p}(m + mu grad phi) in place, mbar = 2 m' - m
+//   k3_phi     phi' = phi + tau (div mbar - rho) in place (+ the terms of R^k)
+// (a node's m' needs phi on three neighbours, its phi' needs mbar on three
+// others: the launch boundary is the synchronisation).  Every K-th step forms
+// R^k of eq. pd_stop (FP32 terms and per-thread values, FP64 across blocks) and
+// the host reads it to decide the level's stop, as in the eager mode of the 2-D
+// plans.  Restriction (2x2x2 means), the voxel-centre Interpolate, prep and the
+// certificates (f(m), the dual bound, the octree route bound) are kernels too.
+// This path is one step per launch over global memory (no temporal blocking or
+// on-chip levels): 3-D grids are outside the measured workloads.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "w1_device.cuh"
+#include "w1_internal.h"
+
+namespace w1 {
+
+static constexpr int T3 = 256;
+
+struct Dims3 {
+    int nx, ny, nz;
+    long long n;
+};
+
+__device__ __forceinline__ void node3(const Dims3& d, long long q, int& i, int& j, int& k)
+{
+    const long long plane = (long long)d.nx * d.ny;
+    k = (int)(q / plane);
+    const long long r = q - (long long)k * plane;
+    j = (int)(r / d.nx);
+    i = (int)(r - (long long)j * d.nx);
+}
+
+// Node-wise proximal map of mu ||.||_p on R^3.
+template <int NORM>
+__device__ __forceinline__ void prox3(const float v[3], float mu, float o[3])
+{
+    if (NORM == W1_NORM_L1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[c] = v[c] - fminf(fmaxf(v[c], -mu), mu);
+    } else if (NORM == W1_NORM_L2) {
+        const float s = fmaxf(1.f - mu * rsqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), 0.f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[c] = v[c] * s;
+    } else {
+        // v - mu Proj_{l1 ball}(v / mu): shrink the magnitudes by the threshold t of
+        // the projection (sorted magnitudes s0 >= s1 >= s2)
+        const float a0 = fabsf(v[0]), a1 = fabsf(v[1]), a2 = fabsf(v[2]);
+        if (a0 + a1 + a2 <= mu) {  // v / mu inside the ball: the projection is v / mu, prox = 0
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[c] = 0.f;
+            return;
+        }
+        float s0 = fmaxf(a0, fmaxf(a1, a2)), s2 = fminf(a0, fminf(a1, a2));
+        float s1 = a0 + a1 + a2 - s0 - s2;
+        // threshold on v / mu scaled by mu: largest r with s_r - (cum_r - mu) / (r + 1) > 0
+        float t = s0 - mu;
+        const float t1 = 0.5f * (s0 + s1 - mu);
+        if (s1 - t1 > 0.f) t = t1;
+        const float t2 = (s0 + s1 + s2 - mu) / 3.f;
+        if (s2 - t2 > 0.f) t = t2;
+        // projection p = sign(v) max(|v| - t, 0) / mu ; prox = v - mu p
+        const float a[3] = {a0, a1, a2};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float pm = fmaxf(a[c] - t, 0.f);  // mu * |p_c|
+            o[c] = copysignf(a[c] - pm, v[c]);
+        }
+    }
+}
+
+template <int NORM>
+__global__ void __launch_bounds__(T3) k3_mprime(Dims3 d, float mu, float ih, float* __restrict__ m1,
+                                                 float* __restrict__ m2, float* __restrict__ m3,
+                                                 const float* __restrict__ phi, float* __restrict__ b1,
+                                                 float* __restrict__ b2, float* __restrict__ b3)
+{
+    const long long q = (long long)blockIdx.x * T3 + threadIdx.x;
+    if (q >= d.n) return;
+    int i, j, k;
+    node3(d, q, i, j, k);
+    const float p = phi[q];
+    const bool e1 = i < d.nx - 1, e2 = j < d.ny - 1, e3 = k < d.nz - 1;
+    const float v[3] = {e1 ? fmaf(mu * ih, phi[q + 1] - p, m1[q]) : 0.f,
+                        e2 ? fmaf(mu * ih, phi[q + d.nx] - p, m2[q]) : 0.f,
+                        e3 ? fmaf(mu * ih, phi[q + (long long)d.nx * d.ny] - p, m3[q]) : 0.f};
+    float o[3];
+    prox3<NORM>(v, mu, o);
+    if (!e1) o[0] = 0.f;
+    if (!e2) o[1] = 0.f;
+    if (!e3) o[2] = 0.f;
+    b1[q] = 2.f * o[0] - m1[q];
+    b2[q] = 2.f * o[1] - m2[q];
+    b3[q] = 2.f * o[2] - m3[q];
+    m1[q] = o[0];
+    m2[q] = o[1];
+    m3[q] = o[2];
+}
+
+// phi' = phi + tau (div mbar - rho); on a test step also R^k (dm = mbar - m').
+template <bool CHECK>
+__global__ void __launch_bounds__(T3) k3_phi(Dims3 d, float tau, float ih, double mu_d, double tau_d, double h,
+                                              const float* __restrict__ rho, float* __restrict__ phi,
+                                              const float* __restrict__ b1, const float* __restrict__ b2,
+                                              const float* __restrict__ b3, const float* __restrict__ m1,
+                                              const float* __restrict__ m2, const float* __restrict__ m3,
+                                              double* part, unsigned int* counter, double* r_out)
+{
+    const long long q = (long long)blockIdx.x * T3 + threadIdx.x;
+    float sa = 0.f, sb = 0.f, sc = 0.f;
+    if (q < d.n) {
+        int i, j, k;
+        node3(d, q, i, j, k);
+        const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+        const float dv = (b1[q] - (i > 0 ? b1[q - 1] : 0.f)) + (b2[q] - (j > 0 ? b2[q - sy] : 0.f)) +
+                         (b3[q] - (k > 0 ? b3[q - sz] : 0.f));
+        const float dp = tau * fmaf(dv, ih, -rho[q]);
+        phi[q] += dp;
+        if (CHECK) {
+            auto dm = [&](const float* b, const float* m, long long x) { return b[x] - m[x]; };
+            const float d1 = dm(b1, m1, q), d2 = dm(b2, m2, q), d3 = dm(b3, m3, q);
+            const float dd = (d1 - (i > 0 ? dm(b1, m1, q - 1) : 0.f)) + (d2 - (j > 0 ? dm(b2, m2, q - sy) : 0.f)) +
+                             (d3 - (k > 0 ? dm(b3, m3, q - sz) : 0.f));
+            sa = d1 * d1 + d2 * d2 + d3 * d3;
+            sb = dp * dp;
+            sc = dp * dd;  // h <dphi, div dm> before the 1/h
+        }
+    }
+    if (!CHECK) return;
+    __shared__ double sh[32 * 3];
+    __shared__ bool last;
+    double v[3] = {(double)sa, (double)sb, (double)sc};
+    block_sum<3>(v, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x * 3 + 0] = v[0];
+        part[blockIdx.x * 3 + 1] = v[1];
+        part[blockIdx.x * 3 + 2] = v[2];
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double t[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        for (int c = 0; c < 3; ++c) t[c] += ((volatile double*)part)[b * 3 + c];
+    block_sum<3>(t, sh);
+    if (threadIdx.x == 0) {
+        *r_out = (t[0] / mu_d + t[1] / tau_d - 2.0 * t[2] / h) * h * h * h;
+        *counter = 0;
+    }
+}
+
+__global__ void k3_restrict(Dims3 c, const float* __restrict__ f, float* __restrict__ out)
+{
+    const long long q = (long long)blockIdx.x * T3 + threadIdx.x;
+    if (q >= c.n) return;
+    int I, J, K;
+    node3(c, q, I, J, K);
+    const int nx = 2 * c.nx, ny = 2 * c.ny;
+    float s = 0.f;
+    for (int cz = 0; cz < 2; ++cz)
+        for (int b = 0; b < 2; ++b) {
+            const float* r = f + ((long long)(2 * K + cz) * ny + (2 * J + b)) * nx + 2 * I;
+            s += r[0] + r[1];
+        }
+    out[q] = 0.125f * s;
+}
+
+__global__ void k3_prolong(Dims3 c, const float* __restrict__ m1c, const float* __restrict__ m2c,
+                           const float* __restrict__ m3c, const float* __restrict__ phic, float* __restrict__ m1f,
+                           float* __restrict__ m2f, float* __restrict__ m3f, float* __restrict__ phif)
+{
+    const Dims3 f{2 * c.nx, 2 * c.ny, 2 * c.nz, 8 * c.n};
+    const long long q = (long long)blockIdx.x * T3 + threadIdx.x;
+    if (q >= f.n) return;
+    int i, j, k;
+    node3(f, q, i, j, k);
+    const int I = i >> 1, J = j >> 1, K = k >> 1;
+    const int In = min(max((i & 1) ? I + 1 : I - 1, 0), c.nx - 1);
+    const int Jn = min(max((j & 1) ? J + 1 : J - 1, 0), c.ny - 1);
+    const int Kn = min(max((k & 1) ? K + 1 : K - 1, 0), c.nz - 1);
+    auto C = [&](const float* a, int z, int y, int x) { return a[((long long)z * c.ny + y) * c.nx + x]; };
+    float p = 0.f;
+    for (int cz = 0; cz < 2; ++cz)
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+                const float w = (a ? 0.25f : 0.75f) * (b ? 0.25f : 0.75f) * (cz ? 0.25f : 0.75f);
+                p += w * C(phic, cz ? Kn : K, b ? Jn : J, a ? In : I);
+            }
+    phif[q] = p;
+    float v1 = (i & 1) ? C(m1c, K, J, I) : 0.5f * ((I > 0 ? C(m1c, K, J, I - 1) : 0.f) + C(m1c, K, J, I));
+    float v2 = (j & 1) ? C(m2c, K, J, I) : 0.5f * ((J > 0 ? C(m2c, K, J - 1, I) : 0.f) + C(m2c, K, J, I));
+    float v3 = (k & 1) ? C(m3c, K, J, I) : 0.5f * ((K > 0 ? C(m3c, K - 1, J, I) : 0.f) + C(m3c, K, J, I));
+    m1f[q] = i == f.nx - 1 ? 0.f : v1;
+    m2f[q] = j == f.ny - 1 ? 0.f : v2;
+    m3f[q] = k == f.nz - 1 ? 0.f : v3;
+}
+
+// Certificates: per-block FP64 partials of f, dual, |residual|, |rho| and the
+// maximum of the dual norm of grad phi; the residual (masses) goes to q.
+template <int NORM>
+__global__ void __launch_bounds__(T3) k3_final_a(Dims3 d, double h, const float* __restrict__ m1,
+                                                  const float* __restrict__ m2, const float* __restrict__ m3,
+                                                  const float* __restrict__ phi, const float* __restrict__ rho,
+                                                  double* __restrict__ q_out, double* part)
+{
+    const long long q = (long long)blockIdx.x * T3 + threadIdx.x;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    double g = 0.0;
+    if (q < d.n) {
+        int i, j, k;
+        node3(d, q, i, j, k);
+        const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+        const double a1 = fabs((double)m1[q]), a2 = fabs((double)m2[q]), a3 = fabs((double)m3[q]);
+        v[0] = NORM == W1_NORM_L1 ? a1 + a2 + a3
+               : NORM == W1_NORM_L2 ? sqrt(a1 * a1 + a2 * a2 + a3 * a3)
+                                    : fmax(a1, fmax(a2, a3));
+        v[1] = -(double)phi[q] * (double)rho[q];
+        const double dv = (((double)m1[q] * (i < d.nx - 1) - (i > 0 ? (double)m1[q - 1] : 0.0)) +
+                           ((double)m2[q] * (j < d.ny - 1) - (j > 0 ? (double)m2[q - sy] : 0.0)) +
+                           ((double)m3[q] * (k < d.nz - 1) - (k > 0 ? (double)m3[q - sz] : 0.0))) / h;
+        const double e = (double)rho[q] - dv;
+        q_out[q] = e * h * h * h;
+        v[2] = fabs(e);
+        v[3] = fabs((double)rho[q]);
+        const double p = phi[q];
+        const double g1 = i < d.nx - 1 ? fabs(((double)phi[q + 1] - p) / h) : 0.0;
+        const double g2 = j < d.ny - 1 ? fabs(((double)phi[q + sy] - p) / h) : 0.0;
+        const double g3 = k < d.nz - 1 ? fabs(((double)phi[q + sz] - p) / h) : 0.0;
+        g = NORM == W1_NORM_L1 ? fmax(g1, fmax(g2, g3))                      // q = infinity
+            : NORM == W1_NORM_L2 ? sqrt(g1 * g1 + g2 * g2 + g3 * g3) : g1 + g2 + g3;  // q = 2, q = 1
+    }
+    __shared__ double sh[32 * 4];
+    block_sum<4>(v, sh);
+    __shared__ double gm[32];
+    g = warp_max(g);
+    if ((threadIdx.x & 31) == 0) gm[threadIdx.x >> 5] = g;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        for (int w = 0; w < T3 / 32; ++w) mx = fmax(mx, gm[w]);
+        for (int c = 0; c < 4; ++c) part[blockIdx.x * 5 + c] = v[c];
+        part[blockIdx.x * 5 + 4] = mx;
+    }
+}
+
+struct Stats3Dev {
+    double f, dual, res_l1, rho_l1, gmax, lb, route, ub;
+};
+
+// One block: the sums of the partials, then the dyadic route bound of the
+// residual masses over the octree (the oracle's route bound): each pass sums
+// 2x2x2 (or 2x2, 2) blocks into a compact coarser grid (ping-pong between q and
+// q2), charging every mass the distance to its block's corner; the masses left
+// on the last grid are charged its diameter.
+__global__ void __launch_bounds__(1024) k3_final_b(Dims3 d, double h, const double* part, int nblk, double* q,
+                                                    double* q2, Stats3Dev* out)
+{
+    __shared__ double sh[32 * 4];
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    double mx = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        for (int c = 0; c < 4; ++c) t[c] += part[b * 5 + c];
+        mx = fmax(mx, part[b * 5 + 4]);
+    }
+    block_sum<4>(t, sh);
+    __shared__ double gmx[32];
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) gmx[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    double* src = q;
+    double* dst = q2;
+    int cx = d.nx, cy = d.ny, cz = d.nz;
+    double hx = h, hy = h, hz = h, cost = 0.0;
+    for (;;) {
+        const int px = cx > 1 && cx % 2 == 0, py = cy > 1 && cy % 2 == 0, pz = cz > 1 && cz % 2 == 0;
+        const int odd = (cx > 1 && cx % 2) || (cy > 1 && cy % 2) || (cz > 1 && cz % 2);
+        if (odd || (!px && !py && !pz)) break;
+        const int bx = px ? 2 : 1, by = py ? 2 : 1, bz = pz ? 2 : 1;
+        const int ncx = cx / bx, ncy = cy / by, ncz = cz / bz;
+        const long long cells = (long long)ncx * ncy * ncz;
+        for (long long c = threadIdx.x; c < cells; c += blockDim.x) {
+            const int K = (int)(c / ((long long)ncx * ncy));
+            const long long r = c - (long long)K * ncx * ncy;
+            const int J = (int)(r / ncx), I = (int)(r - (long long)J * ncx);
+            double tot = 0.0;
+            for (int zc = 0; zc < bz; ++zc)
+                for (int b = 0; b < by; ++b)
+                    for (int a = 0; a < bx; ++a) {
+                        const double qa = src[((long long)(bz * K + zc) * cy + (by * J + b)) * cx + (bx * I + a)];
+                        cost += fabs(qa) * (a * hx + b * hy + zc * hz);
+                        tot += qa;
+                    }
+            dst[c] = tot;
+        }
+        __syncthreads();
+        double* tmp = src;
+        src = dst;
+        dst = tmp;
+        cx = ncx;
+        cy = ncy;
+        cz = ncz;
+        if (px) hx *= 2.0;
+        if (py) hy *= 2.0;
+        if (pz) hz *= 2.0;
+    }
+    double pn[3] = {cost, 0.0, 0.0};
+    for (long long c = threadIdx.x; c < (long long)cx * cy * cz; c += blockDim.x) {
+        const double v = src[c];
+        if (v > 0) pn[1] += v;
+        else pn[2] -= v;
+    }
+    block_sum<3>(pn, sh);
+    if (threadIdx.x == 0) {
+        double g = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) g = fmax(g, gmx[w]);
+        const double h3 = h * h * h;
+        out->f = t[0] * h3;
+        out->dual = t[1] * h3;
+        out->res_l1 = t[2] * h3;
+        out->rho_l1 = t[3] * h3;
+        out->gmax = g;
+        out->lb = out->dual / fmax(1.0, g);
+        out->route = pn[0] + ((cx - 1) * hx + (cy - 1) * hy + (cz - 1) * hz) * fmax(pn[1], pn[2]);
+        out->ub = out->f + out->route;
+    }
+}
+
+static dim3 grid3(long long n) { return dim3((unsigned)((n + T3 - 1) / T3)); }
+
+static cudaError_t launch_mprime(int norm, const Dims3& d, float mu, float ih, float* m1, float* m2, float* m3,
+                                 const float* phi, float* b1, float* b2, float* b3, cudaStream_t s)
+{
+    const dim3 g = grid3(d.n);
+    if (norm == W1_NORM_L1) k3_mprime<W1_NORM_L1><<<g, T3, 0, s>>>(d, mu, ih, m1, m2, m3, phi, b1, b2, b3);
+    else if (norm == W1_NORM_L2) k3_mprime<W1_NORM_L2><<<g, T3, 0, s>>>(d, mu, ih, m1, m2, m3, phi, b1, b2, b3);
+    else k3_mprime<W1_NORM_LINF><<<g, T3, 0, s>>>(d, mu, ih, m1, m2, m3, phi, b1, b2, b3);
+    return cudaGetLastError();
+}
+
+// Device scratch of a 3-D call: mbar planes, partials, counter, R^k, certificate.
+struct Scratch3 {
+    float* b = nullptr;      // 3 planes
+    double* part = nullptr;  // 5 per block
+    unsigned int* counter = nullptr;
+    double* r = nullptr;
+    double* q = nullptr;  // 2 planes of FP64 residual masses
+    Stats3Dev* st = nullptr;
+    ~Scratch3()
+    {
+        cudaFree(b);
+        cudaFree(part);
+        cudaFree(counter);
+        cudaFree(r);
+        cudaFree(q);
+        cudaFree(st);
+    }
+    cudaError_t alloc(long long n, bool certificate)
+    {
+        cudaError_t e = cudaMalloc(&b, 3 * n * sizeof(float));
+        const long long blocks = (n + T3 - 1) / T3;
+        if (e == cudaSuccess) e = cudaMalloc(&part, blocks * 5 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&counter, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemset(counter, 0, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMalloc(&r, sizeof(double));
+        if (e == cudaSuccess && certificate) e = cudaMalloc(&q, 2 * n * sizeof(double));
+        if (e == cudaSuccess && certificate) e = cudaMalloc(&st, sizeof(Stats3Dev));
+        return e;
+    }
+};
+
+// `steps` steps on one level; the last one forms R^k into sc.r when test is set.
+static cudaError_t steps3(int norm, const Dims3& d, double h, float mu, float tau, const float* rho, float* m1,
+                          float* m2, float* m3, float* phi, long long steps, bool test, Scratch3& sc, cudaStream_t s)
+{
+    const float ih = (float)(1.0 / h);
+    const long long n = d.n;
+    float *b1 = sc.b, *b2 = sc.b + n, *b3 = sc.b + 2 * n;
+    for (long long k = 0; k < steps; ++k) {
+        cudaError_t e = launch_mprime(norm, d, mu, ih, m1, m2, m3, phi, b1, b2, b3, s);
+        if (e != cudaSuccess) return e;
+        if (test && k + 1 == steps)
+            k3_phi<true><<<grid3(n), T3, 0, s>>>(d, tau, ih, mu, tau, h, rho, phi, b1, b2, b3, m1, m2, m3, sc.part,
+                                                 sc.counter, sc.r);
+        else
+            k3_phi<false><<<grid3(n), T3, 0, s>>>(d, tau, ih, mu, tau, h, rho, phi, b1, b2, b3, m1, m2, m3, sc.part,
+                                                  sc.counter, sc.r);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t final3(int norm, const Dims3& d, double h, const float* m1, const float* m2, const float* m3,
+                          const float* phi, const float* rho, Scratch3& sc, cudaStream_t s)
+{
+    const dim3 g = grid3(d.n);
+    if (norm == W1_NORM_L1) k3_final_a<W1_NORM_L1><<<g, T3, 0, s>>>(d, h, m1, m2, m3, phi, rho, sc.q, sc.part);
+    else if (norm == W1_NORM_L2) k3_final_a<W1_NORM_L2><<<g, T3, 0, s>>>(d, h, m1, m2, m3, phi, rho, sc.q, sc.part);
+    else k3_final_a<W1_NORM_LINF><<<g, T3, 0, s>>>(d, h, m1, m2, m3, phi, rho, sc.q, sc.part);
+    k3_final_b<<<1, 1024, 0, s>>>(d, h, sc.part, (int)g.x, sc.q, sc.q + d.n, sc.st);
+    return cudaGetLastError();
+}
+
+}  // namespace w1
+
+using namespace w1;
+
+namespace {
+thread_local std::string g_err3;
+w1_status fail3(w1_status st, const std::string& m)
+{
+    g_err3 = m;
+    return st;
+}
+#define W1_CK3(call)                                                                                \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) {                                                                    \
+            cudaGetLastError();                                                                     \
+            return fail3(e_ == cudaErrorMemoryAllocation ? W1_ERR_NOMEM : W1_ERR_CUDA,              \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+        }                                                                                           \
+    } while (0)
+}  // namespace
+
+extern "C" const char* w1_3d_last_error(void) { return g_err3.c_str(); }
+
+extern "C" w1_status w1_cp_steps3d(int nx, int ny, int nz, double h, int norm, float mu, float tau, const float* rho,
+                                   float* m1, float* m2, float* m3, float* phi, long long iters, void* stream,
+                                   double* fpr_last)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !rho || !m1 || !m2 || !m3 || !phi || iters < 0)
+        return fail3(W1_ERR_INVALID_ARG, "bad arguments to w1_cp_steps3d");
+    if (norm != W1_NORM_L1 && norm != W1_NORM_L2 && norm != W1_NORM_LINF)
+        return fail3(W1_ERR_INVALID_ARG, "norm must be 1, 2 or 3");
+    const Dims3 d{nx, ny, nz, (long long)nx * ny * nz};
+    Scratch3 sc;
+    W1_CK3(sc.alloc(d.n, false));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    W1_CK3(steps3(norm, d, h, mu, tau, rho, m1, m2, m3, phi, iters, true, sc, s));
+    double r = 0.0;
+    if (iters > 0) W1_CK3(cudaMemcpyAsync(&r, sc.r, sizeof(double), cudaMemcpyDeviceToHost, s));
+    W1_CK3(cudaStreamSynchronize(s));
+    if (fpr_last) *fpr_last = r;
+    return W1_OK;
+}
+
+extern "C" w1_status w1_restrict3d(int nx, int ny, int nz, const float* fine, float* coarse, void* stream)
+{
+    if (nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 || nz % 2 || !fine || !coarse)
+        return fail3(W1_ERR_SHAPE, "w1_restrict3d needs even nx, ny, nz");
+    const Dims3 c{nx / 2, ny / 2, nz / 2, (long long)(nx / 2) * (ny / 2) * (nz / 2)};
+    k3_restrict<<<grid3(c.n), T3, 0, static_cast<cudaStream_t>(stream)>>>(c, fine, coarse);
+    W1_CK3(cudaGetLastError());
+    return W1_OK;
+}
+
+extern "C" w1_status w1_prolong3d(int ncx, int ncy, int ncz, const float* m1c, const float* m2c, const float* m3c,
+                                  const float* phic, float* m1f, float* m2f, float* m3f, float* phif, void* stream)
+{
+    if (ncx < 1 || ncy < 1 || ncz < 1 || !m1c || !m2c || !m3c || !phic || !m1f || !m2f || !m3f || !phif)
+        return fail3(W1_ERR_INVALID_ARG, "bad arguments to w1_prolong3d");
+    const Dims3 c{ncx, ncy, ncz, (long long)ncx * ncy * ncz};
+    k3_prolong<<<grid3(8 * c.n), T3, 0, static_cast<cudaStream_t>(stream)>>>(c, m1c, m2c, m3c, phic, m1f, m2f, m3f,
+                                                                           phif);
+    W1_CK3(cudaGetLastError());
+    return W1_OK;
+}
+
+extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, int norm, double tol,
+                                const w1_options* opt, const float* rho0, const float* rho1, void* stream,
+                                double* dist, float* flux, float* potential, w1_stats* stats)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || !rho0 || !rho1 || !dist) return fail3(W1_ERR_INVALID_ARG, "bad arguments");
+    if (norm != W1_NORM_L1 && norm != W1_NORM_L2 && norm != W1_NORM_LINF)
+        return fail3(W1_ERR_INVALID_ARG, "norm must be 1, 2 or 3");
+    w1_options o;
+    w1_default_options(&o);
+    if (opt) o = *opt;
+    const int K = o.check_every > 0 ? o.check_every : 32;
+    if (K < 1 || !(o.theta > 0.0) || o.theta > 1.0 || o.max_iters < 1)
+        return fail3(W1_ERR_INVALID_ARG, "bad options");
+    if (!(h > 0.0)) h = 1.0 / (double)std::max(nx, std::max(ny, nz));
+    if (levels <= 0) {  // the paper's L = log2(1/h) - 3, kept divisible, coarsest side >= 2
+        int L = (int)std::lround(std::log2(1.0 / h)) - 3;
+        if (L < 1) L = 1;
+        while (L > 1 && ((nx % (1 << (L - 1))) || (ny % (1 << (L - 1))) || (nz % (1 << (L - 1))) ||
+                         (nx >> (L - 1)) < 2 || (ny >> (L - 1)) < 2 || (nz >> (L - 1)) < 2))
+            --L;
+        levels = L;
+    }
+    if (levels > W1_MAX_LEVELS) return fail3(W1_ERR_SHAPE, "at most 16 levels");
+    const int div = 1 << (levels - 1);
+    if (nx % div || ny % div || nz % div) return fail3(W1_ERR_SHAPE, "nx, ny, nz must be divisible by 2^(levels-1)");
+    if (!(tol > 0.0)) tol = 1e-6 / 128.0 * (512.0 * h) * (512.0 * h);  // eq. stop_tol's 2-D formula (reading)
+    int dev = 0;
+    W1_CK3(cudaGetDevice(&dev));
+    W1_CK3(resident_prepare(dev));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long n = (long long)nx * ny * nz;
+    // per level: rho, m1, m2, m3, phi
+    std::vector<long long> off(levels + 1, 0);
+    for (int l = 0; l < levels; ++l) {
+        const int sh = levels - 1 - l;
+        off[l + 1] = off[l] + 5 * ((long long)(nx >> sh) * (ny >> sh) * (nz >> sh));
+    }
+    float* arena = nullptr;
+    W1_CK3(cudaMalloc(&arena, off[levels] * sizeof(float)));
+    struct Free {
+        float* p;
+        ~Free() { cudaFree(p); }
+    } free_arena{arena};
+    Scratch3 sc;
+    W1_CK3(sc.alloc(n, true));
+    Ctl* ctl = nullptr;
+    double* part = nullptr;
+    W1_CK3(cudaMalloc(&ctl, sizeof(Ctl)));
+    struct FreeC {
+        Ctl* c;
+        double* p;
+        ~FreeC()
+        {
+            cudaFree(c);
+            cudaFree(p);
+        }
+    } free_c{ctl, nullptr};
+    W1_CK3(cudaMalloc(&part, prep_part_doubles(1) * sizeof(double)));
+    free_c.p = part;
+    W1_CK3(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    auto lvl = [&](int l, int c) {
+        const int sh = levels - 1 - l;
+        const long long ln = (long long)(nx >> sh) * (ny >> sh) * (nz >> sh);
+        return arena + off[l] + c * ln;
+    };
+    // prep (masses with h^3 weights: the prep kernel weights by h_2d^2, so pass h^(3/2))
+    W1_CK3(launch_prep(rho0, rho1, n, 1, 1, std::pow(h, 1.5), ctl, part, lvl(levels - 1, 0), s));
+    Ctl host{};
+    W1_CK3(cudaMemcpyAsync(&host, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    W1_CK3(cudaStreamSynchronize(s));
+    if (host.error) {
+        *dist = NAN;
+        return fail3(W1_ERR_MASS, "densities have different mass or a non-finite value");
+    }
+    for (int l = levels - 1; l > 0; --l) {
+        const int sh = levels - 1 - l;
+        const Dims3 c{(nx >> sh) / 2, (ny >> sh) / 2, (nz >> sh) / 2, 0};
+        const Dims3 cc{c.nx, c.ny, c.nz, (long long)c.nx * c.ny * c.nz};
+        k3_restrict<<<grid3(cc.n), T3, 0, s>>>(cc, lvl(l, 0), lvl(l - 1, 0));
+    }
+    W1_CK3(cudaGetLastError());
+    w1_status ret = W1_OK;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    const auto t0 = std::chrono::steady_clock::now();
+    bool all_conv = true;
+    for (int l = 0; l < levels; ++l) {
+        const int sh = levels - 1 - l;
+        const Dims3 d{nx >> sh, ny >> sh, nz >> sh, (long long)(nx >> sh) * (ny >> sh) * (nz >> sh)};
+        const double hl = h * (double)(1 << sh);
+        const float mu = (float)(o.theta * hl / (2.0 * std::sqrt(3.0)));  // theta / ||A_h||, ||A_h|| <= 2 sqrt(3) / h
+        const double tl = tol * std::pow(hl / h, o.alpha);
+        if (l == 0) {
+            W1_CK3(cudaMemsetAsync(lvl(0, 1), 0, 4 * d.n * sizeof(float), s));
+        } else {
+            const Dims3 c{d.nx / 2, d.ny / 2, d.nz / 2, d.n / 8};
+            k3_prolong<<<grid3(d.n), T3, 0, s>>>(c, lvl(l - 1, 1), lvl(l - 1, 2), lvl(l - 1, 3), lvl(l - 1, 4),
+                                                 lvl(l, 1), lvl(l, 2), lvl(l, 3), lvl(l, 4));
+            W1_CK3(cudaGetLastError());
+        }
+        long long it = 0;
+        double r = 0.0;
+        bool conv = false, late = false;
+        while (it < o.max_iters) {
+            W1_CK3(steps3(norm, d, hl, mu, mu, lvl(l, 0), lvl(l, 1), lvl(l, 2), lvl(l, 3), lvl(l, 4), K, true, sc, s));
+            it += K;
+            W1_CK3(cudaMemcpyAsync(&r, sc.r, sizeof(double), cudaMemcpyDeviceToHost, s));
+            W1_CK3(cudaStreamSynchronize(s));
+            if (r < tl) {
+                conv = true;
+                break;
+            }
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > o.time_budget_s) {
+                late = true;
+                break;
+            }
+        }
+        if (stats && l < W1_MAX_LEVELS) {
+            stats->nx[l] = d.nx;
+            stats->ny[l] = d.ny;
+            stats->iters[l] = it;
+            stats->fpr[l] = r;
+            stats->tol[l] = tl;
+            stats->path[l] = 2;
+        }
+        all_conv &= conv;
+        if (late) {
+            ret = fail3(W1_ERR_TIMEOUT, "the time budget ran out");
+            break;
+        }
+        if (!conv && ret == W1_OK) ret = fail3(W1_ERR_NOT_CONVERGED, "a level hit max_iters");
+    }
+    const int L = levels;
+    W1_CK3(final3(norm, Dims3{nx, ny, nz, n}, h, lvl(L - 1, 1), lvl(L - 1, 2), lvl(L - 1, 3), lvl(L - 1, 4),
+                  lvl(L - 1, 0), sc, s));
+    Stats3Dev st{};
+    W1_CK3(cudaMemcpyAsync(&st, sc.st, sizeof(st), cudaMemcpyDeviceToHost, s));
+    if (flux) {
+        W1_CK3(cudaMemcpyAsync(flux, lvl(L - 1, 1), 3 * n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    }
+    if (potential) W1_CK3(cudaMemcpyAsync(potential, lvl(L - 1, 4), n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    W1_CK3(cudaStreamSynchronize(s));
+    *dist = st.f;
+    if (stats) {
+        stats->levels = L;
+        stats->w1 = st.f;
+        stats->dual = st.dual;
+        stats->lb = st.lb;
+        stats->ub = st.ub;
+        stats->route = st.route;
+        stats->res_l1 = st.res_l1;
+        stats->rho_l1 = st.rho_l1;
+        stats->gmax = st.gmax;
+        stats->mass0 = host.mass0;
+        stats->mass1 = host.mass1;
+        stats->mass_shift = host.mean;
+        stats->converged = all_conv && ret == W1_OK;
+    }
+    return ret;
+}

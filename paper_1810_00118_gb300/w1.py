@@ -144,6 +144,12 @@ def _load() -> ctypes.CDLL:
         "w1_state_stats": (st, [I, I, D, I, P, P, P, P, P, ctypes.POINTER(_Stats)]),
         "w1_state_stats_noalloc": (st, [I, I, D, I, P, P, P, P, P, ctypes.POINTER(_Stats)]),
         "w1_noalloc_last_error": (ctypes.c_char_p, []),
+        "w1_solve3d": (st, [I, I, I, D, I, I, D, ctypes.POINTER(Options), P, P, P, ctypes.POINTER(D), P, P,
+                            ctypes.POINTER(_Stats)]),
+        "w1_cp_steps3d": (st, [I, I, I, D, I, F, F, P, P, P, P, P, LL, P, ctypes.POINTER(D)]),
+        "w1_restrict3d": (st, [I, I, I, P, P, P]),
+        "w1_prolong3d": (st, [I, I, I, P, P, P, P, P, P, P, P, P]),
+        "w1_3d_last_error": (ctypes.c_char_p, []),
         "w1_plan_bytes": (ctypes.c_size_t, [I, I, D, I, I, D, I, ctypes.POINTER(Options)]),
         "w1_autotune_level": (st, [I, I, I, I, I, I, ctypes.POINTER(LevelChoice), ctypes.POINTER(LevelChoice),
                                    ctypes.POINTER(I)]),
@@ -443,6 +449,54 @@ def state_stats(rho, m1, m2, phi, h, norm, stream=None) -> Stats:
     _check(_lib.w1_state_stats(nx, ny, h, norm, _dev_ptr(rho), _dev_ptr(m1, rho.shape), _dev_ptr(m2, rho.shape),
                                _dev_ptr(phi, rho.shape), _stream_ptr(stream), ctypes.byref(s)))
     return Stats._from(s)
+
+
+def _check3(status: int, ok=(OK,)):
+    if status not in ok:
+        raise W1Error(status, _lib.w1_3d_last_error().decode())
+    return status
+
+
+def solve3d(rho0, rho1, norm=NORM_L1, h=0.0, levels=0, tol=0.0, flux=None, potential=None, stream=None,
+            **options):
+    """Algorithm 3 on a 3-D grid (w1_solve3d).  rho0, rho1: [nz, ny, nx] device
+    tensors; flux ([3, nz, ny, nx]) and potential ([nz, ny, nx]) receive the finest
+    state when given.  Returns (W1, Stats, status); NOT_CONVERGED and TIMEOUT are
+    returned, other errors raise."""
+    nz, ny, nx = rho0.shape
+    opt = default_options(**options)
+    d = ctypes.c_double(0.0)
+    s = _Stats()
+    st = _lib.w1_solve3d(nx, ny, nz, h, levels, norm, tol, ctypes.byref(opt), _dev_ptr(rho0),
+                         _dev_ptr(rho1, rho0.shape), _stream_ptr(stream), ctypes.byref(d),
+                         _dev_ptr(flux, (3, nz, ny, nx)) if flux is not None else None,
+                         _dev_ptr(potential, rho0.shape) if potential is not None else None, ctypes.byref(s))
+    _check3(st, ok=(OK, ERR_NOT_CONVERGED, ERR_TIMEOUT))
+    return d.value, Stats._from(s), st
+
+
+def cp_steps3d(rho, m1, m2, m3, phi, h, norm, mu, tau, iters, stream=None) -> float:
+    """`iters` steps of eq. primaldual on a 3-D level, in place; returns R^k of the last step."""
+    nz, ny, nx = rho.shape
+    f = ctypes.c_double(0.0)
+    _check3(_lib.w1_cp_steps3d(nx, ny, nz, h, norm, mu, tau, _dev_ptr(rho),
+                               *(_dev_ptr(t, rho.shape) for t in (m1, m2, m3, phi)), int(iters),
+                               _stream_ptr(stream), ctypes.byref(f)))
+    return f.value
+
+
+def restrict3d(fine, out, stream=None):
+    nz, ny, nx = fine.shape
+    _check3(_lib.w1_restrict3d(nx, ny, nz, _dev_ptr(fine), _dev_ptr(out, (nz // 2, ny // 2, nx // 2)),
+                               _stream_ptr(stream)))
+    return out
+
+
+def prolong3d(m1c, m2c, m3c, phic, m1f, m2f, m3f, phif, stream=None):
+    ncz, ncy, ncx = phic.shape
+    fs = (2 * ncz, 2 * ncy, 2 * ncx)
+    _check3(_lib.w1_prolong3d(ncx, ncy, ncz, *(_dev_ptr(t, phic.shape) for t in (m1c, m2c, m3c, phic)),
+                              *(_dev_ptr(t, fs) for t in (m1f, m2f, m3f, phif)), _stream_ptr(stream)))
 
 
 def status_string(status: int) -> str:

@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "centres", "normalise", "gaussian_mixture", "ellipse_texture", "pair",
-    "WORKLOADS", "to_f32_pair",
+    "WORKLOADS", "to_f32_pair", "gaussian_mixture3", "pair3",
 ]
 
 
@@ -127,3 +127,32 @@ def to_f32_pair(r0: np.ndarray, r1: np.ndarray):
     a0 = np.ascontiguousarray(r0, dtype=np.float32)
     a1 = np.ascontiguousarray(r1, dtype=np.float32)
     return a0, a1, a0.astype(np.float64), a1.astype(np.float64)
+
+
+def gaussian_mixture3(nx: int, ny: int, nz: int, k: int, floor: float, rng: np.random.Generator) -> np.ndarray:
+    """The 3-D counterpart of gaussian_mixture: k isotropic Gaussian blobs with
+    centres ~ U[0.2,0.8]^3, s ~ U[0.05,0.12], w ~ U[0.5,1], a constant floor,
+    sampled at voxel centres with h = 1 / max(nx, ny, nz), array [nz, ny, nx],
+    normalised so that sum(rho) h^3 = 1."""
+    h = 1.0 / max(nx, ny, nz)
+    z, y, x = ((np.arange(m) + 0.5) * h for m in (nz, ny, nx))
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    r = np.zeros((nz, ny, nx))
+    for _ in range(k):
+        cx, cy, cz = rng.uniform(0.2, 0.8, 3)
+        s = rng.uniform(0.05, 0.12)
+        w = rng.uniform(0.5, 1.0)
+        r += w * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2) / (2.0 * s * s))
+    r += floor
+    return r / (r.sum() * h ** 3)
+
+
+def pair3(n: int, k: int = 0, nx: int | None = None, ny: int | None = None, nz: int | None = None, blobs: int = 4,
+          floor: float = 1e-3):
+    """Density pair k of the 3-D recipe (float64, unit mass each), drawn from
+    default_rng(7000 + k)."""
+    nx = nx if nx is not None else n
+    ny = ny if ny is not None else n
+    nz = nz if nz is not None else n
+    rng = np.random.default_rng(7000 + k)
+    return (gaussian_mixture3(nx, ny, nz, blobs, floor, rng), gaussian_mixture3(nx, ny, nz, blobs, floor, rng))
