@@ -585,12 +585,15 @@ def main():
     ap.add_argument("--serve-batch", type=int, default=1, help="serving: pairs a slot solves together")
     ap.add_argument("--only", default="solve",
                     choices=["solve", "stream-kernel", "tblock-kernel", "resident-kernel", "pdhg-kernel", "serve",
-                             "mixed", "tol-sweep"],
+                             "mixed", "tol-sweep", "solve3d", "3d-kernel"],
                     help="kernel-only runs for profiling: one level's steps through w1_cp_steps")
     ap.add_argument("--kn", type=int, default=256, help="grid side for --only *-kernel")
     ap.add_argument("--kiters", type=int, default=1000, help="steps for --only *-kernel")
     ap.add_argument("--knorm", type=int, default=1)
     ap.add_argument("--kcluster", type=int, default=0, help="--only resident-kernel: CTAs per level (0: auto)")
+    ap.add_argument("--n3", type=int, default=64, help="--only solve3d: grid side of the 3-D solves")
+    ap.add_argument("--pairs3", type=int, default=8, help="--only solve3d: pairs per norm")
+    ap.add_argument("--roof-n3", type=int, default=256, help="--only solve3d: grid side of the step-kernel timing")
     ap.add_argument("--mixed-norm", type=int, default=2, help="mixed-size batch: ground norm")
     ap.add_argument("--mixed-modes", default="loop,lanes,lockstep,lockstep-tuned,persistent")
     ap.add_argument("--mixed-spec", default="", help="mixed-size batch override, e.g. 64:128,128:96")
@@ -603,6 +606,8 @@ def main():
         return run_mixed(args)
     if args.only == "tol-sweep":
         return run_tol_sweep(args)
+    if args.only == "solve3d":
+        return run_solve3d(args)
     if args.only != "solve":
         return run_kernel_only(args)
     return run_gpu(args)
@@ -781,6 +786,86 @@ def run_tol_sweep(args):
     return 0
 
 
+# Algorithmic bytes per node and step of the two-launch 3-D step: m' reads
+# m1..m3 and phi, writes m1..m3 and mbar (40 B); phi' reads mbar, rho and phi
+# and writes phi (24 B).  Neighbour reads hit cache lines already read.
+BYTES3_PER_NODE_STEP = 64.0
+
+
+def run_solve3d(args):
+    """3-D workload: full Algorithm-3 solves (w1_solve3d, h^3 weights, default
+    levels and tolerance) of Gaussian-mixture voxel pairs, each norm; the step
+    kernels on a grid above L2 against the HBM roofline; the FP64 3-D oracle on
+    the host for one pair at the same size (bounded by a step count)."""
+    import torch
+
+    import synth
+    from paper_1810_00118_gb300 import w1
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n = args.n3
+    pairs = [synth.pair3(n, k) for k in range(args.pairs3)]
+    dev = [(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(b, dtype=np.float32)).cuda()) for a, b in pairs]
+    for norm in (1, 2, 3):
+        w1.solve3d(*dev[0], norm=norm, stream=stream)  # warm-up
+    rows = []
+    with ClockSampler(0) as clk:
+        for norm in (1, 2, 3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            vals, iters, brackets = [], [], []
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for a, b in dev:
+                v, st, status = w1.solve3d(a, b, norm=norm, stream=stream)
+                vals.append(v)
+                iters.append(st.iters)
+                brackets.append((st.ub - st.lb) / max(abs(v), 1e-300))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            rows.append({"norm": norm, "solves_per_s": len(dev) / (ms / 1e3), "ms_per_solve": ms / len(dev),
+                         "levels": st.levels, "iters_pair0": iters[0], "w1_pair0": vals[0],
+                         "max_rel_bracket": float(max(brackets))})
+            print(json.dumps(rows[-1]), flush=True)
+    # step kernels above L2: 256^3 = 16.8M voxels, 1.07 GB per step
+    rn = args.roof_n3
+    rng = np.random.default_rng(3)
+    rho = torch.from_numpy(rng.normal(size=(rn, rn, rn)).astype(np.float32)).cuda()
+    rho -= rho.mean()
+    st4 = [torch.zeros((rn, rn, rn), device="cuda") for _ in range(4)]
+    h = 1.0 / rn
+    mu = float(np.float32(0.5 * h / (2 * np.sqrt(3.0))))
+    w1.cp_steps3d(rho, *st4, h, 1, mu, mu, 4, stream=stream)
+    steps = 64
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    w1.cp_steps3d(rho, *st4, h, 1, mu, mu, steps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / steps
+    peak, src = peaks()
+    gbs = BYTES3_PER_NODE_STEP * rn ** 3 / (us * 1e-6) / 1e9
+    # oracle on the host: one pair at the solve size, steps timed on a bounded run
+    from oracle import d3
+    r0, r1 = pairs[0]
+    t0 = time.perf_counter()
+    ref = d3.multilevel(r0.astype(np.float32).astype(np.float64), r1.astype(np.float32).astype(np.float64),
+                        levels=rows[0]["levels"], norm=1, replay=rows[0]["iters_pair0"])
+    cpu_s = time.perf_counter() - t0
+    out = {"only": "solve3d", "grid": [n, n, n], "pairs_per_norm": len(dev), "rows": rows,
+           "step_kernels": {"grid": [rn, rn, rn], "us_per_step": us, "alg_bytes_per_step": BYTES3_PER_NODE_STEP * rn ** 3,
+                            "achieved_GBps": gbs, "peak_GBps": peak, "frac": gbs / peak, "peak_source": src},
+           "cpu_oracle": {"norm": 1, "s_per_solve": cpu_s, "solves_per_s": 1.0 / cpu_s, "cores": 1,
+                          "w1_rel_diff_vs_gpu": abs(ref.w1 - rows[0]["w1_pair0"]) / abs(ref.w1),
+                          "sample": "pair 0 replaying the GPU's per-level step counts"},
+           "clocks": clk.summary()}
+    print(json.dumps(out))
+    return 0
+
+
 SERVE_SIZES = (128, 256, 512, 1024)
 SERVE_PROBS = (0.4, 0.3, 0.2, 0.1)
 
@@ -865,6 +950,26 @@ def run_kernel_only(args):
     from paper_1810_00118_gb300 import w1
 
     n = args.kn
+    if args.only == "3d-kernel":
+        # steps of the 3-D eq. primaldual (two launches each) on an n^3 grid
+        rng = np.random.default_rng(3)
+        rho = torch.from_numpy(rng.normal(size=(n, n, n)).astype(np.float32)).cuda()
+        rho -= rho.mean()
+        st4 = [torch.zeros((n, n, n), device="cuda") for _ in range(4)]
+        h = 1.0 / n
+        mu = float(np.float32(0.5 * h / (2 * np.sqrt(3.0))))
+        stream = torch.cuda.current_stream()
+        w1.cp_steps3d(rho, *st4, h, args.knorm, mu, mu, 4, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = w1.cp_steps3d(rho, *st4, h, args.knorm, mu, mu, args.kiters, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / args.kiters
+        print(json.dumps({"only": args.only, "n": n, "norm": args.knorm, "steps": args.kiters, "us_per_step": us,
+                          "alg_GBps": BYTES3_PER_NODE_STEP * n ** 3 / (us * 1e-6) / 1e9, "fpr_last": r}))
+        return 0
     r0, r1 = synth.pair(WORKLOAD, 0, n=n)
     rho = torch.from_numpy(np.ascontiguousarray(r0 - r1 - (r0 - r1).mean(), dtype=np.float32)).cuda()
     m1, m2, phi = (torch.zeros((n, n), device="cuda") for _ in range(3))
