@@ -13,9 +13,11 @@ Also measured in the same run:
   roofline : the streaming step kernel on an 8192x8192 grid (1.9 GB of state,
              far above L2), 28 algorithmic bytes per node and step, timed with
              CUDA events on the stream it is launched on;
-  cpu_baseline: the FP64 oracle on this host's cores, per-level step cost
-             measured on a bounded sample and scaled by the oracle's own
-             per-level iteration counts for the same pairs (oracle/iter_table.json).
+  cpu_baseline: the FP64 oracle on this host's cores (one process per core,
+             all at once; one_core_value: a single process alone), per-level
+             step cost measured on a bounded sample and scaled by the oracle's
+             own per-level iteration counts for the same pairs
+             (oracle/iter_table.json).
 
 --impl reference runs that oracle arm alone (CPU only).
 Multi-GPU (torchrun): every rank solves its own pairs (independent replicas).
@@ -170,6 +172,27 @@ def oracle_cost(norm_list, pairs, budget_s=12.0):
     return per_norm, "; ".join(sample)
 
 
+def _oracle_cost_worker(spec):
+    norm_list, pairs, budget_s = spec
+    return oracle_cost(norm_list, pairs, budget_s)
+
+
+def oracle_cost_all_cores(norm_list, pairs, budget_s=12.0):
+    """The same measurement in one spawned process per host core, all at once
+    (independent pairs are the oracle's natural parallelism): solves/s of the
+    whole host = processes x norms / mean seconds per solve of each norm under
+    that load."""
+    import multiprocessing as mp
+
+    import oracle  # builds the oracle library once, before the workers load it
+    oracle._load()
+    workers = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(workers) as pool:
+        res = pool.map(_oracle_cost_worker, [(tuple(norm_list), list(pairs), budget_s)] * workers)
+    per_solve = float(np.mean([sum(r[0].values()) for r in res]))
+    return workers * len(norm_list) / per_solve, workers, res[0][1]
+
+
 def oracle_cost_pdhg(norm_list, budget_s=12.0):
     """Seconds per FP64 oracle solve with Algorithm 4 for each norm: whole
     solves of the bench's first pair, repeated while the budget lasts."""
@@ -196,17 +219,14 @@ def run_reference(args):
     if rank != 0:
         return 0
     pairs = list(range(4))
-    per_solve, sample = None, None
-    times = []
+    sample, cores = None, 1
+    rates = []
     for s in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        per_norm, sample = oracle_cost(NORMS, pairs, budget_s=args.ref_budget)
-        el = time.perf_counter() - t0
+        rate, cores, sample = oracle_cost_all_cores(NORMS, pairs, budget_s=args.ref_budget)
         if s >= args.warmup:
-            times.append(sum(per_norm.values()))
-        per_solve = per_norm
-    t_step = float(np.mean(times))
-    value = len(NORMS) / t_step
+            rates.append(rate)
+    value = float(np.mean(rates))
+    t_step = len(NORMS) / value
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
@@ -214,11 +234,11 @@ def run_reference(args):
         "config": {"workload": "ellipse_texture_512x512_pairs_6_levels_both_norms", "grid": [N, N],
                    "levels": LEVELS, "norms": ["L1", "L2"], "stop": "FPR, eq. stop_tol",
                    "batch_per_norm": args.batch},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": "per-level step cost timed on a bounded sample (" + sample +
-                                   "), scaled by the oracle's own per-level iteration counts"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{cores} processes at once, each timing the per-level step cost on a bounded "
+                                   "sample (" + sample + ") and scaling it by the oracle's own per-level iteration "
+                                   "counts; value = processes x norms / mean seconds per solve"},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "per_solve_s": {f"L{k}": v for k, v in per_solve.items()},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -458,10 +478,13 @@ def run_gpu(args):
                                     "kind": "oracle", "sample": "FP64 prox-PDHG oracle (numpy, one thread): " + sample}
         elif not args.no_cpu_baseline:
             per_norm, sample = oracle_cost(NORMS, list(range(4)), budget_s=args.ref_budget)
-            cpu_v = len(NORMS) / sum(per_norm.values())
-            line["cpu_baseline"] = {"value": cpu_v, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                    "sample": "per-level step cost timed on a bounded sample (" + sample +
-                                              "), scaled by the oracle's own per-level iteration counts"}
+            one = len(NORMS) / sum(per_norm.values())
+            cpu_v, cores, _ = oracle_cost_all_cores(NORMS, list(range(4)), budget_s=args.ref_budget)
+            line["cpu_baseline"] = {"value": cpu_v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                    "sample": f"{cores} processes at once, each timing the per-level step cost on a "
+                                              "bounded sample (" + sample + ") and scaling it by the oracle's own "
+                                              "per-level iteration counts",
+                                    "one_core_value": one}
         print(json.dumps(line), flush=True)
     for p in plans.values():
         for q in (p if isinstance(p, list) else [p]):
