@@ -722,6 +722,9 @@ static constexpr int RES_RED_BYTES = 1024;  // 32 warps x 3 doubles
 static constexpr int RES_SLOT_BYTES = 512;  // 16 CTAs x 3 doubles + decision
 static constexpr int RESW_RUNS = 4;         // wide bands: runs of four nodes per thread
 static constexpr int RESW_MAX_NODES = RES_THREADS * 4 * RESW_RUNS;  // 16384
+// a CTA waiting for a neighbour's halo row gives up after this long and reports
+// a timeout (the neighbour is at most one step behind in a correct run)
+static constexpr unsigned long long RES_HALO_WAIT_NS = 200000000ull;
 
 int resident_max_nodes() { return RES_MAX_NODES; }
 
@@ -1000,6 +1003,12 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
     float* s2 = s1 + nb;
     float* e1s = s2 + nb;
     float* e2s = e1s + nb;
+    // cluster: phi of the row above the band (pushed by CTA rank + 1 after each
+    // step) and m2' of the row below it (pushed by CTA rank - 1 after each m'),
+    // with one mbarrier each in the slot area
+    float* hphi = e2s + nb;
+    float* hm2 = hphi + nx;
+    const uint32_t bar_phi = smem_u32(slots + 56), bar_m2 = smem_u32(slots + 57);
     const size_t off = (size_t)pair * P.stride + (size_t)jb * nx;
     const float mu = P.mu, tau = P.tau;
     const float cm = P.mu * P.ih, ct = P.tau * P.ih;  // mu / h, tau / h
@@ -1031,18 +1040,42 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
         *reinterpret_cast<float4*>(s1 + idx) = x1;
         *reinterpret_cast<float4*>(s2 + idx) = x2;
     }
+    // each halo row arrives as nx floats per step; phase 0 of bar_phi is the
+    // initial phi, phase s the phi after step s; phase s of bar_m2 the m2' of
+    // step s + 1
+    const bool has_up = CL && rank + 1 < C, has_dn = CL && rank > 0;
+    if (CL && t == 0) {
+        mbar_init(bar_phi, 1);
+        mbar_init(bar_m2, 1);
+        if (has_up) mbar_expect(bar_phi, 4u * nx);
+        if (has_dn) mbar_expect(bar_m2, 4u * nx);
+        mbar_init_fence();
+    }
     if (CL) cg::this_cluster().sync();
     else __syncthreads();
     const int last_row = (rows - 1) * nx;
-    uint32_t ph_up = 0, s2_dn = 0, e2_dn = 0, slots0 = smem_u32(slots);
+    const bool row_top = own && jl == rows - 1, row_bot = own && jl == 0;
+    const int t_top = (rows - 1) * W;  // re-arms bar_phi
+    uint32_t s2_dn = 0, e2_dn = 0, slots0 = smem_u32(slots);
     if (CL) {
-        if (rank + 1 < C) ph_up = dsmem_map(smem_u32(ph + i0), rank + 1);
         if (rank > 0) {
             s2_dn = dsmem_map(smem_u32(s2 + last_row + i0), rank - 1);
             e2_dn = dsmem_map(smem_u32(e2s + last_row + i0), rank - 1);
         }
         slots0 = dsmem_map(smem_u32(slots), 0);
+        // the initial phi of the bottom row goes to the CTA below
+        if (row_bot && has_dn)
+            st_async4(dsmem_map(smem_u32(hphi + i0), rank - 1), make_float4(pv[0], pv[1], pv[2], pv[3]),
+                      dsmem_map(bar_phi, rank - 1));
     }
+    unsigned par = 0;       // parity of the halo phase the next step waits for
+    bool sync_fail = false;  // a halo wait ran out of time (reported as a timeout)
+    auto halo_wait = [&](uint32_t bar) {
+        if (!sync_fail && !mbar_wait(bar, par, RES_HALO_WAIT_NS)) {
+            sync_fail = true;
+            dsmem_st_f64(slots0 + 8u * 51, 1.0);
+        }
+    };
     // m2 of the row below the run (zero flux below the grid)
     auto below4 = [&](const float* arr, uint32_t remote) -> float4 {
         if (jl > 0) return *reinterpret_cast<const float4*>(arr + idx - nx);
@@ -1073,6 +1106,7 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
         reinterpret_cast<unsigned long long*>(slots)[50] = globaltimer();
         slots[48] = 0.0;
         slots[49] = 0.0;
+        slots[51] = 0.0;
     }
     if (CL) cg::this_cluster().sync();
     else __syncthreads();
@@ -1089,7 +1123,14 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
         if (own) {
             float up[4] = {pv[0], pv[1], pv[2], pv[3]};
             if (!top) {
-                const float4 u = (jl < rows - 1) ? *reinterpret_cast<const float4*>(ph + idx + nx) : dsmem_ld4(ph_up);
+                float4 u;
+                if (!CL || jl < rows - 1) {
+                    u = *reinterpret_cast<const float4*>(ph + idx + nx);
+                } else {  // the top row of a band below another CTA's
+                    halo_wait(bar_phi);
+                    u = *reinterpret_cast<const float4*>(hphi + i0);
+                    if (t == t_top) mbar_expect(bar_phi, 4u * nx);
+                }
                 up[0] = u.x; up[1] = u.y; up[2] = u.z; up[3] = u.w;
             }
             const float right = last_col ? pv[3] : (lane == 31 ? ph[idx + 4] : rn);
@@ -1117,8 +1158,11 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
             }
             *reinterpret_cast<float4*>(s1 + idx) = make_float4(n1[0], n1[1], n1[2], n1[3]);
             *reinterpret_cast<float4*>(s2 + idx) = make_float4(n2[0], n2[1], n2[2], n2[3]);
+            if (CL && row_top && has_up)
+                st_async4(dsmem_map(smem_u32(hm2 + i0), rank + 1), make_float4(n2[0], n2[1], n2[2], n2[3]),
+                          dsmem_map(bar_m2, rank + 1));
         }
-        if (CL) {
+        if (CL && check) {  // the test step also reads dm2 of the row below from the CTA below
             cluster_arrive();
             cluster_wait();
         } else {
@@ -1128,7 +1172,16 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
         const float ln = __shfl_up_sync(FULL, m1[3], 1);
         if (own) {
             const float l = left_of(ln, s1);
-            const float4 b = below4(s2, s2_dn);
+            float4 b;
+            if (jl > 0) {
+                b = *reinterpret_cast<const float4*>(s2 + idx - nx);
+            } else if (has_dn) {
+                halo_wait(bar_m2);
+                b = *reinterpret_cast<const float4*>(hm2 + i0);
+                if (t == 0) mbar_expect(bar_m2, 4u * nx);
+            } else {
+                b = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             const float bb[4] = {b.x, b.y, b.z, b.w};
             float pn[4];
 #pragma unroll
@@ -1156,13 +1209,12 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
 #pragma unroll
             for (int c = 0; c < 4; ++c) pv[c] = pn[c];
             *reinterpret_cast<float4*>(ph + idx) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+            if (CL && row_bot && has_dn)
+                st_async4(dsmem_map(smem_u32(hphi + i0), rank - 1), make_float4(pn[0], pn[1], pn[2], pn[3]),
+                          dsmem_map(bar_phi, rank - 1));
         }
-        if (CL) {
-            cluster_arrive();
-            cluster_wait();
-        } else {
-            __syncthreads();
-        }
+        par ^= 1u;
+        __syncthreads();
     };
     while (it < cap) {
         // plain steps up to the one that tests
@@ -1190,16 +1242,20 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
                     for (int c = 0; c < 3; ++c) tt[c] += slots[r * 3 + c];
                 const double Rk = (tt[0] / (double)mu + tt[1] / (double)tau - 2.0 * tt[2]) * P.h * P.h;
                 const int cv = Rk < P.tol;
-                const int lt = (globaltimer() - reinterpret_cast<const unsigned long long*>(slots)[50]) > P.budget_ns;
+                const int lt = (globaltimer() - reinterpret_cast<const unsigned long long*>(slots)[50]) > P.budget_ns ||
+                               slots[51] != 0.0;
                 const int stop = P.fixed || cv || lt || it >= cap;
                 slots[48] = Rk;
-                slots[49] = (double)(cv | (lt << 1) | (stop << 2));
+                slots[49] = (double)((cv && slots[51] == 0.0) | (lt << 1) | (stop << 2));
             }
             if (CL) cg::this_cluster().sync();
             else __syncthreads();
             if ((int)dsmem_ld_f64(slots0 + 8u * 49) & 4) break;
         }
     }
+    // the phi pushed by the CTA above after the last step has not been read:
+    // wait for it so that no copy into this CTA is in flight when it exits
+    if (CL && row_top && has_up) halo_wait(bar_phi);
     if (own) {
         *reinterpret_cast<float4*>(a.m1 + off + idx) = make_float4(m1[0], m1[1], m1[2], m1[3]);
         *reinterpret_cast<float4*>(a.m2 + off + idx) = make_float4(m2[0], m2[1], m2[2], m2[3]);
