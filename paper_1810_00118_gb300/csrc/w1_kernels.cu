@@ -725,6 +725,8 @@ static constexpr int RESW_MAX_NODES = RES_THREADS * 4 * RESW_RUNS;  // 16384
 // a CTA waiting for a neighbour's halo row gives up after this long and reports
 // a timeout (the neighbour is at most one step behind in a correct run)
 static constexpr unsigned long long RES_HALO_WAIT_NS = 200000000ull;
+// wide bands in a cluster keep two halo rows of nx floats beside the band
+static constexpr int RESW_MAX_HALO_X = 4096;
 
 int resident_max_nodes() { return RES_MAX_NODES; }
 
@@ -735,8 +737,9 @@ bool resident_fits(int nx, int ny, int cluster)
     const long long band = (long long)(ny / cluster) * nx;
     if (band <= RES_MAX_NODES) return true;
     // wide bands (four runs of four nodes per thread) need nx % 4 == 0 and a
-    // multiple of 128 nodes (so that a warp's runs are all present or all absent)
-    return nx % 4 == 0 && band <= RESW_MAX_NODES && band % 128 == 0;
+    // multiple of 128 nodes (so that a warp's runs are all present or all
+    // absent); in a cluster the halo rows limit nx to 4096
+    return nx % 4 == 0 && band <= RESW_MAX_NODES && band % 128 == 0 && (cluster == 1 || nx <= RESW_MAX_HALO_X);
 }
 
 int resident_cluster_for(int nx, int ny)
@@ -1298,7 +1301,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
 
 static size_t resident_wide_smem(int band)
 {
-    return RES_RED_BYTES + RES_SLOT_BYTES + (size_t)band * 3 * sizeof(float);
+    // + the two halo rows of a cluster band (at most RESW_MAX_HALO_X wide)
+    return RES_RED_BYTES + RES_SLOT_BYTES + (size_t)band * 3 * sizeof(float) + 2 * RESW_MAX_HALO_X * sizeof(float);
 }
 
 template <int NORM, bool CL>
@@ -1319,6 +1323,11 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
     float* ph = reinterpret_cast<float*>(smraw + RES_RED_BYTES + RES_SLOT_BYTES);
     float* s1 = ph + nb;
     float* s2 = s1 + nb;
+    // cluster halo rows and their mbarriers (the exchange of res4_level)
+    float* hphi = s2 + nb;
+    float* hm2 = hphi + nx;
+    const uint32_t bar_phi = smem_u32(slots + 56), bar_m2 = smem_u32(slots + 57);
+    const bool has_up = CL && rank + 1 < C, has_dn = CL && rank > 0;
     const size_t off = (size_t)pair * P.stride + (size_t)jb * nx;
     const float mu = P.mu, tau = P.tau;
     const float cm = P.mu * P.ih, ct = P.tau * P.ih;  // mu / h, tau / h
@@ -1346,26 +1355,51 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             *reinterpret_cast<float4*>(s2 + id) = x2;
         }
     }
+    if (CL && t == 0) {
+        mbar_init(bar_phi, 1);
+        mbar_init(bar_m2, 1);
+        if (has_up) mbar_expect(bar_phi, 4u * nx);
+        if (has_dn) mbar_expect(bar_m2, 4u * nx);
+        mbar_init_fence();
+    }
     group_sync();
     const int last_row = (rows - 1) * nx;
-    uint32_t ph_up = 0u, s2_dn = 0u, slots0 = smem_u32(slots);
+    const int t_top = (last_row >> 2) % T;  // owns the first run of the top row: re-arms bar_phi
+    uint32_t s2_dn = 0u, slots0 = smem_u32(slots);
     if (CL) {
-        if (rank + 1 < C) ph_up = dsmem_map(smem_u32(ph), rank + 1);
         if (rank > 0) s2_dn = dsmem_map(smem_u32(s2 + last_row), rank - 1);
         slots0 = dsmem_map(smem_u32(slots), 0);
     }
+    unsigned par = 0;        // parity of the halo phase the next step waits for
+    bool sync_fail = false;  // a halo wait ran out of time (reported as a timeout)
+    auto halo_wait = [&](uint32_t bar) {
+        if (!sync_fail && !mbar_wait(bar, par, RES_HALO_WAIT_NS)) {
+            sync_fail = true;
+            dsmem_st_f64(slots0 + 8u * 51, 1.0);
+        }
+    };
     // h div of the m currently in s1, s2 at run r (the left neighbour comes from the
     // previous lane by a shuffle: a warp's runs are all present or all absent,
-    // since the band holds a multiple of 128 nodes)
-    auto divergence = [&](int r, float out[4]) {
+    // since the band holds a multiple of 128 nodes); the row below the band is
+    // read from the CTA below (initial state) or from the halo row it pushed
+    auto divergence = [&](int r, float out[4], auto halo) {
         const int jl = pk[r] >> 16, i0 = pk[r] & 0xffff, id = jl * nx + i0;
         const float4 m1 = *reinterpret_cast<const float4*>(s1 + id);
         const float ln = __shfl_up_sync(FULL, m1.w, 1);
         const float4 m2 = *reinterpret_cast<const float4*>(s2 + id);
         const float l = i0 == 0 ? 0.f : (lane == 0 ? s1[id - 1] : ln);
         float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (jl > 0) b = *reinterpret_cast<const float4*>(s2 + id - nx);
-        else if (CL && rank > 0) b = dsmem_ld4(s2_dn + 4u * i0);
+        if (jl > 0) {
+            b = *reinterpret_cast<const float4*>(s2 + id - nx);
+        } else if (has_dn) {
+            if constexpr (decltype(halo)::value) {
+                halo_wait(bar_m2);
+                b = *reinterpret_cast<const float4*>(hm2 + i0);
+                if (t == 0 && r == 0) mbar_expect(bar_m2, 4u * nx);
+            } else {
+                b = dsmem_ld4(s2_dn + 4u * i0);
+            }
+        }
         out[0] = (m1.x - l) + (m2.x - b.x);
         out[1] = (m1.y - m1.x) + (m2.y - b.y);
         out[2] = (m1.z - m1.y) + (m2.z - b.z);
@@ -1373,16 +1407,25 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
     };
 #pragma unroll
     for (int r = 0; r < RESW_RUNS; ++r)
-        if (pk[r] >= 0) divergence(r, Dv[r]);
-    group_sync();
-
+        if (pk[r] >= 0) divergence(r, Dv[r], std::false_type{});
     // the start time, R^k and the decision live in CTA 0's slots (registers are scarce)
     if (rank == 0 && t == 0) {
         reinterpret_cast<unsigned long long*>(slots)[50] = globaltimer();
         slots[48] = 0.0;
         slots[49] = 0.0;
+        slots[51] = 0.0;
     }
     group_sync();
+    // the initial phi of the bottom row goes to the CTA below
+    if (has_dn) {
+#pragma unroll
+        for (int r = 0; r < RESW_RUNS; ++r)
+            if (pk[r] >= 0 && (pk[r] >> 16) == 0) {
+                const int i0 = pk[r] & 0xffff;
+                st_async4(dsmem_map(smem_u32(hphi + i0), rank - 1), *reinterpret_cast<const float4*>(ph + i0),
+                          dsmem_map(bar_phi, rank - 1));
+            }
+    }
     // (a 32-bit step counter with a running "next test" step made this loop
     // several times slower here, measured; the 64-bit modulo costs little per node)
     long long it = 0;
@@ -1403,8 +1446,15 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             const float4 a1 = *reinterpret_cast<const float4*>(s1 + id);
             const float4 a2 = *reinterpret_cast<const float4*>(s2 + id);
             float4 u = p4;
-            if (j < ny - 1)
-                u = (!CL || jl < rows - 1) ? *reinterpret_cast<const float4*>(ph + id + nx) : dsmem_ld4(ph_up + 4u * i0);
+            if (j < ny - 1) {
+                if (!CL || jl < rows - 1) {
+                    u = *reinterpret_cast<const float4*>(ph + id + nx);
+                } else {
+                    halo_wait(bar_phi);
+                    u = *reinterpret_cast<const float4*>(hphi + i0);
+                    if (t == t_top && id == last_row) mbar_expect(bar_phi, 4u * nx);
+                }
+            }
             const float right = last_col ? p4.w : (lane == 31 ? ph[id + 4] : rn);
             const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, up[4] = {u.x, u.y, u.z, u.w};
             const float m1[4] = {a1.x, a1.y, a1.z, a1.w}, m2[4] = {a2.x, a2.y, a2.z, a2.w};
@@ -1420,19 +1470,17 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             }
             *reinterpret_cast<float4*>(s1 + id) = make_float4(n1[0], n1[1], n1[2], n1[3]);
             *reinterpret_cast<float4*>(s2 + id) = make_float4(n2[0], n2[1], n2[2], n2[3]);
+            if (has_up && jl == rows - 1)
+                st_async4(dsmem_map(smem_u32(hm2 + i0), rank + 1), make_float4(n2[0], n2[1], n2[2], n2[3]),
+                          dsmem_map(bar_m2, rank + 1));
         }
-        if (CL) {
-            cluster_arrive();
-            cluster_wait();
-        } else {
-            __syncthreads();
-        }
+        __syncthreads();
         // ---- phase B: phi' = phi + tau (div(2m' - m) - rho)
 #pragma unroll
         for (int r = 0; r < RESW_RUNS; ++r) {
             if (pk[r] < 0) continue;
             float Dn[4];
-            divergence(r, Dn);
+            divergence(r, Dn, std::true_type{});
             const int id = (pk[r] >> 16) * nx + (pk[r] & 0xffff);
             const float4 p4 = *reinterpret_cast<const float4*>(ph + id);
             const float4 r4 = __ldg(reinterpret_cast<const float4*>(rho + id));
@@ -1449,13 +1497,12 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
                 Dv[r][c] = Dn[c];
             }
             *reinterpret_cast<float4*>(ph + id) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+            if (has_dn && id < nx)
+                st_async4(dsmem_map(smem_u32(hphi + id), rank - 1), make_float4(pn[0], pn[1], pn[2], pn[3]),
+                          dsmem_map(bar_phi, rank - 1));
         }
-        if (CL) {
-            cluster_arrive();
-            cluster_wait();
-        } else {
-            __syncthreads();
-        }
+        par ^= 1u;
+        __syncthreads();
         ++it;
         if (check) {
             double v[3] = {(double)sa, (double)sb, (double)sc / P.h};
@@ -1472,14 +1519,23 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
                     for (int c = 0; c < 3; ++c) tt[c] += slots[q * 3 + c];
                 const double Rk = (tt[0] / (double)mu + tt[1] / (double)tau - 2.0 * tt[2]) * P.h * P.h;
                 const int cv = Rk < P.tol;
-                const int lt = (globaltimer() - reinterpret_cast<const unsigned long long*>(slots)[50]) > P.budget_ns;
+                const int lt = (globaltimer() - reinterpret_cast<const unsigned long long*>(slots)[50]) > P.budget_ns ||
+                               slots[51] != 0.0;
                 const int stop = P.fixed || cv || lt || it >= cap;
                 slots[48] = Rk;
-                slots[49] = (double)(cv | (lt << 1) | (stop << 2));
+                slots[49] = (double)((cv && slots[51] == 0.0) | (lt << 1) | (stop << 2));
             }
             group_sync();
             if ((int)dsmem_ld_f64(slots0 + 8u * 49) & 4) break;
         }
+    }
+    // wait for the phi pushed by the CTA above after the last step (no copy
+    // into this CTA may be in flight when it exits)
+    if (has_up) {
+        bool top_run = false;
+#pragma unroll
+        for (int r = 0; r < RESW_RUNS; ++r) top_run |= pk[r] >= 0 && (pk[r] >> 16) == rows - 1;
+        if (top_run) halo_wait(bar_phi);
     }
 #pragma unroll
     for (int r = 0; r < RESW_RUNS; ++r) {

@@ -46,10 +46,12 @@ def rand_state(rng, ny, nx, scale=0.5):
 
 def resident_fits(nx, ny):
     """A cluster of 1..16 CTAs, each holding whole rows, at most 4096 nodes per
-    CTA (16384 when nx is a multiple of 4 and the band a multiple of 128 nodes)."""
+    CTA (16384 when nx is a multiple of 4 and the band a multiple of 128 nodes,
+    and nx <= 4096 in a cluster of several CTAs)."""
     def fits(c):
         band = (ny // c) * nx
-        return ny % c == 0 and (band <= 4096 or (nx % 4 == 0 and band <= 16384 and band % 128 == 0))
+        return ny % c == 0 and (band <= 4096 or (nx % 4 == 0 and band <= 16384 and band % 128 == 0
+                                                 and (c == 1 or nx <= 4096)))
     return any(fits(c) for c in (1, 2, 4, 8, 16))
 
 
@@ -101,10 +103,13 @@ def test_cp_steps_match_oracle(w1, norm, shape, path):
 @pytest.mark.parametrize("norm", [L1, L2, LINF])
 @pytest.mark.parametrize("shape,cluster", [((64, 64), 1), ((64, 64), 16), ((128, 128), 1), ((128, 128), 2),
                                            ((128, 128), 4), ((128, 128), 8), ((256, 256), 4), ((512, 512), 16),
-                                           ((96, 160), 1)])
+                                           ((96, 160), 1), ((16, 1024), 16), ((32, 4096), 16), ((64, 1024), 4),
+                                           ((256, 512), 8)])
 def test_resident_cluster_sizes_match_oracle(w1, norm, shape, cluster):
     """Every on-chip layout: one CTA or a cluster, four nodes per thread (up to
-    4096 per CTA) or wide bands (up to 16384 per CTA, single CTA included)."""
+    4096 per CTA) or wide bands (up to 16384 per CTA, single CTA included),
+    bands of one row (the halo rows above and below meet in one row), wide
+    bands of two rows."""
     ny, nx = shape
     rng = np.random.default_rng(ny + nx + cluster + 10 * norm)
     rho, m1, m2, phi = rand_state(rng, ny, nx)
