@@ -498,7 +498,7 @@ def run_gpu(args):
 # the captures summarised under profiles/; None where no capture of the current
 # kernel exists.  Streaming kernels: captured at 4096^2 and scaled by 4 to 8192^2
 # (their traffic grows with the number of nodes).
-TRAFFIC = {"k_step": 4 * 444.46e6, "k_tblock": 4 * 432.7e6, "k_resident4": 1.0816e6}
+TRAFFIC = {"k_step": 4 * 444.46e6, "k_tblock": 4 * 432.7e6, "k_resident4": 1.157888e6}
 
 FP32_LANES_PER_SM = 128  # FP32 units per SM; two flops per FMA
 SM_MAX_MHZ = 2070.0
