@@ -1430,9 +1430,10 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
     // several times slower here, measured; the 64-bit modulo costs little per node)
     long long it = 0;
     const long long cap = P.cap;
-    while (it < cap) {
-        const bool check = P.fixed ? (it + 1 == cap) : ((it + 1) % P.K == 0);
-        float sa = 0.f, sb = 0.f, sc = 0.f;  // FP32 terms and per-thread partials, FP64 across threads
+    float sa = 0.f, sb = 0.f, sc = 0.f;  // FP32 terms and per-thread partials, FP64 across threads
+    // one step; the test-step sums are compiled only into the step that tests
+    auto wstep = [&](auto test) {
+        constexpr bool check = decltype(test)::value;
         // ---- phase A: m' = prox(m + mu grad phi); on the last column and the top
         // row the gradient component is zero and so is m, hence m' too
 #pragma unroll
@@ -1503,8 +1504,18 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
         }
         par ^= 1u;
         __syncthreads();
+    };
+    while (it < cap) {
+        const bool check = P.fixed ? (it + 1 == cap) : ((it + 1) % P.K == 0);
+        if (!check) {
+            wstep(std::false_type{});
+            ++it;
+            continue;
+        }
+        sa = sb = sc = 0.f;
+        wstep(std::true_type{});
         ++it;
-        if (check) {
+        {
             double v[3] = {(double)sa, (double)sb, (double)sc / P.h};
             block_sum<3>(v, red);
             if (t == 0) {
