@@ -267,6 +267,7 @@ def gen_pairs(specs, world=1):
 def run_gpu(args):
     rank, world, local = dist_env()
     B = args.batch
+    DEPTH = 2 if (args.mode == "lanes" and args.pipeline) else 1
     total_steps = args.warmup + args.steps
     # distinct pairs per step and rank, generated before CUDA starts
     gen = gen_pairs([(WORKLOAD, k, N) for s in range(total_steps) for k in pair_ids(rank, s, B)], world)
@@ -306,51 +307,97 @@ def run_gpu(args):
         if G < 1 or B % G:
             raise SystemExit("--lane-batch must divide --batch")
         nlane = B // G
-        plans = {norm: [w1.Plan(N, N, levels=LEVELS, norm=norm, eager=int(args.eager), algorithm=args.algorithm,
-                                check_every=args.check_every, tune=args.tune, batch=G)
-                        for _ in range(nlane)]
+        # pipelined steps: step s + 1 is enqueued before step s is collected, so
+        # lanes that finish early start on the next step's pairs; two sets of
+        # plans (and of result events) alternate between consecutive steps
+        plans = {norm: [[w1.Plan(N, N, levels=LEVELS, norm=norm, eager=int(args.eager), algorithm=args.algorithm,
+                                 check_every=args.check_every, tune=args.tune, batch=G)
+                         for _ in range(nlane)] for _ in range(DEPTH)]
                  for norm in NORMS}
         lanes = {norm: [torch.cuda.Stream() for _ in range(nlane)] for norm in NORMS}
-        done_ev = {norm: [torch.cuda.Event(enable_timing=True) for _ in range(nlane)] for norm in NORMS}
+        done_ev = {norm: [[torch.cuda.Event(enable_timing=True) for _ in range(nlane)] for _ in range(DEPTH)]
+                   for norm in NORMS}
     pair_ms = []
-    in_dev = [torch.empty((B, N, N), device="cuda") for _ in range(2)]
+    in_dev = [[torch.empty((B, N, N), device="cuda") for _ in range(2)] for _ in range(DEPTH)]
+    ready_ev = [torch.cuda.Event(enable_timing=True) for _ in range(DEPTH)]
+    pending = {}
 
-    def do_step(s, host=False):
+    def submit(s, host=False):
+        q = s % DEPTH
         flush.fill_(float(s))
-        out = []
         if host:
             # end to end: copy this step's inputs from pinned host memory first
-            in_dev[0].copy_(host_pairs[s][0], non_blocking=True)
-            in_dev[1].copy_(host_pairs[s][1], non_blocking=True)
-            t0, t1 = in_dev
+            in_dev[q][0].copy_(host_pairs[s][0], non_blocking=True)
+            in_dev[q][1].copy_(host_pairs[s][1], non_blocking=True)
+            t0, t1 = in_dev[q]
         else:
             t0, t1 = dev_pairs[s]
         if args.mode == "lockstep":
+            out = []
             for norm in NORMS:
                 v, st, _, _ = plans[norm].solve_batch(t0, t1, stream=stream, allow=ok)
                 out.append((v, st))
-            return out
-        ready = torch.cuda.Event(enable_timing=True)
-        ready.record(stream)
+            pending[s] = out
+            return
+        ready_ev[q].record(stream)
         for norm in NORMS:
             for b in range(nlane):
-                lanes[norm][b].wait_event(ready)
+                lanes[norm][b].wait_event(ready_ev[q])
                 if G == 1:
-                    plans[norm][b].solve_async(t0[b], t1[b], stream=lanes[norm][b])
+                    plans[norm][q][b].solve_async(t0[b], t1[b], stream=lanes[norm][b])
                 else:
-                    plans[norm][b].solve_async(t0[b * G:(b + 1) * G], t1[b * G:(b + 1) * G], stream=lanes[norm][b])
-                done_ev[norm][b].record(lanes[norm][b])
-                stream.wait_event(done_ev[norm][b])  # the launching stream joins every lane
+                    plans[norm][q][b].solve_async(t0[b * G:(b + 1) * G], t1[b * G:(b + 1) * G],
+                                                  stream=lanes[norm][b])
+                done_ev[norm][q][b].record(lanes[norm][b])
+
+    def collect(s):
+        if args.mode == "lockstep":
+            return pending.pop(s)
+        q = s % DEPTH
+        out = []
         for norm in NORMS:
             vals, sts = [], []
             for b in range(nlane):
-                lanes[norm][b].synchronize()
-                v, st, _, _ = plans[norm][b].results(allow=ok)
+                done_ev[norm][q][b].synchronize()
+                v, st, _, _ = plans[norm][q][b].results(allow=ok)
                 vals.extend(v)
                 sts.extend(st)
-                pair_ms.extend([ready.elapsed_time(done_ev[norm][b])] * G)
+                pair_ms.extend([ready_ev[q].elapsed_time(done_ev[norm][q][b])] * G)
             out.append((vals, sts))
         return out
+
+    def join_lanes(s):
+        # the launching stream waits for every lane (their earlier work is ordered before)
+        if args.mode != "lockstep":
+            for norm in NORMS:
+                for b in range(nlane):
+                    stream.wait_event(done_ev[norm][s % DEPTH][b])
+
+    def run_steps(first, last, host=False, out=None, step_ms=None):
+        """Steps first .. last - 1, step s + 1 submitted before step s is collected."""
+        t_sub = {}
+        for s in range(first, last):
+            t_sub[s] = time.perf_counter()
+            submit(s, host)
+            if s - first >= DEPTH - 1 and DEPTH > 1 and s > first:
+                r = collect(s - 1)
+                if out is not None:
+                    out.append(r)
+                if step_ms is not None:
+                    step_ms.append((time.perf_counter() - t_sub[s - 1]) * 1e3)
+            elif DEPTH == 1:
+                r = collect(s)
+                if out is not None:
+                    out.append(r)
+                if step_ms is not None:
+                    step_ms.append((time.perf_counter() - t_sub[s]) * 1e3)
+        if DEPTH > 1 and last > first:
+            r = collect(last - 1)
+            if out is not None:
+                out.append(r)
+            if step_ms is not None:
+                step_ms.append((time.perf_counter() - t_sub[last - 1]) * 1e3)
+        join_lanes(last - 1)
 
     def level_launches(p, k):
         # resident: one launch; streaming: one per step (path 2) or per 4 steps
@@ -379,8 +426,7 @@ def run_gpu(args):
     def max_over_ranks(x):
         return reduce_max(dist, x, "cuda")
 
-    for s in range(args.warmup):
-        do_step(s)
+    run_steps(0, args.warmup)
     barrier()
     pair_ms.clear()
     results = []
@@ -390,10 +436,7 @@ def run_gpu(args):
         barrier()
         t0 = time.perf_counter()
         ev0.record(stream)
-        for s in range(args.warmup, total_steps):
-            ts = time.perf_counter()
-            results.append(do_step(s))
-            step_ms.append((time.perf_counter() - ts) * 1e3)
+        run_steps(args.warmup, total_steps, out=results, step_ms=step_ms)
         ev1.record(stream)
         barrier()
         wall = time.perf_counter() - t0
@@ -410,8 +453,7 @@ def run_gpu(args):
     if not args.no_e2e:
         barrier()
         ev0.record(stream)
-        for s in range(args.warmup, total_steps):
-            do_step(s, host=True)
+        run_steps(args.warmup, total_steps, host=True)
         ev1.record(stream)
         barrier()
         e2e_el = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
@@ -456,14 +498,18 @@ def run_gpu(args):
                        "stop": "eq. stop_tol for the algorithm",
                        "batch_per_norm": B, "mode": args.mode,
                        "pairs_per_lane": args.lane_batch if args.mode == "lanes" else B,
-                       "l2": "flushed before every step (256 MiB write, inside the timed region)",
+                       "l2": "flushed before every step (256 MiB write, inside the timed region); each step's "
+                             "inputs (2 x B x 1 MiB) are larger than L2 as well",
+                       "pipelined_steps": DEPTH if args.mode == "lanes" else 1,
                        "parallelism": f"replicas x{world}"},
             "timer": {"kind": "CUDA events on the launching stream, every lane joined to it", "wall_s": wall},
             "batch_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                                 "what": "one step (B pairs, both norms) / 2, submit to W1 values on the host"},
+                                 "what": "one step (B pairs, both norms) / 2, submit to W1 values on the host "
+                                         "(with pipelined steps the next step is already running meanwhile)"},
             "solo_latency_ms": solo,
             "pair_latency_ms": ({"p50": float(np.percentile(pair_lat, 50)), "p99": float(np.percentile(pair_lat, 99)),
-                                 "what": "per pair: step start to the end of its solve on its stream (CUDA events)"}
+                                 "what": "per pair: its step's submission to the end of its solve on its "
+                                         "stream (CUDA events)"}
                                 if pair_lat else None),
             "iters_first_pair": iters,
             "w1_first_step": [[float(x) for x in v] for v, _ in results[0]],
@@ -488,7 +534,8 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     for p in plans.values():
         for q in (p if isinstance(p, list) else [p]):
-            q.close()
+            for r in (q if isinstance(q, list) else [q]):
+                r.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
@@ -581,6 +628,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--batch", type=int, default=128, help="pairs per norm per step")
     ap.add_argument("--lane-batch", type=int, default=1, help="lanes: pairs per lane (a batched plan per lane)")
+    ap.add_argument("--pipeline", type=int, default=1, choices=[0, 1],
+                    help="lanes: submit step s + 1 before collecting step s (1) or drain every step (0)")
     ap.add_argument("--mode", default="lanes", choices=["lanes", "lockstep"],
                     help="lanes: one async plan+stream per pair; lockstep: one batched plan per norm")
     ap.add_argument("--steps", type=int, default=5)
