@@ -425,8 +425,13 @@ const char* w1_noalloc_last_error(void);
  * lowered until every side divides by 2^(L-1) and the coarsest side is >= 2);
  * tol <= 0 gives eq. stop_tol's formula 1e-6/128 (512 h)^2 (the paper states it
  * for 2-D grids; taken unchanged for 3-D); options as for the 2-D solver
- * (check_every 0 = 32; path, tune, eager and algorithm do not apply: every level
- * runs the two-launch step and the host tests R^k).  Writes *dist = f(m) of the
+ * (check_every 0 = 32; path 0 runs a level on chip (all its steps and stop
+ * tests in one launch of one CTA or a cluster of up to 16, each holding at most
+ * 4096 voxels, nx % 4 == 0) where it fits and otherwise with two launches per
+ * step and the host testing R^k every K steps; path 1 requires the on-chip
+ * kernel (W1_ERR_UNSUPPORTED where a level does not fit); paths 2 and 3 use the
+ * two-launch step on every level; time_budget_s applies per level; tune,
+ * eager and algorithm do not apply).  Writes *dist = f(m) of the
  * finest flux; flux (3n floats: m1, m2, m3 planes) and potential (n floats), when
  * not NULL, receive the finest state; stats: per-level iterations, R^k and eps_l
  * (nx[], ny[] hold the level sizes; the level's nz is nz >> (levels-1-l)),
@@ -439,10 +444,17 @@ w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, int norm, dou
 
 /* `iters` steps of eq. primaldual on one 3-D level, in place on m1, m2, m3, phi
  * (zero-mean rho); mu, tau as given.  *fpr_last (may be NULL) = R^k of the last
- * step (0 when iters == 0). */
+ * step (0 when iters == 0).  Runs the two-launch step (path 2). */
 w1_status w1_cp_steps3d(int nx, int ny, int nz, double h, int norm, float mu, float tau, const float* rho,
                         float* m1, float* m2, float* m3, float* phi, long long iters, void* stream,
                         double* fpr_last);
+/* The same with a choice of kernel: path 2 = two launches per step; path 1 =
+ * every step in one launch on chip (nx % 4 == 0, a cluster of `cluster` CTAs
+ * (0: the fewest that fit) each holding nz / cluster planes of at most 4096
+ * voxels; W1_ERR_UNSUPPORTED when the level does not fit). */
+w1_status w1_cp_steps3d_ex(int nx, int ny, int nz, double h, int norm, float mu, float tau, const float* rho,
+                           float* m1, float* m2, float* m3, float* phi, long long iters, int path, int cluster,
+                           void* stream, double* fpr_last);
 
 /* Restriction of Algorithm 3 in 3-D: coarse node = mean of its 2x2x2 block;
  * fine is nx x ny x nz (all even), coarse (nx/2)(ny/2)(nz/2).  Asynchronous. */

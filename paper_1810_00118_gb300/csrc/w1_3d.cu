@@ -16,15 +16,21 @@
 // on-chip levels): 3-D grids are outside the measured workloads.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "w1_device.cuh"
 #include "w1_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace w1 {
 
@@ -340,6 +346,380 @@ __global__ void __launch_bounds__(1024) k3_final_b(Dims3 d, double h, const doub
     }
 }
 
+// ---------------------------------------------------------------------------
+// On-chip level solve: every step of a level inside one launch
+// ---------------------------------------------------------------------------
+//
+// A CTA (or a cluster of C CTAs, each holding a slab of nz / C planes) keeps
+// its voxels' phi, m1, m2, m3 in shared memory for the neighbours to read; a
+// thread owns four consecutive voxels of a row and keeps their m, phi, rho and
+// D = h div m^k in registers.  One step is the 2-D on-chip step with a third
+// axis: phase A forms m' from phi at x+1 (the next lane), y+1 (the row above)
+// and z+1 (the plane above, or the halo plane pushed by the CTA above); phase B
+// forms div m' from m1' at x-1, m2' at y-1 and m3' at z-1 (the plane below, or
+// the halo plane pushed by the CTA below) and the dual step.  Halo planes move
+// by st.async into the neighbour's shared memory, completing a transaction
+// count on its mbarrier (the 2-D kernels' exchange with planes for rows).  The
+// test step's cross term uses div dm = (D' - D) / h, already in registers.
+
+static constexpr int R3_THREADS = 1024;
+static constexpr int R3_MAX_NODES = 4 * R3_THREADS;  // voxels per CTA
+static constexpr int R3_RED_BYTES = 1024;
+static constexpr int R3_SLOT_BYTES = 512;
+static constexpr unsigned long long R3_HALO_WAIT_NS = 200000000ull;
+
+struct Res3 {
+    long long iters;
+    double fpr;
+    int conv;
+    int timeout;
+};
+
+struct R3Args {
+    Dims3 d;
+    float mu, tau, cm, ct;  // cm = mu / h, ct = tau / h
+    double h, tol;
+    int K, fixed;
+    long long cap;
+    unsigned long long budget_ns;
+    const float* rho;
+    float *m1, *m2, *m3, *phi;
+    Res3* res;
+};
+
+static size_t r3_smem(int nb, int plane)
+{
+    return R3_RED_BYTES + R3_SLOT_BYTES + (size_t)nb * 4 * sizeof(float) + (size_t)2 * plane * sizeof(float);
+}
+
+static int r3_cluster_for(int nx, int ny, int nz)
+{
+    if (nx % 4 != 0) return 0;
+    for (int c = 1; c <= 16; c *= 2)
+        if (nz % c == 0 && (long long)(nz / c) * nx * ny <= R3_MAX_NODES) return c;
+    return 0;
+}
+
+template <int NORM, bool CL>
+__global__ void __launch_bounds__(R3_THREADS, 1) k3_resident(R3Args a)
+{
+    int C = 1, rank = 0;
+    if (CL) {
+        cg::cluster_group cl = cg::this_cluster();
+        C = (int)cl.num_blocks();
+        rank = (int)cl.block_rank();
+    }
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nx = a.d.nx, ny = a.d.ny, nz = a.d.nz;
+    const int plane = nx * ny, P = nz / C, kb = rank * P, nb = P * plane;
+    double* red = reinterpret_cast<double*>(smraw);
+    double* slots = reinterpret_cast<double*>(smraw + R3_RED_BYTES);
+    float* ph = reinterpret_cast<float*>(smraw + R3_RED_BYTES + R3_SLOT_BYTES);
+    float* s1 = ph + nb;
+    float* s2 = s1 + nb;
+    float* s3 = s2 + nb;
+    float* hphi = s3 + nb;     // phi of the plane above the slab (from CTA rank + 1)
+    float* hm3 = hphi + plane;  // m3' of the plane below the slab (from CTA rank - 1)
+    const uint32_t bar_phi = smem_u32(slots + 56), bar_m3 = smem_u32(slots + 57);
+    const size_t off = (size_t)kb * plane;
+    const float mu = a.mu, tau = a.tau, cm = a.cm, ct = a.ct;
+
+    const int t = threadIdx.x, lane = t & 31, W = nx >> 2;
+    const bool own = 4 * t < nb;
+    const int id = own ? 4 * t : 0;
+    const int kl = own ? id / plane : 0;
+    const int rem = id - kl * plane;  // index within the plane
+    const int jl = rem / nx, i0 = rem - jl * nx;
+    const bool last_col = own && i0 + 4 == nx, top_row = jl == ny - 1, top_plane = kb + kl == nz - 1;
+    const bool slab_top = own && kl == P - 1, slab_bot = own && kl == 0;
+    const bool has_up = CL && rank + 1 < C, has_dn = CL && rank > 0;
+    (void)W;
+    float m1[4] = {0.f, 0.f, 0.f, 0.f}, m2[4] = {0.f, 0.f, 0.f, 0.f}, m3[4] = {0.f, 0.f, 0.f, 0.f};
+    float pv[4] = {0.f, 0.f, 0.f, 0.f}, rv[4] = {0.f, 0.f, 0.f, 0.f}, Dv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (own) {
+        float4 x1 = *reinterpret_cast<const float4*>(a.m1 + off + id);
+        float4 x2 = *reinterpret_cast<const float4*>(a.m2 + off + id);
+        float4 x3 = *reinterpret_cast<const float4*>(a.m3 + off + id);
+        const float4 xp = *reinterpret_cast<const float4*>(a.phi + off + id);
+        const float4 xr = *reinterpret_cast<const float4*>(a.rho + off + id);
+        // the pinned entries (zero flux through the last face on each axis) are zero
+        if (last_col) x1.w = 0.f;
+        if (top_row) x2 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (top_plane) x3 = make_float4(0.f, 0.f, 0.f, 0.f);
+        m1[0] = x1.x; m1[1] = x1.y; m1[2] = x1.z; m1[3] = x1.w;
+        m2[0] = x2.x; m2[1] = x2.y; m2[2] = x2.z; m2[3] = x2.w;
+        m3[0] = x3.x; m3[1] = x3.y; m3[2] = x3.z; m3[3] = x3.w;
+        pv[0] = xp.x; pv[1] = xp.y; pv[2] = xp.z; pv[3] = xp.w;
+        rv[0] = xr.x; rv[1] = xr.y; rv[2] = xr.z; rv[3] = xr.w;
+        *reinterpret_cast<float4*>(ph + id) = xp;
+        *reinterpret_cast<float4*>(s1 + id) = x1;
+        *reinterpret_cast<float4*>(s2 + id) = x2;
+        *reinterpret_cast<float4*>(s3 + id) = x3;
+    }
+    if (CL && t == 0) {
+        mbar_init(bar_phi, 1);
+        mbar_init(bar_m3, 1);
+        if (has_up) mbar_expect(bar_phi, 4u * plane);
+        if (has_dn) mbar_expect(bar_m3, 4u * plane);
+        mbar_init_fence();
+    }
+    if (CL) cg::this_cluster().sync();
+    else __syncthreads();
+    uint32_t slots0 = smem_u32(slots);
+    if (CL) slots0 = dsmem_map(smem_u32(slots), 0);
+    // m3 of the plane below the voxel run (initial state: read from the CTA below)
+    float4 b3 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (own) {
+        if (kl > 0) b3 = *reinterpret_cast<const float4*>(s3 + id - plane);
+        else if (has_dn) b3 = dsmem_ld4(dsmem_map(smem_u32(s3 + (P - 1) * plane + rem), rank - 1));
+    }
+    {  // D^0 = h div m^0
+        const float ln = __shfl_up_sync(FULL, m1[3], 1);
+        if (own) {
+            const float l = i0 == 0 ? 0.f : (lane == 0 ? s1[id - 1] : ln);
+            const float4 b2 = jl > 0 ? *reinterpret_cast<const float4*>(s2 + id - nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float bb2[4] = {b2.x, b2.y, b2.z, b2.w}, bb3[4] = {b3.x, b3.y, b3.z, b3.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) Dv[c] = (m1[c] - (c ? m1[c - 1] : l)) + (m2[c] - bb2[c]) + (m3[c] - bb3[c]);
+        }
+    }
+    if (rank == 0 && t == 0) {
+        reinterpret_cast<unsigned long long*>(slots)[50] = globaltimer();
+        slots[48] = 0.0;
+        slots[49] = 0.0;
+        slots[51] = 0.0;
+    }
+    if (CL) cg::this_cluster().sync();
+    else __syncthreads();
+    // the initial phi of the bottom plane goes to the CTA below
+    if (slab_bot && has_dn)
+        st_async4(dsmem_map(smem_u32(hphi + rem), rank - 1), make_float4(pv[0], pv[1], pv[2], pv[3]),
+                  dsmem_map(bar_phi, rank - 1));
+    unsigned par = 0;
+    bool sync_fail = false;
+    auto halo_wait = [&](uint32_t bar) {
+        if (!sync_fail && !mbar_wait(bar, par, R3_HALO_WAIT_NS)) {
+            sync_fail = true;
+            dsmem_st_f64(slots0 + 8u * 51, 1.0);
+        }
+    };
+    const int t_top = ((P - 1) * plane) >> 2;  // first thread of the top plane: re-arms bar_phi
+    int it = 0;
+    const int cap = (int)min(a.cap, (long long)INT_MAX);
+    int next = a.fixed ? cap : a.K;
+    float sa = 0.f, sb = 0.f, sc = 0.f;
+    auto one_step = [&](auto test) {
+        constexpr bool check = decltype(test)::value;
+        // ---- phase A: m' = prox(m + mu grad phi)
+        const float rn = __shfl_down_sync(FULL, pv[0], 1);
+        if (own) {
+            float4 uy = make_float4(pv[0], pv[1], pv[2], pv[3]), uz = uy;
+            if (!top_row) uy = *reinterpret_cast<const float4*>(ph + id + nx);
+            if (!top_plane) {
+                if (!CL || kl < P - 1) {
+                    uz = *reinterpret_cast<const float4*>(ph + id + plane);
+                } else {
+                    halo_wait(bar_phi);
+                    uz = *reinterpret_cast<const float4*>(hphi + rem);
+                    if (t == t_top) mbar_expect(bar_phi, 4u * plane);
+                }
+            }
+            const float right = last_col ? pv[3] : (lane == 31 ? ph[id + 4] : rn);
+            const float py[4] = {uy.x, uy.y, uy.z, uy.w}, pz[4] = {uz.x, uz.y, uz.z, uz.w};
+            float n1[4], n2[4], n3[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float pr = c < 3 ? pv[c + 1] : right;
+                const float v[3] = {fmaf(cm, pr - pv[c], m1[c]), fmaf(cm, py[c] - pv[c], m2[c]),
+                                    fmaf(cm, pz[c] - pv[c], m3[c])};
+                float o[3];
+                prox3<NORM>(v, mu, o);
+                n1[c] = o[0];
+                n2[c] = o[1];
+                n3[c] = o[2];
+            }
+            if (last_col) n1[3] = 0.f;
+            if (top_row) n2[0] = n2[1] = n2[2] = n2[3] = 0.f;
+            if (top_plane) n3[0] = n3[1] = n3[2] = n3[3] = 0.f;
+            if constexpr (check) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float d1 = n1[c] - m1[c], d2 = n2[c] - m2[c], d3 = n3[c] - m3[c];
+                    sa = fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, sa)));
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                m1[c] = n1[c];
+                m2[c] = n2[c];
+                m3[c] = n3[c];
+            }
+            *reinterpret_cast<float4*>(s1 + id) = make_float4(n1[0], n1[1], n1[2], n1[3]);
+            *reinterpret_cast<float4*>(s2 + id) = make_float4(n2[0], n2[1], n2[2], n2[3]);
+            *reinterpret_cast<float4*>(s3 + id) = make_float4(n3[0], n3[1], n3[2], n3[3]);
+            if (CL && slab_top && has_up)
+                st_async4(dsmem_map(smem_u32(hm3 + rem), rank + 1), make_float4(n3[0], n3[1], n3[2], n3[3]),
+                          dsmem_map(bar_m3, rank + 1));
+        }
+        __syncthreads();
+        // ---- phase B: phi' = phi + tau (div(2m' - m) - rho)
+        const float ln = __shfl_up_sync(FULL, m1[3], 1);
+        if (own) {
+            const float l = i0 == 0 ? 0.f : (lane == 0 ? s1[id - 1] : ln);
+            const float4 b2 = jl > 0 ? *reinterpret_cast<const float4*>(s2 + id - nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 bz = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (kl > 0) {
+                bz = *reinterpret_cast<const float4*>(s3 + id - plane);
+            } else if (has_dn) {
+                halo_wait(bar_m3);
+                bz = *reinterpret_cast<const float4*>(hm3 + rem);
+                if (t == 0) mbar_expect(bar_m3, 4u * plane);
+            }
+            const float bb2[4] = {b2.x, b2.y, b2.z, b2.w}, bb3[4] = {bz.x, bz.y, bz.z, bz.w};
+            float pn[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float Dn = (m1[c] - (c ? m1[c - 1] : l)) + (m2[c] - bb2[c]) + (m3[c] - bb3[c]);
+                pn[c] = fmaf(ct, fmaf(2.f, Dn, -Dv[c]), fmaf(-tau, rv[c], pv[c]));
+                if constexpr (check) {
+                    const float ep = pn[c] - pv[c];
+                    sb = fmaf(ep, ep, sb);
+                    sc = fmaf(ep, Dn - Dv[c], sc);  // h <dphi, div dm>, scaled below
+                }
+                Dv[c] = Dn;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) pv[c] = pn[c];
+            *reinterpret_cast<float4*>(ph + id) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+            if (CL && slab_bot && has_dn)
+                st_async4(dsmem_map(smem_u32(hphi + rem), rank - 1), make_float4(pn[0], pn[1], pn[2], pn[3]),
+                          dsmem_map(bar_phi, rank - 1));
+        }
+        par ^= 1u;
+        __syncthreads();
+    };
+    while (it < cap) {
+        const int plain = (next - 1 < cap ? next - 1 : cap) - it;
+        for (int r = 0; r < plain; ++r) one_step(std::false_type{});
+        it += plain;
+        if (it >= cap) break;
+        sa = sb = sc = 0.f;
+        one_step(std::true_type{});
+        ++it;
+        next += a.K;
+        double v[3] = {(double)sa, (double)sb, (double)sc / a.h};
+        block_sum<3>(v, red);
+        if (t == 0) {
+            dsmem_st_f64(slots0 + 8u * (rank * 3 + 0), v[0]);
+            dsmem_st_f64(slots0 + 8u * (rank * 3 + 1), v[1]);
+            dsmem_st_f64(slots0 + 8u * (rank * 3 + 2), v[2]);
+        }
+        if (CL) cg::this_cluster().sync();
+        else __syncthreads();
+        if (rank == 0 && t == 0) {
+            double tt[3] = {0.0, 0.0, 0.0};
+            for (int r = 0; r < C; ++r)
+                for (int c = 0; c < 3; ++c) tt[c] += slots[r * 3 + c];
+            const double h3 = a.h * a.h * a.h;
+            const double Rk = (tt[0] / (double)mu + tt[1] / (double)tau - 2.0 * tt[2]) * h3;
+            const int cv = Rk < a.tol && slots[51] == 0.0;
+            const int lt = (globaltimer() - reinterpret_cast<const unsigned long long*>(slots)[50]) > a.budget_ns ||
+                           slots[51] != 0.0;
+            const int stop = a.fixed || cv || lt || it >= cap;
+            slots[48] = Rk;
+            slots[49] = (double)(cv | (lt << 1) | (stop << 2));
+        }
+        if (CL) cg::this_cluster().sync();
+        else __syncthreads();
+        if ((int)dsmem_ld_f64(slots0 + 8u * 49) & 4) break;
+    }
+    // the phi pushed by the CTA above after the last step has not been read
+    if (CL && slab_top && has_up) halo_wait(bar_phi);
+    if (own) {
+        *reinterpret_cast<float4*>(a.m1 + off + id) = make_float4(m1[0], m1[1], m1[2], m1[3]);
+        *reinterpret_cast<float4*>(a.m2 + off + id) = make_float4(m2[0], m2[1], m2[2], m2[3]);
+        *reinterpret_cast<float4*>(a.m3 + off + id) = make_float4(m3[0], m3[1], m3[2], m3[3]);
+        *reinterpret_cast<float4*>(a.phi + off + id) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+    }
+    if (rank == 0 && t == 0) {
+        const int dcs = (int)slots[49];
+        a.res->iters = it;
+        a.res->fpr = slots[48];
+        a.res->conv = dcs & 1;
+        a.res->timeout = ((dcs >> 1) & 1) && !(dcs & 1);
+    }
+    if (CL) cg::this_cluster().sync();
+}
+
+template <int NORM>
+static cudaError_t r3_attr()
+{
+    const int smem = (int)r3_smem(R3_MAX_NODES, R3_MAX_NODES);
+    cudaError_t e = cudaFuncSetAttribute(k3_resident<NORM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k3_resident<NORM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k3_resident<NORM, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+static const void* r3_fn(int norm, bool cl)
+{
+    if (norm == W1_NORM_L1) return cl ? (const void*)k3_resident<W1_NORM_L1, true> : (const void*)k3_resident<W1_NORM_L1, false>;
+    if (norm == W1_NORM_L2) return cl ? (const void*)k3_resident<W1_NORM_L2, true> : (const void*)k3_resident<W1_NORM_L2, false>;
+    return cl ? (const void*)k3_resident<W1_NORM_LINF, true> : (const void*)k3_resident<W1_NORM_LINF, false>;
+}
+
+static void r3_config(const Dims3& d, int C, cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr)
+{
+    const int nb = (d.nz / C) * d.nx * d.ny;
+    cfg = cudaLaunchConfig_t{};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(((nb / 4 + 31) / 32) * 32, 1, 1);
+    cfg.dynamicSmemBytes = r3_smem(nb, d.nx * d.ny);
+    cfg.numAttrs = 0;
+    if (C > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+}
+
+// Cluster size for an on-chip 3-D level (0: the level does not fit, or the
+// cluster cannot be placed on this device).
+static int r3_choose(int norm, const Dims3& d, int want)
+{
+    const int C = want > 0 ? want : r3_cluster_for(d.nx, d.ny, d.nz);
+    if (C < 1 || C > 16 || (C & (C - 1)) || d.nx % 4 || d.nz % C || (long long)(d.nz / C) * d.nx * d.ny > R3_MAX_NODES)
+        return 0;
+    if (r3_attr<W1_NORM_L1>() != cudaSuccess || r3_attr<W1_NORM_L2>() != cudaSuccess ||
+        r3_attr<W1_NORM_LINF>() != cudaSuccess)
+        return 0;
+    if (C == 1) return 1;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    r3_config(d, C, cfg, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, r3_fn(norm, true), &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n > 0 ? C : 0;
+}
+
+static cudaError_t r3_launch(int norm, int C, const R3Args& a, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    r3_config(a.d, C, cfg, attr);
+    cfg.stream = s;
+    void* args[1] = {const_cast<R3Args*>(&a)};
+    return cudaLaunchKernelExC(&cfg, r3_fn(norm, C > 1), args);
+}
+
 static dim3 grid3(long long n) { return dim3((unsigned)((n + T3 - 1) / T3)); }
 
 static cudaError_t launch_mprime(int norm, const Dims3& d, float mu, float ih, float* m1, float* m2, float* m3,
@@ -360,8 +740,10 @@ struct Scratch3 {
     double* r = nullptr;
     double* q = nullptr;  // 2 planes of FP64 residual masses
     Stats3Dev* st = nullptr;
+    Res3* res = nullptr;  // outcome of an on-chip level
     ~Scratch3()
     {
+        cudaFree(res);
         cudaFree(b);
         cudaFree(part);
         cudaFree(counter);
@@ -377,6 +759,7 @@ struct Scratch3 {
         if (e == cudaSuccess) e = cudaMalloc(&counter, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemset(counter, 0, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMalloc(&r, sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&res, sizeof(Res3));
         if (e == cudaSuccess && certificate) e = cudaMalloc(&q, 2 * n * sizeof(double));
         if (e == cudaSuccess && certificate) e = cudaMalloc(&st, sizeof(Stats3Dev));
         return e;
@@ -440,24 +823,46 @@ w1_status fail3(w1_status st, const std::string& m)
 
 extern "C" const char* w1_3d_last_error(void) { return g_err3.c_str(); }
 
-extern "C" w1_status w1_cp_steps3d(int nx, int ny, int nz, double h, int norm, float mu, float tau, const float* rho,
-                                   float* m1, float* m2, float* m3, float* phi, long long iters, void* stream,
-                                   double* fpr_last)
+extern "C" w1_status w1_cp_steps3d_ex(int nx, int ny, int nz, double h, int norm, float mu, float tau,
+                                      const float* rho, float* m1, float* m2, float* m3, float* phi, long long iters,
+                                      int path, int cluster, void* stream, double* fpr_last)
 {
     if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !rho || !m1 || !m2 || !m3 || !phi || iters < 0)
         return fail3(W1_ERR_INVALID_ARG, "bad arguments to w1_cp_steps3d");
     if (norm != W1_NORM_L1 && norm != W1_NORM_L2 && norm != W1_NORM_LINF)
         return fail3(W1_ERR_INVALID_ARG, "norm must be 1, 2 or 3");
+    if (path != 1 && path != 2) return fail3(W1_ERR_INVALID_ARG, "path must be 1 or 2");
     const Dims3 d{nx, ny, nz, (long long)nx * ny * nz};
     Scratch3 sc;
     W1_CK3(sc.alloc(d.n, false));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    W1_CK3(steps3(norm, d, h, mu, tau, rho, m1, m2, m3, phi, iters, true, sc, s));
     double r = 0.0;
-    if (iters > 0) W1_CK3(cudaMemcpyAsync(&r, sc.r, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (path == 1) {
+        const int C = r3_choose(norm, d, cluster);
+        if (C == 0) return fail3(W1_ERR_UNSUPPORTED, "the level does not fit on chip with that cluster");
+        if (iters > 0) {
+            R3Args a{d, mu, tau, (float)(mu / h), (float)(tau / h), h, 0.0, (int)std::min(iters, (long long)INT_MAX),
+                     1, iters, ~0ull, rho, m1, m2, m3, phi, sc.res};
+            W1_CK3(r3_launch(norm, C, a, s));
+            Res3 res{};
+            W1_CK3(cudaMemcpyAsync(&res, sc.res, sizeof(res), cudaMemcpyDeviceToHost, s));
+            W1_CK3(cudaStreamSynchronize(s));
+            r = res.fpr;
+        }
+    } else {
+        W1_CK3(steps3(norm, d, h, mu, tau, rho, m1, m2, m3, phi, iters, true, sc, s));
+        if (iters > 0) W1_CK3(cudaMemcpyAsync(&r, sc.r, sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
     W1_CK3(cudaStreamSynchronize(s));
     if (fpr_last) *fpr_last = r;
     return W1_OK;
+}
+
+extern "C" w1_status w1_cp_steps3d(int nx, int ny, int nz, double h, int norm, float mu, float tau, const float* rho,
+                                   float* m1, float* m2, float* m3, float* phi, long long iters, void* stream,
+                                   double* fpr_last)
+{
+    return w1_cp_steps3d_ex(nx, ny, nz, h, norm, mu, tau, rho, m1, m2, m3, phi, iters, 2, 0, stream, fpr_last);
 }
 
 extern "C" w1_status w1_restrict3d(int nx, int ny, int nz, const float* fine, float* coarse, void* stream)
@@ -493,7 +898,7 @@ extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, in
     w1_default_options(&o);
     if (opt) o = *opt;
     const int K = o.check_every > 0 ? o.check_every : 32;
-    if (K < 1 || !(o.theta > 0.0) || o.theta > 1.0 || o.max_iters < 1)
+    if (K < 1 || !(o.theta > 0.0) || o.theta > 1.0 || o.max_iters < 1 || o.path < 0 || o.path > 3)
         return fail3(W1_ERR_INVALID_ARG, "bad options");
     if (!(h > 0.0)) h = 1.0 / (double)std::max(nx, std::max(ny, nz));
     if (levels <= 0) {  // the paper's L = log2(1/h) - 3, kept divisible, coarsest side >= 2
@@ -565,8 +970,7 @@ extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, in
     W1_CK3(cudaGetLastError());
     w1_status ret = W1_OK;
     if (stats) std::memset(stats, 0, sizeof(*stats));
-    const auto t0 = std::chrono::steady_clock::now();
-    bool all_conv = true;
+    bool all_conv = true, late_any = false;
     for (int l = 0; l < levels; ++l) {
         const int sh = levels - 1 - l;
         const Dims3 d{nx >> sh, ny >> sh, nz >> sh, (long long)(nx >> sh) * (ny >> sh) * (nz >> sh)};
@@ -584,19 +988,41 @@ extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, in
         long long it = 0;
         double r = 0.0;
         bool conv = false, late = false;
-        while (it < o.max_iters) {
-            W1_CK3(steps3(norm, d, hl, mu, mu, lvl(l, 0), lvl(l, 1), lvl(l, 2), lvl(l, 3), lvl(l, 4), K, true, sc, s));
-            it += K;
-            W1_CK3(cudaMemcpyAsync(&r, sc.r, sizeof(double), cudaMemcpyDeviceToHost, s));
+        // on chip where the level fits (path 0 or 1), else two launches per step
+        const int C = (o.path == 0 || o.path == 1) ? r3_choose(norm, d, 0) : 0;
+        if (o.path == 1 && C == 0) return fail3(W1_ERR_UNSUPPORTED, "a level does not fit on chip");
+        if (late_any) {
+            // a coarser level ran out of time: carry the state up without steps
+        } else if (C > 0) {
+            const unsigned long long budget =
+                o.time_budget_s >= 1e9 ? ~0ull : (unsigned long long)(o.time_budget_s * 1e9);
+            R3Args a{d, mu, mu, (float)(mu / hl), (float)(mu / hl), hl, tl, K, 0, o.max_iters, budget,
+                     lvl(l, 0), lvl(l, 1), lvl(l, 2), lvl(l, 3), lvl(l, 4), sc.res};
+            W1_CK3(r3_launch(norm, C, a, s));
+            Res3 res{};
+            W1_CK3(cudaMemcpyAsync(&res, sc.res, sizeof(res), cudaMemcpyDeviceToHost, s));
             W1_CK3(cudaStreamSynchronize(s));
-            if (r < tl) {
-                conv = true;
-                break;
-            }
-            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-            if (el > o.time_budget_s) {
-                late = true;
-                break;
+            it = res.iters;
+            r = res.fpr;
+            conv = res.conv != 0;
+            late = res.timeout != 0;
+        } else {
+            const auto t0 = std::chrono::steady_clock::now();
+            while (it < o.max_iters) {
+                W1_CK3(steps3(norm, d, hl, mu, mu, lvl(l, 0), lvl(l, 1), lvl(l, 2), lvl(l, 3), lvl(l, 4), K, true, sc,
+                              s));
+                it += K;
+                W1_CK3(cudaMemcpyAsync(&r, sc.r, sizeof(double), cudaMemcpyDeviceToHost, s));
+                W1_CK3(cudaStreamSynchronize(s));
+                if (r < tl) {
+                    conv = true;
+                    break;
+                }
+                const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                if (el > o.time_budget_s) {
+                    late = true;
+                    break;
+                }
             }
         }
         if (stats && l < W1_MAX_LEVELS) {
@@ -605,12 +1031,13 @@ extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, in
             stats->iters[l] = it;
             stats->fpr[l] = r;
             stats->tol[l] = tl;
-            stats->path[l] = 2;
+            stats->path[l] = C > 0 ? 1 : 2;
+            stats->cluster[l] = C;
         }
         all_conv &= conv;
-        if (late) {
+        if (late && !late_any) {
+            late_any = true;
             ret = fail3(W1_ERR_TIMEOUT, "the time budget ran out");
-            break;
         }
         if (!conv && ret == W1_OK) ret = fail3(W1_ERR_NOT_CONVERGED, "a level hit max_iters");
     }

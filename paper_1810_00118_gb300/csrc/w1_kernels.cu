@@ -978,15 +978,6 @@ __global__ void __launch_bounds__(NPT >= 8 ? RES_THREADS / 2 : RES_THREADS, 1) k
 // dm on test steps) so that neighbours can read them: the row above and the
 // row below as one 16-byte access, the left/right neighbour of the run as one
 // scalar access.  Same arithmetic and stop test as k_resident.
-__device__ __forceinline__ float4 dsmem_ld4(uint32_t addr)
-{
-    float4 v;
-    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(addr)
-                 : "memory");
-    return v;
-}
 
 // One level of one pair, on CTA `rank` of a group of C (a cluster when CL).
 template <int NORM, bool CL>

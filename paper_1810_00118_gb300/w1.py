@@ -147,6 +147,7 @@ def _load() -> ctypes.CDLL:
         "w1_solve3d": (st, [I, I, I, D, I, I, D, ctypes.POINTER(Options), P, P, P, ctypes.POINTER(D), P, P,
                             ctypes.POINTER(_Stats)]),
         "w1_cp_steps3d": (st, [I, I, I, D, I, F, F, P, P, P, P, P, LL, P, ctypes.POINTER(D)]),
+        "w1_cp_steps3d_ex": (st, [I, I, I, D, I, F, F, P, P, P, P, P, LL, I, I, P, ctypes.POINTER(D)]),
         "w1_restrict3d": (st, [I, I, I, P, P, P]),
         "w1_prolong3d": (st, [I, I, I, P, P, P, P, P, P, P, P, P]),
         "w1_3d_last_error": (ctypes.c_char_p, []),
@@ -475,13 +476,14 @@ def solve3d(rho0, rho1, norm=NORM_L1, h=0.0, levels=0, tol=0.0, flux=None, poten
     return d.value, Stats._from(s), st
 
 
-def cp_steps3d(rho, m1, m2, m3, phi, h, norm, mu, tau, iters, stream=None) -> float:
-    """`iters` steps of eq. primaldual on a 3-D level, in place; returns R^k of the last step."""
+def cp_steps3d(rho, m1, m2, m3, phi, h, norm, mu, tau, iters, path=2, cluster=0, stream=None) -> float:
+    """`iters` steps of eq. primaldual on a 3-D level, in place; returns R^k of the
+    last step.  path 2: two launches per step; 1: on chip (cluster CTAs, 0: auto)."""
     nz, ny, nx = rho.shape
     f = ctypes.c_double(0.0)
-    _check3(_lib.w1_cp_steps3d(nx, ny, nz, h, norm, mu, tau, _dev_ptr(rho),
-                               *(_dev_ptr(t, rho.shape) for t in (m1, m2, m3, phi)), int(iters),
-                               _stream_ptr(stream), ctypes.byref(f)))
+    _check3(_lib.w1_cp_steps3d_ex(nx, ny, nz, h, norm, mu, tau, _dev_ptr(rho),
+                                  *(_dev_ptr(t, rho.shape) for t in (m1, m2, m3, phi)), int(iters), int(path),
+                                  int(cluster), _stream_ptr(stream), ctypes.byref(f)))
     return f.value
 
 

@@ -80,6 +80,40 @@ def test_cp_steps3d_match_oracle(w1, norm, shape):
     assert not host(t[1])[..., -1].any() and not host(t[2])[:, -1, :].any() and not host(t[3])[-1].any()
 
 
+# (shape, cluster): one CTA, clusters of 2..16 slabs (one-plane slabs included)
+RESIDENT3 = [((1, 1, 4), 1), ((2, 3, 8), 1), ((8, 8, 8), 1), ((16, 16, 16), 1), ((4, 12, 16), 2), ((4, 12, 16), 4),
+             ((32, 32, 32), 8), ((32, 32, 32), 16), ((16, 16, 16), 16), ((2, 40, 32), 2), ((16, 8, 64), 4)]
+
+
+@pytest.mark.parametrize("norm", [L1, L2, LINF])
+@pytest.mark.parametrize("shape,cluster", RESIDENT3)
+def test_onchip_steps3d_match_oracle(w1, norm, shape, cluster):
+    """Every step of a level in one launch (one CTA or a cluster of slabs whose
+    halo planes move between CTAs): 40 steps against the oracle; R^k of the last."""
+    nz, ny, nx = shape
+    rng = np.random.default_rng(nx * 131 + ny * 17 + nz + cluster + 7 * norm)
+    rho, m1, m2, m3, phi = rand_state3(rng, nz, ny, nx)
+    h = 1.0 / max(shape)
+    mu = mu3(h)
+    t = [dev(a) for a in (rho, m1, m2, m3, phi)]
+    steps = 40
+    r = w1.cp_steps3d(*t, h, norm, mu, mu, steps, path=1, cluster=cluster)
+    o1, o2, o3, op, rf = d3.cp_iterate(rho.astype(np.float64), m1, m2, m3, phi, h, norm, steps, mu=mu, tau=mu)
+    for got, want in zip(t[1:], (o1, o2, o3, op)):
+        scale = max(1.0, np.abs(want).max())
+        assert np.abs(host(got) - want).max() <= 2e-5 * scale
+    assert r == pytest.approx(rf, rel=2e-3, abs=1e-12)
+
+
+def test_onchip_steps3d_refuses_what_does_not_fit(w1):
+    g = [torch.zeros((32, 32, 32), device="cuda") for _ in range(5)]
+    with pytest.raises(w1.W1Error):
+        w1.cp_steps3d(*g, 1 / 32, L1, 0.01, 0.01, 8, path=1, cluster=1)  # 32768 voxels in one CTA
+    g = [torch.zeros((4, 4, 6), device="cuda") for _ in range(5)]
+    with pytest.raises(w1.W1Error):
+        w1.cp_steps3d(*g, 1 / 6, L1, 0.01, 0.01, 8, path=1)  # nx % 4 != 0
+
+
 @pytest.mark.parametrize("shape", [(2, 2, 2), (4, 6, 8), (8, 34, 66), (64, 64, 64)])
 def test_restrict3d_matches_oracle(w1, shape):
     rng = np.random.default_rng(sum(shape))
@@ -127,13 +161,16 @@ def flux3_rel_l1(f, ref):
     return num / sum(np.abs(w).sum() for w in (ref.m1, ref.m2, ref.m3))
 
 
+@pytest.mark.parametrize("path", [0, 2])
 @pytest.mark.parametrize("norm", [L1, L2, LINF])
-def test_solve3d_16_two_levels(w1, norm):
-    """16^3, two levels 8^3 -> 16^3, default tolerance of eq. stop_tol."""
+def test_solve3d_16_two_levels(w1, norm, path):
+    """16^3, two levels 8^3 -> 16^3, default tolerance of eq. stop_tol; both
+    levels on chip (path 0) or two launches per step (path 2)."""
     r0, r1 = synth.pair3(16, norm)
-    val, st, status, flux, phi, ref = solve3_and_replay(w1, r0, r1, norm, 2)
+    val, st, status, flux, phi, ref = solve3_and_replay(w1, r0, r1, norm, 2, path=path)
     assert status == w1.OK and st.converged
     assert st.levels == 2 and st.sizes == [(8, 8), (16, 16)]
+    assert st.path == ([1, 1] if path == 0 else [2, 2])
     assert all(k % 32 == 0 and k > 0 for k in st.iters)
     assert val == st.w1
     assert abs(val - ref.w1) <= 1e-4 * abs(ref.w1), (val, ref.w1)
@@ -143,6 +180,16 @@ def test_solve3d_16_two_levels(w1, norm):
     # the oracle's own stop decision at the GPU's count: R^k is below eps_l there too
     for k in range(2):
         assert ref.fpr[k] < st.tol[k] * 1.5
+
+
+def test_solve3d_32_cluster_level(w1):
+    """32^3 with two levels: 16^3 on one CTA, 32^3 on an 8-CTA cluster of slabs."""
+    r0, r1 = synth.pair3(32, 6)
+    val, st, status, flux, phi, ref = solve3_and_replay(w1, r0, r1, L1, 2)
+    assert status == w1.OK and st.converged
+    assert st.path == [1, 1] and st.cluster == [1, 8]
+    assert abs(val - ref.w1) <= 1e-4 * abs(ref.w1), (val, ref.w1)
+    assert flux3_rel_l1(flux, ref) <= 1e-3
 
 
 def test_solve3d_ragged_three_levels(w1):
