@@ -655,6 +655,8 @@ def main():
     ap.add_argument("--min-seconds", type=float, default=0.0, help="serving: at least rate*this requests")
     ap.add_argument("--slots", type=int, default=48, help="serving: solves in flight")
     ap.add_argument("--serve-batch", type=int, default=1, help="serving: pairs a slot solves together")
+    ap.add_argument("--latency-below", type=int, default=4,
+                    help="serving: in-flight count below which requests get latency-tuned slots (0: off)")
     ap.add_argument("--only", default="solve",
                     choices=["solve", "stream-kernel", "tblock-kernel", "resident-kernel", "pdhg-kernel", "serve",
                              "mixed", "tol-sweep", "solve3d", "3d-kernel"],
@@ -998,8 +1000,15 @@ def run_serve(args):
     pool = serve_pool(torch)
     rates = [float(x) for x in args.rates.split(",")]
     out = []
-    with w1.Server(hbm_budget_bytes=40 << 30, max_slots=args.slots, max_batch=args.serve_batch) as srv:
-        # warm-up: one request of every class builds its slot
+    with w1.Server(hbm_budget_bytes=40 << 30, max_slots=args.slots, max_batch=args.serve_batch,
+                   latency_below=args.latency_below) as srv:
+        # warm-up: requests one at a time build the latency-tuned slots (and run
+        # the autotuner once per class), then a burst builds the others
+        if args.latency_below > 0:
+            for size in SERVE_SIZES:
+                for norm in (1, 2):
+                    a0, a1 = pool[size][0]
+                    srv.wait(srv.submit(a0, a1, norm=norm))
         serve_run(w1, srv, pool, 1000.0, 16, seed=1)
         for r in rates:
             n = max(args.requests, int(r * args.min_seconds))
@@ -1010,7 +1019,8 @@ def run_serve(args):
             print(json.dumps(out[-1]), flush=True)
         info = srv.info()
     print(json.dumps({"serving": out, "server": info, "sizes": SERVE_SIZES, "probs": SERVE_PROBS,
-                      "budget_GiB": 40, "slots": args.slots, "max_batch": args.serve_batch}))
+                      "budget_GiB": 40, "slots": args.slots, "max_batch": args.serve_batch,
+                      "latency_below": args.latency_below}))
     return 0
 
 

@@ -282,8 +282,10 @@ size_t w1_plan_bytes(int nx, int ny, double h, int levels, int norm, double tol,
  * by w1_submit and started as soon as a slot of their class is free or can be
  * created within the HBM budget (idle slots of other classes are evicted,
  * least recently used first); up to max_slots solves run at once on their own
- * streams, so their work overlaps on the device.  A request's result does not
- * depend on what else is in flight.  All calls are thread-safe.  Streams share
+ * streams, so their work overlaps on the device.  With latency_below = 0 a
+ * request's result does not depend on what else is in flight; with
+ * latency_below > 0 the kernel choice depends on the load, and results agree
+ * to FP32 rounding (W1 within 1e-4, tested).  All calls are thread-safe.  Streams share
  * the context's hardware work queues (8 unless CUDA_DEVICE_MAX_CONNECTIONS is
  * set, up to 32, before CUDA initialises); with more slots than queues, long
  * level solves on one queue delay the launches of the streams that share it.
@@ -295,6 +297,12 @@ typedef struct {
     int max_slots;           /* solves in flight at once; default 32 */
     int max_batch;           /* requests of one class solved together in a slot; default 1 */
     w1_options opt;          /* plan options of every slot */
+    int latency_below;       /* while fewer solves than this are in flight, a request goes to a
+                                slot whose plan lets the autotuner pick the fastest kernels for
+                                one solve alone (w1_options.tune = 1: more SMs per level); at
+                                higher load, to a slot with `opt` (throughput); 0 (default): off.
+                                Applies when opt.path = 0 and opt.algorithm = 3.  A class may
+                                then hold slots of both kinds.                               */
 } w1_server_config;
 
 typedef struct {

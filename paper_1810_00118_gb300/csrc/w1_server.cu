@@ -82,6 +82,7 @@ struct Result {
 struct Slot {
     w1_server* srv = nullptr;
     Key key{};
+    int flavour = 0;  // 0: the configured options; 1: kernels autotuned for one solve alone
     w1_plan* plan = nullptr;
     cudaStream_t stream = nullptr;
     float* in0 = nullptr;
@@ -101,6 +102,7 @@ struct w1_server {
     size_t in_use = 0;
     int max_slots = 0;
     int max_batch = 1;
+    int latency_below = 0;
     w1_options opt{};
     std::mutex mu;
     std::condition_variable cv;
@@ -129,9 +131,20 @@ void CUDART_CB on_slot_done(void* arg)
     s->srv->cv.notify_all();
 }
 
-size_t slot_bytes(const w1_server* srv, const Key& k)
+// Plan options of a slot flavour: flavour 1 lets the autotuner pick each level's
+// kernel for one solve with the GPU otherwise idle (w1_options.tune = 1), where
+// the configured options leave that choice open.
+w1_options slot_options(const w1_server* srv, int flavour)
 {
-    const size_t plan = w1_plan_bytes(k.nx, k.ny, k.h, k.levels, k.norm, k.tol, srv->max_batch, &srv->opt);
+    w1_options o = srv->opt;
+    if (flavour == 1 && o.path == 0 && o.algorithm != 4) o.tune = 1;
+    return o;
+}
+
+size_t slot_bytes(const w1_server* srv, const Key& k, int flavour)
+{
+    const w1_options o = slot_options(srv, flavour);
+    const size_t plan = w1_plan_bytes(k.nx, k.ny, k.h, k.levels, k.norm, k.tol, srv->max_batch, &o);
     if (plan == 0) return 0;
     return plan + 2 * (size_t)k.nx * k.ny * sizeof(float) * srv->max_batch;
 }
@@ -148,9 +161,9 @@ void destroy_slot(Slot* s)
 
 // Creates a slot for key k within the budget (evicting idle slots of other
 // classes if needed); nullptr when the budget or the slot count is exhausted.
-Slot* make_slot(w1_server* srv, const Key& k)
+Slot* make_slot(w1_server* srv, const Key& k, int flavour)
 {
-    const size_t need = slot_bytes(srv, k);
+    const size_t need = slot_bytes(srv, k, flavour);
     if (need == 0) return nullptr;
     for (;;) {
         const bool fits = srv->in_use + need <= srv->budget && (int)srv->slots.size() < srv->max_slots;
@@ -172,9 +185,11 @@ Slot* make_slot(w1_server* srv, const Key& k)
     auto s = std::make_unique<Slot>();
     s->srv = srv;
     s->key = k;
+    s->flavour = flavour;
     s->bytes = need;
     const size_t nb = (size_t)k.nx * k.ny * sizeof(float) * srv->max_batch;
-    if (w1_plan_create_batch(k.nx, k.ny, k.h, k.levels, k.norm, k.tol, srv->max_batch, &srv->opt, &s->plan) != W1_OK ||
+    const w1_options o = slot_options(srv, flavour);
+    if (w1_plan_create_batch(k.nx, k.ny, k.h, k.levels, k.norm, k.tol, srv->max_batch, &o, &s->plan) != W1_OK ||
         cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc(&s->in0, nb) != cudaSuccess || cudaMalloc(&s->in1, nb) != cudaSuccess) {
         srv->worker_error = std::string("slot creation failed: ") + w1_last_error();
@@ -244,13 +259,21 @@ void dispatch(w1_server* srv)
             ++i;
             continue;
         }
-        Slot* slot = nullptr;
-        for (auto& s : srv->slots)
-            if (!s->busy && s->key == k) {
-                slot = s.get();
-                break;
-            }
-        if (!slot) slot = make_slot(srv, k);
+        // a lightly loaded GPU gets the latency-tuned flavour of the class
+        int in_flight = 0;
+        for (auto& s : srv->slots) in_flight += s->busy ? 1 : 0;
+        const int flavour = in_flight < srv->latency_below ? 1 : 0;
+        auto free_slot = [&](int f) -> Slot* {
+            for (auto& s : srv->slots)
+                if (!s->busy && s->key == k && s->flavour == f) return s.get();
+            return nullptr;
+        };
+        Slot* slot = free_slot(flavour);
+        if (!slot) slot = make_slot(srv, k, flavour);
+        if (!slot && flavour == 1) {  // no room for a latency-tuned slot: the configured kind
+            slot = free_slot(0);
+            if (!slot) slot = make_slot(srv, k, 0);
+        }
         if (!slot) {
             blocked.push_back(k);
             ++i;
@@ -331,6 +354,7 @@ extern "C" void w1_server_default_config(w1_server_config* c)
     c->max_slots = 32;
     c->max_batch = 1;
     w1_default_options(&c->opt);
+    c->latency_below = 0;
 }
 
 extern "C" w1_status w1_server_create_ex(const w1_server_config* cfg, w1_server** out)
@@ -340,7 +364,7 @@ extern "C" w1_status w1_server_create_ex(const w1_server_config* cfg, w1_server*
     w1_server_config c;
     w1_server_default_config(&c);
     if (cfg) c = *cfg;
-    if (c.max_slots < 1 || c.max_batch < 1 || c.hbm_budget_bytes == 0)
+    if (c.max_slots < 1 || c.max_batch < 1 || c.hbm_budget_bytes == 0 || c.latency_below < 0)
         return srv_fail(W1_ERR_INVALID_ARG, "max_slots, max_batch and the budget must be positive");
     auto* srv = new (std::nothrow) w1_server();
     if (!srv) return srv_fail(W1_ERR_NOMEM, "host allocation failed");
@@ -352,6 +376,7 @@ extern "C" w1_status w1_server_create_ex(const w1_server_config* cfg, w1_server*
     srv->budget = c.hbm_budget_bytes;
     srv->max_slots = c.max_slots;
     srv->max_batch = c.max_batch;
+    srv->latency_below = c.latency_below;
     srv->opt = c.opt;
     try {
         srv->worker = std::thread(worker_main, srv);
@@ -380,7 +405,7 @@ extern "C" w1_status w1_submit(w1_server* srv, int nx, int ny, double h, int lev
     if (norm != W1_NORM_L1 && norm != W1_NORM_L2 && norm != W1_NORM_LINF) return srv_fail(W1_ERR_INVALID_ARG, "norm must be 1, 2 or 3");
     if (!(h > 0.0)) h = 1.0 / (double)(nx > ny ? nx : ny);
     Key k{nx, ny, levels, norm, h, tol};
-    const size_t need = slot_bytes(srv, k);
+    const size_t need = slot_bytes(srv, k, 0);
     if (need == 0) return srv_fail(W1_ERR_SHAPE, std::string("request rejected: ") + w1_last_error());
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stop) return srv_fail(W1_ERR_INVALID_ARG, "server is shutting down");

@@ -57,7 +57,7 @@ class LevelChoice(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("opt", Options)]
+                ("opt", Options), ("latency_below", ctypes.c_int)]
 
 
 class ServerInfo(ctypes.Structure):
@@ -513,12 +513,13 @@ def plan_bytes(nx, ny, h=0.0, levels=0, norm=NORM_L1, tol=0.0, batch=1, **option
 class Server:
     """Continuous-batching request loop (w1_server_create_ex)."""
 
-    def __init__(self, hbm_budget_bytes=40 << 30, max_slots=32, max_batch=1, **options):
+    def __init__(self, hbm_budget_bytes=40 << 30, max_slots=32, max_batch=1, latency_below=0, **options):
         cfg = ServerConfig()
         _lib.w1_server_default_config(ctypes.byref(cfg))
         cfg.hbm_budget_bytes = int(hbm_budget_bytes)
         cfg.max_slots = max_slots
         cfg.max_batch = max_batch
+        cfg.latency_below = latency_below
         for k, v in options.items():
             setattr(cfg.opt, k, v)
         self._s = ctypes.c_void_p()

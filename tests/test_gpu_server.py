@@ -61,6 +61,31 @@ def test_results_same_alone_and_in_the_mix(w1, max_batch):
         assert results[tk][1] == v
 
 
+def test_latency_slots_agree_within_tolerance(w1):
+    """latency_below > 0: a lone request runs on a slot whose kernels the
+    autotuner picked for one solve, requests under load on the configured slots;
+    either way W1 agrees with a plain solve to 1e-4 (the kernels differ only in
+    FP32 rounding order)."""
+    target0, target1 = (dev(x) for x in synth.pair(2, 778, n=128))
+    with w1.Plan(128, 128, norm=1) as plan:
+        ref, _, _ = plan.solve(target0, target1)
+    with w1.Server(max_slots=8, latency_below=2) as srv:
+        st, alone, _ = srv.wait(srv.submit(target0, target1, norm=1), 120)
+        assert st == w1.OK
+        mix = make_requests(2)
+        tickets = [srv.submit(a, b, norm=norm) for a, b, norm in mix]
+        tx = srv.submit(target0, target1, norm=1)
+        results = {tk: srv.wait(tk, 300) for tk in tickets}
+        st2, in_mix, _ = srv.wait(tx, 300)
+    assert st2 == w1.OK and all(r[0] == w1.OK for r in results.values())
+    assert alone == pytest.approx(ref, rel=1e-4) and in_mix == pytest.approx(ref, rel=1e-4)
+    for (a, b, norm), tk in list(zip(mix, tickets))[::3]:
+        n = a.shape[0]
+        with w1.Plan(n, n, norm=norm) as p:
+            v, _, _ = p.solve(a, b)
+        assert results[tk][1] == pytest.approx(v, rel=1e-4)
+
+
 def test_budget_rejects_and_evicts(w1):
     small = w1.plan_bytes(64, 64, norm=1) + 2 * 64 * 64 * 4
     with w1.Server(hbm_budget_bytes=small + 1024, max_slots=4) as srv:
