@@ -463,20 +463,24 @@ def run_gpu(args):
     # latency of one solve with the GPU otherwise idle: one pair at a time through
     # the blocking entry point, CUDA events around each solve
     solo = {}
+    tuned = args.algorithm == 3  # the latency-tuned plan (tune = 1) beside the default one
     for norm in (NORMS if args.solo > 0 else ()):
-        with w1.Plan(N, N, levels=LEVELS, norm=norm, algorithm=args.algorithm, check_every=args.check_every) as p1:
-            ts = []
-            for k in range(args.solo):
-                t0s, t1s = dev_pairs[k % total_steps][0][k % B], dev_pairs[k % total_steps][1][k % B]
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                p1.solve(t0s, t1s, stream=stream, allow=ok)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ts.append(e0.elapsed_time(e1))
-        solo[f"L{norm}"] = {"p50": float(np.percentile(ts, 50)), "p99": float(np.percentile(ts, 99)),
-                            "pairs": len(ts)}
-    solo["what"] = "one solve with the GPU otherwise idle (w1_solve, CUDA events)"
+        for tune in ((0, 1) if tuned else (0,)):
+            with w1.Plan(N, N, levels=LEVELS, norm=norm, algorithm=args.algorithm, check_every=args.check_every,
+                         tune=tune) as p1:
+                ts = []
+                for k in range(args.solo):
+                    t0s, t1s = dev_pairs[k % total_steps][0][k % B], dev_pairs[k % total_steps][1][k % B]
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    p1.solve(t0s, t1s, stream=stream, allow=ok)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+            solo[f"L{norm}" + ("_latency_tuned" if tune else "")] = {
+                "p50": float(np.percentile(ts, 50)), "p99": float(np.percentile(ts, 99)), "pairs": len(ts)}
+    solo["what"] = ("one solve with the GPU otherwise idle (w1_solve, CUDA events); _latency_tuned: the plan's "
+                    "kernels picked by the autotuner for one solve alone (tune = 1)")
 
     # rooflines (the dominant on-chip kernel; the streaming kernels at 8192^2)
     roof = None
