@@ -71,7 +71,16 @@ struct ResArgs {
     const float* rho;
     int pairs;
     IterArgs it;
+    // fault injection for tests of the bounded halo waits: CTA (drop_rank - 1)
+    // of every cluster skips its halo pushes (0: none; the host sets it from
+    // the W1_FAULT_HALO_RANK environment variable when a plan is built)
+    int drop_rank;
 };
+
+// W1_FAULT_HALO_RANK=r makes CTA r of every on-chip cluster level skip its halo
+// pushes, so that its neighbours' bounded waits run out and the level ends with
+// a timeout status (tests of that path only); returns r + 1, or 0 when unset.
+int fault_halo_rank();
 
 // Kernel launchers (w1_kernels.cu).  All enqueue on `s` and return the launch status.
 // prep: rho = rho0 - rho1 per pair, mass check, exact zero mean; pairs >= nbatch are

@@ -1038,6 +1038,7 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
     // initial phi, phase s the phi after step s; phase s of bar_m2 the m2' of
     // step s + 1
     const bool has_up = CL && rank + 1 < C, has_dn = CL && rank > 0;
+    const bool pushes = rank + 1 != a.drop_rank;  // false only under fault injection
     if (CL && t == 0) {
         mbar_init(bar_phi, 1);
         mbar_init(bar_m2, 1);
@@ -1058,7 +1059,7 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
         }
         slots0 = dsmem_map(smem_u32(slots), 0);
         // the initial phi of the bottom row goes to the CTA below
-        if (row_bot && has_dn)
+        if (row_bot && has_dn && pushes)
             st_async4(dsmem_map(smem_u32(hphi + i0), rank - 1), make_float4(pv[0], pv[1], pv[2], pv[3]),
                       dsmem_map(bar_phi, rank - 1));
     }
@@ -1123,7 +1124,7 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
                 } else {  // the top row of a band below another CTA's
                     halo_wait(bar_phi);
                     u = *reinterpret_cast<const float4*>(hphi + i0);
-                    if (t == t_top) mbar_expect(bar_phi, 4u * nx);
+                    if (t == t_top && !sync_fail) mbar_expect(bar_phi, 4u * nx);
                 }
                 up[0] = u.x; up[1] = u.y; up[2] = u.z; up[3] = u.w;
             }
@@ -1152,7 +1153,7 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
             }
             *reinterpret_cast<float4*>(s1 + idx) = make_float4(n1[0], n1[1], n1[2], n1[3]);
             *reinterpret_cast<float4*>(s2 + idx) = make_float4(n2[0], n2[1], n2[2], n2[3]);
-            if (CL && row_top && has_up)
+            if (CL && row_top && has_up && pushes)
                 st_async4(dsmem_map(smem_u32(hm2 + i0), rank + 1), make_float4(n2[0], n2[1], n2[2], n2[3]),
                           dsmem_map(bar_m2, rank + 1));
         }
@@ -1172,7 +1173,7 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
             } else if (has_dn) {
                 halo_wait(bar_m2);
                 b = *reinterpret_cast<const float4*>(hm2 + i0);
-                if (t == 0) mbar_expect(bar_m2, 4u * nx);
+                if (t == 0 && !sync_fail) mbar_expect(bar_m2, 4u * nx);
             } else {
                 b = make_float4(0.f, 0.f, 0.f, 0.f);
             }
@@ -1203,7 +1204,7 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
 #pragma unroll
             for (int c = 0; c < 4; ++c) pv[c] = pn[c];
             *reinterpret_cast<float4*>(ph + idx) = make_float4(pn[0], pn[1], pn[2], pn[3]);
-            if (CL && row_bot && has_dn)
+            if (CL && row_bot && has_dn && pushes)
                 st_async4(dsmem_map(smem_u32(hphi + i0), rank - 1), make_float4(pn[0], pn[1], pn[2], pn[3]),
                           dsmem_map(bar_phi, rank - 1));
         }
@@ -1319,6 +1320,7 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
     float* hm2 = hphi + nx;
     const uint32_t bar_phi = smem_u32(slots + 56), bar_m2 = smem_u32(slots + 57);
     const bool has_up = CL && rank + 1 < C, has_dn = CL && rank > 0;
+    const bool pushes = rank + 1 != a.drop_rank;  // false only under fault injection
     const size_t off = (size_t)pair * P.stride + (size_t)jb * nx;
     const float mu = P.mu, tau = P.tau;
     const float cm = P.mu * P.ih, ct = P.tau * P.ih;  // mu / h, tau / h
@@ -1386,7 +1388,7 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             if constexpr (decltype(halo)::value) {
                 halo_wait(bar_m2);
                 b = *reinterpret_cast<const float4*>(hm2 + i0);
-                if (t == 0 && r == 0) mbar_expect(bar_m2, 4u * nx);
+                if (t == 0 && r == 0 && !sync_fail) mbar_expect(bar_m2, 4u * nx);
             } else {
                 b = dsmem_ld4(s2_dn + 4u * i0);
             }
@@ -1408,7 +1410,7 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
     }
     group_sync();
     // the initial phi of the bottom row goes to the CTA below
-    if (has_dn) {
+    if (has_dn && pushes) {
 #pragma unroll
         for (int r = 0; r < RESW_RUNS; ++r)
             if (pk[r] >= 0 && (pk[r] >> 16) == 0) {
@@ -1444,7 +1446,7 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
                 } else {
                     halo_wait(bar_phi);
                     u = *reinterpret_cast<const float4*>(hphi + i0);
-                    if (t == t_top && id == last_row) mbar_expect(bar_phi, 4u * nx);
+                    if (t == t_top && id == last_row && !sync_fail) mbar_expect(bar_phi, 4u * nx);
                 }
             }
             const float right = last_col ? p4.w : (lane == 31 ? ph[id + 4] : rn);
@@ -1462,7 +1464,7 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             }
             *reinterpret_cast<float4*>(s1 + id) = make_float4(n1[0], n1[1], n1[2], n1[3]);
             *reinterpret_cast<float4*>(s2 + id) = make_float4(n2[0], n2[1], n2[2], n2[3]);
-            if (has_up && jl == rows - 1)
+            if (has_up && jl == rows - 1 && pushes)
                 st_async4(dsmem_map(smem_u32(hm2 + i0), rank + 1), make_float4(n2[0], n2[1], n2[2], n2[3]),
                           dsmem_map(bar_m2, rank + 1));
         }
@@ -1489,7 +1491,7 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
                 Dv[r][c] = Dn[c];
             }
             *reinterpret_cast<float4*>(ph + id) = make_float4(pn[0], pn[1], pn[2], pn[3]);
-            if (has_dn && id < nx)
+            if (has_dn && id < nx && pushes)
                 st_async4(dsmem_map(smem_u32(hphi + id), rank - 1), make_float4(pn[0], pn[1], pn[2], pn[3]),
                           dsmem_map(bar_phi, rank - 1));
         }

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -134,6 +135,16 @@ struct w1_plan {
     int last_batch;
     const float2* tw;  // prox-PDHG twiddle table (per device)
 };
+
+namespace w1 {
+int fault_halo_rank()
+{
+    const char* e = std::getenv("W1_FAULT_HALO_RANK");
+    if (!e || !*e) return 0;
+    const int r = std::atoi(e);
+    return r >= 0 && r < 16 ? r + 1 : 0;
+}
+}  // namespace w1
 
 extern "C" void w1_default_options(w1_options* o)
 {
@@ -561,6 +572,7 @@ static w1_status build_graph(w1_plan* p)
         }
         if (v.path == 1) {
             ResArgs a{};
+            a.drop_rank = fault_halo_rank();
             a.m1 = v.m1[0];
             a.m2 = v.m2[0];
             a.phi = v.phi[0];
@@ -698,6 +710,7 @@ static w1_status run_eager(w1_plan* p, cudaStream_t s)
         }
         if (v.path == 1) {
             ResArgs a{};
+            a.drop_rank = fault_halo_rank();
             a.m1 = v.m1[0];
             a.m2 = v.m2[0];
             a.phi = v.phi[0];
