@@ -727,6 +727,8 @@ static constexpr int RESW_MAX_NODES = RES_THREADS * 4 * RESW_RUNS;  // 16384
 static constexpr unsigned long long RES_HALO_WAIT_NS = 200000000ull;
 // wide bands in a cluster keep two halo rows of nx floats beside the band
 static constexpr int RESW_MAX_HALO_X = 4096;
+// tensor-memory columns of the wide level kernel (rho of 16 nodes per thread, 32 warps)
+static constexpr uint32_t RESW_TMEM_COLS = 128;
 
 int resident_max_nodes() { return RES_MAX_NODES; }
 
@@ -1297,7 +1299,10 @@ static size_t resident_wide_smem(int band)
     return RES_RED_BYTES + RES_SLOT_BYTES + (size_t)band * 3 * sizeof(float) + 2 * RESW_MAX_HALO_X * sizeof(float);
 }
 
-template <int NORM, bool CL>
+// TM: rho of the thread's nodes lives in tensor memory (16 columns per warp,
+// 128 per CTA) instead of being re-read from L2 every step (shared memory is
+// full with the band)
+template <int NORM, bool CL, bool TM = false>
 __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, const int C, const int rank,
                                            unsigned char* smraw)
 {
@@ -1325,6 +1330,19 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
     const float mu = P.mu, tau = P.tau;
     const float cm = P.mu * P.ih, ct = P.tau * P.ih;  // mu / h, tau / h
     const int t = threadIdx.x, T = blockDim.x, lane = t & 31;
+    // tensor memory: warp w uses lanes 32 (w % 4) .. + 31 and columns 16 (w / 4) .. + 15
+    uint32_t tb = 0;
+    if (TM) {
+        if (t < 32) {
+            tmem_alloc(smem_u32(slots + 58), RESW_TMEM_COLS);
+            tmem_relinquish();
+        }
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+        tb = *reinterpret_cast<volatile uint32_t*>(slots + 58) + ((32u * ((t >> 5) & 3)) << 16) +
+             16u * (uint32_t)(t >> 7);
+    }
     // run r of this thread: nodes 4 q .. 4 q + 3 of the band, q = t + r T;
     // pk = (row << 16) | column of its first node, or -1 past the band
     int pk[RESW_RUNS];
@@ -1346,8 +1364,10 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             *reinterpret_cast<float4*>(ph + id) = xp;
             *reinterpret_cast<float4*>(s1 + id) = x1;
             *reinterpret_cast<float4*>(s2 + id) = x2;
+            if (TM) tmem_st4(tb + 4u * r, __ldg(reinterpret_cast<const float4*>(rho + id)));
         }
     }
+    if (TM) tmem_wait_st();
     if (CL && t == 0) {
         mbar_init(bar_phi, 1);
         mbar_init(bar_m2, 1);
@@ -1477,7 +1497,7 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             divergence(r, Dn, std::true_type{});
             const int id = (pk[r] >> 16) * nx + (pk[r] & 0xffff);
             const float4 p4 = *reinterpret_cast<const float4*>(ph + id);
-            const float4 r4 = __ldg(reinterpret_cast<const float4*>(rho + id));
+            const float4 r4 = TM ? tmem_ld4(tb + 4u * r) : __ldg(reinterpret_cast<const float4*>(rho + id));
             const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, rv[4] = {r4.x, r4.y, r4.z, r4.w};
             float pn[4];
 #pragma unroll
@@ -1549,6 +1569,12 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
         *reinterpret_cast<float4*>(a.m2 + off + id) = *reinterpret_cast<const float4*>(s2 + id);
         *reinterpret_cast<float4*>(a.phi + off + id) = *reinterpret_cast<const float4*>(ph + id);
     }
+    if (TM) {  // every tensor-memory load has completed (each waited for its own)
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+        if (t < 32) tmem_dealloc(*reinterpret_cast<volatile uint32_t*>(slots + 58), RESW_TMEM_COLS);
+    }
     if (rank == 0 && t == 0) {
         const double R = slots[48];
         const int d = (int)slots[49], conv = d & 1, late = (d >> 1) & 1;
@@ -1574,7 +1600,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident_wide(ResArgs a)
         rank = (int)cl.block_rank();
     }
     extern __shared__ __align__(16) unsigned char smraw[];
-    wide_level<NORM, CL>(a, blockIdx.x / C, C, rank, smraw);
+    wide_level<NORM, CL, true>(a, blockIdx.x / C, C, rank, smraw);
 }
 
 // ---------------------------------------------------------------------------
