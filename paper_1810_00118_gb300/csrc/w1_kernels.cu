@@ -727,8 +727,8 @@ static constexpr int RESW_MAX_NODES = RES_THREADS * 4 * RESW_RUNS;  // 16384
 static constexpr unsigned long long RES_HALO_WAIT_NS = 200000000ull;
 // wide bands in a cluster keep two halo rows of nx floats beside the band
 static constexpr int RESW_MAX_HALO_X = 4096;
-// tensor-memory columns of the wide level kernel (rho of 16 nodes per thread, 32 warps)
-static constexpr uint32_t RESW_TMEM_COLS = 128;
+// tensor-memory columns of the wide level kernel (rho and D of 16 nodes per thread, 32 warps)
+static constexpr uint32_t RESW_TMEM_COLS = 256;
 
 int resident_max_nodes() { return RES_MAX_NODES; }
 
@@ -1299,9 +1299,9 @@ static size_t resident_wide_smem(int band)
     return RES_RED_BYTES + RES_SLOT_BYTES + (size_t)band * 3 * sizeof(float) + 2 * RESW_MAX_HALO_X * sizeof(float);
 }
 
-// TM: rho of the thread's nodes lives in tensor memory (16 columns per warp,
-// 128 per CTA) instead of being re-read from L2 every step (shared memory is
-// full with the band)
+// TM: rho and D = h div m^k of the thread's nodes live in tensor memory (32
+// columns per warp, 256 per CTA): rho is not re-read from L2 every step
+// (shared memory is full with the band) and D leaves the registers
 template <int NORM, bool CL, bool TM = false>
 __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, const int C, const int rank,
                                            unsigned char* smraw)
@@ -1341,12 +1341,14 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
         __syncthreads();
         tmem_fence_after();
         tb = *reinterpret_cast<volatile uint32_t*>(slots + 58) + ((32u * ((t >> 5) & 3)) << 16) +
-             16u * (uint32_t)(t >> 7);
+             32u * (uint32_t)(t >> 7);
     }
     // run r of this thread: nodes 4 q .. 4 q + 3 of the band, q = t + r T;
     // pk = (row << 16) | column of its first node, or -1 past the band
     int pk[RESW_RUNS];
-    float Dv[RESW_RUNS][4];  // h div m^k (rho is re-read from L1/L2 every step: registers are scarce)
+    // h div m^k in registers unless it lives in tensor memory (then rho is there
+    // too; otherwise rho is re-read from L1/L2 every step: registers are scarce)
+    float Dv[TM ? 1 : RESW_RUNS][4];
     const float* __restrict__ rho = a.rho + off;
 #pragma unroll
     for (int r = 0; r < RESW_RUNS; ++r) {
@@ -1420,7 +1422,16 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
     };
 #pragma unroll
     for (int r = 0; r < RESW_RUNS; ++r)
-        if (pk[r] >= 0) divergence(r, Dv[r], std::false_type{});
+        if (pk[r] >= 0) {
+            if constexpr (TM) {
+                float d0[4];
+                divergence(r, d0, std::false_type{});
+                tmem_st4(tb + 16u + 4u * r, make_float4(d0[0], d0[1], d0[2], d0[3]));
+            } else {
+                divergence(r, Dv[r], std::false_type{});
+            }
+        }
+    if (TM) tmem_wait_st();
     // the start time, R^k and the decision live in CTA 0's slots (registers are scarce)
     if (rank == 0 && t == 0) {
         reinterpret_cast<unsigned long long*>(slots)[50] = globaltimer();
@@ -1497,24 +1508,34 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             divergence(r, Dn, std::true_type{});
             const int id = (pk[r] >> 16) * nx + (pk[r] & 0xffff);
             const float4 p4 = *reinterpret_cast<const float4*>(ph + id);
-            const float4 r4 = TM ? tmem_ld4(tb + 4u * r) : __ldg(reinterpret_cast<const float4*>(rho + id));
+            float4 r4, d4;
+            if constexpr (TM) {
+                r4 = tmem_ld4(tb + 4u * r);
+                d4 = tmem_ld4(tb + 16u + 4u * r);
+            } else {
+                r4 = __ldg(reinterpret_cast<const float4*>(rho + id));
+                d4 = make_float4(Dv[r][0], Dv[r][1], Dv[r][2], Dv[r][3]);
+            }
             const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, rv[4] = {r4.x, r4.y, r4.z, r4.w};
+            const float Do[4] = {d4.x, d4.y, d4.z, d4.w};
             float pn[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                pn[c] = fmaf(ct, fmaf(2.f, Dn[c], -Dv[r][c]), fmaf(-tau, rv[c], pv[c]));
+                pn[c] = fmaf(ct, fmaf(2.f, Dn[c], -Do[c]), fmaf(-tau, rv[c], pv[c]));
                 if (check) {
                     const float ep = pn[c] - pv[c];
                     sb = fmaf(ep, ep, sb);
-                    sc = fmaf(ep, Dn[c] - Dv[r][c], sc);  // h <dphi, div dm>, scaled below
+                    sc = fmaf(ep, Dn[c] - Do[c], sc);  // h <dphi, div dm>, scaled below
                 }
-                Dv[r][c] = Dn[c];
+                if constexpr (!TM) Dv[r][c] = Dn[c];
             }
+            if constexpr (TM) tmem_st4(tb + 16u + 4u * r, make_float4(Dn[0], Dn[1], Dn[2], Dn[3]));
             *reinterpret_cast<float4*>(ph + id) = make_float4(pn[0], pn[1], pn[2], pn[3]);
             if (has_dn && id < nx && pushes)
                 st_async4(dsmem_map(smem_u32(hphi + id), rank - 1), make_float4(pn[0], pn[1], pn[2], pn[3]),
                           dsmem_map(bar_phi, rank - 1));
         }
+        if constexpr (TM) tmem_wait_st();  // this step's D is in place before the next reads it
         par ^= 1u;
         __syncthreads();
     };
