@@ -727,8 +727,8 @@ static constexpr int RESW_MAX_NODES = RES_THREADS * 4 * RESW_RUNS;  // 16384
 static constexpr unsigned long long RES_HALO_WAIT_NS = 200000000ull;
 // wide bands in a cluster keep two halo rows of nx floats beside the band
 static constexpr int RESW_MAX_HALO_X = 4096;
-// tensor-memory columns of the wide level kernel (rho and D of 16 nodes per thread, 32 warps)
-static constexpr uint32_t RESW_TMEM_COLS = 256;
+// tensor-memory columns of the wide level kernel (rho, D, phi, m1 of 16 nodes per thread, 32 warps)
+static constexpr uint32_t RESW_TMEM_COLS = 512;
 
 int resident_max_nodes() { return RES_MAX_NODES; }
 
@@ -1299,9 +1299,11 @@ static size_t resident_wide_smem(int band)
     return RES_RED_BYTES + RES_SLOT_BYTES + (size_t)band * 3 * sizeof(float) + 2 * RESW_MAX_HALO_X * sizeof(float);
 }
 
-// TM: rho and D = h div m^k of the thread's nodes live in tensor memory (32
-// columns per warp, 256 per CTA): rho is not re-read from L2 every step
-// (shared memory is full with the band) and D leaves the registers
+// TM: the thread's own rho, D = h div m^k, phi and m1 live in tensor memory
+// (16 columns per run, 64 per warp, all 512 of the SM): rho is not re-read from
+// L2 every step (shared memory is full with the band), D leaves the registers,
+// and shared memory serves only what neighbours read (phi, m2, and the last
+// m1 of each run)
 template <int NORM, bool CL, bool TM = false>
 __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, const int C, const int rank,
                                            unsigned char* smraw)
@@ -1341,7 +1343,7 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
         __syncthreads();
         tmem_fence_after();
         tb = *reinterpret_cast<volatile uint32_t*>(slots + 58) + ((32u * ((t >> 5) & 3)) << 16) +
-             32u * (uint32_t)(t >> 7);
+             64u * (uint32_t)(t >> 7);
     }
     // run r of this thread: nodes 4 q .. 4 q + 3 of the band, q = t + r T;
     // pk = (row << 16) | column of its first node, or -1 past the band
@@ -1366,7 +1368,11 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             *reinterpret_cast<float4*>(ph + id) = xp;
             *reinterpret_cast<float4*>(s1 + id) = x1;
             *reinterpret_cast<float4*>(s2 + id) = x2;
-            if (TM) tmem_st4(tb + 4u * r, __ldg(reinterpret_cast<const float4*>(rho + id)));
+            if (TM) {
+                tmem_st4(tb + 16u * r, __ldg(reinterpret_cast<const float4*>(rho + id)));
+                tmem_st4(tb + 16u * r + 8u, xp);
+                tmem_st4(tb + 16u * r + 12u, x1);
+            }
         }
     }
     if (TM) tmem_wait_st();
@@ -1399,7 +1405,9 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
     // read from the CTA below (initial state) or from the halo row it pushed
     auto divergence = [&](int r, float out[4], auto halo) {
         const int jl = pk[r] >> 16, i0 = pk[r] & 0xffff, id = jl * nx + i0;
-        const float4 m1 = *reinterpret_cast<const float4*>(s1 + id);
+        float4 m1;
+        if constexpr (TM && decltype(halo)::value) m1 = tmem_ld4(tb + 16u * r + 12u);
+        else m1 = *reinterpret_cast<const float4*>(s1 + id);
         const float ln = __shfl_up_sync(FULL, m1.w, 1);
         const float4 m2 = *reinterpret_cast<const float4*>(s2 + id);
         const float l = i0 == 0 ? 0.f : (lane == 0 ? s1[id - 1] : ln);
@@ -1426,7 +1434,7 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             if constexpr (TM) {
                 float d0[4];
                 divergence(r, d0, std::false_type{});
-                tmem_st4(tb + 16u + 4u * r, make_float4(d0[0], d0[1], d0[2], d0[3]));
+                tmem_st4(tb + 16u * r + 4u, make_float4(d0[0], d0[1], d0[2], d0[3]));
             } else {
                 divergence(r, Dv[r], std::false_type{});
             }
@@ -1464,11 +1472,11 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
         for (int r = 0; r < RESW_RUNS; ++r) {
             if (pk[r] < 0) continue;
             const int jl = pk[r] >> 16, i0 = pk[r] & 0xffff, id = jl * nx + i0;
-            const float4 p4 = *reinterpret_cast<const float4*>(ph + id);
+            const float4 p4 = TM ? tmem_ld4(tb + 16u * r + 8u) : *reinterpret_cast<const float4*>(ph + id);
             const float rn = __shfl_down_sync(FULL, p4.x, 1);
             const int j = jb + jl;
             const bool last_col = i0 + 4 == nx;
-            const float4 a1 = *reinterpret_cast<const float4*>(s1 + id);
+            const float4 a1 = TM ? tmem_ld4(tb + 16u * r + 12u) : *reinterpret_cast<const float4*>(s1 + id);
             const float4 a2 = *reinterpret_cast<const float4*>(s2 + id);
             float4 u = p4;
             if (j < ny - 1) {
@@ -1493,12 +1501,18 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
                     sa = fmaf(d1, d1, fmaf(d2, d2, sa));
                 }
             }
-            *reinterpret_cast<float4*>(s1 + id) = make_float4(n1[0], n1[1], n1[2], n1[3]);
+            if constexpr (TM) {  // neighbours read only the run's last m1 (left of the next run)
+                tmem_st4(tb + 16u * r + 12u, make_float4(n1[0], n1[1], n1[2], n1[3]));
+                s1[id + 3] = n1[3];
+            } else {
+                *reinterpret_cast<float4*>(s1 + id) = make_float4(n1[0], n1[1], n1[2], n1[3]);
+            }
             *reinterpret_cast<float4*>(s2 + id) = make_float4(n2[0], n2[1], n2[2], n2[3]);
             if (has_up && jl == rows - 1 && pushes)
                 st_async4(dsmem_map(smem_u32(hm2 + i0), rank + 1), make_float4(n2[0], n2[1], n2[2], n2[3]),
                           dsmem_map(bar_m2, rank + 1));
         }
+        if constexpr (TM) tmem_wait_st();  // m1' is in place before phase B reads it
         __syncthreads();
         // ---- phase B: phi' = phi + tau (div(2m' - m) - rho)
 #pragma unroll
@@ -1507,11 +1521,11 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             float Dn[4];
             divergence(r, Dn, std::true_type{});
             const int id = (pk[r] >> 16) * nx + (pk[r] & 0xffff);
-            const float4 p4 = *reinterpret_cast<const float4*>(ph + id);
+            const float4 p4 = TM ? tmem_ld4(tb + 16u * r + 8u) : *reinterpret_cast<const float4*>(ph + id);
             float4 r4, d4;
             if constexpr (TM) {
-                r4 = tmem_ld4(tb + 4u * r);
-                d4 = tmem_ld4(tb + 16u + 4u * r);
+                r4 = tmem_ld4(tb + 16u * r);
+                d4 = tmem_ld4(tb + 16u * r + 4u);
             } else {
                 r4 = __ldg(reinterpret_cast<const float4*>(rho + id));
                 d4 = make_float4(Dv[r][0], Dv[r][1], Dv[r][2], Dv[r][3]);
@@ -1529,13 +1543,16 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
                 }
                 if constexpr (!TM) Dv[r][c] = Dn[c];
             }
-            if constexpr (TM) tmem_st4(tb + 16u + 4u * r, make_float4(Dn[0], Dn[1], Dn[2], Dn[3]));
+            if constexpr (TM) {
+                tmem_st4(tb + 16u * r + 4u, make_float4(Dn[0], Dn[1], Dn[2], Dn[3]));
+                tmem_st4(tb + 16u * r + 8u, make_float4(pn[0], pn[1], pn[2], pn[3]));
+            }
             *reinterpret_cast<float4*>(ph + id) = make_float4(pn[0], pn[1], pn[2], pn[3]);
             if (has_dn && id < nx && pushes)
                 st_async4(dsmem_map(smem_u32(hphi + id), rank - 1), make_float4(pn[0], pn[1], pn[2], pn[3]),
                           dsmem_map(bar_phi, rank - 1));
         }
-        if constexpr (TM) tmem_wait_st();  // this step's D is in place before the next reads it
+        if constexpr (TM) tmem_wait_st();  // this step's D and phi are in place before the next reads them
         par ^= 1u;
         __syncthreads();
     };
@@ -1586,7 +1603,8 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
     for (int r = 0; r < RESW_RUNS; ++r) {
         if (pk[r] < 0) continue;
         const int id = (pk[r] >> 16) * nx + (pk[r] & 0xffff);
-        *reinterpret_cast<float4*>(a.m1 + off + id) = *reinterpret_cast<const float4*>(s1 + id);
+        *reinterpret_cast<float4*>(a.m1 + off + id) =
+            TM ? tmem_ld4(tb + 16u * r + 12u) : *reinterpret_cast<const float4*>(s1 + id);
         *reinterpret_cast<float4*>(a.m2 + off + id) = *reinterpret_cast<const float4*>(s2 + id);
         *reinterpret_cast<float4*>(a.phi + off + id) = *reinterpret_cast<const float4*>(ph + id);
     }
