@@ -1666,7 +1666,7 @@ __device__ __noinline__ void cascade_level_small(const ResArgs& a, int pair, uns
 template <int NORM>
 __device__ __noinline__ void cascade_level_wide(const ResArgs& a, int pair, unsigned char* smraw)
 {
-    wide_level<NORM, false>(a, pair, 1, 0, smraw);
+    wide_level<NORM, false, true>(a, pair, 1, 0, smraw);
 }
 
 template <int NORM, bool WIDE>
