@@ -12,8 +12,8 @@
 // the host reads it to decide the level's stop, as in the eager mode of the 2-D
 // plans.  Restriction (2x2x2 means), the voxel-centre Interpolate, prep and the
 // certificates (f(m), the dual bound, the octree route bound) are kernels too.
-// This path is one step per launch over global memory (no temporal blocking or
-// on-chip levels): 3-D grids are outside the measured workloads.
+// Levels of at most 4096 voxels per CTA (one CTA, or a cluster of z-slabs) run
+// all their steps and stop tests in one launch on chip instead (k3_resident).
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -711,8 +711,14 @@ cudaError_t launch_decide(const Ctl* ctl, int pairs, cudaGraphConditionalHandle 
 //   phase B: Dn = div m' (left, below; the row below the band from the previous
 //            CTA), div mbar = 2 Dn - D, phi' = phi + tau (div mbar - rho),
 //            D <- Dn, publish phi'
-// With C > 1 the phases are separated by cluster barriers (release/acquire),
-// which also order the distributed-shared-memory reads of the halo rows.
+// With C > 1 (this node-per-thread fallback) the phases are separated by
+// cluster barriers (release/acquire), which also order the distributed-shared-
+// memory reads of the halo rows.  The four-nodes-per-thread and wide-band
+// kernels below replace those barriers by neighbour pushes: after m' a CTA
+// sends its top row's m2' to the CTA above, after phi' its bottom row's phi to
+// the CTA below (st.async into the neighbour's halo row, completing a
+// transaction count on its mbarrier); only the boundary rows wait, with a
+// bounded wait, and the CTA itself synchronises with __syncthreads.
 // Stop tests: each CTA's FP64 partials go to CTA 0, which decides; every CTA
 // reads the decision, so all leave the loop after the same step.
 
@@ -1288,10 +1294,13 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident4(ResArgs a)
 
 // Wide-band variant for levels of up to 16 x 16384 nodes (512 x 512 in one
 // 16-CTA cluster): a thread owns four runs of four nodes.  Shared memory holds
-// only phi, m1 and m2 of the band (12 B per node, 192 KB at 16384 nodes), own
-// values are re-read from it, and rho and D = div m^k stay in registers.  The
-// test step's cross term <dphi, div dm> uses div dm = div m' - div m^k, both
-// already formed in FP32 (no shared-memory copy of dm is needed).
+// phi, m1 and m2 of the band (12 B per node, 192 KB at 16384 nodes) and two
+// halo rows for the neighbours; each thread's own rho, D = h div m^k, phi and
+// m1 live in tensor memory (wide_level with TM; without it, own values are
+// re-read from shared memory, rho from L1/L2, and D stays in registers).  The
+// test step's cross term
+// <dphi, div dm> uses div dm = div m' - div m^k, both already formed in FP32
+// (no shared-memory copy of dm is needed).
 
 static size_t resident_wide_smem(int band)
 {
