@@ -435,7 +435,9 @@ const char* w1_noalloc_last_error(void);
  * for 2-D grids; taken unchanged for 3-D); options as for the 2-D solver
  * (check_every 0 = 32; path 0 runs a level on chip (all its steps and stop
  * tests in one launch of one CTA or a cluster of up to 16, each holding at most
- * 4096 voxels, nx % 4 == 0) where it fits and otherwise with two launches per
+ * 4096 voxels in registers or, as wide slabs with each thread's own state in
+ * tensor memory, 16384 voxels (a multiple of 128; in a cluster nx ny <= 4096);
+ * nx % 4 == 0) where it fits and otherwise with two launches per
  * step and the host testing R^k every K steps; path 1 requires the on-chip
  * kernel (W1_ERR_UNSUPPORTED where a level does not fit); paths 2 and 3 use the
  * two-launch step on every level; time_budget_s applies per level; tune,
@@ -458,8 +460,9 @@ w1_status w1_cp_steps3d(int nx, int ny, int nz, double h, int norm, float mu, fl
                         double* fpr_last);
 /* The same with a choice of kernel: path 2 = two launches per step; path 1 =
  * every step in one launch on chip (nx % 4 == 0, a cluster of `cluster` CTAs
- * (0: the fewest that fit) each holding nz / cluster planes of at most 4096
- * voxels; W1_ERR_UNSUPPORTED when the level does not fit). */
+ * (0: the library's choice) each holding nz / cluster planes: at most 4096
+ * voxels, or 16384 as a wide slab (see w1_solve3d); W1_ERR_UNSUPPORTED when
+ * the level does not fit); path 1 needs 16-byte aligned planes. */
 w1_status w1_cp_steps3d_ex(int nx, int ny, int nz, double h, int norm, float mu, float tau, const float* rho,
                            float* m1, float* m2, float* m3, float* phi, long long iters, int path, int cluster,
                            void* stream, double* fpr_last);

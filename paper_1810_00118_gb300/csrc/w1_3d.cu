@@ -392,11 +392,17 @@ static size_t r3_smem(int nb, int plane)
     return R3_RED_BYTES + R3_SLOT_BYTES + (size_t)nb * 4 * sizeof(float) + (size_t)2 * plane * sizeof(float);
 }
 
+static bool r3_fits(int nx, int ny, int nz, int C);
+
+// The fewest CTAs with at most 4096 voxels each; else the most CTAs (the
+// fastest step) with wide slabs of up to 16384.
 static int r3_cluster_for(int nx, int ny, int nz)
 {
     if (nx % 4 != 0) return 0;
     for (int c = 1; c <= 16; c *= 2)
         if (nz % c == 0 && (long long)(nz / c) * nx * ny <= R3_MAX_NODES) return c;
+    for (int c = 16; c >= 1; c /= 2)
+        if (r3_fits(nx, ny, nz, c)) return c;
     return 0;
 }
 
@@ -651,6 +657,331 @@ __global__ void __launch_bounds__(R3_THREADS, 1) k3_resident(R3Args a)
     if (CL) cg::this_cluster().sync();
 }
 
+
+// Wide slabs (the 3-D counterpart of the 2-D wide bands): up to 16384 voxels
+// per CTA, a thread owning four runs of four voxels (run r at voxel 4 (t + r T)
+// of the slab).  Shared memory holds what neighbours read: phi, m2 and m3 of
+// the slab, the last m1 of each warp's 128 voxels (the left neighbour of the
+// next warp's lane 0), and two halo planes.  Each thread's own rho, D, phi and
+// m1 live in tensor memory: 16 columns per run, 64 per warp in the warp's lane
+// quarter, all 512 columns of the SM (allocated by warp 0, freed before exit).
+static constexpr int R3W_RUNS = 4;
+static constexpr int R3W_MAX_NODES = 4 * R3W_RUNS * R3_THREADS;  // 16384
+static constexpr int R3W_MAX_PLANE = 4096;                       // halo planes of a cluster slab
+static constexpr uint32_t R3W_TMEM_COLS = 512;
+
+// floats of the per-warp m1 array, padded to 16 bytes so that the halo planes
+// after it stay aligned for 16-byte accesses
+__host__ __device__ constexpr int r3w_s1b_floats(int nb) { return ((nb / 128) + 3) & ~3; }
+
+static size_t r3w_smem(int nb, int plane, bool cl)
+{
+    return R3_RED_BYTES + R3_SLOT_BYTES + (size_t)nb * 3 * sizeof(float) + (size_t)r3w_s1b_floats(nb) * sizeof(float) +
+           (cl ? (size_t)2 * plane * sizeof(float) : 0);
+}
+
+template <int NORM, bool CL>
+__global__ void __launch_bounds__(R3_THREADS, 1) k3_wide(R3Args a)
+{
+    int C = 1, rank = 0;
+    if (CL) {
+        cg::cluster_group cl = cg::this_cluster();
+        C = (int)cl.num_blocks();
+        rank = (int)cl.block_rank();
+    }
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nx = a.d.nx, ny = a.d.ny, nz = a.d.nz;
+    const int plane = nx * ny, P = nz / C, kb = rank * P, nb = P * plane;
+    double* red = reinterpret_cast<double*>(smraw);
+    double* slots = reinterpret_cast<double*>(smraw + R3_RED_BYTES);
+    float* ph = reinterpret_cast<float*>(smraw + R3_RED_BYTES + R3_SLOT_BYTES);
+    float* s2 = ph + nb;
+    float* s3 = s2 + nb;
+    float* s1b = s3 + nb;        // m1 of the last voxel of each warp's 128
+    float* hphi = s1b + r3w_s1b_floats(nb);  // phi of the plane above the slab (from CTA rank + 1)
+    float* hm3 = hphi + plane;   // m3' of the plane below the slab (from CTA rank - 1)
+    const uint32_t bar_phi = smem_u32(slots + 56), bar_m3 = smem_u32(slots + 57);
+    const size_t off = (size_t)kb * plane;
+    const float mu = a.mu, tau = a.tau, cm = a.cm, ct = a.ct;
+    const int t = threadIdx.x, T = blockDim.x, lane = t & 31;
+    const bool has_up = CL && rank + 1 < C, has_dn = CL && rank > 0;
+
+    // tensor memory
+    if (t < 32) {
+        tmem_alloc(smem_u32(slots + 58), R3W_TMEM_COLS);
+        tmem_relinquish();
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const uint32_t tb = *reinterpret_cast<volatile uint32_t*>(slots + 58) + ((32u * ((t >> 5) & 3)) << 16) +
+                        64u * (uint32_t)(t >> 7);
+    // run r: rho at 16 r, D at 16 r + 4, phi at 16 r + 8, m1 at 16 r + 12
+
+    // pk = (kl << 24) | (jl << 12) | (i0 >> 2) of the run's first voxel, or -1
+    int pk[R3W_RUNS];
+#pragma unroll
+    for (int r = 0; r < R3W_RUNS; ++r) {
+        const int id = 4 * (t + r * T);
+        pk[r] = -1;
+        if (id < nb) {
+            const int kl = id / plane, rem = id - kl * plane, jl = rem / nx, i0 = rem - jl * nx;
+            pk[r] = (kl << 24) | (jl << 12) | (i0 >> 2);
+            float4 x1 = *reinterpret_cast<const float4*>(a.m1 + off + id);
+            float4 x2 = *reinterpret_cast<const float4*>(a.m2 + off + id);
+            float4 x3 = *reinterpret_cast<const float4*>(a.m3 + off + id);
+            const float4 xp = *reinterpret_cast<const float4*>(a.phi + off + id);
+            if (i0 + 4 == nx) x1.w = 0.f;
+            if (jl == ny - 1) x2 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (kb + kl == nz - 1) x3 = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4*>(ph + id) = xp;
+            *reinterpret_cast<float4*>(s2 + id) = x2;
+            *reinterpret_cast<float4*>(s3 + id) = x3;
+            if (lane == 31) s1b[id >> 7] = x1.w;
+            tmem_st4(tb + 16u * r, __ldg(reinterpret_cast<const float4*>(a.rho + off + id)));
+            tmem_st4(tb + 16u * r + 8u, xp);
+            tmem_st4(tb + 16u * r + 12u, x1);
+        }
+    }
+    tmem_wait_st();
+    if (CL && t == 0) {
+        mbar_init(bar_phi, 1);
+        mbar_init(bar_m3, 1);
+        if (has_up) mbar_expect(bar_phi, 4u * plane);
+        if (has_dn) mbar_expect(bar_m3, 4u * plane);
+        mbar_init_fence();
+    }
+    if (CL) cg::this_cluster().sync();
+    else __syncthreads();
+    uint32_t slots0 = smem_u32(slots);
+    if (CL) slots0 = dsmem_map(smem_u32(slots), 0);
+    unsigned par = 0;
+    bool sync_fail = false;
+    auto halo_wait = [&](uint32_t bar) {
+        if (!sync_fail && !mbar_wait(bar, par, R3_HALO_WAIT_NS)) {
+            sync_fail = true;
+            dsmem_st_f64(slots0 + 8u * 51, 1.0);
+        }
+    };
+    const int id_top = (P - 1) * plane;  // first voxel of the top plane: its owner re-arms bar_phi
+    // h div m of run r (left: previous lane, or the previous warp's last m1;
+    // below in y: the slab; below in z: the slab, the CTA below's top plane
+    // (initial state) or the halo plane it pushed)
+    auto divergence = [&](int r, const float4& m1, float out[4], auto halo) {
+        const int kl = pk[r] >> 24, jl = (pk[r] >> 12) & 0xfff, i0 = (pk[r] & 0xfff) << 2;
+        const int rem = jl * nx + i0, id = kl * plane + rem;
+        const float ln = __shfl_up_sync(FULL, m1.w, 1);
+        const float l = i0 == 0 ? 0.f : (lane == 0 ? s1b[(id >> 7) - 1] : ln);
+        const float4 m2 = *reinterpret_cast<const float4*>(s2 + id);
+        const float4 m3 = *reinterpret_cast<const float4*>(s3 + id);
+        const float4 b2 = jl > 0 ? *reinterpret_cast<const float4*>(s2 + id - nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 b3 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kl > 0) {
+            b3 = *reinterpret_cast<const float4*>(s3 + id - plane);
+        } else if (has_dn) {
+            if constexpr (decltype(halo)::value) {
+                halo_wait(bar_m3);
+                b3 = *reinterpret_cast<const float4*>(hm3 + rem);
+                if (t == 0 && r == 0 && !sync_fail) mbar_expect(bar_m3, 4u * plane);
+            } else {
+                b3 = dsmem_ld4(dsmem_map(smem_u32(s3 + (P - 1) * plane + rem), rank - 1));
+            }
+        }
+        out[0] = (m1.x - l) + (m2.x - b2.x) + (m3.x - b3.x);
+        out[1] = (m1.y - m1.x) + (m2.y - b2.y) + (m3.y - b3.y);
+        out[2] = (m1.z - m1.y) + (m2.z - b2.z) + (m3.z - b3.z);
+        out[3] = (m1.w - m1.z) + (m2.w - b2.w) + (m3.w - b3.w);
+    };
+#pragma unroll
+    for (int r = 0; r < R3W_RUNS; ++r)
+        if (pk[r] >= 0) {
+            float d0[4];
+            divergence(r, tmem_ld4(tb + 16u * r + 12u), d0, std::false_type{});
+            tmem_st4(tb + 16u * r + 4u, make_float4(d0[0], d0[1], d0[2], d0[3]));
+        }
+    tmem_wait_st();
+    if (rank == 0 && t == 0) {
+        reinterpret_cast<unsigned long long*>(slots)[50] = globaltimer();
+        slots[48] = 0.0;
+        slots[49] = 0.0;
+        slots[51] = 0.0;
+    }
+    if (CL) cg::this_cluster().sync();
+    else __syncthreads();
+    // the initial phi of the bottom plane goes to the CTA below
+    if (has_dn) {
+#pragma unroll
+        for (int r = 0; r < R3W_RUNS; ++r)
+            if (pk[r] >= 0 && (pk[r] >> 24) == 0) {
+                const int rem = ((pk[r] >> 12) & 0xfff) * nx + ((pk[r] & 0xfff) << 2);
+                st_async4(dsmem_map(smem_u32(hphi + rem), rank - 1), *reinterpret_cast<const float4*>(ph + rem),
+                          dsmem_map(bar_phi, rank - 1));
+            }
+    }
+    float sa = 0.f, sb = 0.f, sc = 0.f;
+    auto wstep = [&](auto test) {
+        constexpr bool check = decltype(test)::value;
+        // ---- phase A: m' = prox(m + mu grad phi)
+#pragma unroll
+        for (int r = 0; r < R3W_RUNS; ++r) {
+            if (pk[r] < 0) continue;
+            const int kl = pk[r] >> 24, jl = (pk[r] >> 12) & 0xfff, i0 = (pk[r] & 0xfff) << 2;
+            const int rem = jl * nx + i0, id = kl * plane + rem;
+            const bool last_col = i0 + 4 == nx, top_row = jl == ny - 1, top_plane = kb + kl == nz - 1;
+            const float4 p4 = tmem_ld4(tb + 16u * r + 8u);
+            const float rn = __shfl_down_sync(FULL, p4.x, 1);
+            const float4 a1 = tmem_ld4(tb + 16u * r + 12u);
+            const float4 a2 = *reinterpret_cast<const float4*>(s2 + id);
+            const float4 a3 = *reinterpret_cast<const float4*>(s3 + id);
+            float4 uy = p4, uz = p4;
+            if (!top_row) uy = *reinterpret_cast<const float4*>(ph + id + nx);
+            if (!top_plane) {
+                if (!CL || kl < P - 1) {
+                    uz = *reinterpret_cast<const float4*>(ph + id + plane);
+                } else {
+                    halo_wait(bar_phi);
+                    uz = *reinterpret_cast<const float4*>(hphi + rem);
+                    if (id == id_top && !sync_fail) mbar_expect(bar_phi, 4u * plane);
+                }
+            }
+            const float right = last_col ? p4.w : (lane == 31 ? ph[id + 4] : rn);
+            const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, py[4] = {uy.x, uy.y, uy.z, uy.w},
+                        pz[4] = {uz.x, uz.y, uz.z, uz.w};
+            const float m1[4] = {a1.x, a1.y, a1.z, a1.w}, m2[4] = {a2.x, a2.y, a2.z, a2.w},
+                        m3[4] = {a3.x, a3.y, a3.z, a3.w};
+            float n1[4], n2[4], n3[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float pr = c < 3 ? pv[c + 1] : right;
+                const float v[3] = {fmaf(cm, pr - pv[c], m1[c]), fmaf(cm, py[c] - pv[c], m2[c]),
+                                    fmaf(cm, pz[c] - pv[c], m3[c])};
+                float o[3];
+                prox3<NORM>(v, mu, o);
+                n1[c] = o[0];
+                n2[c] = o[1];
+                n3[c] = o[2];
+            }
+            if (last_col) n1[3] = 0.f;
+            if (top_row) n2[0] = n2[1] = n2[2] = n2[3] = 0.f;
+            if (top_plane) n3[0] = n3[1] = n3[2] = n3[3] = 0.f;
+            if constexpr (check) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float d1 = n1[c] - m1[c], d2 = n2[c] - m2[c], d3 = n3[c] - m3[c];
+                    sa = fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, sa)));
+                }
+            }
+            tmem_st4(tb + 16u * r + 12u, make_float4(n1[0], n1[1], n1[2], n1[3]));
+            if (lane == 31) s1b[id >> 7] = n1[3];
+            *reinterpret_cast<float4*>(s2 + id) = make_float4(n2[0], n2[1], n2[2], n2[3]);
+            *reinterpret_cast<float4*>(s3 + id) = make_float4(n3[0], n3[1], n3[2], n3[3]);
+            if (has_up && kl == P - 1)
+                st_async4(dsmem_map(smem_u32(hm3 + rem), rank + 1), make_float4(n3[0], n3[1], n3[2], n3[3]),
+                          dsmem_map(bar_m3, rank + 1));
+        }
+        tmem_wait_st();
+        __syncthreads();
+        // ---- phase B: phi' = phi + tau (div(2m' - m) - rho)
+#pragma unroll
+        for (int r = 0; r < R3W_RUNS; ++r) {
+            if (pk[r] < 0) continue;
+            float Dn[4];
+            divergence(r, tmem_ld4(tb + 16u * r + 12u), Dn, std::true_type{});
+            const int kl = pk[r] >> 24, rem = ((pk[r] >> 12) & 0xfff) * nx + ((pk[r] & 0xfff) << 2);
+            const int id = kl * plane + rem;
+            const float4 r4 = tmem_ld4(tb + 16u * r), d4 = tmem_ld4(tb + 16u * r + 4u),
+                         p4 = tmem_ld4(tb + 16u * r + 8u);
+            const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, rv[4] = {r4.x, r4.y, r4.z, r4.w},
+                        Do[4] = {d4.x, d4.y, d4.z, d4.w};
+            float pn[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                pn[c] = fmaf(ct, fmaf(2.f, Dn[c], -Do[c]), fmaf(-tau, rv[c], pv[c]));
+                if constexpr (check) {
+                    const float ep = pn[c] - pv[c];
+                    sb = fmaf(ep, ep, sb);
+                    sc = fmaf(ep, Dn[c] - Do[c], sc);
+                }
+            }
+            tmem_st4(tb + 16u * r + 4u, make_float4(Dn[0], Dn[1], Dn[2], Dn[3]));
+            tmem_st4(tb + 16u * r + 8u, make_float4(pn[0], pn[1], pn[2], pn[3]));
+            *reinterpret_cast<float4*>(ph + id) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+            if (has_dn && kl == 0)
+                st_async4(dsmem_map(smem_u32(hphi + rem), rank - 1), make_float4(pn[0], pn[1], pn[2], pn[3]),
+                          dsmem_map(bar_phi, rank - 1));
+        }
+        tmem_wait_st();
+        par ^= 1u;
+        __syncthreads();
+    };
+    long long it = 0;
+    const long long cap = a.cap;
+    while (it < cap) {
+        const bool check = a.fixed ? (it + 1 == cap) : ((it + 1) % a.K == 0);
+        if (!check) {
+            wstep(std::false_type{});
+            ++it;
+            continue;
+        }
+        sa = sb = sc = 0.f;
+        wstep(std::true_type{});
+        ++it;
+        double v[3] = {(double)sa, (double)sb, (double)sc / a.h};
+        block_sum<3>(v, red);
+        if (t == 0) {
+            dsmem_st_f64(slots0 + 8u * (rank * 3 + 0), v[0]);
+            dsmem_st_f64(slots0 + 8u * (rank * 3 + 1), v[1]);
+            dsmem_st_f64(slots0 + 8u * (rank * 3 + 2), v[2]);
+        }
+        if (CL) cg::this_cluster().sync();
+        else __syncthreads();
+        if (rank == 0 && t == 0) {
+            double tt[3] = {0.0, 0.0, 0.0};
+            for (int q = 0; q < C; ++q)
+                for (int c = 0; c < 3; ++c) tt[c] += slots[q * 3 + c];
+            const double h3 = a.h * a.h * a.h;
+            const double Rk = (tt[0] / (double)mu + tt[1] / (double)tau - 2.0 * tt[2]) * h3;
+            const int cv = Rk < a.tol && slots[51] == 0.0;
+            const int lt = (globaltimer() - reinterpret_cast<const unsigned long long*>(slots)[50]) > a.budget_ns ||
+                           slots[51] != 0.0;
+            const int stop = a.fixed || cv || lt || it >= cap;
+            slots[48] = Rk;
+            slots[49] = (double)(cv | (lt << 1) | (stop << 2));
+        }
+        if (CL) cg::this_cluster().sync();
+        else __syncthreads();
+        if ((int)dsmem_ld_f64(slots0 + 8u * 49) & 4) break;
+    }
+    // the phi pushed by the CTA above after the last step has not been read
+    if (has_up) {
+        bool top_run = false;
+#pragma unroll
+        for (int r = 0; r < R3W_RUNS; ++r) top_run |= pk[r] >= 0 && (pk[r] >> 24) == P - 1;
+        if (top_run) halo_wait(bar_phi);
+    }
+#pragma unroll
+    for (int r = 0; r < R3W_RUNS; ++r) {
+        if (pk[r] < 0) continue;
+        const int id = (pk[r] >> 24) * plane + ((pk[r] >> 12) & 0xfff) * nx + ((pk[r] & 0xfff) << 2);
+        *reinterpret_cast<float4*>(a.m1 + off + id) = tmem_ld4(tb + 16u * r + 12u);
+        *reinterpret_cast<float4*>(a.m2 + off + id) = *reinterpret_cast<const float4*>(s2 + id);
+        *reinterpret_cast<float4*>(a.m3 + off + id) = *reinterpret_cast<const float4*>(s3 + id);
+        *reinterpret_cast<float4*>(a.phi + off + id) = *reinterpret_cast<const float4*>(ph + id);
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (t < 32) tmem_dealloc(*reinterpret_cast<volatile uint32_t*>(slots + 58), R3W_TMEM_COLS);
+    if (rank == 0 && t == 0) {
+        const int dcs = (int)slots[49];
+        a.res->iters = it;
+        a.res->fpr = slots[48];
+        a.res->conv = dcs & 1;
+        a.res->timeout = ((dcs >> 1) & 1) && !(dcs & 1);
+    }
+    if (CL) cg::this_cluster().sync();
+}
+
 template <int NORM>
 static cudaError_t r3_attr()
 {
@@ -660,23 +991,50 @@ static cudaError_t r3_attr()
         e = cudaFuncSetAttribute(k3_resident<NORM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k3_resident<NORM, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    const int wsmem = (int)r3w_smem(R3W_MAX_NODES, R3W_MAX_PLANE, true);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k3_wide<NORM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k3_wide<NORM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k3_wide<NORM, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
 }
 
-static const void* r3_fn(int norm, bool cl)
+static const void* r3_fn(int norm, bool cl, bool wide)
 {
+    if (wide) {
+        if (norm == W1_NORM_L1) return cl ? (const void*)k3_wide<W1_NORM_L1, true> : (const void*)k3_wide<W1_NORM_L1, false>;
+        if (norm == W1_NORM_L2) return cl ? (const void*)k3_wide<W1_NORM_L2, true> : (const void*)k3_wide<W1_NORM_L2, false>;
+        return cl ? (const void*)k3_wide<W1_NORM_LINF, true> : (const void*)k3_wide<W1_NORM_LINF, false>;
+    }
     if (norm == W1_NORM_L1) return cl ? (const void*)k3_resident<W1_NORM_L1, true> : (const void*)k3_resident<W1_NORM_L1, false>;
     if (norm == W1_NORM_L2) return cl ? (const void*)k3_resident<W1_NORM_L2, true> : (const void*)k3_resident<W1_NORM_L2, false>;
     return cl ? (const void*)k3_resident<W1_NORM_LINF, true> : (const void*)k3_resident<W1_NORM_LINF, false>;
 }
 
+// A slab of nb voxels: the four-voxel layout up to 4096, the wide layout (tensor
+// memory) up to 16384 when nb is a multiple of 128 and, in a cluster, the halo
+// planes fit (plane <= 4096).
+static bool r3_fits(int nx, int ny, int nz, int C)
+{
+    if (C < 1 || C > 16 || (C & (C - 1)) || nx % 4 || nz % C) return false;
+    const long long nb = (long long)(nz / C) * nx * ny;
+    if (nb <= R3_MAX_NODES) return true;
+    return nb <= R3W_MAX_NODES && nb % 128 == 0 && (C == 1 || (long long)nx * ny <= R3W_MAX_PLANE) &&
+           nx <= 4096 && ny <= 4096;
+}
+
+static bool r3_is_wide(const Dims3& d, int C) { return (long long)(d.nz / C) * d.nx * d.ny > R3_MAX_NODES; }
+
 static void r3_config(const Dims3& d, int C, cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr)
 {
     const int nb = (d.nz / C) * d.nx * d.ny;
+    const bool wide = r3_is_wide(d, C);
     cfg = cudaLaunchConfig_t{};
     cfg.gridDim = dim3(C, 1, 1);
-    cfg.blockDim = dim3(((nb / 4 + 31) / 32) * 32, 1, 1);
-    cfg.dynamicSmemBytes = r3_smem(nb, d.nx * d.ny);
+    cfg.blockDim = dim3(wide ? R3_THREADS : ((nb / 4 + 31) / 32) * 32, 1, 1);
+    cfg.dynamicSmemBytes = wide ? r3w_smem(nb, d.nx * d.ny, C > 1) : r3_smem(nb, d.nx * d.ny);
     cfg.numAttrs = 0;
     if (C > 1) {
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -693,8 +1051,7 @@ static void r3_config(const Dims3& d, int C, cudaLaunchConfig_t& cfg, cudaLaunch
 static int r3_choose(int norm, const Dims3& d, int want)
 {
     const int C = want > 0 ? want : r3_cluster_for(d.nx, d.ny, d.nz);
-    if (C < 1 || C > 16 || (C & (C - 1)) || d.nx % 4 || d.nz % C || (long long)(d.nz / C) * d.nx * d.ny > R3_MAX_NODES)
-        return 0;
+    if (!r3_fits(d.nx, d.ny, d.nz, C)) return 0;
     if (r3_attr<W1_NORM_L1>() != cudaSuccess || r3_attr<W1_NORM_L2>() != cudaSuccess ||
         r3_attr<W1_NORM_LINF>() != cudaSuccess)
         return 0;
@@ -703,7 +1060,7 @@ static int r3_choose(int norm, const Dims3& d, int want)
     cudaLaunchAttribute attr[1];
     r3_config(d, C, cfg, attr);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, r3_fn(norm, true), &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, r3_fn(norm, true, r3_is_wide(d, C)), &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -717,7 +1074,7 @@ static cudaError_t r3_launch(int norm, int C, const R3Args& a, cudaStream_t s)
     r3_config(a.d, C, cfg, attr);
     cfg.stream = s;
     void* args[1] = {const_cast<R3Args*>(&a)};
-    return cudaLaunchKernelExC(&cfg, r3_fn(norm, C > 1), args);
+    return cudaLaunchKernelExC(&cfg, r3_fn(norm, C > 1, r3_is_wide(a.d, C)), args);
 }
 
 static dim3 grid3(long long n) { return dim3((unsigned)((n + T3 - 1) / T3)); }
@@ -838,6 +1195,9 @@ extern "C" w1_status w1_cp_steps3d_ex(int nx, int ny, int nz, double h, int norm
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double r = 0.0;
     if (path == 1) {
+        for (const void* q : {(const void*)rho, (const void*)m1, (const void*)m2, (const void*)m3, (const void*)phi})
+            if (reinterpret_cast<uintptr_t>(q) % 16 != 0)
+                return fail3(W1_ERR_INVALID_ARG, "the on-chip kernels need 16-byte aligned planes");
         const int C = r3_choose(norm, d, cluster);
         if (C == 0) return fail3(W1_ERR_UNSUPPORTED, "the level does not fit on chip with that cluster");
         if (iters > 0) {
@@ -919,11 +1279,14 @@ extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, in
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long n = (long long)nx * ny * nz;
     // per level: rho, m1, m2, m3, phi
-    std::vector<long long> off(levels + 1, 0);
-    for (int l = 0; l < levels; ++l) {
+    // per level: rho, m1, m2, m3, phi, each plane padded to 16 bytes so that every
+    // plane of every level is aligned for the kernels' 16-byte accesses
+    auto plane_stride = [&](int l) {
         const int sh = levels - 1 - l;
-        off[l + 1] = off[l] + 5 * ((long long)(nx >> sh) * (ny >> sh) * (nz >> sh));
-    }
+        return (((long long)(nx >> sh) * (ny >> sh) * (nz >> sh)) + 3) & ~3LL;
+    };
+    std::vector<long long> off(levels + 1, 0);
+    for (int l = 0; l < levels; ++l) off[l + 1] = off[l] + 5 * plane_stride(l);
     float* arena = nullptr;
     W1_CK3(cudaMalloc(&arena, off[levels] * sizeof(float)));
     struct Free {
@@ -947,11 +1310,7 @@ extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, in
     W1_CK3(cudaMalloc(&part, prep_part_doubles(1) * sizeof(double)));
     free_c.p = part;
     W1_CK3(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
-    auto lvl = [&](int l, int c) {
-        const int sh = levels - 1 - l;
-        const long long ln = (long long)(nx >> sh) * (ny >> sh) * (nz >> sh);
-        return arena + off[l] + c * ln;
-    };
+    auto lvl = [&](int l, int c) { return arena + off[l] + c * plane_stride(l); };
     // prep (masses with h^3 weights: the prep kernel weights by h_2d^2, so pass h^(3/2))
     W1_CK3(launch_prep(rho0, rho1, n, 1, 1, std::pow(h, 1.5), ctl, part, lvl(levels - 1, 0), s));
     Ctl host{};
@@ -978,7 +1337,7 @@ extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, in
         const float mu = (float)(o.theta * hl / (2.0 * std::sqrt(3.0)));  // theta / ||A_h||, ||A_h|| <= 2 sqrt(3) / h
         const double tl = tol * std::pow(hl / h, o.alpha);
         if (l == 0) {
-            W1_CK3(cudaMemsetAsync(lvl(0, 1), 0, 4 * d.n * sizeof(float), s));
+            W1_CK3(cudaMemsetAsync(lvl(0, 1), 0, 4 * plane_stride(0) * sizeof(float), s));
         } else {
             const Dims3 c{d.nx / 2, d.ny / 2, d.nz / 2, d.n / 8};
             k3_prolong<<<grid3(d.n), T3, 0, s>>>(c, lvl(l - 1, 1), lvl(l - 1, 2), lvl(l - 1, 3), lvl(l - 1, 4),
@@ -1047,7 +1406,8 @@ extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, in
     Stats3Dev st{};
     W1_CK3(cudaMemcpyAsync(&st, sc.st, sizeof(st), cudaMemcpyDeviceToHost, s));
     if (flux) {
-        W1_CK3(cudaMemcpyAsync(flux, lvl(L - 1, 1), 3 * n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        for (int c = 0; c < 3; ++c)
+            W1_CK3(cudaMemcpyAsync(flux + c * n, lvl(L - 1, 1 + c), n * sizeof(float), cudaMemcpyDeviceToDevice, s));
     }
     if (potential) W1_CK3(cudaMemcpyAsync(potential, lvl(L - 1, 4), n * sizeof(float), cudaMemcpyDeviceToDevice, s));
     W1_CK3(cudaStreamSynchronize(s));

@@ -82,7 +82,9 @@ def test_cp_steps3d_match_oracle(w1, norm, shape):
 
 # (shape, cluster): one CTA, clusters of 2..16 slabs (one-plane slabs included)
 RESIDENT3 = [((1, 1, 4), 1), ((2, 3, 8), 1), ((8, 8, 8), 1), ((16, 16, 16), 1), ((4, 12, 16), 2), ((4, 12, 16), 4),
-             ((32, 32, 32), 8), ((32, 32, 32), 16), ((16, 16, 16), 16), ((2, 40, 32), 2), ((16, 8, 64), 4)]
+             ((32, 32, 32), 8), ((32, 32, 32), 16), ((16, 16, 16), 16), ((2, 40, 32), 2), ((16, 8, 64), 4),
+             # wide slabs (up to 16384 voxels per CTA, own state in tensor memory)
+             ((8, 32, 64), 1), ((32, 32, 32), 4), ((64, 64, 64), 16), ((16, 64, 64), 4), ((48, 48, 48), 16)]
 
 
 @pytest.mark.parametrize("norm", [L1, L2, LINF])
@@ -188,6 +190,17 @@ def test_solve3d_32_cluster_level(w1):
     val, st, status, flux, phi, ref = solve3_and_replay(w1, r0, r1, L1, 2)
     assert status == w1.OK and st.converged
     assert st.path == [1, 1] and st.cluster == [1, 8]
+    assert abs(val - ref.w1) <= 1e-4 * abs(ref.w1), (val, ref.w1)
+    assert flux3_rel_l1(flux, ref) <= 1e-3
+
+
+def test_solve3d_64_wide_level(w1):
+    """64^3 with three levels: 16^3 on one CTA, 32^3 on 8 CTAs, 64^3 on a
+    16-CTA cluster of wide slabs (four planes of 4096 voxels each)."""
+    r0, r1 = synth.pair3(64, 0)
+    val, st, status, flux, phi, ref = solve3_and_replay(w1, r0, r1, L1, 3)
+    assert status == w1.OK and st.converged
+    assert st.path == [1, 1, 1] and st.cluster == [1, 8, 16]
     assert abs(val - ref.w1) <= 1e-4 * abs(ref.w1), (val, ref.w1)
     assert flux3_rel_l1(flux, ref) <= 1e-3
 
