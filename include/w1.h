@@ -451,6 +451,10 @@ const char* w1_noalloc_last_error(void);
 w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, int norm, double tol,
                      const w1_options* opt, const float* rho0, const float* rho1, void* stream,
                      double* dist, float* flux, float* potential, w1_stats* stats);
+/* w1_solve3d keeps its device workspace (level arena, scratch) in a
+ * process-wide pool between calls, one per concurrent caller; this frees it
+ * (no call may be in flight). */
+void w1_3d_release_workspace(void);
 
 /* `iters` steps of eq. primaldual on one 3-D level, in place on m1, m2, m3, phi
  * (zero-mean rho); mu, tau as given.  *fpr_last (may be NULL) = R^k of the last

@@ -22,6 +22,8 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -1176,7 +1178,73 @@ w1_status fail3(w1_status st, const std::string& m)
                          std::string(#call) + ": " + cudaGetErrorString(e_));                       \
         }                                                                                           \
     } while (0)
+// Device workspace of w1_solve3d: the level arena, the step scratch and the
+// control block, kept in a process-wide pool between calls (allocation and
+// release cost milliseconds; concurrent callers each take their own).
+struct Work3 {
+    int device = -1;
+    long long arena_floats = 0, n = 0;
+    float* arena = nullptr;
+    Scratch3 sc;
+    Ctl* ctl = nullptr;
+    double* part = nullptr;
+    ~Work3()
+    {
+        cudaFree(arena);
+        cudaFree(ctl);
+        cudaFree(part);
+    }
+};
+std::mutex g_pool_mu;
+std::vector<Work3*> g_pool;
+
+cudaError_t work3_acquire(int dev, long long arena_floats, long long n, Work3** out)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        for (size_t k = 0; k < g_pool.size(); ++k) {
+            Work3* w = g_pool[k];
+            if (w->device == dev && w->arena_floats >= arena_floats && w->n >= n) {
+                g_pool.erase(g_pool.begin() + (long)k);
+                *out = w;
+                return cudaSuccess;
+            }
+        }
+    }
+    auto* w = new (std::nothrow) Work3();
+    if (!w) return cudaErrorMemoryAllocation;
+    w->device = dev;
+    w->arena_floats = arena_floats;
+    w->n = n;
+    cudaError_t e = cudaMalloc(&w->arena, arena_floats * sizeof(float));
+    if (e == cudaSuccess) e = w->sc.alloc(n, true);
+    if (e == cudaSuccess) e = cudaMalloc(&w->ctl, sizeof(Ctl));
+    if (e == cudaSuccess) e = cudaMalloc(&w->part, prep_part_doubles(1) * sizeof(double));
+    if (e != cudaSuccess) {
+        delete w;
+        return e;
+    }
+    *out = w;
+    return cudaSuccess;
+}
+
+void work3_release(Work3* w)
+{
+    if (!w) return;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    g_pool.push_back(w);
+}
 }  // namespace
+
+extern "C" void w1_3d_release_workspace(void)
+{
+    std::vector<Work3*> all;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        all.swap(g_pool);
+    }
+    for (Work3* w : all) delete w;
+}
 
 extern "C" const char* w1_3d_last_error(void) { return g_err3.c_str(); }
 
@@ -1287,29 +1355,19 @@ extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, in
     };
     std::vector<long long> off(levels + 1, 0);
     for (int l = 0; l < levels; ++l) off[l + 1] = off[l] + 5 * plane_stride(l);
-    float* arena = nullptr;
-    W1_CK3(cudaMalloc(&arena, off[levels] * sizeof(float)));
-    struct Free {
-        float* p;
-        ~Free() { cudaFree(p); }
-    } free_arena{arena};
-    Scratch3 sc;
-    W1_CK3(sc.alloc(n, true));
-    Ctl* ctl = nullptr;
-    double* part = nullptr;
-    W1_CK3(cudaMalloc(&ctl, sizeof(Ctl)));
-    struct FreeC {
-        Ctl* c;
-        double* p;
-        ~FreeC()
-        {
-            cudaFree(c);
-            cudaFree(p);
-        }
-    } free_c{ctl, nullptr};
-    W1_CK3(cudaMalloc(&part, prep_part_doubles(1) * sizeof(double)));
-    free_c.p = part;
+    // device workspace from the pool (kept between calls; w1_3d_release_workspace frees it)
+    Work3* w = nullptr;
+    W1_CK3(work3_acquire(dev, off[levels], n, &w));
+    struct Back {
+        Work3* w;
+        ~Back() { work3_release(w); }
+    } back{w};
+    float* arena = w->arena;
+    Scratch3& sc = w->sc;
+    Ctl* ctl = w->ctl;
+    double* part = w->part;
     W1_CK3(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    W1_CK3(cudaMemsetAsync(sc.counter, 0, sizeof(unsigned int), s));
     auto lvl = [&](int l, int c) { return arena + off[l] + c * plane_stride(l); };
     // prep (masses with h^3 weights: the prep kernel weights by h_2d^2, so pass h^(3/2))
     W1_CK3(launch_prep(rho0, rho1, n, 1, 1, std::pow(h, 1.5), ctl, part, lvl(levels - 1, 0), s));

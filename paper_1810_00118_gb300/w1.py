@@ -151,6 +151,7 @@ def _load() -> ctypes.CDLL:
         "w1_restrict3d": (st, [I, I, I, P, P, P]),
         "w1_prolong3d": (st, [I, I, I, P, P, P, P, P, P, P, P, P]),
         "w1_3d_last_error": (ctypes.c_char_p, []),
+        "w1_3d_release_workspace": (None, []),
         "w1_plan_bytes": (ctypes.c_size_t, [I, I, D, I, I, D, I, ctypes.POINTER(Options)]),
         "w1_autotune_level": (st, [I, I, I, I, I, I, ctypes.POINTER(LevelChoice), ctypes.POINTER(LevelChoice),
                                    ctypes.POINTER(I)]),
@@ -474,6 +475,11 @@ def solve3d(rho0, rho1, norm=NORM_L1, h=0.0, levels=0, tol=0.0, flux=None, poten
                          _dev_ptr(potential, rho0.shape) if potential is not None else None, ctypes.byref(s))
     _check3(st, ok=(OK, ERR_NOT_CONVERGED, ERR_TIMEOUT))
     return d.value, Stats._from(s), st
+
+
+def release_workspace3d():
+    """Frees the device workspace w1_solve3d keeps between calls."""
+    _lib.w1_3d_release_workspace()
 
 
 def cp_steps3d(rho, m1, m2, m3, phi, h, norm, mu, tau, iters, path=2, cluster=0, stream=None) -> float:

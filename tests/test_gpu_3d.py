@@ -272,6 +272,20 @@ def test_solve3d_single_voxel_and_identical(w1):
     assert status == w1.OK and val == 0.0 and st.converged
 
 
+def test_solve3d_workspace_reuse(w1):
+    """Repeated solves of different sizes reuse the pooled workspace and give the
+    same result as after the pool is freed."""
+    r0, r1 = synth.pair3(16, 11)
+    a0, a1 = dev(r0), dev(r1)
+    v1, _, _ = w1.solve3d(a0, a1, norm=L2, levels=2)
+    s0, s1 = synth.pair3(8, 12)
+    w1.solve3d(dev(s0), dev(s1), norm=L1)
+    v2, _, _ = w1.solve3d(a0, a1, norm=L2, levels=2)
+    w1.release_workspace3d()
+    v3, _, _ = w1.solve3d(a0, a1, norm=L2, levels=2)
+    assert v1 == v2 == v3
+
+
 def test_solve3d_errors(w1):
     z = dev(np.ones((4, 4, 4)))
     with pytest.raises(w1.W1Error) as e:
