@@ -300,17 +300,16 @@ __global__ void __launch_bounds__(1024) k3_final_b(Dims3 d, double h, const doub
         if (odd || (!px && !py && !pz)) break;
         const int bx = px ? 2 : 1, by = py ? 2 : 1, bz = pz ? 2 : 1;
         const int ncx = cx / bx, ncy = cy / by, ncz = cz / bz;
-        const long long cells = (long long)ncx * ncy * ncz;
-        for (long long c = threadIdx.x; c < cells; c += blockDim.x) {
-            const int K = (int)(c / ((long long)ncx * ncy));
-            const long long r = c - (long long)K * ncx * ncy;
-            const int J = (int)(r / ncx), I = (int)(r - (long long)J * ncx);
+        const int cplane = ncx * ncy, cells = cplane * ncz;  // grids of up to 2^31 voxels
+        for (int c = threadIdx.x; c < cells; c += blockDim.x) {
+            const int K = c / cplane, r = c - K * cplane;
+            const int J = r / ncx, I = r - J * ncx;
             double tot = 0.0;
             for (int zc = 0; zc < bz; ++zc)
                 for (int b = 0; b < by; ++b)
                     for (int a = 0; a < bx; ++a) {
                         const double qa = src[((long long)(bz * K + zc) * cy + (by * J + b)) * cx + (bx * I + a)];
-                        cost += fabs(qa) * (a * hx + b * hy + zc * hz);
+                        cost = fma(fabs(qa), (a ? hx : 0.0) + (b ? hy : 0.0) + (zc ? hz : 0.0), cost);
                         tot += qa;
                     }
             dst[c] = tot;

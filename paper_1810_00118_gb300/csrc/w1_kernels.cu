@@ -2124,14 +2124,15 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
         if (stopx || stopy || (!px && !py)) break;
         const int bx = px ? 2 : 1, by = py ? 2 : 1;
         const int ncx = cx / bx, ncy = cy / by;
-        const long long nc = (long long)ncx * ncy;
-        for (long long k = threadIdx.x; k < nc; k += blockDim.x) {
-            const int J = (int)(k / ncx), I = (int)(k - (long long)J * ncx);
+        const int nc = ncx * ncy;  // grids of up to 2^31 nodes
+        const double w[2][2] = {{0.0, hx}, {hy, hx + hy}};  // distance to the block's corner
+        for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+            const int J = k / ncx, I = k - J * ncx;
             double total = 0.0;
             for (int b = 0; b < by; ++b)
                 for (int a = 0; a < bx; ++a) {
                     const double qa = src[(size_t)(by * J + b) * cx + (bx * I + a)];
-                    cost += fabs(qa) * (a * hx + b * hy);
+                    cost = fma(fabs(qa), w[b][a], cost);
                     total += qa;
                 }
             dst[k] = total;
@@ -2146,16 +2147,16 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
         if (py) hy *= 2.0;
     }
     double pos = 0.0, neg = 0.0;
-    for (long long k = threadIdx.x; k < (long long)cx * cy; k += blockDim.x) {
+    for (int k = threadIdx.x; k < cx * cy; k += blockDim.x) {
         const double x = src[k];
         if (x > 0) pos += x;
         else neg -= x;
     }
-    double w[4] = {cost, pos, neg, 0.0};
-    block_sum<4>(w, sh);
+    double ws[4] = {cost, pos, neg, 0.0};
+    block_sum<4>(ws, sh);
     if (threadIdx.x == 0) {
         const double diam = (cx - 1) * hx + (cy - 1) * hy;
-        const double route = w[0] + diam * fmax(w[1], w[2]);
+        const double route = ws[0] + diam * fmax(ws[1], ws[2]);
         ctl->f = tot[0];
         ctl->dual = tot[1];
         ctl->res_l1 = tot[2];
