@@ -1401,6 +1401,7 @@ extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, in
                                                  lvl(l, 1), lvl(l, 2), lvl(l, 3), lvl(l, 4));
             W1_CK3(cudaGetLastError());
         }
+        NvtxRange range("w1 3-D level %d %dx%dx%d", l, d.nx, d.ny, d.nz);
         long long it = 0;
         double r = 0.0;
         bool conv = false, late = false;

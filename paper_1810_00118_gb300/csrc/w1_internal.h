@@ -8,11 +8,30 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
+
+#include <cstdio>
 #include <stdint.h>
 
 #include "../../include/w1.h"
 
 namespace w1 {
+
+// NVTX range on the host timeline (a no-op unless a profiler is attached):
+// plan solves, levels of eager and 3-D solves, server requests, autotuning.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    template <class... A>
+    NvtxRange(const char* fmt, A... a)
+    {
+        char buf[96];
+        std::snprintf(buf, sizeof(buf), fmt, a...);
+        nvtxRangePushA(buf);
+    }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Per-pair device control block: reduction counter, flags, per-level iteration
 // counts and residuals, and the final statistics.

@@ -696,6 +696,7 @@ static w1_status run_eager(w1_plan* p, cudaStream_t s)
     std::vector<Ctl> host(B);
     for (int l = 0; l < p->L; ++l) {
         LevelPlan& v = p->lv[l];
+        NvtxRange range("w1 level %d %dx%d path %d", l, v.nx, v.ny, v.path);
         const size_t b = (size_t)v.nx * v.ny * sizeof(float) * B;
         W1_CK(launch_level_begin(p->ctl, l, B, s));
         if (v.path == 4) {
@@ -761,6 +762,7 @@ static w1_status run_eager(w1_plan* p, cudaStream_t s)
 // result block.  Nothing waits.
 static w1_status enqueue(w1_plan* p, int nbatch, const float* rho0, const float* rho1, cudaStream_t s, float* flux)
 {
+    NvtxRange range("w1 solve %dx%d p%d x%d", p->nx, p->ny, p->norm, nbatch);
     if (!p->opt.eager && !p->graph_ok) {
         w1_status st = build_graph(p);
         if (st != W1_OK) return st;

@@ -92,6 +92,7 @@ struct Slot {
     std::atomic<bool> done{false};
     std::vector<Request> reqs;
     double last_used = 0.0;
+    nvtxRangeId_t nvtx = 0;  // the in-flight batch on the host timeline
 };
 
 }  // namespace
@@ -222,6 +223,7 @@ void finish_slot(w1_server* srv, Slot* s)
         srv->pending.erase(r.ticket);
         ++srv->completed;
     }
+    nvtxRangeEnd(s->nvtx);
     s->reqs.clear();
     s->busy = false;
     s->done.store(false);
@@ -310,6 +312,12 @@ void dispatch(w1_server* srv)
         }
         slot->busy = true;
         slot->last_used = now_s();
+        {
+            char name[96];
+            std::snprintf(name, sizeof(name), "w1 request %llu %dx%d p%d x%d", (unsigned long long)slot->reqs[0].ticket,
+                          k.nx, k.ny, k.norm, (int)slot->reqs.size());
+            slot->nvtx = nvtxRangeStartA(name);
+        }
     }
 }
 

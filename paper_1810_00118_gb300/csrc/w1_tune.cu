@@ -155,6 +155,7 @@ double time_candidate(int norm, int path, int cluster, int nx, int ny, int pairs
 extern "C" w1_status w1_autotune_level(int nx, int ny, int norm, int batch, int objective, int steps,
                                        w1_level_choice* best, w1_level_choice* all, int* n_all)
 {
+    NvtxRange range("w1 autotune %dx%d p%d", nx, ny, norm);
     if (nx < 1 || ny < 1 || batch < 1 || !best || objective < 1 || objective > 3) {
         g_tune_err = "bad arguments to w1_autotune_level";
         return W1_ERR_INVALID_ARG;
