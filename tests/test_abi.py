@@ -60,3 +60,30 @@ def test_oracle_is_not_imported_by_the_product():
             if f.endswith((".py", ".cu", ".h", ".cuh")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text and "w1_oracle" not in text, f
+
+
+def test_ctypes_mirrors_match_the_c_layouts(tmp_path):
+    """Sizes and field offsets of every struct the binding mirrors, as the C
+    compiler lays them out from include/w1.h (gcc, host only)."""
+    import shutil
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    from paper_1810_00118_gb300 import w1
+    mirrors = {"w1_options": w1.Options, "w1_stats": w1._Stats, "w1_level_choice": w1.LevelChoice,
+               "w1_server_config": w1.ServerConfig, "w1_server_info": w1.ServerInfo}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "w1.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    c = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for cname, py in mirrors.items():
+        assert c[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert c[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
