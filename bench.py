@@ -663,7 +663,7 @@ def main():
                     help="serving: in-flight count below which requests get latency-tuned slots (0: off)")
     ap.add_argument("--only", default="solve",
                     choices=["solve", "stream-kernel", "tblock-kernel", "resident-kernel", "pdhg-kernel", "serve",
-                             "mixed", "tol-sweep", "solve3d", "3d-kernel"],
+                             "mixed", "tol-sweep", "solve3d", "3d-kernel", "cascade-vs-single"],
                     help="kernel-only runs for profiling: one level's steps through w1_cp_steps")
     ap.add_argument("--kn", type=int, default=256, help="grid side for --only *-kernel")
     ap.add_argument("--kiters", type=int, default=1000, help="steps for --only *-kernel")
@@ -686,6 +686,8 @@ def main():
         return run_tol_sweep(args)
     if args.only == "solve3d":
         return run_solve3d(args)
+    if args.only == "cascade-vs-single":
+        return run_cascade_vs_single(args)
     if args.only != "solve":
         return run_kernel_only(args)
     return run_gpu(args)
@@ -861,6 +863,49 @@ def run_tol_sweep(args):
                 print(json.dumps(out[-1]), flush=True)
     print(json.dumps({"only": "tol-sweep", "grid": N, "pairs": B, "eps_L": eps,
                       "reference": "same pairs, alpha -1, default levels, eps_L / 100", "rows": out}))
+    return 0
+
+
+def run_cascade_vs_single(args):
+    """256^2 Gaussian-mixture pairs (8 components, 1e-4 floor), p = 2: the 5-level
+    cascade 16 -> 256 (Algorithm 3) against a single level started from zero
+    (Algorithm 1) with the same finest-level tolerance, same GPU, one solve at a
+    time (CUDA events): time per solve, finest-level steps, W1 agreement."""
+    import torch
+
+    import synth
+    from paper_1810_00118_gb300 import w1
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n, norm, npairs = 256, 2, 4
+    pairs = []
+    for k in range(npairs):
+        r0, r1 = synth.pair(1, k)
+        pairs.append(tuple(torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda() for x in (r0, r1)))
+    out = {}
+    for levels in (5, 1):
+        with w1.Plan(n, n, levels=levels, norm=norm, max_iters=4_000_000) as plan:
+            plan.solve(*pairs[0], stream=stream, allow=(w1.OK, w1.ERR_NOT_CONVERGED))  # warm-up (graph build)
+            ms, vals, fin = [], [], []
+            for a, b in pairs:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                v, st, status = plan.solve(a, b, stream=stream, allow=(w1.OK, w1.ERR_NOT_CONVERGED))
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                vals.append(v)
+                fin.append(st.iters[-1])
+            out[levels] = {"levels": levels, "ms_per_solve": float(np.mean(ms)), "finest_steps": fin, "w1": vals,
+                           "converged": bool(st.converged)}
+        print(json.dumps(out[levels]), flush=True)
+    rel = [abs(a - b) / abs(b) for a, b in zip(out[5]["w1"], out[1]["w1"])]
+    print(json.dumps({"only": "cascade-vs-single", "grid": [n, n], "norm": "L2", "pairs": npairs,
+                      "speedup": out[1]["ms_per_solve"] / out[5]["ms_per_solve"],
+                      "finest_step_ratio": float(np.mean(out[1]["finest_steps"]) / np.mean(out[5]["finest_steps"])),
+                      "max_rel_w1_diff": float(max(rel)), "cascade": out[5], "single": out[1]}))
     return 0
 
 

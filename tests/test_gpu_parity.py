@@ -240,6 +240,23 @@ def test_solve_256_l2_five_levels(w1):
     assert_parity(val, st, flux, ref)
 
 
+def test_cascade_against_single_level_256_l2(w1):
+    """Algorithm 3 (5 levels, 16 -> 256) against Algorithm 1 from zero on one level
+    with the same finest-level tolerance: far fewer finest-level steps for the
+    same W1 (each stops at its own R^k < eps, so they agree to the tolerance's
+    accuracy, not bitwise)."""
+    r0, r1 = synth.pair(1, 0)
+    a0, a1 = dev(r0), dev(r1)
+    with w1.Plan(256, 256, levels=5, norm=L2) as p:
+        v5, st5, _ = p.solve(a0, a1)
+    with w1.Plan(256, 256, levels=1, norm=L2, max_iters=4_000_000) as p:
+        v1, st1, status = p.solve(a0, a1, allow=(w1.OK, w1.ERR_NOT_CONVERGED))
+    assert st5.converged
+    assert st5.iters[-1] * 5 < st1.iters[0]
+    if status == w1.OK:
+        assert v5 == pytest.approx(v1, rel=5e-3)
+
+
 @pytest.mark.parametrize("norm", [L2, L1, LINF])
 def test_solve_512_six_levels(w1, norm):
     """The 512x512 image-shaped workload, 6 levels 16->512, the bench configuration."""
