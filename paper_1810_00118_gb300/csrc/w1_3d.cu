@@ -710,7 +710,6 @@ __global__ void __launch_bounds__(R3_THREADS, 1) k3_wide(R3Args a)
     // tensor memory
     if (t < 32) {
         tmem_alloc(smem_u32(slots + 58), R3W_TMEM_COLS);
-        tmem_relinquish();
     }
     tmem_fence_before();
     __syncthreads();

@@ -1345,8 +1345,9 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
     uint32_t tb = 0;
     if (TM) {
         if (t < 32) {
+            // no relinquish_alloc_permit: the persistent cascade allocates again
+            // for every wide level it runs (one CTA per SM, nothing else competes)
             tmem_alloc(smem_u32(slots + 58), RESW_TMEM_COLS);
-            tmem_relinquish();
         }
         tmem_fence_before();
         __syncthreads();
