@@ -302,7 +302,10 @@ typedef struct {
                                 one solve alone (w1_options.tune = 1: more SMs per level); at
                                 higher load, to a slot with `opt` (throughput); 0 (default): off.
                                 Applies when opt.path = 0 and opt.algorithm = 3.  A class may
-                                then hold slots of both kinds.                               */
+                                then hold slots of both kinds.  The first latency-tuned slot
+                                of a class runs the autotuner on the worker thread (tens of
+                                milliseconds per level, once per class and process; the
+                                choices are cached): warm each class up with one request. */
 } w1_server_config;
 
 typedef struct {
