@@ -1,14 +1,16 @@
 """Planted mistakes are caught by the oracle's pins.  Each test patches one step
-of the oracle (on the CPU, for the duration of the test) with a plausible error
-and checks that the pin covering that step fails: a dropped factor in the
-Poisson eigenvalues, a sign error in the gradient, the wrong radius of the dual
-ball, a wrong objective, a lost boundary condition, a wrong restriction weight
-and a wrong Interpolate weight."""
+of an oracle (the prox-PDHG, 3-D and 2-D ones; on the CPU, for the duration of
+the test) with a plausible error and checks that the pin covering that step
+fails: a dropped factor in the Poisson eigenvalues, a sign error in the
+gradient, the wrong radius of the dual ball, a wrong objective, a lost boundary
+condition, a wrong shrink threshold, wrong restriction weights and wrong
+Interpolate weights."""
 import numpy as np
 import pytest
 
 import oracle
 from oracle import d3, pdhg
+from tests import test_oracle as pins2
 from tests import test_oracle_3d as pins3
 from tests import test_oracle_pdhg as pins
 
@@ -80,3 +82,36 @@ def test_interpolate_with_the_wrong_weights(monkeypatch):
 
     monkeypatch.setattr(d3, "prolong", half_weight)
     caught(pins3.test_restrict_prolong_identities)
+
+
+# --- the 2-D oracle (planted through its Python wrappers) -------------------------
+
+
+def test_2d_prox_with_twice_the_threshold(monkeypatch):
+    good = oracle.prox
+    monkeypatch.setattr(oracle, "prox", lambda norm, mu, v1, v2: good(norm, 2.0 * mu, v1, v2))
+    caught(pins2.test_prox_is_the_argmin, L1)
+
+
+def test_2d_gradient_with_the_wrong_sign(monkeypatch):
+    good = oracle.grad
+    monkeypatch.setattr(oracle, "grad", lambda phi, h: tuple(-g for g in good(phi, h)))
+    caught(pins2.test_div_grad_adjoint, 3, 5)
+
+
+def test_2d_restriction_by_sums_instead_of_means(monkeypatch):
+    good = oracle.restrict
+    monkeypatch.setattr(oracle, "restrict", lambda fine: 4.0 * good(fine))
+    caught(pins2.test_restrict_conserves_mass_and_constants)
+
+
+def test_2d_interpolate_that_copies_phi(monkeypatch):
+    good = oracle.prolong
+
+    def nearest_phi(m1c, m2c, phic):
+        f1, f2, _ = good(m1c, m2c, phic)
+        return f1, f2, np.kron(np.asarray(phic, dtype=np.float64), np.ones((2, 2)))
+
+    monkeypatch.setattr(oracle, "prolong", nearest_phi)
+    caught(pins2.test_prolong_golden_2x2)
+    caught(pins2.test_prolong_phi_reproduces_affine_inside)
