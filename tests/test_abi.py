@@ -87,3 +87,24 @@ def test_ctypes_mirrors_match_the_c_layouts(tmp_path):
         assert c[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert c[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_no_cpu_fallback_errors_are_loud():
+    """Without a GPU, building a plan or a server fails with a W1Error (there is
+    no CPU path); host tensors are refused before any call."""
+    import numpy as np
+    import torch
+    from paper_1810_00118_gb300 import w1
+    cpu = torch.zeros((8, 8, 8), dtype=torch.float32)
+    with pytest.raises(TypeError):
+        w1.solve3d(cpu, cpu)
+    with pytest.raises(TypeError):
+        w1.cp_steps(*(torch.zeros((8, 8)) for _ in range(4)), 0.125, 1, 0.01, 0.01, 4)
+    with pytest.raises(TypeError):
+        w1.cp_steps(np.zeros((8, 8), np.float32), *(torch.zeros((8, 8)) for _ in range(3)), 0.125, 1, 0.01, 0.01, 4)
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the no-GPU errors cannot be observed here")
+    with pytest.raises(w1.W1Error):
+        w1.Plan(64, 64)
+    with pytest.raises(w1.W1Error):
+        w1.Server(max_slots=2)
