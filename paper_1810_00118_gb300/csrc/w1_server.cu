@@ -54,10 +54,6 @@ double now_s()
 struct Key {
     int nx, ny, levels, norm;
     double h, tol;
-    bool operator<(const Key& o) const
-    {
-        return std::tie(nx, ny, levels, norm, h, tol) < std::tie(o.nx, o.ny, o.levels, o.norm, o.h, o.tol);
-    }
     bool operator==(const Key& o) const
     {
         return nx == o.nx && ny == o.ny && levels == o.levels && norm == o.norm && h == o.h && tol == o.tol;
