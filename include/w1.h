@@ -92,9 +92,18 @@ typedef struct {
                               stop G^k < eps_l of eq. pdhg_stop; mu = tau = theta, the paper's
                               1/2; tol <= 0 gives eq. stop_tol for Alg. 4); level sides must
                               be powers of two in [2, 1024]; path and tune do not apply    */
+    int estimate;          /* which value dist and w1_stats.w1 report:
+                              0 (default): the saddle value, the Lagrangian of eq. minmax_cp
+                                L(m, phi) = f(m) + <phi, div m - rho>_h at the returned pair;
+                                it corrects f(m) to first order for the constraint residual
+                                div m - rho that the stopped iteration leaves;
+                              1: the primal objective f(m) of the returned flux (the value
+                                Sec. 5 prints as the approximation, f(m^K));
+                              both are also in w1_stats.saddle and w1_stats.primal          */
 } w1_options;
 
-/* What a solve reports.  Values are FP64 sums of the FP32 state. */
+/* What a solve reports.  Values are FP64 compensated sums (TwoSum error terms
+ * carried beside every running sum) of per-node terms of the FP32 state. */
 typedef struct {
     int levels;
     int nx[W1_MAX_LEVELS];          /* level sizes, coarsest first */
@@ -104,10 +113,10 @@ typedef struct {
     double tol[W1_MAX_LEVELS];      /* eps_l of each level */
     int path[W1_MAX_LEVELS];        /* 1 resident (cluster size in cluster[]), 2 streaming, 3 blocked */
     int cluster[W1_MAX_LEVELS];
-    double w1;       /* f(m) of the returned finest flux: the W1 estimate (Sec. 5 reports f(m^K)) */
+    double w1;       /* the W1 estimate chosen by w1_options.estimate (default: saddle) */
     double dual;     /* -<phi, rho>_h of the returned potential */
     double lb;       /* certified lower bound on the discrete W1: dual / max(1, gmax) */
-    double ub;       /* certified upper bound: w1 + route */
+    double ub;       /* certified upper bound: primal + route */
     double route;    /* cost of an explicit flux carrying the residual rho - div m */
     double res_l1;   /* sum |rho - div m| h^2 */
     double rho_l1;   /* sum |rho| h^2 */
@@ -116,6 +125,8 @@ typedef struct {
     double mass1;    /* sum rho1 h^2 */
     double mass_shift; /* mean of rho0 - rho1 removed so that the constraint is solvable */
     int converged;   /* 1 when every level met its tolerance */
+    double primal;   /* f(m) = sum ||m(x)||_p h^2 of the returned flux (eq. opt_flux_dis) */
+    double saddle;   /* L(m, phi) = f(m) + <phi, div m - rho>_h (eq. minmax_cp)           */
 } w1_stats;
 
 typedef struct w1_plan w1_plan;
@@ -157,7 +168,7 @@ w1_status w1_plan_set_workspace(w1_plan* plan, void* device_ptr, size_t bytes);
 /*
  * One W1 solve (Algorithm 3), enqueued on `stream`.
  *   rho0, rho1 : device, [ny][nx] float32 densities, caller-owned, read only.
- *   dist       : host; receives the W1 estimate f(m) (blocks until the stream
+ *   dist       : host; receives the W1 estimate (w1_options.estimate; blocks until the stream
  *                reaches the end of the solve).
  *   flux       : device [2][ny][nx] float32 (m1 then m2) or NULL.
  *   stats      : host or NULL.
@@ -385,18 +396,19 @@ w1_status w1_restrict(int nx, int ny, const float* fine, float* coarse, void* st
 w1_status w1_prolong(int ncx, int ncy, const float* m1c, const float* m2c, const float* phic, float* m1f,
                      float* m2f, float* phif, void* stream);
 
-/* Statistics of a state (fields w1, dual, lb, ub, route, res_l1, rho_l1, gmax
- * of *out), rho already balanced; blocks until done. */
+/* Statistics of a state (fields w1 (= saddle), primal, saddle, dual, lb, ub,
+ * route, res_l1, rho_l1, gmax of *out), rho already balanced; blocks until done. */
 w1_status w1_state_stats(int nx, int ny, double h, int norm, const float* rho, const float* m1, const float* m2,
                          const float* phi, void* stream, w1_stats* out);
 
 /*
  * w1_state_stats without allocating device memory.  The paper has no
- * counterpart; this exists for callers that cannot call cudaMalloc: code that
- * runs while a stream is captured into a CUDA graph (allocation is not allowed
- * there), loops that must not pay cudaMalloc/cudaFree's implicit device
- * synchronisation, and frameworks that own all device memory through their
- * own pools.  Same arguments, results and numbers as w1_state_stats.
+ * counterpart; this exists for callers that cannot call cudaMalloc: loops
+ * that must not pay the implicit device-wide synchronisation of
+ * cudaMalloc/cudaFree, frameworks that own all device memory through their own
+ * pools (an allocation behind their back breaks their accounting and limits),
+ * and services that must run in a fixed, preallocated memory footprint.  Same
+ * arguments, results and numbers as w1_state_stats.
  *   - Scratch lives in one file-scope static device array of about 4.2 MB
  *     (control block, partial sums, 2 * W1_NOALLOC_MAX_NODES FP64 masses) that
  *     every GPU loading the library holds until the process exits.
@@ -408,7 +420,8 @@ w1_status w1_state_stats(int nx, int ny, double h, int norm, const float* rho, c
  *     contents (the call clears what must start at zero).  Calls whose work
  *     overlaps on the GPU (other streams, other host threads) race on it:
  *     serialise them.
- *   - The call copies the result to the host and synchronises the stream.
+ *   - Before it returns, the call copies the statistics to the host and
+ *     synchronises the stream.
  */
 #define W1_NOALLOC_MAX_NODES 262144
 w1_status w1_state_stats_noalloc(int nx, int ny, double h, int norm, const float* rho, const float* m1,

@@ -42,7 +42,7 @@ ERR_NOMEM = -4
 
 class _Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_double) for name in
-                ("f", "dual", "res_l1", "rho_l1", "gmax", "lb", "route", "ub", "fpr")]
+                ("f", "dual", "res_l1", "rho_l1", "gmax", "lb", "route", "ub", "fpr", "saddle")]
 
 
 @dataclass
@@ -57,6 +57,7 @@ class Stats:
     route: float
     ub: float
     fpr: float
+    saddle: float
 
     @staticmethod
     def _from(s: _Stats) -> "Stats":
@@ -240,9 +241,13 @@ class Result:
 
 
 def multilevel(rho0, rho1, h=0.0, levels=1, norm=NORM_L1, tol=1e-4, alpha=-1.0, theta=0.5, stop=STOP_GAP,
-               check_every=32, max_iters=200000, replay=None) -> Result:
+               check_every=32, max_iters=200000, replay=None, estimate="saddle") -> Result:
     """Algorithm 3 (cascadic multilevel Algorithm 1).  Raises on argument errors;
-    returns status NOT_CONVERGED (with the best result) if a level hit max_iters."""
+    returns status NOT_CONVERGED (with the best result) if a level hit max_iters.
+    Result.w1 is the W1 estimate of the returned finest pair (m, phi): the
+    saddle value L(m, phi) of eq. minmax_cp (estimate="saddle", the default)
+    or the primal objective f(m) that Sec. 5 prints (estimate="primal"); both
+    are in Result.stats (.saddle, .f)."""
     rho0, rho1 = _f64(rho0), _f64(rho1)
     ny, nx = rho0.shape
     m1, m2, phi = np.empty_like(rho0), np.empty_like(rho0), np.empty_like(rho0)
@@ -259,4 +264,8 @@ def multilevel(rho0, rho1, h=0.0, levels=1, norm=NORM_L1, tol=1e-4, alpha=-1.0, 
     if st < 0:
         raise ValueError({ERR_ARG: "invalid argument", ERR_SHAPE: "shape not divisible by 2^(levels-1)",
                           ERR_MASS: "mass imbalance or non-finite input", ERR_NOMEM: "out of memory"}[st])
-    return Result(w1.value, m1, m2, phi, [iters[k] for k in range(levels)], Stats._from(s), st)
+    stats_ = Stats._from(s)
+    if estimate not in ("saddle", "primal"):
+        raise ValueError("estimate must be 'saddle' or 'primal'")
+    w = stats_.saddle if estimate == "saddle" else w1.value
+    return Result(w, m1, m2, phi, [iters[k] for k in range(levels)], stats_, st)

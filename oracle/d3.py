@@ -15,7 +15,8 @@ from . import _load as _load2d
 
 
 class _Stats3(ctypes.Structure):
-    _fields_ = [(name, ctypes.c_double) for name in ("f", "dual", "res_l1", "rho_l1", "gmax", "lb", "route", "ub")]
+    _fields_ = [(name, ctypes.c_double) for name in ("f", "dual", "res_l1", "rho_l1", "gmax", "lb", "route", "ub",
+                                                      "saddle")]
 
 
 _lib = None
@@ -112,6 +113,7 @@ class Stats3:
     lb: float
     route: float
     ub: float
+    saddle: float
 
 
 def stats(rho, m1, m2, m3, phi, h, norm) -> Stats3:
@@ -152,8 +154,10 @@ class Result3:
 
 
 def multilevel(rho0, rho1, h=0.0, levels=1, norm=1, tol=1e-6, alpha=-1.0, theta=0.5, check_every=32,
-               max_iters=1_000_000, replay=None) -> Result3:
-    """Algorithm 3 on a 3-D grid with the FPR stop (R^k < eps_l after every K-th step)."""
+               max_iters=1_000_000, replay=None, estimate="saddle") -> Result3:
+    """Algorithm 3 on a 3-D grid with the FPR stop (R^k < eps_l after every K-th step).
+    Result3.w1 is the saddle value (the Lagrangian of eq. minmax_cp at the
+    returned pair) or, with estimate="primal", f(m); both are in .stats."""
     r0, r1 = _f64(rho0), _f64(rho1)
     nz, ny, nx = r0.shape
     out = [np.empty_like(r0) for _ in range(4)]
@@ -171,5 +175,8 @@ def multilevel(rho0, rho1, h=0.0, levels=1, norm=1, tol=1e-6, alpha=-1.0, theta=
     if st < 0:
         raise ValueError({-1: "invalid argument", -2: "shape not divisible by 2^(levels-1)",
                           -3: "mass imbalance or non-finite input", -4: "out of memory"}[st])
-    return Result3(w1.value, *out, [iters[k] for k in range(levels)], [fprs[k] for k in range(levels)],
-                   Stats3(*(getattr(s, n) for n, _ in _Stats3._fields_)), st)
+    s3 = Stats3(*(getattr(s, n) for n, _ in _Stats3._fields_))
+    if estimate not in ("saddle", "primal"):
+        raise ValueError("estimate must be 'saddle' or 'primal'")
+    w = s3.saddle if estimate == "saddle" else w1.value
+    return Result3(w, *out, [iters[k] for k in range(levels)], [fprs[k] for k in range(levels)], s3, st)

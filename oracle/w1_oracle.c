@@ -55,6 +55,7 @@ typedef struct {
     double route;  /* cost of an explicit flux that carries the residual rho - div m */
     double ub;     /* certified upper bound f(m) + route */
     double fpr;    /* fixed-point residual R^k of eq. pd_stop for the step out of this state */
+    double saddle; /* L(m, phi) = f(m) + <phi, A m - rho>_h, the Lagrangian of eq. minmax_cp */
 } w1o_stats_t;
 
 #define AT(a, j, i) ((a)[(size_t)(j) * (size_t)nx + (size_t)(i)])
@@ -359,6 +360,15 @@ void w1o_stats(int nx, int ny, double h, int norm, const double* rho, const doub
     out->lb = out->dual / fmax(1.0, out->gmax);
     out->route = w1o_route_bound(nx, ny, h, e);
     out->ub = out->f + out->route;
+    /* the saddle value: the min-max Lagrangian of eq. minmax_cp evaluated at
+     * the state, L(m, phi) = f(m) + <phi, A_h m - rho>_h; at a saddle point it
+     * equals W1_h, and near one it corrects f(m) for the residual A_h m - rho */
+    {
+        double inner = 0.0;
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) inner += AT(phi, j, i) * (AT(d, j, i) - AT(rho, j, i)) * h * h;
+        out->saddle = out->f + inner;
+    }
 done:
     free(d); free(g1); free(g2); free(e);
 }

@@ -237,6 +237,7 @@ double w1o3_route_bound(int nx, int ny, int nz, double h, const double* e)
 
 typedef struct {
     double f, dual, res_l1, rho_l1, gmax, lb, route, ub;
+    double saddle; /* L(m, phi) = f(m) + <phi, A m - rho>_h, the Lagrangian of eq. minmax_cp */
 } w1o3_stats_t;
 
 void w1o3_stats(int nx, int ny, int nz, double h, int norm, const double* rho, const double* m1, const double* m2,
@@ -267,6 +268,9 @@ void w1o3_stats(int nx, int ny, int nz, double h, int norm, const double* rho, c
     out->lb = out->dual / fmax(1.0, gmax);
     out->route = w1o3_route_bound(nx, ny, nz, h, e);
     out->ub = out->f + out->route;
+    double inner = 0.0; /* <phi, A m - rho>_h */
+    for (size_t q = 0; q < n; ++q) inner += phi[q] * (d[q] - rho[q]) * h3;
+    out->saddle = out->f + inner;
     free(w);
 }
 

@@ -148,10 +148,10 @@ __global__ void __launch_bounds__(T3) k3_phi(Dims3 d, float tau, float ih, doubl
         }
     }
     if (!CHECK) return;
-    __shared__ double sh[32 * 3];
+    __shared__ double sh[64 * 3];
     __shared__ bool last;
-    double v[3] = {(double)sa, (double)sb, (double)sc};
-    block_sum<3>(v, sh);
+    double v[3];
+    ff_block_sum3(sa, sb, sc, reinterpret_cast<float*>(sh), v);
     if (threadIdx.x == 0) {
         part[blockIdx.x * 3 + 0] = v[0];
         part[blockIdx.x * 3 + 1] = v[1];
@@ -162,12 +162,12 @@ __global__ void __launch_bounds__(T3) k3_phi(Dims3 d, float tau, float ih, doubl
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double t[3] = {0.0, 0.0, 0.0};
+    CSum t[3];
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-        for (int c = 0; c < 3; ++c) t[c] += ((volatile double*)part)[b * 3 + c];
-    block_sum<3>(t, sh);
+        for (int c = 0; c < 3; ++c) t[c].add(((volatile double*)part)[b * 3 + c]);
+    block_csum<3>(t, sh);
     if (threadIdx.x == 0) {
-        *r_out = (t[0] / mu_d + t[1] / tau_d - 2.0 * t[2] / h) * h * h * h;
+        *r_out = (t[0].value() / mu_d + t[1].value() / tau_d - 2.0 * t[2].value() / h) * h * h * h;
         *counter = 0;
     }
 }
@@ -218,8 +218,11 @@ __global__ void k3_prolong(Dims3 c, const float* __restrict__ m1c, const float* 
     m3f[q] = k == f.nz - 1 ? 0.f : v3;
 }
 
-// Certificates: per-block FP64 partials of f, dual, |residual|, |rho| and the
-// maximum of the dual norm of grad phi; the residual (masses) goes to q.
+// Certificates: per-block compensated FP64 partials (s, c) of sum ||m||_p,
+// sum phi rho, sum |e|, sum |rho| and sum phi e (e = rho - div m; unscaled,
+// h^3 applied once at the end), and the maximum of the dual norm of grad phi;
+// the residual (masses) goes to q.
+static constexpr int FIN3_PART = 11;
 template <int NORM>
 __global__ void __launch_bounds__(T3) k3_final_a(Dims3 d, double h, const float* __restrict__ m1,
                                                   const float* __restrict__ m2, const float* __restrict__ m3,
@@ -227,33 +230,34 @@ __global__ void __launch_bounds__(T3) k3_final_a(Dims3 d, double h, const float*
                                                   double* __restrict__ q_out, double* part)
 {
     const long long q = (long long)blockIdx.x * T3 + threadIdx.x;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    CSum v[5];
     double g = 0.0;
     if (q < d.n) {
         int i, j, k;
         node3(d, q, i, j, k);
         const long long sy = d.nx, sz = (long long)d.nx * d.ny;
         const double a1 = fabs((double)m1[q]), a2 = fabs((double)m2[q]), a3 = fabs((double)m3[q]);
-        v[0] = NORM == W1_NORM_L1 ? a1 + a2 + a3
-               : NORM == W1_NORM_L2 ? sqrt(a1 * a1 + a2 * a2 + a3 * a3)
-                                    : fmax(a1, fmax(a2, a3));
-        v[1] = -(double)phi[q] * (double)rho[q];
+        v[0].add(NORM == W1_NORM_L1 ? __dadd_rn(__dadd_rn(a1, a2), a3)
+                 : NORM == W1_NORM_L2 ? sqrt(__dadd_rn(__dadd_rn(__dmul_rn(a1, a1), __dmul_rn(a2, a2)), __dmul_rn(a3, a3)))
+                                      : fmax(a1, fmax(a2, a3)));
+        const double p = phi[q], r = rho[q];
+        v[1].add(__dmul_rn(p, r));
         const double dv = (((double)m1[q] * (i < d.nx - 1) - (i > 0 ? (double)m1[q - 1] : 0.0)) +
                            ((double)m2[q] * (j < d.ny - 1) - (j > 0 ? (double)m2[q - sy] : 0.0)) +
                            ((double)m3[q] * (k < d.nz - 1) - (k > 0 ? (double)m3[q - sz] : 0.0))) / h;
-        const double e = (double)rho[q] - dv;
+        const double e = __dsub_rn(r, dv);
         q_out[q] = e * h * h * h;
-        v[2] = fabs(e);
-        v[3] = fabs((double)rho[q]);
-        const double p = phi[q];
+        v[2].add(fabs(e));
+        v[3].add(fabs(r));
+        v[4].add(__dmul_rn(p, e));
         const double g1 = i < d.nx - 1 ? fabs(((double)phi[q + 1] - p) / h) : 0.0;
         const double g2 = j < d.ny - 1 ? fabs(((double)phi[q + sy] - p) / h) : 0.0;
         const double g3 = k < d.nz - 1 ? fabs(((double)phi[q + sz] - p) / h) : 0.0;
         g = NORM == W1_NORM_L1 ? fmax(g1, fmax(g2, g3))                      // q = infinity
             : NORM == W1_NORM_L2 ? sqrt(g1 * g1 + g2 * g2 + g3 * g3) : g1 + g2 + g3;  // q = 2, q = 1
     }
-    __shared__ double sh[32 * 4];
-    block_sum<4>(v, sh);
+    __shared__ double sh[64 * 5];
+    block_csum<5>(v, sh);
     __shared__ double gm[32];
     g = warp_max(g);
     if ((threadIdx.x & 31) == 0) gm[threadIdx.x >> 5] = g;
@@ -261,13 +265,16 @@ __global__ void __launch_bounds__(T3) k3_final_a(Dims3 d, double h, const float*
     if (threadIdx.x == 0) {
         double mx = 0.0;
         for (int w = 0; w < T3 / 32; ++w) mx = fmax(mx, gm[w]);
-        for (int c = 0; c < 4; ++c) part[blockIdx.x * 5 + c] = v[c];
-        part[blockIdx.x * 5 + 4] = mx;
+        for (int c = 0; c < 5; ++c) {
+            part[blockIdx.x * FIN3_PART + 2 * c] = v[c].s;
+            part[blockIdx.x * FIN3_PART + 2 * c + 1] = v[c].c;
+        }
+        part[blockIdx.x * FIN3_PART + 10] = mx;
     }
 }
 
 struct Stats3Dev {
-    double f, dual, res_l1, rho_l1, gmax, lb, route, ub;
+    double f, dual, res_l1, rho_l1, gmax, lb, route, ub, saddle;
 };
 
 // One block: the sums of the partials, then the dyadic route bound of the
@@ -278,14 +285,28 @@ struct Stats3Dev {
 __global__ void __launch_bounds__(1024) k3_final_b(Dims3 d, double h, const double* part, int nblk, double* q,
                                                     double* q2, Stats3Dev* out)
 {
-    __shared__ double sh[32 * 4];
-    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    __shared__ double sh[64 * 5];
+    CSum t[5];
     double mx = 0.0;
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-        for (int c = 0; c < 4; ++c) t[c] += part[b * 5 + c];
-        mx = fmax(mx, part[b * 5 + 4]);
+        for (int c = 0; c < 5; ++c) {
+            CSum x;
+            x.s = part[b * FIN3_PART + 2 * c];
+            x.c = part[b * FIN3_PART + 2 * c + 1];
+            t[c].add(x);
+        }
+        mx = fmax(mx, part[b * FIN3_PART + 10]);
     }
-    block_sum<4>(t, sh);
+    block_csum<5>(t, sh);
+    __shared__ double tot[5], sad;
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 5; ++c) tot[c] = t[c].value();
+        CSum lag = t[0], pe;
+        pe.s = -t[4].s;
+        pe.c = -t[4].c;
+        lag.add(pe);
+        sad = lag.value();
+    }
     __shared__ double gmx[32];
     mx = warp_max(mx);
     if ((threadIdx.x & 31) == 0) gmx[threadIdx.x >> 5] = mx;
@@ -293,7 +314,8 @@ __global__ void __launch_bounds__(1024) k3_final_b(Dims3 d, double h, const doub
     double* src = q;
     double* dst = q2;
     int cx = d.nx, cy = d.ny, cz = d.nz;
-    double hx = h, hy = h, hz = h, cost = 0.0;
+    double hx = h, hy = h, hz = h;
+    CSum cost;
     for (;;) {
         const int px = cx > 1 && cx % 2 == 0, py = cy > 1 && cy % 2 == 0, pz = cz > 1 && cz % 2 == 0;
         const int odd = (cx > 1 && cx % 2) || (cy > 1 && cy % 2) || (cz > 1 && cz % 2);
@@ -309,7 +331,8 @@ __global__ void __launch_bounds__(1024) k3_final_b(Dims3 d, double h, const doub
                 for (int b = 0; b < by; ++b)
                     for (int a = 0; a < bx; ++a) {
                         const double qa = src[((long long)(bz * K + zc) * cy + (by * J + b)) * cx + (bx * I + a)];
-                        cost = fma(fabs(qa), (a ? hx : 0.0) + (b ? hy : 0.0) + (zc ? hz : 0.0), cost);
+                        if (a | b | zc)
+                            cost.add(__dmul_rn(fabs(qa), (a ? hx : 0.0) + (b ? hy : 0.0) + (zc ? hz : 0.0)));
                         tot += qa;
                     }
             dst[c] = tot;
@@ -325,24 +348,26 @@ __global__ void __launch_bounds__(1024) k3_final_b(Dims3 d, double h, const doub
         if (py) hy *= 2.0;
         if (pz) hz *= 2.0;
     }
-    double pn[3] = {cost, 0.0, 0.0};
+    CSum pn[3];
+    pn[0] = cost;
     for (long long c = threadIdx.x; c < (long long)cx * cy * cz; c += blockDim.x) {
         const double v = src[c];
-        if (v > 0) pn[1] += v;
-        else pn[2] -= v;
+        if (v > 0) pn[1].add(v);
+        else pn[2].add(-v);
     }
-    block_sum<3>(pn, sh);
+    block_csum<3>(pn, sh);
     if (threadIdx.x == 0) {
         double g = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) g = fmax(g, gmx[w]);
         const double h3 = h * h * h;
-        out->f = t[0] * h3;
-        out->dual = t[1] * h3;
-        out->res_l1 = t[2] * h3;
-        out->rho_l1 = t[3] * h3;
+        out->f = tot[0] * h3;
+        out->dual = -tot[1] * h3;
+        out->res_l1 = tot[2] * h3;
+        out->rho_l1 = tot[3] * h3;
+        out->saddle = sad * h3;
         out->gmax = g;
         out->lb = out->dual / fmax(1.0, g);
-        out->route = pn[0] + ((cx - 1) * hx + (cy - 1) * hy + (cz - 1) * hz) * fmax(pn[1], pn[2]);
+        out->route = pn[0].value() + ((cx - 1) * hx + (cy - 1) * hy + (cz - 1) * hz) * fmax(pn[1].value(), pn[2].value());
         out->ub = out->f + out->route;
     }
 }
@@ -614,8 +639,8 @@ __global__ void __launch_bounds__(R3_THREADS, 1) k3_resident(R3Args a)
         one_step(std::true_type{});
         ++it;
         next += a.K;
-        double v[3] = {(double)sa, (double)sb, (double)sc / a.h};
-        block_sum<3>(v, red);
+        double v[3];
+        ff_block_sum3(sa, sb, sc, reinterpret_cast<float*>(red), v);
         if (t == 0) {
             dsmem_st_f64(slots0 + 8u * (rank * 3 + 0), v[0]);
             dsmem_st_f64(slots0 + 8u * (rank * 3 + 1), v[1]);
@@ -624,11 +649,11 @@ __global__ void __launch_bounds__(R3_THREADS, 1) k3_resident(R3Args a)
         if (CL) cg::this_cluster().sync();
         else __syncthreads();
         if (rank == 0 && t == 0) {
-            double tt[3] = {0.0, 0.0, 0.0};
+            CSum tt[3];
             for (int r = 0; r < C; ++r)
-                for (int c = 0; c < 3; ++c) tt[c] += slots[r * 3 + c];
+                for (int c = 0; c < 3; ++c) tt[c].add(slots[r * 3 + c]);
             const double h3 = a.h * a.h * a.h;
-            const double Rk = (tt[0] / (double)mu + tt[1] / (double)tau - 2.0 * tt[2]) * h3;
+            const double Rk = (tt[0].value() / (double)mu + tt[1].value() / (double)tau - 2.0 * (tt[2].value() / a.h)) * h3;
             const int cv = Rk < a.tol && slots[51] == 0.0;
             const int lt = (globaltimer() - reinterpret_cast<const unsigned long long*>(slots)[50]) > a.budget_ns ||
                            slots[51] != 0.0;
@@ -926,8 +951,8 @@ __global__ void __launch_bounds__(R3_THREADS, 1) k3_wide(R3Args a)
         sa = sb = sc = 0.f;
         wstep(std::true_type{});
         ++it;
-        double v[3] = {(double)sa, (double)sb, (double)sc / a.h};
-        block_sum<3>(v, red);
+        double v[3];
+        ff_block_sum3(sa, sb, sc, reinterpret_cast<float*>(red), v);
         if (t == 0) {
             dsmem_st_f64(slots0 + 8u * (rank * 3 + 0), v[0]);
             dsmem_st_f64(slots0 + 8u * (rank * 3 + 1), v[1]);
@@ -936,11 +961,11 @@ __global__ void __launch_bounds__(R3_THREADS, 1) k3_wide(R3Args a)
         if (CL) cg::this_cluster().sync();
         else __syncthreads();
         if (rank == 0 && t == 0) {
-            double tt[3] = {0.0, 0.0, 0.0};
+            CSum tt[3];
             for (int q = 0; q < C; ++q)
-                for (int c = 0; c < 3; ++c) tt[c] += slots[q * 3 + c];
+                for (int c = 0; c < 3; ++c) tt[c].add(slots[q * 3 + c]);
             const double h3 = a.h * a.h * a.h;
-            const double Rk = (tt[0] / (double)mu + tt[1] / (double)tau - 2.0 * tt[2]) * h3;
+            const double Rk = (tt[0].value() / (double)mu + tt[1].value() / (double)tau - 2.0 * (tt[2].value() / a.h)) * h3;
             const int cv = Rk < a.tol && slots[51] == 0.0;
             const int lt = (globaltimer() - reinterpret_cast<const unsigned long long*>(slots)[50]) > a.budget_ns ||
                            slots[51] != 0.0;
@@ -1092,7 +1117,7 @@ static cudaError_t launch_mprime(int norm, const Dims3& d, float mu, float ih, f
 // Device scratch of a 3-D call: mbar planes, partials, counter, R^k, certificate.
 struct Scratch3 {
     float* b = nullptr;      // 3 planes
-    double* part = nullptr;  // 5 per block
+    double* part = nullptr;  // FIN3_PART per block
     unsigned int* counter = nullptr;
     double* r = nullptr;
     double* q = nullptr;  // 2 planes of FP64 residual masses
@@ -1112,7 +1137,7 @@ struct Scratch3 {
     {
         cudaError_t e = cudaMalloc(&b, 3 * n * sizeof(float));
         const long long blocks = (n + T3 - 1) / T3;
-        if (e == cudaSuccess) e = cudaMalloc(&part, blocks * 5 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&part, blocks * FIN3_PART * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&counter, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemset(counter, 0, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMalloc(&r, sizeof(double));
@@ -1468,10 +1493,12 @@ extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, in
     }
     if (potential) W1_CK3(cudaMemcpyAsync(potential, lvl(L - 1, 4), n * sizeof(float), cudaMemcpyDeviceToDevice, s));
     W1_CK3(cudaStreamSynchronize(s));
-    *dist = st.f;
+    *dist = o.estimate == 1 ? st.f : st.saddle;
     if (stats) {
         stats->levels = L;
-        stats->w1 = st.f;
+        stats->w1 = *dist;
+        stats->primal = st.f;
+        stats->saddle = st.saddle;
         stats->dual = st.dual;
         stats->lb = st.lb;
         stats->ub = st.ub;

@@ -198,6 +198,148 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
+// ---------------------------------------------------------------------------
+// Compensated sums
+// ---------------------------------------------------------------------------
+//
+// Knuth's TwoSum gives s = fl(a + b) and the exact rounding error e, so that
+// s + e == a + b exactly.  The explicitly rounded intrinsics keep the compiler
+// from contracting or reordering the steps.  A compensated sum (Neumaier's
+// scheme, with the error term of every addition from TwoSum) carries the
+// running value as the unevaluated pair s + c: its error is about one rounding
+// of the result plus n u^2 sum|x_i|, instead of about n u sum|x_i| for a plain
+// left-to-right sum (u the unit roundoff).
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e)
+{
+    s = __dadd_rn(a, b);
+    const double bb = __dsub_rn(s, a);
+    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+struct CSum {
+    double s = 0.0, c = 0.0;
+    __device__ __forceinline__ void add(double x)
+    {
+        double t, e;
+        two_sum(s, x, t, e);
+        s = t;
+        c = __dadd_rn(c, e);
+    }
+    // adds another compensated sum
+    __device__ __forceinline__ void add(const CSum& o)
+    {
+        double t, e;
+        two_sum(s, o.s, t, e);
+        s = t;
+        c = __dadd_rn(c, __dadd_rn(o.c, e));
+    }
+    __device__ __forceinline__ double value() const { return __dadd_rn(s, c); }
+};
+
+// Compensated sums of N values over the block, in a fixed order (lanes by
+// shuffles, then the warps' sums in warp 0); result valid in thread 0.
+// sh: 64*N doubles.
+template <int N>
+__device__ void block_csum(CSum (&v)[N], double* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            CSum r;
+            r.s = __shfl_xor_sync(FULL, v[c].s, o);
+            r.c = __shfl_xor_sync(FULL, v[c].c, o);
+            v[c].add(r);
+        }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            sh[(warp * N + c) * 2] = v[c].s;
+            sh[(warp * N + c) * 2 + 1] = v[c].c;
+        }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            v[c].s = (lane < nw) ? sh[(lane * N + c) * 2] : 0.0;
+            v[c].c = (lane < nw) ? sh[(lane * N + c) * 2 + 1] : 0.0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                CSum r;
+                r.s = __shfl_xor_sync(FULL, v[c].s, o);
+                r.c = __shfl_xor_sync(FULL, v[c].c, o);
+                v[c].add(r);
+            }
+    }
+    __syncthreads();
+}
+
+// Block sums of three per-thread FP32 values (the terms of the stop test),
+// compensated in float pairs: every addition is a TwoSum whose error goes into
+// the pair's low part, first across the lanes of each warp, then across the
+// warps' pairs in warp 0.  GB300's FP64 rate is a small fraction of its FP32
+// rate, so the block-wide tree stays in FP32 pairs (about 48 significant bits);
+// thread 0 gets each sum as FP64 hi + lo.  sh: at least 32 * 6 floats.
+__device__ __forceinline__ void ff_warp_add(float& hi, float& lo, int o)
+{
+    const float h2 = __shfl_xor_sync(FULL, hi, o), l2 = __shfl_xor_sync(FULL, lo, o);
+    float s, e;
+    two_sum(hi, h2, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(l2, e));
+}
+// one value at a time (few live registers: this runs inside the level kernels)
+__device__ __forceinline__ void ff_warp_sum(float x, float& hi, float& lo)
+{
+    hi = x;
+    lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ff_warp_add(hi, lo, o);
+}
+static __device__ __noinline__ void ff_block_sum3(float a, float b, float c, float* sh, double (&out)[3])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    float hi, lo;
+    __syncthreads();
+    ff_warp_sum(a, hi, lo);
+    if (lane == 0) {
+        sh[warp * 6] = hi;
+        sh[warp * 6 + 1] = lo;
+    }
+    ff_warp_sum(b, hi, lo);
+    if (lane == 0) {
+        sh[warp * 6 + 2] = hi;
+        sh[warp * 6 + 3] = lo;
+    }
+    ff_warp_sum(c, hi, lo);
+    if (lane == 0) {
+        sh[warp * 6 + 4] = hi;
+        sh[warp * 6 + 5] = lo;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int k = 0; k < 3; ++k) {
+            hi = lane < nw ? sh[lane * 6 + 2 * k] : 0.f;
+            lo = lane < nw ? sh[lane * 6 + 2 * k + 1] : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ff_warp_add(hi, lo, o);
+            out[k] = (double)hi + (double)lo;
+        }
+    }
+    __syncthreads();
+}
+
 // Sums N values over the block; result valid in thread 0.  sh: 32*N doubles.
 template <int N>
 __device__ void block_sum(double (&v)[N], double* sh)

@@ -45,8 +45,9 @@ struct Ctl {
     double fpr[W1_MAX_LEVELS];
     int conv[W1_MAX_LEVELS];
     unsigned long long t_start[W1_MAX_LEVELS];
-    // final statistics of the returned finest state
-    double f, dual, res_l1, rho_l1, gmax, route, lb, ub;
+    // final statistics of the returned finest state (saddle: the Lagrangian of
+    // eq. minmax_cp at the state)
+    double f, dual, res_l1, rho_l1, gmax, route, lb, ub, saddle;
 };
 
 // Iteration arguments shared by both level paths.
@@ -211,6 +212,11 @@ cudaError_t launch_pd_poisson(const PdArgs& a, float* dst, float scale, cudaStre
 // phi_out = the Kantorovich potential recovered from phi (Appendix B), sign of Algorithm 1's.
 cudaError_t launch_pd_potential(const PdArgs& a, float* phi_out, cudaStream_t s);
 // Final statistics of a state into ctl (q: FP64 scratch of 2 * nx * ny per pair).
+// The first kernel runs FIN_BLOCKS_PER_PAIR blocks per pair, each leaving
+// FIN_PART_PER_BLOCK doubles of partial sums: final_part_doubles(pairs) =
+// FIN_BLOCKS_PER_PAIR * FIN_PART_PER_BLOCK * pairs.
+static constexpr int FIN_BLOCKS_PER_PAIR = 64;
+static constexpr int FIN_PART_PER_BLOCK = 11;  // five compensated sums (s, c) and a maximum
 cudaError_t launch_final(int norm, const float* m1, const float* m2, const float* phi, const float* rho, int nx,
                          int ny, double h, double* q, double* part, Ctl* ctl, int pairs, cudaStream_t s);
 size_t final_part_doubles(int pairs);

@@ -46,13 +46,15 @@ static constexpr int PREP_THREADS = 256;
 static constexpr int PREP_BLOCKS_PER_PAIR = 64;
 static int prep_blocks_per_pair(int) { return PREP_BLOCKS_PER_PAIR; }
 
-size_t prep_part_doubles(int pairs) { return (size_t)prep_blocks_per_pair(pairs) * pairs * 4; }
+// per block: compensated sums (s, c) of r0, r1 and r0 - r1, then the non-finite count
+static constexpr int PREP_PART_PER_BLOCK = 7;
+size_t prep_part_doubles(int pairs) { return (size_t)prep_blocks_per_pair(pairs) * pairs * PREP_PART_PER_BLOCK; }
 
 __global__ void __launch_bounds__(PREP_THREADS) k_prep_reduce(const float* __restrict__ r0,
                                                               const float* __restrict__ r1, long long n, int nbatch,
                                                               double h, Ctl* ctls, double* part)
 {
-    __shared__ double sh[32 * 4];
+    __shared__ double sh[64 * 3];
     __shared__ bool last;
     const int pair = blockIdx.y;
     Ctl* ctl = ctls + pair;
@@ -66,35 +68,53 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep_reduce(const float* __res
     }
     r0 += (size_t)pair * n;
     r1 += (size_t)pair * n;
-    double* pp = part + (size_t)pair * gridDim.x * 4;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};  // sum r0, sum r1, sum (r0 - r1), non-finite count
+    double* pp = part + (size_t)pair * gridDim.x * PREP_PART_PER_BLOCK;
+    // compensated sums of r0, r1 and r0 - r1 (each difference of two FP32 values is exact in FP64)
+    CSum v[3];
+    unsigned bad = 0;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         float a = r0[k], b = r1[k];
-        if (!isfinite(a) || !isfinite(b)) v[3] += 1.0;
-        v[0] += a;
-        v[1] += b;
-        v[2] += (double)a - (double)b;
+        if (!isfinite(a) || !isfinite(b)) ++bad;
+        v[0].add(a);
+        v[1].add(b);
+        v[2].add(__dsub_rn((double)a, (double)b));
     }
-    block_sum<4>(v, sh);
+    block_csum<3>(v, sh);
+    double nb[1] = {(double)bad};
+    block_sum<1>(nb, sh);
     if (threadIdx.x == 0) {
-        for (int c = 0; c < 4; ++c) pp[blockIdx.x * 4 + c] = v[c];
+        for (int c = 0; c < 3; ++c) {
+            pp[blockIdx.x * PREP_PART_PER_BLOCK + 2 * c] = v[c].s;
+            pp[blockIdx.x * PREP_PART_PER_BLOCK + 2 * c + 1] = v[c].c;
+        }
+        pp[blockIdx.x * PREP_PART_PER_BLOCK + 6] = nb[0];
         __threadfence();
         last = (atomicAdd(&ctl->counter, 1u) == gridDim.x - 1);
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double t[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-        for (int c = 0; c < 4; ++c) t[c] += ((volatile double*)pp)[b * 4 + c];
-    block_sum<4>(t, sh);
+    CSum t[3];
+    double nf[1] = {0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        const volatile double* q = pp + (size_t)b * PREP_PART_PER_BLOCK;
+        for (int c = 0; c < 3; ++c) {
+            CSum x;
+            x.s = q[2 * c];
+            x.c = q[2 * c + 1];
+            t[c].add(x);
+        }
+        nf[0] += q[6];
+    }
+    block_csum<3>(t, sh);
+    block_sum<1>(nf, sh);
     if (threadIdx.x == 0) {
-        double M0 = t[0] * h * h, M1 = t[1] * h * h;
+        const double M0 = t[0].value() * h * h, M1 = t[1].value() * h * h;
         ctl->mass0 = M0;
         ctl->mass1 = M1;
-        ctl->mean = t[2] / (double)n;
-        int bad = (t[3] > 0.0) || !(fabs(M0 - M1) <= 1e-6 * fmax(fabs(M0), fabs(M1)));
-        ctl->error = bad;
+        ctl->mean = t[2].value() / (double)n;
+        int bad_in = (nf[0] > 0.0) || !(fabs(M0 - M1) <= 1e-6 * fmax(fabs(M0), fabs(M1)));
+        ctl->error = bad_in;
         ctl->timeout = 0;
         ctl->counter = 0;
     }
@@ -379,10 +399,10 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
     if (!CHECK) return;
 
     // R^k = (|dm|^2 / mu + |dphi|^2 / tau - 2 <dphi, div dm>) h^2   (eq. pd_stop)
-    __shared__ double sh[32 * 3];
+    __shared__ double sh[64 * 3];
     __shared__ bool last;
-    double v[3] = {(double)sa, (double)sb, (double)sc / P.h};
-    block_sum<3>(v, sh);
+    double v[3];
+    ff_block_sum3(sa, sb, sc, reinterpret_cast<float*>(sh), v);
     const int nblk = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     double* pp = a.part + (size_t)pair * nblk * 3;
@@ -396,13 +416,13 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(StepArgs a)
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double t[3] = {0.0, 0.0, 0.0};
+    CSum t[3];
     for (int b = threadIdx.x; b < nblk; b += blockDim.x)
-        for (int c = 0; c < 3; ++c) t[c] += ((volatile double*)pp)[b * 3 + c];
-    block_sum<3>(t, sh);
+        for (int c = 0; c < 3; ++c) t[c].add(((volatile double*)pp)[b * 3 + c]);
+    block_csum<3>(t, sh);
     if (threadIdx.x == 0) {
         const double h2 = P.h * P.h;
-        const double R = (t[0] / (double)P.mu + t[1] / (double)P.tau - 2.0 * t[2]) * h2;
+        const double R = (t[0].value() / (double)P.mu + t[1].value() / (double)P.tau - 2.0 * (t[2].value() / P.h)) * h2;
         pc->counter = 0;
         if (P.fpr_out) P.fpr_out[pair] = R;
         if (a.use_cond) {
@@ -612,10 +632,10 @@ __global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
         *reinterpret_cast<float4*>(a.phio + g) = make_float4(pv[0], pv[1], pv[2], pv[3]);
     }
     if (!CHECK) return;
-    __shared__ double sh[32 * 3];
+    __shared__ double sh[64 * 3];
     __shared__ bool lastblk;
-    double v[3] = {(double)sa, (double)sb, (double)sc / P.h};
-    block_sum<3>(v, sh);
+    double v[3];
+    ff_block_sum3(sa, sb, sc, reinterpret_cast<float*>(sh), v);
     const int nblk = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     double* pp = a.part + (size_t)pair * nblk * 3;
@@ -629,13 +649,14 @@ __global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
     __syncthreads();
     if (!lastblk) return;
     __threadfence();
-    double tt[3] = {0.0, 0.0, 0.0};
+    CSum tt[3];
     for (int b = t; b < nblk; b += blockDim.x)
-        for (int c = 0; c < 3; ++c) tt[c] += ((volatile double*)pp)[b * 3 + c];
-    block_sum<3>(tt, sh);
+        for (int c = 0; c < 3; ++c) tt[c].add(((volatile double*)pp)[b * 3 + c]);
+    block_csum<3>(tt, sh);
     if (t == 0) {
         const double h2 = P.h * P.h;
-        const double R = (tt[0] / (double)P.mu + tt[1] / (double)P.tau - 2.0 * tt[2]) * h2;
+        const double R =
+            (tt[0].value() / (double)P.mu + tt[1].value() / (double)P.tau - 2.0 * (tt[2].value() / P.h)) * h2;
         pc->counter = 0;
         if (P.fpr_out) P.fpr_out[pair] = R;
         if (a.use_cond) {
@@ -928,8 +949,8 @@ __global__ void __launch_bounds__(NPT >= 8 ? RES_THREADS / 2 : RES_THREADS, 1) k
         }
         ++it;
         if (check) {
-            double v[3] = {(double)sa, (double)sb, (double)sc / P.h};
-            block_sum<3>(v, red);
+            double v[3];
+            ff_block_sum3(sa, sb, sc, reinterpret_cast<float*>(red), v);
             if (threadIdx.x == 0) {
                 dsmem_st_f64(slots0 + 8u * (rank * 3 + 0), v[0]);
                 dsmem_st_f64(slots0 + 8u * (rank * 3 + 1), v[1]);
@@ -938,10 +959,11 @@ __global__ void __launch_bounds__(NPT >= 8 ? RES_THREADS / 2 : RES_THREADS, 1) k
             if (CL) cg::this_cluster().sync();
             else __syncthreads();
             if (rank == 0 && threadIdx.x == 0) {
-                double t[3] = {0.0, 0.0, 0.0};
+                CSum t[3];
                 for (int r = 0; r < C; ++r)
-                    for (int c = 0; c < 3; ++c) t[c] += slots[r * 3 + c];
-                const double Rk = (t[0] / (double)mu + t[1] / (double)tau - 2.0 * t[2]) * P.h * P.h;
+                    for (int c = 0; c < 3; ++c) t[c].add(slots[r * 3 + c]);
+                const double Rk = (t[0].value() / (double)mu + t[1].value() / (double)tau -
+                                   2.0 * (t[2].value() / P.h)) * P.h * P.h;
                 const int cv = Rk < P.tol;
                 const int lt = (globaltimer() - t0) > P.budget_ns;
                 const int stop = P.fixed || cv || lt || it >= cap;
@@ -1230,8 +1252,8 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
         ++it;
         {
             next += P.K;
-            double v[3] = {(double)sa, (double)sb, (double)sc / P.h};
-            block_sum<3>(v, red);
+            double v[3];
+            ff_block_sum3(sa, sb, sc, reinterpret_cast<float*>(red), v);
             if (t == 0) {
                 dsmem_st_f64(slots0 + 8u * (rank * 3 + 0), v[0]);
                 dsmem_st_f64(slots0 + 8u * (rank * 3 + 1), v[1]);
@@ -1240,10 +1262,11 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
             if (CL) cg::this_cluster().sync();
             else __syncthreads();
             if (rank == 0 && t == 0) {
-                double tt[3] = {0.0, 0.0, 0.0};
+                CSum tt[3];
                 for (int r = 0; r < C; ++r)
-                    for (int c = 0; c < 3; ++c) tt[c] += slots[r * 3 + c];
-                const double Rk = (tt[0] / (double)mu + tt[1] / (double)tau - 2.0 * tt[2]) * P.h * P.h;
+                    for (int c = 0; c < 3; ++c) tt[c].add(slots[r * 3 + c]);
+                const double Rk = (tt[0].value() / (double)mu + tt[1].value() / (double)tau -
+                                   2.0 * (tt[2].value() / P.h)) * P.h * P.h;
                 const int cv = Rk < P.tol;
                 const int lt = (globaltimer() - reinterpret_cast<const unsigned long long*>(slots)[50]) > P.budget_ns ||
                                slots[51] != 0.0;
@@ -1577,8 +1600,8 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
         wstep(std::true_type{});
         ++it;
         {
-            double v[3] = {(double)sa, (double)sb, (double)sc / P.h};
-            block_sum<3>(v, red);
+            double v[3];
+            ff_block_sum3(sa, sb, sc, reinterpret_cast<float*>(red), v);
             if (t == 0) {
                 dsmem_st_f64(slots0 + 8u * (rank * 3 + 0), v[0]);
                 dsmem_st_f64(slots0 + 8u * (rank * 3 + 1), v[1]);
@@ -1586,10 +1609,11 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             }
             group_sync();
             if (rank == 0 && t == 0) {
-                double tt[3] = {0.0, 0.0, 0.0};
+                CSum tt[3];
                 for (int q = 0; q < C; ++q)
-                    for (int c = 0; c < 3; ++c) tt[c] += slots[q * 3 + c];
-                const double Rk = (tt[0] / (double)mu + tt[1] / (double)tau - 2.0 * tt[2]) * P.h * P.h;
+                    for (int c = 0; c < 3; ++c) tt[c].add(slots[q * 3 + c]);
+                const double Rk = (tt[0].value() / (double)mu + tt[1].value() / (double)tau -
+                                   2.0 * (tt[2].value() / P.h)) * P.h * P.h;
                 const int cv = Rk < P.tol;
                 const int lt = (globaltimer() - reinterpret_cast<const unsigned long long*>(slots)[50]) > P.budget_ns ||
                                slots[51] != 0.0;
@@ -2025,19 +2049,24 @@ cudaError_t launch_resident(int norm, int cluster, const ResArgs& a, cudaStream_
 
 static constexpr int FIN_THREADS = 256;
 
-// Fixed per pair for the same reason as the prep blocks.
-static constexpr int FIN_BLOCKS_PER_PAIR = 64;
+// FIN_BLOCKS_PER_PAIR blocks per pair whatever the batch (same reason as the
+// prep blocks); each leaves FIN_PART_PER_BLOCK doubles (w1_internal.h).
 static int final_blocks_per_pair(int) { return FIN_BLOCKS_PER_PAIR; }
 
-size_t final_part_doubles(int pairs) { return (size_t)final_blocks_per_pair(pairs) * pairs * 5; }
+size_t final_part_doubles(int pairs) { return (size_t)final_blocks_per_pair(pairs) * pairs * FIN_PART_PER_BLOCK; }
 
+// Per node (FP64 from the FP32 state; e = rho - div m the constraint residual):
+//   ||m(x)||_p, phi rho, |e|, |rho|, phi e, and ||grad phi(x)||_q.
+// Each sum is compensated and left unscaled; h^2 is applied once at the end.
+// Every term except the p = 2 norm and e is exact in FP64 (products and sums
+// of two FP32 values).
 template <int NORM>
 __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict__ m1, const float* __restrict__ m2,
                                                          const float* __restrict__ phi, const float* __restrict__ rho,
                                                          int nx, int ny, double h, double* __restrict__ q,
                                                          double* part, const Ctl* ctls)
 {
-    __shared__ double sh[32 * 4];
+    __shared__ double sh[64 * 5];
     const int pair = blockIdx.y;
     if (ctls && ctls[pair].error == 2) return;
     const long long n = (long long)nx * ny;
@@ -2047,48 +2076,55 @@ __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict
     phi += off;
     rho += off;
     q += 2 * off;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};  // f, dual, res_l1, rho_l1
+    CSum v[5];  // sum ||m||_p, sum phi rho, sum |e|, sum |rho|, sum phi e
     double gm = 0.0;
     const double h2 = h * h;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(k / nx), i = (int)(k - (long long)j * nx);
         const double a1 = (i < nx - 1) ? (double)m1[k] : 0.0;
         const double a2 = (j < ny - 1) ? (double)m2[k] : 0.0;
-        v[0] += (NORM == W1_NORM_L1 ? fabs(a1) + fabs(a2)
-                                    : (NORM == W1_NORM_LINF ? fmax(fabs(a1), fabs(a2)) : sqrt(a1 * a1 + a2 * a2))) * h2;
+        v[0].add(NORM == W1_NORM_L1     ? __dadd_rn(fabs(a1), fabs(a2))
+                 : NORM == W1_NORM_LINF ? fmax(fabs(a1), fabs(a2))
+                                        : sqrt(__dadd_rn(__dmul_rn(a1, a1), __dmul_rn(a2, a2))));
         const double p = phi[k], r = rho[k];
-        v[1] -= p * r * h2;
-        double d = a1 + a2;
-        if (i > 0) d -= (double)m1[k - 1];
-        if (j > 0) d -= (double)m2[k - nx];
-        const double e = r - d / h;
+        v[1].add(__dmul_rn(p, r));
+        double d = __dadd_rn(a1, a2);
+        if (i > 0) d = __dsub_rn(d, (double)m1[k - 1]);
+        if (j > 0) d = __dsub_rn(d, (double)m2[k - nx]);
+        const double e = __dsub_rn(r, __ddiv_rn(d, h));
         q[k] = e * h2;
-        v[2] += fabs(e) * h2;
-        v[3] += fabs(r) * h2;
+        v[2].add(fabs(e));
+        v[3].add(fabs(r));
+        v[4].add(__dmul_rn(p, e));
         const double g1 = (i < nx - 1) ? ((double)phi[k + 1] - p) / h : 0.0;
         const double g2 = (j < ny - 1) ? ((double)phi[k + nx] - p) / h : 0.0;
         const double gq = (NORM == W1_NORM_L1) ? fmax(fabs(g1), fabs(g2))
                           : (NORM == W1_NORM_LINF ? fabs(g1) + fabs(g2) : sqrt(g1 * g1 + g2 * g2));
         gm = fmax(gm, gq);
     }
-    block_sum<4>(v, sh);
+    block_csum<5>(v, sh);
     gm = warp_max(gm);
     __shared__ double shm[32];
     if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = gm;
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) gm = fmax(gm, shm[w]);
-        double* pp = part + ((size_t)pair * gridDim.x + blockIdx.x) * 5;
-        for (int c = 0; c < 4; ++c) pp[c] = v[c];
-        pp[4] = gm;
+        double* pp = part + ((size_t)pair * gridDim.x + blockIdx.x) * FIN_PART_PER_BLOCK;
+        for (int c = 0; c < 5; ++c) {
+            pp[2 * c] = v[c].s;
+            pp[2 * c + 1] = v[c].c;
+        }
+        pp[10] = gm;
     }
 }
 
-// One block per pair: sums the partials, then routes the residual masses q
-// along the dyadic tree (each 2x2 block sends its masses to its first node;
-// offsets (1,0), (0,1) cost one edge of the current spacing, (1,1) two),
-// finishing with a diameter bound on the last grid.  This is an explicit flux
-// carrying rho - div m, hence f + route >= W1 of the discrete problem.
+// One block per pair: sums the partials (compensated), then routes the
+// residual masses q along the dyadic tree (each 2x2 block sends its masses to
+// its first node; offsets (1,0), (0,1) cost one edge of the current spacing,
+// (1,1) two), finishing with a diameter bound on the last grid.  This is an
+// explicit flux carrying rho - div m, hence f + route >= W1 of the discrete
+// problem.  The saddle value is the Lagrangian of eq. minmax_cp at the state,
+// L(m, phi) = f(m) + <phi, div m - rho>_h = h^2 (sum ||m||_p - sum phi e).
 __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, double* q, const double* part,
                                                   int nparts, Ctl* ctls)
 {
@@ -2098,18 +2134,29 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
     const size_t n = (size_t)nx * ny;
     double* src = q + 2 * n * pair;
     double* dst = src + n;
-    part += (size_t)pair * nparts * 5;
-    __shared__ double sh[32 * 4];
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    part += (size_t)pair * nparts * FIN_PART_PER_BLOCK;
+    __shared__ double sh[64 * 5];
+    CSum v[5];
     double gm = 0.0;
     for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
-        for (int c = 0; c < 4; ++c) v[c] += part[b * 5 + c];
-        gm = fmax(gm, part[b * 5 + 4]);
+        for (int c = 0; c < 5; ++c) {
+            CSum x;
+            x.s = part[b * FIN_PART_PER_BLOCK + 2 * c];
+            x.c = part[b * FIN_PART_PER_BLOCK + 2 * c + 1];
+            v[c].add(x);
+        }
+        gm = fmax(gm, part[b * FIN_PART_PER_BLOCK + 10]);
     }
-    block_sum<4>(v, sh);
-    __shared__ double tot[4];
-    if (threadIdx.x == 0)
-        for (int c = 0; c < 4; ++c) tot[c] = v[c];
+    block_csum<5>(v, sh);
+    __shared__ double tot[5], sad;
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 5; ++c) tot[c] = v[c].value();
+        CSum lag = v[0], pe;
+        pe.s = -v[4].s;
+        pe.c = -v[4].c;
+        lag.add(pe);
+        sad = lag.value();
+    }
     gm = warp_max(gm);
     __shared__ double shm[32];
     if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = gm;
@@ -2118,7 +2165,8 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) gm = fmax(gm, shm[w]);
 
     int cx = nx, cy = ny;
-    double hx = h, hy = h, cost = 0.0;
+    double hx = h, hy = h;
+    CSum cost;
     for (;;) {
         const int px = (cx > 1 && (cx & 1) == 0), py = (cy > 1 && (cy & 1) == 0);
         const int stopx = (cx > 1 && (cx & 1)), stopy = (cy > 1 && (cy & 1));
@@ -2133,7 +2181,7 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
             for (int b = 0; b < by; ++b)
                 for (int a = 0; a < bx; ++a) {
                     const double qa = src[(size_t)(by * J + b) * cx + (bx * I + a)];
-                    cost = fma(fabs(qa), w[b][a], cost);
+                    if (a | b) cost.add(__dmul_rn(fabs(qa), w[b][a]));
                     total += qa;
                 }
             dst[k] = total;
@@ -2147,25 +2195,27 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
         if (px) hx *= 2.0;
         if (py) hy *= 2.0;
     }
-    double pos = 0.0, neg = 0.0;
+    CSum ws[3];
+    ws[0] = cost;
     for (int k = threadIdx.x; k < cx * cy; k += blockDim.x) {
         const double x = src[k];
-        if (x > 0) pos += x;
-        else neg -= x;
+        if (x > 0) ws[1].add(x);
+        else ws[2].add(-x);
     }
-    double ws[4] = {cost, pos, neg, 0.0};
-    block_sum<4>(ws, sh);
+    block_csum<3>(ws, sh);
     if (threadIdx.x == 0) {
+        const double h2 = h * h;
         const double diam = (cx - 1) * hx + (cy - 1) * hy;
-        const double route = ws[0] + diam * fmax(ws[1], ws[2]);
-        ctl->f = tot[0];
-        ctl->dual = tot[1];
-        ctl->res_l1 = tot[2];
-        ctl->rho_l1 = tot[3];
+        const double route = ws[0].value() + diam * fmax(ws[1].value(), ws[2].value());
+        ctl->f = tot[0] * h2;
+        ctl->dual = -tot[1] * h2;
+        ctl->res_l1 = tot[2] * h2;
+        ctl->rho_l1 = tot[3] * h2;
+        ctl->saddle = sad * h2;
         ctl->gmax = gm;
         ctl->route = route;
-        ctl->lb = tot[1] / fmax(1.0, gm);
-        ctl->ub = tot[0] + route;
+        ctl->lb = ctl->dual / fmax(1.0, gm);
+        ctl->ub = ctl->f + route;
     }
 }
 

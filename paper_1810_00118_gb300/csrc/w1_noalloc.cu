@@ -2,13 +2,14 @@
 //
 // w1_state_stats allocates its scratch (FP64 residual masses for the route
 // bound, per-block partial sums, a control block) with cudaMalloc on every
-// call.  Some callers cannot do that: code that runs while a stream is being
-// captured into a CUDA graph (cudaMalloc is not allowed there), code that must
-// not trigger the implicit device synchronisation of cudaMalloc/cudaFree in a
-// latency-critical loop, and hosts whose framework owns every byte of device
-// memory through its own pool.  This file gives them w1_state_stats_noalloc:
-// the same kernels, with the scratch in a file-scope static device array that
-// every GPU loading this library holds until the process exits.
+// call.  Some callers cannot do that: code that must not trigger the implicit
+// device synchronisation of cudaMalloc/cudaFree in a latency-critical loop,
+// hosts whose framework owns every byte of device memory through its own pool,
+// and services that run in a fixed, preallocated footprint.  This file gives
+// them w1_state_stats_noalloc: the same kernels, with the scratch in a
+// file-scope static device array that every GPU loading this library holds
+// until the process exits.  The call copies the statistics to the host and
+// synchronises the stream before it returns.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -26,7 +27,10 @@ constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign;
 
 // Layout of the static scratch: control block | partial sums | 2 * n FP64 masses.
 constexpr size_t kCtlBytes = align_up(sizeof(Ctl));
-constexpr size_t kPartBytes = align_up(304 * 5 * sizeof(double));  // >= final_part_doubles(1)
+constexpr size_t kPartBytes = align_up(304 * 5 * sizeof(double));
+// the final statistics' partial sums of one pair must fit their reserve
+static_assert((size_t)FIN_BLOCKS_PER_PAIR * FIN_PART_PER_BLOCK * sizeof(double) <= kPartBytes,
+              "partial-sum reserve smaller than final_part_doubles(1)");
 constexpr size_t kQBytes = 2 * (size_t)W1_NOALLOC_MAX_NODES * sizeof(double);
 constexpr size_t kScratchBytes = kCtlBytes + kPartBytes + kQBytes;
 
@@ -97,7 +101,9 @@ extern "C" w1_status w1_state_stats_noalloc(int nx, int ny, double h, int norm, 
         return na_fail(W1_ERR_CUDA, std::string("w1_state_stats_noalloc: ") + cudaGetErrorString(e));
     }
     std::memset(out, 0, sizeof(*out));
-    out->w1 = c.f;
+    out->w1 = c.saddle;
+    out->primal = c.f;
+    out->saddle = c.saddle;
     out->dual = c.dual;
     out->lb = c.lb;
     out->ub = c.ub;

@@ -303,10 +303,10 @@ __global__ void __launch_bounds__(256) k_pd_update(PdArgs a)
     }
     if (!CHECK) return;
     // G^k = (|dm|^2 / mu + |dphi|^2 / tau + 2 <dphi, dm>) h^2   (eq. pdhg_stop)
-    __shared__ double sh[32 * 3];
+    __shared__ double sh[64 * 3];
     __shared__ bool last;
-    double v[3] = {(double)sa, (double)sb, (double)sc};
-    block_sum<3>(v, sh);
+    double v[3];
+    ff_block_sum3(sa, sb, sc, reinterpret_cast<float*>(sh), v);
     const int nblk = gridDim.x * gridDim.y;
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
     double* pp = a.part + (size_t)pair * nblk * 3;
@@ -321,12 +321,13 @@ __global__ void __launch_bounds__(256) k_pd_update(PdArgs a)
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double tt[3] = {0.0, 0.0, 0.0};
+    CSum tt[3];
     for (int b = t; b < nblk; b += blockDim.x)
-        for (int c = 0; c < 3; ++c) tt[c] += ((volatile double*)pp)[b * 3 + c];
-    block_sum<3>(tt, sh);
+        for (int c = 0; c < 3; ++c) tt[c].add(((volatile double*)pp)[b * 3 + c]);
+    block_csum<3>(tt, sh);
     if (t == 0) {
-        const double G = (tt[0] / (double)a.mu + tt[1] / (double)a.tau + 2.0 * tt[2]) * a.h * a.h;
+        const double G =
+            (tt[0].value() / (double)a.mu + tt[1].value() / (double)a.tau + 2.0 * tt[2].value()) * a.h * a.h;
         pc->counter = 0;
         if (a.g_out) a.g_out[pair] = G;
         if (a.use_cond) {

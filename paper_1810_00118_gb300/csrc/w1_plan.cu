@@ -159,6 +159,7 @@ extern "C" void w1_default_options(w1_options* o)
     o->eager = 0;
     o->tune = 0;
     o->algorithm = 3;
+    o->estimate = 0;
 }
 
 extern "C" const char* w1_last_error(void) { return g_err.c_str(); }
@@ -266,6 +267,7 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
     if (o.max_iters < 1) return fail(W1_ERR_INVALID_ARG, "max_iters must be >= 1");
     if (o.path < 0 || o.path > 3) return fail(W1_ERR_INVALID_ARG, "path must be 0, 1, 2 or 3");
     if (o.tune < 0 || o.tune > 3) return fail(W1_ERR_INVALID_ARG, "tune must be 0, 1, 2 or 3");
+    if (o.estimate < 0 || o.estimate > 1) return fail(W1_ERR_INVALID_ARG, "estimate must be 0 or 1");
     if (o.check_every % (2 * tblock_depth()) != 0)
         return fail(W1_ERR_INVALID_ARG, "check_every must be a multiple of twice the temporal block depth (8)");
     // stop tests happen every K steps, so the cap is a multiple of K
@@ -671,7 +673,9 @@ static void fill_stats(const w1_plan* p, const Ctl* c, w1_stats* st)
         st->cluster[l] = p->lv[l].cluster;
         conv &= c->conv[l] ? 1 : 0;
     }
-    st->w1 = c->f;
+    st->w1 = p->opt.estimate == 1 ? c->f : c->saddle;
+    st->primal = c->f;
+    st->saddle = c->saddle;
     st->dual = c->dual;
     st->lb = c->lb;
     st->ub = c->ub;
@@ -800,7 +804,7 @@ static w1_status results(w1_plan* p, double* dist, w1_stats* stats, int* status)
         const Ctl* c = p->host_ctl + b;
         if (stats) fill_stats(p, c, &stats[b]);
         const w1_status sb = pair_status(p, c);
-        if (dist) dist[b] = sb == W1_ERR_MASS ? NAN : c->f;
+        if (dist) dist[b] = sb == W1_ERR_MASS ? NAN : (p->opt.estimate == 1 ? c->f : c->saddle);
         if (status) status[b] = sb;
         if (worst == W1_OK && sb != W1_OK) worst = sb;
     }
@@ -1426,7 +1430,9 @@ extern "C" w1_status w1_state_stats(int nx, int ny, double h, int norm, const fl
         return fail(W1_ERR_CUDA, std::string("w1_state_stats: ") + cudaGetErrorString(e));
     }
     std::memset(out, 0, sizeof(*out));
-    out->w1 = c.f;
+    out->w1 = c.saddle;
+    out->primal = c.f;
+    out->saddle = c.saddle;
     out->dual = c.dual;
     out->lb = c.lb;
     out->ub = c.ub;

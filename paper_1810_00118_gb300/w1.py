@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
     _fields_ = [("check_every", ctypes.c_int), ("max_iters", ctypes.c_longlong), ("theta", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("time_budget_s", ctypes.c_double), ("path", ctypes.c_int),
                 ("rows_per_thread", ctypes.c_int), ("eager", ctypes.c_int), ("tune", ctypes.c_int),
-                ("algorithm", ctypes.c_int)]
+                ("algorithm", ctypes.c_int), ("estimate", ctypes.c_int)]
 
 
 class LevelChoice(ctypes.Structure):
@@ -73,7 +73,8 @@ class _Stats(ctypes.Structure):
                 ("w1", ctypes.c_double), ("dual", ctypes.c_double), ("lb", ctypes.c_double),
                 ("ub", ctypes.c_double), ("route", ctypes.c_double), ("res_l1", ctypes.c_double),
                 ("rho_l1", ctypes.c_double), ("gmax", ctypes.c_double), ("mass0", ctypes.c_double),
-                ("mass1", ctypes.c_double), ("mass_shift", ctypes.c_double), ("converged", ctypes.c_int)]
+                ("mass1", ctypes.c_double), ("mass_shift", ctypes.c_double), ("converged", ctypes.c_int),
+                ("primal", ctypes.c_double), ("saddle", ctypes.c_double)]
 
 
 @dataclass
@@ -97,6 +98,8 @@ class Stats:
     mass1: float = 0.0
     mass_shift: float = 0.0
     converged: bool = False
+    primal: float = 0.0
+    saddle: float = 0.0
 
     @staticmethod
     def _from(s: _Stats) -> "Stats":
@@ -104,7 +107,7 @@ class Stats:
         return Stats(L, [(s.nx[k], s.ny[k]) for k in range(L)], [s.iters[k] for k in range(L)],
                      [s.fpr[k] for k in range(L)], [s.tol[k] for k in range(L)], [s.path[k] for k in range(L)],
                      [s.cluster[k] for k in range(L)], s.w1, s.dual, s.lb, s.ub, s.route, s.res_l1, s.rho_l1,
-                     s.gmax, s.mass0, s.mass1, s.mass_shift, bool(s.converged))
+                     s.gmax, s.mass0, s.mass1, s.mass_shift, bool(s.converged), s.primal, s.saddle)
 
 
 def _load() -> ctypes.CDLL:

@@ -43,13 +43,33 @@ def test_host_only_entry_points_work_without_gpu():
     assert w1.status_string(99) == "unknown status"
 
 
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a struct of include/w1.h, printed by a C program
+    that gcc compiles against the header (no GPU needed)."""
+    import subprocess
+    import tempfile
+    body = "\n".join(f'printf("%zu\\n", offsetof({struct}, {f}));' for f in fields)
+    src = (f'#include <stdio.h>\n#include <stddef.h>\n#include "w1.h"\n'
+           f'int main(void) {{ printf("%zu\\n", sizeof({struct})); {body} return 0; }}\n')
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        with open(c, "w") as f:
+            f.write(src)
+        subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return [int(x) for x in out]
+
+
 def test_binding_struct_layout_matches_header():
-    """ctypes mirrors of w1_options / w1_stats have the C sizes."""
+    """ctypes mirrors of w1_options / w1_stats / w1_server_config have the C
+    sizes and field offsets (taken from the header by a C compiler)."""
     from paper_1810_00118_gb300 import w1
-    # w1_options: int, long long, 3 doubles, 4 ints -> 4 (+4 pad) + 8 + 24 + 16 = 56
-    assert ctypes.sizeof(w1.Options) == 64
-    # w1_stats: int + 2*16 ints (132, pad to 136) + 16 ll + 2*16 doubles + 2*16 ints + 11 doubles + int (+pad)
-    assert ctypes.sizeof(w1._Stats) == 136 + 128 + 256 + 128 + 88 + 8
+    for struct, py in (("w1_options", w1.Options), ("w1_stats", w1._Stats), ("w1_server_config", w1.ServerConfig)):
+        names = [n for n, _ in py._fields_]
+        got = _c_layout(struct, names)
+        assert ctypes.sizeof(py) == got[0], struct
+        for n, off in zip(names, got[1:]):
+            assert getattr(py, n).offset == off, (struct, n)
 
 
 def test_oracle_is_not_imported_by_the_product():

@@ -227,7 +227,9 @@ def test_solve3d_certificates_match_oracle(w1):
     rho = (rho - rho.mean()).astype(np.float32).astype(np.float64)
     f = host(flux)
     s = d3.stats(rho, f[0], f[1], f[2], host(phi), 1 / 16, L1)
-    assert st.w1 == pytest.approx(s.f, rel=1e-9)
+    assert st.primal == pytest.approx(s.f, rel=1e-9)
+    assert st.saddle == pytest.approx(s.saddle, rel=1e-9)
+    assert st.w1 == st.saddle
     assert st.dual == pytest.approx(s.dual, rel=1e-9)
     assert st.gmax == pytest.approx(s.gmax, rel=1e-9)
     assert st.res_l1 == pytest.approx(s.res_l1, rel=1e-7)

@@ -1,0 +1,154 @@
+"""GPU W1 against converged values that do not depend on the oracle's iteration.
+
+Each case solves on the GPU (FP32 iterates, through the C ABI) at a tolerance
+tighter than eq. stop_tol and compares the reported W1 (the saddle value of
+eq. minmax_cp) with an exact value at relative 1e-4 (the accuracy the build
+targets):
+  - the exact discrete p = 1 and p = infinity values by LP (HiGHS) on grids up
+    to 16 x 16 (the discrete problem is a min-cost flow on the grid graph);
+  - the 1-D closed form sum |C_i| h on 1 x N strips, all norms (Sec. 2);
+  - translated bumps: W1 = (|a| + |b|) h for a unit-mass bump shifted by (a, b)
+    pixels away from the walls (p = 1; axis-aligned shifts for p = 2).
+A last test checks that the FP64 sums are compensated: on inputs built to
+cancel, the GPU's statistics equal the exactly rounded sums (math.fsum) of
+their FP64 terms.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import synth  # noqa: E402
+
+L1, L2, LINF = 1, 2, 3
+
+
+@pytest.fixture(scope="module")
+def w1():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1810_00118_gb300 import w1 as mod
+    return mod
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def stop_tol(n):
+    """eps_L of eq. stop_tol for Algorithm 3."""
+    return 1e-6 / 128 * (512.0 / n) ** 2
+
+
+def solve(w1, r0, r1, norm, levels, tol, **opt):
+    a0 = np.ascontiguousarray(r0, dtype=np.float32)
+    a1 = np.ascontiguousarray(r1, dtype=np.float32)
+    ny, nx = a0.shape
+    with w1.Plan(nx, ny, levels=levels, norm=norm, tol=tol, **opt) as plan:
+        val, st, status = plan.solve(dev(a0), dev(a1), allow=(w1.OK, w1.ERR_NOT_CONVERGED))
+    return val, st, status, a0.astype(np.float64), a1.astype(np.float64)
+
+
+def lp_value(a0, a1, h, norm):
+    from tests import lp_ref
+    rho = a0 - a1
+    rho = rho - rho.mean()
+    return lp_ref.w1_lp(rho, h) if norm == L1 else lp_ref.w1_lp_linf(rho, h)
+
+
+@pytest.mark.parametrize("norm", [L1, LINF])
+@pytest.mark.parametrize("workload,k,n,levels", [(0, 0, 16, 2), (0, 3, 16, 3), (2, 1, 16, 2), (2, 5, 12, 1)])
+def test_matches_exact_lp(w1, norm, workload, k, n, levels):
+    """Small grids against the exact LP of the discrete problem (eq. opt_flux_dis):
+    Gaussian mixtures and ellipse textures, single and multilevel."""
+    pytest.importorskip("scipy")
+    r0, r1 = synth.pair(workload, k, n=n)
+    val, st, status, a0, a1 = solve(w1, r0, r1, norm, levels, stop_tol(n) / 100, max_iters=2_000_000)
+    exact = lp_value(a0, a1, 1.0 / n, norm)
+    assert abs(val - exact) <= 1e-4 * exact, (val, exact, st.iters, status)
+    assert st.lb <= exact * (1 + 1e-6) and st.ub >= exact * (1 - 1e-6)
+
+
+@pytest.mark.parametrize("norm", [L1, L2, LINF])
+@pytest.mark.parametrize("n,horizontal", [(64, True), (128, False), (256, True)])
+def test_strip_closed_form(w1, norm, n, horizontal):
+    """1 x N and N x 1 strips: W1 = sum_i |C_i| h with C_i the cumulative mass
+    difference (the 1-D closed form); unique for every norm."""
+    rng = np.random.default_rng(n + norm)
+    h = 1.0 / n
+    r0 = rng.uniform(0.1, 1.0, n)
+    r1 = rng.uniform(0.1, 1.0, n)
+    r0 /= r0.sum() * h * h
+    r1 /= r1.sum() * h * h
+    shape = (1, n) if horizontal else (n, 1)
+    a0 = r0.astype(np.float32)
+    a1 = r1.astype(np.float32)
+    C = np.cumsum((a0.astype(np.float64) - a1.astype(np.float64)) * h * h)
+    C -= np.arange(1, n + 1) * C[-1] / n  # the solver balances rho by its mean
+    exact = np.abs(C[:-1]).sum() * h
+    val, st, status, _, _ = solve(w1, a0.reshape(shape), a1.reshape(shape), norm, 1, 1e-11,
+                                  max_iters=4_000_000, theta=1.0)
+    assert abs(val - exact) <= 1e-4 * exact, (val, exact, st.iters, status)
+
+
+@pytest.mark.parametrize("norm,shift", [(L1, (3, 2)), (L1, (-5, 4)), (L2, (6, 0)), (L2, (0, -3))])
+def test_translated_bump_64(w1, norm, shift):
+    """A unit-mass bump on 64^2 and its translate by (a, b) pixels (support away
+    from the walls): W1 = (|a| + |b|) h for p = 1, the dual potential
+    -(sgn a x + sgn b y) being feasible and tight; p = 2 for axis shifts."""
+    n = 64
+    h = 1.0 / n
+    a, b = shift
+    X, Y, _ = synth.centres(n, n)
+    bump = np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2) / (2 * 0.08 ** 2))
+    bump[(np.abs(X - 0.5) > 0.3) | (np.abs(Y - 0.5) > 0.3)] = 0.0
+    bump = (bump / (bump.sum() * h * h)).astype(np.float32)
+    r0 = bump
+    r1 = np.roll(np.roll(bump, b, axis=0), a, axis=1)
+    exact = (abs(a) + abs(b)) * h * float(r0.astype(np.float64).sum()) * h * h
+    val, st, status, _, _ = solve(w1, r0, r1, norm, 3, stop_tol(n) / 100, max_iters=2_000_000)
+    assert abs(val - exact) <= 1e-4 * exact, (val, exact, st.iters, status)
+
+
+def _fsum_products(x, y):
+    """Exactly rounded sum of the FP64 products x_i y_i (each product of two FP32
+    values is exact in FP64)."""
+    return math.fsum((x.astype(np.float64) * y.astype(np.float64)).ravel().tolist())
+
+
+def test_compensated_sums_match_fsum(w1):
+    """Cancellation: phi on a pedestal of 1e4 against a zero-mean rho, so the
+    terms phi rho of the dual objective are about 1e4 while their sum is about
+    1e-3 of that.  A plain FP64 sum of 262144 such terms is typically off by
+    ~1e-12 relative; the compensated sums must equal math.fsum of the same FP64
+    terms to within a few units in the last place.  Same for the masses of
+    densities on a pedestal, through a solve."""
+    n = 512
+    h = 1.0 / n
+    rng = np.random.default_rng(11)
+    rho = rng.normal(size=(n, n))
+    rho = (rho - rho.mean()).astype(np.float32)
+    phi = (1e4 + rng.normal(scale=0.1, size=(n, n))).astype(np.float32)
+    z = np.zeros((n, n), dtype=np.float32)
+    g = w1.state_stats(dev(rho), dev(z), dev(z), dev(phi), h, L1)
+    dual = -_fsum_products(phi, rho) * h * h
+    assert abs(g.dual - dual) <= 8 * np.spacing(abs(dual)), (g.dual, dual)
+    # with m = 0 the residual is rho itself: L(0, phi) = dual as well
+    assert abs(g.saddle - dual) <= 8 * np.spacing(abs(dual)), (g.saddle, dual)
+    rho_l1 = math.fsum(np.abs(rho.astype(np.float64)).ravel().tolist()) * h * h
+    assert abs(g.rho_l1 - rho_l1) <= 8 * np.spacing(rho_l1)
+
+    # masses on a pedestal, through the prep kernel of a solve (one test step only)
+    base = synth.pair(2, 0, n=n)
+    r0 = (100.0 + base[0]).astype(np.float32)
+    r1 = (100.0 + base[1]).astype(np.float32)
+    with w1.Plan(n, n, levels=6, norm=L1, max_iters=32) as plan:
+        _, st, status = plan.solve(dev(r0), dev(r1), allow=(w1.OK, w1.ERR_NOT_CONVERGED))
+    m0 = math.fsum(r0.astype(np.float64).ravel().tolist()) * h * h
+    m1 = math.fsum(r1.astype(np.float64).ravel().tolist()) * h * h
+    assert abs(st.mass0 - m0) <= 8 * np.spacing(m0) and abs(st.mass1 - m1) <= 8 * np.spacing(m1)
+    shift = math.fsum((r0.astype(np.float64) - r1.astype(np.float64)).ravel().tolist()) / (n * n)
+    assert abs(st.mass_shift - shift) <= 1e-15 * 100.0

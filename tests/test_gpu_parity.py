@@ -178,9 +178,10 @@ def test_state_stats_match_oracle(w1, norm, shape):
     h = 1.0 / max(shape)
     g = w1.state_stats(dev(rho), dev(m1), dev(m2), dev(phi), h, norm)
     o = oracle.stats(rho, m1, m2, phi, h, norm)
-    for name in ("f", "dual", "res_l1", "rho_l1", "gmax", "route", "lb", "ub"):
-        got = getattr(g, "w1" if name == "f" else name)
+    for name in ("f", "dual", "res_l1", "rho_l1", "gmax", "route", "lb", "ub", "saddle"):
+        got = getattr(g, "primal" if name == "f" else name)
         assert got == pytest.approx(getattr(o, name), rel=1e-9, abs=1e-13), name
+    assert g.w1 == g.saddle
 
 
 # --------------------------------------------------------------------------------------

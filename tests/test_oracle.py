@@ -452,3 +452,81 @@ def test_fpr_stop_meets_paper_grid_error_scale():
     exact = lp_ref.w1_lp(r0 - r1 - (r0 - r1).mean(), h)
     coarse = lp_ref.w1_lp(oracle.restrict(r0 - r1 - (r0 - r1).mean()), 2 * h)
     assert abs(res.w1 - exact) <= 1.5 * abs(exact - coarse) + 1e-4 * exact
+
+
+# --------------------------------------------------------------------------------------
+# The saddle value L(m, phi) of eq. minmax_cp (the default W1 estimate)
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("norm", [L1, L2, LINF])
+def test_saddle_value_equals_primal_on_feasible_flux(norm):
+    """For a flux with div m = rho exactly (the unique 1-D flux m_i = C_i / h of
+    a strip), L(m, phi) = f(m) whatever phi is: the residual term vanishes.
+    A wrong divergence or a dropped boundary term in the residual breaks this."""
+    rng = np.random.default_rng(norm)
+    n = 24
+    h = 1.0 / n
+    rho = rng.normal(size=n)
+    rho -= rho.mean()
+    C = np.cumsum(rho * h * h)
+    m1 = np.zeros((1, n))
+    m1[0, :-1] = C[:-1] / h  # (m_i - m_{i-1}) / h = rho_i
+    m2 = np.zeros((1, n))
+    phi = rng.normal(size=(1, n)) * 5.0
+    s = oracle.stats(rho.reshape(1, n), m1, m2, phi, h, norm)
+    f_direct = np.abs(C[:-1]).sum() * h  # sum |m_i| h^2
+    assert s.f == pytest.approx(f_direct, rel=1e-12)
+    assert s.saddle == pytest.approx(s.f, rel=1e-10, abs=1e-14)
+
+
+def test_saddle_value_at_zero_flux_is_the_dual_objective():
+    """With m = 0, L(0, phi) = -<phi, rho>_h, the dual objective: pins the sign
+    and the rho term of the residual part."""
+    rng = np.random.default_rng(3)
+    ny, nx = 6, 9
+    h = 1.0 / 9
+    rho = rng.normal(size=(ny, nx))
+    rho -= rho.mean()
+    phi = rng.normal(size=(ny, nx))
+    z = np.zeros((ny, nx))
+    s = oracle.stats(rho, z, z, phi, h, L1)
+    expect = -sum(float(p) * float(r) for p, r in zip(phi.ravel(), rho.ravel())) * h * h
+    assert s.saddle == pytest.approx(expect, rel=1e-12)
+    assert s.dual == pytest.approx(expect, rel=1e-12)
+
+
+def test_saddle_value_is_linear_in_phi_shift():
+    """phi -> phi + c changes L by c <1, div m - rho>_h = -c sum(rho) h^2 = 0 for a
+    balanced rho (div of a zero-flux field sums to zero): a constant in phi must
+    not move the estimate (a dropped boundary term in div would)."""
+    rng = np.random.default_rng(4)
+    ny, nx = 7, 5
+    h = 0.2
+    rho = rng.normal(size=(ny, nx))
+    rho -= rho.mean()
+    m1, m2, phi = rng.normal(size=(3, ny, nx))
+    a = oracle.stats(rho, m1, m2, phi, h, L2)
+    b = oracle.stats(rho, m1, m2, phi + 123.0, h, L2)
+    assert b.saddle == pytest.approx(a.saddle, rel=1e-9, abs=1e-9)
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_saddle_value_meets_exact_lp_at_paper_tolerance(n):
+    """At the paper's Alg. 3 tolerance rule (eq. stop_tol) the saddle value is at
+    least ten times closer to the exact p = 1 value (LP) than f(m) of the same
+    state (the Lagrangian corrects f for the residual), and at a tenth of that
+    tolerance it is within relative 1e-4 (eq. stop_tol scales with (512 h)^2,
+    so it is loose on these small grids)."""
+    r0, r1 = synth.pair(2, 0, n=n)
+    h = 1.0 / n
+    eps_L = 1e-6 / 128 * (h * 512) ** 2
+    levels = 2 if n == 16 else 3
+    rho = r0 - r1
+    exact = lp_ref.w1_lp(rho - rho.mean(), h)
+    res = oracle.multilevel(r0, r1, levels=levels, norm=L1, tol=eps_L, alpha=-1.0, stop=oracle.STOP_FPR)
+    assert abs(res.stats.saddle - exact) <= 0.1 * abs(res.stats.f - exact)
+    assert res.w1 == res.stats.saddle
+    assert oracle.multilevel(r0, r1, levels=levels, norm=L1, tol=eps_L, stop=oracle.STOP_FPR,
+                             estimate="primal").w1 == res.stats.f
+    tight_ = oracle.multilevel(r0, r1, levels=levels, norm=L1, tol=eps_L / 10, alpha=-1.0, stop=oracle.STOP_FPR)
+    assert abs(tight_.w1 - exact) <= 1e-4 * exact

@@ -1,9 +1,10 @@
 """w1_state_stats_noalloc: certificate statistics for callers that cannot
-allocate device memory (e.g. while a stream is being captured into a CUDA
-graph, or inside a framework that owns all device memory).  Its scratch is a
-static device array; this test calls it through the C ABI and checks it
-against w1_state_stats, twice in a row with different grids, so that the
-contents a previous call left behind cannot leak into the next result.
+allocate device memory (loops that must not pay cudaMalloc's implicit device
+synchronisation, frameworks that own all device memory through their own
+pools, services with a fixed preallocated footprint).  Its scratch is a static
+device array; this test calls it through the C ABI and checks it against
+w1_state_stats, several calls in a row with different grids and norms, so that
+the contents a previous call left behind cannot leak into the next result.
 
 Collected last on purpose (file name), so a failure here comes after every
 other test has run."""
@@ -15,7 +16,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-FIELDS = ("w1", "dual", "res_l1", "rho_l1", "gmax", "route", "lb", "ub")
+FIELDS = ("w1", "primal", "saddle", "dual", "res_l1", "rho_l1", "gmax", "route", "lb", "ub")
 
 
 def _lib():
@@ -46,8 +47,11 @@ def test_noalloc_stats_match_allocating_stats_two_calls_in_a_row():
     lib = w1.lib()
     stream = torch.cuda.current_stream()
     rng = np.random.default_rng(2024)
-    # a large grid first, then a smaller one: the second call must not see the first's leftovers
-    for (ny, nx), norm in (((512, 512), 1), ((96, 80), 2)):
+    # a large grid first, then smaller ones: no call may see an earlier call's
+    # leftovers; every norm; the maximum size as a square, a 1 x N strip and a
+    # non-square grid; odd sides (the dyadic route of the bound stops early)
+    for (ny, nx), norm in (((512, 512), 1), ((96, 80), 2), ((1, 262144), 3), ((1024, 256), 2), ((37, 53), 3),
+                           ((256, 1024), 1), ((5, 7), 2)):
         t = _state(rng, ny, nx)
         h = 1.0 / max(nx, ny)
         s_ref, ref = _call(lib.w1_state_stats, t, nx, ny, h, norm, stream)
