@@ -130,67 +130,52 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_cost(norm_list, pairs, budget_s=12.0):
-    """Seconds per oracle solve for each norm, from per-level step costs
-    measured here (bounded sample) and the oracle's iteration counts."""
+# eps_L of eq. stop_tol at h = 1/N, scaled per ground norm.  The scales are
+# calibrated against the converged values of tests/golden/converged_512.json:
+# with them every reference pair's reported W1 (the saddle value) lies within
+# relative 1e-4 of its converged value with a margin of at least three (p = 1
+# meets it at the paper's own eps_L; p = 2 needs a tenth of it).
+TOL_SCALE = {1: 1.0, 2: 0.1}
+
+
+def stop_tol(n: int, norm: int) -> float:
+    return 1e-6 / 128 * (512.0 / n) ** 2 * TOL_SCALE[norm]
+
+
+def _oracle_solve(spec):
+    """One whole Algorithm-3 solve by the FP64 oracle (a spawned worker)."""
     import oracle
     import synth
-
-    with open(os.path.join(ROOT, "oracle", "iter_table.json")) as f:
-        table = json.load(f)
-    r0, r1 = synth.pair(WORKLOAD, pairs[0])
+    k, norm, n, levels = spec
+    r0, r1 = synth.pair(WORKLOAD, k, n=n)
     _, _, d0, d1 = synth.to_f32_pair(r0, r1)
-    rho = d0 - d1
-    rho -= rho.mean()
-    pyr = [rho]
-    for _ in range(LEVELS - 1):
-        pyr.append(oracle.restrict(pyr[-1]))
-    pyr = pyr[::-1]
-    per_norm = {}
-    sample = []
-    per_level_budget = budget_s / (len(norm_list) * LEVELS)
-    for norm in norm_list:
-        counts = np.mean([table[f"{norm}"][str(k)] for k in pairs if str(k) in table[f"{norm}"]], axis=0)
-        total = 0.0
-        for lvl, rl in enumerate(pyr):
-            n = rl.shape[0]
-            h = 1.0 / n
-            z = np.zeros_like(rl)
-            # calibrate the number of steps that fit the budget
-            steps, dt = 8, 0.0
-            while True:
-                t0 = time.perf_counter()
-                oracle.cp_iterate(rl, z, z, z, h, norm, steps)
-                dt = time.perf_counter() - t0
-                if dt > per_level_budget / 4 or steps >= counts[lvl]:
-                    break
-                steps *= 2
-            per_step = dt / steps
-            total += per_step * counts[lvl]
-            sample.append(f"p{norm} {n}^2: {steps} steps")
-        per_norm[norm] = total
-    return per_norm, "; ".join(sample)
+    t0 = time.perf_counter()
+    res = oracle.multilevel(d0, d1, levels=levels, norm=norm, tol=stop_tol(n, norm), stop=oracle.STOP_FPR)
+    return norm, time.perf_counter() - t0, res.status
 
 
-def _oracle_cost_worker(spec):
-    norm_list, pairs, budget_s = spec
-    return oracle_cost(norm_list, pairs, budget_s)
-
-
-def oracle_cost_all_cores(norm_list, pairs, budget_s=12.0):
-    """The same measurement in one spawned process per host core, all at once
-    (independent pairs are the oracle's natural parallelism): solves/s of the
-    whole host = processes x norms / mean seconds per solve of each norm under
-    that load."""
+def oracle_whole_solves(seeds, n=N, levels=LEVELS, workers=None):
+    """Whole Algorithm-3 solves of the given pairs, both norms, by the FP64
+    oracle as it stands, at the benchmark's stop rule, one spawned process per
+    host core all at once (independent pairs are the oracle's natural
+    parallelism).  Returns (solves/s of the host, cores, mean seconds per solve
+    for each norm, sample text)."""
     import multiprocessing as mp
 
     import oracle  # builds the oracle library once, before the workers load it
     oracle._load()
-    workers = os.cpu_count() or 1
+    workers = workers or os.cpu_count() or 1
+    jobs = [(k, norm, n, levels) for norm in NORMS for k in seeds]  # p = 1 (the long solves) first
     with mp.get_context("spawn").Pool(workers) as pool:
-        res = pool.map(_oracle_cost_worker, [(tuple(norm_list), list(pairs), budget_s)] * workers)
-    per_solve = float(np.mean([sum(r[0].values()) for r in res]))
-    return workers * len(norm_list) / per_solve, workers, res[0][1]
+        pool.map(_oracle_solve, [(seeds[0], 2, 16, 1)] * workers)  # start every worker
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_solve, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+    per = {f"L{nm}": float(np.mean([t for x, t, _ in res if x == nm])) for nm in NORMS}
+    sample = (f"{len(jobs)} whole Algorithm-3 solves ({len(seeds)} pairs x {len(NORMS)} norms, {n}^2, {levels} levels, "
+              f"the benchmark's stop rule) of pairs {seeds[0]}..{seeds[-1]} (the GPU arm's first timed pairs), "
+              f"{workers} processes at once; value = solves / wall time")
+    return len(jobs) / wall, workers, per, sample
 
 
 def oracle_cost_pdhg(norm_list, budget_s=12.0):
@@ -215,29 +200,29 @@ def oracle_cost_pdhg(norm_list, budget_s=12.0):
 
 
 def run_reference(args):
+    """The FP64 oracle as the reference arm: whole solves of the GPU arm's
+    first timed pairs at the same stop rule, on every host core.  One sample
+    (one solve per pair and norm) covers the run; ms_per_step is the time of
+    that sample divided by the number of steps."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    pairs = list(range(4))
-    sample, cores = None, 1
-    rates = []
-    for s in range(args.warmup + args.steps):
-        rate, cores, sample = oracle_cost_all_cores(NORMS, pairs, budget_s=args.ref_budget)
-        if s >= args.warmup:
-            rates.append(rate)
-    value = float(np.mean(rates))
-    t_step = len(NORMS) / value
+    cores = os.cpu_count() or 1
+    seeds = pair_ids(0, args.warmup, args.batch)[:max(1, min(cores, args.batch))]
+    n = args.ref_n
+    levels = max(1, min(LEVELS, int(np.log2(n)) - 3))
+    value, cores, per, sample = oracle_whole_solves(seeds, n=n, levels=levels, workers=cores)
+    wall = len(seeds) * len(NORMS) / value
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "ellipse_texture_512x512_pairs_6_levels_both_norms", "grid": [N, N],
-                   "levels": LEVELS, "norms": ["L1", "L2"], "stop": "FPR, eq. stop_tol",
-                   "batch_per_norm": args.batch},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{cores} processes at once, each timing the per-level step cost on a bounded "
-                                   "sample (" + sample + ") and scaling it by the oracle's own per-level iteration "
-                                   "counts; value = processes x norms / mean seconds per solve"},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"ellipse_texture_{n}x{n}_pairs_{levels}_levels_both_norms", "grid": [n, n],
+                   "levels": levels, "norms": ["L1", "L2"],
+                   "stop": "FPR R^k < eps_l, eps_L of eq. stop_tol x " + str(TOL_SCALE),
+                   "estimate": "saddle value (Lagrangian of eq. minmax_cp)"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample,
+                         "seconds_per_solve": per},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -264,13 +249,35 @@ def gen_pairs(specs, world=1):
         return list(ex.map(_gen_pair, specs, chunksize=max(1, len(specs) // (4 * workers))))
 
 
+# bytes a solve reads back to the host per pair: the plan's device control
+# block (struct Ctl of w1_internal.h: counters and flags, masses, per-level
+# steps, R^k, flags and start times, the final statistics)
+CTL_BYTES = 560
+
+
+def load_converged():
+    """The stored converged values (tests/golden/converged_512.json, written by
+    oracle/make_converged_table.py from the FP64 oracle and the exact LP)."""
+    path = os.path.join(ROOT, "tests", "golden", "converged_512.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    return {norm: {int(k): float(v["w1"]) for k, v in t.get(f"L{norm}", {}).items()} for norm in NORMS}
+
+
 def run_gpu(args):
     rank, world, local = dist_env()
     B = args.batch
     DEPTH = 2 if (args.mode == "lanes" and args.pipeline) else 1
     total_steps = args.warmup + args.steps
-    # distinct pairs per step and rank, generated before CUDA starts
-    gen = gen_pairs([(WORKLOAD, k, N) for s in range(total_steps) for k in pair_ids(rank, s, B)], world)
+    conv = load_converged() if (rank == 0 and args.algorithm == 3) else None
+    acc_ids = sorted(set(conv[1]) & set(conv[2])) if conv else []
+    # distinct pairs per step and rank (and the reference pairs), generated before CUDA starts
+    specs = [(WORKLOAD, k, N) for s in range(total_steps) for k in pair_ids(rank, s, B)]
+    gen = gen_pairs(specs + [(WORKLOAD, k, N) for k in acc_ids], world)
+    acc_pairs = gen[len(specs):]
 
     import torch
 
@@ -292,12 +299,17 @@ def run_gpu(args):
         host_pairs.append((torch.from_numpy(a0).pin_memory(), torch.from_numpy(a1).pin_memory()))
         dev_pairs.append((torch.from_numpy(a0).cuda(), torch.from_numpy(a1).cuda()))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    ok = (w1.OK, w1.ERR_NOT_CONVERGED)
+    every = (w1.OK, w1.ERR_NOT_CONVERGED, w1.ERR_TIMEOUT, w1.ERR_MASS)  # read every result; only OK counts
+    tol = {norm: (stop_tol(N, norm) if args.algorithm == 3 else 0.0) for norm in NORMS}
+
+    def new_plan(norm, batch=1, tune=None):
+        return w1.Plan(N, N, levels=LEVELS, norm=norm, tol=tol[norm], batch=batch, eager=int(args.eager),
+                       algorithm=args.algorithm, check_every=args.check_every,
+                       tune=args.tune if tune is None else tune)
+
     if args.mode == "lockstep":
         # one batched plan per norm: every launch advances all B pairs together
-        plans = {norm: w1.Plan(N, N, levels=LEVELS, norm=norm, batch=B, eager=int(args.eager), algorithm=args.algorithm,
-                               check_every=args.check_every)
-                 for norm in NORMS}
+        plans = {norm: new_plan(norm, batch=B, tune=0) for norm in NORMS}
     else:
         # lanes: one plan and one stream per pair, all enqueued asynchronously, so
         # every pair moves through its levels at its own pace and the kernels of
@@ -310,33 +322,23 @@ def run_gpu(args):
         # pipelined steps: step s + 1 is enqueued before step s is collected, so
         # lanes that finish early start on the next step's pairs; two sets of
         # plans (and of result events) alternate between consecutive steps
-        plans = {norm: [[w1.Plan(N, N, levels=LEVELS, norm=norm, eager=int(args.eager), algorithm=args.algorithm,
-                                 check_every=args.check_every, tune=args.tune, batch=G)
-                         for _ in range(nlane)] for _ in range(DEPTH)]
-                 for norm in NORMS}
+        plans = {norm: [[new_plan(norm, batch=G) for _ in range(nlane)] for _ in range(DEPTH)] for norm in NORMS}
         lanes = {norm: [torch.cuda.Stream() for _ in range(nlane)] for norm in NORMS}
         done_ev = {norm: [[torch.cuda.Event(enable_timing=True) for _ in range(nlane)] for _ in range(DEPTH)]
                    for norm in NORMS}
     pair_ms = []
-    in_dev = [[torch.empty((B, N, N), device="cuda") for _ in range(2)] for _ in range(DEPTH)]
     ready_ev = [torch.cuda.Event(enable_timing=True) for _ in range(DEPTH)]
     pending = {}
 
-    def submit(s, host=False):
+    def submit(s, pair_set=None):
         q = s % DEPTH
         flush.fill_(float(s))
-        if host:
-            # end to end: copy this step's inputs from pinned host memory first
-            in_dev[q][0].copy_(host_pairs[s][0], non_blocking=True)
-            in_dev[q][1].copy_(host_pairs[s][1], non_blocking=True)
-            t0, t1 = in_dev[q]
-        else:
-            t0, t1 = dev_pairs[s]
+        t0, t1 = dev_pairs[s] if pair_set is None else pair_set
         if args.mode == "lockstep":
             out = []
             for norm in NORMS:
-                v, st, _, _ = plans[norm].solve_batch(t0, t1, stream=stream, allow=ok)
-                out.append((v, st))
+                v, st, ps, _ = plans[norm].solve_batch(t0, t1, stream=stream, allow=every)
+                out.append((v, st, ps))
             pending[s] = out
             return
         ready_ev[q].record(stream)
@@ -356,14 +358,15 @@ def run_gpu(args):
         q = s % DEPTH
         out = []
         for norm in NORMS:
-            vals, sts = [], []
+            vals, sts, pss = [], [], []
             for b in range(nlane):
                 done_ev[norm][q][b].synchronize()
-                v, st, _, _ = plans[norm][q][b].results(allow=ok)
+                v, st, ps, _ = plans[norm][q][b].results(allow=every)
                 vals.extend(v)
                 sts.extend(st)
+                pss.extend(ps)
                 pair_ms.extend([ready_ev[q].elapsed_time(done_ev[norm][q][b])] * G)
-            out.append((vals, sts))
+            out.append((vals, sts, pss))
         return out
 
     def join_lanes(s):
@@ -373,12 +376,12 @@ def run_gpu(args):
                 for b in range(nlane):
                     stream.wait_event(done_ev[norm][s % DEPTH][b])
 
-    def run_steps(first, last, host=False, out=None, step_ms=None):
+    def run_steps(first, last, out=None, step_ms=None):
         """Steps first .. last - 1, step s + 1 submitted before step s is collected."""
         t_sub = {}
         for s in range(first, last):
             t_sub[s] = time.perf_counter()
-            submit(s, host)
+            submit(s)
             if s - first >= DEPTH - 1 and DEPTH > 1 and s > first:
                 r = collect(s - 1)
                 if out is not None:
@@ -401,10 +404,11 @@ def run_gpu(args):
 
     def level_launches(p, k):
         # resident: one launch; streaming: one per step (path 2) or per 4 steps
-        # (path 3, temporal blocking), plus one decide kernel per 32 steps
+        # (path 3, temporal blocking), plus one decide kernel per K steps
         if p == 1:
             return 1
-        return (k if p == 2 else k // 4) + k // 32
+        K = args.check_every or 32
+        return (k if p == 2 else k // 4) + k // K
 
     def launches(sts):
         # prep 2, restrictions, level starts, prolongations, final 2, and the levels
@@ -443,22 +447,79 @@ def run_gpu(args):
     # device time on the launching stream (every lane joins it), max over ranks
     elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
     wall = max_over_ranks(wall)
-    solves = args.steps * len(NORMS) * B * world
+    n_ok = sum(1 for step in results for _, _, pss in step for x in pss if x == w1.OK)
+    not_ok = sum(1 for step in results for _, _, pss in step for x in pss if x != w1.OK)
+    solves = max_over_ranks(float(n_ok)) * world if world > 1 else n_ok
     value = solves / elapsed
-    n_launch = sum(launches(sts) for step in results for _, sts in step)
+    n_launch = sum(launches(sts) for step in results for _, sts, _ in step)
     pair_lat = list(pair_ms)
 
-    # end to end through the host entry point
+    # end to end through the C ABI with host buffers: w1_solve_host (host
+    # densities in pinned memory, copies to the device, the solve and the W1
+    # read-back inside the call), one plan and stream per pair as above, the
+    # calls issued from host threads (the binding releases the GIL in the call)
     e2e = None
-    if not args.no_e2e:
-        barrier()
-        ev0.record(stream)
-        run_steps(args.warmup, total_steps, host=True)
-        ev1.record(stream)
-        barrier()
-        e2e_el = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
-        e2e = {"value": solves / e2e_el, "unit": "solves/s",
-               "h2d_bytes_per_step": 2 * N * N * 4 * B, "d2h_bytes_per_step": 552 * B * len(NORMS)}
+    if not args.no_e2e and args.mode == "lanes" and G == 1:
+        import concurrent.futures as cf
+        jobs = [(norm, b) for norm in NORMS for b in range(nlane)]
+        nthr = min(len(jobs), args.e2e_threads)
+        host_np = [(h0.numpy(), h1.numpy()) for h0, h1 in host_pairs]
+
+        def worker(tid, s, out):
+            for norm, b in jobs[tid::nthr]:
+                v, st, status = plans[norm][0][b].solve_host(host_np[s][0][b], host_np[s][1][b],
+                                                             stream=lanes[norm][b], allow=every)
+                out.append(status)
+
+        def e2e_step(s, ex):
+            flush.fill_(float(s))
+            torch.cuda.synchronize()
+            outs = [[] for _ in range(nthr)]
+            list(ex.map(lambda t: worker(t, s, outs[t]), range(nthr)))
+            return [x for o in outs for x in o]
+
+        with cf.ThreadPoolExecutor(max_workers=nthr) as ex:
+            e2e_step(0, ex)  # warm-up: the plans' input buffers
+            barrier()
+            t0e = time.perf_counter()
+            sts_e2e = [e2e_step(s, ex) for s in range(args.warmup, total_steps)]
+            barrier()
+            e2e_wall = max_over_ranks(time.perf_counter() - t0e)
+        ok_e2e = sum(1 for st_ in sts_e2e for x in st_ if x == w1.OK)
+        e2e = {"value": (ok_e2e * world) / e2e_wall, "unit": "solves/s",
+               "h2d_bytes_per_step": 2 * N * N * 4 * B * len(NORMS),
+               "d2h_bytes_per_step": CTL_BYTES * B * len(NORMS),
+               "path": f"w1_solve_host (C ABI, host densities in pinned memory) from {nthr} host threads, one plan "
+                       "and stream per pair; wall clock around each step's calls",
+               "not_ok": sum(1 for st_ in sts_e2e for x in st_ if x != w1.OK)}
+
+    # accuracy: the reference pairs solved by the same plans (lanes) and compared
+    # with their stored converged values (FP64 oracle / exact LP)
+    accuracy = None
+    if conv and acc_ids and args.mode == "lanes" and G == 1:
+        a0 = torch.from_numpy(np.stack([x[0] for x in acc_pairs])).cuda()
+        a1 = torch.from_numpy(np.stack([x[1] for x in acc_pairs])).cuda()
+        errs, prim, sts_acc = {}, {}, {}
+        for norm in NORMS:
+            e, pe, ss = [], [], []
+            for i, k in enumerate(acc_ids):
+                p = plans[norm][0][i % nlane]
+                p.solve_async(a0[i], a1[i], stream=lanes[norm][i % nlane])
+                lanes[norm][i % nlane].synchronize()
+                v, st, ps, _ = p.results(allow=every)
+                ref = conv[norm][k]
+                e.append(abs(v[0] - ref) / ref)
+                pe.append(abs(st[0].primal - ref) / ref)
+                ss.append(ps[0])
+            errs[f"L{norm}"], prim[f"L{norm}"], sts_acc[f"L{norm}"] = e, pe, ss
+        accuracy = {"max_rel_err_vs_converged": {k: float(max(v)) for k, v in errs.items()},
+                    "rel_err_vs_converged": errs,
+                    "primal_max_rel_err_vs_converged": {k: float(max(v)) for k, v in prim.items()},
+                    "pairs": acc_ids, "statuses": sts_acc,
+                    "reference": "tests/golden/converged_512.json (p = 1: exact LP; p = 2: FP64 oracle at "
+                                 "eps_L / 1e4), written by oracle/make_converged_table.py",
+                    "what": "reported W1 (saddle value) of each reference pair against its converged value; "
+                            "primal: f(m) of the same solves"}
 
     # latency of one solve with the GPU otherwise idle: one pair at a time through
     # the blocking entry point, CUDA events around each solve
@@ -466,14 +527,13 @@ def run_gpu(args):
     tuned = args.algorithm == 3  # the latency-tuned plan (tune = 1) beside the default one
     for norm in (NORMS if args.solo > 0 else ()):
         for tune in ((0, 1) if tuned else (0,)):
-            with w1.Plan(N, N, levels=LEVELS, norm=norm, algorithm=args.algorithm, check_every=args.check_every,
-                         tune=tune) as p1:
+            with new_plan(norm, tune=tune) as p1:
                 ts = []
                 for k in range(args.solo):
                     t0s, t1s = dev_pairs[k % total_steps][0][k % B], dev_pairs[k % total_steps][1][k % B]
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    p1.solve(t0s, t1s, stream=stream, allow=ok)
+                    p1.solve(t0s, t1s, stream=stream, allow=every)
                     e1.record(stream)
                     torch.cuda.synchronize()
                     ts.append(e0.elapsed_time(e1))
@@ -482,10 +542,22 @@ def run_gpu(args):
     solo["what"] = ("one solve with the GPU otherwise idle (w1_solve, CUDA events); _latency_tuned: the plan's "
                     "kernels picked by the autotuner for one solve alone (tune = 1)")
 
+    for p in plans.values():
+        for q in (p if isinstance(p, list) else [p]):
+            for r in (q if isinstance(q, list) else [q]):
+                r.close()
+    torch.cuda.synchronize()
+
     # rooflines (the dominant on-chip kernel; the streaming kernels at 8192^2)
     roof = None
     if not args.no_roofline:
         roof = roofline(w1, torch, stream, args)
+
+    # serving (Poisson arrivals of mixed sizes) and the mixed-size batch, short
+    serving = mixed = None
+    if rank == 0 and not args.no_extras and args.algorithm == 3:
+        serving = serve_summary(w1, torch, args)
+        mixed = mixed_summary(w1, torch, args)
 
     line = None
     if rank == 0:
@@ -494,12 +566,17 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 iterates, f64 reductions", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 iterates, compensated f64 reductions",
+            "data": "synthetic",
             "config": {"workload": "ellipse_texture_512x512_pairs_6_levels_both_norms", "grid": [N, N],
                        "levels": LEVELS, "norms": ["L1", "L2"],
                        "algorithm": {3: "Algorithm 3 (multilevel Chambolle-Pock)",
                                      4: "Algorithm 4 (multilevel prox-PDHG)"}[args.algorithm],
-                       "stop": "eq. stop_tol for the algorithm",
+                       "stop": ("FPR R^k < eps_l (eq. pd_stop), eps_l = eps_L (h_l/h)^-1, eps_L of eq. stop_tol x "
+                                + json.dumps({f"L{k}": v for k, v in TOL_SCALE.items()}))
+                       if args.algorithm == 3 else "eq. stop_tol for Algorithm 4",
+                       "tol": {f"L{k}": v for k, v in tol.items()},
+                       "estimate": "saddle value: Lagrangian of eq. minmax_cp at the returned pair",
                        "batch_per_norm": B, "mode": args.mode,
                        "pairs_per_lane": args.lane_batch if args.mode == "lanes" else B,
                        "l2": "flushed before every step (256 MiB write, inside the timed region); each step's "
@@ -507,6 +584,9 @@ def run_gpu(args):
                        "pipelined_steps": DEPTH if args.mode == "lanes" else 1,
                        "parallelism": f"replicas x{world}"},
             "timer": {"kind": "CUDA events on the launching stream, every lane joined to it", "wall_s": wall},
+            "solves_counted": "status W1_OK only", "not_ok": not_ok,
+            "max_rel_err_vs_converged": accuracy["max_rel_err_vs_converged"] if accuracy else None,
+            "accuracy": accuracy,
             "batch_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                  "what": "one step (B pairs, both norms) / 2, submit to W1 values on the host "
                                          "(with pipelined steps the next step is already running meanwhile)"},
@@ -515,8 +595,9 @@ def run_gpu(args):
                                  "what": "per pair: its step's submission to the end of its solve on its "
                                          "stream (CUDA events)"}
                                 if pair_lat else None),
+            "serving": serving,
+            "mixed": mixed,
             "iters_first_pair": iters,
-            "w1_first_step": [[float(x) for x in v] for v, _ in results[0]],
             "gpu_launches": n_launch,
             "e2e": e2e,
             "roofline": roof,
@@ -527,19 +608,12 @@ def run_gpu(args):
             line["cpu_baseline"] = {"value": len(NORMS) / sum(per_norm.values()), "unit": "solves/s", "cores": 1,
                                     "kind": "oracle", "sample": "FP64 prox-PDHG oracle (numpy, one thread): " + sample}
         elif not args.no_cpu_baseline:
-            per_norm, sample = oracle_cost(NORMS, list(range(4)), budget_s=args.ref_budget)
-            one = len(NORMS) / sum(per_norm.values())
-            cpu_v, cores, _ = oracle_cost_all_cores(NORMS, list(range(4)), budget_s=args.ref_budget)
+            cores = os.cpu_count() or 1
+            seeds = pair_ids(0, args.warmup, B)[:min(cores, B)]
+            cpu_v, cores, per, sample = oracle_whole_solves(seeds, workers=cores)
             line["cpu_baseline"] = {"value": cpu_v, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                                    "sample": f"{cores} processes at once, each timing the per-level step cost on a "
-                                              "bounded sample (" + sample + ") and scaling it by the oracle's own "
-                                              "per-level iteration counts",
-                                    "one_core_value": one}
+                                    "sample": sample, "seconds_per_solve": per}
         print(json.dumps(line), flush=True)
-    for p in plans.values():
-        for q in (p if isinstance(p, list) else [p]):
-            for r in (q if isinstance(q, list) else [q]):
-                r.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
@@ -622,6 +696,24 @@ def roofline(w1, torch, stream, args):
            "steps_per_launch": kr, "flops_per_node_step": FLOPS_PER_NODE_STEP[1],
            "note": "issue and barrier-latency bound: no HBM traffic per step; traffic is per launch of "
                    f"{kr} steps (the level is loaded once)"}
+    # the same per-step time against 28 algorithmic bytes per node and step (the
+    # measure of the streaming kernels; this level is on chip, so it is not DRAM traffic)
+    res["bytes_per_node_step"] = 28
+    res["achieved_alg_GBps"] = 28.0 * nr * nr / (ms_step * 1e-3) / 1e9
+    res["frac_alg_bytes_vs_hbm"] = res["achieved_alg_GBps"] / peak
+    del rr
+    # the wide on-chip kernel: the 512^2 level on a 16-CTA cluster
+    nw = 512
+    hw = 1.0 / nw
+    rw = torch.randn((nw, nw), device="cuda") * 0.1
+    rw -= rw.mean()
+    muw = float(np.float32(0.5 * hw / (2 * np.sqrt(2.0))))
+    msw = _time_steps(w1, torch, stream, rw, hw, 1, muw, 1, 64, 64 + 500, cluster=16)
+    res["wide"] = {"kernel": "k_resident_wide (512^2 level, cluster of 16 CTAs, p = 1)", "us_per_step": msw * 1e3,
+                   "achieved_alg_GBps": 28.0 * nw * nw / (msw * 1e-3) / 1e9,
+                   "frac_alg_bytes_vs_hbm": 28.0 * nw * nw / (msw * 1e-3) / 1e9 / peak,
+                   "achieved_TFLOPs": FLOPS_PER_NODE_STEP[1] * nw * nw / (msw * 1e-3) / 1e12,
+                   "frac_alu": FLOPS_PER_NODE_STEP[1] * nw * nw / (msw * 1e-3) / 1e12 / fpeak}
     res["streaming"] = out["k_step"]
     res["temporal_blocking"] = out["k_tblock"]
     return res
@@ -643,8 +735,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--roof-n", type=int, default=8192)
     ap.add_argument("--roof-iters", type=int, default=96)
-    ap.add_argument("--ref-budget", type=float, default=12.0)
+    ap.add_argument("--ref-budget", type=float, default=12.0, help="Algorithm 4 CPU baseline: seconds")
+    ap.add_argument("--ref-n", type=int, default=N, help="oracle arm: grid side of the whole solves")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-threads", type=int, default=64, help="e2e: host threads calling w1_solve_host")
+    ap.add_argument("--no-extras", action="store_true", help="skip the short serving and mixed-batch legs")
     ap.add_argument("--solo", type=int, default=8, help="pairs solved one at a time for the latency figure")
     ap.add_argument("--tune", type=int, default=0, choices=[0, 1, 2, 3],
                     help="lanes: per-level kernel choice (0 fixed rules, 1 latency, 3 SM-time; see w1_options.tune)")
@@ -675,6 +770,9 @@ def main():
     ap.add_argument("--mixed-norm", type=int, default=2, help="mixed-size batch: ground norm")
     ap.add_argument("--mixed-modes", default="loop,lanes,lockstep,lockstep-tuned,persistent")
     ap.add_argument("--mixed-spec", default="", help="mixed-size batch override, e.g. 64:128,128:96")
+    ap.add_argument("--mixed-passes", type=int, default=2, help="default line: timed passes of the mixed batch")
+    ap.add_argument("--serve-summary", default="30:300,300:2000",
+                    help="default line: serving rates and request counts, rate:requests,...")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -1006,9 +1104,10 @@ def serve_pool(torch, rank=0, per_size=(24, 16, 8, 4)):
     return pool
 
 
-def serve_run(w1, srv, pool, rate, n_req, seed):
+def serve_run(w1, srv, pool, rate, n_req, seed, tol_of=None):
     """Poisson arrivals at `rate` req/s of mixed sizes and norms; returns
-    (p50 ms, p99 ms, completed/s, statuses)."""
+    (p50 ms, p99 ms, completed/s, statuses).  tol_of(n, norm): the request's
+    eps_L (None: the library's default, eq. stop_tol)."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, n_req)
     sizes = rng.choice(SERVE_SIZES, size=n_req, p=SERVE_PROBS)
@@ -1026,7 +1125,8 @@ def serve_run(w1, srv, pool, rate, n_req, seed):
             time.sleep(min(d, 0.002))
         lst = pool[int(sizes[k])]
         a, b = lst[picks[k] % len(lst)]
-        tickets.append(srv.submit(a, b, norm=int(norms[k])))
+        tol = tol_of(int(sizes[k]), int(norms[k])) if tol_of else 0.0
+        tickets.append(srv.submit(a, b, norm=int(norms[k]), tol=tol))
     lat, statuses = [], []
     for t in tickets:
         while True:
@@ -1039,6 +1139,118 @@ def serve_run(w1, srv, pool, rate, n_req, seed):
     t_end = time.perf_counter()
     lat = np.array(lat) * 1e3
     return float(np.percentile(lat, 50)), float(np.percentile(lat, 99)), n_req / (t_end - t0), statuses
+
+
+def serve_summary(w1, torch, args):
+    """Short serving run for the default line: Poisson arrivals of the mixed
+    sizes {128^2 .. 1024^2} at 0.4/0.3/0.2/0.1, both norms, 40 GB budget,
+    requests at the benchmark's calibrated tolerance; one low rate and one
+    high rate with at least 2000 requests."""
+    pool = serve_pool(torch)
+    out = []
+    with w1.Server(hbm_budget_bytes=40 << 30, max_slots=args.slots, max_batch=args.serve_batch,
+                   latency_below=args.latency_below) as srv:
+        if args.latency_below > 0:
+            for size in SERVE_SIZES:
+                for norm in NORMS:
+                    a0, a1 = pool[size][0]
+                    srv.wait(srv.submit(a0, a1, norm=norm, tol=stop_tol(size, norm)))
+        serve_run(w1, srv, pool, 1000.0, 32, seed=1, tol_of=stop_tol)
+        for rate, n_req in ((float(r), int(q)) for r, q in (x.split(":") for x in args.serve_summary.split(","))):
+            p50, p99, thr, sts = serve_run(w1, srv, pool, rate, n_req, seed=int(rate), tol_of=stop_tol)
+            out.append({"rate_req_s": rate, "requests": n_req, "p50_ms": p50, "p99_ms": p99, "solves_per_s": thr,
+                        "not_ok": sum(1 for x in sts if x != w1.OK)})
+        info = srv.info()
+    return {"rates": out, "p50_ms": out[-1]["p50_ms"], "p99_ms": out[-1]["p99_ms"],
+            "solves_per_s": out[-1]["solves_per_s"], "requests_at_headline_rate": out[-1]["requests"],
+            "sizes": SERVE_SIZES, "probs": SERVE_PROBS, "budget_GiB": 40, "slots": args.slots,
+            "latency_below": args.latency_below, "evictions": info.get("evictions"),
+            "what": "submit to completion (w1_poll_latency), Poisson arrivals; headline = the last rate"}
+
+
+def mixed_summary(w1, torch, args):
+    """The mixed-size batch (128 x 64^2 + 96 x 128^2 + 32 x 256^2, Gaussian
+    mixtures, p = 2) per pass: one persistent launch (with the classes that do
+    not fit one CTA beside it), per-size batched plans, and a loop of single
+    solves; CUDA events on the launching stream, L2 flushed before each pass."""
+    import synth
+    stream = torch.cuda.current_stream()
+    norm = args.mixed_norm
+    passes = 1 + args.mixed_passes
+    data = []
+    for s in range(passes):
+        per = []
+        for ci, (n, B, _) in enumerate(MIXED):
+            r = [synth.pair(3, 100000 * s + 1000 * ci + k, n=n) for k in range(B)]
+            per.append(tuple(torch.from_numpy(np.ascontiguousarray(np.stack([x[j] for x in r]), dtype=np.float32)).cuda()
+                             for j in (0, 1)))
+        data.append(per)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    every = (w1.OK, w1.ERR_NOT_CONVERGED, w1.ERR_TIMEOUT, w1.ERR_MASS)
+    total = sum(B for _, B, _ in MIXED)
+    out, first = {}, None
+    for mode in ("persistent", "lockstep", "loop"):
+        if mode == "persistent":
+            obj = w1.Mixed([(n, n, B) for n, B, _ in MIXED], norm=norm)
+        elif mode == "lockstep":
+            obj = [w1.Plan(n, n, levels=L, norm=norm, batch=B) for n, B, L in MIXED]
+            lanes = [torch.cuda.Stream() for _ in MIXED]
+        else:
+            obj = [w1.Plan(n, n, levels=L, norm=norm) for n, _, L in MIXED]
+
+        def one_pass(s):
+            flush.fill_(float(s))
+            vals, sts = [], []
+            if mode == "persistent":
+                obj.solve_async([d[0] for d in data[s]], [d[1] for d in data[s]], stream=stream)
+                stream.synchronize()
+                for ci in range(len(MIXED)):
+                    v, _, ps, _ = obj.results(ci, allow=every)
+                    vals.extend(v)
+                    sts.extend(ps)
+            elif mode == "lockstep":
+                ready = torch.cuda.Event()
+                ready.record(stream)
+                for ci in range(len(MIXED)):
+                    lanes[ci].wait_event(ready)
+                    obj[ci].solve_async(data[s][ci][0], data[s][ci][1], stream=lanes[ci])
+                for ci in range(len(MIXED)):
+                    stream.wait_stream(lanes[ci])
+                    lanes[ci].synchronize()
+                    v, _, ps, _ = obj[ci].results(allow=every)
+                    vals.extend(v)
+                    sts.extend(ps)
+            else:
+                for ci, (n, B, _) in enumerate(MIXED):
+                    for b in range(B):
+                        v, _, st_ = obj[ci].solve(data[s][ci][0][b], data[s][ci][1][b], stream=stream, allow=every)
+                        vals.append(v)
+                        sts.append(st_)
+            return vals, sts
+
+        one_pass(0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = [one_pass(s) for s in range(1, passes)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        vals = np.array([v for r in res for v in r[0]])
+        n_ok = sum(1 for r in res for x in r[1] if x == w1.OK)
+        if first is None:
+            first = vals
+        out[mode] = {"solves_per_s": n_ok / (ms / 1e3), "ms_per_pass": ms / (passes - 1),
+                     "max_rel_diff_vs_persistent": float(np.max(np.abs(vals - first) / np.abs(first)))}
+        if mode == "persistent":
+            out[mode]["persistent_classes"] = [obj.persistent(c) for c in range(len(MIXED))]
+            obj.close()
+        else:
+            for p in obj:
+                p.close()
+    return {"workload": ", ".join(f"{B} x {n}^2 ({L} levels)" for n, B, L in MIXED), "norm": f"L{norm}",
+            "pairs_per_pass": total, "passes": passes - 1, "modes": out,
+            "speedup_vs_loop": out["persistent"]["solves_per_s"] / out["loop"]["solves_per_s"]}
 
 
 def run_serve(args):

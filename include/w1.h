@@ -43,6 +43,8 @@ extern "C" {
 #endif
 
 #define W1_MAX_LEVELS 16
+#define W1_TILE_VARIANTS 5 /* tile shapes of the temporally blocked streaming kernel */
+#define W1_TUNE_MAX_CANDIDATES 16 /* configurations w1_autotune_level reports at most */
 
 typedef enum {
     W1_NORM_L1 = 1,  /* p = 1, anisotropic: ||m(x)|| = |m1| + |m2|, componentwise shrink */
@@ -92,6 +94,12 @@ typedef struct {
                               stop G^k < eps_l of eq. pdhg_stop; mu = tau = theta, the paper's
                               1/2; tol <= 0 gives eq. stop_tol for Alg. 4); level sides must
                               be powers of two in [2, 1024]; path and tune do not apply    */
+    int tile;              /* tile of the temporally blocked levels (path 3): 0 automatic (the
+                              first variant, or the autotuner's pick when tune > 0); k in
+                              1..W1_TILE_VARIANTS forces variant k - 1 of
+                                64x32 nodes 4 steps, 128x16 4, 32x64 4, 64x32 8, 32x32 8
+                              (interior nodes of a tile and steps per launch; check_every
+                              must be a multiple of twice the steps)                       */
     int estimate;          /* which value dist and w1_stats.w1 report:
                               0 (default): the saddle value, the Lagrangian of eq. minmax_cp
                                 L(m, phi) = f(m) + <phi, div m - rho>_h at the returned pair;
@@ -112,7 +120,7 @@ typedef struct {
     double fpr[W1_MAX_LEVELS];      /* R^k at the last stop test of each level */
     double tol[W1_MAX_LEVELS];      /* eps_l of each level */
     int path[W1_MAX_LEVELS];        /* 1 resident (cluster size in cluster[]), 2 streaming, 3 blocked */
-    int cluster[W1_MAX_LEVELS];
+    int cluster[W1_MAX_LEVELS];     /* path 1: CTAs per pair; path 3: tile variant + 1 (w1_options.tile) */
     double w1;       /* the W1 estimate chosen by w1_options.estimate (default: saddle) */
     double dual;     /* -<phi, rho>_h of the returned potential */
     double lb;       /* certified lower bound on the discrete W1: dual / max(1, gmax) */
@@ -258,6 +266,7 @@ typedef struct {
     double us_per_step; /* measured time of one step of the whole batch */
     int concurrent;     /* path 1: pairs whose level fits on the GPU at once (CTAs or clusters
                            resident together); streaming: 1 (a launch spans the GPU) */
+    int tile;           /* path 3: the tile variant (see w1_options.tile), 0-based */
 } w1_level_choice;
 
 /*
@@ -267,7 +276,8 @@ typedef struct {
  * `batch` pairs advancing together as in a batched plan (throughput: a
  * configuration with fewer CTAs per pair can finish a large batch sooner);
  * objective 3: least SM-time per step of one pair (time x SMs it holds: for many
- * independent solves sharing the GPU, as with one plan per stream).  `all` (room for 8) receives every
+ * independent solves sharing the GPU, as with one plan per stream).  `all` (room
+ * for W1_TUNE_MAX_CANDIDATES) receives every
  * measured candidate when not NULL, n_all their number.  Results are cached
  * per device, grid, norm and batch for the process, and in the file named by
  * the environment variable W1_AUTOTUNE_CACHE when it is set.  The choice is
@@ -368,8 +378,11 @@ const char* w1_server_last_error(void);
 w1_status w1_cp_steps(int nx, int ny, double h, int norm, float mu, float tau, const float* rho, float* m1,
                       float* m2, float* phi, long long iters, int path, void* stream, double* fpr_last);
 /* w1_cp_steps with the cluster size of the resident path chosen by the caller
- * (cluster = 1, 2, 4, 8 or 16 CTAs; 0 picks it as w1_cp_steps does; ignored by
- * paths 2 and 3).  W1_ERR_UNSUPPORTED if the level does not fit that cluster. */
+ * (cluster = 1, 2, 4, 8 or 16 CTAs; 0 picks it as w1_cp_steps does;
+ * W1_ERR_UNSUPPORTED if the level does not fit that cluster).  For path 3 the
+ * same argument picks the tile variant as w1_options.tile does (0: the first;
+ * k in 1..W1_TILE_VARIANTS: variant k - 1; iters must be a multiple of its
+ * depth); path 2 ignores it. */
 w1_status w1_cp_steps_ex(int nx, int ny, double h, int norm, float mu, float tau, const float* rho, float* m1,
                          float* m2, float* phi, long long iters, int path, int cluster, void* stream,
                          double* fpr_last);

@@ -81,6 +81,7 @@ struct StepArgs {
     IterArgs it;
     double* part;  // per-pair, per-block partials (check step)
     int use_cond;  // graph mode: keep per-pair active flags and counts
+    int tile;      // temporally blocked launches: the tile variant (index into the tile table)
 };
 
 // Shared-memory resident level solver arguments (state in place).
@@ -115,11 +116,13 @@ cudaError_t launch_prolong(int ncx, int ncy, const float* m1c, const float* m2c,
 cudaError_t launch_level_begin(Ctl* ctl, int level, int pairs, cudaStream_t s);
 // Streaming step; check selects the variant that forms R^k and tests it.
 cudaError_t launch_step(int norm, bool check, const StepArgs& a, cudaStream_t s);
-// Temporally blocked streaming steps: tblock_depth() steps per launch (the
-// last one forms R^k when check is set); same arguments as launch_step.
+// Temporally blocked streaming steps: tblock_depth(a.tile) steps per launch
+// on tiles of the variant a.tile (the last step forms R^k when check is set);
+// same arguments as launch_step.  Partial sums: at most tblock_part_doubles
+// (the largest over the variants).
 cudaError_t launch_tblock(int norm, bool check, const StepArgs& a, cudaStream_t s);
-int tblock_depth();
-dim3 tblock_grid(int nx, int ny, int pairs);
+int tblock_depth(int tile = 0);
+dim3 tblock_grid(int nx, int ny, int pairs, int tile = 0);
 size_t tblock_part_doubles(int nx, int ny, int pairs);
 // After a check step in graph mode: continue the WHILE node while any pair is active.
 cudaError_t launch_decide(const Ctl* ctl, int pairs, cudaGraphConditionalHandle cond, cudaStream_t s);

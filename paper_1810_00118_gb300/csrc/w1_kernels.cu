@@ -468,22 +468,45 @@ cudaError_t launch_step(int norm, bool check, const StepArgs& a, cudaStream_t s)
 // the last step forms the interior nodes' share of R^k, summed per pair as in
 // k_step.  Global traffic per step: (16 B x tile/interior + 12 B) / TB per node.
 
-static constexpr int TBX = 64, TBY = 32, TB = 4;
-static_assert(TB % 4 == 0 && TBX % 4 == 0, "runs of four nodes must not straddle the tile's interior edge");
-static constexpr int TLW = TBX + 2 * TB, TLH = TBY + 2 * TB, TLN = TLW * TLH;  // 72 x 40 = 2880
-static constexpr int TB_THREADS = ((TLN / 4 + 31) / 32) * 32;                // 736
+// The tile (TBX x TBY interior nodes) and the depth TB (steps per launch) are
+// compile-time parameters of each instantiation; the plan (or the autotuner)
+// picks one of TB_SHAPES per level.  Wider tiles waste less on halos, deeper
+// ones read global memory less often, at the cost of more halo work per step.
+struct TbShape {
+    int x, y, t;
+};
+static constexpr TbShape TB_SHAPES[W1_TILE_VARIANTS] = {{64, 32, 4}, {128, 16, 4}, {32, 64, 4}, {64, 32, 8}, {32, 32, 8}};
+template <int TBX, int TBY, int TB>
+struct TbGeom {
+    static_assert(TB % 4 == 0 && TBX % 4 == 0, "runs of four nodes must not straddle the tile's interior edge");
+    static constexpr int TLW = TBX + 2 * TB, TLH = TBY + 2 * TB, TLN = TLW * TLH;
+    static constexpr int THREADS = ((TLN / 4 + 31) / 32) * 32;
+    static_assert(THREADS <= 1024, "one thread per run of four tile nodes");
+    static constexpr size_t SMEM_PLAIN = 3 * TLN * sizeof(float), SMEM_CHECK = 5 * TLN * sizeof(float);
+};
 
-dim3 tblock_grid(int nx, int ny, int pairs) { return dim3((nx + TBX - 1) / TBX, (ny + TBY - 1) / TBY, pairs); }
+static int tile_index(int tile) { return (tile >= 0 && tile < W1_TILE_VARIANTS) ? tile : 0; }
+dim3 tblock_grid(int nx, int ny, int pairs, int tile)
+{
+    const TbShape& sh = TB_SHAPES[tile_index(tile)];
+    return dim3((nx + sh.x - 1) / sh.x, (ny + sh.y - 1) / sh.y, pairs);
+}
 size_t tblock_part_doubles(int nx, int ny, int pairs)
 {
-    dim3 g = tblock_grid(nx, ny, pairs);
-    return (size_t)g.x * g.y * g.z * 3;
+    size_t m = 0;
+    for (int k = 0; k < W1_TILE_VARIANTS; ++k) {
+        dim3 g = tblock_grid(nx, ny, pairs, k);
+        const size_t v = (size_t)g.x * g.y * g.z * 3;
+        if (v > m) m = v;
+    }
+    return m;
 }
-int tblock_depth() { return TB; }
+int tblock_depth(int tile) { return TB_SHAPES[tile_index(tile)].t; }
 
-template <int NORM, bool CHECK>
-__global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
+template <int NORM, bool CHECK, int TBX, int TBY, int TB>
+__global__ void __launch_bounds__(TbGeom<TBX, TBY, TB>::THREADS) k_tblock(StepArgs a)
 {
+    constexpr int TLW = TbGeom<TBX, TBY, TB>::TLW, TLH = TbGeom<TBX, TBY, TB>::TLH, TLN = TbGeom<TBX, TBY, TB>::TLN;
     const IterArgs& P = a.it;
     const int pair = blockIdx.z;
     Ctl* pc = P.ctl ? P.ctl + pair : nullptr;
@@ -672,34 +695,62 @@ __global__ void __launch_bounds__(TB_THREADS) k_tblock(StepArgs a)
     }
 }
 
-static constexpr size_t TB_SMEM_PLAIN = 3 * TLN * sizeof(float), TB_SMEM_CHECK = 5 * TLN * sizeof(float);
+template <int NORM, bool CHECK, int X, int Y, int T>
+static cudaError_t tb_attr()
+{
+    return cudaFuncSetAttribute(k_tblock<NORM, CHECK, X, Y, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(CHECK ? TbGeom<X, Y, T>::SMEM_CHECK : TbGeom<X, Y, T>::SMEM_PLAIN));
+}
+template <int X, int Y, int T>
+static cudaError_t tb_attr_all()
+{
+    cudaError_t e;
+    if ((e = tb_attr<W1_NORM_L1, true, X, Y, T>()) != cudaSuccess) return e;
+    if ((e = tb_attr<W1_NORM_L1, false, X, Y, T>()) != cudaSuccess) return e;
+    if ((e = tb_attr<W1_NORM_L2, true, X, Y, T>()) != cudaSuccess) return e;
+    if ((e = tb_attr<W1_NORM_L2, false, X, Y, T>()) != cudaSuccess) return e;
+    if ((e = tb_attr<W1_NORM_LINF, true, X, Y, T>()) != cudaSuccess) return e;
+    return tb_attr<W1_NORM_LINF, false, X, Y, T>();
+}
 
 cudaError_t tblock_prepare()
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_tblock<W1_NORM_L1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)TB_SMEM_CHECK)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_tblock<W1_NORM_L2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)TB_SMEM_CHECK)) != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(k_tblock<W1_NORM_LINF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)TB_SMEM_CHECK);
+    if ((e = tb_attr_all<64, 32, 4>()) != cudaSuccess) return e;
+    if ((e = tb_attr_all<128, 16, 4>()) != cudaSuccess) return e;
+    if ((e = tb_attr_all<32, 64, 4>()) != cudaSuccess) return e;
+    if ((e = tb_attr_all<64, 32, 8>()) != cudaSuccess) return e;
+    return tb_attr_all<32, 32, 8>();
+}
+
+template <int X, int Y, int T>
+static void tb_launch(int norm, bool check, const StepArgs& a, cudaStream_t s)
+{
+    using G = TbGeom<X, Y, T>;
+    const TbShape sh{X, Y, T};
+    const dim3 g((a.it.nx + sh.x - 1) / sh.x, (a.it.ny + sh.y - 1) / sh.y, a.pairs);
+    if (norm == W1_NORM_L1) {
+        if (check) k_tblock<W1_NORM_L1, true, X, Y, T><<<g, G::THREADS, G::SMEM_CHECK, s>>>(a);
+        else k_tblock<W1_NORM_L1, false, X, Y, T><<<g, G::THREADS, G::SMEM_PLAIN, s>>>(a);
+    } else if (norm == W1_NORM_L2) {
+        if (check) k_tblock<W1_NORM_L2, true, X, Y, T><<<g, G::THREADS, G::SMEM_CHECK, s>>>(a);
+        else k_tblock<W1_NORM_L2, false, X, Y, T><<<g, G::THREADS, G::SMEM_PLAIN, s>>>(a);
+    } else {
+        if (check) k_tblock<W1_NORM_LINF, true, X, Y, T><<<g, G::THREADS, G::SMEM_CHECK, s>>>(a);
+        else k_tblock<W1_NORM_LINF, false, X, Y, T><<<g, G::THREADS, G::SMEM_PLAIN, s>>>(a);
+    }
 }
 
 cudaError_t launch_tblock(int norm, bool check, const StepArgs& a, cudaStream_t s)
 {
-    dim3 g = tblock_grid(a.it.nx, a.it.ny, a.pairs);
-    if (norm == W1_NORM_L1) {
-        if (check) k_tblock<W1_NORM_L1, true><<<g, TB_THREADS, TB_SMEM_CHECK, s>>>(a);
-        else k_tblock<W1_NORM_L1, false><<<g, TB_THREADS, TB_SMEM_PLAIN, s>>>(a);
-    } else if (norm == W1_NORM_L2) {
-        if (check) k_tblock<W1_NORM_L2, true><<<g, TB_THREADS, TB_SMEM_CHECK, s>>>(a);
-        else k_tblock<W1_NORM_L2, false><<<g, TB_THREADS, TB_SMEM_PLAIN, s>>>(a);
-    } else {
-        if (check) k_tblock<W1_NORM_LINF, true><<<g, TB_THREADS, TB_SMEM_CHECK, s>>>(a);
-        else k_tblock<W1_NORM_LINF, false><<<g, TB_THREADS, TB_SMEM_PLAIN, s>>>(a);
+    switch (tile_index(a.tile)) {
+    case 1: tb_launch<128, 16, 4>(norm, check, a, s); break;
+    case 2: tb_launch<32, 64, 4>(norm, check, a, s); break;
+    case 3: tb_launch<64, 32, 8>(norm, check, a, s); break;
+    case 4: tb_launch<32, 32, 8>(norm, check, a, s); break;
+    default: tb_launch<64, 32, 4>(norm, check, a, s); break;
     }
+    static_assert(W1_TILE_VARIANTS == 5, "one case per entry of TB_SHAPES");
     return cudaGetLastError();
 }
 

@@ -100,6 +100,7 @@ struct LevelPlan {
     int path;     // 1 resident, 2 streaming
     int cluster;  // resident cluster size
     int rows;     // streaming march length
+    int tile;     // path 3: tile variant (w1_options.tile)
     float* rho;
     float* m1[2];
     float* m2[2];
@@ -268,8 +269,9 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
     if (o.path < 0 || o.path > 3) return fail(W1_ERR_INVALID_ARG, "path must be 0, 1, 2 or 3");
     if (o.tune < 0 || o.tune > 3) return fail(W1_ERR_INVALID_ARG, "tune must be 0, 1, 2 or 3");
     if (o.estimate < 0 || o.estimate > 1) return fail(W1_ERR_INVALID_ARG, "estimate must be 0 or 1");
-    if (o.check_every % (2 * tblock_depth()) != 0)
-        return fail(W1_ERR_INVALID_ARG, "check_every must be a multiple of twice the temporal block depth (8)");
+    if (o.tile < 0 || o.tile > W1_TILE_VARIANTS) return fail(W1_ERR_INVALID_ARG, "tile must lie in [0, W1_TILE_VARIANTS]");
+    if (o.check_every % (2 * tblock_depth(o.tile > 0 ? o.tile - 1 : 0)) != 0)
+        return fail(W1_ERR_INVALID_ARG, "check_every must be a multiple of twice the temporal block depth");
     // stop tests happen every K steps, so the cap is a multiple of K
     o.max_iters = (o.max_iters + o.check_every - 1) / o.check_every * o.check_every;
     if (!(h > 0.0)) h = 1.0 / (double)(nx > ny ? nx : ny);
@@ -337,11 +339,14 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
         else
             v.path = 2;  // one step per launch
         v.cluster = v.path == 1 ? c : 0;
+        v.tile = o.tile > 0 ? o.tile - 1 : 0;
         if (o.tune && o.path == 0 && tune_now) {
             w1_level_choice ch;
-            if (w1_autotune_level(v.nx, v.ny, norm, max_batch, o.tune, 128, &ch, nullptr, nullptr) == W1_OK) {
+            if (w1_autotune_level(v.nx, v.ny, norm, max_batch, o.tune, 128, &ch, nullptr, nullptr) == W1_OK &&
+                (ch.path != 3 || o.check_every % (2 * tblock_depth(ch.tile)) == 0)) {
                 v.path = ch.path;
                 v.cluster = ch.path == 1 ? ch.cluster : 0;
+                if (ch.path == 3 && o.tile == 0) v.tile = ch.tile;
             }
         }
         v.rows = o.rows_per_thread > 0 ? o.rows_per_thread : stream_rows_auto(v.nx, v.ny, max_batch);
@@ -603,7 +608,7 @@ static w1_status build_graph(w1_plan* p)
             CAP_CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
             CAP_CK(cudaStreamBeginCaptureToGraph(p->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
             const int K = p->opt.check_every;
-            const int per = v.path == 3 ? tblock_depth() : 1;  // steps per launch
+            const int per = v.path == 3 ? tblock_depth(v.tile) : 1;  // steps per launch
             const int nl = K / per;                             // launches per body (even: K and per are)
             cudaError_t e = cudaSuccess;
             if (v.path == 4) {
@@ -625,6 +630,7 @@ static w1_status build_graph(w1_plan* p)
                 a.it = iter_args(p, l);
                 a.part = p->part;
                 a.use_cond = 1;
+                a.tile = v.tile;
                 e = v.path == 3 ? launch_tblock(p->norm, k == nl - 1, a, p->body_stream)
                                 : launch_step(p->norm, k == nl - 1, a, p->body_stream);
             }
@@ -670,7 +676,7 @@ static void fill_stats(const w1_plan* p, const Ctl* c, w1_stats* st)
         st->fpr[l] = c->fpr[l];
         st->tol[l] = p->lv[l].tol;
         st->path[l] = p->lv[l].path;
-        st->cluster[l] = p->lv[l].cluster;
+        st->cluster[l] = p->lv[l].path == 3 ? p->lv[l].tile + 1 : p->lv[l].cluster;
         conv &= c->conv[l] ? 1 : 0;
     }
     st->w1 = p->opt.estimate == 1 ? c->f : c->saddle;
@@ -726,7 +732,7 @@ static w1_status run_eager(w1_plan* p, cudaStream_t s)
             continue;
         }
         const int K = p->opt.check_every;
-        const int per = v.path == 3 ? tblock_depth() : 1;
+        const int per = v.path == 3 ? tblock_depth(v.tile) : 1;
         const int nl = K / per;
         for (;;) {
             if (v.path == 4) {
@@ -748,6 +754,7 @@ static w1_status run_eager(w1_plan* p, cudaStream_t s)
                 a.it = iter_args(p, l);
                 a.part = p->part;
                 a.use_cond = 1;
+                a.tile = v.tile;
                 W1_CK(v.path == 3 ? launch_tblock(p->norm, k == nl - 1, a, s) : launch_step(p->norm, k == nl - 1, a, s));
             }
             W1_CK(cudaMemcpyAsync(host.data(), p->ctl, sizeof(Ctl) * B, cudaMemcpyDeviceToHost, s));
@@ -1328,13 +1335,19 @@ extern "C" w1_status w1_cp_steps_ex(int nx, int ny, double h, int norm, float mu
         cudaError_t e = launch_resident(norm, c, a, s);
         if (e != cudaSuccess) ret = fail(W1_ERR_CUDA, std::string("resident launch: ") + cudaGetErrorString(e));
     } else {
-        if (path == 3 && (nx % 4 != 0 || iters % tblock_depth() != 0)) {
+        // path 3: `cluster` k >= 1 selects tile variant k - 1 (as w1_options.tile); 0 the first
+        const int tile = (path == 3 && cluster > 0) ? cluster - 1 : 0;
+        if (path == 3 && (cluster < 0 || cluster > W1_TILE_VARIANTS)) {
             cudaFree(dfpr);
-            return fail(W1_ERR_UNSUPPORTED, "temporal blocking needs nx % 4 == 0 and iters % 4 == 0");
+            return fail(W1_ERR_INVALID_ARG, "tile variant out of range");
+        }
+        if (path == 3 && (nx % 4 != 0 || iters % tblock_depth(tile) != 0)) {
+            cudaFree(dfpr);
+            return fail(W1_ERR_UNSUPPORTED, "temporal blocking needs nx % 4 == 0 and iters a multiple of its depth");
         }
         const size_t n = (size_t)nx * ny;
         const int rows = stream_rows_auto(nx, ny, 1);
-        const long long launches = path == 3 ? iters / tblock_depth() : iters;
+        const long long launches = path == 3 ? iters / tblock_depth(tile) : iters;
         size_t pd = step_part_doubles(nx, ny, rows, 1);
         if (tblock_part_doubles(nx, ny, 1) > pd) pd = tblock_part_doubles(nx, ny, 1);
         float* buf = nullptr;
@@ -1363,6 +1376,7 @@ extern "C" w1_status w1_cp_steps_ex(int nx, int ny, double h, int norm, float mu
             a.it.ctl = ctl;
             a.part = part;
             a.use_cond = 0;
+            a.tile = tile;
             e = path == 3 ? launch_tblock(norm, k == launches - 1, a, s) : launch_step(norm, k == launches - 1, a, s);
         }
         if (e == cudaSuccess && (launches & 1)) {

@@ -6,7 +6,8 @@
 //   * on chip (path 1) with each feasible cluster size (bands of whole rows,
 //     at most 4096 nodes per CTA, or 16384 with the wide layout);
 //   * streaming, one step per launch (path 2);
-//   * streaming with temporal blocking (path 3, nx % 4 == 0).
+//   * streaming with temporal blocking (path 3, nx % 4 == 0), each tile shape
+//     and depth of the kernel's table.
 // The measured quantity is the time of one step of the whole batch, so the
 // choice accounts for how many pairs fit on the GPU at once (a configuration
 // with fewer CTAs per pair is slower for one pair but may finish a large batch
@@ -56,8 +57,8 @@ void load_cache_file()
     if (!f) return;
     TuneKey k;
     w1_level_choice c;
-    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %lf %d", &k.dev, &k.nx, &k.ny, &k.norm, &k.batch, &c.path,
-                       &c.cluster, &c.batch, &c.us_per_step, &c.concurrent) == 10)
+    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %lf %d %d", &k.dev, &k.nx, &k.ny, &k.norm, &k.batch, &c.path,
+                       &c.cluster, &c.batch, &c.us_per_step, &c.concurrent, &c.tile) == 11)
         g_tune_cache[k] = c;
     std::fclose(f);
 }
@@ -68,14 +69,14 @@ void append_cache_file(const TuneKey& k, const w1_level_choice& c)
     if (!p) return;
     FILE* f = std::fopen(p, "a");
     if (!f) return;
-    std::fprintf(f, "%d %d %d %d %d %d %d %d %.6f %d\n", k.dev, k.nx, k.ny, k.norm, k.batch, c.path, c.cluster,
-                 c.batch, c.us_per_step, c.concurrent);
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %.6f %d %d\n", k.dev, k.nx, k.ny, k.norm, k.batch, c.path, c.cluster,
+                 c.batch, c.us_per_step, c.concurrent, c.tile);
     std::fclose(f);
 }
 
 // Times `steps` steps of one candidate on `pairs` pairs; microseconds per step
 // of the whole batch (< 0 on failure).
-double time_candidate(int norm, int path, int cluster, int nx, int ny, int pairs, int steps, float* buf,
+double time_candidate(int norm, int path, int cluster, int tile, int nx, int ny, int pairs, int steps, float* buf,
                       double* part, Ctl* ctl, cudaStream_t s)
 {
     const size_t n = (size_t)nx * ny, plane = n * pairs;
@@ -108,7 +109,7 @@ double time_candidate(int norm, int path, int cluster, int nx, int ny, int pairs
             a.it.cap = nsteps;
             return launch_resident(norm, cluster, a, s);
         }
-        const int per = path == 3 ? tblock_depth() : 1;
+        const int per = path == 3 ? tblock_depth(tile) : 1;
         const int launches = nsteps / per;
         for (int k = 0; k < launches; ++k) {
             StepArgs a{};
@@ -127,6 +128,7 @@ double time_candidate(int norm, int path, int cluster, int nx, int ny, int pairs
             a.it.ctl = ctl;
             a.part = part;
             a.use_cond = 0;
+            a.tile = tile;
             cudaError_t e = path == 3 ? launch_tblock(norm, false, a, s) : launch_step(norm, false, a, s);
             if (e != cudaSuccess) return e;
         }
@@ -199,9 +201,10 @@ extern "C" w1_status w1_autotune_level(int nx, int ny, int norm, int batch, int 
     const int cs[5] = {1, 2, 4, 8, 16};
     for (int c : cs)
         if (resident_fits(nx, ny, c) && resident_cluster_ok(norm, c, nx, ny) > 0)
-            cands.push_back(w1_level_choice{1, c, B, 0.0, resident_cluster_ok(norm, c, nx, ny)});
-    cands.push_back(w1_level_choice{2, 0, B, 0.0, 1});
-    if (nx % 4 == 0) cands.push_back(w1_level_choice{3, 0, B, 0.0, 1});
+            cands.push_back(w1_level_choice{1, c, B, 0.0, resident_cluster_ok(norm, c, nx, ny), 0});
+    cands.push_back(w1_level_choice{2, 0, B, 0.0, 1, 0});
+    if (nx % 4 == 0)
+        for (int tile = 0; tile < W1_TILE_VARIANTS; ++tile) cands.push_back(w1_level_choice{3, 0, B, 0.0, 1, tile});
 
     float* buf = nullptr;
     double* part = nullptr;
@@ -226,7 +229,7 @@ extern "C" w1_status w1_autotune_level(int nx, int ny, int norm, int batch, int 
     }
     w1_status ret = W1_OK;
     int n_ok = 0;
-    w1_level_choice pick{0, 0, B, 0.0, 0};
+    w1_level_choice pick{0, 0, B, 0.0, 0, 0};
     double best_cost = 1e300;
     if (e != cudaSuccess) {
         g_tune_err = std::string("autotune allocation: ") + cudaGetErrorString(e);
@@ -235,7 +238,7 @@ extern "C" w1_status w1_autotune_level(int nx, int ny, int norm, int batch, int 
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
         for (auto& c : cands) {
-            const double us = time_candidate(norm, c.path, c.cluster, nx, ny, P, steps, buf, part, ctl, s);
+            const double us = time_candidate(norm, c.path, c.cluster, c.tile, nx, ny, P, steps, buf, part, ctl, s);
             if (us <= 0.0) continue;
             c.us_per_step = us * (double)B / (double)P;
             // objective 3: SM-time of a step (on-chip levels hold one CTA per SM; a
@@ -245,7 +248,7 @@ extern "C" w1_status w1_autotune_level(int nx, int ny, int norm, int batch, int 
                 best_cost = cost;
                 pick = c;
             }
-            if (all && n_ok < 8) all[n_ok] = c;
+            if (all && n_ok < W1_TUNE_MAX_CANDIDATES) all[n_ok] = c;
             ++n_ok;
         }
         if (n_ok == 0) {
@@ -258,7 +261,7 @@ extern "C" w1_status w1_autotune_level(int nx, int ny, int norm, int batch, int 
     cudaFree(ctl);
     if (s) cudaStreamDestroy(s);
     cudaGetLastError();
-    if (n_all) *n_all = n_ok < 8 ? n_ok : 8;
+    if (n_all) *n_all = n_ok < W1_TUNE_MAX_CANDIDATES ? n_ok : W1_TUNE_MAX_CANDIDATES;
     if (ret != W1_OK) return ret;
     *best = pick;
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -47,12 +47,12 @@ class Options(ctypes.Structure):
     _fields_ = [("check_every", ctypes.c_int), ("max_iters", ctypes.c_longlong), ("theta", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("time_budget_s", ctypes.c_double), ("path", ctypes.c_int),
                 ("rows_per_thread", ctypes.c_int), ("eager", ctypes.c_int), ("tune", ctypes.c_int),
-                ("algorithm", ctypes.c_int), ("estimate", ctypes.c_int)]
+                ("algorithm", ctypes.c_int), ("tile", ctypes.c_int), ("estimate", ctypes.c_int)]
 
 
 class LevelChoice(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("cluster", ctypes.c_int), ("batch", ctypes.c_int),
-                ("us_per_step", ctypes.c_double), ("concurrent", ctypes.c_int)]
+                ("us_per_step", ctypes.c_double), ("concurrent", ctypes.c_int), ("tile", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -586,9 +586,10 @@ class Server:
 
 def autotune_level(nx, ny, norm=NORM_L1, objective=2, steps=256, batch=1):
     """(best, all candidates) as dicts: path, cluster, batch, us_per_step (one
-    step of the whole batch; objective 1 times one pair alone)."""
+    step of the whole batch; objective 1 times one pair alone), concurrent,
+    tile (path 3: the tile variant, 0-based)."""
     best = LevelChoice()
-    allc = (LevelChoice * 8)()
+    allc = (LevelChoice * 16)()  # W1_TUNE_MAX_CANDIDATES
     n = ctypes.c_int(0)
     st = _lib.w1_autotune_level(nx, ny, norm, batch, objective, steps, ctypes.byref(best), allc, ctypes.byref(n))
     if st != OK:

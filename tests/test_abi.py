@@ -64,7 +64,8 @@ def test_binding_struct_layout_matches_header():
     """ctypes mirrors of w1_options / w1_stats / w1_server_config have the C
     sizes and field offsets (taken from the header by a C compiler)."""
     from paper_1810_00118_gb300 import w1
-    for struct, py in (("w1_options", w1.Options), ("w1_stats", w1._Stats), ("w1_server_config", w1.ServerConfig)):
+    for struct, py in (("w1_options", w1.Options), ("w1_stats", w1._Stats), ("w1_server_config", w1.ServerConfig),
+                       ("w1_level_choice", w1.LevelChoice)):
         names = [n for n, _ in py._fields_]
         got = _c_layout(struct, names)
         assert ctypes.sizeof(py) == got[0], struct

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def run(env_extra):
     env = dict(os.environ, **env_extra)
     return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                           "--warmup", "0", "--ref-budget", "0.3"], cwd=ROOT, env=env, capture_output=True,
+                           "--warmup", "0", "--batch", "4", "--ref-n", "32"], cwd=ROOT, env=env, capture_output=True,
                           text=True, timeout=600)
 
 

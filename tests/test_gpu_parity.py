@@ -441,3 +441,79 @@ def test_eager_mode_equals_graph_mode(w1, norm):
         out.append((v, st.iters, f))
     assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
     assert torch.equal(out[0][2], out[1][2])
+
+
+# --------------------------------------------------------------------------------------
+# Tolerance schedules (eq. tol_formula_propose, the alpha study of Sec. 6.2) and level
+# counts other than the paper's L = log2(1/h) - 3 (Sec. 6.3)
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,norm,levels,alpha", [(256, L2, 5, 0.0), (256, L1, 6, 0.0), (512, L2, 7, -1.0),
+                                                 (128, LINF, 4, 1.0)])
+def test_tolerance_schedule_and_level_count(w1, n, norm, levels, alpha):
+    """eps_l = eps_L (h_l / h)^alpha on every level (checked against the formula),
+    replay parity with the oracle at that schedule, and the oracle's own stop
+    decisions under the same schedule land on about the same step counts."""
+    workload = 1 if n == 256 else 2
+    r0, r1 = synth.pair(workload, 3, n=n)
+    eps_L = 1e-6 / 128 * (512.0 / n) ** 2
+    val, st, flux, _, ref = solve_and_replay(w1, r0, r1, norm, levels, tol=eps_L, alpha=alpha)
+    assert st.levels == levels and st.sizes[0] == (n >> (levels - 1),) * 2
+    for lvl in range(levels):
+        h_ratio = 2.0 ** (levels - 1 - lvl)
+        assert st.tol[lvl] == pytest.approx(eps_L * h_ratio ** alpha, rel=1e-12)
+    assert_parity(val, st, flux, ref)
+    if n <= 256:
+        a0, a1, d0, d1 = synth.to_f32_pair(r0, r1)
+        free = oracle.multilevel(d0, d1, levels=levels, norm=norm, tol=eps_L, alpha=alpha, stop=oracle.STOP_FPR)
+        assert abs(val - free.w1) <= 1e-4 * free.w1
+        for a, b in zip(st.iters, free.iters):
+            assert abs(a - b) <= max(0.1 * b, 64)
+
+
+# --------------------------------------------------------------------------------------
+# Tile shapes and depths of the temporally blocked kernel (picked per level by the
+# autotuner or forced with w1_options.tile)
+# --------------------------------------------------------------------------------------
+
+TILES = [(1, "64x32, 4 steps"), (2, "128x16, 4"), (3, "32x64, 4"), (4, "64x32, 8"), (5, "32x32, 8")]
+
+
+@pytest.mark.parametrize("norm", [L1, L2, LINF])
+@pytest.mark.parametrize("tile", [t for t, _ in TILES])
+@pytest.mark.parametrize("shape", [(3, 8), (40, 36), (130, 72), (200, 300), (96, 256)])
+def test_tile_variants_match_oracle(w1, norm, tile, shape):
+    """Every tile variant against the oracle on ragged grids (tiles cut by the
+    grid's edges, grids smaller than one tile), 8 and 16 steps."""
+    ny, nx = shape
+    rng = np.random.default_rng(ny * 7 + nx + 31 * tile + norm)
+    rho, m1, m2, phi = rand_state(rng, ny, nx)
+    h = 1.0 / max(nx, ny)
+    mu = mu_of(h)
+    for iters in (8, 16):
+        g = [dev(a) for a in (rho, m1, m2, phi)]
+        fpr = w1.cp_steps(g[0], g[1], g[2], g[3], h, norm, mu, mu, iters, path=3, cluster=tile)
+        o1, o2, op, ofpr = oracle.cp_iterate(rho, m1, m2, phi, h, norm, iters, mu=mu, tau=mu)
+        scale = max(np.abs(o1).max(), np.abs(o2).max(), np.abs(op).max(), 1.0)
+        for got, want in ((g[1], o1), (g[2], o2), (g[3], op)):
+            assert np.abs(host(got) - want).max() <= 2e-5 * scale, (iters, tile)
+        assert fpr == pytest.approx(ofpr, rel=2e-3, abs=1e-12 * scale)
+
+
+@pytest.mark.parametrize("tile", [2, 4, 5])
+def test_plan_with_forced_tile_matches_replay(w1, tile):
+    """A plan whose streaming levels all run a non-default tile (path 3 forced)
+    against the oracle replaying its step counts; the tile is reported in
+    stats.cluster of those levels."""
+    r0, r1 = synth.pair(2, 9, n=256)
+    val, st, flux, _, ref = solve_and_replay(w1, r0, r1, L2, 5, path=3, tile=tile)
+    assert st.path == [3] * 5 and st.cluster == [tile] * 5
+    assert_parity(val, st, flux, ref)
+
+
+def test_autotuner_reports_tile_candidates(w1):
+    """The tuner times every tile variant of a streaming level among its candidates."""
+    best, cands = w1.autotune_level(1024, 1024, L1, objective=1, steps=64)
+    tiles = sorted(c["tile"] for c in cands if c["path"] == 3)
+    assert tiles == list(range(5))
+    assert best["us_per_step"] == min(c["us_per_step"] for c in cands)
