@@ -273,7 +273,7 @@ def run_gpu(args):
     DEPTH = 2 if (args.mode == "lanes" and args.pipeline) else 1
     total_steps = args.warmup + args.steps
     conv = load_converged() if (rank == 0 and args.algorithm == 3) else None
-    acc_ids = sorted(set(conv[1]) & set(conv[2])) if conv else []
+    acc_ids = sorted(set(conv[1]) | set(conv[2])) if conv else []
     # distinct pairs per step and rank (and the reference pairs), generated before CUDA starts
     specs = [(WORKLOAD, k, N) for s in range(total_steps) for k in pair_ids(rank, s, B)]
     gen = gen_pairs(specs + [(WORKLOAD, k, N) for k in acc_ids], world)
@@ -496,13 +496,15 @@ def run_gpu(args):
     # accuracy: the reference pairs solved by the same plans (lanes) and compared
     # with their stored converged values (FP64 oracle / exact LP)
     accuracy = None
-    if conv and acc_ids and args.mode == "lanes" and G == 1:
+    if conv and acc_ids and args.mode == "lanes" and G == 1 and not args.no_accuracy:
         a0 = torch.from_numpy(np.stack([x[0] for x in acc_pairs])).cuda()
         a1 = torch.from_numpy(np.stack([x[1] for x in acc_pairs])).cuda()
         errs, prim, sts_acc = {}, {}, {}
         for norm in NORMS:
             e, pe, ss = [], [], []
             for i, k in enumerate(acc_ids):
+                if k not in conv[norm]:
+                    continue
                 p = plans[norm][0][i % nlane]
                 p.solve_async(a0[i], a1[i], stream=lanes[norm][i % nlane])
                 lanes[norm][i % nlane].synchronize()
@@ -512,10 +514,10 @@ def run_gpu(args):
                 pe.append(abs(st[0].primal - ref) / ref)
                 ss.append(ps[0])
             errs[f"L{norm}"], prim[f"L{norm}"], sts_acc[f"L{norm}"] = e, pe, ss
-        accuracy = {"max_rel_err_vs_converged": {k: float(max(v)) for k, v in errs.items()},
+        accuracy = {"max_rel_err_vs_converged": {k: (float(max(v)) if v else None) for k, v in errs.items()},
                     "rel_err_vs_converged": errs,
-                    "primal_max_rel_err_vs_converged": {k: float(max(v)) for k, v in prim.items()},
-                    "pairs": acc_ids, "statuses": sts_acc,
+                    "primal_max_rel_err_vs_converged": {k: (float(max(v)) if v else None) for k, v in prim.items()},
+                    "pairs": {f"L{n}": sorted(conv[n]) for n in NORMS}, "statuses": sts_acc,
                     "reference": "tests/golden/converged_512.json (p = 1: exact LP; p = 2: FP64 oracle at "
                                  "eps_L / 1e4), written by oracle/make_converged_table.py",
                     "what": "reported W1 (saddle value) of each reference pair against its converged value; "
@@ -740,6 +742,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-threads", type=int, default=64, help="e2e: host threads calling w1_solve_host")
     ap.add_argument("--no-extras", action="store_true", help="skip the short serving and mixed-batch legs")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the solves of the reference pairs")
     ap.add_argument("--solo", type=int, default=8, help="pairs solved one at a time for the latency figure")
     ap.add_argument("--tune", type=int, default=0, choices=[0, 1, 2, 3],
                     help="lanes: per-level kernel choice (0 fixed rules, 1 latency, 3 SM-time; see w1_options.tune)")
@@ -908,59 +911,67 @@ def run_mixed(args):
 
 
 def run_tol_sweep(args):
-    """Tolerance schedule study (eq. tol_formula_propose): per level tolerance
-    eps_l = eps_L (h_l / h)^alpha for several alpha, and the number of levels,
-    on the 512^2 workload; W1 error against a reference solve with the finest
-    tolerance divided by 100, and time per solve (lanes, CUDA events)."""
+    """Tolerance schedule study (eq. tol_formula_propose, the alpha study of
+    Sec. 6.2, the level count of Sec. 6.3) on the 512^2 workload: for each
+    norm, eps_l = s * eps_L (h_l / h)^alpha with eps_L of eq. stop_tol, for
+    several scales s, alphas and level counts; the reported W1 (saddle value)
+    of the reference pairs against their converged values
+    (tests/golden/converged_512.json) and the throughput of a batch of lanes
+    (one plan and stream per pair, CUDA events)."""
     import torch
 
     import synth
     from paper_1810_00118_gb300 import w1
 
+    conv = load_converged()
+    if not conv:
+        raise SystemExit("tests/golden/converged_512.json is missing")
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    B = args.batch
-    pairs = [synth.pair(WORKLOAD, 700 + k) for k in range(B)]
-    t0 = torch.from_numpy(np.ascontiguousarray(np.stack([p[0] for p in pairs]), dtype=np.float32)).cuda()
-    t1 = torch.from_numpy(np.ascontiguousarray(np.stack([p[1] for p in pairs]), dtype=np.float32)).cuda()
-    eps = 1e-6 / 128 * (512 / N) ** 2  # eq. stop_tol at h = 1/512
-    ok = (w1.OK, w1.ERR_NOT_CONVERGED)
-    lanes = [torch.cuda.Stream() for _ in range(B)]
-
-    def solve_all(norm, levels, alpha, tol):
-        plans = [w1.Plan(N, N, levels=levels, norm=norm, tol=tol, alpha=alpha) for _ in range(B)]
-        ready = torch.cuda.Event()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        ready.record(stream)
-        for b in range(B):
-            lanes[b].wait_event(ready)
-            plans[b].solve_async(t0[b], t1[b], stream=lanes[b])
-            stream.wait_stream(lanes[b])
-        e1.record(stream)
-        torch.cuda.synchronize()
-        vals, iters = [], []
-        for p in plans:
-            v, st, _, _ = p.results(allow=ok)
-            vals.append(v[0])
-            iters.append(st[0].iters)
-            p.close()
-        return np.array(vals), e0.elapsed_time(e1), iters
-
+    every = (w1.OK, w1.ERR_NOT_CONVERGED, w1.ERR_TIMEOUT, w1.ERR_MASS)
     out = []
     for norm in NORMS:
-        ref, _, _ = solve_all(norm, LEVELS, -1.0, eps / 100)
-        for levels in (LEVELS - 1, LEVELS, LEVELS + 1):
-            for alpha in (-2.0, -1.0, 0.0, 1.0):
-                vals, ms, iters = solve_all(norm, levels, alpha, eps)
-                err = np.abs(vals - ref) / np.abs(ref)
-                out.append({"norm": norm, "levels": levels, "alpha": alpha, "ms_per_batch": ms,
-                            "solves_per_s": B / (ms / 1e3), "max_rel_err": float(err.max()),
-                            "mean_rel_err": float(err.mean()), "iters_pair0": iters[0]})
-                print(json.dumps(out[-1]), flush=True)
-    print(json.dumps({"only": "tol-sweep", "grid": N, "pairs": B, "eps_L": eps,
-                      "reference": "same pairs, alpha -1, default levels, eps_L / 100", "rows": out}))
+        ids = sorted(conv[norm])
+        if not ids:
+            continue
+        pairs = [synth.pair(WORKLOAD, k) for k in ids]
+        t0 = torch.from_numpy(np.ascontiguousarray(np.stack([p[0] for p in pairs]), dtype=np.float32)).cuda()
+        t1 = torch.from_numpy(np.ascontiguousarray(np.stack([p[1] for p in pairs]), dtype=np.float32)).cuda()
+        # the throughput batch: the reference pairs repeated to args.batch lanes
+        B = max(args.batch, len(ids))
+        lanes = [torch.cuda.Stream() for _ in range(B)]
+        scales = (10.0, 3.0, 1.0, 0.3) if norm == 1 else (0.3, 0.1, 0.03)
+        for levels in (LEVELS, LEVELS + 1):
+            for alpha in (-1.0, -0.5, 0.0, 0.5):
+                for scale in scales:
+                    tol = 1e-6 / 128 * scale
+                    plans = [w1.Plan(N, N, levels=levels, norm=norm, tol=tol, alpha=alpha) for _ in range(B)]
+                    for rep in range(2):  # first pass: graph builds; second: timed
+                        ready = torch.cuda.Event()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        torch.cuda.synchronize()
+                        e0.record(stream)
+                        ready.record(stream)
+                        for b in range(B):
+                            lanes[b].wait_event(ready)
+                            plans[b].solve_async(t0[b % len(ids)], t1[b % len(ids)], stream=lanes[b])
+                            stream.wait_stream(lanes[b])
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                    errs, ok = [], 0
+                    for b, p in enumerate(plans):
+                        v, st, ps, _ = p.results(allow=every)
+                        ok += ps[0] == w1.OK
+                        if b < len(ids):
+                            errs.append((v[0] - conv[norm][ids[b]]) / conv[norm][ids[b]])
+                        p.close()
+                    ms = e0.elapsed_time(e1)
+                    out.append({"norm": norm, "levels": levels, "alpha": alpha, "scale": scale,
+                                "solves_per_s": ok / (ms / 1e3), "max_abs_rel_err": float(np.max(np.abs(errs))),
+                                "rel_errs": [float(x) for x in errs]})
+                    print(json.dumps(out[-1]), flush=True)
+    print(json.dumps({"only": "tol-sweep", "grid": N, "batch": args.batch, "reference_pairs": {
+        f"L{n}": sorted(conv[n]) for n in NORMS}, "rows": out}))
     return 0
 
 

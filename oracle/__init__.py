@@ -87,28 +87,33 @@ def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB)
-        d, i, l, p = ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_void_p
-        lib.w1o_div.argtypes = [i, i, d, p, p, p]
-        lib.w1o_grad.argtypes = [i, i, d, p, p, p]
-        lib.w1o_prox.argtypes = [i, d, i, p, p, p, p]
-        lib.w1o_cp_iterate.argtypes = [i, i, d, i, d, d, p, p, p, p, l, p]
-        lib.w1o_cp_iterate.restype = i
-        lib.w1o_route_bound.argtypes = [i, i, d, p]
-        lib.w1o_route_bound.restype = d
-        lib.w1o_stats.argtypes = [i, i, d, i, p, p, p, p, ctypes.POINTER(_Stats)]
-        lib.w1o_restrict.argtypes = [i, i, p, p]
-        lib.w1o_prolong.argtypes = [i, i, p, p, p, p, p, p]
-        lib.w1o_step_size.argtypes = [d, d]
-        lib.w1o_step_size.restype = d
-        lib.w1o_solve_level.argtypes = [i, i, d, i, d, p, p, p, p, d, i, i, l, l, ctypes.POINTER(l),
-                                        ctypes.POINTER(_Stats)]
-        lib.w1o_solve_level.restype = i
-        lib.w1o_multilevel.argtypes = [i, i, d, i, i, d, d, d, i, i, l, p, p, p, p, p, p, p,
-                                       ctypes.POINTER(_Stats), ctypes.POINTER(d)]
-        lib.w1o_multilevel.restype = i
-        _lib = lib
+        _lib = bind(ctypes.CDLL(_LIB))
     return _lib
+
+
+def bind(lib):
+    """Sets the ctypes signatures of the oracle's C functions on a loaded library
+    (the built one, or a test's deliberately mutated copy of it)."""
+    d, i, l, p = ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_void_p
+    lib.w1o_div.argtypes = [i, i, d, p, p, p]
+    lib.w1o_grad.argtypes = [i, i, d, p, p, p]
+    lib.w1o_prox.argtypes = [i, d, i, p, p, p, p]
+    lib.w1o_cp_iterate.argtypes = [i, i, d, i, d, d, p, p, p, p, l, p]
+    lib.w1o_cp_iterate.restype = i
+    lib.w1o_route_bound.argtypes = [i, i, d, p]
+    lib.w1o_route_bound.restype = d
+    lib.w1o_stats.argtypes = [i, i, d, i, p, p, p, p, ctypes.POINTER(_Stats)]
+    lib.w1o_restrict.argtypes = [i, i, p, p]
+    lib.w1o_prolong.argtypes = [i, i, p, p, p, p, p, p]
+    lib.w1o_step_size.argtypes = [d, d]
+    lib.w1o_step_size.restype = d
+    lib.w1o_solve_level.argtypes = [i, i, d, i, d, p, p, p, p, d, i, i, l, l, ctypes.POINTER(l),
+                                    ctypes.POINTER(_Stats)]
+    lib.w1o_solve_level.restype = i
+    lib.w1o_multilevel.argtypes = [i, i, d, i, i, d, d, d, i, i, l, p, p, p, p, p, p, p,
+                                   ctypes.POINTER(_Stats), ctypes.POINTER(d)]
+    lib.w1o_multilevel.restype = i
+    return lib
 
 
 def _f64(a) -> np.ndarray:

@@ -13,7 +13,7 @@ workload) that the benchmark and the GPU tests compare against at relative
 
 Inputs are the FP32 densities the GPU receives (synth.to_f32_pair), balanced
 by their FP64 mean.  Usage:
-  python oracle/make_converged_table.py [--pairs 8] [--norms 1,2] [--workers N]
+  python oracle/make_converged_table.py [--first 0] [--pairs 8] [--norms 1,2] [--workers N]
 (rows are merged into an existing table).
 """
 from __future__ import annotations
@@ -67,13 +67,14 @@ def main():
     import argparse
     ap = argparse.ArgumentParser()
     ap.add_argument("--pairs", type=int, default=8)
+    ap.add_argument("--first", type=int, default=0, help="first pair index")
     ap.add_argument("--norms", default="1,2")
     ap.add_argument("--workers", type=int, default=os.cpu_count() or 1)
     args = ap.parse_args()
     import oracle
     oracle.build()
     norms = [int(x) for x in args.norms.split(",")]
-    specs = [(nm, k) for nm in sorted(norms, reverse=True) for k in range(args.pairs)]
+    specs = [(nm, k) for nm in sorted(norms, reverse=True) for k in range(args.first, args.first + args.pairs)]
     with mp.get_context("spawn").Pool(args.workers) as pool:
         rows = pool.map(_job, specs, chunksize=1)
     table = {}

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "w1_internal.h"
 
@@ -51,6 +52,36 @@ __device__ __forceinline__ void prox(float v1, float v2, float mu, float& o1, fl
         const float s = fmaxf(1.f - mu * rsqrtf(fmaf(v1, v1, v2 * v2)), 0.f);
         o1 = v1 * s;
         o2 = v2 * s;
+    }
+}
+
+// Packed FP32 (two lanes per instruction, sm_100+): the same IEEE round-to-
+// nearest operations as the scalar forms, two at a time; a - b is written as
+// a + (-b), which rounds identically.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
+
+// prox of two nodes at once, each given as (component 1 of nodes a, b) and
+// (component 2 of nodes a, b); p = infinity falls back to the scalar form
+template <int NORM>
+__device__ __forceinline__ void prox_pair(float2 v1, float2 v2, float mu, float2& o1, float2& o2)
+{
+    if (NORM == W1_NORM_L1) {
+        const float2 c1 = make_float2(fminf(fmaxf(v1.x, -mu), mu), fminf(fmaxf(v1.y, -mu), mu));
+        const float2 c2 = make_float2(fminf(fmaxf(v2.x, -mu), mu), fminf(fmaxf(v2.y, -mu), mu));
+        o1 = sub2(v1, c1);
+        o2 = sub2(v2, c2);
+    } else if (NORM == W1_NORM_L2) {
+        const float2 q = __ffma2_rn(v1, v1, __fmul2_rn(v2, v2));
+        const float2 r = make_float2(rsqrtf(q.x), rsqrtf(q.y));
+        const float2 t = __ffma2_rn(splat2(-mu), r, splat2(1.f));
+        const float2 s = make_float2(fmaxf(t.x, 0.f), fmaxf(t.y, 0.f));
+        o1 = __fmul2_rn(v1, s);
+        o2 = __fmul2_rn(v2, s);
+    } else {
+        prox<NORM>(v1.x, v2.x, mu, o1.x, o2.x);
+        prox<NORM>(v1.y, v2.y, mu, o1.y, o2.y);
     }
 }
 
@@ -110,15 +141,19 @@ __device__ __forceinline__ void mbar_expect(uint32_t bar, unsigned bytes)
     asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                  : "memory");
 }
+// try_wait suspends the thread until the phase completes or about
+// MBAR_SUSPEND_NS have passed, so a waiting warp does not take issue slots
+// from the warps that still compute by polling.
+static constexpr unsigned MBAR_SUSPEND_NS = 20000;
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, unsigned parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "n"(MBAR_SUSPEND_NS)
         : "memory");
     return ok != 0;
 }
@@ -129,8 +164,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity, unsigne
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (;;) {
-        for (int k = 0; k < 32; ++k)
-            if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait(bar, parity)) return true;
         if (globaltimer() - t0 > limit_ns) return false;
     }
 }
@@ -179,6 +213,38 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, float4 v)
                  : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// The same with a compile-time column offset folded into the address operand.
+template <int OFF>
+__device__ __forceinline__ float4 tmem_ld4_at(uint32_t taddr)
+{
+    uint32_t a, b, c, d;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4+%5];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+        : "r"(taddr), "n"(OFF)
+        : "memory");
+    return make_float4(__uint_as_float(a), __uint_as_float(b), __uint_as_float(c), __uint_as_float(d));
+}
+template <int OFF>
+__device__ __forceinline__ void tmem_st4_at(uint32_t taddr, float4 v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0+%1], {%2, %3, %4, %5};" ::"r"(taddr), "n"(OFF),
+                 "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
+                 "r"(__float_as_uint(v.w))
+                 : "memory");
+}
+
+// Calls f(std::integral_constant<int, r>{}) for r = 0 .. N - 1 (a loop whose
+// index is a compile-time constant in the body).
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    if constexpr (N > 0) {
+        static_for<N - 1>(f);
+        f(std::integral_constant<int, N - 1>{});
+    }
+}
 
 // Split cluster barrier (release on arrive, acquire on wait).
 __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }

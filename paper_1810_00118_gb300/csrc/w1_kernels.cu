@@ -800,6 +800,7 @@ static constexpr int RES_RED_BYTES = 1024;  // 32 warps x 3 doubles
 static constexpr int RES_SLOT_BYTES = 512;  // 16 CTAs x 3 doubles + decision
 static constexpr int RESW_RUNS = 4;         // wide bands: runs of four nodes per thread
 static constexpr int RESW_MAX_NODES = RES_THREADS * 4 * RESW_RUNS;  // 16384
+static constexpr int RESW_RUN_STRIDE = 4 * RES_THREADS;              // band nodes between a thread's runs
 // a CTA waiting for a neighbour's halo row gives up after this long and reports
 // a timeout (the neighbour is at most one step behind in a correct run)
 static constexpr unsigned long long RES_HALO_WAIT_NS = 200000000ull;
@@ -1211,10 +1212,28 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
             }
             const float right = last_col ? pv[3] : (lane == 31 ? ph[idx + 4] : rn);
             float n1[4], n2[4];
+            if constexpr (!CL) {  // one CTA: scalar (measured faster than packed here)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float pr_ = c < 3 ? pv[c + 1] : right;
-                prox<NORM>(fmaf(cm, pr_ - pv[c], m1[c]), fmaf(cm, up[c] - pv[c], m2[c]), mu, n1[c], n2[c]);
+                for (int c = 0; c < 4; ++c) {
+                    const float pr_ = c < 3 ? pv[c + 1] : right;
+                    prox<NORM>(fmaf(cm, pr_ - pv[c], m1[c]), fmaf(cm, up[c] - pv[c], m2[c]), mu, n1[c], n2[c]);
+                }
+            } else {
+            // two nodes per packed instruction: nodes (0, 1) and (2, 3)
+#pragma unroll
+            for (int c = 0; c < 4; c += 2) {
+                const float2 p2 = make_float2(pv[c], pv[c + 1]);
+                const float2 r2 = make_float2(pv[c + 1], c + 2 < 4 ? pv[c + 2] : right);
+                const float2 v1 = __ffma2_rn(splat2(cm), sub2(r2, p2), make_float2(m1[c], m1[c + 1]));
+                const float2 v2 = __ffma2_rn(splat2(cm), sub2(make_float2(up[c], up[c + 1]), p2),
+                                             make_float2(m2[c], m2[c + 1]));
+                float2 o1, o2;
+                prox_pair<NORM>(v1, v2, mu, o1, o2);
+                n1[c] = o1.x;
+                n1[c + 1] = o1.y;
+                n2[c] = o2.x;
+                n2[c + 1] = o2.y;
+            }
             }
             if constexpr (check) {
                 float d1[4], d2[4];
@@ -1260,11 +1279,26 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
             }
             const float bb[4] = {b.x, b.y, b.z, b.w};
             float pn[4];
+            if constexpr (!CL) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float Dn = (m1[c] - (c ? m1[c - 1] : l)) + (m2[c] - bb[c]);
-                pn[c] = fmaf(ct, fmaf(2.f, Dn, -Dv[c]), fmaf(-tau, rv[c], pv[c]));
-                Dv[c] = Dn;
+                for (int c = 0; c < 4; ++c) {
+                    const float Dn = (m1[c] - (c ? m1[c - 1] : l)) + (m2[c] - bb[c]);
+                    pn[c] = fmaf(ct, fmaf(2.f, Dn, -Dv[c]), fmaf(-tau, rv[c], pv[c]));
+                    Dv[c] = Dn;
+                }
+            } else {
+#pragma unroll
+            for (int c = 0; c < 4; c += 2) {
+                const float2 Dn = __fadd2_rn(sub2(make_float2(m1[c], m1[c + 1]), make_float2(c ? m1[c - 1] : l, m1[c])),
+                                             sub2(make_float2(m2[c], m2[c + 1]), make_float2(bb[c], bb[c + 1])));
+                const float2 q = __ffma2_rn(splat2(ct), __ffma2_rn(splat2(2.f), Dn, neg2(make_float2(Dv[c], Dv[c + 1]))),
+                                            __ffma2_rn(splat2(-tau), make_float2(rv[c], rv[c + 1]),
+                                                       make_float2(pv[c], pv[c + 1])));
+                pn[c] = q.x;
+                pn[c + 1] = q.y;
+                Dv[c] = Dn.x;
+                Dv[c + 1] = Dn.y;
+            }
             }
             if constexpr (check) {
                 const float4 e1 = *reinterpret_cast<const float4*>(e1s + idx);
@@ -1432,6 +1466,8 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
     // run r of this thread: nodes 4 q .. 4 q + 3 of the band, q = t + r T;
     // pk = (row << 16) | column of its first node, or -1 past the band
     int pk[RESW_RUNS];
+    // the band index of run r's first node is id0 + r RESW_RUN_STRIDE (blockDim.x == RES_THREADS)
+    const int id0 = 4 * t;
     // h div m^k in registers unless it lives in tensor memory (then rho is there
     // too; otherwise rho is re-read from L1/L2 every step: registers are scarce)
     float Dv[TM ? 1 : RESW_RUNS][4];
@@ -1487,10 +1523,11 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
     // previous lane by a shuffle: a warp's runs are all present or all absent,
     // since the band holds a multiple of 128 nodes); the row below the band is
     // read from the CTA below (initial state) or from the halo row it pushed
-    auto divergence = [&](int r, float out[4], auto halo) {
-        const int jl = pk[r] >> 16, i0 = pk[r] & 0xffff, id = jl * nx + i0;
+    auto divergence = [&](auto rc, float out[4], auto halo) {
+        constexpr int r = decltype(rc)::value;
+        const int jl = pk[r] >> 16, i0 = pk[r] & 0xffff, id = id0 + r * RESW_RUN_STRIDE;
         float4 m1;
-        if constexpr (TM && decltype(halo)::value) m1 = tmem_ld4(tb + 16u * r + 12u);
+        if constexpr (TM && decltype(halo)::value) m1 = tmem_ld4_at<16 * r + 12>(tb);
         else m1 = *reinterpret_cast<const float4*>(s1 + id);
         const float ln = __shfl_up_sync(FULL, m1.w, 1);
         const float4 m2 = *reinterpret_cast<const float4*>(s2 + id);
@@ -1507,22 +1544,27 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
                 b = dsmem_ld4(s2_dn + 4u * i0);
             }
         }
-        out[0] = (m1.x - l) + (m2.x - b.x);
-        out[1] = (m1.y - m1.x) + (m2.y - b.y);
-        out[2] = (m1.z - m1.y) + (m2.z - b.z);
-        out[3] = (m1.w - m1.z) + (m2.w - b.w);
+        const float2 d01 = __fadd2_rn(sub2(make_float2(m1.x, m1.y), make_float2(l, m1.x)),
+                                      sub2(make_float2(m2.x, m2.y), make_float2(b.x, b.y)));
+        const float2 d23 = __fadd2_rn(sub2(make_float2(m1.z, m1.w), make_float2(m1.y, m1.z)),
+                                      sub2(make_float2(m2.z, m2.w), make_float2(b.z, b.w)));
+        out[0] = d01.x;
+        out[1] = d01.y;
+        out[2] = d23.x;
+        out[3] = d23.y;
     };
-#pragma unroll
-    for (int r = 0; r < RESW_RUNS; ++r)
+    static_for<RESW_RUNS>([&](auto rc) {
+        constexpr int r = decltype(rc)::value;
         if (pk[r] >= 0) {
             if constexpr (TM) {
                 float d0[4];
-                divergence(r, d0, std::false_type{});
-                tmem_st4(tb + 16u * r + 4u, make_float4(d0[0], d0[1], d0[2], d0[3]));
+                divergence(rc, d0, std::false_type{});
+                tmem_st4_at<16 * r + 4>(tb, make_float4(d0[0], d0[1], d0[2], d0[3]));
             } else {
-                divergence(r, Dv[r], std::false_type{});
+                divergence(rc, Dv[r], std::false_type{});
             }
         }
+    });
     if (TM) tmem_wait_st();
     // the start time, R^k and the decision live in CTA 0's slots (registers are scarce)
     if (rank == 0 && t == 0) {
@@ -1552,15 +1594,15 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
         constexpr bool check = decltype(test)::value;
         // ---- phase A: m' = prox(m + mu grad phi); on the last column and the top
         // row the gradient component is zero and so is m, hence m' too
-#pragma unroll
-        for (int r = 0; r < RESW_RUNS; ++r) {
-            if (pk[r] < 0) continue;
-            const int jl = pk[r] >> 16, i0 = pk[r] & 0xffff, id = jl * nx + i0;
-            const float4 p4 = TM ? tmem_ld4(tb + 16u * r + 8u) : *reinterpret_cast<const float4*>(ph + id);
+        static_for<RESW_RUNS>([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            if (pk[r] < 0) return;
+            const int jl = pk[r] >> 16, i0 = pk[r] & 0xffff, id = id0 + r * RESW_RUN_STRIDE;
+            const float4 p4 = TM ? tmem_ld4_at<16 * r + 8>(tb) : *reinterpret_cast<const float4*>(ph + id);
             const float rn = __shfl_down_sync(FULL, p4.x, 1);
             const int j = jb + jl;
             const bool last_col = i0 + 4 == nx;
-            const float4 a1 = TM ? tmem_ld4(tb + 16u * r + 12u) : *reinterpret_cast<const float4*>(s1 + id);
+            const float4 a1 = TM ? tmem_ld4_at<16 * r + 12>(tb) : *reinterpret_cast<const float4*>(s1 + id);
             const float4 a2 = *reinterpret_cast<const float4*>(s2 + id);
             float4 u = p4;
             if (j < ny - 1) {
@@ -1577,16 +1619,28 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             const float m1[4] = {a1.x, a1.y, a1.z, a1.w}, m2[4] = {a2.x, a2.y, a2.z, a2.w};
             float n1[4], n2[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float pr_ = c < 3 ? pv[c + 1] : right;
-                prox<NORM>(fmaf(cm, pr_ - pv[c], m1[c]), fmaf(cm, up[c] - pv[c], m2[c]), mu, n1[c], n2[c]);
-                if (check) {
+            for (int c = 0; c < 4; c += 2) {  // two nodes per packed instruction
+                const float2 p2 = make_float2(pv[c], pv[c + 1]);
+                const float2 r2 = make_float2(pv[c + 1], c + 2 < 4 ? pv[c + 2] : right);
+                const float2 v1 = __ffma2_rn(splat2(cm), sub2(r2, p2), make_float2(m1[c], m1[c + 1]));
+                const float2 v2 = __ffma2_rn(splat2(cm), sub2(make_float2(up[c], up[c + 1]), p2),
+                                             make_float2(m2[c], m2[c + 1]));
+                float2 o1, o2;
+                prox_pair<NORM>(v1, v2, mu, o1, o2);
+                n1[c] = o1.x;
+                n1[c + 1] = o1.y;
+                n2[c] = o2.x;
+                n2[c + 1] = o2.y;
+            }
+            if (check) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
                     const float d1 = n1[c] - m1[c], d2 = n2[c] - m2[c];
                     sa = fmaf(d1, d1, fmaf(d2, d2, sa));
                 }
             }
             if constexpr (TM) {  // neighbours read only the run's last m1 (left of the next run)
-                tmem_st4(tb + 16u * r + 12u, make_float4(n1[0], n1[1], n1[2], n1[3]));
+                tmem_st4_at<16 * r + 12>(tb, make_float4(n1[0], n1[1], n1[2], n1[3]));
                 s1[id + 3] = n1[3];
             } else {
                 *reinterpret_cast<float4*>(s1 + id) = make_float4(n1[0], n1[1], n1[2], n1[3]);
@@ -1595,21 +1649,21 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             if (has_up && jl == rows - 1 && pushes)
                 st_async4(dsmem_map(smem_u32(hm2 + i0), rank + 1), make_float4(n2[0], n2[1], n2[2], n2[3]),
                           dsmem_map(bar_m2, rank + 1));
-        }
+        });
         if constexpr (TM) tmem_wait_st();  // m1' is in place before phase B reads it
         __syncthreads();
         // ---- phase B: phi' = phi + tau (div(2m' - m) - rho)
-#pragma unroll
-        for (int r = 0; r < RESW_RUNS; ++r) {
-            if (pk[r] < 0) continue;
+        static_for<RESW_RUNS>([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            if (pk[r] < 0) return;
             float Dn[4];
-            divergence(r, Dn, std::true_type{});
-            const int id = (pk[r] >> 16) * nx + (pk[r] & 0xffff);
-            const float4 p4 = TM ? tmem_ld4(tb + 16u * r + 8u) : *reinterpret_cast<const float4*>(ph + id);
+            divergence(rc, Dn, std::true_type{});
+            const int id = id0 + r * RESW_RUN_STRIDE;
+            const float4 p4 = TM ? tmem_ld4_at<16 * r + 8>(tb) : *reinterpret_cast<const float4*>(ph + id);
             float4 r4, d4;
             if constexpr (TM) {
-                r4 = tmem_ld4(tb + 16u * r);
-                d4 = tmem_ld4(tb + 16u * r + 4u);
+                r4 = tmem_ld4_at<16 * r>(tb);
+                d4 = tmem_ld4_at<16 * r + 4>(tb);
             } else {
                 r4 = __ldg(reinterpret_cast<const float4*>(rho + id));
                 d4 = make_float4(Dv[r][0], Dv[r][1], Dv[r][2], Dv[r][3]);
@@ -1618,8 +1672,15 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             const float Do[4] = {d4.x, d4.y, d4.z, d4.w};
             float pn[4];
 #pragma unroll
+            for (int c = 0; c < 4; c += 2) {
+                const float2 q = __ffma2_rn(
+                    splat2(ct), __ffma2_rn(splat2(2.f), make_float2(Dn[c], Dn[c + 1]), neg2(make_float2(Do[c], Do[c + 1]))),
+                    __ffma2_rn(splat2(-tau), make_float2(rv[c], rv[c + 1]), make_float2(pv[c], pv[c + 1])));
+                pn[c] = q.x;
+                pn[c + 1] = q.y;
+            }
+#pragma unroll
             for (int c = 0; c < 4; ++c) {
-                pn[c] = fmaf(ct, fmaf(2.f, Dn[c], -Do[c]), fmaf(-tau, rv[c], pv[c]));
                 if (check) {
                     const float ep = pn[c] - pv[c];
                     sb = fmaf(ep, ep, sb);
@@ -1628,14 +1689,14 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
                 if constexpr (!TM) Dv[r][c] = Dn[c];
             }
             if constexpr (TM) {
-                tmem_st4(tb + 16u * r + 4u, make_float4(Dn[0], Dn[1], Dn[2], Dn[3]));
-                tmem_st4(tb + 16u * r + 8u, make_float4(pn[0], pn[1], pn[2], pn[3]));
+                tmem_st4_at<16 * r + 4>(tb, make_float4(Dn[0], Dn[1], Dn[2], Dn[3]));
+                tmem_st4_at<16 * r + 8>(tb, make_float4(pn[0], pn[1], pn[2], pn[3]));
             }
             *reinterpret_cast<float4*>(ph + id) = make_float4(pn[0], pn[1], pn[2], pn[3]);
             if (has_dn && id < nx && pushes)
                 st_async4(dsmem_map(smem_u32(hphi + id), rank - 1), make_float4(pn[0], pn[1], pn[2], pn[3]),
                           dsmem_map(bar_phi, rank - 1));
-        }
+        });
         if constexpr (TM) tmem_wait_st();  // this step's D and phi are in place before the next reads them
         par ^= 1u;
         __syncthreads();

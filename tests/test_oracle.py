@@ -113,6 +113,8 @@ def test_p1_matches_exact_lp(shape):
     res = tight(rho, h, L1, tol=1e-8)
     assert abs(res.stats.f - exact) <= 1e-6 * exact
     assert res.stats.lb <= exact * (1 + 1e-12) and res.stats.ub >= exact * (1 - 1e-12)
+    # strong duality and dual feasibility of the potential (||grad phi||_inf <= 1, eq. opt_dual3)
+    assert abs(res.stats.dual - exact) <= 1e-6 * exact and res.stats.gmax <= 1.0 + 1e-5
 
 
 def test_p1_matches_network_simplex_16x16():
