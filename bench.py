@@ -130,12 +130,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# eps_L of eq. stop_tol at h = 1/N, scaled per ground norm.  The scales are
+# eps_L of eq. stop_tol at h = 1/N, scaled per ground norm, and the alpha of the
+# level schedule: the library's calibrated schedule (w1_options.schedule = 1),
+# copied here for the oracle arm, which runs without the library.  They are
 # calibrated against the converged values of tests/golden/converged_512.json:
 # with them every reference pair's reported W1 (the saddle value) lies within
 # relative 1e-4 of its converged value with a margin of at least three (p = 1
 # meets it at the paper's own eps_L; p = 2 needs a tenth of it).
 TOL_SCALE = {1: 1.0, 2: 0.1}
+ALPHA = {1: -1.0, 2: -1.0}  # eps_l = eps_L (h_l / h)^alpha (eq. tol_formula_propose)
 
 
 def stop_tol(n: int, norm: int) -> float:
@@ -150,7 +153,8 @@ def _oracle_solve(spec):
     r0, r1 = synth.pair(WORKLOAD, k, n=n)
     _, _, d0, d1 = synth.to_f32_pair(r0, r1)
     t0 = time.perf_counter()
-    res = oracle.multilevel(d0, d1, levels=levels, norm=norm, tol=stop_tol(n, norm), stop=oracle.STOP_FPR)
+    res = oracle.multilevel(d0, d1, levels=levels, norm=norm, tol=stop_tol(n, norm), alpha=ALPHA[norm],
+                            stop=oracle.STOP_FPR)
     return norm, time.perf_counter() - t0, res.status
 
 
@@ -219,7 +223,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"ellipse_texture_{n}x{n}_pairs_{levels}_levels_both_norms", "grid": [n, n],
                    "levels": levels, "norms": ["L1", "L2"],
-                   "stop": "FPR R^k < eps_l, eps_L of eq. stop_tol x " + str(TOL_SCALE),
+                   "stop": "FPR R^k < eps_l, eps_L of eq. stop_tol x " + str(TOL_SCALE) + ", alpha " + str(ALPHA),
                    "estimate": "saddle value (Lagrangian of eq. minmax_cp)"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample,
                          "seconds_per_solve": per},
@@ -303,8 +307,9 @@ def run_gpu(args):
     tol = {norm: (stop_tol(N, norm) if args.algorithm == 3 else 0.0) for norm in NORMS}
 
     def new_plan(norm, batch=1, tune=None):
-        return w1.Plan(N, N, levels=LEVELS, norm=norm, tol=tol[norm], batch=batch, eager=int(args.eager),
-                       algorithm=args.algorithm, check_every=args.check_every,
+        # Algorithm 3: the calibrated schedule (tol <= 0: its eps_L scale and alpha)
+        return w1.Plan(N, N, levels=LEVELS, norm=norm, tol=0.0, batch=batch, eager=int(args.eager),
+                       algorithm=args.algorithm, check_every=args.check_every, schedule=int(args.algorithm == 3),
                        tune=args.tune if tune is None else tune)
 
     if args.mode == "lockstep":
@@ -574,8 +579,10 @@ def run_gpu(args):
                        "levels": LEVELS, "norms": ["L1", "L2"],
                        "algorithm": {3: "Algorithm 3 (multilevel Chambolle-Pock)",
                                      4: "Algorithm 4 (multilevel prox-PDHG)"}[args.algorithm],
-                       "stop": ("FPR R^k < eps_l (eq. pd_stop), eps_l = eps_L (h_l/h)^-1, eps_L of eq. stop_tol x "
-                                + json.dumps({f"L{k}": v for k, v in TOL_SCALE.items()}))
+                       "stop": ("FPR R^k < eps_l (eq. pd_stop), eps_l = eps_L (h_l/h)^alpha, eps_L of eq. stop_tol x "
+                                "scale; the calibrated schedule (w1_options.schedule = 1): scale "
+                                + json.dumps({f"L{k}": v for k, v in TOL_SCALE.items()}) + ", alpha "
+                                + json.dumps({f"L{k}": v for k, v in ALPHA.items()}))
                        if args.algorithm == 3 else "eq. stop_tol for Algorithm 4",
                        "tol": {f"L{k}": v for k, v in tol.items()},
                        "estimate": "saddle value: Lagrangian of eq. minmax_cp at the returned pair",
@@ -1160,15 +1167,15 @@ def serve_summary(w1, torch, args):
     pool = serve_pool(torch)
     out = []
     with w1.Server(hbm_budget_bytes=40 << 30, max_slots=args.slots, max_batch=args.serve_batch,
-                   latency_below=args.latency_below) as srv:
+                   latency_below=args.latency_below, schedule=1) as srv:
         if args.latency_below > 0:
             for size in SERVE_SIZES:
                 for norm in NORMS:
                     a0, a1 = pool[size][0]
-                    srv.wait(srv.submit(a0, a1, norm=norm, tol=stop_tol(size, norm)))
-        serve_run(w1, srv, pool, 1000.0, 32, seed=1, tol_of=stop_tol)
+                    srv.wait(srv.submit(a0, a1, norm=norm))
+        serve_run(w1, srv, pool, 1000.0, 32, seed=1)
         for rate, n_req in ((float(r), int(q)) for r, q in (x.split(":") for x in args.serve_summary.split(","))):
-            p50, p99, thr, sts = serve_run(w1, srv, pool, rate, n_req, seed=int(rate), tol_of=stop_tol)
+            p50, p99, thr, sts = serve_run(w1, srv, pool, rate, n_req, seed=int(rate))
             out.append({"rate_req_s": rate, "requests": n_req, "p50_ms": p50, "p99_ms": p99, "solves_per_s": thr,
                         "not_ok": sum(1 for x in sts if x != w1.OK)})
         info = srv.info()

@@ -147,6 +147,30 @@ int fault_halo_rank()
 }
 }  // namespace w1
 
+// The calibrated tolerance schedules (w1_options.schedule = 1), p = 1 then p = 2:
+// the scale of eq. stop_tol's eps_L and the alpha of eq. tol_formula_propose.
+struct CalibratedSchedule {
+    double tol_scale, alpha;
+};
+static constexpr CalibratedSchedule kCalibrated[2] = {{1.0, -1.0}, {0.1, -1.0}};
+
+extern "C" w1_status w1_calibrated_schedule(int norm, double* tol_scale, double* alpha)
+{
+    if (!tol_scale || !alpha) return fail(W1_ERR_INVALID_ARG, "NULL output");
+    if (norm == W1_NORM_L1 || norm == W1_NORM_L2) {
+        const CalibratedSchedule& c = kCalibrated[norm == W1_NORM_L1 ? 0 : 1];
+        *tol_scale = c.tol_scale;
+        *alpha = c.alpha;
+        return W1_OK;
+    }
+    if (norm == W1_NORM_LINF) {
+        *tol_scale = 1.0;
+        *alpha = -1.0;
+        return W1_OK;
+    }
+    return fail(W1_ERR_INVALID_ARG, "norm must be 1, 2 or 3");
+}
+
 extern "C" void w1_default_options(w1_options* o)
 {
     if (!o) return;
@@ -160,6 +184,7 @@ extern "C" void w1_default_options(w1_options* o)
     o->eager = 0;
     o->tune = 0;
     o->algorithm = 3;
+    o->schedule = 0;
     o->estimate = 0;
 }
 
@@ -269,6 +294,7 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
     if (o.path < 0 || o.path > 3) return fail(W1_ERR_INVALID_ARG, "path must be 0, 1, 2 or 3");
     if (o.tune < 0 || o.tune > 3) return fail(W1_ERR_INVALID_ARG, "tune must be 0, 1, 2 or 3");
     if (o.estimate < 0 || o.estimate > 1) return fail(W1_ERR_INVALID_ARG, "estimate must be 0 or 1");
+    if (o.schedule < 0 || o.schedule > 1) return fail(W1_ERR_INVALID_ARG, "schedule must be 0 or 1");
     if (o.tile < 0 || o.tile > W1_TILE_VARIANTS) return fail(W1_ERR_INVALID_ARG, "tile must lie in [0, W1_TILE_VARIANTS]");
     if (o.check_every % (2 * tblock_depth(o.tile > 0 ? o.tile - 1 : 0)) != 0)
         return fail(W1_ERR_INVALID_ARG, "check_every must be a multiple of twice the temporal block depth");
@@ -289,10 +315,18 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
     if (nx % div || ny % div) return fail(W1_ERR_SHAPE, "nx and ny must be divisible by 2^(levels-1)");
     const bool alg4 = o.algorithm == 4;
     if (o.algorithm != 0 && o.algorithm != 3 && !alg4) return fail(W1_ERR_INVALID_ARG, "algorithm must be 3 or 4");
+    double tol_scale = 1.0;
+    if (o.schedule == 1 && !alg4 && norm != W1_NORM_LINF) {
+        // calibrated schedule (w1_options.schedule): measured on the 512^2
+        // ellipse-texture pairs against their converged W1 with the saddle estimate
+        const CalibratedSchedule& c = kCalibrated[norm == W1_NORM_L1 ? 0 : 1];
+        tol_scale = c.tol_scale;
+        o.alpha = c.alpha;
+    }
     if (!(tol > 0.0)) {
         const double s2 = (512.0 * h) * (512.0 * h);
         tol = alg4 ? std::min(2e-4, 1e-4 / 32.0 * s2)  // eq. stop_tol, Alg. 4
-                   : 1e-6 / 128.0 * s2;                // eq. stop_tol, Alg. 3
+                   : 1e-6 / 128.0 * s2 * tol_scale;    // eq. stop_tol, Alg. 3
     }
     int dev = 0;
     W1_CK(cudaGetDevice(&dev));

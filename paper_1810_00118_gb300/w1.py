@@ -47,7 +47,8 @@ class Options(ctypes.Structure):
     _fields_ = [("check_every", ctypes.c_int), ("max_iters", ctypes.c_longlong), ("theta", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("time_budget_s", ctypes.c_double), ("path", ctypes.c_int),
                 ("rows_per_thread", ctypes.c_int), ("eager", ctypes.c_int), ("tune", ctypes.c_int),
-                ("algorithm", ctypes.c_int), ("tile", ctypes.c_int), ("estimate", ctypes.c_int)]
+                ("algorithm", ctypes.c_int), ("tile", ctypes.c_int), ("schedule", ctypes.c_int),
+                ("estimate", ctypes.c_int)]
 
 
 class LevelChoice(ctypes.Structure):
@@ -119,6 +120,7 @@ def _load() -> ctypes.CDLL:
     st = ctypes.c_int
     sig = {
         "w1_default_options": (None, [ctypes.POINTER(Options)]),
+        "w1_calibrated_schedule": (st, [I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "w1_plan_create": (st, [I, I, D, I, I, D, ctypes.POINTER(P)]),
         "w1_plan_create_ex": (st, [I, I, D, I, I, D, ctypes.POINTER(Options), ctypes.POINTER(P)]),
         "w1_plan_create_batch": (st, [I, I, D, I, I, D, I, ctypes.POINTER(Options), ctypes.POINTER(P)]),
@@ -200,6 +202,13 @@ def default_options(**kw) -> Options:
             raise TypeError(f"unknown option {k}")
         setattr(o, k, v)
     return o
+
+
+def calibrated_schedule(norm) -> tuple:
+    """(eps_L scale, alpha) of w1_options.schedule = 1 for a norm (host only)."""
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(_lib.w1_calibrated_schedule(norm, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def _dev_ptr(t, shape=None):

@@ -37,3 +37,13 @@ def test_pair_ids_disjoint_across_ranks_and_steps():
             ids = bench.pair_ids(rank, step, 128)
             assert len(ids) == 128 and not (seen & set(ids))
             seen |= set(ids)
+
+
+def test_bench_schedule_is_the_library_calibrated_schedule():
+    """The oracle arm needs the benchmark's tolerance schedule without a GPU, so
+    bench.py keeps its own copy; it must equal the library's
+    w1_options.schedule = 1 table (a host-only call)."""
+    from paper_1810_00118_gb300 import w1
+    for norm in bench.NORMS:
+        scale, alpha = w1.calibrated_schedule(norm)
+        assert scale == bench.TOL_SCALE[norm] and alpha == bench.ALPHA[norm]
