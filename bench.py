@@ -921,7 +921,8 @@ def run_tol_sweep(args):
     """Tolerance schedule study (eq. tol_formula_propose, the alpha study of
     Sec. 6.2, the level count of Sec. 6.3) on the 512^2 workload: for each
     norm, eps_l = s * eps_L (h_l / h)^alpha with eps_L of eq. stop_tol, for
-    several scales s, alphas and level counts; the reported W1 (saddle value)
+    several scales s, alphas and step sizes theta (mu = tau = theta / ||A_h||);
+    the reported W1 (saddle value)
     of the reference pairs against their converged values
     (tests/golden/converged_512.json) and the throughput of a batch of lanes
     (one plan and stream per pair, CUDA events)."""
@@ -947,12 +948,14 @@ def run_tol_sweep(args):
         # the throughput batch: the reference pairs repeated to args.batch lanes
         B = max(args.batch, len(ids))
         lanes = [torch.cuda.Stream() for _ in range(B)]
-        scales = (10.0, 3.0, 1.0, 0.3) if norm == 1 else (0.3, 0.1, 0.03)
-        for levels in (LEVELS, LEVELS + 1):
-            for alpha in (-1.0, -0.5, 0.0, 0.5):
+        scales = (100.0, 30.0, 10.0, 3.0) if norm == 1 else (1.0, 0.3, 0.1, 0.03)
+        levels = LEVELS
+        for theta in (0.5, 1.0):
+            for alpha in (-1.0, 0.0, 0.5):
                 for scale in scales:
                     tol = 1e-6 / 128 * scale
-                    plans = [w1.Plan(N, N, levels=levels, norm=norm, tol=tol, alpha=alpha) for _ in range(B)]
+                    plans = [w1.Plan(N, N, levels=levels, norm=norm, tol=tol, alpha=alpha, theta=theta)
+                             for _ in range(B)]
                     for rep in range(2):  # first pass: graph builds; second: timed
                         ready = torch.cuda.Event()
                         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -965,17 +968,21 @@ def run_tol_sweep(args):
                             stream.wait_stream(lanes[b])
                         e1.record(stream)
                         torch.cuda.synchronize()
-                    errs, ok = [], 0
+                    errs, ok = {}, 0
                     for b, p in enumerate(plans):
                         v, st, ps, _ = p.results(allow=every)
                         ok += ps[0] == w1.OK
                         if b < len(ids):
-                            errs.append((v[0] - conv[norm][ids[b]]) / conv[norm][ids[b]])
+                            errs[ids[b]] = (v[0] - conv[norm][ids[b]]) / conv[norm][ids[b]]
                         p.close()
                     ms = e0.elapsed_time(e1)
-                    out.append({"norm": norm, "levels": levels, "alpha": alpha, "scale": scale,
-                                "solves_per_s": ok / (ms / 1e3), "max_abs_rel_err": float(np.max(np.abs(errs))),
-                                "rel_errs": [float(x) for x in errs]})
+                    cal = [abs(e) for k, e in errs.items() if k < 8]
+                    held = [abs(e) for k, e in errs.items() if k >= 8]
+                    out.append({"norm": norm, "levels": levels, "theta": theta, "alpha": alpha, "scale": scale,
+                                "solves_per_s": ok / (ms / 1e3), "not_ok": B - ok,
+                                "max_abs_rel_err_calibration": float(max(cal)) if cal else None,
+                                "max_abs_rel_err_held_out": float(max(held)) if held else None,
+                                "rel_errs": {str(k): float(e) for k, e in errs.items()}})
                     print(json.dumps(out[-1]), flush=True)
     print(json.dumps({"only": "tol-sweep", "grid": N, "batch": args.batch, "reference_pairs": {
         f"L{n}": sorted(conv[n]) for n in NORMS}, "rows": out}))

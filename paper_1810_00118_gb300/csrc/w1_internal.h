@@ -219,7 +219,7 @@ cudaError_t launch_pd_potential(const PdArgs& a, float* phi_out, cudaStream_t s)
 // FIN_PART_PER_BLOCK doubles of partial sums: final_part_doubles(pairs) =
 // FIN_BLOCKS_PER_PAIR * FIN_PART_PER_BLOCK * pairs.
 static constexpr int FIN_BLOCKS_PER_PAIR = 64;
-static constexpr int FIN_PART_PER_BLOCK = 11;  // five compensated sums (s, c) and a maximum
+static constexpr int FIN_PART_PER_BLOCK = 13;  // six compensated sums (s, c) and a maximum
 cudaError_t launch_final(int norm, const float* m1, const float* m2, const float* phi, const float* rho, int nx,
                          int ny, double h, double* q, double* part, Ctl* ctl, int pairs, cudaStream_t s);
 size_t final_part_doubles(int pairs);

@@ -2171,14 +2171,17 @@ size_t final_part_doubles(int pairs) { return (size_t)final_blocks_per_pair(pair
 //   ||m(x)||_p, phi rho, |e|, |rho|, phi e, and ||grad phi(x)||_q.
 // Each sum is compensated and left unscaled; h^2 is applied once at the end.
 // Every term except the p = 2 norm and e is exact in FP64 (products and sums
-// of two FP32 values).
+// of two FP32 values).  When nx and ny are both even, each thread takes 2 x 2
+// blocks of nodes and also does the first level of the route bound (see
+// k_final_b): the cost of sending each node's residual mass to its block's
+// first node, and the block's total, stored compactly in q for the next level.
 template <int NORM>
 __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict__ m1, const float* __restrict__ m2,
                                                          const float* __restrict__ phi, const float* __restrict__ rho,
                                                          int nx, int ny, double h, double* __restrict__ q,
                                                          double* part, const Ctl* ctls)
 {
-    __shared__ double sh[64 * 5];
+    __shared__ double sh[64 * 6];
     const int pair = blockIdx.y;
     if (ctls && ctls[pair].error == 2) return;
     const long long n = (long long)nx * ny;
@@ -2188,11 +2191,12 @@ __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict
     phi += off;
     rho += off;
     q += 2 * off;
-    CSum v[5];  // sum ||m||_p, sum phi rho, sum |e|, sum |rho|, sum phi e
+    CSum v[6];  // sum ||m||_p, sum phi rho, sum |e|, sum |rho|, sum phi e, first-level route cost
     double gm = 0.0;
     const double h2 = h * h;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(k / nx), i = (int)(k - (long long)j * nx);
+    // the node's terms; returns its residual mass e h^2
+    auto node = [&](int i, int j) -> double {
+        const long long k = (long long)j * nx + i;
         const double a1 = (i < nx - 1) ? (double)m1[k] : 0.0;
         const double a2 = (j < ny - 1) ? (double)m2[k] : 0.0;
         v[0].add(NORM == W1_NORM_L1     ? __dadd_rn(fabs(a1), fabs(a2))
@@ -2204,7 +2208,6 @@ __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict
         if (i > 0) d = __dsub_rn(d, (double)m1[k - 1]);
         if (j > 0) d = __dsub_rn(d, (double)m2[k - nx]);
         const double e = __dsub_rn(r, __ddiv_rn(d, h));
-        q[k] = e * h2;
         v[2].add(fabs(e));
         v[3].add(fabs(r));
         v[4].add(__dmul_rn(p, e));
@@ -2213,8 +2216,29 @@ __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict
         const double gq = (NORM == W1_NORM_L1) ? fmax(fabs(g1), fabs(g2))
                           : (NORM == W1_NORM_LINF ? fabs(g1) + fabs(g2) : sqrt(g1 * g1 + g2 * g2));
         gm = fmax(gm, gq);
+        return e * h2;
+    };
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if ((nx & 1) == 0 && (ny & 1) == 0) {
+        const int ncx = nx / 2;
+        const long long nc = n / 4;
+        for (long long kb = blockIdx.x * (long long)blockDim.x + threadIdx.x; kb < nc; kb += stride) {
+            const int J = (int)(kb / ncx), I = (int)(kb - (long long)J * ncx);
+            const double q00 = node(2 * I, 2 * J), q10 = node(2 * I + 1, 2 * J);
+            const double q01 = node(2 * I, 2 * J + 1), q11 = node(2 * I + 1, 2 * J + 1);
+            // offsets (1,0) and (0,1) cost one edge h, (1,1) two
+            v[5].add(__dmul_rn(fabs(q10), h));
+            v[5].add(__dmul_rn(fabs(q01), h));
+            v[5].add(__dmul_rn(fabs(q11), 2.0 * h));
+            q[kb] = ((q00 + q10) + q01) + q11;
+        }
+    } else {
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += stride) {
+            const int j = (int)(k / nx), i = (int)(k - (long long)j * nx);
+            q[k] = node(i, j);
+        }
     }
-    block_csum<5>(v, sh);
+    block_csum<6>(v, sh);
     gm = warp_max(gm);
     __shared__ double shm[32];
     if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = gm;
@@ -2222,11 +2246,11 @@ __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) gm = fmax(gm, shm[w]);
         double* pp = part + ((size_t)pair * gridDim.x + blockIdx.x) * FIN_PART_PER_BLOCK;
-        for (int c = 0; c < 5; ++c) {
+        for (int c = 0; c < 6; ++c) {
             pp[2 * c] = v[c].s;
             pp[2 * c + 1] = v[c].c;
         }
-        pp[10] = gm;
+        pp[12] = gm;
     }
 }
 
@@ -2247,20 +2271,21 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
     double* src = q + 2 * n * pair;
     double* dst = src + n;
     part += (size_t)pair * nparts * FIN_PART_PER_BLOCK;
-    __shared__ double sh[64 * 5];
-    CSum v[5];
+    __shared__ double sh[64 * 6];
+    CSum v[6];
     double gm = 0.0;
     for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
-        for (int c = 0; c < 5; ++c) {
+        for (int c = 0; c < 6; ++c) {
             CSum x;
             x.s = part[b * FIN_PART_PER_BLOCK + 2 * c];
             x.c = part[b * FIN_PART_PER_BLOCK + 2 * c + 1];
             v[c].add(x);
         }
-        gm = fmax(gm, part[b * FIN_PART_PER_BLOCK + 10]);
+        gm = fmax(gm, part[b * FIN_PART_PER_BLOCK + 12]);
     }
-    block_csum<5>(v, sh);
+    block_csum<6>(v, sh);
     __shared__ double tot[5], sad;
+    __shared__ CSum cost0;
     if (threadIdx.x == 0) {
         for (int c = 0; c < 5; ++c) tot[c] = v[c].value();
         CSum lag = v[0], pe;
@@ -2268,6 +2293,7 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
         pe.c = -v[4].c;
         lag.add(pe);
         sad = lag.value();
+        cost0 = v[5];
     }
     gm = warp_max(gm);
     __shared__ double shm[32];
@@ -2276,8 +2302,10 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
     if (threadIdx.x == 0)
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) gm = fmax(gm, shm[w]);
 
-    int cx = nx, cy = ny;
-    double hx = h, hy = h;
+    // k_final_a did the first level of the tree when both sides are even
+    const bool pooled = (nx & 1) == 0 && (ny & 1) == 0;
+    int cx = pooled ? nx / 2 : nx, cy = pooled ? ny / 2 : ny;
+    double hx = pooled ? 2.0 * h : h, hy = pooled ? 2.0 * h : h;
     CSum cost;
     for (;;) {
         const int px = (cx > 1 && (cx & 1) == 0), py = (cy > 1 && (cy & 1) == 0);
@@ -2309,6 +2337,7 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
     }
     CSum ws[3];
     ws[0] = cost;
+    if (threadIdx.x == 0) ws[0].add(cost0);
     for (int k = threadIdx.x; k < cx * cy; k += blockDim.x) {
         const double x = src[k];
         if (x > 0) ws[1].add(x);

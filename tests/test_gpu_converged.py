@@ -9,9 +9,12 @@ targets):
   - the 1-D closed form sum |C_i| h on 1 x N strips, all norms (Sec. 2);
   - translated bumps: W1 = (|a| + |b|) h for a unit-mass bump shifted by (a, b)
     pixels away from the walls (p = 1; axis-aligned shifts for p = 2).
-A last test checks that the FP64 sums are compensated: on inputs built to
-cancel, the GPU's statistics equal the exactly rounded sums (math.fsum) of
-their FP64 terms.
+  - the 512^2 benchmark pairs against their converged values stored in
+    tests/golden/converged_512.json (exact LP for p = 1, the FP64 oracle at a
+    tolerance 10^4 times tighter than eq. stop_tol for p = 2).
+One test checks that the FP64 sums are compensated: on inputs built to cancel,
+the GPU's statistics equal the exactly rounded sums (math.fsum) of their FP64
+terms.
 """
 import math
 
@@ -152,3 +155,28 @@ def test_compensated_sums_match_fsum(w1):
     assert abs(st.mass0 - m0) <= 8 * np.spacing(m0) and abs(st.mass1 - m1) <= 8 * np.spacing(m1)
     shift = math.fsum((r0.astype(np.float64) - r1.astype(np.float64)).ravel().tolist()) / (n * n)
     assert abs(st.mass_shift - shift) <= 1e-15 * 100.0
+
+
+def _converged_512():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "converged_512.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("norm", [L1, L2])
+def test_512_pairs_meet_converged_values(w1, norm):
+    """The 512^2 ellipse-texture pairs of the benchmark, solved as the benchmark
+    does (6 levels, the calibrated schedule w1_options.schedule = 1), against
+    their converged W1 stored by oracle/make_converged_table.py (p = 1: exact
+    LP; p = 2: the FP64 oracle at eps_L / 1e4): relative 1e-4, on the pairs the
+    schedule was calibrated on and on held-out ones."""
+    table = _converged_512()[f"L{norm}"]
+    ids = sorted(int(k) for k in table)
+    with w1.Plan(512, 512, levels=6, norm=norm, schedule=1) as plan:
+        for k in ids:
+            r0, r1 = synth.pair(2, k)
+            val, st, status = plan.solve(dev(r0), dev(r1))
+            ref = table[str(k)]["w1"]
+            assert abs(val - ref) <= 1e-4 * ref, (k, val, ref, st.iters)
