@@ -133,12 +133,12 @@ class ClockSampler:
 # eps_L of eq. stop_tol at h = 1/N, scaled per ground norm, and the alpha of the
 # level schedule: the library's calibrated schedule (w1_options.schedule = 1),
 # copied here for the oracle arm, which runs without the library.  They are
-# calibrated against the converged values of tests/golden/converged_512.json:
-# with them every reference pair's reported W1 (the saddle value) lies within
-# relative 1e-4 of its converged value with a margin of at least three (p = 1
-# meets it at the paper's own eps_L; p = 2 needs a tenth of it).
-TOL_SCALE = {1: 1.0, 2: 0.1}
-ALPHA = {1: -1.0, 2: -1.0}  # eps_l = eps_L (h_l / h)^alpha (eq. tol_formula_propose)
+# calibrated against the converged values of tests/golden/converged_512.json
+# (bench.py --only tol-sweep): the fastest setting whose worst error over the
+# calibration pairs 0-7 is at most 2.5e-5, four times below 1e-4.
+TOL_SCALE = {1: 30.0, 2: 0.1}
+ALPHA = {1: 0.5, 2: -1.0}  # eps_l = eps_L (h_l / h)^alpha (eq. tol_formula_propose)
+THETA = {1: 1.0, 2: 1.0}   # mu = tau = theta / ||A_h|| (eq. primaldual; 1/2 the paper's, 1 its footnote's)
 
 
 def stop_tol(n: int, norm: int) -> float:
@@ -154,7 +154,7 @@ def _oracle_solve(spec):
     _, _, d0, d1 = synth.to_f32_pair(r0, r1)
     t0 = time.perf_counter()
     res = oracle.multilevel(d0, d1, levels=levels, norm=norm, tol=stop_tol(n, norm), alpha=ALPHA[norm],
-                            stop=oracle.STOP_FPR)
+                            theta=THETA[norm], stop=oracle.STOP_FPR)
     return norm, time.perf_counter() - t0, res.status
 
 
@@ -223,7 +223,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"ellipse_texture_{n}x{n}_pairs_{levels}_levels_both_norms", "grid": [n, n],
                    "levels": levels, "norms": ["L1", "L2"],
-                   "stop": "FPR R^k < eps_l, eps_L of eq. stop_tol x " + str(TOL_SCALE) + ", alpha " + str(ALPHA),
+                   "stop": "FPR R^k < eps_l, eps_L of eq. stop_tol x " + str(TOL_SCALE) + ", alpha " + str(ALPHA)
+                           + ", theta " + str(THETA),
                    "estimate": "saddle value (Lagrangian of eq. minmax_cp)"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample,
                          "seconds_per_solve": per},
@@ -528,6 +529,58 @@ def run_gpu(args):
                     "what": "reported W1 (saddle value) of each reference pair against its converged value; "
                             "primal: f(m) of the same solves"}
 
+    # secondary: the paper's own schedule (eq. stop_tol, alpha = -1, theta = 1/2)
+    # for the same pairs and lanes: throughput and the reference pairs' errors
+    paper = None
+    if args.paper_steps > 0 and args.mode == "lanes" and G == 1 and args.algorithm == 3:
+        pp = {norm: [w1.Plan(N, N, levels=LEVELS, norm=norm, batch=1) for _ in range(nlane)] for norm in NORMS}
+
+        def paper_step(s):
+            flush.fill_(float(s))
+            t0_, t1_ = dev_pairs[s]
+            ready_ev[0].record(stream)
+            for norm in NORMS:
+                for b in range(nlane):
+                    lanes[norm][b].wait_event(ready_ev[0])
+                    pp[norm][b].solve_async(t0_[b], t1_[b], stream=lanes[norm][b])
+                    done_ev[norm][0][b].record(lanes[norm][b])
+            sts_ = []
+            for norm in NORMS:
+                for b in range(nlane):
+                    done_ev[norm][0][b].synchronize()
+                    sts_.extend(pp[norm][b].results(allow=every)[2])
+                    stream.wait_event(done_ev[norm][0][b])
+            return sts_
+
+        paper_step(0)
+        barrier()
+        e0p, e1p = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0p.record(stream)
+        sts_p = [paper_step(args.warmup + s) for s in range(min(args.paper_steps, args.steps))]
+        e1p.record(stream)
+        barrier()
+        n_ok_p = sum(1 for x in sts_p for y in x if y == w1.OK)
+        paper = {"solves_per_s": n_ok_p / (e0p.elapsed_time(e1p) / 1e3), "steps": len(sts_p),
+                 "schedule": "eq. stop_tol eps_L, alpha -1, theta 1/2 (the paper's; w1_options.schedule = 0)"}
+        if conv and acc_ids:
+            a0p = torch.from_numpy(np.stack([x[0] for x in acc_pairs])).cuda()
+            a1p = torch.from_numpy(np.stack([x[1] for x in acc_pairs])).cuda()
+            errs_p = {}
+            for norm in NORMS:
+                e = []
+                for i, k in enumerate(acc_ids):
+                    if k not in conv[norm]:
+                        continue
+                    p = pp[norm][i % nlane]
+                    p.solve_async(a0p[i], a1p[i], stream=lanes[norm][i % nlane])
+                    lanes[norm][i % nlane].synchronize()
+                    e.append(abs(p.results(allow=every)[0][0] - conv[norm][k]) / conv[norm][k])
+                errs_p[f"L{norm}"] = float(max(e)) if e else None
+            paper["max_rel_err_vs_converged"] = errs_p
+        for norm in NORMS:
+            for p in pp[norm]:
+                p.close()
+
     # latency of one solve with the GPU otherwise idle: one pair at a time through
     # the blocking entry point, CUDA events around each solve
     solo = {}
@@ -582,7 +635,8 @@ def run_gpu(args):
                        "stop": ("FPR R^k < eps_l (eq. pd_stop), eps_l = eps_L (h_l/h)^alpha, eps_L of eq. stop_tol x "
                                 "scale; the calibrated schedule (w1_options.schedule = 1): scale "
                                 + json.dumps({f"L{k}": v for k, v in TOL_SCALE.items()}) + ", alpha "
-                                + json.dumps({f"L{k}": v for k, v in ALPHA.items()}))
+                                + json.dumps({f"L{k}": v for k, v in ALPHA.items()}) + ", theta "
+                                + json.dumps({f"L{k}": v for k, v in THETA.items()}))
                        if args.algorithm == 3 else "eq. stop_tol for Algorithm 4",
                        "tol": {f"L{k}": v for k, v in tol.items()},
                        "estimate": "saddle value: Lagrangian of eq. minmax_cp at the returned pair",
@@ -596,6 +650,7 @@ def run_gpu(args):
             "solves_counted": "status W1_OK only", "not_ok": not_ok,
             "max_rel_err_vs_converged": accuracy["max_rel_err_vs_converged"] if accuracy else None,
             "accuracy": accuracy,
+            "paper_schedule": paper,
             "batch_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                  "what": "one step (B pairs, both norms) / 2, submit to W1 values on the host "
                                          "(with pipelined steps the next step is already running meanwhile)"},
@@ -750,6 +805,8 @@ def main():
     ap.add_argument("--e2e-threads", type=int, default=64, help="e2e: host threads calling w1_solve_host")
     ap.add_argument("--no-extras", action="store_true", help="skip the short serving and mixed-batch legs")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the solves of the reference pairs")
+    ap.add_argument("--paper-steps", type=int, default=2,
+                    help="steps timed with the paper's own schedule beside the headline (0: skip)")
     ap.add_argument("--solo", type=int, default=8, help="pairs solved one at a time for the latency figure")
     ap.add_argument("--tune", type=int, default=0, choices=[0, 1, 2, 3],
                     help="lanes: per-level kernel choice (0 fixed rules, 1 latency, 3 SM-time; see w1_options.tune)")

@@ -103,11 +103,12 @@ typedef struct {
     int schedule;          /* level tolerances: 0 (default) eps_l = tol (h_l / h)^alpha as given;
                               1 the calibrated schedule for the saddle-value estimate at
                               relative 1e-4: per norm, an eps_L scale (applied to eq. stop_tol
-                              when tol <= 0) and an alpha that replaces opt.alpha, measured on
+                              when tol <= 0), an alpha and a theta that replace opt.alpha and
+                              opt.theta, measured on
                               the 512^2 ellipse-texture workload against converged W1 (the
-                              fastest setting whose worst error over the calibration pairs is
-                              at most 1e-4 / 3); p = infinity and 3-D solves keep the
-                              paper's values                                                */
+                              fastest setting whose worst error over the calibration pairs was
+                              at most 2.5e-5; w1_calibrated_schedule reports the values);
+                              p = infinity and 3-D solves keep the paper's values            */
     int estimate;          /* which value dist and w1_stats.w1 report:
                               0 (default): the saddle value, the Lagrangian of eq. minmax_cp
                                 L(m, phi) = f(m) + <phi, div m - rho>_h at the returned pair;
@@ -150,10 +151,10 @@ typedef struct w1_plan w1_plan;
 /* Fills *opt with the defaults documented in w1_options. */
 void w1_default_options(w1_options* opt);
 /* The calibrated schedule of w1_options.schedule = 1 for a norm: the factor on
- * eq. stop_tol's eps_L and the alpha of eq. tol_formula_propose (host only,
- * needs no device).  The paper has no counterpart: the values come from
- * measurement against converged W1 (see w1_options.schedule). */
-w1_status w1_calibrated_schedule(int norm, double* tol_scale, double* alpha);
+ * eq. stop_tol's eps_L, the alpha of eq. tol_formula_propose and the step-size
+ * factor theta (host only, needs no device).  The paper has no counterpart: the
+ * values come from measurement against converged W1 (see w1_options.schedule). */
+w1_status w1_calibrated_schedule(int norm, double* tol_scale, double* alpha, double* theta);
 
 /*
  * Creates a plan for nx x ny grids (Algorithm 3 input, Sec. 3.2).

@@ -120,7 +120,7 @@ def _load() -> ctypes.CDLL:
     st = ctypes.c_int
     sig = {
         "w1_default_options": (None, [ctypes.POINTER(Options)]),
-        "w1_calibrated_schedule": (st, [I, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "w1_calibrated_schedule": (st, [I, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
         "w1_plan_create": (st, [I, I, D, I, I, D, ctypes.POINTER(P)]),
         "w1_plan_create_ex": (st, [I, I, D, I, I, D, ctypes.POINTER(Options), ctypes.POINTER(P)]),
         "w1_plan_create_batch": (st, [I, I, D, I, I, D, I, ctypes.POINTER(Options), ctypes.POINTER(P)]),
@@ -205,10 +205,10 @@ def default_options(**kw) -> Options:
 
 
 def calibrated_schedule(norm) -> tuple:
-    """(eps_L scale, alpha) of w1_options.schedule = 1 for a norm (host only)."""
-    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
-    _check(_lib.w1_calibrated_schedule(norm, ctypes.byref(a), ctypes.byref(b)))
-    return a.value, b.value
+    """(eps_L scale, alpha, theta) of w1_options.schedule = 1 for a norm (host only)."""
+    a, b, c = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(_lib.w1_calibrated_schedule(norm, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
 
 
 def _dev_ptr(t, shape=None):

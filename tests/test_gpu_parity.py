@@ -522,12 +522,13 @@ def test_autotuner_reports_tile_candidates(w1):
 @pytest.mark.parametrize("norm", [L1, L2, LINF])
 def test_calibrated_schedule_sets_level_tolerances(w1, norm):
     """w1_options.schedule = 1 with tol <= 0: eps_L = eq. stop_tol x the calibrated
-    scale and eps_l = eps_L (h_l / h)^alpha with the calibrated alpha, both from
-    w1_calibrated_schedule; the solve still meets the oracle replay."""
+    scale, eps_l = eps_L (h_l / h)^alpha and the step sizes theta / ||A_h||, all
+    from w1_calibrated_schedule; the solve still meets the oracle replay."""
     r0, r1 = synth.pair(2, 4, n=128)
-    scale, alpha = w1.calibrated_schedule(norm)
+    scale, alpha, theta = w1.calibrated_schedule(norm)
     eps_L = 1e-6 / 128 * (512.0 / 128) ** 2 * scale
-    val, st, flux, _, ref = solve_and_replay(w1, r0, r1, norm, 4, schedule=1)
+    # the schedule sets the plan's theta; the same theta goes to the oracle replay
+    val, st, flux, _, ref = solve_and_replay(w1, r0, r1, norm, 4, schedule=1, theta=theta)
     for lvl in range(4):
         assert st.tol[lvl] == pytest.approx(eps_L * (2.0 ** (3 - lvl)) ** alpha, rel=1e-12)
     assert_parity(val, st, flux, ref)
