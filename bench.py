@@ -138,7 +138,8 @@ class ClockSampler:
 # calibration pairs 0-7 is at most 2.5e-5, four times below 1e-4.
 TOL_SCALE = {1: 30.0, 2: 0.1}
 ALPHA = {1: 0.5, 2: -1.0}  # eps_l = eps_L (h_l / h)^alpha (eq. tol_formula_propose)
-THETA = {1: 1.0, 2: 1.0}   # mu = tau = theta / ||A_h|| (eq. primaldual; 1/2 the paper's, 1 its footnote's)
+THETA = {1: 1.0, 2: 1.0}   # mu tau = (theta / ||A_h||)^2 (eq. primaldual; 1/2 the paper's, 1 its footnote's)
+RATIO = {1: 1.0, 2: 1.0}   # tau / mu (1: mu = tau, the paper's)
 
 
 def stop_tol(n: int, norm: int) -> float:
@@ -154,7 +155,7 @@ def _oracle_solve(spec):
     _, _, d0, d1 = synth.to_f32_pair(r0, r1)
     t0 = time.perf_counter()
     res = oracle.multilevel(d0, d1, levels=levels, norm=norm, tol=stop_tol(n, norm), alpha=ALPHA[norm],
-                            theta=THETA[norm], stop=oracle.STOP_FPR)
+                            theta=THETA[norm], ratio=RATIO[norm], stop=oracle.STOP_FPR)
     return norm, time.perf_counter() - t0, res.status
 
 
@@ -224,7 +225,7 @@ def run_reference(args):
         "config": {"workload": f"ellipse_texture_{n}x{n}_pairs_{levels}_levels_both_norms", "grid": [n, n],
                    "levels": levels, "norms": ["L1", "L2"],
                    "stop": "FPR R^k < eps_l, eps_L of eq. stop_tol x " + str(TOL_SCALE) + ", alpha " + str(ALPHA)
-                           + ", theta " + str(THETA),
+                           + ", theta " + str(THETA) + ", tau / mu " + str(RATIO),
                    "estimate": "saddle value (Lagrangian of eq. minmax_cp)"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample,
                          "seconds_per_solve": per},
@@ -636,7 +637,8 @@ def run_gpu(args):
                                 "scale; the calibrated schedule (w1_options.schedule = 1): scale "
                                 + json.dumps({f"L{k}": v for k, v in TOL_SCALE.items()}) + ", alpha "
                                 + json.dumps({f"L{k}": v for k, v in ALPHA.items()}) + ", theta "
-                                + json.dumps({f"L{k}": v for k, v in THETA.items()}))
+                                + json.dumps({f"L{k}": v for k, v in THETA.items()}) + ", tau / mu "
+                                + json.dumps({f"L{k}": v for k, v in RATIO.items()}))
                        if args.algorithm == 3 else "eq. stop_tol for Algorithm 4",
                        "tol": {f"L{k}": v for k, v in tol.items()},
                        "estimate": "saddle value: Lagrangian of eq. minmax_cp at the returned pair",
@@ -687,7 +689,7 @@ def run_gpu(args):
 # the captures summarised under profiles/; None where no capture of the current
 # kernel exists.  Streaming kernels: captured at 4096^2 and scaled by 4 to 8192^2
 # (their traffic grows with the number of nodes).
-TRAFFIC = {"k_step": 4 * 444.46e6, "k_tblock": 4 * 432.7e6, "k_resident4": 1.157888e6}
+TRAFFIC = {"k_step": 4 * 444.46e6, "k_tblock": 4 * 432.7e6, "k_resident4": 1105408.0}
 
 FP32_LANES_PER_SM = 128  # FP32 units per SM; two flops per FMA
 SM_MAX_MHZ = 2070.0
@@ -718,7 +720,7 @@ def roofline(w1, torch, stream, args):
     """Rooflines, timed with CUDA events on the launching stream.
 
     resident (the dominant kernel of a solve: the on-chip level solve, here a
-    256^2 level in a 16-CTA cluster, p = 1): arithmetic of eq. primaldual per
+    256^2 level in a 16-CTA cluster, p = 2): arithmetic of eq. primaldual per
     node and step against the FP32 rate of the SMs the launch occupies (its
     limit in practice is instruction issue and the two cluster barriers per step).
     streaming: one step per launch on an 8192^2 grid (1.9 GB, far above L2),
@@ -744,20 +746,22 @@ def roofline(w1, torch, stream, args):
     out["k_tblock"]["note"] = ("effective bandwidth, not DRAM traffic: 28 B per node-step; the tile and its "
                                "halo are read once per 4 steps")
     del rho
-    nr, kr = 256, 2000
+    # the dominant kernel of the benchmark's solves (launch list: the p = 2 cluster
+    # levels, 128^2 and 256^2, 35 % of the device time): the 256^2 level on 16 CTAs
+    nr, kr, nm = 256, 2000, 2
     hr = 1.0 / nr
     rr = torch.randn((nr, nr), device="cuda") * 0.1
     rr -= rr.mean()
     mur = float(np.float32(0.5 * hr / (2 * np.sqrt(2.0))))
-    ms_step = _time_steps(w1, torch, stream, rr, hr, 1, mur, 1, 256, 256 + kr, cluster=16)
-    flops_step = FLOPS_PER_NODE_STEP[1] * nr * nr
+    ms_step = _time_steps(w1, torch, stream, rr, hr, nm, mur, 1, 256, 256 + kr, cluster=16)
+    flops_step = FLOPS_PER_NODE_STEP[nm] * nr * nr
     fpeak = 16 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved = flops_step / (ms_step * 1e-3) / 1e12
-    res = {"kernel": "k_resident4 (on-chip level solve, 256^2 level, cluster of 16 CTAs, p = 1)", "grid": [nr, nr],
+    res = {"kernel": "k_resident4 (on-chip level solve, 256^2 level, cluster of 16 CTAs, p = 2)", "grid": [nr, nr],
            "bound": "alu", "achieved": achieved, "peak": fpeak,
            "peak_kind": "derived: 16 SMs x 128 FP32 lanes x 2 flops x 2070 MHz", "unit": "TFLOP/s",
            "frac": achieved / fpeak, "traffic": TRAFFIC["k_resident4"], "us_per_step": ms_step * 1e3,
-           "steps_per_launch": kr, "flops_per_node_step": FLOPS_PER_NODE_STEP[1],
+           "steps_per_launch": kr, "flops_per_node_step": FLOPS_PER_NODE_STEP[nm],
            "note": "issue and barrier-latency bound: no HBM traffic per step; traffic is per launch of "
                    f"{kr} steps (the level is loaded once)"}
     # the same per-step time against 28 algorithmic bytes per node and step (the
@@ -772,12 +776,12 @@ def roofline(w1, torch, stream, args):
     rw = torch.randn((nw, nw), device="cuda") * 0.1
     rw -= rw.mean()
     muw = float(np.float32(0.5 * hw / (2 * np.sqrt(2.0))))
-    msw = _time_steps(w1, torch, stream, rw, hw, 1, muw, 1, 64, 64 + 500, cluster=16)
-    res["wide"] = {"kernel": "k_resident_wide (512^2 level, cluster of 16 CTAs, p = 1)", "us_per_step": msw * 1e3,
+    msw = _time_steps(w1, torch, stream, rw, hw, nm, muw, 1, 64, 64 + 500, cluster=16)
+    res["wide"] = {"kernel": "k_resident_wide (512^2 level, cluster of 16 CTAs, p = 2)", "us_per_step": msw * 1e3,
                    "achieved_alg_GBps": 28.0 * nw * nw / (msw * 1e-3) / 1e9,
                    "frac_alg_bytes_vs_hbm": 28.0 * nw * nw / (msw * 1e-3) / 1e9 / peak,
-                   "achieved_TFLOPs": FLOPS_PER_NODE_STEP[1] * nw * nw / (msw * 1e-3) / 1e12,
-                   "frac_alu": FLOPS_PER_NODE_STEP[1] * nw * nw / (msw * 1e-3) / 1e12 / fpeak}
+                   "achieved_TFLOPs": FLOPS_PER_NODE_STEP[nm] * nw * nw / (msw * 1e-3) / 1e12,
+                   "frac_alu": FLOPS_PER_NODE_STEP[nm] * nw * nw / (msw * 1e-3) / 1e12 / fpeak}
     res["streaming"] = out["k_step"]
     res["temporal_blocking"] = out["k_tblock"]
     return res
@@ -1005,14 +1009,18 @@ def run_tol_sweep(args):
         # the throughput batch: the reference pairs repeated to args.batch lanes
         B = max(args.batch, len(ids))
         lanes = [torch.cuda.Stream() for _ in range(B)]
-        scales = (100.0, 30.0, 10.0, 3.0) if norm == 1 else (1.0, 0.3, 0.1, 0.03)
+        # (theta, alpha, ratio, scales): the step ratio tau / mu around the current choice
+        if norm == 1:
+            grid = [(1.0, 0.5, r, (50.0, 30.0, 20.0)) for r in (1.0, 2.0)]
+        else:
+            grid = [(1.0, a, r, (1.0, 0.5, 0.3, 0.2)) for a in (-1.0, 0.0) for r in (0.03, 0.0625, 0.125, 0.25)]
         levels = LEVELS
-        for theta in (0.5, 1.0):
-            for alpha in (-1.0, 0.0, 0.5):
+        for theta, alpha, ratio, scales in grid:
+            for _once in (0,):
                 for scale in scales:
                     tol = 1e-6 / 128 * scale
-                    plans = [w1.Plan(N, N, levels=levels, norm=norm, tol=tol, alpha=alpha, theta=theta)
-                             for _ in range(B)]
+                    plans = [w1.Plan(N, N, levels=levels, norm=norm, tol=tol, alpha=alpha, theta=theta,
+                                     step_ratio=ratio) for _ in range(B)]
                     for rep in range(2):  # first pass: graph builds; second: timed
                         ready = torch.cuda.Event()
                         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1035,7 +1043,8 @@ def run_tol_sweep(args):
                     ms = e0.elapsed_time(e1)
                     cal = [abs(e) for k, e in errs.items() if k < 8]
                     held = [abs(e) for k, e in errs.items() if k >= 8]
-                    out.append({"norm": norm, "levels": levels, "theta": theta, "alpha": alpha, "scale": scale,
+                    out.append({"norm": norm, "levels": levels, "theta": theta, "alpha": alpha, "ratio": ratio,
+                                "scale": scale,
                                 "solves_per_s": ok / (ms / 1e3), "not_ok": B - ok,
                                 "max_abs_rel_err_calibration": float(max(cal)) if cal else None,
                                 "max_abs_rel_err_held_out": float(max(held)) if held else None,
@@ -1344,7 +1353,7 @@ def run_serve(args):
     rates = [float(x) for x in args.rates.split(",")]
     out = []
     with w1.Server(hbm_budget_bytes=40 << 30, max_slots=args.slots, max_batch=args.serve_batch,
-                   latency_below=args.latency_below) as srv:
+                   latency_below=args.latency_below, schedule=1) as srv:
         # warm-up: requests one at a time build the latency-tuned slots (and run
         # the autotuner once per class), then a burst builds the others
         if args.latency_below > 0:

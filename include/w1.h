@@ -100,11 +100,14 @@ typedef struct {
                                 64x32 nodes 4 steps, 128x16 4, 32x64 4, 64x32 8, 32x32 8
                               (interior nodes of a tile and steps per launch; check_every
                               must be a multiple of twice the steps)                       */
+    double step_ratio;     /* tau / mu of eq. primaldual at a fixed product mu tau = (theta /
+                              ||A_h||)^2: mu = theta / ||A_h|| / sqrt(r), tau = theta / ||A_h||
+                              * sqrt(r) (default 1: mu = tau, the paper's); 2-D Algorithm 3 */
     int schedule;          /* level tolerances: 0 (default) eps_l = tol (h_l / h)^alpha as given;
                               1 the calibrated schedule for the saddle-value estimate at
                               relative 1e-4: per norm, an eps_L scale (applied to eq. stop_tol
-                              when tol <= 0), an alpha and a theta that replace opt.alpha and
-                              opt.theta, measured on
+                              when tol <= 0), an alpha, a theta and a step ratio that replace
+                              opt.alpha, opt.theta and opt.step_ratio, measured on
                               the 512^2 ellipse-texture workload against converged W1 (the
                               fastest setting whose worst error over the calibration pairs was
                               at most 2.5e-5; w1_calibrated_schedule reports the values);
@@ -151,10 +154,10 @@ typedef struct w1_plan w1_plan;
 /* Fills *opt with the defaults documented in w1_options. */
 void w1_default_options(w1_options* opt);
 /* The calibrated schedule of w1_options.schedule = 1 for a norm: the factor on
- * eq. stop_tol's eps_L, the alpha of eq. tol_formula_propose and the step-size
- * factor theta (host only, needs no device).  The paper has no counterpart: the
+ * eq. stop_tol's eps_L, the alpha of eq. tol_formula_propose, the step-size
+ * factor theta and the step ratio tau / mu (host only, needs no device).  The paper has no counterpart: the
  * values come from measurement against converged W1 (see w1_options.schedule). */
-w1_status w1_calibrated_schedule(int norm, double* tol_scale, double* alpha, double* theta);
+w1_status w1_calibrated_schedule(int norm, double* tol_scale, double* alpha, double* theta, double* step_ratio);
 
 /*
  * Creates a plan for nx x ny grids (Algorithm 3 input, Sec. 3.2).

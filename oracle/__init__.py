@@ -107,10 +107,10 @@ def bind(lib):
     lib.w1o_prolong.argtypes = [i, i, p, p, p, p, p, p]
     lib.w1o_step_size.argtypes = [d, d]
     lib.w1o_step_size.restype = d
-    lib.w1o_solve_level.argtypes = [i, i, d, i, d, p, p, p, p, d, i, i, l, l, ctypes.POINTER(l),
+    lib.w1o_solve_level.argtypes = [i, i, d, i, d, d, p, p, p, p, d, i, i, l, l, ctypes.POINTER(l),
                                     ctypes.POINTER(_Stats)]
     lib.w1o_solve_level.restype = i
-    lib.w1o_multilevel.argtypes = [i, i, d, i, i, d, d, d, i, i, l, p, p, p, p, p, p, p,
+    lib.w1o_multilevel.argtypes = [i, i, d, i, i, d, d, d, d, i, i, l, p, p, p, p, p, p, p,
                                    ctypes.POINTER(_Stats), ctypes.POINTER(d)]
     lib.w1o_multilevel.restype = i
     return lib
@@ -217,8 +217,9 @@ class LevelResult:
 
 
 def solve_level(rho, h, norm, m1=None, m2=None, phi=None, tol=1e-4, stop=STOP_GAP, check_every=32,
-                max_iters=200000, replay=-1, theta=0.5) -> LevelResult:
-    """Algorithm 1 on one grid from (m1, m2, phi) (zeros if None)."""
+                max_iters=200000, replay=-1, theta=0.5, ratio=1.0) -> LevelResult:
+    """Algorithm 1 on one grid from (m1, m2, phi) (zeros if None); step sizes
+    mu = s / sqrt(ratio), tau = s sqrt(ratio) with s = theta / ||A_h||."""
     rho = _f64(rho)
     ny, nx = rho.shape
     z = np.zeros_like(rho)
@@ -227,7 +228,7 @@ def solve_level(rho, h, norm, m1=None, m2=None, phi=None, tol=1e-4, stop=STOP_GA
     phi = (z if phi is None else _f64(phi)).copy()
     it = ctypes.c_long(0)
     s = _Stats()
-    st = _load().w1o_solve_level(nx, ny, h, norm, theta, _ptr(rho), _ptr(m1), _ptr(m2), _ptr(phi), tol, stop,
+    st = _load().w1o_solve_level(nx, ny, h, norm, theta, ratio, _ptr(rho), _ptr(m1), _ptr(m2), _ptr(phi), tol, stop,
                                  check_every, int(max_iters), int(replay), ctypes.byref(it), ctypes.byref(s))
     if st < 0:
         raise RuntimeError(f"w1o_solve_level failed: {st}")
@@ -246,7 +247,7 @@ class Result:
 
 
 def multilevel(rho0, rho1, h=0.0, levels=1, norm=NORM_L1, tol=1e-4, alpha=-1.0, theta=0.5, stop=STOP_GAP,
-               check_every=32, max_iters=200000, replay=None, estimate="saddle") -> Result:
+               check_every=32, max_iters=200000, replay=None, estimate="saddle", ratio=1.0) -> Result:
     """Algorithm 3 (cascadic multilevel Algorithm 1).  Raises on argument errors;
     returns status NOT_CONVERGED (with the best result) if a level hit max_iters.
     Result.w1 is the W1 estimate of the returned finest pair (m, phi): the
@@ -263,7 +264,7 @@ def multilevel(rho0, rho1, h=0.0, levels=1, norm=NORM_L1, tol=1e-4, alpha=-1.0, 
         rp = ctypes.cast(rp_arr, ctypes.c_void_p)
     s = _Stats()
     w1 = ctypes.c_double(0.0)
-    st = _load().w1o_multilevel(nx, ny, h, levels, norm, tol, alpha, theta, stop, check_every, int(max_iters),
+    st = _load().w1o_multilevel(nx, ny, h, levels, norm, tol, alpha, theta, ratio, stop, check_every, int(max_iters),
                                 _ptr(rho0), _ptr(rho1), rp, _ptr(m1), _ptr(m2), _ptr(phi),
                                 ctypes.cast(iters, ctypes.c_void_p), ctypes.byref(s), ctypes.byref(w1))
     if st < 0:

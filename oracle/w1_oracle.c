@@ -475,12 +475,14 @@ static int converged(int stop_mode, const w1o_stats_t* st, double tol)
  * The level returns z^k.  If replay >= 0 the test is skipped and exactly
  * `replay` steps are taken.  Returns W1O_OK, or W1O_NOT_CONVERGED when
  * max_iters steps passed without the test passing. */
-int w1o_solve_level(int nx, int ny, double h, int norm, double theta, const double* rho, double* m1, double* m2,
-                    double* phi, double tol, int stop_mode, int check_every, long max_iters, long replay,
+int w1o_solve_level(int nx, int ny, double h, int norm, double theta, double ratio, const double* rho, double* m1,
+                    double* m2, double* phi, double tol, int stop_mode, int check_every, long max_iters, long replay,
                     long* iters_out, w1o_stats_t* stats_out)
 {
-    if (nx < 1 || ny < 1 || !(h > 0.0) || check_every < 1) return W1O_ERR_ARG;
-    const double mu = w1o_step_size(h, theta), tau = mu;
+    if (nx < 1 || ny < 1 || !(h > 0.0) || check_every < 1 || !(ratio > 0.0)) return W1O_ERR_ARG;
+    /* mu tau = (theta / ||A_h||)^2 whatever the ratio tau / mu (the convergence
+     * condition of eq. primaldual bounds the product only) */
+    const double mu = w1o_step_size(h, theta) / sqrt(ratio), tau = w1o_step_size(h, theta) * sqrt(ratio);
     scratch_t s;
     if (scratch_alloc(&s, nx, ny) != W1O_OK) {
         scratch_free(&s);
@@ -540,7 +542,7 @@ int w1o_solve_level(int nx, int ny, double h, int norm, double theta, const doub
  * Outputs: the finest (m1, m2, phi), the iterations per level, the stats of the
  * returned finest state, and *w1 = f(m) of the returned finest state. */
 int w1o_multilevel(int nx, int ny, double h, int levels, int norm, double tol, double alpha, double theta,
-                   int stop_mode, int check_every, long max_iters, const double* rho0, const double* rho1,
+                   double ratio, int stop_mode, int check_every, long max_iters, const double* rho0, const double* rho1,
                    const long* replay, double* m1_out, double* m2_out, double* phi_out, long* iters_out,
                    w1o_stats_t* stats_out, double* w1)
 {
@@ -606,7 +608,7 @@ int w1o_multilevel(int nx, int ny, double h, int levels, int norm, double tol, d
         const double tol_l = tol * pow(hl / h, alpha);
         long it = 0;
         w1o_stats_t st;
-        int s = w1o_solve_level(lnx, lny, hl, norm, theta, rho[l], m1, m2, phi, tol_l, stop_mode, check_every,
+        int s = w1o_solve_level(lnx, lny, hl, norm, theta, ratio, rho[l], m1, m2, phi, tol_l, stop_mode, check_every,
                                 max_iters, replay ? replay[l] : -1, &it, &st);
         if (iters_out) iters_out[l] = it;
         if (s < 0) {

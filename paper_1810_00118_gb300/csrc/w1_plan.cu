@@ -157,24 +157,27 @@ int fault_halo_rank()
 // step mu = tau = 1 / ||A_h|| bound; mu tau ||A_h||^2 < 1 still holds, since the
 // largest eigenvalue of A_h A_h^* (the Neumann Laplacian) is below 8 / h^2.
 struct CalibratedSchedule {
-    double tol_scale, alpha, theta;
+    double tol_scale, alpha, theta, step_ratio;
 };
-static constexpr CalibratedSchedule kCalibrated[2] = {{30.0, 0.5, 1.0}, {0.1, -1.0, 1.0}};
+static constexpr CalibratedSchedule kCalibrated[2] = {{30.0, 0.5, 1.0, 1.0}, {0.1, -1.0, 1.0, 1.0}};
 
-extern "C" w1_status w1_calibrated_schedule(int norm, double* tol_scale, double* alpha, double* theta)
+extern "C" w1_status w1_calibrated_schedule(int norm, double* tol_scale, double* alpha, double* theta,
+                                            double* step_ratio)
 {
-    if (!tol_scale || !alpha || !theta) return fail(W1_ERR_INVALID_ARG, "NULL output");
+    if (!tol_scale || !alpha || !theta || !step_ratio) return fail(W1_ERR_INVALID_ARG, "NULL output");
     if (norm == W1_NORM_L1 || norm == W1_NORM_L2) {
         const CalibratedSchedule& c = kCalibrated[norm == W1_NORM_L1 ? 0 : 1];
         *tol_scale = c.tol_scale;
         *alpha = c.alpha;
         *theta = c.theta;
+        *step_ratio = c.step_ratio;
         return W1_OK;
     }
     if (norm == W1_NORM_LINF) {
         *tol_scale = 1.0;
         *alpha = -1.0;
         *theta = 0.5;
+        *step_ratio = 1.0;
         return W1_OK;
     }
     return fail(W1_ERR_INVALID_ARG, "norm must be 1, 2 or 3");
@@ -193,6 +196,7 @@ extern "C" void w1_default_options(w1_options* o)
     o->eager = 0;
     o->tune = 0;
     o->algorithm = 3;
+    o->step_ratio = 1.0;
     o->schedule = 0;
     o->estimate = 0;
 }
@@ -304,6 +308,8 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
     if (o.tune < 0 || o.tune > 3) return fail(W1_ERR_INVALID_ARG, "tune must be 0, 1, 2 or 3");
     if (o.estimate < 0 || o.estimate > 1) return fail(W1_ERR_INVALID_ARG, "estimate must be 0 or 1");
     if (o.schedule < 0 || o.schedule > 1) return fail(W1_ERR_INVALID_ARG, "schedule must be 0 or 1");
+    if (!(o.step_ratio > 0.0) || o.step_ratio > 1e6 || o.step_ratio < 1e-6)
+        return fail(W1_ERR_INVALID_ARG, "step_ratio must lie in [1e-6, 1e6]");
     if (o.tile < 0 || o.tile > W1_TILE_VARIANTS) return fail(W1_ERR_INVALID_ARG, "tile must lie in [0, W1_TILE_VARIANTS]");
     if (o.check_every % (2 * tblock_depth(o.tile > 0 ? o.tile - 1 : 0)) != 0)
         return fail(W1_ERR_INVALID_ARG, "check_every must be a multiple of twice the temporal block depth");
@@ -332,6 +338,7 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
         tol_scale = c.tol_scale;
         o.alpha = c.alpha;
         o.theta = c.theta;
+        o.step_ratio = c.step_ratio;
     }
     if (!(tol > 0.0)) {
         const double s2 = (512.0 * h) * (512.0 * h);
@@ -358,8 +365,8 @@ static w1_status configure(w1_plan* p, int nx, int ny, double h, int levels, int
         v.ny = ny >> sh;
         v.h = h * (double)(1 << sh);
         const double mu = o.theta * v.h / (2.0 * std::sqrt(2.0));  // theta / ||A_h||, ||A_h|| <= 2 sqrt(2) / h
-        v.mu = (float)mu;
-        v.tau = (float)mu;
+        v.mu = (float)(mu / std::sqrt(o.step_ratio));  // mu tau = mu^2 for any ratio tau / mu
+        v.tau = (float)(mu * std::sqrt(o.step_ratio));
         v.tol = tol * std::pow(v.h / h, o.alpha);  // eq. tol_formula_propose
         if (alg4) {
             // prox-PDHG: mu = tau = theta (the paper's 1/2), every level on path 4

@@ -47,8 +47,8 @@ class Options(ctypes.Structure):
     _fields_ = [("check_every", ctypes.c_int), ("max_iters", ctypes.c_longlong), ("theta", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("time_budget_s", ctypes.c_double), ("path", ctypes.c_int),
                 ("rows_per_thread", ctypes.c_int), ("eager", ctypes.c_int), ("tune", ctypes.c_int),
-                ("algorithm", ctypes.c_int), ("tile", ctypes.c_int), ("schedule", ctypes.c_int),
-                ("estimate", ctypes.c_int)]
+                ("algorithm", ctypes.c_int), ("tile", ctypes.c_int), ("step_ratio", ctypes.c_double),
+                ("schedule", ctypes.c_int), ("estimate", ctypes.c_int)]
 
 
 class LevelChoice(ctypes.Structure):
@@ -120,7 +120,8 @@ def _load() -> ctypes.CDLL:
     st = ctypes.c_int
     sig = {
         "w1_default_options": (None, [ctypes.POINTER(Options)]),
-        "w1_calibrated_schedule": (st, [I, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "w1_calibrated_schedule": (st, [I, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
+                                        ctypes.POINTER(D)]),
         "w1_plan_create": (st, [I, I, D, I, I, D, ctypes.POINTER(P)]),
         "w1_plan_create_ex": (st, [I, I, D, I, I, D, ctypes.POINTER(Options), ctypes.POINTER(P)]),
         "w1_plan_create_batch": (st, [I, I, D, I, I, D, I, ctypes.POINTER(Options), ctypes.POINTER(P)]),
@@ -205,10 +206,10 @@ def default_options(**kw) -> Options:
 
 
 def calibrated_schedule(norm) -> tuple:
-    """(eps_L scale, alpha, theta) of w1_options.schedule = 1 for a norm (host only)."""
-    a, b, c = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
-    _check(_lib.w1_calibrated_schedule(norm, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-    return a.value, b.value, c.value
+    """(eps_L scale, alpha, theta, step ratio) of w1_options.schedule = 1 for a norm (host only)."""
+    a, b, c, r = (ctypes.c_double(0.0) for _ in range(4))
+    _check(_lib.w1_calibrated_schedule(norm, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(r)))
+    return a.value, b.value, c.value, r.value
 
 
 def _dev_ptr(t, shape=None):

@@ -45,5 +45,6 @@ def test_bench_schedule_is_the_library_calibrated_schedule():
     w1_options.schedule = 1 table (a host-only call)."""
     from paper_1810_00118_gb300 import w1
     for norm in bench.NORMS:
-        scale, alpha, theta = w1.calibrated_schedule(norm)
+        scale, alpha, theta, ratio = w1.calibrated_schedule(norm)
         assert scale == bench.TOL_SCALE[norm] and alpha == bench.ALPHA[norm] and theta == bench.THETA[norm]
+        assert ratio == bench.RATIO[norm]

@@ -197,7 +197,8 @@ def solve_and_replay(w1, r0, r1, norm, levels, tol=0.0, **opt):
         val, st, _ = plan.solve(dev(a0), dev(a1), flux=flux)
         plan.potential(phi)
     theta = opt.get("theta", 0.5)
-    ref = oracle.multilevel(d0, d1, levels=levels, norm=norm, theta=theta, replay=st.iters)
+    ratio = opt.get("step_ratio", 1.0)
+    ref = oracle.multilevel(d0, d1, levels=levels, norm=norm, theta=theta, ratio=ratio, replay=st.iters)
     return val, st, host(flux), host(phi), ref
 
 
@@ -525,10 +526,19 @@ def test_calibrated_schedule_sets_level_tolerances(w1, norm):
     scale, eps_l = eps_L (h_l / h)^alpha and the step sizes theta / ||A_h||, all
     from w1_calibrated_schedule; the solve still meets the oracle replay."""
     r0, r1 = synth.pair(2, 4, n=128)
-    scale, alpha, theta = w1.calibrated_schedule(norm)
+    scale, alpha, theta, ratio = w1.calibrated_schedule(norm)
     eps_L = 1e-6 / 128 * (512.0 / 128) ** 2 * scale
-    # the schedule sets the plan's theta; the same theta goes to the oracle replay
-    val, st, flux, _, ref = solve_and_replay(w1, r0, r1, norm, 4, schedule=1, theta=theta)
+    # the schedule sets the plan's theta and step ratio; the same go to the oracle replay
+    val, st, flux, _, ref = solve_and_replay(w1, r0, r1, norm, 4, schedule=1, theta=theta, step_ratio=ratio)
     for lvl in range(4):
         assert st.tol[lvl] == pytest.approx(eps_L * (2.0 ** (3 - lvl)) ** alpha, rel=1e-12)
+    assert_parity(val, st, flux, ref)
+
+
+@pytest.mark.parametrize("norm,ratio", [(L1, 0.25), (L2, 4.0), (LINF, 2.0)])
+def test_step_ratio_matches_replay(w1, norm, ratio):
+    """Unequal step sizes (tau / mu = ratio at mu tau = (theta / ||A_h||)^2) on every
+    level against the oracle replaying the same steps."""
+    r0, r1 = synth.pair(2, 6, n=128)
+    val, st, flux, _, ref = solve_and_replay(w1, r0, r1, norm, 4, step_ratio=ratio)
     assert_parity(val, st, flux, ref)

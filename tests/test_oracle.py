@@ -532,3 +532,19 @@ def test_saddle_value_meets_exact_lp_at_paper_tolerance(n):
                              estimate="primal").w1 == res.stats.f
     tight_ = oracle.multilevel(r0, r1, levels=levels, norm=L1, tol=eps_L / 10, alpha=-1.0, stop=oracle.STOP_FPR)
     assert abs(tight_.w1 - exact) <= 1e-4 * exact
+
+
+@pytest.mark.parametrize("ratio", [0.25, 4.0])
+def test_unequal_step_sizes_reach_exact_lp(ratio):
+    """Steps mu = s / sqrt(r), tau = s sqrt(r) keep mu tau ||A_h||^2 < 1, so Algorithm 1
+    still converges to the discrete optimum: the exact LP value (p = 1), and strong
+    duality with a feasible potential."""
+    rng = np.random.default_rng(41)
+    rho = rand_zero_mass(rng, 8, 10, 0.1)
+    h = 0.1
+    exact = lp_ref.w1_lp(rho, h)
+    res = oracle.solve_level(rho, h, L1, tol=1e-8, stop=oracle.STOP_GAP, check_every=64, max_iters=3_000_000,
+                             theta=1.0, ratio=ratio)
+    assert res.status == oracle.OK
+    assert abs(res.stats.f - exact) <= 1e-6 * exact and abs(res.stats.dual - exact) <= 1e-6 * exact
+    assert res.stats.gmax <= 1.0 + 1e-5
