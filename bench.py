@@ -136,14 +136,15 @@ class ClockSampler:
 # calibrated against the converged values of tests/golden/converged_512.json
 # (bench.py --only tol-sweep): the fastest setting whose worst error over the
 # calibration pairs 0-7 is at most 2.5e-5, four times below 1e-4.
-TOL_SCALE = {1: 30.0, 2: 0.1}
+TOL_SCALE = {1: 30.0, 2: 2.0}
 ALPHA = {1: 0.5, 2: -1.0}  # eps_l = eps_L (h_l / h)^alpha (eq. tol_formula_propose)
 THETA = {1: 1.0, 2: 1.0}   # mu tau = (theta / ||A_h||)^2 (eq. primaldual; 1/2 the paper's, 1 its footnote's)
-RATIO = {1: 1.0, 2: 1.0}   # tau / mu (1: mu = tau, the paper's)
+RATIO = {1: 1.0, 2: 0.02}  # tau / mu (1: mu = tau, the paper's)
 
 
 def stop_tol(n: int, norm: int) -> float:
-    return 1e-6 / 128 * (512.0 / n) ** 2 * TOL_SCALE[norm]
+    # the calibrated schedule keeps eps_L at its 512^2 value on coarser grids
+    return 1e-6 / 128 * min((512.0 / n) ** 2, 1.0) * TOL_SCALE[norm]
 
 
 def _oracle_solve(spec):
@@ -261,10 +262,12 @@ def gen_pairs(specs, world=1):
 CTL_BYTES = 560
 
 
-def load_converged():
-    """The stored converged values (tests/golden/converged_512.json, written by
+def load_converged(n=N, workload=WORKLOAD):
+    """The stored converged values (tests/golden/converged_512.json, or
+    converged_w<workload>_<n>.json for other grids, written by
     oracle/make_converged_table.py from the FP64 oracle and the exact LP)."""
-    path = os.path.join(ROOT, "tests", "golden", "converged_512.json")
+    name = "converged_512.json" if (n, workload) == (N, WORKLOAD) else f"converged_w{workload}_{n}.json"
+    path = os.path.join(ROOT, "tests", "golden", name)
     try:
         with open(path) as f:
             t = json.load(f)
@@ -832,6 +835,7 @@ def main():
                              "mixed", "tol-sweep", "solve3d", "3d-kernel", "cascade-vs-single"],
                     help="kernel-only runs for profiling: one level's steps through w1_cp_steps")
     ap.add_argument("--kn", type=int, default=256, help="grid side for --only *-kernel")
+    ap.add_argument("--sweep-size", type=int, default=0, help="--only tol-sweep: grid side (0: 512)")
     ap.add_argument("--kiters", type=int, default=1000, help="steps for --only *-kernel")
     ap.add_argument("--knorm", type=int, default=1)
     ap.add_argument("--kcluster", type=int, default=0, help="--only resident-kernel: CTAs per level (0: auto)")
@@ -980,21 +984,24 @@ def run_mixed(args):
 
 def run_tol_sweep(args):
     """Tolerance schedule study (eq. tol_formula_propose, the alpha study of
-    Sec. 6.2, the level count of Sec. 6.3) on the 512^2 workload: for each
-    norm, eps_l = s * eps_L (h_l / h)^alpha with eps_L of eq. stop_tol, for
-    several scales s, alphas and step sizes theta (mu = tau = theta / ||A_h||);
-    the reported W1 (saddle value)
-    of the reference pairs against their converged values
-    (tests/golden/converged_512.json) and the throughput of a batch of lanes
+    Sec. 6.2, the level count of Sec. 6.3) on grids with stored converged values
+    (--kn: 512 for the benchmark's pairs, 128 or 256 for the serving mix's): for
+    each norm, eps_l = s * eps_L (h_l / h)^alpha with eps_L of eq. stop_tol, for
+    several scales s, alphas, step sizes theta (mu tau = (theta / ||A_h||)^2)
+    and step ratios tau / mu; the reported W1 (saddle value) of the reference
+    pairs against their converged values and the throughput of a batch of lanes
     (one plan and stream per pair, CUDA events)."""
     import torch
 
     import synth
     from paper_1810_00118_gb300 import w1
 
-    conv = load_converged()
+    n = args.sweep_size or N
+    workload = WORKLOAD if n == N else 4
+    conv = load_converged(n, workload)
     if not conv:
-        raise SystemExit("tests/golden/converged_512.json is missing")
+        raise SystemExit("no stored converged values for this grid")
+    levels = max(1, int(np.log2(n)) - 3)
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     every = (w1.OK, w1.ERR_NOT_CONVERGED, w1.ERR_TIMEOUT, w1.ERR_MASS)
@@ -1003,56 +1010,55 @@ def run_tol_sweep(args):
         ids = sorted(conv[norm])
         if not ids:
             continue
-        pairs = [synth.pair(WORKLOAD, k) for k in ids]
+        pairs = [synth.pair(workload, k, n=n) for k in ids]
         t0 = torch.from_numpy(np.ascontiguousarray(np.stack([p[0] for p in pairs]), dtype=np.float32)).cuda()
         t1 = torch.from_numpy(np.ascontiguousarray(np.stack([p[1] for p in pairs]), dtype=np.float32)).cuda()
         # the throughput batch: the reference pairs repeated to args.batch lanes
         B = max(args.batch, len(ids))
         lanes = [torch.cuda.Stream() for _ in range(B)]
-        # (theta, alpha, ratio, scales): the step ratio tau / mu around the current choice
-        if norm == 1:
-            grid = [(1.0, 0.5, r, (50.0, 30.0, 20.0)) for r in (1.0, 2.0)]
-        else:
-            grid = [(1.0, a, r, (1.0, 0.5, 0.3, 0.2)) for a in (-1.0, 0.0) for r in (0.03, 0.0625, 0.125, 0.25)]
-        levels = LEVELS
+        grid = SWEEP_GRID[norm]
+        n_cal = max(1, len(ids) // 2)  # the first half calibrates, the second half is held out
         for theta, alpha, ratio, scales in grid:
-            for _once in (0,):
-                for scale in scales:
-                    tol = 1e-6 / 128 * scale
-                    plans = [w1.Plan(N, N, levels=levels, norm=norm, tol=tol, alpha=alpha, theta=theta,
-                                     step_ratio=ratio) for _ in range(B)]
-                    for rep in range(2):  # first pass: graph builds; second: timed
-                        ready = torch.cuda.Event()
-                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                        torch.cuda.synchronize()
-                        e0.record(stream)
-                        ready.record(stream)
-                        for b in range(B):
-                            lanes[b].wait_event(ready)
-                            plans[b].solve_async(t0[b % len(ids)], t1[b % len(ids)], stream=lanes[b])
-                            stream.wait_stream(lanes[b])
-                        e1.record(stream)
-                        torch.cuda.synchronize()
-                    errs, ok = {}, 0
-                    for b, p in enumerate(plans):
-                        v, st, ps, _ = p.results(allow=every)
-                        ok += ps[0] == w1.OK
-                        if b < len(ids):
-                            errs[ids[b]] = (v[0] - conv[norm][ids[b]]) / conv[norm][ids[b]]
-                        p.close()
-                    ms = e0.elapsed_time(e1)
-                    cal = [abs(e) for k, e in errs.items() if k < 8]
-                    held = [abs(e) for k, e in errs.items() if k >= 8]
-                    out.append({"norm": norm, "levels": levels, "theta": theta, "alpha": alpha, "ratio": ratio,
-                                "scale": scale,
-                                "solves_per_s": ok / (ms / 1e3), "not_ok": B - ok,
-                                "max_abs_rel_err_calibration": float(max(cal)) if cal else None,
-                                "max_abs_rel_err_held_out": float(max(held)) if held else None,
-                                "rel_errs": {str(k): float(e) for k, e in errs.items()}})
-                    print(json.dumps(out[-1]), flush=True)
-    print(json.dumps({"only": "tol-sweep", "grid": N, "batch": args.batch, "reference_pairs": {
-        f"L{n}": sorted(conv[n]) for n in NORMS}, "rows": out}))
+            for scale in scales:
+                tol = 1e-6 / 128 * (512.0 / n) ** 2 * scale
+                plans = [w1.Plan(n, n, levels=levels, norm=norm, tol=tol, alpha=alpha, theta=theta,
+                                 step_ratio=ratio) for _ in range(B)]
+                for rep in range(2):  # first pass: graph builds; second: timed
+                    ready = torch.cuda.Event()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    ready.record(stream)
+                    for b in range(B):
+                        lanes[b].wait_event(ready)
+                        plans[b].solve_async(t0[b % len(ids)], t1[b % len(ids)], stream=lanes[b])
+                        stream.wait_stream(lanes[b])
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                errs, ok = {}, 0
+                for b, p in enumerate(plans):
+                    v, st, ps, _ = p.results(allow=every)
+                    ok += ps[0] == w1.OK
+                    if b < len(ids):
+                        errs[ids[b]] = (v[0] - conv[norm][ids[b]]) / conv[norm][ids[b]]
+                    p.close()
+                ms = e0.elapsed_time(e1)
+                cal = [abs(errs[k]) for k in ids[:n_cal]]
+                held = [abs(errs[k]) for k in ids[n_cal:]]
+                out.append({"n": n, "norm": norm, "levels": levels, "theta": theta, "alpha": alpha, "ratio": ratio,
+                            "scale": scale, "solves_per_s": ok / (ms / 1e3), "not_ok": B - ok,
+                            "max_abs_rel_err_calibration": float(max(cal)) if cal else None,
+                            "max_abs_rel_err_held_out": float(max(held)) if held else None,
+                            "rel_errs": {str(k): float(e) for k, e in errs.items()}})
+                print(json.dumps(out[-1]), flush=True)
+    print(json.dumps({"only": "tol-sweep", "grid": n, "batch": args.batch, "reference_pairs": {
+        f"L{m}": sorted(conv[m]) for m in NORMS}, "rows": out}))
     return 0
+
+
+# (theta, alpha, tau / mu, eps_L scales) per norm for --only tol-sweep
+SWEEP_GRID = {1: [(1.0, 0.5, 1.0, (30.0, 10.0, 5.0, 3.0, 1.0))],
+              2: [(1.0, -1.0, 0.02, (2.0, 1.0, 0.5, 0.25))]}
 
 
 def run_cascade_vs_single(args):
@@ -1219,17 +1225,25 @@ def serve_run(w1, srv, pool, rate, n_req, seed, tol_of=None):
         tol = tol_of(int(sizes[k]), int(norms[k])) if tol_of else 0.0
         tickets.append(srv.submit(a, b, norm=int(norms[k]), tol=tol))
     lat, statuses = [], []
-    for t in tickets:
+    for k, t in enumerate(tickets):
         while True:
             st, v, stats, l = srv.poll(t)
             if st != w1.PENDING:
                 break
             time.sleep(0.0005)
         statuses.append(st)
+        if st != w1.OK and len(serve_run.failed) < 16:
+            serve_run.failed.append({"size": int(sizes[k]), "norm": int(norms[k]), "status": int(st),
+                                     "pair": int(picks[k] % len(pool[int(sizes[k])])),
+                                     "iters": [int(x) for x in stats.iters] if stats else None,
+                                     "fpr_over_tol": [f / t for f, t in zip(stats.fpr, stats.tol)] if stats else None})
         lat.append(l)
     t_end = time.perf_counter()
     lat = np.array(lat) * 1e3
     return float(np.percentile(lat, 50)), float(np.percentile(lat, 99)), n_req / (t_end - t0), statuses
+
+
+serve_run.failed = []  # requests that ended with another status than W1_OK (first 16)
 
 
 def serve_summary(w1, torch, args):
@@ -1256,6 +1270,7 @@ def serve_summary(w1, torch, args):
             "solves_per_s": out[-1]["solves_per_s"], "requests_at_headline_rate": out[-1]["requests"],
             "sizes": SERVE_SIZES, "probs": SERVE_PROBS, "budget_GiB": 40, "slots": args.slots,
             "latency_below": args.latency_below, "evictions": info.get("evictions"),
+            "not_ok_requests": serve_run.failed,
             "what": "submit to completion (w1_poll_latency), Poisson arrivals; headline = the last rate"}
 
 

@@ -106,7 +106,9 @@ typedef struct {
     int schedule;          /* level tolerances: 0 (default) eps_l = tol (h_l / h)^alpha as given;
                               1 the calibrated schedule for the saddle-value estimate at
                               relative 1e-4: per norm, an eps_L scale (applied to eq. stop_tol
-                              when tol <= 0), an alpha, a theta and a step ratio that replace
+                              when tol <= 0, whose (512 h)^2 factor is then capped at 1 so
+                              that grids coarser than 512^2 keep the 512^2 eps_L), an alpha,
+                              a theta and a step ratio that replace
                               opt.alpha, opt.theta and opt.step_ratio, measured on
                               the 512^2 ellipse-texture workload against converged W1 (the
                               fastest setting whose worst error over the calibration pairs was

@@ -1523,12 +1523,12 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
     // previous lane by a shuffle: a warp's runs are all present or all absent,
     // since the band holds a multiple of 128 nodes); the row below the band is
     // read from the CTA below (initial state) or from the halo row it pushed
-    auto divergence = [&](auto rc, float out[4], auto halo) {
+    // m1 of the run: given by the caller (tm1, loaded from tensor memory with the
+    // run's other values), else read from shared memory
+    auto divergence = [&](auto rc, float out[4], auto halo, const float4* tm1) {
         constexpr int r = decltype(rc)::value;
         const int jl = pk[r] >> 16, i0 = pk[r] & 0xffff, id = id0 + r * RESW_RUN_STRIDE;
-        float4 m1;
-        if constexpr (TM && decltype(halo)::value) m1 = tmem_ld4_at<16 * r + 12>(tb);
-        else m1 = *reinterpret_cast<const float4*>(s1 + id);
+        const float4 m1 = tm1 ? *tm1 : *reinterpret_cast<const float4*>(s1 + id);
         const float ln = __shfl_up_sync(FULL, m1.w, 1);
         const float4 m2 = *reinterpret_cast<const float4*>(s2 + id);
         const float l = i0 == 0 ? 0.f : (lane == 0 ? s1[id - 1] : ln);
@@ -1558,10 +1558,10 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
         if (pk[r] >= 0) {
             if constexpr (TM) {
                 float d0[4];
-                divergence(rc, d0, std::false_type{});
+                divergence(rc, d0, std::false_type{}, nullptr);
                 tmem_st4_at<16 * r + 4>(tb, make_float4(d0[0], d0[1], d0[2], d0[3]));
             } else {
-                divergence(rc, Dv[r], std::false_type{});
+                divergence(rc, Dv[r], std::false_type{}, nullptr);
             }
         }
     });
@@ -1598,11 +1598,16 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             constexpr int r = decltype(rc)::value;
             if (pk[r] < 0) return;
             const int jl = pk[r] >> 16, i0 = pk[r] & 0xffff, id = id0 + r * RESW_RUN_STRIDE;
-            const float4 p4 = TM ? tmem_ld4_at<16 * r + 8>(tb) : *reinterpret_cast<const float4*>(ph + id);
+            float4 p4, a1;  // the run's phi and m1: two loads behind one wait
+            if constexpr (TM) {
+                tmem_ld4x2_at<16 * r + 8, 16 * r + 12>(tb, p4, a1);
+            } else {
+                p4 = *reinterpret_cast<const float4*>(ph + id);
+                a1 = *reinterpret_cast<const float4*>(s1 + id);
+            }
             const float rn = __shfl_down_sync(FULL, p4.x, 1);
             const int j = jb + jl;
             const bool last_col = i0 + 4 == nx;
-            const float4 a1 = TM ? tmem_ld4_at<16 * r + 12>(tb) : *reinterpret_cast<const float4*>(s1 + id);
             const float4 a2 = *reinterpret_cast<const float4*>(s2 + id);
             float4 u = p4;
             if (j < ny - 1) {
@@ -1657,14 +1662,15 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
             constexpr int r = decltype(rc)::value;
             if (pk[r] < 0) return;
             float Dn[4];
-            divergence(rc, Dn, std::true_type{});
             const int id = id0 + r * RESW_RUN_STRIDE;
-            const float4 p4 = TM ? tmem_ld4_at<16 * r + 8>(tb) : *reinterpret_cast<const float4*>(ph + id);
-            float4 r4, d4;
+            float4 p4, r4, d4;
             if constexpr (TM) {
-                r4 = tmem_ld4_at<16 * r>(tb);
-                d4 = tmem_ld4_at<16 * r + 4>(tb);
+                float4 m1v;  // the run's m1', phi, rho and D: four loads behind one wait
+                tmem_ld4x4_at<16 * r + 12, 16 * r + 8, 16 * r, 16 * r + 4>(tb, m1v, p4, r4, d4);
+                divergence(rc, Dn, std::true_type{}, &m1v);
             } else {
+                divergence(rc, Dn, std::true_type{}, nullptr);
+                p4 = *reinterpret_cast<const float4*>(ph + id);
                 r4 = __ldg(reinterpret_cast<const float4*>(rho + id));
                 d4 = make_float4(Dv[r][0], Dv[r][1], Dv[r][2], Dv[r][3]);
             }

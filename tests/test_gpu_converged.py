@@ -180,3 +180,23 @@ def test_512_pairs_meet_converged_values(w1, norm):
             val, st, status = plan.solve(dev(r0), dev(r1))
             ref = table[str(k)]["w1"]
             assert abs(val - ref) <= 1e-4 * ref, (k, val, ref, st.iters)
+
+
+@pytest.mark.parametrize("n", [128, 256])
+@pytest.mark.parametrize("norm", [L1, L2])
+def test_serving_sizes_meet_converged_values(w1, n, norm):
+    """The serving mix's pairs at 128^2 and 256^2 (synthetic workload 4, the
+    seeds the serving pool draws), solved with the calibrated schedule that was
+    measured at 512^2, against their converged values
+    (tests/golden/converged_w4_<n>.json): relative 1e-4."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"converged_w4_{n}.json")
+    with open(path) as f:
+        table = json.load(f)[f"L{norm}"]
+    with w1.Plan(n, n, norm=norm, schedule=1) as plan:
+        for k in sorted(int(x) for x in table):
+            r0, r1 = synth.pair(4, k, n=n)
+            val, st, status = plan.solve(dev(r0), dev(r1))
+            ref = table[str(k)]["w1"]
+            assert abs(val - ref) <= 1e-4 * ref, (n, k, val, ref, st.iters)

@@ -523,11 +523,13 @@ def test_autotuner_reports_tile_candidates(w1):
 @pytest.mark.parametrize("norm", [L1, L2, LINF])
 def test_calibrated_schedule_sets_level_tolerances(w1, norm):
     """w1_options.schedule = 1 with tol <= 0: eps_L = eq. stop_tol x the calibrated
-    scale, eps_l = eps_L (h_l / h)^alpha and the step sizes theta / ||A_h||, all
-    from w1_calibrated_schedule; the solve still meets the oracle replay."""
+    scale (for p = 1, 2 with stop_tol's (512 h)^2 capped at 1 on this 128^2 grid),
+    eps_l = eps_L (h_l / h)^alpha and the step sizes theta / ||A_h||, all from
+    w1_calibrated_schedule; the solve still meets the oracle replay."""
     r0, r1 = synth.pair(2, 4, n=128)
     scale, alpha, theta, ratio = w1.calibrated_schedule(norm)
-    eps_L = 1e-6 / 128 * (512.0 / 128) ** 2 * scale
+    growth = (512.0 / 128) ** 2 if norm == LINF else 1.0
+    eps_L = 1e-6 / 128 * growth * scale
     # the schedule sets the plan's theta and step ratio; the same go to the oracle replay
     val, st, flux, _, ref = solve_and_replay(w1, r0, r1, norm, 4, schedule=1, theta=theta, step_ratio=ratio)
     for lvl in range(4):
