@@ -219,45 +219,86 @@ __global__ void k3_prolong(Dims3 c, const float* __restrict__ m1c, const float* 
 }
 
 // Certificates: per-block compensated FP64 partials (s, c) of sum ||m||_p,
-// sum phi rho, sum |e|, sum |rho| and sum phi e (e = rho - div m; unscaled,
-// h^3 applied once at the end), and the maximum of the dual norm of grad phi;
-// the residual (masses) goes to q.
-static constexpr int FIN3_PART = 11;
+// sum phi rho, sum |e|, sum |rho|, sum phi e (e = rho - div m; unscaled, h^3
+// applied once at the end) and the first level of the route bound, and the
+// maximum of the dual norm of grad phi (kept squared for p = 2, one square root
+// per block).  When every side is even each thread takes a 2 x 2 x 2 cell: the
+// non-negative terms of the cell are added in plain FP64 before their
+// compensated sums, the masses of its voxels go to their cell's first voxel
+// (an offset with s nonzero coordinates costs s h) and the cell's mass to q;
+// otherwise q gets every voxel's mass.  1/h multiplies instead of dividing.
+static constexpr int FIN3_PART = 13;
+__host__ __device__ static inline bool final3_pooled(const Dims3& d)
+{
+    return d.nx % 2 == 0 && d.ny % 2 == 0 && d.nz % 2 == 0;
+}
 template <int NORM>
 __global__ void __launch_bounds__(T3) k3_final_a(Dims3 d, double h, const float* __restrict__ m1,
                                                   const float* __restrict__ m2, const float* __restrict__ m3,
                                                   const float* __restrict__ phi, const float* __restrict__ rho,
                                                   double* __restrict__ q_out, double* part)
 {
-    const long long q = (long long)blockIdx.x * T3 + threadIdx.x;
-    CSum v[5];
+    const long long t = (long long)blockIdx.x * T3 + threadIdx.x;
+    CSum v[6];
     double g = 0.0;
-    if (q < d.n) {
-        int i, j, k;
-        node3(d, q, i, j, k);
-        const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+    const double inv_h = 1.0 / h, h3 = h * h * h;
+    // the voxel's terms (non-negative ones into acc); returns its mass e h^3
+    auto voxel = [&](int i, int j, int k, double (&acc)[3]) -> double {
+        const long long q = k * sz + j * sy + i;
         const double a1 = fabs((double)m1[q]), a2 = fabs((double)m2[q]), a3 = fabs((double)m3[q]);
-        v[0].add(NORM == W1_NORM_L1 ? __dadd_rn(__dadd_rn(a1, a2), a3)
-                 : NORM == W1_NORM_L2 ? sqrt(__dadd_rn(__dadd_rn(__dmul_rn(a1, a1), __dmul_rn(a2, a2)), __dmul_rn(a3, a3)))
-                                      : fmax(a1, fmax(a2, a3)));
+        acc[0] += NORM == W1_NORM_L1 ? __dadd_rn(__dadd_rn(a1, a2), a3)
+                  : NORM == W1_NORM_L2 ? sqrt(__dadd_rn(__dadd_rn(__dmul_rn(a1, a1), __dmul_rn(a2, a2)), __dmul_rn(a3, a3)))
+                                       : fmax(a1, fmax(a2, a3));
         const double p = phi[q], r = rho[q];
         v[1].add(__dmul_rn(p, r));
-        const double dv = (((double)m1[q] * (i < d.nx - 1) - (i > 0 ? (double)m1[q - 1] : 0.0)) +
-                           ((double)m2[q] * (j < d.ny - 1) - (j > 0 ? (double)m2[q - sy] : 0.0)) +
-                           ((double)m3[q] * (k < d.nz - 1) - (k > 0 ? (double)m3[q - sz] : 0.0))) / h;
-        const double e = __dsub_rn(r, dv);
-        q_out[q] = e * h * h * h;
-        v[2].add(fabs(e));
-        v[3].add(fabs(r));
+        const double dv = ((double)m1[q] * (i < d.nx - 1) - (i > 0 ? (double)m1[q - 1] : 0.0)) +
+                          ((double)m2[q] * (j < d.ny - 1) - (j > 0 ? (double)m2[q - sy] : 0.0)) +
+                          ((double)m3[q] * (k < d.nz - 1) - (k > 0 ? (double)m3[q - sz] : 0.0));
+        const double e = __dsub_rn(r, __dmul_rn(dv, inv_h));
+        acc[1] += fabs(e);
+        acc[2] += fabs(r);
         v[4].add(__dmul_rn(p, e));
-        const double g1 = i < d.nx - 1 ? fabs(((double)phi[q + 1] - p) / h) : 0.0;
-        const double g2 = j < d.ny - 1 ? fabs(((double)phi[q + sy] - p) / h) : 0.0;
-        const double g3 = k < d.nz - 1 ? fabs(((double)phi[q + sz] - p) / h) : 0.0;
-        g = NORM == W1_NORM_L1 ? fmax(g1, fmax(g2, g3))                      // q = infinity
-            : NORM == W1_NORM_L2 ? sqrt(g1 * g1 + g2 * g2 + g3 * g3) : g1 + g2 + g3;  // q = 2, q = 1
+        const double g1 = i < d.nx - 1 ? fabs(((double)phi[q + 1] - p) * inv_h) : 0.0;
+        const double g2 = j < d.ny - 1 ? fabs(((double)phi[q + sy] - p) * inv_h) : 0.0;
+        const double g3 = k < d.nz - 1 ? fabs(((double)phi[q + sz] - p) * inv_h) : 0.0;
+        g = fmax(g, NORM == W1_NORM_L1   ? fmax(g1, fmax(g2, g3))              // q = infinity
+                    : NORM == W1_NORM_L2 ? g1 * g1 + g2 * g2 + g3 * g3 : g1 + g2 + g3);  // q = 2 (squared), q = 1
+        return e * h3;
+    };
+    auto flush = [&](const double (&acc)[3]) {
+        v[0].add(acc[0]);
+        v[2].add(acc[1]);
+        v[3].add(acc[2]);
+    };
+    if (final3_pooled(d)) {
+        const int cx = d.nx / 2, cy = d.ny / 2;
+        const long long cplane = (long long)cx * cy;
+        if (t < d.n / 8) {
+            const int K = (int)(t / cplane), r = (int)(t - K * cplane);
+            const int J = r / cx, I = r - J * cx;
+            double acc[3] = {0.0, 0.0, 0.0};
+            double tot = 0.0, cost = 0.0;
+            for (int zc = 0; zc < 2; ++zc)
+                for (int b = 0; b < 2; ++b)
+                    for (int a = 0; a < 2; ++a) {
+                        const double qa = voxel(2 * I + a, 2 * J + b, 2 * K + zc, acc);
+                        cost += fabs(qa) * (double)(a + b + zc);
+                        tot += qa;
+                    }
+            flush(acc);
+            v[5].add(__dmul_rn(cost, h));
+            q_out[t] = tot;
+        }
+    } else if (t < d.n) {
+        int i, j, k;
+        node3(d, t, i, j, k);
+        double acc[3] = {0.0, 0.0, 0.0};
+        q_out[t] = voxel(i, j, k, acc);
+        flush(acc);
     }
-    __shared__ double sh[64 * 5];
-    block_csum<5>(v, sh);
+    __shared__ double sh[2 * 6 * T3];
+    block_csum_sh<6>(v, sh);
     __shared__ double gm[32];
     g = warp_max(g);
     if ((threadIdx.x & 31) == 0) gm[threadIdx.x >> 5] = g;
@@ -265,11 +306,11 @@ __global__ void __launch_bounds__(T3) k3_final_a(Dims3 d, double h, const float*
     if (threadIdx.x == 0) {
         double mx = 0.0;
         for (int w = 0; w < T3 / 32; ++w) mx = fmax(mx, gm[w]);
-        for (int c = 0; c < 5; ++c) {
+        for (int c = 0; c < 6; ++c) {
             part[blockIdx.x * FIN3_PART + 2 * c] = v[c].s;
             part[blockIdx.x * FIN3_PART + 2 * c + 1] = v[c].c;
         }
-        part[blockIdx.x * FIN3_PART + 10] = mx;
+        part[blockIdx.x * FIN3_PART + 12] = NORM == W1_NORM_L2 ? sqrt(mx) : mx;
     }
 }
 
@@ -282,22 +323,22 @@ struct Stats3Dev {
 // 2x2x2 (or 2x2, 2) blocks into a compact coarser grid (ping-pong between q and
 // q2), charging every mass the distance to its block's corner; the masses left
 // on the last grid are charged its diameter.
-__global__ void __launch_bounds__(1024) k3_final_b(Dims3 d, double h, const double* part, int nblk, double* q,
-                                                    double* q2, Stats3Dev* out)
+__global__ void __launch_bounds__(T3) k3_final_b(Dims3 d, double h, const double* part, int nblk, double* q,
+                                                  double* q2, Stats3Dev* out)
 {
-    __shared__ double sh[64 * 5];
-    CSum t[5];
+    __shared__ double sh[2 * 6 * T3];
+    CSum t[6];
     double mx = 0.0;
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-        for (int c = 0; c < 5; ++c) {
+        for (int c = 0; c < 6; ++c) {
             CSum x;
             x.s = part[b * FIN3_PART + 2 * c];
             x.c = part[b * FIN3_PART + 2 * c + 1];
             t[c].add(x);
         }
-        mx = fmax(mx, part[b * FIN3_PART + 10]);
+        mx = fmax(mx, part[b * FIN3_PART + 12]);
     }
-    block_csum<5>(t, sh);
+    block_csum_sh<6>(t, sh);
     __shared__ double tot[5], sad;
     if (threadIdx.x == 0) {
         for (int c = 0; c < 5; ++c) tot[c] = t[c].value();
@@ -311,10 +352,13 @@ __global__ void __launch_bounds__(1024) k3_final_b(Dims3 d, double h, const doub
     mx = warp_max(mx);
     if ((threadIdx.x & 31) == 0) gmx[threadIdx.x >> 5] = mx;
     __syncthreads();
+    // k3_final_a did the first level of the octree when every side is even
+    // (its cost is t[5], valid in thread 0)
     double* src = q;
     double* dst = q2;
-    int cx = d.nx, cy = d.ny, cz = d.nz;
-    double hx = h, hy = h, hz = h;
+    const int pool = final3_pooled(d) ? 2 : 1;
+    int cx = d.nx / pool, cy = d.ny / pool, cz = d.nz / pool;
+    double hx = pool * h, hy = pool * h, hz = pool * h;
     CSum cost;
     for (;;) {
         const int px = cx > 1 && cx % 2 == 0, py = cy > 1 && cy % 2 == 0, pz = cz > 1 && cz % 2 == 0;
@@ -326,15 +370,15 @@ __global__ void __launch_bounds__(1024) k3_final_b(Dims3 d, double h, const doub
         for (int c = threadIdx.x; c < cells; c += blockDim.x) {
             const int K = c / cplane, r = c - K * cplane;
             const int J = r / ncx, I = r - J * ncx;
-            double tot = 0.0;
+            double tot = 0.0, cs = 0.0;  // the block's costs are non-negative: one compensated add
             for (int zc = 0; zc < bz; ++zc)
                 for (int b = 0; b < by; ++b)
                     for (int a = 0; a < bx; ++a) {
                         const double qa = src[((long long)(bz * K + zc) * cy + (by * J + b)) * cx + (bx * I + a)];
-                        if (a | b | zc)
-                            cost.add(__dmul_rn(fabs(qa), (a ? hx : 0.0) + (b ? hy : 0.0) + (zc ? hz : 0.0)));
+                        if (a | b | zc) cs += __dmul_rn(fabs(qa), (a ? hx : 0.0) + (b ? hy : 0.0) + (zc ? hz : 0.0));
                         tot += qa;
                     }
+            cost.add(cs);
             dst[c] = tot;
         }
         __syncthreads();
@@ -350,12 +394,13 @@ __global__ void __launch_bounds__(1024) k3_final_b(Dims3 d, double h, const doub
     }
     CSum pn[3];
     pn[0] = cost;
+    if (threadIdx.x == 0) pn[0].add(t[5]);
     for (long long c = threadIdx.x; c < (long long)cx * cy * cz; c += blockDim.x) {
         const double v = src[c];
         if (v > 0) pn[1].add(v);
         else pn[2].add(-v);
     }
-    block_csum<3>(pn, sh);
+    block_csum_sh<3>(pn, sh);
     if (threadIdx.x == 0) {
         double g = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) g = fmax(g, gmx[w]);
@@ -1173,11 +1218,11 @@ static cudaError_t steps3(int norm, const Dims3& d, double h, float mu, float ta
 static cudaError_t final3(int norm, const Dims3& d, double h, const float* m1, const float* m2, const float* m3,
                           const float* phi, const float* rho, Scratch3& sc, cudaStream_t s)
 {
-    const dim3 g = grid3(d.n);
+    const dim3 g = grid3(final3_pooled(d) ? d.n / 8 : d.n);
     if (norm == W1_NORM_L1) k3_final_a<W1_NORM_L1><<<g, T3, 0, s>>>(d, h, m1, m2, m3, phi, rho, sc.q, sc.part);
     else if (norm == W1_NORM_L2) k3_final_a<W1_NORM_L2><<<g, T3, 0, s>>>(d, h, m1, m2, m3, phi, rho, sc.q, sc.part);
     else k3_final_a<W1_NORM_LINF><<<g, T3, 0, s>>>(d, h, m1, m2, m3, phi, rho, sc.q, sc.part);
-    k3_final_b<<<1, 1024, 0, s>>>(d, h, sc.part, (int)g.x, sc.q, sc.q + d.n, sc.st);
+    k3_final_b<<<1, T3, 0, s>>>(d, h, sc.part, (int)g.x, sc.q, sc.q + d.n, sc.st);
     return cudaGetLastError();
 }
 

@@ -307,21 +307,27 @@ __device__ __forceinline__ double warp_max(double v)
 // Knuth's TwoSum gives s = fl(a + b) and the exact rounding error e, so that
 // s + e == a + b exactly.  The explicitly rounded intrinsics keep the compiler
 // from contracting or reordering the steps.  A compensated sum (Neumaier's
-// scheme, with the error term of every addition from TwoSum) carries the
+// scheme, with the exact error term of every addition) carries the
 // running value as the unevaluated pair s + c: its error is about one rounding
 // of the result plus n u^2 sum|x_i|, instead of about n u sum|x_i| for a plain
 // left-to-right sum (u the unit roundoff).
-__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e)
-{
-    s = __dadd_rn(a, b);
-    const double bb = __dsub_rn(s, a);
-    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
-}
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// s = fl(a + b) and its exact rounding error e from Dekker's Fast2Sum on the operands ordered by
+// magnitude (Neumaier's comparison): e = (big - s) + small is exact when
+// |big| >= |small|.  Three FP64 additions and a comparison instead of six
+// additions; the selects run on the integer pipe.  GB300 issues FP64 at a
+// small fraction of its FP32 rate, so the compensated sums use this form.
+__device__ __forceinline__ void two_sum_ordered(double a, double b, double& s, double& e)
+{
+    s = __dadd_rn(a, b);
+    const bool ge = fabs(a) >= fabs(b);
+    const double big = ge ? a : b, small = ge ? b : a;
+    e = __dadd_rn(__dsub_rn(big, s), small);
 }
 
 struct CSum {
@@ -329,7 +335,7 @@ struct CSum {
     __device__ __forceinline__ void add(double x)
     {
         double t, e;
-        two_sum(s, x, t, e);
+        two_sum_ordered(s, x, t, e);
         s = t;
         c = __dadd_rn(c, e);
     }
@@ -337,7 +343,7 @@ struct CSum {
     __device__ __forceinline__ void add(const CSum& o)
     {
         double t, e;
-        two_sum(s, o.s, t, e);
+        two_sum_ordered(s, o.s, t, e);
         s = t;
         c = __dadd_rn(c, __dadd_rn(o.c, e));
     }
@@ -385,6 +391,48 @@ __device__ void block_csum(CSum (&v)[N], double* sh)
             }
     }
     __syncthreads();
+}
+
+// The same sums through shared memory, for blocks whose lanes would otherwise
+// spend most of a shuffle tree adding zeros in FP64: every thread stores its N
+// sums, then each level adds the upper half of every sum's column into its
+// lower half, the N columns sharing the level's threads.  A level of width w
+// costs N w additions in total instead of N per lane.  Fixed order; result
+// valid in thread 0.  sh: 2 N blockDim.x doubles; blockDim.x a power of two.
+template <int N>
+__device__ void block_csum_sh(CSum (&v)[N], double* sh)
+{
+    const int T = blockDim.x, tid = threadIdx.x;
+    double* S = sh;
+    double* C = sh + N * T;
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        S[c * T + tid] = v[c].s;
+        C[c * T + tid] = v[c].c;
+    }
+    __syncthreads();
+    for (int w = T / 2; w >= 1; w >>= 1) {
+        for (int idx = tid; idx < N * w; idx += T) {
+            const int c = idx / w, k = c * T + (idx - c * w);
+            CSum a, b;
+            a.s = S[k];
+            a.c = C[k];
+            b.s = S[k + w];
+            b.c = C[k + w];
+            a.add(b);
+            S[k] = a.s;
+            C[k] = a.c;
+        }
+        __syncthreads();
+    }
+    if (tid == 0)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            v[c].s = S[c * T];
+            v[c].c = C[c * T];
+        }
+    __syncthreads();  // sh free for the caller again
 }
 
 // Block sums of three per-thread FP32 values (the terms of the stop test),

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep_reduce(const float* __res
                                                               const float* __restrict__ r1, long long n, int nbatch,
                                                               double h, Ctl* ctls, double* part)
 {
-    __shared__ double sh[64 * 3];
+    __shared__ double sh[2 * 3 * PREP_THREADS];
     __shared__ bool last;
     const int pair = blockIdx.y;
     Ctl* ctl = ctls + pair;
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep_reduce(const float* __res
         v[1].add(b);
         v[2].add(__dsub_rn((double)a, (double)b));
     }
-    block_csum<3>(v, sh);
+    block_csum_sh<3>(v, sh);
     double nb[1] = {(double)bad};
     block_sum<1>(nb, sh);
     if (threadIdx.x == 0) {
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep_reduce(const float* __res
         }
         nf[0] += q[6];
     }
-    block_csum<3>(t, sh);
+    block_csum_sh<3>(t, sh);
     block_sum<1>(nf, sh);
     if (threadIdx.x == 0) {
         const double M0 = t[0].value() * h * h, M1 = t[1].value() * h * h;
@@ -2173,21 +2173,44 @@ static int final_blocks_per_pair(int) { return FIN_BLOCKS_PER_PAIR; }
 
 size_t final_part_doubles(int pairs) { return (size_t)final_blocks_per_pair(pairs) * pairs * FIN_PART_PER_BLOCK; }
 
+// Grids whose sides are multiples of FIN_TILE do the first five levels of the
+// route bound inside k_final_a, one FIN_TILE x FIN_TILE tile per block step
+// ((FIN_TILE / 2)^2 = FIN_THREADS cells of 2 x 2 nodes, one per thread).
+static constexpr int FIN_TILE = 32;
+static_assert((FIN_TILE / 2) * (FIN_TILE / 2) == FIN_THREADS, "one 2x2 cell per thread");
+
+// Nodes per side that k_final_a pools before k_final_b continues the tree.
+__host__ __device__ static inline int final_pool(int nx, int ny)
+{
+    if (nx % FIN_TILE == 0 && ny % FIN_TILE == 0) return FIN_TILE;
+    return ((nx & 1) == 0 && (ny & 1) == 0) ? 2 : 1;
+}
+
 // Per node (FP64 from the FP32 state; e = rho - div m the constraint residual):
 //   ||m(x)||_p, phi rho, |e|, |rho|, phi e, and ||grad phi(x)||_q.
 // Each sum is compensated and left unscaled; h^2 is applied once at the end.
-// Every term except the p = 2 norm and e is exact in FP64 (products and sums
-// of two FP32 values).  When nx and ny are both even, each thread takes 2 x 2
-// blocks of nodes and also does the first level of the route bound (see
-// k_final_b): the cost of sending each node's residual mass to its block's
-// first node, and the block's total, stored compactly in q for the next level.
+// The signed sums (phi rho, phi e) add every node's term to their compensated
+// sum; the non-negative ones (||m||_p, |e|, |rho|, route costs) add a 2 x 2
+// cell's terms in plain FP64 first (relative error at most 3 units of
+// roundoff, which no cancellation can amplify) and that to the compensated
+// sum.  Every term except the p = 2 norm and e is exact in FP64 (products and
+// sums of two FP32 values); 1/h multiplies instead of dividing by h (one
+// rounding more where h is not a power of two).  For p = 2 the running maximum
+// of ||grad phi||_2 is kept squared, with one square root per block (the
+// square root is monotone and correctly rounded, so the maximum is the same).
+// When nx and ny are both even each thread takes 2 x 2 cells and also does the
+// first level of the route bound (see k_final_b): the cost of sending each
+// node's residual mass to its cell's first node; with both sides multiples of
+// FIN_TILE the block carries the tree on to one node per tile.  The masses
+// left (per cell or per tile) go to q, compactly, for k_final_b.
 template <int NORM>
 __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict__ m1, const float* __restrict__ m2,
                                                          const float* __restrict__ phi, const float* __restrict__ rho,
                                                          int nx, int ny, double h, double* __restrict__ q,
                                                          double* part, const Ctl* ctls)
 {
-    __shared__ double sh[64 * 6];
+    __shared__ double sh[2 * 6 * FIN_THREADS];
+    __shared__ double tq[2][FIN_THREADS];
     const int pair = blockIdx.y;
     if (ctls && ctls[pair].error == 2) return;
     const long long n = (long long)nx * ny;
@@ -2197,54 +2220,96 @@ __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict
     phi += off;
     rho += off;
     q += 2 * off;
-    CSum v[6];  // sum ||m||_p, sum phi rho, sum |e|, sum |rho|, sum phi e, first-level route cost
-    double gm = 0.0;
-    const double h2 = h * h;
-    // the node's terms; returns its residual mass e h^2
-    auto node = [&](int i, int j) -> double {
+    CSum v[6];  // sum ||m||_p, sum phi rho, sum |e|, sum |rho|, sum phi e, route cost
+    double gm = 0.0;  // max ||grad phi||_q (squared for p = 2)
+    const double h2 = h * h, inv_h = 1.0 / h;
+    // the node's terms (non-negative ones into acc); returns its residual mass e h^2
+    auto node = [&](int i, int j, double (&acc)[3]) -> double {
         const long long k = (long long)j * nx + i;
         const double a1 = (i < nx - 1) ? (double)m1[k] : 0.0;
         const double a2 = (j < ny - 1) ? (double)m2[k] : 0.0;
-        v[0].add(NORM == W1_NORM_L1     ? __dadd_rn(fabs(a1), fabs(a2))
-                 : NORM == W1_NORM_LINF ? fmax(fabs(a1), fabs(a2))
-                                        : sqrt(__dadd_rn(__dmul_rn(a1, a1), __dmul_rn(a2, a2))));
+        acc[0] += NORM == W1_NORM_L1     ? __dadd_rn(fabs(a1), fabs(a2))
+                  : NORM == W1_NORM_LINF ? fmax(fabs(a1), fabs(a2))
+                                         : sqrt(__dadd_rn(__dmul_rn(a1, a1), __dmul_rn(a2, a2)));
         const double p = phi[k], r = rho[k];
         v[1].add(__dmul_rn(p, r));
         double d = __dadd_rn(a1, a2);
         if (i > 0) d = __dsub_rn(d, (double)m1[k - 1]);
         if (j > 0) d = __dsub_rn(d, (double)m2[k - nx]);
-        const double e = __dsub_rn(r, __ddiv_rn(d, h));
-        v[2].add(fabs(e));
-        v[3].add(fabs(r));
+        const double e = __dsub_rn(r, __dmul_rn(d, inv_h));
+        acc[1] += fabs(e);
+        acc[2] += fabs(r);
         v[4].add(__dmul_rn(p, e));
-        const double g1 = (i < nx - 1) ? ((double)phi[k + 1] - p) / h : 0.0;
-        const double g2 = (j < ny - 1) ? ((double)phi[k + nx] - p) / h : 0.0;
+        const double g1 = (i < nx - 1) ? __dmul_rn((double)phi[k + 1] - p, inv_h) : 0.0;
+        const double g2 = (j < ny - 1) ? __dmul_rn((double)phi[k + nx] - p, inv_h) : 0.0;
         const double gq = (NORM == W1_NORM_L1) ? fmax(fabs(g1), fabs(g2))
-                          : (NORM == W1_NORM_LINF ? fabs(g1) + fabs(g2) : sqrt(g1 * g1 + g2 * g2));
+                          : (NORM == W1_NORM_LINF ? fabs(g1) + fabs(g2) : g1 * g1 + g2 * g2);
         gm = fmax(gm, gq);
         return e * h2;
     };
+    auto flush = [&](const double (&acc)[3]) {
+        v[0].add(acc[0]);
+        v[2].add(acc[1]);
+        v[3].add(acc[2]);
+    };
+    // a 2 x 2 cell with first node (i, j): its terms and the first route
+    // level (offsets (1,0) and (0,1) cost one edge hl, (1,1) two); returns the
+    // cell's mass.  The same step, on masses, serves the coarser levels.
+    auto pool4 = [&](double a00, double a10, double a01, double a11, double hl) -> double {
+        v[5].add(__dmul_rn(__dadd_rn(__dadd_rn(fabs(a10), fabs(a01)), __dmul_rn(2.0, fabs(a11))), hl));
+        return ((a00 + a10) + a01) + a11;
+    };
+    auto cell = [&](int i, int j) -> double {
+        double acc[3] = {0.0, 0.0, 0.0};
+        const double q00 = node(i, j, acc), q10 = node(i + 1, j, acc);
+        const double q01 = node(i, j + 1, acc), q11 = node(i + 1, j + 1, acc);
+        flush(acc);
+        return pool4(q00, q10, q01, q11, h);
+    };
     const long long stride = (long long)gridDim.x * blockDim.x;
-    if ((nx & 1) == 0 && (ny & 1) == 0) {
+    const int pool = final_pool(nx, ny);
+    if (pool == FIN_TILE) {
+        const int tx = nx / FIN_TILE, ntile = tx * (ny / FIN_TILE);
+        const int half0 = FIN_TILE / 2, ci = threadIdx.x % half0, cj = threadIdx.x / half0;
+        for (int t = blockIdx.x; t < ntile; t += gridDim.x) {  // uniform over the block
+            const int TJ = t / tx, TI = t - TJ * tx;
+            tq[0][threadIdx.x] = cell(TI * FIN_TILE + 2 * ci, TJ * FIN_TILE + 2 * cj);
+            // the tile's cells down to one node: side 16 -> 8 -> 4 -> 2 -> 1 (ping-pong
+            // buffers; the barrier before each level orders it after the last one)
+            int side = half0, src = 0;
+            double hl = 2.0 * h;
+            while (side > 1) {
+                __syncthreads();
+                const int half = side / 2;
+                if ((int)threadIdx.x < half * half) {
+                    const int J = threadIdx.x / half, I = threadIdx.x - J * half;
+                    const double* sq = tq[src] + 2 * J * side + 2 * I;
+                    tq[src ^ 1][threadIdx.x] = pool4(sq[0], sq[1], sq[side], sq[side + 1], hl);
+                }
+                src ^= 1;
+                side = half;
+                hl *= 2.0;
+            }
+            // thread 0 wrote the last level itself; the next tile's cells overwrite
+            // only entries no thread reads any more
+            if (threadIdx.x == 0) q[t] = tq[src][0];
+        }
+    } else if (pool == 2) {
         const int ncx = nx / 2;
         const long long nc = n / 4;
         for (long long kb = blockIdx.x * (long long)blockDim.x + threadIdx.x; kb < nc; kb += stride) {
             const int J = (int)(kb / ncx), I = (int)(kb - (long long)J * ncx);
-            const double q00 = node(2 * I, 2 * J), q10 = node(2 * I + 1, 2 * J);
-            const double q01 = node(2 * I, 2 * J + 1), q11 = node(2 * I + 1, 2 * J + 1);
-            // offsets (1,0) and (0,1) cost one edge h, (1,1) two
-            v[5].add(__dmul_rn(fabs(q10), h));
-            v[5].add(__dmul_rn(fabs(q01), h));
-            v[5].add(__dmul_rn(fabs(q11), 2.0 * h));
-            q[kb] = ((q00 + q10) + q01) + q11;
+            q[kb] = cell(2 * I, 2 * J);
         }
     } else {
         for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += stride) {
             const int j = (int)(k / nx), i = (int)(k - (long long)j * nx);
-            q[k] = node(i, j);
+            double acc[3] = {0.0, 0.0, 0.0};
+            q[k] = node(i, j, acc);
+            flush(acc);
         }
     }
-    block_csum<6>(v, sh);
+    block_csum_sh<6>(v, sh);
     gm = warp_max(gm);
     __shared__ double shm[32];
     if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = gm;
@@ -2256,7 +2321,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict
             pp[2 * c] = v[c].s;
             pp[2 * c + 1] = v[c].c;
         }
-        pp[12] = gm;
+        pp[12] = NORM == W1_NORM_L2 ? sqrt(gm) : gm;
     }
 }
 
@@ -2267,8 +2332,8 @@ __global__ void __launch_bounds__(FIN_THREADS) k_final_a(const float* __restrict
 // explicit flux carrying rho - div m, hence f + route >= W1 of the discrete
 // problem.  The saddle value is the Lagrangian of eq. minmax_cp at the state,
 // L(m, phi) = f(m) + <phi, div m - rho>_h = h^2 (sum ||m||_p - sum phi e).
-__global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, double* q, const double* part,
-                                                  int nparts, Ctl* ctls)
+__global__ void __launch_bounds__(FIN_THREADS) k_final_b(int nx, int ny, double h, double* q, const double* part,
+                                                         int nparts, Ctl* ctls)
 {
     const int pair = blockIdx.x;
     Ctl* ctl = ctls + pair;
@@ -2277,7 +2342,7 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
     double* src = q + 2 * n * pair;
     double* dst = src + n;
     part += (size_t)pair * nparts * FIN_PART_PER_BLOCK;
-    __shared__ double sh[64 * 6];
+    __shared__ double sh[2 * 6 * FIN_THREADS];
     CSum v[6];
     double gm = 0.0;
     for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
@@ -2289,7 +2354,7 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
         }
         gm = fmax(gm, part[b * FIN_PART_PER_BLOCK + 12]);
     }
-    block_csum<6>(v, sh);
+    block_csum_sh<6>(v, sh);
     __shared__ double tot[5], sad;
     __shared__ CSum cost0;
     if (threadIdx.x == 0) {
@@ -2308,10 +2373,11 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
     if (threadIdx.x == 0)
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) gm = fmax(gm, shm[w]);
 
-    // k_final_a did the first level of the tree when both sides are even
-    const bool pooled = (nx & 1) == 0 && (ny & 1) == 0;
-    int cx = pooled ? nx / 2 : nx, cy = pooled ? ny / 2 : ny;
-    double hx = pooled ? 2.0 * h : h, hy = pooled ? 2.0 * h : h;
+    // k_final_a did the first levels of the tree: one (both sides even) or
+    // five (both sides multiples of FIN_TILE)
+    const int pool = final_pool(nx, ny);
+    int cx = nx / pool, cy = ny / pool;
+    double hx = pool * h, hy = pool * h;
     CSum cost;
     for (;;) {
         const int px = (cx > 1 && (cx & 1) == 0), py = (cy > 1 && (cy & 1) == 0);
@@ -2323,13 +2389,14 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
         const double w[2][2] = {{0.0, hx}, {hy, hx + hy}};  // distance to the block's corner
         for (int k = threadIdx.x; k < nc; k += blockDim.x) {
             const int J = k / ncx, I = k - J * ncx;
-            double total = 0.0;
+            double total = 0.0, cs = 0.0;  // the block's costs are non-negative: one compensated add
             for (int b = 0; b < by; ++b)
                 for (int a = 0; a < bx; ++a) {
                     const double qa = src[(size_t)(by * J + b) * cx + (bx * I + a)];
-                    if (a | b) cost.add(__dmul_rn(fabs(qa), w[b][a]));
+                    if (a | b) cs += __dmul_rn(fabs(qa), w[b][a]);
                     total += qa;
                 }
+            cost.add(cs);
             dst[k] = total;
         }
         __syncthreads();
@@ -2349,7 +2416,7 @@ __global__ void __launch_bounds__(1024) k_final_b(int nx, int ny, double h, doub
         if (x > 0) ws[1].add(x);
         else ws[2].add(-x);
     }
-    block_csum<3>(ws, sh);
+    block_csum_sh<3>(ws, sh);
     if (threadIdx.x == 0) {
         const double h2 = h * h;
         const double diam = (cx - 1) * hx + (cy - 1) * hy;
@@ -2377,7 +2444,7 @@ cudaError_t launch_final(int norm, const float* m1, const float* m2, const float
         k_final_a<W1_NORM_L2><<<g, FIN_THREADS, 0, s>>>(m1, m2, phi, rho, nx, ny, h, q, part, ctl);
     else
         k_final_a<W1_NORM_LINF><<<g, FIN_THREADS, 0, s>>>(m1, m2, phi, rho, nx, ny, h, q, part, ctl);
-    k_final_b<<<pairs, 1024, 0, s>>>(nx, ny, h, q, part, bpp, ctl);
+    k_final_b<<<pairs, FIN_THREADS, 0, s>>>(nx, ny, h, q, part, bpp, ctl);
     return cudaGetLastError();
 }
 

@@ -171,8 +171,12 @@ def test_prolong_matches_oracle(w1, shape):
 
 
 @pytest.mark.parametrize("norm", [L1, L2, LINF])
-@pytest.mark.parametrize("shape", [(1, 16), (5, 7), (64, 64), (96, 80), (512, 512)])
+@pytest.mark.parametrize("shape", [(1, 16), (5, 7), (64, 64), (96, 80), (32, 96), (160, 64), (512, 512)])
 def test_state_stats_match_oracle(w1, norm, shape):
+    """Certificate statistics of a random state against the oracle's: odd sides
+    (no pooling), even sides (one route level pooled per thread), and sides that
+    are multiples of 32 (route levels pooled per 32 x 32 tile, the coarse tree
+    ending on a 3 x 1 grid and on a 2 x 5 grid with an odd side)."""
     rng = np.random.default_rng(5)
     rho, m1, m2, phi = rand_state(rng, *shape, scale=0.2)
     h = 1.0 / max(shape)
