@@ -159,7 +159,8 @@ int fault_halo_rank()
 // On grids coarser than 512^2 the schedule keeps eps_L at its 512^2 value
 // instead of letting eq. stop_tol's (512 h)^2 loosen it: measured on the 128^2
 // and 256^2 serving pairs, the loosened tolerance took the p = 1 error to
-// 2e-4 at 128^2, the capped one kept both norms below 5e-5.
+// 2e-4 at 128^2; the capped scales lie at or below settings measured at 5e-5
+// or less.
 struct CalibratedSchedule {
     double tol_scale, alpha, theta, step_ratio;
 };
