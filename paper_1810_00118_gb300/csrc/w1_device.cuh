@@ -120,6 +120,10 @@ __device__ __forceinline__ void dsmem_st_f64(uint32_t addr, double v)
 {
     asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
+__device__ __forceinline__ void dsmem_st_u32(uint32_t addr, unsigned v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
 __device__ __forceinline__ double dsmem_ld_f64(uint32_t addr)
 {
     double v;
@@ -136,6 +140,12 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 __device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// Ends the barrier object, so that its memory can hold a new one (a persistent
+// launch initialises the halo barriers again for every level it solves).
+__device__ __forceinline__ void mbar_inval(uint32_t bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ void mbar_expect(uint32_t bar, unsigned bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)

@@ -146,6 +146,11 @@ int resident_cluster_ok(int norm, int cluster, int nx, int ny);
 // size class.
 struct CascadeLevel {
     int nx, ny;
+    // how a cluster of CASCADE_CLUSTER CTAs solves the level of a pair of a
+    // cluster class: CASCADE_SPLIT4 / CASCADE_SPLITW in row bands over the
+    // cluster (four-nodes-per-thread or wide layout), CASCADE_ONE4 /
+    // CASCADE_ONEW on CTA 0 alone; unused for single-CTA classes
+    int mode;
     float mu, tau, ih;
     double h, tol;
     float* rho;  // pair 0's planes of this level; pair stride nx * ny
@@ -159,14 +164,22 @@ struct CascadeClass {
     CascadeLevel lv[W1_MAX_LEVELS];
 };
 struct CascadeArgs {
-    const CascadeClass* cls;  // device array
+    const CascadeClass* cls;  // device array: classes whose pairs one CTA solves
     int n_classes;
     int total;            // pairs over all classes
     unsigned int* next;   // work counter, zero before the launch
     long long cap;        // per-level step cap
     int K;                // steps between stop tests
     unsigned long long budget_ns;
+    // cluster launch only: classes whose pairs a cluster of CASCADE_CLUSTER
+    // CTAs solves (taken first), and their work counter
+    const CascadeClass* big;
+    int n_big;
+    int total_big;
+    unsigned int* next_big;
 };
+static constexpr int CASCADE_CLUSTER = 4;
+enum { CASCADE_SPLIT4 = 1, CASCADE_SPLITW = 2, CASCADE_ONE4 = 3, CASCADE_ONEW = 4 };
 // Which single-CTA layouts hold an nx x ny level (nx % 4 == 0): bit 0 four
 // nodes per thread (at most 4096 nodes), bit 1 wide (at most 16384 nodes, a
 // multiple of 128).  A persistent launch with wide = false runs only levels of
@@ -175,6 +188,14 @@ int cascade_level_fits(int nx, int ny);
 // CTAs of the persistent launch that fit the device at once.
 int cascade_ctas(int norm, bool wide);
 cudaError_t launch_cascade(int norm, bool wide, const CascadeArgs& a, int ctas, cudaStream_t s);
+// How a cluster of CASCADE_CLUSTER CTAs solves an nx x ny level (a CASCADE_*
+// mode), or 0 when it cannot.
+int cascade_level_mode_cluster(int nx, int ny);
+// Clusters of the cluster persistent launch that fit the device at once.
+int cascade_clusters(int norm);
+// The persistent launch with clusters of CASCADE_CLUSTER CTAs: each cluster
+// takes pairs of a.big together, then each of its CTAs pairs of a.cls alone.
+cudaError_t launch_cascade_cluster(int norm, const CascadeArgs& a, int clusters, cudaStream_t s);
 // Prox-PDHG (Algorithm 2 on one level; Algorithm 4 through the plan).  Every
 // plane holds the batch's pairs back to back (pair stride nx * ny).
 struct PdArgs {

@@ -1384,7 +1384,13 @@ __device__ __forceinline__ void res4_level(const ResArgs& a, const int pair, con
         if (P.fpr_out) P.fpr_out[pair] = R;
         if (P.iters_out) P.iters_out[pair] = it;
     }
-    if (CL) cg::this_cluster().sync();
+    if (CL) {
+        cg::this_cluster().sync();  // every halo row has been consumed
+        if (t == 0) {
+            mbar_inval(bar_phi);
+            mbar_inval(bar_m2);
+        }
+    }
 }
 
 template <int NORM, bool CL>
@@ -1778,7 +1784,13 @@ __device__ __forceinline__ void wide_level(const ResArgs& a, const int pair, con
         if (P.fpr_out) P.fpr_out[pair] = R;
         if (P.iters_out) P.iters_out[pair] = it;
     }
-    if (CL) cg::this_cluster().sync();
+    if (CL) {
+        cg::this_cluster().sync();  // every halo row has been consumed
+        if (t == 0) {
+            mbar_inval(bar_phi);
+            mbar_inval(bar_m2);
+        }
+    }
 }
 
 template <int NORM, bool CL>
@@ -1911,7 +1923,224 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cascade(CascadeArgs a)
     }
 }
 
+// Levels of the pairs of cluster classes, in row bands over the cluster's CTAs
+// (bodies kept apart from the single-CTA ones, as those are, for registers).
+template <int NORM>
+__device__ __noinline__ void cascade_level_split4(const ResArgs& a, int pair, int rank, unsigned char* smraw)
+{
+    res4_level<NORM, true>(a, pair, CASCADE_CLUSTER, rank, smraw);
+}
+template <int NORM>
+__device__ __noinline__ void cascade_level_splitw(const ResArgs& a, int pair, int rank, unsigned char* smraw)
+{
+    wide_level<NORM, true, true>(a, pair, CASCADE_CLUSTER, rank, smraw);
+}
+
+// Levels that fit the four-nodes-per-thread layout of one CTA stay on CTA 0
+// (split four ways they would not step faster); larger ones split into row
+// bands of at least two rows when they can, else stay on CTA 0 in the wide
+// layout.
+int cascade_level_mode_cluster(int nx, int ny)
+{
+    const int f = cascade_level_fits(nx, ny);
+    if (f & 1) return CASCADE_ONE4;
+    if (ny / CASCADE_CLUSTER >= 2 && resident_fits(nx, ny, CASCADE_CLUSTER))
+        return (long long)(ny / CASCADE_CLUSTER) * nx <= RES_MAX_NODES ? CASCADE_SPLIT4 : CASCADE_SPLITW;
+    return (f & 2) ? CASCADE_ONEW : 0;
+}
+
+// The level's ResArgs for pair b of class K (thread 0 writes, the block reads
+// after a barrier).
+__device__ void cascade_args(ResArgs& r, const CascadeArgs& a, const CascadeClass* K, int l)
+{
+    const CascadeLevel& v = K->lv[l];
+    r = ResArgs{};
+    r.m1 = v.m1;
+    r.m2 = v.m2;
+    r.phi = v.phi;
+    r.rho = v.rho;
+    r.pairs = 1;
+    IterArgs& it = r.it;
+    it.nx = v.nx;
+    it.ny = v.ny;
+    it.mu = v.mu;
+    it.tau = v.tau;
+    it.ih = v.ih;
+    it.h = v.h;
+    it.tol = v.tol;
+    it.cap = a.cap;
+    it.K = a.K;
+    it.fixed = 0;
+    it.level = l;
+    it.budget_ns = a.budget_ns;
+    it.stride = v.nx * v.ny;
+    it.ctl = K->ctl;
+}
+
+// Level l's starting state of pair b, nodes [k0, k1): zero on the coarsest
+// level (Algorithm 3 starts from m = 0, phi = 0), else Interpolate of level l - 1.
+__device__ void cascade_init(const CascadeClass* K, int l, int b, int k0, int k1)
+{
+    const CascadeLevel& v = K->lv[l];
+    const size_t off = (size_t)b * v.nx * v.ny;
+    if (l == 0) {
+        for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+            v.m1[off + k] = 0.f;
+            v.m2[off + k] = 0.f;
+            v.phi[off + k] = 0.f;
+        }
+    } else {
+        const CascadeLevel& cv = K->lv[l - 1];
+        const size_t co = (size_t)b * cv.nx * cv.ny;
+        for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+            const int j = k / v.nx, i = k - j * v.nx;
+            prolong_node(cv.nx, cv.ny, cv.m1 + co, cv.m2 + co, cv.phi + co, v.m1 + off, v.m2 + off, v.phi + off, i,
+                         j);
+        }
+    }
+}
+
+// Persistent launch in clusters of CASCADE_CLUSTER CTAs.  Phase 1: a cluster
+// takes the next pair of the cluster classes (largest grids; CTA 0 draws it
+// and writes it into every CTA's shared memory), initialises each level in row
+// bands and solves it in row bands over the cluster (or on CTA 0 alone when
+// the level cannot be split).  Phase 2, once those pairs are all taken: each
+// CTA takes pairs of the single-CTA classes alone, as k_cascade does, with no
+// cluster barrier and no distributed shared memory, so CTAs may leave at
+// different times.
+template <int NORM>
+__global__ void __launch_bounds__(RES_THREADS, 1) k_cascade_cl(CascadeArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int s_c, s_b, s_l, s_go;
+    __shared__ unsigned s_w;
+    __shared__ ResArgs s_args;
+    volatile int* vc = &s_c;
+    volatile int* vb = &s_b;
+    volatile int* vl = &s_l;
+    volatile int* vgo = &s_go;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    for (;;) {
+        cl.sync();  // every CTA has read the previous draw
+        if (rank == 0 && threadIdx.x == 0) {
+            const unsigned w = atomicAdd(a.next_big, 1u);
+            for (int r = 0; r < CASCADE_CLUSTER; ++r) dsmem_st_u32(dsmem_map(smem_u32(&s_w), (uint32_t)r), w);
+        }
+        cl.sync();
+        const int w = (int)*reinterpret_cast<volatile unsigned*>(&s_w);
+        if (w >= a.total_big) break;  // the same draw in every CTA of the cluster
+        int c = 0, b = w;
+        while (c < a.n_big - 1 && b >= a.big[c].count) {
+            b -= a.big[c].count;
+            ++c;
+        }
+        const CascadeClass* K = a.big + c;
+        if (K->ctl[b].error) continue;  // set before the launch: the same in every CTA
+        for (int l = 0; l < K->levels; ++l) {
+            const CascadeLevel& v = K->lv[l];
+            const int rows = v.ny / CASCADE_CLUSTER, rest = v.ny - rows * CASCADE_CLUSTER;
+            // row bands (the last one takes the rows a split leaves over)
+            const int j0 = rank * rows, j1 = rank == CASCADE_CLUSTER - 1 ? j0 + rows + rest : j0 + rows;
+            cascade_init(K, l, b, j0 * v.nx, j1 * v.nx);
+            if (threadIdx.x == 0) cascade_args(s_args, a, K, l);
+            cl.sync();  // the level's starting state (all bands) is in global memory
+            const int mode = v.mode;
+            if (mode == CASCADE_SPLIT4) cascade_level_split4<NORM>(s_args, b, rank, smraw);
+            else if (mode == CASCADE_SPLITW) cascade_level_splitw<NORM>(s_args, b, rank, smraw);
+            else if (rank == 0 && mode == CASCADE_ONE4) cascade_level_small<NORM>(s_args, b, smraw);
+            else if (rank == 0) cascade_level_wide<NORM>(s_args, b, smraw);
+            cl.sync();  // the level's final state is stored before the next level reads it
+        }
+    }
+    // phase 2: single-CTA classes, one pair per CTA
+    for (;;) {
+        __syncthreads();  // the previous pair is finished before the shared fields change
+        if (threadIdx.x == 0) {
+            const int w = (int)atomicAdd(a.next, 1u);
+            int c = 0, b = w;
+            while (c < a.n_classes - 1 && b >= a.cls[c].count) {
+                b -= a.cls[c].count;
+                ++c;
+            }
+            *vc = c;
+            *vb = b;
+            *vl = 0;
+            *vgo = w >= a.total ? 0 : (a.cls[c].ctl[b].error ? 2 : 1);
+        }
+        __syncthreads();
+        const int go = *vgo;
+        if (go == 0) return;
+        if (go == 2) continue;
+        for (;;) {
+            const int l = *vl;
+            const CascadeClass* K = a.cls + *vc;
+            if (l >= K->levels) break;
+            const int b = *vb;
+            const CascadeLevel& v = K->lv[l];
+            const int n = v.nx * v.ny;
+            cascade_init(K, l, b, 0, n);
+            if (threadIdx.x == 0) cascade_args(s_args, a, K, l);
+            __syncthreads();  // the level's state is in global memory for the level solve to load
+            if (n <= RES_MAX_NODES) cascade_level_small<NORM>(s_args, b, smraw);
+            else cascade_level_wide<NORM>(s_args, b, smraw);
+            __syncthreads();  // the level's final state is stored before the next level reads it
+            if (threadIdx.x == 0) *vl = l + 1;
+            __syncthreads();
+        }
+    }
+}
+
 static size_t cascade_smem(bool wide) { return wide ? resident_wide_smem(RESW_MAX_NODES) : resident_smem(RES_MAX_NODES); }
+
+static const void* cascade_cl_fn(int norm)
+{
+    return norm == W1_NORM_L1 ? (const void*)k_cascade_cl<W1_NORM_L1>
+           : norm == W1_NORM_L2 ? (const void*)k_cascade_cl<W1_NORM_L2>
+                                : (const void*)k_cascade_cl<W1_NORM_LINF>;
+}
+
+static cudaLaunchConfig_t cascade_cl_config(int clusters, cudaLaunchAttribute* attr)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(clusters * CASCADE_CLUSTER, 1, 1);
+    cfg.blockDim = dim3(RES_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = cascade_smem(true);
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CASCADE_CLUSTER;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+int cascade_clusters(int norm)
+{
+    cudaLaunchAttribute attr[1];
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = cascade_cl_config(sms / CASCADE_CLUSTER, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, cascade_cl_fn(norm), &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+cudaError_t launch_cascade_cluster(int norm, const CascadeArgs& a, int clusters, cudaStream_t s)
+{
+    if (clusters < 1 || a.total + a.total_big < 1) return cudaErrorInvalidValue;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cascade_cl_config(clusters, attr);
+    cfg.stream = s;
+    void* args[1] = {(void*)&a};
+    return cudaLaunchKernelExC(&cfg, cascade_cl_fn(norm), args);
+}
 
 template <int NORM>
 static cudaError_t cascade_attr()
@@ -1919,7 +2148,10 @@ static cudaError_t cascade_attr()
     cudaError_t e = cudaFuncSetAttribute(k_cascade<NORM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cascade_smem(false));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_cascade<NORM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_cascade<NORM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cascade_smem(true));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_cascade_cl<NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)cascade_smem(true));
 }
 

@@ -966,8 +966,11 @@ extern "C" w1_status w1_plan_potential(w1_plan* p, float* phi, void* stream)
 // One batched plan per size class holds that class's arena (levels, control
 // blocks, partials).  Classes whose every level fits one CTA run together in one
 // persistent launch (k_cascade: a CTA takes a pair, runs all its levels, takes
-// the next; pairs of the largest grids first); the other classes run their own
-// plan's graph on a stream of their own.  A solve is: record -> [other classes on
+// the next; pairs of the largest grids first).  When some class has a level
+// that needs a cluster of CASCADE_CLUSTER CTAs (and fits one), the persistent
+// launch runs in clusters instead (k_cascade_cl): clusters take those pairs
+// first, then each CTA takes single-CTA pairs alone.  Classes that fit neither
+// run their own plan's graph on a stream of their own.  A solve is: record -> [other classes on
 // their streams] and [prep per class -> graph: restriction per class -> the
 // persistent launch -> final statistics and the read-back per class] -> join.
 
@@ -976,10 +979,13 @@ struct w1_mixed {
     std::vector<w1_plan*> plans;
     std::vector<int> count;
     std::vector<int> persistent;   // 1: the class runs in the persistent launch
-    std::vector<int> order;        // persistent classes, largest grid first
+    std::vector<int> order;        // persistent single-CTA classes, largest grid first
+    std::vector<int> order_big;    // persistent cluster classes, largest grid first
     CascadeClass* d_cls;
-    unsigned int* d_next;
-    int ctas, total;
+    CascadeClass* d_big;
+    unsigned int* d_next;          // two work counters: single-CTA pairs, cluster pairs
+    int ctas, total, total_big;
+    int clusters;                  // > 0: the persistent launch runs in clusters (some class needs one)
     bool wide;                     // the persistent launch's level layout
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> done;
@@ -994,9 +1000,11 @@ struct w1_mixed {
 // statistics and read-back of every persistent class, enqueued on s
 static w1_status mixed_sequence(w1_mixed* m, cudaStream_t s)
 {
-    if (m->total == 0) return W1_OK;
-    W1_CK(cudaMemsetAsync(m->d_next, 0, sizeof(unsigned int), s));
-    for (int c : m->order) {
+    if (m->total + m->total_big == 0) return W1_OK;
+    W1_CK(cudaMemsetAsync(m->d_next, 0, 2 * sizeof(unsigned int), s));
+    std::vector<int> all(m->order_big);
+    all.insert(all.end(), m->order.begin(), m->order.end());
+    for (int c : all) {
         w1_plan* p = m->plans[c];
         for (int l = p->L - 1; l > 0; --l)
             W1_CK(launch_restrict(p->lv[l].rho, p->lv[l].nx, p->lv[l].ny, p->lv[l - 1].rho, p->batch, p->ctl, s));
@@ -1006,12 +1014,17 @@ static w1_status mixed_sequence(w1_mixed* m, cudaStream_t s)
     a.n_classes = (int)m->order.size();
     a.total = m->total;
     a.next = m->d_next;
-    const w1_options& o = m->plans[m->order[0]]->opt;
+    a.big = m->d_big;
+    a.n_big = (int)m->order_big.size();
+    a.total_big = m->total_big;
+    a.next_big = m->d_next + 1;
+    const w1_options& o = m->plans[all[0]]->opt;
     a.cap = o.max_iters;
     a.K = o.check_every;
     a.budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
-    W1_CK(launch_cascade(m->norm, m->wide, a, m->ctas, s));
-    for (int c : m->order) {
+    if (m->clusters > 0) W1_CK(launch_cascade_cluster(m->norm, a, m->clusters, s));
+    else W1_CK(launch_cascade(m->norm, m->wide, a, m->ctas, s));
+    for (int c : all) {
         w1_plan* p = m->plans[c];
         const LevelPlan& f = p->lv[p->L - 1];
         W1_CK(launch_final(p->norm, f.m1[0], f.m2[0], f.phi[0], f.rho, f.nx, f.ny, f.h, p->q, p->part, p->ctl,
@@ -1037,6 +1050,7 @@ extern "C" w1_status w1_mixed_destroy(w1_mixed* m)
     if (m->graph) cudaGraphDestroy(m->graph);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     if (m->d_cls) cudaFree(m->d_cls);
+    if (m->d_big) cudaFree(m->d_big);
     if (m->d_next) cudaFree(m->d_next);
     cudaGetLastError();
     cudaSetDevice(cur);
@@ -1070,65 +1084,98 @@ extern "C" w1_status w1_mixed_create(int n_classes, const int* nx, const int* ny
         m->plans.push_back(p);
         m->count.push_back(count[c]);
         // 1: every level fits the four-nodes-per-thread layout; 2: some level needs
-        // the wide one; 0: some level fits neither (or a path is forced)
+        // the wide one; 3: some level needs a cluster of CASCADE_CLUSTER CTAs and
+        // every level fits one; 0: some level fits none of these (or a path is forced)
         int kind = (opt && (opt->path != 0 || opt->algorithm == 4)) ? 0 : 1;
         for (int l = 0; l < p->L && kind; ++l) {
             const int f = cascade_level_fits(p->lv[l].nx, p->lv[l].ny);
-            if (f == 0) kind = 0;
-            else if (!(f & 1)) kind = 2;
+            if (f == 0) kind = cascade_level_mode_cluster(p->lv[l].nx, p->lv[l].ny) ? 3 : 0;
+            else if (!(f & 1) && kind == 1) kind = 2;
         }
+        if (kind == 3)  // every level of a cluster class must have a cluster mode
+            for (int l = 0; l < p->L; ++l)
+                if (!cascade_level_mode_cluster(p->lv[l].nx, p->lv[l].ny)) kind = 0;
         m->persistent.push_back(kind);
     }
     m->wide = false;
+    bool any_big = false;
     for (int c = 0; c < n_classes; ++c) {
         if (m->persistent[c] == 2) m->wide = true;
-        m->persistent[c] = m->persistent[c] ? 1 : 0;
+        if (m->persistent[c] == 3) any_big = true;
     }
     // persistent classes, largest grid first
-    for (int c = 0; c < n_classes; ++c)
-        if (m->persistent[c]) m->order.push_back(c);
-    for (size_t a = 0; a < m->order.size(); ++a)
-        for (size_t b = a + 1; b < m->order.size(); ++b) {
-            const w1_plan* pa = m->plans[m->order[a]];
-            const w1_plan* pb = m->plans[m->order[b]];
-            if ((long long)pb->nx * pb->ny > (long long)pa->nx * pa->ny) std::swap(m->order[a], m->order[b]);
-        }
-    std::vector<CascadeClass> cls;
-    for (int c : m->order) {
-        const w1_plan* p = m->plans[c];
-        CascadeClass k{};
-        k.levels = p->L;
-        k.count = p->batch;
-        k.ctl = p->ctl;
-        for (int l = 0; l < p->L; ++l) {
-            const LevelPlan& v = p->lv[l];
-            CascadeLevel& d = k.lv[l];
-            d.nx = v.nx;
-            d.ny = v.ny;
-            d.mu = v.mu;
-            d.tau = v.tau;
-            d.ih = (float)(1.0 / v.h);
-            d.h = v.h;
-            d.tol = v.tol;
-            d.rho = v.rho;
-            d.m1 = v.m1[0];
-            d.m2 = v.m2[0];
-            d.phi = v.phi[0];
-        }
-        cls.push_back(k);
-        m->total += p->batch;
+    auto by_size = [&](std::vector<int>& ord) {
+        for (size_t a = 0; a < ord.size(); ++a)
+            for (size_t b = a + 1; b < ord.size(); ++b) {
+                const w1_plan* pa = m->plans[ord[a]];
+                const w1_plan* pb = m->plans[ord[b]];
+                if ((long long)pb->nx * pb->ny > (long long)pa->nx * pa->ny) std::swap(ord[a], ord[b]);
+            }
+    };
+    for (int c = 0; c < n_classes; ++c) {
+        if (m->persistent[c] == 3) m->order_big.push_back(c);
+        else if (m->persistent[c]) m->order.push_back(c);
+        m->persistent[c] = m->persistent[c] ? 1 : 0;
     }
-    cudaError_t e = cudaSuccess;
-    if (!cls.empty()) {
-        m->ctas = cascade_ctas(norm, m->wide);
-        if (m->ctas < 1) {
-            w1_mixed_destroy(m);
-            return fail(W1_ERR_CUDA, "the persistent launch cannot be resident");
+    by_size(m->order);
+    by_size(m->order_big);
+    auto classes_of = [&](const std::vector<int>& ord, bool big, int& total) {
+        std::vector<CascadeClass> out;
+        for (int c : ord) {
+            const w1_plan* p = m->plans[c];
+            CascadeClass k{};
+            k.levels = p->L;
+            k.count = p->batch;
+            k.ctl = p->ctl;
+            for (int l = 0; l < p->L; ++l) {
+                const LevelPlan& v = p->lv[l];
+                CascadeLevel& d = k.lv[l];
+                d.nx = v.nx;
+                d.ny = v.ny;
+                d.mode = big ? cascade_level_mode_cluster(v.nx, v.ny) : 0;
+                d.mu = v.mu;
+                d.tau = v.tau;
+                d.ih = (float)(1.0 / v.h);
+                d.h = v.h;
+                d.tol = v.tol;
+                d.rho = v.rho;
+                d.m1 = v.m1[0];
+                d.m2 = v.m2[0];
+                d.phi = v.phi[0];
+            }
+            out.push_back(k);
+            total += p->batch;
         }
-        e = cudaMalloc(&m->d_cls, sizeof(CascadeClass) * cls.size());
-        if (e == cudaSuccess)
-            e = cudaMemcpy(m->d_cls, cls.data(), sizeof(CascadeClass) * cls.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMalloc(&m->d_next, sizeof(unsigned int));
+        return out;
+    };
+    std::vector<CascadeClass> cls = classes_of(m->order, false, m->total);
+    std::vector<CascadeClass> big = classes_of(m->order_big, true, m->total_big);
+    cudaError_t e = cudaSuccess;
+    if (!cls.empty() || !big.empty()) {
+        if (any_big) {
+            m->clusters = cascade_clusters(norm);
+            if (m->clusters < 1) {
+                w1_mixed_destroy(m);
+                return fail(W1_ERR_CUDA, "the cluster persistent launch cannot be resident");
+            }
+        } else {
+            m->ctas = cascade_ctas(norm, m->wide);
+            if (m->ctas < 1) {
+                w1_mixed_destroy(m);
+                return fail(W1_ERR_CUDA, "the persistent launch cannot be resident");
+            }
+        }
+        if (!cls.empty()) {
+            e = cudaMalloc(&m->d_cls, sizeof(CascadeClass) * cls.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(m->d_cls, cls.data(), sizeof(CascadeClass) * cls.size(), cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess && !big.empty()) {
+            e = cudaMalloc(&m->d_big, sizeof(CascadeClass) * big.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(m->d_big, big.data(), sizeof(CascadeClass) * big.size(), cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&m->d_next, 2 * sizeof(unsigned int));
     }
     m->streams.assign(n_classes, nullptr);
     m->done.assign(n_classes, nullptr);
@@ -1144,7 +1191,7 @@ extern "C" w1_status w1_mixed_create(int n_classes, const int* nx, const int* ny
         w1_mixed_destroy(m);
         return fail(W1_ERR_CUDA, std::string("mixed batch set-up: ") + cudaGetErrorString(e));
     }
-    if (!cls.empty() && !m->eager) {
+    if ((!cls.empty() || !big.empty()) && !m->eager) {
         // the persistent part as one CUDA graph
         W1_CK(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeRelaxed));
         w1_status st = mixed_sequence(m, m->cap_stream);
@@ -1190,13 +1237,15 @@ extern "C" w1_status w1_mixed_solve_async(w1_mixed* m, const float* const* rho0,
         if (st != W1_OK) return st;
         W1_CK(cudaEventRecord(m->done[c], m->streams[c]));
     }
-    for (int c : m->order) {
+    std::vector<int> all(m->order_big);
+    all.insert(all.end(), m->order.begin(), m->order.end());
+    for (int c : all) {
         w1_plan* p = m->plans[c];
         W1_CK(launch_prep(rho0[c], rho1[c], (long long)p->nx * p->ny, p->batch, p->batch, p->h, p->ctl, p->part,
                           p->lv[p->L - 1].rho, s));
         p->last_batch = p->batch;
     }
-    if (!m->order.empty()) {
+    if (!all.empty()) {
         if (m->eager) {
             w1_status st = mixed_sequence(m, s);
             if (st != W1_OK) return st;

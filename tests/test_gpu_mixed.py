@@ -1,7 +1,9 @@
 """Mixed-size batches: classes whose levels fit one CTA run in one persistent
-launch (every level of a pair on one CTA), the others as batched plans beside
-it.  Each pair is checked against the FP64 oracle replaying its step counts
-(W1 relative 1e-4, as the other full solves)."""
+launch (every level of a pair on one CTA); when a class has a level that needs
+a cluster of four CTAs, that launch runs in clusters (those pairs on a whole
+cluster, the others on one CTA each); classes that fit neither run as batched
+plans beside it.  Each pair is checked against the FP64 oracle replaying its
+step counts (W1 relative 1e-4, as the other full solves)."""
 import numpy as np
 import pytest
 
@@ -44,9 +46,12 @@ def solve(w1, classes, norm, **opt):
 
 @pytest.mark.parametrize("norm", [1, 2, 3])
 def test_mixed_batch_matches_the_oracle(w1, norm):
-    classes = [(64, 64, 5), (128, 128, 3), (32, 32, 4), (256, 256, 1)]
+    """The 256^2 class makes the persistent launch a cluster launch: its pairs
+    run on four-CTA clusters (128^2 and 256^2 levels split in row bands), the
+    other classes one pair per CTA in the same launch."""
+    classes = [(64, 64, 5), (128, 128, 3), (32, 32, 4), (256, 256, 2)]
     out, pers, host = solve(w1, classes, norm)
-    assert pers == [True, True, True, False]
+    assert pers == [True, True, True, True]
     for ci, (vals, sts, statuses, _) in enumerate(out):
         a0, a1 = host[ci]
         for k, (v, st) in enumerate(zip(vals, sts)):
@@ -55,6 +60,38 @@ def test_mixed_batch_matches_the_oracle(w1, norm):
                                     replay=st.iters)
             assert abs(v - ref.w1) <= 1e-4 * abs(ref.w1), (ci, k, v, ref.w1)
             assert st.lb <= st.ub
+
+
+def test_cluster_launch_without_single_cta_classes(w1):
+    """Only cluster classes (256^2 and a 128 x 512 grid whose 512-wide levels
+    split in four row bands): the launch's second phase finds no work."""
+    classes = [(256, 256, 3), (512, 128, 1)]
+    out, pers, host = solve(w1, classes, 1)
+    assert pers == [True, True]
+    for ci, (vals, sts, statuses, _) in enumerate(out):
+        a0, a1 = host[ci]
+        for k, (v, st) in enumerate(zip(vals, sts)):
+            assert statuses[k] == w1.OK and st.converged
+            ref = oracle.multilevel(a0[k].astype(np.float64), a1[k].astype(np.float64), levels=st.levels, norm=1,
+                                    replay=st.iters)
+            assert abs(v - ref.w1) <= 1e-4 * abs(ref.w1), (ci, k, v, ref.w1)
+
+
+def test_cluster_launch_rejects_a_bad_pair_alone(w1):
+    """A rejected pair of a cluster class is skipped by its cluster; the others
+    (cluster and single-CTA classes) are unaffected."""
+    classes = [(256, 256, 3), (64, 64, 2)]
+    r0, r1, host = make(classes, seed0=91)
+    r1[0][1] *= 1.5
+    with w1.Mixed(classes, norm=2) as mx:
+        mx.solve_async(r0, r1)
+        torch.cuda.synchronize()
+        assert [mx.persistent(c) for c in range(2)] == [True, True]
+        vals, sts, statuses, _ = mx.results(0)
+        assert statuses == [w1.OK, w1.ERR_MASS, w1.OK]
+        assert np.isnan(vals[1]) and np.isfinite(vals[0]) and np.isfinite(vals[2])
+        _, _, st1, _ = mx.results(1)
+        assert st1 == [w1.OK, w1.OK]
 
 
 def test_persistent_launch_equals_the_batched_plan_with_the_same_kernels(w1):
