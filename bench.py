@@ -843,6 +843,8 @@ def main():
     ap.add_argument("--pairs3", type=int, default=8, help="--only solve3d: pairs per norm")
     ap.add_argument("--roof-n3", type=int, default=256, help="--only solve3d: grid side of the step-kernel timing")
     ap.add_argument("--mixed-norm", type=int, default=2, help="mixed-size batch: ground norm")
+    ap.add_argument("--mixed-schedule", type=int, default=1, choices=[0, 1],
+                    help="mixed-size batch: level tolerances (1 the calibrated schedule, 0 the paper's)")
     ap.add_argument("--mixed-modes", default="loop,lanes,lockstep,lockstep-tuned,persistent")
     ap.add_argument("--mixed-spec", default="", help="mixed-size batch override, e.g. 64:128,128:96")
     ap.add_argument("--mixed-passes", type=int, default=2, help="default line: timed passes of the mixed batch")
@@ -905,17 +907,18 @@ def run_mixed(args):
     modes = [m for m in args.mixed_modes.split(",") if m]
     out = {}
     w1_ref = None
+    sch = args.mixed_schedule
     for mode in modes:
         if mode == "loop":
-            plans = [w1.Plan(n, n, levels=L, norm=norm) for n, _, L in MIXED]
+            plans = [w1.Plan(n, n, levels=L, norm=norm, schedule=sch) for n, _, L in MIXED]
         elif mode == "lanes":
-            plans = [[w1.Plan(n, n, levels=L, norm=norm) for _ in range(B)] for n, B, L in MIXED]
+            plans = [[w1.Plan(n, n, levels=L, norm=norm, schedule=sch) for _ in range(B)] for n, B, L in MIXED]
             lanes = [[torch.cuda.Stream() for _ in range(B)] for _, B, _ in MIXED]
         elif mode == "persistent":
-            plans = w1.Mixed([(n, n, B) for n, B, _ in MIXED], norm=norm)
+            plans = w1.Mixed([(n, n, B) for n, B, _ in MIXED], norm=norm, schedule=sch)
         else:
             tune = 2 if mode == "lockstep-tuned" else 0
-            plans = [w1.Plan(n, n, levels=L, norm=norm, batch=B, tune=tune) for n, B, L in MIXED]
+            plans = [w1.Plan(n, n, levels=L, norm=norm, batch=B, tune=tune, schedule=sch) for n, B, L in MIXED]
             lanes = [torch.cuda.Stream() for _ in MIXED]
 
         def one_pass(s):
@@ -1276,8 +1279,8 @@ def serve_summary(w1, torch, args):
 
 def mixed_summary(w1, torch, args):
     """The mixed-size batch (128 x 64^2 + 96 x 128^2 + 32 x 256^2, Gaussian
-    mixtures, p = 2) per pass: one persistent launch (with the classes that do
-    not fit one CTA beside it), per-size batched plans, and a loop of single
+    mixtures, p = 2, the calibrated schedule unless --mixed-schedule 0) per
+    pass: one persistent launch, per-size batched plans, and a loop of single
     solves; CUDA events on the launching stream, L2 flushed before each pass."""
     import synth
     stream = torch.cuda.current_stream()
@@ -1295,14 +1298,15 @@ def mixed_summary(w1, torch, args):
     every = (w1.OK, w1.ERR_NOT_CONVERGED, w1.ERR_TIMEOUT, w1.ERR_MASS)
     total = sum(B for _, B, _ in MIXED)
     out, first = {}, None
+    sch = args.mixed_schedule
     for mode in ("persistent", "lockstep", "loop"):
         if mode == "persistent":
-            obj = w1.Mixed([(n, n, B) for n, B, _ in MIXED], norm=norm)
+            obj = w1.Mixed([(n, n, B) for n, B, _ in MIXED], norm=norm, schedule=sch)
         elif mode == "lockstep":
-            obj = [w1.Plan(n, n, levels=L, norm=norm, batch=B) for n, B, L in MIXED]
+            obj = [w1.Plan(n, n, levels=L, norm=norm, batch=B, schedule=sch) for n, B, L in MIXED]
             lanes = [torch.cuda.Stream() for _ in MIXED]
         else:
-            obj = [w1.Plan(n, n, levels=L, norm=norm) for n, _, L in MIXED]
+            obj = [w1.Plan(n, n, levels=L, norm=norm, schedule=sch) for n, _, L in MIXED]
 
         def one_pass(s):
             flush.fill_(float(s))
@@ -1355,6 +1359,7 @@ def mixed_summary(w1, torch, args):
             for p in obj:
                 p.close()
     return {"workload": ", ".join(f"{B} x {n}^2 ({L} levels)" for n, B, L in MIXED), "norm": f"L{norm}",
+            "schedule": "calibrated (w1_options.schedule = 1)" if sch else "the paper's (eq. stop_tol, alpha -1)",
             "pairs_per_pass": total, "passes": passes - 1, "modes": out,
             "speedup_vs_loop": out["persistent"]["solves_per_s"] / out["loop"]["solves_per_s"]}
 
