@@ -976,6 +976,7 @@ def run_mixed(args):
                      "max_rel_diff_vs_first_mode": float(np.max(np.abs(flat - w1_ref) / np.abs(w1_ref)))}
         if mode == "persistent":
             out[mode]["persistent_classes"] = [plans.persistent(c) for c in range(len(MIXED))]
+            out[mode]["launch"] = plans.launch_info()
             plans.close()
         del plans
         torch.cuda.synchronize()
@@ -1354,6 +1355,7 @@ def mixed_summary(w1, torch, args):
                      "max_rel_diff_vs_persistent": float(np.max(np.abs(vals - first) / np.abs(first)))}
         if mode == "persistent":
             out[mode]["persistent_classes"] = [obj.persistent(c) for c in range(len(MIXED))]
+            out[mode]["launch"] = obj.launch_info()
             obj.close()
         else:
             for p in obj:

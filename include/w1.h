@@ -257,8 +257,14 @@ typedef struct w1_mixed w1_mixed;
  * w1_plan_create with levels = 0, h = 0).  Classes whose every level fits one
  * CTA (nx % 4 == 0 at every level, at most 16384 nodes) run in ONE persistent
  * launch: each CTA takes a pair, runs all of its levels (interpolation and the
- * level solves) on chip, and takes the next pair, largest grids first.  Other
- * classes run as batched plans on streams of their own, overlapping the
+ * level solves) on chip, and takes the next pair, largest grids first.  When a
+ * class has a level larger than one CTA holds that four CTAs hold in row bands
+ * (each at most 16384 nodes, nx <= 4096), the persistent launch runs in clusters
+ * of four CTAs: clusters take those pairs first (their larger levels split over
+ * the cluster), then every CTA takes pairs of the other classes alone.  The
+ * levels of at most 1024 nodes of every pair run before, in a coarse launch of
+ * 256-thread CTAs (several to an SM), one pair per CTA.  Classes that fit
+ * neither run as batched plans on streams of their own, overlapping the
  * persistent launch.  opt->path != 0 sends every class to the batched plans.
  * The batch owns its device memory (one arena per class).
  */
@@ -267,6 +273,11 @@ w1_status w1_mixed_create(int n_classes, const int* nx, const int* ny, const int
 w1_status w1_mixed_destroy(w1_mixed* batch);
 /* 1 if class cls runs in the persistent launch, 0 if as a batched plan, -1 on bad arguments. */
 int w1_mixed_persistent(const w1_mixed* batch, int cls);
+/* The persistent launches' sizes (0 where a launch is not used): CTAs of the
+ * single-CTA persistent launch (beside the cluster launch, on the SMs no whole
+ * cluster uses, when there is one), clusters of the cluster launch, CTAs of the
+ * coarse launch.  Any output may be NULL. */
+w1_status w1_mixed_launch_info(const w1_mixed* batch, int* ctas, int* clusters, int* coarse_ctas);
 /*
  * Enqueues a solve of every pair on `stream` and returns without waiting.
  * rho0[c], rho1[c]: device [count[c]][ny[c]][nx[c]] float32 (host arrays of

@@ -160,6 +160,9 @@ struct CascadeLevel {
 };
 struct CascadeClass {
     int levels, count;
+    // levels 0 .. split - 1 (at most CASCADE_COARSE_NODES nodes each) run in the
+    // coarse launch, levels split .. levels - 1 in the persistent launch
+    int split;
     Ctl* ctl;  // per-pair control blocks of the class
     CascadeLevel lv[W1_MAX_LEVELS];
 };
@@ -179,6 +182,10 @@ struct CascadeArgs {
     unsigned int* next_big;
 };
 static constexpr int CASCADE_CLUSTER = 4;
+// Levels of at most this many nodes run in the coarse launch (CTAs of
+// CASCADE_COARSE_THREADS threads, several per SM) before the persistent launch.
+static constexpr int CASCADE_COARSE_NODES = 1024;
+static constexpr int CASCADE_COARSE_THREADS = 256;
 enum { CASCADE_SPLIT4 = 1, CASCADE_SPLITW = 2, CASCADE_ONE4 = 3, CASCADE_ONEW = 4 };
 // Which single-CTA layouts hold an nx x ny level (nx % 4 == 0): bit 0 four
 // nodes per thread (at most 4096 nodes), bit 1 wide (at most 16384 nodes, a
@@ -196,6 +203,11 @@ int cascade_clusters(int norm);
 // The persistent launch with clusters of CASCADE_CLUSTER CTAs: each cluster
 // takes pairs of a.big together, then each of its CTAs pairs of a.cls alone.
 cudaError_t launch_cascade_cluster(int norm, const CascadeArgs& a, int clusters, cudaStream_t s);
+// The coarse launch: pairs of a.cls (every persistent class), levels 0 ..
+// split - 1, one pair per CTA of CASCADE_COARSE_THREADS threads; CTAs resident
+// at once from cascade_coarse_ctas.
+int cascade_coarse_ctas(int norm);
+cudaError_t launch_cascade_coarse(int norm, const CascadeArgs& a, int ctas, cudaStream_t s);
 // Prox-PDHG (Algorithm 2 on one level; Algorithm 4 through the plan).  Every
 // plane holds the batch's pairs back to back (pair stride nx * ny).
 struct PdArgs {

@@ -1857,7 +1857,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cascade(CascadeArgs a)
             }
             *vc = c;
             *vb = b;
-            *vl = 0;
+            *vl = w >= a.total ? 0 : a.cls[c].split;  // the coarse launch did the levels before
             // 0: no work left; 1: solve; 2: skip (rejected input or unused slot)
             *vgo = w >= a.total ? 0 : (a.cls[c].ctl[b].error ? 2 : 1);
         }
@@ -2037,7 +2037,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cascade_cl(CascadeArgs a)
         }
         const CascadeClass* K = a.big + c;
         if (K->ctl[b].error) continue;  // set before the launch: the same in every CTA
-        for (int l = 0; l < K->levels; ++l) {
+        for (int l = K->split; l < K->levels; ++l) {  // the coarse launch did the levels before
             const CascadeLevel& v = K->lv[l];
             const int rows = v.ny / CASCADE_CLUSTER, rest = v.ny - rows * CASCADE_CLUSTER;
             // row bands (the last one takes the rows a split leaves over)
@@ -2065,7 +2065,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cascade_cl(CascadeArgs a)
             }
             *vc = c;
             *vb = b;
-            *vl = 0;
+            *vl = w >= a.total ? 0 : a.cls[c].split;
             *vgo = w >= a.total ? 0 : (a.cls[c].ctl[b].error ? 2 : 1);
         }
         __syncthreads();
@@ -2142,6 +2142,81 @@ cudaError_t launch_cascade_cluster(int norm, const CascadeArgs& a, int clusters,
     return cudaLaunchKernelExC(&cfg, cascade_cl_fn(norm), args);
 }
 
+// The coarse levels of every pair of a persistent launch (at most
+// CASCADE_COARSE_NODES nodes each: 16^2 and 32^2 for the usual cascades).  The
+// persistent CTA has 1024 threads and the whole SM; a 16^2 level keeps 64 of
+// them busy for thousands of steps.  Here a CTA of CASCADE_COARSE_THREADS takes
+// a pair and runs its coarse levels, several CTAs to an SM; the persistent
+// launch that follows continues every pair from its first larger level.
+template <int NORM>
+__global__ void __launch_bounds__(CASCADE_COARSE_THREADS, 3) k_cascade_coarse(CascadeArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int s_c, s_b, s_go;
+    __shared__ ResArgs s_args;
+    volatile int* vc = &s_c;
+    volatile int* vb = &s_b;
+    volatile int* vgo = &s_go;
+    for (;;) {
+        __syncthreads();  // the previous pair is finished before the shared fields change
+        if (threadIdx.x == 0) {
+            const int w = (int)atomicAdd(a.next, 1u);
+            int c = 0, b = w;
+            while (c < a.n_classes - 1 && b >= a.cls[c].count) {
+                b -= a.cls[c].count;
+                ++c;
+            }
+            *vc = c;
+            *vb = b;
+            *vgo = w >= a.total ? 0 : (a.cls[c].ctl[b].error ? 2 : 1);
+        }
+        __syncthreads();
+        const int go = *vgo;
+        if (go == 0) return;
+        if (go == 2) continue;
+        const CascadeClass* K = a.cls + *vc;
+        const int b = *vb;
+        for (int l = 0; l < K->split; ++l) {
+            const CascadeLevel& v = K->lv[l];
+            cascade_init(K, l, b, 0, v.nx * v.ny);
+            if (threadIdx.x == 0) cascade_args(s_args, a, K, l);
+            __syncthreads();  // the level's state is in global memory for the level solve to load
+            res4_level<NORM, false>(s_args, b, 1, 0, smraw);
+            __syncthreads();  // the level's final state is stored before the next level reads it
+        }
+    }
+}
+
+static size_t cascade_coarse_smem() { return resident_smem(CASCADE_COARSE_NODES); }
+
+static const void* cascade_coarse_fn(int norm)
+{
+    return norm == W1_NORM_L1 ? (const void*)k_cascade_coarse<W1_NORM_L1>
+           : norm == W1_NORM_L2 ? (const void*)k_cascade_coarse<W1_NORM_L2>
+                                : (const void*)k_cascade_coarse<W1_NORM_LINF>;
+}
+
+int cascade_coarse_ctas(int norm)
+{
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, cascade_coarse_fn(norm), CASCADE_COARSE_THREADS,
+                                                      cascade_coarse_smem()) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms * per;
+}
+
+cudaError_t launch_cascade_coarse(int norm, const CascadeArgs& a, int ctas, cudaStream_t s)
+{
+    if (ctas < 1 || a.total < 1) return cudaErrorInvalidValue;
+    const int grid = ctas < a.total ? ctas : a.total;
+    void* args[1] = {(void*)&a};
+    return cudaLaunchKernel(cascade_coarse_fn(norm), dim3(grid), dim3(CASCADE_COARSE_THREADS), args,
+                            cascade_coarse_smem(), s);
+}
+
 template <int NORM>
 static cudaError_t cascade_attr()
 {
@@ -2151,8 +2226,10 @@ static cudaError_t cascade_attr()
     e = cudaFuncSetAttribute(k_cascade<NORM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)cascade_smem(true));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_cascade_cl<NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)cascade_smem(true));
+    e = cudaFuncSetAttribute(k_cascade_cl<NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cascade_smem(true));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_cascade_coarse<NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)cascade_coarse_smem());
 }
 
 static const void* cascade_fn(int norm, bool wide)

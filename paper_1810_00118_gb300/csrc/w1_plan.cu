@@ -983,8 +983,14 @@ struct w1_mixed {
     std::vector<int> order_big;    // persistent cluster classes, largest grid first
     CascadeClass* d_cls;
     CascadeClass* d_big;
-    unsigned int* d_next;          // two work counters: single-CTA pairs, cluster pairs
+    CascadeClass* d_all;           // every persistent class, for the coarse launch
+    unsigned int* d_next;          // work counters: single-CTA pairs, cluster pairs, coarse launch
     int ctas, total, total_big;
+    int coarse_ctas;               // > 0: the coarse launch runs first
+    int side_ctas;                 // > 0: single-CTA persistent CTAs beside the cluster launch
+    bool fine_work;                // some class has a level beyond the coarse launch
+    cudaStream_t side;             // their stream (forked from the solve's stream and joined back)
+    cudaEvent_t fork, join;
     int clusters;                  // > 0: the persistent launch runs in clusters (some class needs one)
     bool wide;                     // the persistent launch's level layout
     std::vector<cudaStream_t> streams;
@@ -1001,7 +1007,7 @@ struct w1_mixed {
 static w1_status mixed_sequence(w1_mixed* m, cudaStream_t s)
 {
     if (m->total + m->total_big == 0) return W1_OK;
-    W1_CK(cudaMemsetAsync(m->d_next, 0, 2 * sizeof(unsigned int), s));
+    W1_CK(cudaMemsetAsync(m->d_next, 0, 3 * sizeof(unsigned int), s));
     std::vector<int> all(m->order_big);
     all.insert(all.end(), m->order.begin(), m->order.end());
     for (int c : all) {
@@ -1022,8 +1028,38 @@ static w1_status mixed_sequence(w1_mixed* m, cudaStream_t s)
     a.cap = o.max_iters;
     a.K = o.check_every;
     a.budget_ns = (unsigned long long)(o.time_budget_s * 1e9);
-    if (m->clusters > 0) W1_CK(launch_cascade_cluster(m->norm, a, m->clusters, s));
-    else W1_CK(launch_cascade(m->norm, m->wide, a, m->ctas, s));
+    if (m->coarse_ctas > 0) {
+        CascadeArgs c = a;
+        c.cls = m->d_all;
+        c.n_classes = (int)all.size();
+        c.total = m->total + m->total_big;
+        c.next = m->d_next + 2;
+        c.big = nullptr;
+        c.n_big = 0;
+        c.total_big = 0;
+        c.next_big = nullptr;
+        W1_CK(launch_cascade_coarse(m->norm, c, m->coarse_ctas, s));
+    }
+    if (m->fine_work) {
+        if (m->clusters > 0) {
+            // SMs that no whole cluster can use run single-CTA persistent CTAs,
+            // which draw single-CTA pairs from the same counter as the clusters'
+            // second phase
+            const bool side = m->side_ctas > 0 && a.total > 0;
+            if (side) {
+                W1_CK(cudaEventRecord(m->fork, s));
+                W1_CK(cudaStreamWaitEvent(m->side, m->fork, 0));
+            }
+            W1_CK(launch_cascade_cluster(m->norm, a, m->clusters, s));
+            if (side) {
+                W1_CK(launch_cascade(m->norm, m->wide, a, m->side_ctas, m->side));
+                W1_CK(cudaEventRecord(m->join, m->side));
+                W1_CK(cudaStreamWaitEvent(s, m->join, 0));
+            }
+        } else {
+            W1_CK(launch_cascade(m->norm, m->wide, a, m->ctas, s));
+        }
+    }
     for (int c : all) {
         w1_plan* p = m->plans[c];
         const LevelPlan& f = p->lv[p->L - 1];
@@ -1049,8 +1085,12 @@ extern "C" w1_status w1_mixed_destroy(w1_mixed* m)
     if (m->exec) cudaGraphExecDestroy(m->exec);
     if (m->graph) cudaGraphDestroy(m->graph);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    if (m->side) cudaStreamDestroy(m->side);
+    if (m->fork) cudaEventDestroy(m->fork);
+    if (m->join) cudaEventDestroy(m->join);
     if (m->d_cls) cudaFree(m->d_cls);
     if (m->d_big) cudaFree(m->d_big);
+    if (m->d_all) cudaFree(m->d_all);
     if (m->d_next) cudaFree(m->d_next);
     cudaGetLastError();
     cudaSetDevice(cur);
@@ -1127,6 +1167,10 @@ extern "C" w1_status w1_mixed_create(int n_classes, const int* nx, const int* ny
             k.levels = p->L;
             k.count = p->batch;
             k.ctl = p->ctl;
+            k.split = 0;
+            while (k.split < p->L && (long long)p->lv[k.split].nx * p->lv[k.split].ny <= CASCADE_COARSE_NODES &&
+                   p->lv[k.split].nx % 4 == 0)
+                ++k.split;
             for (int l = 0; l < p->L; ++l) {
                 const LevelPlan& v = p->lv[l];
                 CascadeLevel& d = k.lv[l];
@@ -1150,6 +1194,13 @@ extern "C" w1_status w1_mixed_create(int n_classes, const int* nx, const int* ny
     };
     std::vector<CascadeClass> cls = classes_of(m->order, false, m->total);
     std::vector<CascadeClass> big = classes_of(m->order_big, true, m->total_big);
+    std::vector<CascadeClass> allc(big);
+    allc.insert(allc.end(), cls.begin(), cls.end());
+    bool any_coarse = false;
+    for (const CascadeClass& k : allc) {
+        if (k.split > 0) any_coarse = true;
+        if (k.split < k.levels) m->fine_work = true;
+    }
     cudaError_t e = cudaSuccess;
     if (!cls.empty() || !big.empty()) {
         if (any_big) {
@@ -1157,6 +1208,24 @@ extern "C" w1_status w1_mixed_create(int n_classes, const int* nx, const int* ny
             if (m->clusters < 1) {
                 w1_mixed_destroy(m);
                 return fail(W1_ERR_CUDA, "the cluster persistent launch cannot be resident");
+            }
+            int dev = 0, sms = 0;
+            if (!cls.empty() && cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
+                const int left = sms - CASCADE_CLUSTER * m->clusters;
+                const int fit = cascade_ctas(norm, m->wide);
+                m->side_ctas = left > 0 ? std::min(left, fit) : 0;
+            }
+            cudaGetLastError();
+            if (m->side_ctas > 0) {
+                e = cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->join, cudaEventDisableTiming);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    w1_mixed_destroy(m);
+                    return fail(W1_ERR_CUDA, std::string("side stream: ") + cudaGetErrorString(e));
+                }
             }
         } else {
             m->ctas = cascade_ctas(norm, m->wide);
@@ -1175,7 +1244,17 @@ extern "C" w1_status w1_mixed_create(int n_classes, const int* nx, const int* ny
             if (e == cudaSuccess)
                 e = cudaMemcpy(m->d_big, big.data(), sizeof(CascadeClass) * big.size(), cudaMemcpyHostToDevice);
         }
-        if (e == cudaSuccess) e = cudaMalloc(&m->d_next, 2 * sizeof(unsigned int));
+        if (e == cudaSuccess && any_coarse) {
+            m->coarse_ctas = cascade_coarse_ctas(norm);
+            if (m->coarse_ctas < 1) {
+                w1_mixed_destroy(m);
+                return fail(W1_ERR_CUDA, "the coarse launch cannot be resident");
+            }
+            e = cudaMalloc(&m->d_all, sizeof(CascadeClass) * allc.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(m->d_all, allc.data(), sizeof(CascadeClass) * allc.size(), cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&m->d_next, 3 * sizeof(unsigned int));
     }
     m->streams.assign(n_classes, nullptr);
     m->done.assign(n_classes, nullptr);
@@ -1212,6 +1291,15 @@ extern "C" w1_status w1_mixed_create(int n_classes, const int* nx, const int* ny
         }
     }
     *out = m;
+    return W1_OK;
+}
+
+extern "C" w1_status w1_mixed_launch_info(const w1_mixed* m, int* ctas, int* clusters, int* coarse_ctas)
+{
+    if (!m) return fail(W1_ERR_INVALID_ARG, "NULL batch");
+    if (ctas) *ctas = m->clusters > 0 ? m->side_ctas : m->ctas;
+    if (clusters) *clusters = m->clusters;
+    if (coarse_ctas) *coarse_ctas = m->coarse_ctas;
     return W1_OK;
 }
 

@@ -143,6 +143,7 @@ def _load() -> ctypes.CDLL:
         "w1_mixed_create": (st, [I, P, P, P, I, D, ctypes.POINTER(Options), ctypes.POINTER(P)]),
         "w1_mixed_destroy": (st, [P]),
         "w1_mixed_persistent": (I, [P, I]),
+        "w1_mixed_launch_info": (st, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "w1_mixed_solve_async": (st, [P, P, P, P]),
         "w1_mixed_results": (st, [P, I, P, P, P]),
         "w1_restrict": (st, [I, I, P, P, P]),
@@ -376,6 +377,13 @@ class Mixed:
 
     def persistent(self, cls) -> bool:
         return _lib.w1_mixed_persistent(self._p, cls) == 1
+
+    def launch_info(self) -> dict:
+        """CTAs of the single-CTA persistent launch, clusters of the cluster
+        launch and CTAs of the coarse launch (0 where unused)."""
+        a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(_lib.w1_mixed_launch_info(self._p, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"ctas": a.value, "clusters": b.value, "coarse_ctas": c.value}
 
     def solve_async(self, rho0, rho1, stream=None):
         """rho0, rho1: lists (one per class) of device tensors [count, ny, nx]."""
