@@ -41,10 +41,17 @@ namespace w1 {
 
 static constexpr int PREP_THREADS = 256;
 
-// A fixed number of blocks per pair, whatever the batch size, so that every
-// pair's sums run in the same order alone and inside a batch (bitwise equal results).
+// Blocks per pair from the grid alone, whatever the batch size, so that every
+// pair's sums run in the same order alone and inside a batch (bitwise equal
+// results): one per 2048 nodes, at most PREP_BLOCKS_PER_PAIR.  Each block ends
+// with a block-wide FP64 sum, so small grids take few blocks.
 static constexpr int PREP_BLOCKS_PER_PAIR = 64;
 static int prep_blocks_per_pair(int) { return PREP_BLOCKS_PER_PAIR; }
+static int prep_blocks(long long n)
+{
+    const long long b = (n + 2047) / 2048;
+    return (int)(b < 1 ? 1 : b > PREP_BLOCKS_PER_PAIR ? PREP_BLOCKS_PER_PAIR : b);
+}
 
 // per block: compensated sums (s, c) of r0, r1 and r0 - r1, then the non-finite count
 static constexpr int PREP_PART_PER_BLOCK = 7;
@@ -134,7 +141,7 @@ __global__ void k_prep_apply(const float* __restrict__ r0, const float* __restri
 cudaError_t launch_prep(const float* r0, const float* r1, long long n, int nbatch, int pairs, double h, Ctl* ctl,
                         double* part, float* rho, cudaStream_t s)
 {
-    const int bpp = prep_blocks_per_pair(pairs);
+    const int bpp = prep_blocks(n);
     k_prep_reduce<<<dim3(bpp, pairs), PREP_THREADS, 0, s>>>(r0, r1, n, nbatch, h, ctl, part);
     k_prep_apply<<<dim3(2 * bpp, pairs), 256, 0, s>>>(r0, r1, n, nbatch, ctl, rho);
     return cudaGetLastError();
@@ -2476,8 +2483,8 @@ cudaError_t launch_resident(int norm, int cluster, const ResArgs& a, cudaStream_
 
 static constexpr int FIN_THREADS = 256;
 
-// FIN_BLOCKS_PER_PAIR blocks per pair whatever the batch (same reason as the
-// prep blocks); each leaves FIN_PART_PER_BLOCK doubles (w1_internal.h).
+// At most FIN_BLOCKS_PER_PAIR blocks per pair, from the grid alone (same reason
+// as the prep blocks); each leaves FIN_PART_PER_BLOCK doubles (w1_internal.h).
 static int final_blocks_per_pair(int) { return FIN_BLOCKS_PER_PAIR; }
 
 size_t final_part_doubles(int pairs) { return (size_t)final_blocks_per_pair(pairs) * pairs * FIN_PART_PER_BLOCK; }
@@ -2745,7 +2752,12 @@ __global__ void __launch_bounds__(FIN_THREADS) k_final_b(int nx, int ny, double 
 cudaError_t launch_final(int norm, const float* m1, const float* m2, const float* phi, const float* rho, int nx,
                          int ny, double h, double* q, double* part, Ctl* ctl, int pairs, cudaStream_t s)
 {
-    const int bpp = final_blocks_per_pair(pairs);
+    // one block per 32 x 32 tile, or per 1024 cells (nodes, or 2 x 2 blocks of
+    // nodes), at most FIN_BLOCKS_PER_PAIR: each block ends with a block-wide FP64 sum
+    const int pool = final_pool(nx, ny);
+    const long long units = pool == FIN_TILE ? (long long)(nx / FIN_TILE) * (ny / FIN_TILE)
+                                             : ((long long)nx * ny / (pool * pool) + 1023) / 1024;
+    const int bpp = (int)(units < 1 ? 1 : units > FIN_BLOCKS_PER_PAIR ? FIN_BLOCKS_PER_PAIR : units);
     dim3 g(bpp, pairs);
     if (norm == W1_NORM_L1)
         k_final_a<W1_NORM_L1><<<g, FIN_THREADS, 0, s>>>(m1, m2, phi, rho, nx, ny, h, q, part, ctl);
