@@ -232,12 +232,15 @@ w1_status w1_solve_async(w1_plan* plan, int batch, const float* rho0, const floa
 w1_status w1_plan_results(w1_plan* plan, double* dist, w1_stats* stats, int* status);
 
 /* w1_solve_batch for host (pageable or pinned) densities and flux; the copies
- * to and from the device are part of the call. */
+ * to and from the device are part of the call.  The call waits for its solve
+ * asleep (an event with blocking synchronisation) rather than spinning, so that
+ * many host threads calling it at once do not take each other's cores. */
 w1_status w1_solve_batch_host(w1_plan* plan, int batch, const float* rho0, const float* rho1, void* stream,
                               double* dist, float* flux, w1_stats* stats, int* status);
 
 /* Same as w1_solve, for densities and flux in (pageable or pinned) host
- * memory: the copies to and from the device are part of the call. */
+ * memory: the copies to and from the device are part of the call (and the
+ * wait is asleep, as w1_solve_batch_host's). */
 w1_status w1_solve_host(w1_plan* plan, const float* rho0, const float* rho1, void* stream, double* dist,
                         float* flux, w1_stats* stats);
 

@@ -133,6 +133,7 @@ struct w1_plan {
     float* in0;
     float* in1;
     float* flux_d;
+    cudaEvent_t host_done;  // host-buffer solves wait on it asleep (blocking sync)
     int last_batch;
     const float2* tw;  // prox-PDHG twiddle table (per device)
 };
@@ -487,6 +488,7 @@ extern "C" w1_status w1_plan_destroy(w1_plan* p)
     if (p->in0) cudaFree(p->in0);
     if (p->in1) cudaFree(p->in1);
     if (p->flux_d) cudaFree(p->flux_d);
+    if (p->host_done) cudaEventDestroy(p->host_done);
     cudaGetLastError();
     cudaSetDevice(cur);
     delete p;
@@ -932,9 +934,18 @@ extern "C" w1_status w1_solve_batch_host(w1_plan* p, int nbatch, const float* rh
     if (!p->in1) W1_CK(cudaMalloc(&p->in1, bytes));
     if (flux && !p->flux_d) W1_CK(cudaMalloc(&p->flux_d, 2 * bytes));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // Host-buffer calls are the ones a service issues from many host threads at
+    // once; a thread that spins in the driver until its solve ends takes a core
+    // from the threads that still submit work, so this call waits asleep.
+    if (!p->host_done) W1_CK(cudaEventCreateWithFlags(&p->host_done, cudaEventBlockingSync | cudaEventDisableTiming));
     W1_CK(cudaMemcpyAsync(p->in0, rho0, n * sizeof(float) * nbatch, cudaMemcpyHostToDevice, s));
     W1_CK(cudaMemcpyAsync(p->in1, rho1, n * sizeof(float) * nbatch, cudaMemcpyHostToDevice, s));
-    w1_status st = solve_device(p, nbatch, p->in0, p->in1, s, dist, flux ? p->flux_d : nullptr, stats, status);
+    w1_status st = enqueue(p, nbatch, p->in0, p->in1, s, flux ? p->flux_d : nullptr);
+    if (st == W1_OK) {
+        W1_CK(cudaEventRecord(p->host_done, s));
+        W1_CK(cudaEventSynchronize(p->host_done));
+        st = results(p, dist, stats, status);
+    }
     if (flux && st != W1_ERR_CUDA && st != W1_ERR_NOMEM && st != W1_ERR_INVALID_ARG) {
         W1_CK(cudaMemcpyAsync(flux, p->flux_d, 2 * n * sizeof(float) * nbatch, cudaMemcpyDeviceToHost, s));
         W1_CK(cudaStreamSynchronize(s));
