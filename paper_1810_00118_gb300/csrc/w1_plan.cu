@@ -165,7 +165,7 @@ int fault_halo_rank()
 struct CalibratedSchedule {
     double tol_scale, alpha, theta, step_ratio;
 };
-static constexpr CalibratedSchedule kCalibrated[2] = {{30.0, 0.5, 1.0, 1.0}, {2.0, -1.0, 1.0, 0.02}};
+static constexpr CalibratedSchedule kCalibrated[2] = {{30.0, 0.5, 1.0, 1.0}, {3.0, -1.0, 1.0, 0.02}};
 
 extern "C" w1_status w1_calibrated_schedule(int norm, double* tol_scale, double* alpha, double* theta,
                                             double* step_ratio)
