@@ -178,8 +178,8 @@ w1_status w1_plan_create_ex(int nx, int ny, double h, int levels, int norm, doub
 w1_status w1_plan_destroy(w1_plan* plan);
 
 /*
- * A plan for batches of up to max_batch pairs of the same grid (north-star
- * batching; every kernel launch advances all pairs of the batch).  Arguments
+ * A plan for batches of up to max_batch pairs of the same grid (every kernel
+ * launch advances all pairs of the batch).  Arguments
  * as w1_plan_create_ex.  Device memory grows linearly with max_batch.
  */
 w1_status w1_plan_create_batch(int nx, int ny, double h, int levels, int norm, double tol, int max_batch,
