@@ -693,10 +693,11 @@ def run_gpu(args):
 
 
 # ncu DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum), from
-# the captures summarised under profiles/; None where no capture of the current
-# kernel exists.  Streaming kernels: captured at 4096^2 and scaled by 4 to 8192^2
-# (their traffic grows with the number of nodes).
-TRAFFIC = {"k_step": 4 * 444.46e6, "k_tblock": 4 * 432.7e6, "k_resident4": 1105408.0}
+# the captures summarised under profiles/ (taken with the current kernels); None
+# where no capture of the current kernel exists.  Streaming kernels: captured at
+# 4096^2 and scaled by 4 to 8192^2 (their traffic grows with the number of nodes);
+# k_resident4: the 256^2 level on 16 CTAs, p = 2, 2000 steps per launch.
+TRAFFIC = {"k_step": 4 * 441.28e6, "k_tblock": 4 * 431.0e6, "k_resident4": 1102592.0}
 
 FP32_LANES_PER_SM = 128  # FP32 units per SM; two flops per FMA
 SM_MAX_MHZ = 2070.0
