@@ -41,6 +41,16 @@ def solve(w1, classes, norm, **opt):
         torch.cuda.synchronize()
         out = [mx.results(c) for c in range(len(classes))]
         pers = [mx.persistent(c) for c in range(len(classes))]
+        info = mx.launch_info()
+    # launch sizes: the coarse launch whenever some persistent class has levels of at
+    # most 1024 nodes; clusters when a persistent class needs them, else single CTAs
+    if any(pers):
+        assert info["coarse_ctas"] > 0
+        big = any(p and nx * ny > 16384 for p, (nx, ny, _) in zip(pers, classes))
+        assert (info["clusters"] > 0) == big
+        assert info["clusters"] > 0 or info["ctas"] > 0
+    else:
+        assert info == {"ctas": 0, "clusters": 0, "coarse_ctas": 0}
     return out, pers, host
 
 
