@@ -844,6 +844,8 @@ def main():
     ap.add_argument("--kiters", type=int, default=1000, help="steps for --only *-kernel")
     ap.add_argument("--knorm", type=int, default=1)
     ap.add_argument("--kcluster", type=int, default=0, help="--only resident-kernel: CTAs per level (0: auto)")
+    ap.add_argument("--kpath3", type=int, default=2, choices=[2, 3],
+                    help="--only 3d-kernel: 2 two launches per step, 3 one launch per step")
     ap.add_argument("--n3", type=int, default=64, help="--only solve3d: grid side of the 3-D solves")
     ap.add_argument("--pairs3", type=int, default=8, help="--only solve3d: pairs per norm")
     ap.add_argument("--roof-n3", type=int, default=256, help="--only solve3d: grid side of the step-kernel timing")
@@ -1113,10 +1115,12 @@ def run_cascade_vs_single(args):
     return 0
 
 
-# Algorithmic bytes per node and step of the two-launch 3-D step: m' reads
-# m1..m3 and phi, writes m1..m3 and mbar (40 B); phi' reads mbar, rho and phi
-# and writes phi (24 B).  Neighbour reads hit cache lines already read.
+# Algorithmic bytes per node and step of the streamed 3-D step.  Two launches:
+# m' reads m1..m3 and phi, writes m1..m3 and mbar (40 B); phi' reads mbar, rho
+# and phi and writes phi (24 B).  One launch: reads m1..m3, phi and rho, writes
+# m1..m3 and phi (36 B).  Neighbour reads hit cache lines already read.
 BYTES3_PER_NODE_STEP = 64.0
+BYTES3_ONE_LAUNCH = 36.0
 
 
 def run_solve3d(args):
@@ -1164,17 +1168,22 @@ def run_solve3d(args):
     st4 = [torch.zeros((rn, rn, rn), device="cuda") for _ in range(4)]
     h = 1.0 / rn
     mu = float(np.float32(0.5 * h / (2 * np.sqrt(3.0))))
-    w1.cp_steps3d(rho, *st4, h, 1, mu, mu, 4, stream=stream)
     steps = 64
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    w1.cp_steps3d(rho, *st4, h, 1, mu, mu, steps, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    us = e0.elapsed_time(e1) * 1e3 / steps
     peak, src = peaks()
-    gbs = BYTES3_PER_NODE_STEP * rn ** 3 / (us * 1e-6) / 1e9
+    kern = {}
+    for path, nbytes in ((2, BYTES3_PER_NODE_STEP), (3, BYTES3_ONE_LAUNCH)):
+        w1.cp_steps3d(rho, *st4, h, 1, mu, mu, 4, path=path, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        w1.cp_steps3d(rho, *st4, h, 1, mu, mu, steps, path=path, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us_p = e0.elapsed_time(e1) * 1e3 / steps
+        gbs_p = nbytes * rn ** 3 / (us_p * 1e-6) / 1e9
+        kern[path] = {"us_per_step": us_p, "alg_bytes_per_step": nbytes * rn ** 3, "achieved_GBps": gbs_p,
+                      "peak_GBps": peak, "frac": gbs_p / peak, "peak_source": src}
+    us, gbs = kern[2]["us_per_step"], kern[2]["achieved_GBps"]
     # oracle on the host: one pair at the solve size, steps timed on a bounded run
     from oracle import d3
     r0, r1 = pairs[0]
@@ -1184,7 +1193,10 @@ def run_solve3d(args):
     cpu_s = time.perf_counter() - t0
     out = {"only": "solve3d", "grid": [n, n, n], "pairs_per_norm": len(dev), "rows": rows,
            "step_kernels": {"grid": [rn, rn, rn], "us_per_step": us, "alg_bytes_per_step": BYTES3_PER_NODE_STEP * rn ** 3,
-                            "achieved_GBps": gbs, "peak_GBps": peak, "frac": gbs / peak, "peak_source": src},
+                            "achieved_GBps": gbs, "peak_GBps": peak, "frac": gbs / peak, "peak_source": src,
+                            "what": "two launches per step (k3_mprime, k3_phi)",
+                            "one_launch": dict(kern[3], what="k3_step: one launch per step, m' recomputed on the "
+                                                             "lower neighbours (36 B per voxel-step)")},
            "cpu_oracle": {"norm": 1, "s_per_solve": cpu_s, "solves_per_s": 1.0 / cpu_s, "cores": 1,
                           "w1_rel_diff_vs_gpu": abs(ref.w1 - rows[0]["w1_pair0"]) / abs(ref.w1),
                           "sample": "pair 0 replaying the GPU's per-level step counts"},
@@ -1412,7 +1424,7 @@ def run_kernel_only(args):
 
     n = args.kn
     if args.only == "3d-kernel":
-        # steps of the 3-D eq. primaldual (two launches each) on an n^3 grid
+        # steps of the 3-D eq. primaldual (two launches each, or one with --kpath3 3) on an n^3 grid
         rng = np.random.default_rng(3)
         rho = torch.from_numpy(rng.normal(size=(n, n, n)).astype(np.float32)).cuda()
         rho -= rho.mean()
@@ -1420,16 +1432,18 @@ def run_kernel_only(args):
         h = 1.0 / n
         mu = float(np.float32(0.5 * h / (2 * np.sqrt(3.0))))
         stream = torch.cuda.current_stream()
-        w1.cp_steps3d(rho, *st4, h, args.knorm, mu, mu, 4, stream=stream)
+        kp = args.kpath3
+        w1.cp_steps3d(rho, *st4, h, args.knorm, mu, mu, 4, path=kp, stream=stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        r = w1.cp_steps3d(rho, *st4, h, args.knorm, mu, mu, args.kiters, stream=stream)
+        r = w1.cp_steps3d(rho, *st4, h, args.knorm, mu, mu, args.kiters, path=kp, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
         us = e0.elapsed_time(e1) * 1e3 / args.kiters
-        print(json.dumps({"only": args.only, "n": n, "norm": args.knorm, "steps": args.kiters, "us_per_step": us,
-                          "alg_GBps": BYTES3_PER_NODE_STEP * n ** 3 / (us * 1e-6) / 1e9, "fpr_last": r}))
+        nb = BYTES3_PER_NODE_STEP if kp == 2 else BYTES3_ONE_LAUNCH
+        print(json.dumps({"only": args.only, "n": n, "norm": args.knorm, "path": kp, "steps": args.kiters,
+                          "us_per_step": us, "alg_GBps": nb * n ** 3 / (us * 1e-6) / 1e9, "fpr_last": r}))
         return 0
     r0, r1 = synth.pair(WORKLOAD, 0, n=n)
     rho = torch.from_numpy(np.ascontiguousarray(r0 - r1 - (r0 - r1).mean(), dtype=np.float32)).cuda()

@@ -480,8 +480,10 @@ const char* w1_noalloc_last_error(void);
  * [nz][ny][nx] FP32 (x fastest), flux components m1, m2, m3 along x, y, z
  * (the last x-, y-, z-face of the grid carries zero flux), sums weighted by
  * h^3, backward-difference divergence and forward-difference gradient,
- * ||A_h|| <= 2 sqrt(3) / h so mu = tau = theta h / (2 sqrt 3).  Each step of
- * eq. primaldual is two launches (m' with the mbar extrapolation, then phi');
+ * ||A_h|| <= 2 sqrt(3) / h so mu = tau = theta h / (2 sqrt 3).  A level too
+ * large for the on-chip kernels streams each step of eq. primaldual through HBM
+ * in one launch (m' recomputed on each voxel's lower neighbours, the new state
+ * written beside the old) or two (m' with the mbar extrapolation, then phi');
  * the host reads R^k of eq. pd_stop after every K-th step.  Every pointer is a
  * device pointer owned by the caller (16-byte alignment not required); the
  * calls allocate their own scratch and synchronise the stream before they
@@ -499,10 +501,12 @@ const char* w1_noalloc_last_error(void);
  * tests in one launch of one CTA or a cluster of up to 16, each holding at most
  * 4096 voxels in registers or, as wide slabs with each thread's own state in
  * tensor memory, 16384 voxels (a multiple of 128; in a cluster nx ny <= 4096);
- * nx % 4 == 0) where it fits and otherwise with two launches per
+ * nx % 4 == 0) where it fits and otherwise with one launch per
  * step and the host testing R^k every K steps; path 1 requires the on-chip
- * kernel (W1_ERR_UNSUPPORTED where a level does not fit); paths 2 and 3 use the
- * two-launch step on every level; time_budget_s applies per level; tune,
+ * kernel (W1_ERR_UNSUPPORTED where a level does not fit); path 2 uses the
+ * two-launch step and path 3 the one-launch step on every level (stats->path:
+ * 1 on chip, 2 two launches, 3 one launch per step); time_budget_s applies per
+ * level; tune,
  * eager and algorithm do not apply).  Writes *dist = f(m) of the
  * finest flux; flux (3n floats: m1, m2, m3 planes) and potential (n floats), when
  * not NULL, receive the finest state; stats: per-level iterations, R^k and eps_l
@@ -524,7 +528,9 @@ void w1_3d_release_workspace(void);
 w1_status w1_cp_steps3d(int nx, int ny, int nz, double h, int norm, float mu, float tau, const float* rho,
                         float* m1, float* m2, float* m3, float* phi, long long iters, void* stream,
                         double* fpr_last);
-/* The same with a choice of kernel: path 2 = two launches per step; path 1 =
+/* The same with a choice of kernel: path 2 = two launches per step; path 3 = one
+ * launch per step (the state alternates with scratch planes and ends in m1, m2,
+ * m3, phi; the new state is bitwise path 2's, R^k may differ in rounding); path 1 =
  * every step in one launch on chip (nx % 4 == 0, a cluster of `cluster` CTAs
  * (0: the library's choice) each holding nz / cluster planes: at most 4096
  * voxels, or 16384 as a wide slab (see w1_solve3d); W1_ERR_UNSUPPORTED when

@@ -3,11 +3,14 @@
 //
 // Voxel-centre grid nx x ny x nz, arrays [nz][ny][nx] (x fastest), flux
 // components m1, m2, m3 along x, y, z with zero flux through the boundary,
-// inner products weighted by h^3.  One step of eq. primaldual is two launches:
-//   k3_mprime  m' = prox_{mu||.||_p}(m + mu grad phi) in place, mbar = 2 m' - m
-//   k3_phi     phi' = phi + tau (div mbar - rho) in place (+ the terms of R^k)
-// (a node's m' needs phi on three neighbours, its phi' needs mbar on three
-// others: the launch boundary is the synchronisation).  Every K-th step forms
+// inner products weighted by h^3.  A streamed step of eq. primaldual is one
+// launch (k3_step: m' at each voxel and its lower neighbours, then phi', from
+// the old state into other buffers) or two (k3_mprime: m' = prox_{mu||.||_p}
+// (m + mu grad phi) in place and mbar = 2 m' - m; k3_phi: phi' = phi + tau
+// (div mbar - rho) in place, + the terms of R^k).  A node's m' needs phi on
+// three neighbours and its phi' needs mbar on three others: the two-launch step
+// synchronises at the launch boundary, the one-launch step recomputes m' on the
+// lower neighbours instead.  Every K-th step forms
 // R^k of eq. pd_stop (FP32 terms and per-thread values, FP64 across blocks) and
 // the host reads it to decide the level's stop, as in the eager mode of the 2-D
 // plans.  Restriction (2x2x2 means), the voxel-centre Interpolate, prep and the
@@ -142,6 +145,104 @@ __global__ void __launch_bounds__(T3) k3_phi(Dims3 d, float tau, float ih, doubl
             const float d1 = dm(b1, m1, q), d2 = dm(b2, m2, q), d3 = dm(b3, m3, q);
             const float dd = (d1 - (i > 0 ? dm(b1, m1, q - 1) : 0.f)) + (d2 - (j > 0 ? dm(b2, m2, q - sy) : 0.f)) +
                              (d3 - (k > 0 ? dm(b3, m3, q - sz) : 0.f));
+            sa = d1 * d1 + d2 * d2 + d3 * d3;
+            sb = dp * dp;
+            sc = dp * dd;  // h <dphi, div dm> before the 1/h
+        }
+    }
+    if (!CHECK) return;
+    __shared__ double sh[64 * 3];
+    __shared__ bool last;
+    double v[3];
+    ff_block_sum3(sa, sb, sc, reinterpret_cast<float*>(sh), v);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x * 3 + 0] = v[0];
+        part[blockIdx.x * 3 + 1] = v[1];
+        part[blockIdx.x * 3 + 2] = v[2];
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    CSum t[3];
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        for (int c = 0; c < 3; ++c) t[c].add(((volatile double*)part)[b * 3 + c]);
+    block_csum<3>(t, sh);
+    if (threadIdx.x == 0) {
+        *r_out = (t[0].value() / mu_d + t[1].value() / tau_d - 2.0 * t[2].value() / h) * h * h * h;
+        *counter = 0;
+    }
+}
+
+// One step of eq. primaldual in one launch, for levels too large for the
+// on-chip kernels.  Each thread forms m' at its voxel and at its three lower
+// neighbours (recomputed there from the old state with k3_mprime's arithmetic),
+// then div mbar (mbar = 2 m' - m) and phi' (k3_phi's arithmetic).  The old
+// state is read and the new one written to other buffers, since neighbours
+// read old values: DRAM moves m, phi and rho in and m', phi' out (36 B per
+// voxel; the two-launch step moves 64 B).  The new state is bitwise the
+// two-launch step's; R^k may differ in rounding (contraction of its sums).
+template <int NORM, bool CHECK>
+__global__ void __launch_bounds__(T3) k3_step(Dims3 d, float mu, float tau, float ih, double mu_d, double tau_d,
+                                               double h, const float* __restrict__ rho,
+                                               const float* __restrict__ m1, const float* __restrict__ m2,
+                                               const float* __restrict__ m3, const float* __restrict__ phi,
+                                               float* __restrict__ n1, float* __restrict__ n2,
+                                               float* __restrict__ n3, float* __restrict__ nphi, double* part,
+                                               unsigned int* counter, double* r_out)
+{
+    const long long q = (long long)blockIdx.x * T3 + threadIdx.x;
+    float sa = 0.f, sb = 0.f, sc = 0.f;
+    if (q < d.n) {
+        int i, j, k;
+        node3(d, q, i, j, k);
+        const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+        // m' at voxel x = (xi, xj, xk) (index x), as k3_mprime forms it
+        auto mprime = [&](long long x, int xi, int xj, int xk, float (&o)[3]) {
+            const float p = phi[x];
+            const bool e1 = xi < d.nx - 1, e2 = xj < d.ny - 1, e3 = xk < d.nz - 1;
+            const float v[3] = {e1 ? fmaf(mu * ih, phi[x + 1] - p, m1[x]) : 0.f,
+                                e2 ? fmaf(mu * ih, phi[x + sy] - p, m2[x]) : 0.f,
+                                e3 ? fmaf(mu * ih, phi[x + sz] - p, m3[x]) : 0.f};
+            prox3<NORM>(v, mu, o);
+            if (!e1) o[0] = 0.f;
+            if (!e2) o[1] = 0.f;
+            if (!e3) o[2] = 0.f;
+        };
+        float o[3];
+        mprime(q, i, j, k, o);
+        const float b1 = 2.f * o[0] - m1[q], b2 = 2.f * o[1] - m2[q], b3 = 2.f * o[2] - m3[q];
+        // the lower neighbours' mbar component across the shared face (and dm there)
+        float l1 = 0.f, l2 = 0.f, l3 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
+        if (i > 0) {
+            float t[3];
+            mprime(q - 1, i - 1, j, k, t);
+            l1 = 2.f * t[0] - m1[q - 1];
+            e1 = l1 - t[0];
+        }
+        if (j > 0) {
+            float t[3];
+            mprime(q - sy, i, j - 1, k, t);
+            l2 = 2.f * t[1] - m2[q - sy];
+            e2 = l2 - t[1];
+        }
+        if (k > 0) {
+            float t[3];
+            mprime(q - sz, i, j, k - 1, t);
+            l3 = 2.f * t[2] - m3[q - sz];
+            e3 = l3 - t[2];
+        }
+        const float dv = (b1 - l1) + (b2 - l2) + (b3 - l3);
+        const float p = phi[q];
+        const float dp = tau * fmaf(dv, ih, -rho[q]);
+        nphi[q] = p + dp;
+        n1[q] = o[0];
+        n2[q] = o[1];
+        n3[q] = o[2];
+        if (CHECK) {
+            const float d1 = b1 - o[0], d2 = b2 - o[1], d3 = b3 - o[2];
+            const float dd = (d1 - e1) + (d2 - e2) + (d3 - e3);
             sa = d1 * d1 + d2 * d2 + d3 * d3;
             sb = dp * dp;
             sc = dp * dd;  // h <dphi, div dm> before the 1/h
@@ -1161,7 +1262,7 @@ static cudaError_t launch_mprime(int norm, const Dims3& d, float mu, float ih, f
 
 // Device scratch of a 3-D call: mbar planes, partials, counter, R^k, certificate.
 struct Scratch3 {
-    float* b = nullptr;      // 3 planes
+    float* b = nullptr;      // 4 planes: mbar (two-launch step) or the other state (one-launch step)
     double* part = nullptr;  // FIN3_PART per block
     unsigned int* counter = nullptr;
     double* r = nullptr;
@@ -1180,7 +1281,7 @@ struct Scratch3 {
     }
     cudaError_t alloc(long long n, bool certificate)
     {
-        cudaError_t e = cudaMalloc(&b, 3 * n * sizeof(float));
+        cudaError_t e = cudaMalloc(&b, 4 * n * sizeof(float));
         const long long blocks = (n + T3 - 1) / T3;
         if (e == cudaSuccess) e = cudaMalloc(&part, blocks * FIN3_PART * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&counter, sizeof(unsigned int));
@@ -1213,6 +1314,46 @@ static cudaError_t steps3(int norm, const Dims3& d, double h, float mu, float ta
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// The same steps with one launch each (k3_step): the state alternates between
+// (m1, m2, m3, phi) and the scratch planes, and ends in (m1, m2, m3, phi).
+template <int NORM>
+static cudaError_t steps3_one_norm(const Dims3& d, double h, float mu, float tau, const float* rho, float* m1,
+                                   float* m2, float* m3, float* phi, long long steps, bool test, Scratch3& sc,
+                                   cudaStream_t s)
+{
+    const float ih = (float)(1.0 / h);
+    const long long n = d.n;
+    float* A[4] = {m1, m2, m3, phi};
+    float* B[4] = {sc.b, sc.b + n, sc.b + 2 * n, sc.b + 3 * n};
+    for (long long k = 0; k < steps; ++k) {
+        float** in = (k & 1) ? B : A;
+        float** out = (k & 1) ? A : B;
+        if (test && k + 1 == steps)
+            k3_step<NORM, true><<<grid3(n), T3, 0, s>>>(d, mu, tau, ih, mu, tau, h, rho, in[0], in[1], in[2], in[3],
+                                                        out[0], out[1], out[2], out[3], sc.part, sc.counter, sc.r);
+        else
+            k3_step<NORM, false><<<grid3(n), T3, 0, s>>>(d, mu, tau, ih, mu, tau, h, rho, in[0], in[1], in[2], in[3],
+                                                         out[0], out[1], out[2], out[3], sc.part, sc.counter, sc.r);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (steps & 1)  // the last step wrote the scratch planes
+        for (int c = 0; c < 4; ++c) {
+            cudaError_t e = cudaMemcpyAsync(A[c], B[c], n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+static cudaError_t steps3_one(int norm, const Dims3& d, double h, float mu, float tau, const float* rho, float* m1,
+                              float* m2, float* m3, float* phi, long long steps, bool test, Scratch3& sc,
+                              cudaStream_t s)
+{
+    if (norm == W1_NORM_L1) return steps3_one_norm<W1_NORM_L1>(d, h, mu, tau, rho, m1, m2, m3, phi, steps, test, sc, s);
+    if (norm == W1_NORM_L2) return steps3_one_norm<W1_NORM_L2>(d, h, mu, tau, rho, m1, m2, m3, phi, steps, test, sc, s);
+    return steps3_one_norm<W1_NORM_LINF>(d, h, mu, tau, rho, m1, m2, m3, phi, steps, test, sc, s);
 }
 
 static cudaError_t final3(int norm, const Dims3& d, double h, const float* m1, const float* m2, const float* m3,
@@ -1324,7 +1465,7 @@ extern "C" w1_status w1_cp_steps3d_ex(int nx, int ny, int nz, double h, int norm
         return fail3(W1_ERR_INVALID_ARG, "bad arguments to w1_cp_steps3d");
     if (norm != W1_NORM_L1 && norm != W1_NORM_L2 && norm != W1_NORM_LINF)
         return fail3(W1_ERR_INVALID_ARG, "norm must be 1, 2 or 3");
-    if (path != 1 && path != 2) return fail3(W1_ERR_INVALID_ARG, "path must be 1 or 2");
+    if (path < 1 || path > 3) return fail3(W1_ERR_INVALID_ARG, "path must be 1, 2 or 3");
     const Dims3 d{nx, ny, nz, (long long)nx * ny * nz};
     Scratch3 sc;
     W1_CK3(sc.alloc(d.n, false));
@@ -1346,7 +1487,8 @@ extern "C" w1_status w1_cp_steps3d_ex(int nx, int ny, int nz, double h, int norm
             r = res.fpr;
         }
     } else {
-        W1_CK3(steps3(norm, d, h, mu, tau, rho, m1, m2, m3, phi, iters, true, sc, s));
+        if (path == 2) W1_CK3(steps3(norm, d, h, mu, tau, rho, m1, m2, m3, phi, iters, true, sc, s));
+        else W1_CK3(steps3_one(norm, d, h, mu, tau, rho, m1, m2, m3, phi, iters, true, sc, s));
         if (iters > 0) W1_CK3(cudaMemcpyAsync(&r, sc.r, sizeof(double), cudaMemcpyDeviceToHost, s));
     }
     W1_CK3(cudaStreamSynchronize(s));
@@ -1474,7 +1616,8 @@ extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, in
         long long it = 0;
         double r = 0.0;
         bool conv = false, late = false;
-        // on chip where the level fits (path 0 or 1), else two launches per step
+        // on chip where the level fits (path 0 or 1); else one launch per step
+        // (path 0 or 3), or two (path 2)
         const int C = (o.path == 0 || o.path == 1) ? r3_choose(norm, d, 0) : 0;
         if (o.path == 1 && C == 0) return fail3(W1_ERR_UNSUPPORTED, "a level does not fit on chip");
         if (late_any) {
@@ -1495,8 +1638,12 @@ extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, in
         } else {
             const auto t0 = std::chrono::steady_clock::now();
             while (it < o.max_iters) {
-                W1_CK3(steps3(norm, d, hl, mu, mu, lvl(l, 0), lvl(l, 1), lvl(l, 2), lvl(l, 3), lvl(l, 4), K, true, sc,
-                              s));
+                if (o.path == 2)
+                    W1_CK3(steps3(norm, d, hl, mu, mu, lvl(l, 0), lvl(l, 1), lvl(l, 2), lvl(l, 3), lvl(l, 4), K, true,
+                                  sc, s));
+                else
+                    W1_CK3(steps3_one(norm, d, hl, mu, mu, lvl(l, 0), lvl(l, 1), lvl(l, 2), lvl(l, 3), lvl(l, 4), K,
+                                      true, sc, s));
                 it += K;
                 W1_CK3(cudaMemcpyAsync(&r, sc.r, sizeof(double), cudaMemcpyDeviceToHost, s));
                 W1_CK3(cudaStreamSynchronize(s));
@@ -1517,7 +1664,7 @@ extern "C" w1_status w1_solve3d(int nx, int ny, int nz, double h, int levels, in
             stats->iters[l] = it;
             stats->fpr[l] = r;
             stats->tol[l] = tl;
-            stats->path[l] = C > 0 ? 1 : 2;
+            stats->path[l] = C > 0 ? 1 : (o.path == 2 ? 2 : 3);  // on chip, two launches, one launch per step
             stats->cluster[l] = C;
         }
         all_conv &= conv;

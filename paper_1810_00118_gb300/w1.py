@@ -505,7 +505,8 @@ def release_workspace3d():
 
 def cp_steps3d(rho, m1, m2, m3, phi, h, norm, mu, tau, iters, path=2, cluster=0, stream=None) -> float:
     """`iters` steps of eq. primaldual on a 3-D level, in place; returns R^k of the
-    last step.  path 2: two launches per step; 1: on chip (cluster CTAs, 0: auto)."""
+    last step.  path 2: two launches per step; 3: one launch per step; 1: on chip
+    (cluster CTAs, 0: auto)."""
     nz, ny, nx = rho.shape
     f = ctypes.c_double(0.0)
     _check3(_lib.w1_cp_steps3d_ex(nx, ny, nz, h, norm, mu, tau, _dev_ptr(rho),

@@ -59,9 +59,12 @@ SHAPES3 = [(1, 1, 1), (2, 3, 5), (9, 10, 11), (16, 16, 16), (3, 40, 33), (1, 1, 
            (33, 17, 64)]
 
 
+@pytest.mark.parametrize("path", [2, 3])
 @pytest.mark.parametrize("norm", [L1, L2, LINF])
 @pytest.mark.parametrize("shape", SHAPES3)
-def test_cp_steps3d_match_oracle(w1, norm, shape):
+def test_cp_steps3d_match_oracle(w1, norm, shape, path):
+    """Streamed steps, two launches (path 2) or one (path 3) per step, against the
+    oracle: 7 steps (an odd count, so the one-launch step copies its state back)."""
     nz, ny, nx = shape
     rng = np.random.default_rng(nx * 10007 + ny * 101 + nz + norm)
     rho, m1, m2, m3, phi = rand_state3(rng, nz, ny, nx)
@@ -69,7 +72,7 @@ def test_cp_steps3d_match_oracle(w1, norm, shape):
     mu = mu3(h)
     t = [dev(a) for a in (rho, m1, m2, m3, phi)]
     steps = 7
-    r = w1.cp_steps3d(*t, h, norm, mu, mu, steps)
+    r = w1.cp_steps3d(*t, h, norm, mu, mu, steps, path=path)
     o1, o2, o3, op, rf = d3.cp_iterate(rho.astype(np.float64), m1, m2, m3, phi, h, norm, steps, mu=mu, tau=mu)
     for got, want in zip(t[1:], (o1, o2, o3, op)):
         g = host(got)
@@ -163,16 +166,16 @@ def flux3_rel_l1(f, ref):
     return num / sum(np.abs(w).sum() for w in (ref.m1, ref.m2, ref.m3))
 
 
-@pytest.mark.parametrize("path", [0, 2])
+@pytest.mark.parametrize("path", [0, 2, 3])
 @pytest.mark.parametrize("norm", [L1, L2, LINF])
 def test_solve3d_16_two_levels(w1, norm, path):
     """16^3, two levels 8^3 -> 16^3, default tolerance of eq. stop_tol; both
-    levels on chip (path 0) or two launches per step (path 2)."""
+    levels on chip (path 0), two launches per step (path 2) or one (path 3)."""
     r0, r1 = synth.pair3(16, norm)
     val, st, status, flux, phi, ref = solve3_and_replay(w1, r0, r1, norm, 2, path=path)
     assert status == w1.OK and st.converged
     assert st.levels == 2 and st.sizes == [(8, 8), (16, 16)]
-    assert st.path == ([1, 1] if path == 0 else [2, 2])
+    assert st.path == ([1, 1] if path == 0 else [path, path])
     assert all(k % 32 == 0 and k > 0 for k in st.iters)
     assert val == st.w1
     assert abs(val - ref.w1) <= 1e-4 * abs(ref.w1), (val, ref.w1)
@@ -311,3 +314,23 @@ def test_solve3d_max_iters_reports_not_converged(w1):
     val, st, status = w1.solve3d(dev(r0), dev(r1), norm=L1, levels=1, tol=1e-30, max_iters=64)
     assert status == w1.ERR_NOT_CONVERGED and not st.converged
     assert st.iters == [64] and np.isfinite(val) and st.lb <= st.ub
+
+
+@pytest.mark.parametrize("norm", [L1, L2, LINF])
+@pytest.mark.parametrize("shape,steps", [((24, 20, 36), 6), ((9, 13, 7), 5)])
+def test_one_launch_step_equals_two_launch_step(w1, norm, shape, steps):
+    """The one-launch step recomputes m' on each voxel's lower neighbours with the
+    two-launch step's arithmetic: the new state is the same bit for bit (even and
+    odd step counts); R^k agrees to rounding."""
+    nz, ny, nx = shape
+    rng = np.random.default_rng(nx + 31 * ny + 977 * nz + norm)
+    rho, m1, m2, m3, phi = rand_state3(rng, nz, ny, nx)
+    h = 1.0 / max(shape)
+    mu = mu3(h)
+    a = [dev(x) for x in (rho, m1, m2, m3, phi)]
+    b = [dev(x) for x in (rho, m1, m2, m3, phi)]
+    ra = w1.cp_steps3d(*a, h, norm, mu, mu, steps, path=2)
+    rb = w1.cp_steps3d(*b, h, norm, mu, mu, steps, path=3)
+    for x, y in zip(a[1:], b[1:]):
+        assert np.array_equal(host(x), host(y))
+    assert rb == pytest.approx(ra, rel=1e-5, abs=1e-14)
