@@ -130,9 +130,10 @@ __global__ void __launch_bounds__(T3) k3_phi(Dims3 d, float tau, float ih, doubl
                                               const float* __restrict__ m2, const float* __restrict__ m3,
                                               double* part, unsigned int* counter, double* r_out)
 {
-    const long long q = (long long)blockIdx.x * T3 + threadIdx.x;
     float sa = 0.f, sb = 0.f, sc = 0.f;
-    if (q < d.n) {
+    // one voxel per thread; a test step runs on fewer blocks, its threads taking
+    // several voxels (see check_grid3)
+    auto voxel = [&](const long long q) {
         int i, j, k;
         node3(d, q, i, j, k);
         const long long sy = d.nx, sz = (long long)d.nx * d.ny;
@@ -145,10 +146,16 @@ __global__ void __launch_bounds__(T3) k3_phi(Dims3 d, float tau, float ih, doubl
             const float d1 = dm(b1, m1, q), d2 = dm(b2, m2, q), d3 = dm(b3, m3, q);
             const float dd = (d1 - (i > 0 ? dm(b1, m1, q - 1) : 0.f)) + (d2 - (j > 0 ? dm(b2, m2, q - sy) : 0.f)) +
                              (d3 - (k > 0 ? dm(b3, m3, q - sz) : 0.f));
-            sa = d1 * d1 + d2 * d2 + d3 * d3;
-            sb = dp * dp;
-            sc = dp * dd;  // h <dphi, div dm> before the 1/h
+            sa += d1 * d1 + d2 * d2 + d3 * d3;
+            sb += dp * dp;
+            sc += dp * dd;  // h <dphi, div dm> before the 1/h
         }
+    };
+    if (CHECK) {
+        for (long long q = (long long)blockIdx.x * T3 + threadIdx.x; q < d.n; q += (long long)gridDim.x * T3) voxel(q);
+    } else {
+        const long long q = (long long)blockIdx.x * T3 + threadIdx.x;
+        if (q < d.n) voxel(q);
     }
     if (!CHECK) return;
     __shared__ double sh[64 * 3];
@@ -192,9 +199,10 @@ __global__ void __launch_bounds__(T3) k3_step(Dims3 d, float mu, float tau, floa
                                                float* __restrict__ n3, float* __restrict__ nphi, double* part,
                                                unsigned int* counter, double* r_out)
 {
-    const long long q = (long long)blockIdx.x * T3 + threadIdx.x;
     float sa = 0.f, sb = 0.f, sc = 0.f;
-    if (q < d.n) {
+    // one voxel per thread; a test step runs on fewer blocks, its threads taking
+    // several voxels (see check_grid3)
+    auto voxel = [&](const long long q) {
         int i, j, k;
         node3(d, q, i, j, k);
         const long long sy = d.nx, sz = (long long)d.nx * d.ny;
@@ -243,10 +251,16 @@ __global__ void __launch_bounds__(T3) k3_step(Dims3 d, float mu, float tau, floa
         if (CHECK) {
             const float d1 = b1 - o[0], d2 = b2 - o[1], d3 = b3 - o[2];
             const float dd = (d1 - e1) + (d2 - e2) + (d3 - e3);
-            sa = d1 * d1 + d2 * d2 + d3 * d3;
-            sb = dp * dp;
-            sc = dp * dd;  // h <dphi, div dm> before the 1/h
+            sa += d1 * d1 + d2 * d2 + d3 * d3;
+            sb += dp * dp;
+            sc += dp * dd;  // h <dphi, div dm> before the 1/h
         }
+    };
+    if (CHECK) {
+        for (long long q = (long long)blockIdx.x * T3 + threadIdx.x; q < d.n; q += (long long)gridDim.x * T3) voxel(q);
+    } else {
+        const long long q = (long long)blockIdx.x * T3 + threadIdx.x;
+        if (q < d.n) voxel(q);
     }
     if (!CHECK) return;
     __shared__ double sh[64 * 3];
@@ -1260,6 +1274,21 @@ static cudaError_t launch_mprime(int norm, const Dims3& d, float mu, float ih, f
     return cudaGetLastError();
 }
 
+// Blocks of a test step: every block leaves FP64 partials that the last block
+// adds up on one SM, where FP64 runs at a small fraction of the FP32 rate, so a
+// test step runs on at most 8 blocks per SM (threads then take several voxels).
+static unsigned check_grid3(long long n)
+{
+    int dev = 0, sms = 0;
+    const unsigned full = grid3(n).x;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return full;
+    }
+    const unsigned cap = 8u * (unsigned)sms;
+    return full < cap ? full : cap;
+}
+
 // Device scratch of a 3-D call: mbar planes, partials, counter, R^k, certificate.
 struct Scratch3 {
     float* b = nullptr;      // 4 planes: mbar (two-launch step) or the other state (one-launch step)
@@ -1305,7 +1334,7 @@ static cudaError_t steps3(int norm, const Dims3& d, double h, float mu, float ta
         cudaError_t e = launch_mprime(norm, d, mu, ih, m1, m2, m3, phi, b1, b2, b3, s);
         if (e != cudaSuccess) return e;
         if (test && k + 1 == steps)
-            k3_phi<true><<<grid3(n), T3, 0, s>>>(d, tau, ih, mu, tau, h, rho, phi, b1, b2, b3, m1, m2, m3, sc.part,
+            k3_phi<true><<<check_grid3(n), T3, 0, s>>>(d, tau, ih, mu, tau, h, rho, phi, b1, b2, b3, m1, m2, m3, sc.part,
                                                  sc.counter, sc.r);
         else
             k3_phi<false><<<grid3(n), T3, 0, s>>>(d, tau, ih, mu, tau, h, rho, phi, b1, b2, b3, m1, m2, m3, sc.part,
@@ -1331,7 +1360,7 @@ static cudaError_t steps3_one_norm(const Dims3& d, double h, float mu, float tau
         float** in = (k & 1) ? B : A;
         float** out = (k & 1) ? A : B;
         if (test && k + 1 == steps)
-            k3_step<NORM, true><<<grid3(n), T3, 0, s>>>(d, mu, tau, ih, mu, tau, h, rho, in[0], in[1], in[2], in[3],
+            k3_step<NORM, true><<<check_grid3(n), T3, 0, s>>>(d, mu, tau, ih, mu, tau, h, rho, in[0], in[1], in[2], in[3],
                                                         out[0], out[1], out[2], out[3], sc.part, sc.counter, sc.r);
         else
             k3_step<NORM, false><<<grid3(n), T3, 0, s>>>(d, mu, tau, ih, mu, tau, h, rho, in[0], in[1], in[2], in[3],
