@@ -140,6 +140,7 @@ TOL_SCALE = {1: 30.0, 2: 3.0}
 ALPHA = {1: 0.5, 2: -1.0}  # eps_l = eps_L (h_l / h)^alpha (eq. tol_formula_propose)
 THETA = {1: 1.0, 2: 1.0}   # mu tau = (theta / ||A_h||)^2 (eq. primaldual; 1/2 the paper's, 1 its footnote's)
 RATIO = {1: 1.0, 2: 0.02}  # tau / mu (1: mu = tau, the paper's)
+CHECK_EVERY = 64  # steps between stop tests under the calibrated schedule (the library's default there)
 
 
 def stop_tol(n: int, norm: int) -> float:
@@ -156,7 +157,7 @@ def _oracle_solve(spec):
     _, _, d0, d1 = synth.to_f32_pair(r0, r1)
     t0 = time.perf_counter()
     res = oracle.multilevel(d0, d1, levels=levels, norm=norm, tol=stop_tol(n, norm), alpha=ALPHA[norm],
-                            theta=THETA[norm], ratio=RATIO[norm], stop=oracle.STOP_FPR)
+                            theta=THETA[norm], ratio=RATIO[norm], stop=oracle.STOP_FPR, check_every=CHECK_EVERY)
     return norm, time.perf_counter() - t0, res.status
 
 
@@ -645,7 +646,8 @@ def run_gpu(args):
                                 + json.dumps({f"L{k}": v for k, v in TOL_SCALE.items()}) + ", alpha "
                                 + json.dumps({f"L{k}": v for k, v in ALPHA.items()}) + ", theta "
                                 + json.dumps({f"L{k}": v for k, v in THETA.items()}) + ", tau / mu "
-                                + json.dumps({f"L{k}": v for k, v in RATIO.items()}))
+                                + json.dumps({f"L{k}": v for k, v in RATIO.items()})
+                                + f", tested every {args.check_every or CHECK_EVERY} steps")
                        if args.algorithm == 3 else "eq. stop_tol for Algorithm 4",
                        "tol": {f"L{k}": v for k, v in tol.items()},
                        "estimate": "saddle value: Lagrangian of eq. minmax_cp at the returned pair",
@@ -823,7 +825,8 @@ def main():
     ap.add_argument("--tune", type=int, default=0, choices=[0, 1, 2, 3],
                     help="lanes: per-level kernel choice (0 fixed rules, 1 latency, 3 SM-time; see w1_options.tune)")
     ap.add_argument("--check-every", type=int, default=0,
-                    help="steps between stop tests (multiple of 8; 0: 32 for Algorithm 3, 8 for Algorithm 4)")
+                    help="steps between stop tests (multiple of 8; 0: the library's default, 64 for Algorithm 3 "
+                         "under the calibrated schedule, 8 for Algorithm 4)")
     ap.add_argument("--algorithm", type=int, default=3, choices=[3, 4],
                     help="3: multilevel Chambolle-Pock (the headline); 4: multilevel prox-PDHG")
     ap.add_argument("--eager", action="store_true",

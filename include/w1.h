@@ -70,7 +70,8 @@ typedef enum {
 /* Plan options; w1_default_options() fills the defaults given here. */
 typedef struct {
     int check_every;       /* K: steps between stop tests, a multiple of 8; 0 (default): 32
-                              for Algorithm 3, 8 for Algorithm 4                            */
+                              for Algorithm 3 (64 with schedule = 1 for p = 1, 2), 8 for
+                              Algorithm 4                                                    */
     long long max_iters;   /* cap on steps per level (default 1000000)                        */
     double theta;          /* mu = tau = theta / ||A_h||, ||A_h|| <= 2 sqrt(2) / h (Sec. 4);
                               0.5 is the paper's choice (default), 1.0 its footnote's         */
